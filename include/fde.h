@@ -1,0 +1,185 @@
+/*
+ * fde.h -- C ABI of the GB300 (sm_103a) Strang-preconditioned BVM/GMRES solver
+ * for one-dimensional two-sided space-fractional diffusion equations.
+ *
+ * Method: X.-M. Gu, T.-Z. Huang, X.-L. Zhao, H.-B. Li, L. Li, "Strang-type
+ * preconditioners for solving fractional diffusion equations by boundary value
+ * methods" (arXiv:1305.6653).  Equation numbers are the paper's labels.
+ *
+ *   Problem (Sec. 2, eq. (1.1)):
+ *     u_t = d+(x) D^alpha_+ u + d-(x) D^alpha_- u + f(x,t),  x in (xL,xR), t in (t0,T],
+ *     u(xL,t) = u(xR,t) = 0,  u(x,t0) = u0(x),  1 < alpha < 2,  d+, d- >= 0, d+ + d- != 0.
+ *   Space (Sec. 2.1, eqs. (1.2)-(1.5)): m interior points, dx = (xR-xL)/(m+1),
+ *     J = dx^-alpha (D+ G + D- G^T), G the shifted-Grunwald Toeplitz matrix.
+ *   Time (Sec. 2.2, eqs. (1.7)-(1.10)): s steps, h = (T-t0)/s, a mu-step BVM with
+ *     nu initial and mu-nu final conditions; all time levels at once:
+ *     M u = (A (x) I - h B (x) J) u = b.
+ *     The given u_0 is eliminated, so the unknowns are u_1..u_s (n = s*m values),
+ *     stored time-major: x[(t-1)*m + (i-1)] = u_i at time level t.
+ *   Preconditioner (Sec. 3.1, eq. (1.11)): S = s(A) (x) I - h s(B) (x) J, applied as
+ *     a length-s FFT along time, s/2+1 dense complex solves with
+ *     phi_k I - h psi_k J (LU factored once), and an inverse FFT (Sec. 3.2).
+ *   Solver (Sec. 3.2, Sec. 4): restarted GMRES; here the flexible, right-
+ *     preconditioned form with FP64 Arnoldi (CGS2), FP64 Givens least squares and
+ *     an FP64 true-residual check at every restart.
+ *
+ * Conventions for every entry point:
+ *   - Return value: FDE_OK (0) on success, a negative FDE_ERR_* code otherwise.
+ *     The message of the last error on the calling thread is fde_last_error().
+ *   - Pointers marked "device" are CUDA device pointers of the current device;
+ *     pointers marked "host" are ordinary host memory.  Pointers in a
+ *     fde_problem_desc are host or device according to desc->device_ptrs.
+ *   - All work is enqueued on the CUDA stream given to fde_problem_create (NULL =
+ *     the legacy default stream).  Entry points that return results to the host
+ *     (pgmres_solve's stats, fde_last_error) synchronise that stream.
+ *   - Calls on one fde_problem are not thread-safe; distinct problems are
+ *     independent.  No entry point falls back to a CPU implementation: if the
+ *     GPU path cannot run, the call fails with FDE_ERR_CUDA.
+ */
+#ifndef FDE_H_
+#define FDE_H_
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define FDE_OK 0
+#define FDE_ERR_ARG (-1)           /* invalid argument (message says which) */
+#define FDE_ERR_ALLOC (-2)         /* device allocation failed */
+#define FDE_ERR_CUDA (-3)          /* a CUDA runtime call or kernel failed */
+#define FDE_ERR_SINGULAR (-4)      /* zero / non-finite pivot in a block LU */
+#define FDE_ERR_NOT_CONVERGED (-5) /* maxit reached before the tolerance */
+#define FDE_ERR_NAN (-6)           /* non-finite residual or Hessenberg entry */
+#define FDE_ERR_STATE (-7)         /* call order violated (e.g. solve before factor) */
+#define FDE_ERR_TIMEOUT (-8)       /* a bounded device wait ran out */
+
+/* ---- BVM families (Sec. 2.2; Sec. 4 uses the fifth-order GAM, mu = 4) ---- */
+#define FDE_GBDF 1 /* generalised BDF: beta = e_nu, order mu */
+#define FDE_GAM 2  /* generalised Adams: rho(z) = z^nu - z^(nu-1), order mu+1 */
+#define FDE_ETR 3  /* extended trapezoidal rule: the GAM with odd mu (symmetric) */
+
+/* ---- precision of the preconditioner (block LU, its solves, the time FFT) */
+#define FDE_FP64 0 /* everything in FP64: the plain method */
+#define FDE_FP32 1 /* FP32 factors computed on CUDA cores */
+#define FDE_TF32 2 /* FP32 factors, trailing updates on tcgen05 tensor cores (TF32 in, FP32 acc) */
+#define FDE_BF16 3 /* FP32 factors, trailing updates on tcgen05 tensor cores (BF16 in, FP32 acc) */
+
+/* Limits of this implementation. */
+#define FDE_MAX_MU 6      /* BVM steps */
+#define FDE_MAX_S 1024    /* time steps; s must be a power of two, s >= 2*mu */
+#define FDE_MAX_M 4095    /* interior points; the Toeplitz FFT length is <= 8192 */
+
+/* Problem description (eq. (1.1) on the grid of Sec. 2.1/2.2).  Copied by
+ * fde_problem_create; the caller may free its buffers afterwards. */
+typedef struct {
+    int m;          /* interior spatial points N (Sec. 2.1), 1 <= m <= FDE_MAX_M */
+    int s;          /* time steps (Sec. 2.2), power of two, 2*mu <= s <= FDE_MAX_S */
+    double alpha;   /* fractional order, 1 < alpha < 2 */
+    double xL, xR;  /* spatial interval, xL < xR */
+    double t0, T;   /* time interval, t0 < T */
+    const double* dplus;  /* length m: d+(x_i), i = 1..m, or NULL to use dplus_c */
+    const double* dminus; /* length m: d-(x_i), or NULL to use dminus_c */
+    double dplus_c, dminus_c; /* constant coefficients used when the arrays are NULL */
+    int family;     /* FDE_GBDF, FDE_GAM or FDE_ETR */
+    int mu;         /* number of steps, 1 <= mu <= FDE_MAX_MU (ETR: odd) */
+    const double* u0; /* length m: u0(x_i) */
+    const double* f;  /* length (s+1)*m, row-major [n][i]: f(x_i, t_n), n = 0..s */
+    int device_ptrs;  /* 0: dplus/dminus/u0/f are host pointers, 1: device pointers */
+} fde_problem_desc;
+
+/* Options of pgmres_solve. */
+typedef struct {
+    double tol;    /* stop when ||b - M x||_2 <= tol * ||b||_2 (true FP64 residual) */
+    int restart;   /* Krylov subspace size per cycle (the paper uses 20) */
+    int maxit;     /* cap on the total number of inner iterations */
+    int reorth;    /* 1: classical Gram-Schmidt with one re-orthogonalisation (CGS2); 0: CGS */
+} fde_pgmres_opts;
+
+/* Statistics returned by pgmres_solve. */
+typedef struct {
+    int status;          /* FDE_OK or the FDE_ERR_* code also returned */
+    int iterations;      /* total inner (Arnoldi) iterations, the paper's ITS */
+    int restarts;        /* completed restart cycles */
+    int precision;       /* precision of the factors used */
+    double rel_residual; /* final ||b - M x|| / ||b|| (FP64, recomputed) */
+    double rel_residual_estimate; /* final Givens estimate of the last cycle */
+    double ms_solve;     /* device time of the solve (CUDA events) */
+} fde_stats;
+
+typedef struct fde_problem fde_problem;
+
+/* Validate desc (alpha in (1,2), d+/d- >= 0 with d+ + d- != 0 at every point,
+ * sizes, scheme, finite inputs), copy its arrays to the device and derive the BVM
+ * coefficients of eqs. (1.7)-(1.9) (exact rationals) and the Strang symbols.
+ * stream: a cudaStream_t (NULL = default stream).  *out receives the handle, owned
+ * by the caller and released with fde_problem_destroy.  Errors: FDE_ERR_ARG,
+ * FDE_ERR_ALLOC, FDE_ERR_CUDA. */
+int fde_problem_create(const fde_problem_desc* desc, void* stream, fde_problem** out);
+
+/* Assemble the space-time system (eqs. (1.2)-(1.5), (1.10)): Grunwald weights
+ * g_0..g_{m+1} (eq. (1.2) recurrence), the FFT symbol of the circulant embedding
+ * of G, and the right-hand side b = -A[:,0] (x) u0 + h B[:,0] (x) (J u0 + f_0)
+ * + h (B[:,1:] (x) I) f_{1:s}.  M itself is never formed.  Errors: FDE_ERR_CUDA. */
+int bvm_assemble(fde_problem* p);
+
+/* Form and factor the s/2+1 distinct Strang blocks phi_k I - h psi_k J
+ * (eq. (1.11), Sec. 3.2) by blocked complex LU without pivoting (the blocks are
+ * strictly row diagonally dominant), in the given precision (FDE_FP64, FDE_FP32,
+ * FDE_TF32, FDE_BF16).  The library owns the factors (FP64: 16*(s/2+1)*mp^2
+ * bytes, otherwise 8*(s/2+1)*mp^2, mp = m rounded up to 64).  Requires
+ * bvm_assemble.  Errors: FDE_ERR_ARG, FDE_ERR_ALLOC, FDE_ERR_SINGULAR,
+ * FDE_ERR_STATE, FDE_ERR_CUDA. */
+int strang_precond_factor(fde_problem* p, int precision);
+
+/* Solve M u = b by flexible GMRES(restart) right-preconditioned with S.
+ * x0: device, length s*m initial guess, or NULL for zero.  x_out: device, length
+ * s*m (may alias x0).  st: host, may be NULL.  On FDE_ERR_NOT_CONVERGED x_out
+ * holds the last iterate.  Requires strang_precond_factor.  Errors: FDE_ERR_ARG,
+ * FDE_ERR_STATE, FDE_ERR_NOT_CONVERGED, FDE_ERR_NAN, FDE_ERR_CUDA. */
+int pgmres_solve(fde_problem* p, const fde_pgmres_opts* opts, const double* x0, double* x_out,
+                 fde_stats* st);
+
+/* Release the handle and every device buffer it owns.  NULL is ignored. */
+void fde_problem_destroy(fde_problem* p);
+
+/* Message of the last error on this thread ("" if none).  Owned by the library. */
+const char* fde_last_error(void);
+
+/* ---- step-level entry points (the same kernels the solver runs) ---------- */
+
+/* y = M z (eq. (1.10), u_0 eliminated) in FP64 on the device: the band of A and B
+ * along time and J applied to all s time columns through the FFT of the Toeplitz
+ * circulant embedding (Sec. 2.1).  z, y: device, length s*m, must not alias.
+ * Requires bvm_assemble.  Errors: FDE_ERR_STATE, FDE_ERR_CUDA. */
+int fde_matvec(fde_problem* p, const double* z, double* y);
+
+/* z = S^{-1} r with the current factors (Sec. 3.2): FFT along time, the s/2+1
+ * block solves, inverse FFT.  r, z: device, length s*m (may alias).  Requires
+ * strang_precond_factor.  Errors: FDE_ERR_STATE, FDE_ERR_CUDA. */
+int fde_precond_apply(fde_problem* p, const double* r, double* z);
+
+/* Copy the assembled right-hand side b (device, length s*m).  Requires
+ * bvm_assemble.  Errors: FDE_ERR_STATE, FDE_ERR_CUDA. */
+int fde_get_rhs(fde_problem* p, double* b);
+
+/* Copy the packed LU factors of Strang block k (0 <= k <= s/2) to host memory as
+ * FP64 complex: re and im, each m*m row-major (unit-lower L below the diagonal,
+ * U on and above it).  Requires strang_precond_factor.  Errors: FDE_ERR_ARG,
+ * FDE_ERR_STATE, FDE_ERR_CUDA. */
+int fde_get_factor_block(fde_problem* p, int k, double* re, double* im);
+
+/* Copy the Grunwald weights g_0..g_{m+1} (host, m+2 values) computed on the
+ * device by the recurrence of eq. (1.2).  Errors: FDE_ERR_STATE, FDE_ERR_CUDA. */
+int fde_get_grunwald(fde_problem* p, double* g);
+
+/* Sizes of a created problem: n = s*m unknowns, number of Strang blocks s/2+1. */
+int fde_problem_sizes(const fde_problem* p, int* m, int* s, int* nblocks);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FDE_H_ */

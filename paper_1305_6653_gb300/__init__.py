@@ -1,0 +1,189 @@
+"""GB300-native Strang-preconditioned BVM/GMRES solver for space-fractional diffusion.
+
+Method: Gu, Huang, Zhao, Li & Li, "Strang-type preconditioners for solving
+fractional diffusion equations by boundary value methods" (arXiv:1305.6653).
+
+The compute path is libfde.so (CUDA, sm_103a) behind the C ABI of include/fde.h.
+This package is the thin Python binding: it marshals arguments (PyTorch only
+provides device memory and the CUDA stream) and calls the library with the same
+entry-point names.  Importing the package does not load the library; the first
+call does, and fails loudly if it is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+from . import _lib
+from ._lib import (FDE_BF16, FDE_ETR, FDE_FP32, FDE_FP64, FDE_GAM, FDE_GBDF, FDE_TF32, FdeError,  # noqa: F401
+                   FdePgmresOpts, FdeProblemDesc, FdeStats, PRECISIONS, FAMILIES)
+
+__all__ = ["FDEProblem", "fde_problem_create", "bvm_assemble", "strang_precond_factor", "pgmres_solve",
+           "fde_problem_destroy", "fde_matvec", "fde_precond_apply", "FdeError", "PRECISIONS"]
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_handle(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+# ---- thin wrappers with the C-ABI names ------------------------------------
+
+def fde_problem_create(desc: FdeProblemDesc, stream=None) -> C.c_void_p:
+    h = C.c_void_p()
+    _lib.check(_lib.load().fde_problem_create(C.byref(desc), _stream_handle(stream), C.byref(h)),
+               "fde_problem_create")
+    return h
+
+
+def bvm_assemble(h) -> None:
+    _lib.check(_lib.load().bvm_assemble(h), "bvm_assemble")
+
+
+def strang_precond_factor(h, precision) -> None:
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    _lib.check(_lib.load().strang_precond_factor(h, prec), "strang_precond_factor")
+
+
+def pgmres_solve(h, opts: FdePgmresOpts, x0_ptr: int | None, x_ptr: int, raise_on_error: bool = True) -> FdeStats:
+    st = FdeStats()
+    rc = _lib.load().pgmres_solve(h, C.byref(opts), C.c_void_p(x0_ptr) if x0_ptr else None, C.c_void_p(x_ptr),
+                                  C.byref(st))
+    if raise_on_error:
+        _lib.check(rc, "pgmres_solve")
+    return st
+
+
+def fde_problem_destroy(h) -> None:
+    if h:
+        _lib.load().fde_problem_destroy(h)
+
+
+def fde_matvec(h, z_ptr: int, y_ptr: int) -> None:
+    _lib.check(_lib.load().fde_matvec(h, C.c_void_p(z_ptr), C.c_void_p(y_ptr)), "fde_matvec")
+
+
+def fde_precond_apply(h, r_ptr: int, z_ptr: int) -> None:
+    _lib.check(_lib.load().fde_precond_apply(h, C.c_void_p(r_ptr), C.c_void_p(z_ptr)), "fde_precond_apply")
+
+
+# ---- convenience object ------------------------------------------------------
+
+class FDEProblem:
+    """One instance of eq. (1.1) on the device.
+
+    Inputs (dplus, dminus, u0, f) may be numpy arrays (host, copied by the
+    library) or CUDA float64 tensors (device).  Vectors returned are CUDA
+    float64 tensors of length s*m, time-major (u_1 .. u_s).
+    """
+
+    def __init__(self, *, m, s, alpha, xL, xR, t0, T, dplus, dminus, u0, f, family, mu, stream=None,
+                 device_inputs: bool | None = None):
+        torch = _torch()
+        self.m, self.s = int(m), int(s)
+        self.n = self.m * self.s
+        self.stream = stream
+        fam = FAMILIES[family] if isinstance(family, str) else int(family)
+        keep = []
+
+        def ptr(a):
+            if a is None:
+                return None
+            if isinstance(a, torch.Tensor):
+                t = a.contiguous().to(torch.float64)
+                keep.append(t)
+                return t.data_ptr()
+            import numpy as np
+            arr = np.ascontiguousarray(a, dtype=np.float64)
+            keep.append(arr)
+            return arr.ctypes.data
+
+        if device_inputs is None:
+            device_inputs = isinstance(u0, torch.Tensor) and u0.is_cuda
+        self.desc = FdeProblemDesc(self.m, self.s, float(alpha), float(xL), float(xR), float(t0), float(T),
+                                   ptr(dplus), ptr(dminus), 0.0, 0.0, fam, int(mu), ptr(u0), ptr(f),
+                                   1 if device_inputs else 0)
+        self.h = fde_problem_create(self.desc, stream)
+        del keep
+
+    @classmethod
+    def from_inputs(cls, prob, stream=None, device_inputs: bool = False):
+        """Build from an fde_inputs.Problem (host arrays unless device_inputs)."""
+        torch = _torch()
+        fam, mu = prob.family, prob.mu
+        arrays = dict(dplus=prob.dplus, dminus=prob.dminus, u0=prob.u0, f=prob.f)
+        if device_inputs:
+            arrays = {k: torch.as_tensor(v, dtype=torch.float64, device="cuda") for k, v in arrays.items()}
+        return cls(m=prob.m, s=prob.s, alpha=prob.alpha, xL=prob.xL, xR=prob.xR, t0=prob.t0, T=prob.T,
+                   family=fam, mu=mu, stream=stream, device_inputs=device_inputs, **arrays)
+
+    def assemble(self):
+        bvm_assemble(self.h)
+        return self
+
+    def factor(self, precision="fp64"):
+        strang_precond_factor(self.h, precision)
+        return self
+
+    def solve(self, tol=1e-10, restart=20, maxit=1000, reorth=1, x0=None, out=None, raise_on_error=True):
+        torch = _torch()
+        x = out if out is not None else torch.empty(self.n, dtype=torch.float64, device="cuda")
+        opts = FdePgmresOpts(float(tol), int(restart), int(maxit), int(reorth))
+        st = pgmres_solve(self.h, opts, x0.data_ptr() if x0 is not None else None, x.data_ptr(),
+                          raise_on_error=raise_on_error)
+        return x, st.as_dict()
+
+    def matvec(self, z):
+        torch = _torch()
+        y = torch.empty(self.n, dtype=torch.float64, device="cuda")
+        fde_matvec(self.h, z.data_ptr(), y.data_ptr())
+        return y
+
+    def precond_apply(self, r):
+        torch = _torch()
+        z = torch.empty(self.n, dtype=torch.float64, device="cuda")
+        fde_precond_apply(self.h, r.data_ptr(), z.data_ptr())
+        return z
+
+    def rhs(self):
+        torch = _torch()
+        b = torch.empty(self.n, dtype=torch.float64, device="cuda")
+        _lib.check(_lib.load().fde_get_rhs(self.h, C.c_void_p(b.data_ptr())), "fde_get_rhs")
+        return b
+
+    def grunwald(self):
+        import numpy as np
+        g = np.empty(self.m + 2)
+        _lib.check(_lib.load().fde_get_grunwald(self.h, C.c_void_p(g.ctypes.data)), "fde_get_grunwald")
+        return g
+
+    def factor_block(self, k):
+        import numpy as np
+        re = np.empty((self.m, self.m))
+        im = np.empty((self.m, self.m))
+        _lib.check(_lib.load().fde_get_factor_block(self.h, int(k), C.c_void_p(re.ctypes.data),
+                                                     C.c_void_p(im.ctypes.data)), "fde_get_factor_block")
+        return re + 1j * im
+
+    def close(self):
+        if getattr(self, "h", None):
+            fde_problem_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,112 @@
+"""ctypes binding of libfde.so (include/fde.h).  Argument marshalling only: every
+numerical step runs in the library's CUDA kernels.  There is no CPU fallback; if
+the library is missing, loading it raises."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfde.so")
+
+FDE_OK = 0
+FDE_ERR_ARG = -1
+FDE_ERR_ALLOC = -2
+FDE_ERR_CUDA = -3
+FDE_ERR_SINGULAR = -4
+FDE_ERR_NOT_CONVERGED = -5
+FDE_ERR_NAN = -6
+FDE_ERR_STATE = -7
+FDE_ERR_TIMEOUT = -8
+
+FDE_GBDF, FDE_GAM, FDE_ETR = 1, 2, 3
+FDE_FP64, FDE_FP32, FDE_TF32, FDE_BF16 = 0, 1, 2, 3
+PRECISIONS = {"fp64": FDE_FP64, "fp32": FDE_FP32, "tf32": FDE_TF32, "bf16": FDE_BF16}
+FAMILIES = {"GBDF": FDE_GBDF, "GAM": FDE_GAM, "ETR": FDE_ETR}
+
+ERROR_NAMES = {
+    FDE_ERR_ARG: "FDE_ERR_ARG", FDE_ERR_ALLOC: "FDE_ERR_ALLOC", FDE_ERR_CUDA: "FDE_ERR_CUDA",
+    FDE_ERR_SINGULAR: "FDE_ERR_SINGULAR", FDE_ERR_NOT_CONVERGED: "FDE_ERR_NOT_CONVERGED",
+    FDE_ERR_NAN: "FDE_ERR_NAN", FDE_ERR_STATE: "FDE_ERR_STATE", FDE_ERR_TIMEOUT: "FDE_ERR_TIMEOUT",
+}
+
+# Every symbol declared in include/fde.h (checked by the CPU tests).
+EXPORTED = [
+    "fde_problem_create", "bvm_assemble", "strang_precond_factor", "pgmres_solve", "fde_problem_destroy",
+    "fde_last_error", "fde_matvec", "fde_precond_apply", "fde_get_rhs", "fde_get_factor_block",
+    "fde_get_grunwald", "fde_problem_sizes",
+]
+
+
+class FdeProblemDesc(C.Structure):
+    _fields_ = [
+        ("m", C.c_int), ("s", C.c_int), ("alpha", C.c_double), ("xL", C.c_double), ("xR", C.c_double),
+        ("t0", C.c_double), ("T", C.c_double), ("dplus", C.c_void_p), ("dminus", C.c_void_p),
+        ("dplus_c", C.c_double), ("dminus_c", C.c_double), ("family", C.c_int), ("mu", C.c_int),
+        ("u0", C.c_void_p), ("f", C.c_void_p), ("device_ptrs", C.c_int),
+    ]
+
+
+class FdePgmresOpts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("restart", C.c_int), ("maxit", C.c_int), ("reorth", C.c_int)]
+
+
+class FdeStats(C.Structure):
+    _fields_ = [
+        ("status", C.c_int), ("iterations", C.c_int), ("restarts", C.c_int), ("precision", C.c_int),
+        ("rel_residual", C.c_double), ("rel_residual_estimate", C.c_double), ("ms_solve", C.c_double),
+    ]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class FdeError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str):
+        super().__init__(f"{where}: {ERROR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> C.CDLL:
+    """Load libfde.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build() "
+                           "(there is no CPU fallback)")
+    lib = C.CDLL(path)
+    vp, i32, f64 = C.c_void_p, C.c_int, C.c_double
+    sig = {
+        "fde_problem_create": (i32, [C.POINTER(FdeProblemDesc), vp, C.POINTER(vp)]),
+        "bvm_assemble": (i32, [vp]),
+        "strang_precond_factor": (i32, [vp, i32]),
+        "pgmres_solve": (i32, [vp, C.POINTER(FdePgmresOpts), vp, vp, C.POINTER(FdeStats)]),
+        "fde_problem_destroy": (None, [vp]),
+        "fde_last_error": (C.c_char_p, []),
+        "fde_matvec": (i32, [vp, vp, vp]),
+        "fde_precond_apply": (i32, [vp, vp, vp]),
+        "fde_get_rhs": (i32, [vp, vp]),
+        "fde_get_factor_block": (i32, [vp, i32, vp, vp]),
+        "fde_get_grunwald": (i32, [vp, vp]),
+        "fde_problem_sizes": (i32, [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def last_error() -> str:
+    return load().fde_last_error().decode()
+
+
+def check(code: int, where: str) -> int:
+    if code != FDE_OK:
+        raise FdeError(code, where, last_error())
+    return code

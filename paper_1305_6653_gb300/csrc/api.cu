@@ -1,0 +1,647 @@
+// C ABI of libfde (declared in include/fde.h): problem lifecycle, BVM coefficient
+// derivation, and the host driver of the flexible GMRES iteration.  All numerical
+// work of the path runs in the kernels of the other translation units.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "fde_internal.h"
+
+namespace fde {
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_last_error;
+
+int set_error(int code, const std::string& msg) {
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_error(cudaError_t e, const char* what) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return FDE_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// exact rational arithmetic for the BVM coefficients (Sec. 2.2)
+// ---------------------------------------------------------------------------
+struct Rat {
+    __int128 p = 0, q = 1;
+};
+static __int128 gcd128(__int128 a, __int128 b) {
+    if (a < 0) a = -a;
+    if (b < 0) b = -b;
+    while (b != 0) {
+        __int128 t = a % b;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+static Rat norm(Rat r) {
+    if (r.q < 0) { r.p = -r.p; r.q = -r.q; }
+    __int128 g = gcd128(r.p, r.q);
+    if (g > 1) { r.p /= g; r.q /= g; }
+    if (r.p == 0) r.q = 1;
+    return r;
+}
+static Rat R(long v) { Rat r; r.p = v; r.q = 1; return r; }
+static Rat add(Rat a, Rat b) { Rat r; r.p = a.p * b.q + b.p * a.q; r.q = a.q * b.q; return norm(r); }
+static Rat sub(Rat a, Rat b) { b.p = -b.p; return add(a, b); }
+static Rat mul(Rat a, Rat b) { Rat r; r.p = a.p * b.p; r.q = a.q * b.q; return norm(r); }
+static Rat dvd(Rat a, Rat b) { Rat r; r.p = a.p * b.q; r.q = a.q * b.p; return norm(r); }
+static double to_d(Rat a) { return (double)a.p / (double)a.q; }
+static Rat ipow(long base, int e) {
+    Rat r = R(1);
+    for (int i = 0; i < e; ++i) r = mul(r, R(base));
+    return r;
+}
+
+// Solve the (n x n) system a x = b exactly (Gauss-Jordan with a nonzero pivot).
+static bool solve_exact(std::vector<std::vector<Rat>> a, std::vector<Rat> b, std::vector<Rat>& x) {
+    const int n = (int)b.size();
+    for (int c = 0; c < n; ++c) {
+        int piv = -1;
+        for (int r = c; r < n; ++r)
+            if (a[r][c].p != 0) { piv = r; break; }
+        if (piv < 0) return false;
+        std::swap(a[c], a[piv]);
+        std::swap(b[c], b[piv]);
+        for (int r = 0; r < n; ++r) {
+            if (r == c || a[r][c].p == 0) continue;
+            Rat f = dvd(a[r][c], a[c][c]);
+            for (int k = c; k < n; ++k) a[r][k] = sub(a[r][k], mul(f, a[c][k]));
+            b[r] = sub(b[r], mul(f, b[c]));
+        }
+    }
+    x.resize(n);
+    for (int i = 0; i < n; ++i) x[i] = dvd(b[i], a[i][i]);
+    return true;
+}
+
+static int nu_for(int family, int mu) {
+    if (family == FDE_GBDF) return (mu % 2) ? (mu + 1) / 2 : mu / 2 + 1;
+    if (family == FDE_GAM) return (mu % 2) ? (mu + 1) / 2 : mu / 2;
+    if (family == FDE_ETR) return (mu % 2) ? (mu + 1) / 2 : -1;
+    return -1;
+}
+
+// Coefficients of the mu-step formula on points 0..mu approximating u' at point ell.
+// Order conditions sum_i a_i i^q = q sum_i b_i i^(q-1):
+//   GBDF: b = e_ell, q = 0..mu;  GAM/ETR: a = e_ell - e_{ell-1}, q = 1..mu+1.
+static bool formula(int family, int mu, int ell, double* a, double* b) {
+    std::vector<Rat> av(mu + 1, R(0)), bv(mu + 1, R(0));
+    const int n = mu + 1;
+    std::vector<std::vector<Rat>> mat(n, std::vector<Rat>(n));
+    std::vector<Rat> rhs(n), sol;
+    if (family == FDE_GBDF) {
+        bv[ell] = R(1);
+        for (int q = 0; q <= mu; ++q) {
+            for (int i = 0; i <= mu; ++i) mat[q][i] = ipow(i, q);
+            rhs[q] = q == 0 ? R(0) : mul(R(q), ipow(ell, q - 1));
+        }
+        if (!solve_exact(mat, rhs, sol)) return false;
+        av = sol;
+    } else {
+        av[ell] = R(1);
+        av[ell - 1] = R(-1);
+        for (int q = 1; q <= mu + 1; ++q) {
+            for (int i = 0; i <= mu; ++i) mat[q - 1][i] = mul(R(q), ipow(i, q - 1));
+            rhs[q - 1] = sub(ipow(ell, q), ipow(ell - 1, q));
+        }
+        if (!solve_exact(mat, rhs, sol)) return false;
+        bv = sol;
+    }
+    for (int i = 0; i <= mu; ++i) {
+        a[i] = to_d(av[i]);
+        b[i] = to_d(bv[i]);
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+template <typename T>
+static int dalloc(T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) return FDE_OK;
+    cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return set_error(FDE_ERR_ALLOC, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+    }
+    return FDE_OK;
+}
+
+static void dfree(void* p) {
+    if (p) cudaFree(p);
+}
+
+static void free_workspace(Problem& P) {
+    dfree(P.d_V); dfree(P.d_Z); dfree(P.d_H); dfree(P.d_cs); dfree(P.d_sn); dfree(P.d_gv); dfree(P.d_y);
+    P.d_V = P.d_Z = P.d_H = P.d_cs = P.d_sn = P.d_gv = P.d_y = nullptr;
+    P.restart_cap = 0;
+}
+
+static int ensure_workspace(Problem& P, int restart) {
+    if (P.restart_cap >= restart) return FDE_OK;
+    free_workspace(P);
+    int rc;
+    if ((rc = dalloc(&P.d_V, (size_t)(restart + 1) * P.n))) return rc;
+    if ((rc = dalloc(&P.d_Z, (size_t)restart * P.n))) return rc;
+    if ((rc = dalloc(&P.d_H, (size_t)(restart + 1) * restart))) return rc;
+    if ((rc = dalloc(&P.d_cs, (size_t)restart))) return rc;
+    if ((rc = dalloc(&P.d_sn, (size_t)restart))) return rc;
+    if ((rc = dalloc(&P.d_gv, (size_t)restart + 1))) return rc;
+    if ((rc = dalloc(&P.d_y, (size_t)restart))) return rc;
+    P.restart_cap = restart;
+    return FDE_OK;
+}
+
+static int apply_precond(Problem& P, const double* r, double* z) {
+    int rc;
+    if ((rc = launch_time_fft_fwd(P, r, P.d_rhat, P.precision, P.stream))) return rc;
+    if ((rc = launch_block_trsv(P, P.d_rhat, P.stream))) return rc;
+    return launch_time_fft_inv(P, P.d_rhat, z, P.precision, P.stream);
+}
+
+// ||v||^2 on the device into d_scal[slot]; optionally returned to the host (synchronises).
+static int norm2(Problem& P, const double* v, int slot, double* host_out, double* pinned) {
+    int rc = launch_norm(v, P.n, P.d_scal + slot, P.d_partial, P.d_counter, P.stream);
+    if (rc) return rc;
+    if (host_out) {
+        FDE_CUDA_TRY(cudaMemcpyAsync(pinned, P.d_scal + slot, sizeof(double), cudaMemcpyDeviceToHost, P.stream));
+        FDE_CUDA_TRY(cudaStreamSynchronize(P.stream));
+        *host_out = *pinned;
+    }
+    return FDE_OK;
+}
+
+}  // namespace fde
+
+using namespace fde;
+
+struct fde_problem {
+    Problem P;
+    double* pinned = nullptr;  // small pinned host buffer for device -> host scalars
+};
+
+extern "C" {
+
+const char* fde_last_error(void) { return g_last_error.c_str(); }
+
+int fde_problem_create(const fde_problem_desc* d, void* stream, fde_problem** out) {
+    g_last_error.clear();
+    if (!d || !out) return set_error(FDE_ERR_ARG, "desc and out must not be NULL");
+    *out = nullptr;
+    if (d->m < 1 || d->m > FDE_MAX_M) return set_error(FDE_ERR_ARG, "m out of range [1, FDE_MAX_M]");
+    if (d->s < 2 || d->s > FDE_MAX_S || (d->s & (d->s - 1)))
+        return set_error(FDE_ERR_ARG, "s must be a power of two in [2, FDE_MAX_S]");
+    if (!(d->alpha > 1.0 && d->alpha < 2.0)) return set_error(FDE_ERR_ARG, "alpha must lie in (1, 2)");
+    if (!(d->xR > d->xL) || !std::isfinite(d->xL) || !std::isfinite(d->xR))
+        return set_error(FDE_ERR_ARG, "need finite xL < xR");
+    if (!(d->T > d->t0) || !std::isfinite(d->t0) || !std::isfinite(d->T))
+        return set_error(FDE_ERR_ARG, "need finite t0 < T");
+    if (d->mu < 1 || d->mu > FDE_MAX_MU) return set_error(FDE_ERR_ARG, "mu out of range [1, FDE_MAX_MU]");
+    const int nu = nu_for(d->family, d->mu);
+    if (nu < 0) return set_error(FDE_ERR_ARG, "unknown BVM family or ETR with even mu");
+    if (d->s < 2 * d->mu) return set_error(FDE_ERR_ARG, "need s >= 2*mu");
+    if (!d->u0 || !d->f) return set_error(FDE_ERR_ARG, "u0 and f must not be NULL");
+
+    fde_problem* h = new (std::nothrow) fde_problem();
+    if (!h) return set_error(FDE_ERR_ALLOC, "host allocation failed");
+    Problem& P = h->P;
+    P.m = d->m;
+    P.s = d->s;
+    P.mu = d->mu;
+    P.nu = nu;
+    P.family = d->family;
+    P.alpha = d->alpha;
+    P.xL = d->xL; P.xR = d->xR; P.t0 = d->t0; P.T = d->T;
+    P.dx = (d->xR - d->xL) / (d->m + 1);
+    P.h = (d->T - d->t0) / d->s;
+    P.dxa = std::pow(P.dx, -d->alpha);
+    P.L = 1;
+    while (P.L < 2 * P.m) P.L <<= 1;
+    if (P.L < 2) P.L = 2;
+    P.logL = ilog2(P.L);
+    P.logs = ilog2(P.s);
+    P.nblk = P.s / 2 + 1;
+    P.mp = round_up(P.m, 64);
+    P.n = (long)P.m * P.s;
+    P.stream = (cudaStream_t)stream;
+
+    // BVM band rows t = 1..s (eqs. (1.7)-(1.9)); row 0 is the initial condition.
+    std::vector<double> ha((size_t)(P.s + 1) * (P.mu + 1), 0.0), hb((size_t)(P.s + 1) * (P.mu + 1), 0.0);
+    std::vector<int> hst(P.s + 1, 0);
+    ha[0] = 1.0;
+    for (int t = 1; t <= P.s; ++t) {
+        int st;
+        if (t < nu) st = 0;
+        else if (t <= P.s - P.mu + nu) st = t - nu;
+        else st = P.s - P.mu;
+        hst[t] = st;
+        if (!formula(P.family, P.mu, t - st, &ha[(size_t)t * (P.mu + 1)], &hb[(size_t)t * (P.mu + 1)])) {
+            delete h;
+            return set_error(FDE_ERR_ARG, "BVM order conditions are singular");
+        }
+    }
+    if (!formula(P.family, P.mu, nu, P.h_a_main, P.h_b_main)) {
+        delete h;
+        return set_error(FDE_ERR_ARG, "BVM order conditions are singular");
+    }
+    for (int t = 0; t <= P.s; ++t) P.h_start[t] = hst[t];
+
+    // validate coefficient arrays on the host when they are host pointers
+    const size_t m = P.m;
+    std::vector<double> dp(m), dm(m);
+    auto fetch = [&](const double* src, double cval, std::vector<double>& dst) -> int {
+        if (!src) {
+            for (size_t i = 0; i < m; ++i) dst[i] = cval;
+            return FDE_OK;
+        }
+        if (d->device_ptrs) {
+            cudaError_t e = cudaMemcpy(dst.data(), src, m * sizeof(double), cudaMemcpyDefault);
+            if (e != cudaSuccess) return cuda_error(e, "copy of d+/d-");
+        } else {
+            std::memcpy(dst.data(), src, m * sizeof(double));
+        }
+        return FDE_OK;
+    };
+    int rc;
+    if ((rc = fetch(d->dplus, d->dplus_c, dp)) || (rc = fetch(d->dminus, d->dminus_c, dm))) {
+        delete h;
+        return rc;
+    }
+    for (size_t i = 0; i < m; ++i) {
+        if (!(dp[i] >= 0.0) || !(dm[i] >= 0.0) || !(dp[i] + dm[i] > 0.0) || !std::isfinite(dp[i]) ||
+            !std::isfinite(dm[i])) {
+            delete h;
+            return set_error(FDE_ERR_ARG, "need d+ >= 0, d- >= 0, d+ + d- != 0 and finite at every point");
+        }
+    }
+    if (!d->device_ptrs) {
+        for (size_t i = 0; i < m; ++i)
+            if (!std::isfinite(d->u0[i])) { delete h; return set_error(FDE_ERR_ARG, "u0 is not finite"); }
+        for (size_t i = 0; i < (size_t)(P.s + 1) * m; ++i)
+            if (!std::isfinite(d->f[i])) { delete h; return set_error(FDE_ERR_ARG, "f is not finite"); }
+    }
+
+#define TRY(x)            \
+    do {                  \
+        rc = (x);         \
+        if (rc) {         \
+            fde_problem_destroy(h); \
+            return rc;    \
+        }                 \
+    } while (0)
+    TRY(dalloc(&P.d_start, P.s + 1));
+    TRY(dalloc(&P.d_a, ha.size()));
+    TRY(dalloc(&P.d_b, hb.size()));
+    TRY(dalloc(&P.d_dplus, m));
+    TRY(dalloc(&P.d_dminus, m));
+    TRY(dalloc(&P.d_u0, m));
+    TRY(dalloc(&P.d_f, (size_t)(P.s + 1) * m));
+    TRY(dalloc(&P.d_g, m + 2));
+    TRY(dalloc(&P.d_twL, (size_t)P.L / 2 + 1));
+    TRY(dalloc(&P.d_twL32, (size_t)P.L / 2 + 1));
+    TRY(dalloc(&P.d_sym, (size_t)P.L));
+    TRY(dalloc(&P.d_sym32, (size_t)P.L));
+    TRY(dalloc(&P.d_tws, (size_t)P.s / 2 + 1));
+    TRY(dalloc(&P.d_tws32, (size_t)P.s / 2 + 1));
+    TRY(dalloc(&P.d_phi, (size_t)P.nblk));
+    TRY(dalloc(&P.d_psi, (size_t)P.nblk));
+    TRY(dalloc(&P.d_b_rhs, (size_t)P.n));
+    TRY(dalloc(&P.d_work, (size_t)P.n));
+    TRY(dalloc(&P.d_scal, 256));
+    TRY(dalloc(&P.d_partial, (size_t)304 * 64));
+    TRY(dalloc(&P.d_counter, 4));
+    TRY(dalloc(&P.d_info, (size_t)P.nblk));
+    if (cudaMallocHost((void**)&h->pinned, 64 * sizeof(double)) != cudaSuccess) {
+        h->pinned = nullptr;
+        fde_problem_destroy(h);
+        return set_error(FDE_ERR_ALLOC, "cudaMallocHost failed");
+    }
+    cudaStream_t st = P.stream;
+    const cudaMemcpyKind kind = cudaMemcpyDefault;
+#define CUTRY(x)                                  \
+    do {                                          \
+        cudaError_t e_ = (x);                     \
+        if (e_ != cudaSuccess) {                  \
+            rc = cuda_error(e_, #x);              \
+            fde_problem_destroy(h);               \
+            return rc;                            \
+        }                                         \
+    } while (0)
+    CUTRY(cudaMemcpyAsync(P.d_start, hst.data(), (P.s + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
+    CUTRY(cudaMemcpyAsync(P.d_a, ha.data(), ha.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    CUTRY(cudaMemcpyAsync(P.d_b, hb.data(), hb.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    CUTRY(cudaMemcpyAsync(P.d_dplus, dp.data(), m * sizeof(double), cudaMemcpyHostToDevice, st));
+    CUTRY(cudaMemcpyAsync(P.d_dminus, dm.data(), m * sizeof(double), cudaMemcpyHostToDevice, st));
+    CUTRY(cudaMemcpyAsync(P.d_u0, d->u0, m * sizeof(double), kind, st));
+    CUTRY(cudaMemcpyAsync(P.d_f, d->f, (size_t)(P.s + 1) * m * sizeof(double), kind, st));
+    CUTRY(cudaMemsetAsync(P.d_counter, 0, 4 * sizeof(unsigned int), st));
+    CUTRY(cudaMemsetAsync(P.d_scal, 0, 256 * sizeof(double), st));
+    // host vectors go out of scope: wait for the copies
+    CUTRY(cudaStreamSynchronize(st));
+#undef CUTRY
+#undef TRY
+    *out = h;
+    return FDE_OK;
+}
+
+void fde_problem_destroy(fde_problem* h) {
+    if (!h) return;
+    Problem& P = h->P;
+    if (P.stream) cudaStreamSynchronize(P.stream);
+    else cudaDeviceSynchronize();
+    free_workspace(P);
+    void* bufs[] = {P.d_start, P.d_a, P.d_b, P.d_dplus, P.d_dminus, P.d_u0, P.d_f, P.d_g, P.d_twL, P.d_twL32,
+                    P.d_sym, P.d_sym32, P.d_tws, P.d_tws32, P.d_phi, P.d_psi, P.d_b_rhs, P.d_work, P.d_rhat,
+                    P.d_fac, P.d_dinv, P.d_info, P.d_scal, P.d_partial, P.d_counter};
+    for (void* b : bufs) dfree(b);
+    if (h->pinned) cudaFreeHost(h->pinned);
+    delete h;
+}
+
+int fde_problem_sizes(const fde_problem* h, int* m, int* s, int* nblocks) {
+    if (!h) return set_error(FDE_ERR_ARG, "NULL problem");
+    if (m) *m = h->P.m;
+    if (s) *s = h->P.s;
+    if (nblocks) *nblocks = h->P.nblk;
+    return FDE_OK;
+}
+
+int bvm_assemble(fde_problem* h) {
+    g_last_error.clear();
+    if (!h) return set_error(FDE_ERR_ARG, "NULL problem");
+    Problem& P = h->P;
+    int rc;
+    double* d_main = nullptr;
+    if ((rc = launch_grunwald(P.alpha, P.m + 2, P.d_g, P.stream))) return rc;
+    if ((rc = launch_twiddles(P.L, P.d_twL, P.d_twL32, P.stream))) return rc;
+    if ((rc = launch_twiddles(P.s, P.d_tws, P.d_tws32, P.stream))) return rc;
+    if ((rc = launch_toeplitz_symbol(P.d_g, P.m, P.L, P.dxa, P.d_twL, P.d_sym, P.d_sym32, nullptr, P.stream)))
+        return rc;
+    // main-formula coefficients for the Strang symbols
+    if ((rc = dalloc(&d_main, 2 * (FDE_MAX_MU + 1)))) return rc;
+    double hm[2 * (FDE_MAX_MU + 1)];
+    for (int i = 0; i <= P.mu; ++i) {
+        hm[i] = P.h_a_main[i];
+        hm[FDE_MAX_MU + 1 + i] = P.h_b_main[i];
+    }
+    cudaError_t e = cudaMemcpyAsync(d_main, hm, sizeof(hm), cudaMemcpyHostToDevice, P.stream);
+    if (e == cudaSuccess)
+        rc = launch_strang_symbols(d_main, d_main + FDE_MAX_MU + 1, P.mu, P.nu, P.s, P.d_phi, P.d_psi, P.stream);
+    else
+        rc = cuda_error(e, "copy of BVM coefficients");
+    if (!rc) {
+        e = cudaStreamSynchronize(P.stream);  // hm is a stack buffer; d_main is freed below
+        if (e != cudaSuccess) rc = cuda_error(e, "bvm_assemble");
+    }
+    cudaFree(d_main);
+    if (rc) return rc;
+    // J u0 (one Toeplitz-like apply), then b
+    if ((rc = launch_japply64(P, P.d_u0, P.d_work, 1, P.stream))) return rc;
+    if ((rc = launch_rhs(P, P.d_work, P.stream))) return rc;
+    FDE_CUDA_TRY(cudaGetLastError());
+    P.assembled = true;
+    return FDE_OK;
+}
+
+int strang_precond_factor(fde_problem* h, int precision) {
+    g_last_error.clear();
+    if (!h) return set_error(FDE_ERR_ARG, "NULL problem");
+    Problem& P = h->P;
+    if (!P.assembled) return set_error(FDE_ERR_STATE, "bvm_assemble must run before strang_precond_factor");
+    if (precision != FDE_FP64 && precision != FDE_FP32)
+        return set_error(FDE_ERR_ARG, "precision not supported by this build");
+    const size_t esz = precision == FDE_FP64 ? sizeof(double) : sizeof(float);
+    const size_t fac_bytes = (size_t)P.nblk * 2 * P.mp * P.mp * esz;
+    int rc;
+    if (P.d_fac && (P.fac_bytes != fac_bytes || P.precision != precision)) {
+        dfree(P.d_fac); dfree(P.d_dinv); dfree(P.d_rhat);
+        P.d_fac = P.d_dinv = P.d_rhat = nullptr;
+    }
+    if (!P.d_fac) {
+        unsigned char* f = nullptr;
+        if ((rc = dalloc(&f, fac_bytes))) return rc;
+        P.d_fac = f;
+        P.fac_bytes = fac_bytes;
+        unsigned char* dv = nullptr;
+        if ((rc = dalloc(&dv, (size_t)P.nblk * P.mp * 2 * esz))) return rc;
+        P.d_dinv = dv;
+        unsigned char* rh = nullptr;
+        if ((rc = dalloc(&rh, (size_t)P.nblk * P.mp * 2 * esz))) return rc;
+        P.d_rhat = rh;
+    }
+    P.factored = false;
+    P.precision = precision;
+    FDE_CUDA_TRY(cudaMemsetAsync(P.d_info, 0, P.nblk * sizeof(int), P.stream));
+    if ((rc = launch_block_lu(P, precision, P.stream))) return rc;
+    std::vector<int> info(P.nblk);
+    FDE_CUDA_TRY(cudaMemcpyAsync(info.data(), P.d_info, P.nblk * sizeof(int), cudaMemcpyDeviceToHost, P.stream));
+    FDE_CUDA_TRY(cudaStreamSynchronize(P.stream));
+    for (int k = 0; k < P.nblk; ++k)
+        if (info[k]) {
+            char buf[128];
+            std::snprintf(buf, sizeof buf, "zero or non-finite pivot in Strang block %d at row %d", k, info[k] - 1);
+            return set_error(FDE_ERR_SINGULAR, buf);
+        }
+    P.factored = true;
+    return FDE_OK;
+}
+
+int fde_matvec(fde_problem* h, const double* z, double* y) {
+    g_last_error.clear();
+    if (!h || !z || !y) return set_error(FDE_ERR_ARG, "NULL argument");
+    if (!h->P.assembled) return set_error(FDE_ERR_STATE, "bvm_assemble must run first");
+    return launch_matvec64(h->P, z, y, h->P.stream);
+}
+
+int fde_precond_apply(fde_problem* h, const double* r, double* z) {
+    g_last_error.clear();
+    if (!h || !r || !z) return set_error(FDE_ERR_ARG, "NULL argument");
+    if (!h->P.factored) return set_error(FDE_ERR_STATE, "strang_precond_factor must run first");
+    return apply_precond(h->P, r, z);
+}
+
+int fde_get_rhs(fde_problem* h, double* b) {
+    g_last_error.clear();
+    if (!h || !b) return set_error(FDE_ERR_ARG, "NULL argument");
+    if (!h->P.assembled) return set_error(FDE_ERR_STATE, "bvm_assemble must run first");
+    FDE_CUDA_TRY(cudaMemcpyAsync(b, h->P.d_b_rhs, h->P.n * sizeof(double), cudaMemcpyDeviceToDevice, h->P.stream));
+    return FDE_OK;
+}
+
+int fde_get_grunwald(fde_problem* h, double* g) {
+    g_last_error.clear();
+    if (!h || !g) return set_error(FDE_ERR_ARG, "NULL argument");
+    if (!h->P.assembled) return set_error(FDE_ERR_STATE, "bvm_assemble must run first");
+    FDE_CUDA_TRY(cudaMemcpyAsync(g, h->P.d_g, (h->P.m + 2) * sizeof(double), cudaMemcpyDeviceToHost, h->P.stream));
+    FDE_CUDA_TRY(cudaStreamSynchronize(h->P.stream));
+    return FDE_OK;
+}
+
+int fde_get_factor_block(fde_problem* h, int k, double* re, double* im) {
+    g_last_error.clear();
+    if (!h || !re || !im) return set_error(FDE_ERR_ARG, "NULL argument");
+    Problem& P = h->P;
+    if (!P.factored) return set_error(FDE_ERR_STATE, "strang_precond_factor must run first");
+    if (k < 0 || k >= P.nblk) return set_error(FDE_ERR_ARG, "block index out of range");
+    const size_t mp2 = (size_t)P.mp * P.mp;
+    const bool f64 = P.precision == FDE_FP64;
+    const size_t esz = f64 ? 8 : 4;
+    std::vector<unsigned char> buf(2 * mp2 * esz);
+    const unsigned char* src = (const unsigned char*)P.d_fac + (size_t)k * 2 * mp2 * esz;
+    FDE_CUDA_TRY(cudaMemcpyAsync(buf.data(), src, buf.size(), cudaMemcpyDeviceToHost, P.stream));
+    FDE_CUDA_TRY(cudaStreamSynchronize(P.stream));
+    for (int i = 0; i < P.m; ++i)
+        for (int j = 0; j < P.m; ++j) {
+            const size_t e = (size_t)i * P.mp + j;
+            if (f64) {
+                re[(size_t)i * P.m + j] = ((const double*)buf.data())[e];
+                im[(size_t)i * P.m + j] = ((const double*)buf.data())[mp2 + e];
+            } else {
+                re[(size_t)i * P.m + j] = ((const float*)buf.data())[e];
+                im[(size_t)i * P.m + j] = ((const float*)buf.data())[mp2 + e];
+            }
+        }
+    return FDE_OK;
+}
+
+int pgmres_solve(fde_problem* h, const fde_pgmres_opts* opts, const double* x0, double* x, fde_stats* stats) {
+    g_last_error.clear();
+    if (!h || !x) return set_error(FDE_ERR_ARG, "NULL argument");
+    Problem& P = h->P;
+    if (!P.factored) return set_error(FDE_ERR_STATE, "strang_precond_factor must run before pgmres_solve");
+    fde_pgmres_opts o{1e-10, 20, 1000, 1};
+    if (opts) o = *opts;
+    if (!(o.tol > 0.0) || o.restart < 1 || o.restart > 63 || o.maxit < 1)
+        return set_error(FDE_ERR_ARG, "need tol > 0, 1 <= restart <= 63, maxit >= 1");
+    int rc = ensure_workspace(P, o.restart);
+    if (rc) return rc;
+    cudaStream_t st = P.stream;
+    const long n = P.n;
+    double* pin = h->pinned;
+    cudaEvent_t ev0, ev1;
+    FDE_CUDA_TRY(cudaEventCreate(&ev0));
+    FDE_CUDA_TRY(cudaEventCreate(&ev1));
+    FDE_CUDA_TRY(cudaEventRecord(ev0, st));
+
+    fde_stats S;
+    std::memset(&S, 0, sizeof S);
+    S.precision = P.precision;
+    double* V = P.d_V;
+    double* Z = P.d_Z;
+    double* sc = P.d_scal;
+    const int ldh = o.restart + 1;
+    int status = FDE_OK;
+    double bnorm2 = 0, beta2 = 0;
+
+    auto finish = [&](int code) -> int {
+        cudaEventRecord(ev1, st);
+        cudaEventSynchronize(ev1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, ev0, ev1);
+        cudaEventDestroy(ev0);
+        cudaEventDestroy(ev1);
+        S.ms_solve = ms;
+        S.status = code;
+        if (stats) *stats = S;
+        return code;
+    };
+
+    if (x0 && x0 != x) {
+        cudaError_t e = cudaMemcpyAsync(x, x0, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return finish(cuda_error(e, "copy of x0"));
+    } else if (!x0) {
+        cudaError_t e = cudaMemsetAsync(x, 0, n * sizeof(double), st);
+        if (e != cudaSuccess) return finish(cuda_error(e, "zero x"));
+    }
+    if ((rc = norm2(P, P.d_b_rhs, 131, &bnorm2, pin))) return finish(rc);
+    const double bnorm = std::sqrt(bnorm2);
+    if (!std::isfinite(bnorm)) return finish(set_error(FDE_ERR_NAN, "right-hand side is not finite"));
+    if (bnorm == 0.0) {
+        cudaMemsetAsync(x, 0, n * sizeof(double), st);
+        S.rel_residual = 0.0;
+        return finish(FDE_OK);
+    }
+    // r = b - M x -> V_0
+    if (x0) {
+        if ((rc = launch_matvec64(P, x, P.d_work, st))) return finish(rc);
+        if ((rc = launch_sub(P.d_b_rhs, P.d_work, V, n, st))) return finish(rc);
+    } else {
+        cudaError_t e = cudaMemcpyAsync(V, P.d_b_rhs, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return finish(cuda_error(e, "copy of b"));
+    }
+    if ((rc = norm2(P, V, 132, &beta2, pin))) return finish(rc);
+    int its = 0;
+    std::vector<double> g0(o.restart + 1, 0.0);
+    double est = 0.0;
+    for (;;) {
+        const double beta = std::sqrt(beta2);
+        S.rel_residual = beta / bnorm;
+        if (!std::isfinite(beta)) { status = set_error(FDE_ERR_NAN, "residual is not finite"); break; }
+        if (beta <= o.tol * bnorm) { status = FDE_OK; break; }
+        if (its >= o.maxit) {
+            status = set_error(FDE_ERR_NOT_CONVERGED, "maxit reached before the tolerance");
+            break;
+        }
+        if ((rc = launch_scale(V, sc + 132, V, n, st))) return finish(rc);
+        g0[0] = beta;
+        std::fill(g0.begin() + 1, g0.end(), 0.0);
+        FDE_CUDA_TRY(cudaMemcpyAsync(P.d_gv, g0.data(), g0.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+        int j = 0;
+        for (; j < o.restart; ++j) {
+            double* vj = V + (size_t)j * n;
+            double* w = V + (size_t)(j + 1) * n;
+            double* zj = Z + (size_t)j * n;
+            if ((rc = apply_precond(P, vj, zj))) return finish(rc);
+            if ((rc = launch_matvec64(P, zj, w, st))) return finish(rc);
+            if ((rc = launch_dots(V, j + 1, w, n, sc, P.d_partial, P.d_counter, st))) return finish(rc);
+            if ((rc = launch_update(V, j + 1, sc, -1.0, w, n, st))) return finish(rc);
+            if (o.reorth) {
+                if ((rc = launch_dots(V, j + 1, w, n, sc + 64, P.d_partial, P.d_counter, st))) return finish(rc);
+                if ((rc = launch_update(V, j + 1, sc + 64, -1.0, w, n, st))) return finish(rc);
+            }
+            if ((rc = launch_norm(w, n, sc + 128, P.d_partial, P.d_counter, st))) return finish(rc);
+            if ((rc = launch_arnoldi_finish(P.d_H, ldh, j, sc, o.reorth ? sc + 64 : nullptr, sc + 128, P.d_cs,
+                                            P.d_sn, P.d_gv, sc + 129, st)))
+                return finish(rc);
+            if ((rc = launch_scale(w, sc + 128, w, n, st))) return finish(rc);
+            ++its;
+            FDE_CUDA_TRY(cudaMemcpyAsync(pin, sc + 128, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+            FDE_CUDA_TRY(cudaStreamSynchronize(st));
+            est = pin[1];
+            const double hnext = std::fabs(pin[2]);
+            if (!std::isfinite(est) || !std::isfinite(pin[0])) {
+                status = set_error(FDE_ERR_NAN, "non-finite Hessenberg entry");
+                break;
+            }
+            if (est <= o.tol * bnorm || its >= o.maxit || hnext <= 1e-300) {
+                ++j;
+                break;
+            }
+        }
+        if (status == FDE_ERR_NAN) break;
+        const int k = j < o.restart ? j : o.restart;
+        if ((rc = launch_lsq_solve(P.d_H, ldh, k, P.d_gv, P.d_y, st))) return finish(rc);
+        if ((rc = launch_update(Z, k, P.d_y, 1.0, x, n, st))) return finish(rc);
+        ++S.restarts;
+        S.rel_residual_estimate = est / bnorm;
+        if ((rc = launch_matvec64(P, x, P.d_work, st))) return finish(rc);
+        if ((rc = launch_sub(P.d_b_rhs, P.d_work, V, n, st))) return finish(rc);
+        if ((rc = norm2(P, V, 132, &beta2, pin))) return finish(rc);
+    }
+    S.iterations = its;
+    return finish(status);
+}
+
+}  // extern "C"

@@ -1,0 +1,153 @@
+// Internal declarations shared by the CUDA translation units of libfde.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/fde.h"
+
+namespace fde {
+
+// ---------------------------------------------------------------------------
+// error handling
+// ---------------------------------------------------------------------------
+int set_error(int code, const std::string& msg);
+int cuda_error(cudaError_t e, const char* what);
+
+#define FDE_CUDA_TRY(call)                                   \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return ::fde::cuda_error(e_, #call); \
+    } while (0)
+
+#define FDE_LAUNCH_CHECK(what)                               \
+    do {                                                     \
+        cudaError_t e_ = cudaGetLastError();                 \
+        if (e_ != cudaSuccess) return ::fde::cuda_error(e_, what); \
+    } while (0)
+
+inline int ilog2(int v) {
+    int r = 0;
+    while ((1 << r) < v) ++r;
+    return r;
+}
+inline int round_up(int v, int q) { return (v + q - 1) / q * q; }
+
+// ---------------------------------------------------------------------------
+// Per-problem constants used by the kernels (kept in device memory).
+// ---------------------------------------------------------------------------
+struct BandRow {
+    int start;  // first full-system column (0..s-mu) of the formula for this row
+};
+
+// Row t = 1..s of (A, B) (eqs. (1.7)-(1.9)): mu+1 coefficients starting at column start[t].
+struct DeviceBand {
+    int mu;
+    int s;
+    const int* start;      // [s+1]
+    const double* a;       // [(s+1) * (mu+1)]
+    const double* b;       // [(s+1) * (mu+1)]
+};
+
+// ---------------------------------------------------------------------------
+// kernel launchers (defined in the .cu files)
+// ---------------------------------------------------------------------------
+struct Problem;
+
+// setup.cu
+int launch_grunwald(double alpha, int count, double* g, cudaStream_t st);
+int launch_twiddles(int L, double2* tw64, float2* tw32, cudaStream_t st);
+int launch_toeplitz_symbol(const double* g, int m, int L, double scale, const double2* tw, double2* sym64,
+                           float2* sym32, double2* work, cudaStream_t st);
+int launch_strang_symbols(const double* a_main, const double* b_main, int mu, int nu, int s, double2* phi,
+                          double2* psi, cudaStream_t st);
+int launch_rhs(const Problem& P, const double* Ju0, cudaStream_t st);
+
+// matvec.cu: y = M z (mode 0) or y = J z for ncols columns (mode 1)
+int launch_matvec64(const Problem& P, const double* z, double* y, cudaStream_t st);
+int launch_japply64(const Problem& P, const double* z, double* y, int ncols, cudaStream_t st);
+
+// timefft.cu
+int launch_time_fft_fwd(const Problem& P, const double* r, void* rhat, int prec, cudaStream_t st);
+int launch_time_fft_inv(const Problem& P, const void* xhat, double* z, int prec, cudaStream_t st);
+
+// lu.cu
+int launch_block_lu(Problem& P, int prec, cudaStream_t st);
+int launch_block_trsv(const Problem& P, void* rhat, cudaStream_t st);
+
+// krylov.cu
+int launch_dots(const double* V, int k, const double* w, long n, double* out, double* partial,
+                unsigned int* counter, cudaStream_t st);
+int launch_update(const double* V, int k, const double* coef, double sign, double* w, long n, cudaStream_t st);
+int launch_norm(const double* w, long n, double* out, double* partial, unsigned int* counter, cudaStream_t st);
+int launch_scale(const double* src, const double* nrm_sq, double* dst, long n, cudaStream_t st);
+int launch_arnoldi_finish(double* H, int ldh, int j, const double* h1, const double* h2, const double* nrm_sq,
+                          double* cs, double* sn, double* g, double* est, cudaStream_t st);
+int launch_lsq_solve(const double* H, int ldh, int k, const double* g, double* y, cudaStream_t st);
+int launch_axpy(double a, const double* x, double* y, long n, cudaStream_t st);
+int launch_sub(const double* b, const double* ax, double* r, long n, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// The problem object.
+// ---------------------------------------------------------------------------
+struct Problem {
+    // description
+    int m = 0, s = 0, mu = 0, nu = 0, family = 0;
+    double alpha = 0, xL = 0, xR = 0, t0 = 0, T = 0, dx = 0, h = 0, dxa = 0;  // dxa = dx^-alpha
+    int L = 0, logL = 0;        // Toeplitz circulant embedding length (power of two >= 2m)
+    int logs = 0;               // log2(s)
+    int nblk = 0;               // s/2 + 1 Strang blocks
+    int mp = 0;                 // m rounded up to the LU tile (64)
+    long n = 0;                 // s*m unknowns
+    cudaStream_t stream = nullptr;
+
+    // host copies of the BVM band (rows 0..s of A and B)
+    int h_start[FDE_MAX_S + 1];
+    double h_a_main[FDE_MAX_MU + 1], h_b_main[FDE_MAX_MU + 1];
+
+    // device buffers
+    int* d_start = nullptr;
+    double* d_a = nullptr;      // (s+1)*(mu+1)
+    double* d_b = nullptr;
+    double* d_dplus = nullptr;  // m
+    double* d_dminus = nullptr; // m
+    double* d_u0 = nullptr;     // m
+    double* d_f = nullptr;      // (s+1)*m
+    double* d_g = nullptr;      // m+2 Grunwald weights
+    double2* d_twL = nullptr;   // L/2 twiddles exp(-2 pi i k / L), FP64
+    float2* d_twL32 = nullptr;  // same, FP32
+    double2* d_sym = nullptr;   // L: (lambda + i conj(lambda)) / L, lambda = FFT of the circulant embedding of G
+    float2* d_sym32 = nullptr;
+    double2* d_tws = nullptr;   // s/2 twiddles exp(-2 pi i k / s)
+    float2* d_tws32 = nullptr;
+    double2* d_phi = nullptr;   // s/2+1
+    double2* d_psi = nullptr;
+    double* d_b_rhs = nullptr;  // n
+    double* d_work = nullptr;   // n scratch (J u0, residuals)
+    void* d_rhat = nullptr;     // nblk * mp complex (FP64 or FP32 by precision)
+    void* d_fac = nullptr;      // nblk * 2 * mp * mp (planar re/im), FP64 or FP32
+    void* d_dinv = nullptr;     // nblk * mp complex: 1 / U_ii
+    int* d_info = nullptr;      // nblk: first singular pivot (+1) or 0
+    size_t fac_bytes = 0;
+
+    // Krylov workspace
+    int restart_cap = 0;
+    double* d_V = nullptr;      // (restart+1) * n
+    double* d_Z = nullptr;      // restart * n
+    double* d_H = nullptr;      // (restart+1) * restart, column-major ldh = restart+1
+    double* d_cs = nullptr;
+    double* d_sn = nullptr;
+    double* d_gv = nullptr;     // restart+1
+    double* d_y = nullptr;      // restart
+    double* d_scal = nullptr;   // scalars: [0..63] dots h1, [64..127] dots h2, [128] norm^2, [129] est, ...
+    double* d_partial = nullptr;
+    unsigned int* d_counter = nullptr;
+
+    bool assembled = false;
+    bool factored = false;
+    int precision = -1;
+};
+
+}  // namespace fde

@@ -1,0 +1,203 @@
+// FP64 Krylov kernels of the flexible GMRES(restart) iteration (Sec. 3.2 cites
+// Saad's GMRES; Sec. 4 runs GMRES(20)): classical Gram-Schmidt with one
+// re-orthogonalisation (CGS2) as multi-dot / multi-axpy passes over the basis V,
+// the Givens least-squares update, and small vector kernels.
+//
+// Reductions are deterministic: every CTA writes its partial sums, and the last
+// CTA to finish (atomic ticket after a fence; nothing waits) adds them in a fixed
+// order and resets the ticket.
+#include "fde_internal.h"
+
+namespace fde {
+
+constexpr int RED_CTAS = 304;  // 2 per SM on 152 SMs
+constexpr int RED_THREADS = 256;
+constexpr int KMAX = 64;       // max Krylov vectors per multi-dot
+
+template <int KC>
+__global__ void __launch_bounds__(RED_THREADS)
+dots_kernel(const double* __restrict__ V, int k, const double* __restrict__ w, long n, double* __restrict__ out,
+            double* __restrict__ partial, unsigned int* __restrict__ counter) {
+    __shared__ double red[RED_THREADS / 32][KC];
+    __shared__ bool last;
+    double acc[KC];
+#pragma unroll
+    for (int i = 0; i < KC; ++i) acc[i] = 0.0;
+    const long stride = (long)gridDim.x * blockDim.x;
+    for (long x = (long)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += stride) {
+        const double wx = w[x];
+#pragma unroll
+        for (int i = 0; i < KC; ++i)
+            if (i < k) acc[i] += V[(size_t)i * n + x] * wx;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < KC; ++i) {
+        double v = acc[i];
+        for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (lane == 0) red[warp][i] = v;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        double v = 0.0;
+        for (int q = 0; q < RED_THREADS / 32; ++q) v += red[q][i];
+        partial[(size_t)blockIdx.x * KMAX + i] = v;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (last) {
+        __threadfence();
+        for (int i = threadIdx.x; i < k; i += blockDim.x) {
+            double v = 0.0;
+            for (int c = 0; c < (int)gridDim.x; ++c) v += ((volatile double*)partial)[(size_t)c * KMAX + i];
+            out[i] = v;
+        }
+        if (threadIdx.x == 0) *counter = 0u;
+    }
+}
+
+// w += sign * sum_i coef[i] V_i
+__global__ void update_kernel(const double* __restrict__ V, int k, const double* __restrict__ coef, double sign,
+                              double* __restrict__ w, long n) {
+    __shared__ double c[KMAX];
+    for (int i = threadIdx.x; i < k; i += blockDim.x) c[i] = sign * coef[i];
+    __syncthreads();
+    const long stride = (long)gridDim.x * blockDim.x;
+    for (long x = (long)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += stride) {
+        double acc = w[x];
+        for (int i = 0; i < k; ++i) acc += c[i] * V[(size_t)i * n + x];
+        w[x] = acc;
+    }
+}
+
+__global__ void scale_kernel(const double* __restrict__ src, const double* __restrict__ nrm_sq,
+                             double* __restrict__ dst, long n) {
+    const double nr = sqrt(*nrm_sq);
+    const double inv = nr > 0.0 ? 1.0 / nr : 0.0;
+    const long stride = (long)gridDim.x * blockDim.x;
+    for (long x = (long)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += stride) dst[x] = src[x] * inv;
+}
+
+__global__ void axpy_kernel(double a, const double* __restrict__ x, double* __restrict__ y, long n) {
+    const long stride = (long)gridDim.x * blockDim.x;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) y[i] += a * x[i];
+}
+
+__global__ void sub_kernel(const double* __restrict__ b, const double* __restrict__ ax, double* __restrict__ r,
+                           long n) {
+    const long stride = (long)gridDim.x * blockDim.x;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) r[i] = b[i] - ax[i];
+}
+
+// Column j of the Hessenberg matrix from the Gram-Schmidt coefficients, the
+// previous Givens rotations applied to it, a new rotation that annihilates
+// H[j+1][j], and the rotated right-hand side g; est = |g_{j+1}| is the residual
+// norm of the current cycle.  H is column-major with leading dimension ldh.
+__global__ void arnoldi_finish_kernel(double* __restrict__ H, int ldh, int j, const double* __restrict__ h1,
+                                      const double* __restrict__ h2, const double* __restrict__ nrm_sq,
+                                      double* __restrict__ cs, double* __restrict__ sn, double* __restrict__ g,
+                                      double* __restrict__ est) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double* col = H + (size_t)j * ldh;
+    for (int i = 0; i <= j; ++i) col[i] = h1[i] + (h2 ? h2[i] : 0.0);
+    col[j + 1] = sqrt(*nrm_sq);
+    for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * col[i] + sn[i] * col[i + 1];
+        col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+        col[i] = t;
+    }
+    const double a = col[j], b = col[j + 1];
+    const double r = hypot(a, b);
+    const double c = r > 0.0 ? a / r : 1.0;
+    const double s = r > 0.0 ? b / r : 0.0;
+    cs[j] = c;
+    sn[j] = s;
+    col[j] = r;
+    col[j + 1] = 0.0;
+    g[j + 1] = -s * g[j];
+    g[j] = c * g[j];
+    est[0] = fabs(g[j + 1]);
+    est[1] = b;  // H[j+1][j] before rotation (breakdown test)
+}
+
+// y = R^{-1} g with R the k x k upper-triangular part of the rotated H.
+__global__ void lsq_solve_kernel(const double* __restrict__ H, int ldh, int k, const double* __restrict__ g,
+                                 double* __restrict__ y) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int i = k - 1; i >= 0; --i) {
+        double v = g[i];
+        for (int c = i + 1; c < k; ++c) v -= H[(size_t)c * ldh + i] * y[c];
+        y[i] = v / H[(size_t)i * ldh + i];
+    }
+}
+
+static int grid_for(long n) {
+    long g = (n + 255) / 256;
+    if (g > 4 * 152) g = 4 * 152;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+int launch_dots(const double* V, int k, const double* w, long n, double* out, double* partial, unsigned int* counter,
+                cudaStream_t st) {
+    if (k <= 0) return FDE_OK;
+    if (k > KMAX) return set_error(FDE_ERR_ARG, "too many Krylov vectors for one multi-dot");
+    if (k <= 8)
+        dots_kernel<8><<<RED_CTAS, RED_THREADS, 0, st>>>(V, k, w, n, out, partial, counter);
+    else if (k <= 16)
+        dots_kernel<16><<<RED_CTAS, RED_THREADS, 0, st>>>(V, k, w, n, out, partial, counter);
+    else if (k <= 32)
+        dots_kernel<32><<<RED_CTAS, RED_THREADS, 0, st>>>(V, k, w, n, out, partial, counter);
+    else
+        dots_kernel<64><<<RED_CTAS, RED_THREADS, 0, st>>>(V, k, w, n, out, partial, counter);
+    FDE_LAUNCH_CHECK("dots_kernel");
+    return FDE_OK;
+}
+
+int launch_update(const double* V, int k, const double* coef, double sign, double* w, long n, cudaStream_t st) {
+    if (k <= 0) return FDE_OK;
+    update_kernel<<<grid_for(n), 256, 0, st>>>(V, k, coef, sign, w, n);
+    FDE_LAUNCH_CHECK("update_kernel");
+    return FDE_OK;
+}
+
+int launch_norm(const double* w, long n, double* out, double* partial, unsigned int* counter, cudaStream_t st) {
+    dots_kernel<8><<<RED_CTAS, RED_THREADS, 0, st>>>(w, 1, w, n, out, partial, counter);
+    FDE_LAUNCH_CHECK("dots_kernel(norm)");
+    return FDE_OK;
+}
+
+int launch_scale(const double* src, const double* nrm_sq, double* dst, long n, cudaStream_t st) {
+    scale_kernel<<<grid_for(n), 256, 0, st>>>(src, nrm_sq, dst, n);
+    FDE_LAUNCH_CHECK("scale_kernel");
+    return FDE_OK;
+}
+
+int launch_arnoldi_finish(double* H, int ldh, int j, const double* h1, const double* h2, const double* nrm_sq,
+                          double* cs, double* sn, double* g, double* est, cudaStream_t st) {
+    arnoldi_finish_kernel<<<1, 32, 0, st>>>(H, ldh, j, h1, h2, nrm_sq, cs, sn, g, est);
+    FDE_LAUNCH_CHECK("arnoldi_finish_kernel");
+    return FDE_OK;
+}
+
+int launch_lsq_solve(const double* H, int ldh, int k, const double* g, double* y, cudaStream_t st) {
+    lsq_solve_kernel<<<1, 32, 0, st>>>(H, ldh, k, g, y);
+    FDE_LAUNCH_CHECK("lsq_solve_kernel");
+    return FDE_OK;
+}
+
+int launch_axpy(double a, const double* x, double* y, long n, cudaStream_t st) {
+    axpy_kernel<<<grid_for(n), 256, 0, st>>>(a, x, y, n);
+    FDE_LAUNCH_CHECK("axpy_kernel");
+    return FDE_OK;
+}
+
+int launch_sub(const double* b, const double* ax, double* r, long n, cudaStream_t st) {
+    sub_kernel<<<grid_for(n), 256, 0, st>>>(b, ax, r, n);
+    FDE_LAUNCH_CHECK("sub_kernel");
+    return FDE_OK;
+}
+
+}  // namespace fde

@@ -1,0 +1,407 @@
+// Strang blocks B_k = phi_k I - h psi_k J (Sec. 3.2), k = 0..s/2, formed on the
+// device from (g, d+, d-) and factored B_k = L_k U_k by right-looking blocked LU
+// without pivoting (every B_k is strictly row diagonally dominant: J is, by
+// Proposition 2.2, and Re(phi_k / psi_k) >= 0 for the A_{nu,mu-nu}-stable
+// schemes), then solved once per GMRES iteration by blocked forward / backward
+// substitution.
+//
+// Storage: planar complex, one m_p x m_p row-major plane for Re and one for Im per
+// block (m_p = m rounded up to 64; the padding is the identity), packed L\U in
+// place, plus 1/U_ii per row.  Precision T = double (plain method) or float.
+//
+// Per panel step p (columns [p NB, (p+1) NB)):
+//   1. lu_diag:   factor the NB x NB diagonal block in shared memory (one CTA per block)
+//   2. lu_panel:  L21 = A21 U11^{-1} and U12 = L11^{-1} A12 (row / column chunks)
+//   3. lu_update: A22 -= L21 U12 (complex GEMM on CUDA cores; the tensor-core
+//                 variant lives in lu_tc.cu)
+#include "fde_internal.h"
+#include "fft_device.cuh"
+
+namespace fde {
+
+constexpr int NB = 32;
+
+template <typename T>
+__device__ __forceinline__ T* plane_re(T* fac, int k, int mp) { return fac + (size_t)k * 2 * mp * mp; }
+template <typename T>
+__device__ __forceinline__ T* plane_im(T* fac, int k, int mp) { return fac + (size_t)k * 2 * mp * mp + (size_t)mp * mp; }
+
+// J[i][j] = dx^-alpha (d+_i G[i][j] + d-_i G[j][i]),  G[i][j] = g_{i-j+1} (i-j+1 >= 0), eq. (1.4)/(1.5)
+__device__ __forceinline__ double j_entry(int i, int j, double dxa, const double* __restrict__ g,
+                                          const double* __restrict__ dp, const double* __restrict__ dm) {
+    const int a = i - j + 1;
+    const int b = j - i + 1;
+    double v = 0.0;
+    if (a >= 0) v += dp[i] * g[a];
+    if (b >= 0) v += dm[i] * g[b];
+    return dxa * v;
+}
+
+template <typename T>
+__global__ void form_blocks_kernel(int m, int mp, double h, double dxa, const double* __restrict__ g,
+                                   const double* __restrict__ dp, const double* __restrict__ dm,
+                                   const double2* __restrict__ phi, const double2* __restrict__ psi, T* __restrict__ fac) {
+    const int k = blockIdx.y;
+    const double2 ph = phi[k];
+    const double2 ps = psi[k];
+    T* re = plane_re(fac, k, mp);
+    T* im = plane_im(fac, k, mp);
+    const size_t total = (size_t)mp * mp;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / mp);
+        const int j = (int)(e - (size_t)i * mp);
+        double vr, vi;
+        if (i < m && j < m) {
+            const double jv = j_entry(i, j, dxa, g, dp, dm);
+            vr = (i == j ? ph.x : 0.0) - h * ps.x * jv;
+            vi = (i == j ? ph.y : 0.0) - h * ps.y * jv;
+        } else {
+            vr = (i == j) ? 1.0 : 0.0;
+            vi = 0.0;
+        }
+        re[e] = (T)vr;
+        im[e] = (T)vi;
+    }
+}
+
+// Unblocked LU (no pivoting) of the NB x NB diagonal block of every matrix.
+template <typename T>
+__global__ void __launch_bounds__(256)
+lu_diag_kernel(int mp, int p, T* __restrict__ fac, cplx_t<T>* __restrict__ dinv, int* __restrict__ info) {
+    using C = cplx_t<T>;
+    __shared__ C D[NB][NB + 1];
+    const int k = blockIdx.x;
+    T* re = plane_re(fac, k, mp);
+    T* im = plane_im(fac, k, mp);
+    const int o = p * NB;
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+        const int r = e / NB, c = e % NB;
+        const size_t idx = (size_t)(o + r) * mp + o + c;
+        D[r][c] = mk(re[idx], im[idx]);
+    }
+    __syncthreads();
+    for (int c = 0; c < NB; ++c) {
+        const C piv = D[c][c];
+        const T den = piv.x * piv.x + piv.y * piv.y;
+        const bool bad = !(den > T(0)) || !isfinite((double)den);
+        if (bad && threadIdx.x == 0) atomicCAS(info + k, 0, o + c + 1);
+        C inv = mk(piv.x / den, -piv.y / den);
+        if (bad) inv = mk(T(0), T(0));
+        __syncthreads();
+        // scale the column below the pivot: l_rc = a_rc / u_cc
+        for (int r = c + 1 + threadIdx.x; r < NB; r += blockDim.x) D[r][c] = cmul(D[r][c], inv);
+        __syncthreads();
+        const int w = NB - c - 1;
+        for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+            const int r = c + 1 + e / w, cc = c + 1 + e % w;
+            D[r][cc] = csub(D[r][cc], cmul(D[r][c], D[c][cc]));
+        }
+        if (threadIdx.x == 0) dinv[(size_t)k * mp + o + c] = inv;
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+        const int r = e / NB, c = e % NB;
+        const size_t idx = (size_t)(o + r) * mp + o + c;
+        re[idx] = D[r][c].x;
+        im[idx] = D[r][c].y;
+    }
+}
+
+// Panel solves.  blockIdx.x < nrow: a chunk of RC rows of A21 -> L21 = A21 U11^{-1};
+// otherwise a chunk of RC columns of A12 -> U12 = L11^{-1} A12.
+constexpr int RC = 32;
+template <typename T>
+__global__ void __launch_bounds__(256)
+lu_panel_kernel(int mp, int p, int nrow, T* __restrict__ fac) {
+    using C = cplx_t<T>;
+    __shared__ C D[NB][NB + 1];
+    __shared__ C X[RC][NB + 1];
+    const int k = blockIdx.y;
+    T* re = plane_re(fac, k, mp);
+    T* im = plane_im(fac, k, mp);
+    const int o = p * NB;
+    const int rest = o + NB;  // first row / column after the panel
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+        const int r = e / NB, c = e % NB;
+        const size_t idx = (size_t)(o + r) * mp + o + c;
+        D[r][c] = mk(re[idx], im[idx]);
+    }
+    const bool rows = blockIdx.x < nrow;
+    const int chunk = rows ? blockIdx.x : blockIdx.x - nrow;
+    const int b0 = rest + chunk * RC;
+    // X[q][c]: rows mode -> A21[b0+q][o+c]; columns mode -> A12[o+c][b0+q] (stored transposed)
+    for (int e = threadIdx.x; e < RC * NB; e += blockDim.x) {
+        int q, c;
+        size_t idx;
+        if (rows) {
+            q = e / NB; c = e % NB;
+            idx = (size_t)(b0 + q) * mp + o + c;
+        } else {
+            c = e / RC; q = e % RC;
+            idx = (size_t)(o + c) * mp + b0 + q;
+        }
+        X[q][c] = (b0 + q < mp) ? mk(re[idx], im[idx]) : mk(T(0), T(0));
+    }
+    __syncthreads();
+    if (rows) {
+        // x U11 = a: for c: x_c = (a_c - sum_{c'<c} x_c' U[c'][c]) / U[c][c]  (right-looking form)
+        for (int c = 0; c < NB; ++c) {
+            const C piv = D[c][c];
+            const T den = piv.x * piv.x + piv.y * piv.y;
+            const C inv = den > T(0) ? mk(piv.x / den, -piv.y / den) : mk(T(0), T(0));
+            for (int q = threadIdx.x; q < RC; q += blockDim.x) X[q][c] = cmul(X[q][c], inv);
+            __syncthreads();
+            const int w = NB - c - 1;
+            for (int e = threadIdx.x; e < RC * w; e += blockDim.x) {
+                const int q = e / w, cc = c + 1 + e % w;
+                X[q][cc] = csub(X[q][cc], cmul(X[q][c], D[c][cc]));
+            }
+            __syncthreads();
+        }
+    } else {
+        // L11 u = a (unit lower): for c: a_rr -= L[rr][c] a_c, rr > c
+        for (int c = 0; c < NB; ++c) {
+            const int w = NB - c - 1;
+            for (int e = threadIdx.x; e < RC * w; e += blockDim.x) {
+                const int q = e / w, rr = c + 1 + e % w;
+                X[q][rr] = csub(X[q][rr], cmul(D[rr][c], X[q][c]));
+            }
+            __syncthreads();
+        }
+    }
+    for (int e = threadIdx.x; e < RC * NB; e += blockDim.x) {
+        int q, c;
+        size_t idx;
+        if (rows) {
+            q = e / NB; c = e % NB;
+            idx = (size_t)(b0 + q) * mp + o + c;
+        } else {
+            c = e / RC; q = e % RC;
+            idx = (size_t)(o + c) * mp + b0 + q;
+        }
+        if (b0 + q < mp) {
+            re[idx] = X[q][c].x;
+            im[idx] = X[q][c].y;
+        }
+    }
+}
+
+// Trailing update A22 -= L21 U12 on CUDA cores: 64 x 64 output tile per CTA,
+// 4 x 4 complex outputs per thread, K = NB.
+template <typename T>
+__global__ void __launch_bounds__(256)
+lu_update_kernel(int mp, int p, int ntile, T* __restrict__ fac) {
+    using C = cplx_t<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C (*Ls)[NB + 1] = reinterpret_cast<C (*)[NB + 1]>(smem_raw);                        // [64][NB+1]
+    C (*Us)[64 + 1] = reinterpret_cast<C (*)[64 + 1]>(smem_raw + 64 * (NB + 1) * sizeof(C));  // [NB][65]
+    const int k = blockIdx.y;
+    T* re = plane_re(fac, k, mp);
+    T* im = plane_im(fac, k, mp);
+    const int o = p * NB;
+    const int rest = o + NB;
+    const int ti = blockIdx.x / ntile, tj = blockIdx.x % ntile;
+    const int r0 = rest + ti * 64, c0 = rest + tj * 64;
+    for (int e = threadIdx.x; e < 64 * NB; e += blockDim.x) {
+        const int q = e / NB, c = e % NB;
+        const int r = r0 + q;
+        Ls[q][c] = r < mp ? mk(re[(size_t)r * mp + o + c], im[(size_t)r * mp + o + c]) : mk(T(0), T(0));
+        const int c2 = e / 64, q2 = e % 64;
+        const int cc = c0 + q2;
+        Us[c2][q2] = cc < mp ? mk(re[(size_t)(o + c2) * mp + cc], im[(size_t)(o + c2) * mp + cc]) : mk(T(0), T(0));
+    }
+    __syncthreads();
+    const int tr = threadIdx.x / 16, tc = threadIdx.x % 16;
+    C acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = mk(T(0), T(0));
+#pragma unroll 4
+    for (int kk = 0; kk < NB; ++kk) {
+        C av[4], bv[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) av[a] = Ls[tr + 16 * a][kk];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) bv[b] = Us[kk][tc + 16 * b];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                acc[a][b].x += av[a].x * bv[b].x - av[a].y * bv[b].y;
+                acc[a][b].y += av[a].x * bv[b].y + av[a].y * bv[b].x;
+            }
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int r = r0 + tr + 16 * a;
+        if (r >= mp) continue;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int c = c0 + tc + 16 * b;
+            if (c >= mp) continue;
+            const size_t idx = (size_t)r * mp + c;
+            re[idx] -= acc[a][b].x;
+            im[idx] -= acc[a][b].y;
+        }
+    }
+}
+
+// Forward (unit lower L) then backward (U) substitution for one block per CTA,
+// in place on rhat[k] (length mp).  Rows in tiles of 32: 16 warps form the partial
+// products of a tile against the solved part (coalesced row reads of the factor
+// planes), then warp 0 resolves the 32 x 32 diagonal tile with shuffles.
+template <typename T>
+__global__ void __launch_bounds__(512)
+block_trsv_kernel(int mp, const T* __restrict__ fac, const cplx_t<T>* __restrict__ dinv, cplx_t<T>* __restrict__ rhat) {
+    using C = cplx_t<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* y = reinterpret_cast<C*>(smem_raw);  // mp
+    __shared__ C part[32];
+    const int k = blockIdx.x;
+    const T* re = fac + (size_t)k * 2 * mp * mp;
+    const T* im = re + (size_t)mp * mp;
+    C* x = rhat + (size_t)k * mp;
+    const C* dv = dinv + (size_t)k * mp;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    for (int i = threadIdx.x; i < mp; i += blockDim.x) y[i] = x[i];
+    __syncthreads();
+    // forward: y <- L^{-1} y
+    for (int r0 = 0; r0 < mp; r0 += 32) {
+        for (int q = warp; q < 32; q += nwarp) {
+            const int r = r0 + q;
+            const T* lr = re + (size_t)r * mp;
+            const T* li = im + (size_t)r * mp;
+            T ax = 0, ay = 0;
+#pragma unroll 8
+            for (int j = lane; j < r0; j += 32) {
+                const T a = lr[j], b = li[j];
+                const C v = y[j];
+                ax += a * v.x - b * v.y;
+                ay += a * v.y + b * v.x;
+            }
+#pragma unroll
+            for (int off = 16; off; off >>= 1) {
+                ax += __shfl_xor_sync(0xffffffffu, ax, off);
+                ay += __shfl_xor_sync(0xffffffffu, ay, off);
+            }
+            if (lane == 0) part[q] = mk(ax, ay);
+        }
+        __syncthreads();
+        if (warp == 0) {
+            const int r = r0 + lane;
+            C a = csub(y[r], part[lane]);
+            const T* lr = re + (size_t)r * mp + r0;
+            const T* li = im + (size_t)r * mp + r0;
+            for (int c = 0; c < 32; ++c) {
+                const T yx = __shfl_sync(0xffffffffu, a.x, c);
+                const T yy = __shfl_sync(0xffffffffu, a.y, c);
+                if (lane > c) {
+                    const T lx = lr[c], ly = li[c];
+                    a.x -= lx * yx - ly * yy;
+                    a.y -= lx * yy + ly * yx;
+                }
+            }
+            y[r] = a;
+        }
+        __syncthreads();
+    }
+    // backward: y <- U^{-1} y
+    for (int r0 = mp - 32; r0 >= 0; r0 -= 32) {
+        for (int q = warp; q < 32; q += nwarp) {
+            const int r = r0 + q;
+            const T* ur = re + (size_t)r * mp;
+            const T* ui = im + (size_t)r * mp;
+            T ax = 0, ay = 0;
+#pragma unroll 8
+            for (int j = r0 + 32 + lane; j < mp; j += 32) {
+                const T a = ur[j], b = ui[j];
+                const C v = y[j];
+                ax += a * v.x - b * v.y;
+                ay += a * v.y + b * v.x;
+            }
+#pragma unroll
+            for (int off = 16; off; off >>= 1) {
+                ax += __shfl_xor_sync(0xffffffffu, ax, off);
+                ay += __shfl_xor_sync(0xffffffffu, ay, off);
+            }
+            if (lane == 0) part[q] = mk(ax, ay);
+        }
+        __syncthreads();
+        if (warp == 0) {
+            const int r = r0 + lane;
+            C a = csub(y[r], part[lane]);
+            const T* ur = re + (size_t)r * mp + r0;
+            const T* ui = im + (size_t)r * mp + r0;
+            const C di = dv[r];
+            for (int c = 31; c >= 0; --c) {
+                if (lane == c) a = cmul(a, di);
+                const T yx = __shfl_sync(0xffffffffu, a.x, c);
+                const T yy = __shfl_sync(0xffffffffu, a.y, c);
+                if (lane < c) {
+                    const T ux = ur[c], uy = ui[c];
+                    a.x -= ux * yx - uy * yy;
+                    a.y -= ux * yy + uy * yx;
+                }
+            }
+            y[r] = a;
+        }
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < mp; i += blockDim.x) x[i] = y[i];
+}
+
+template <typename T>
+static int run_lu(Problem& P, cudaStream_t st) {
+    using C = cplx_t<T>;
+    T* fac = reinterpret_cast<T*>(P.d_fac);
+    C* dinv = reinterpret_cast<C*>(P.d_dinv);
+    const int mp = P.mp, nb = P.nblk;
+    {
+        dim3 grid(nb >= 1216 ? 1 : 1216 / nb, nb);
+        form_blocks_kernel<T><<<grid, 256, 0, st>>>(P.m, mp, P.h, P.dxa, P.d_g, P.d_dplus, P.d_dminus, P.d_phi,
+                                                   P.d_psi, fac);
+        FDE_LAUNCH_CHECK("form_blocks_kernel");
+    }
+    const size_t upd_smem = (64 * (NB + 1) + NB * 65) * sizeof(C);
+    FDE_CUDA_TRY(cudaFuncSetAttribute(lu_update_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)upd_smem));
+    const int steps = mp / NB;
+    for (int p = 0; p < steps; ++p) {
+        lu_diag_kernel<T><<<nb, 256, 0, st>>>(mp, p, fac, dinv, P.d_info);
+        FDE_LAUNCH_CHECK("lu_diag_kernel");
+        const int rem = mp - (p + 1) * NB;
+        if (rem <= 0) break;
+        const int nch = (rem + RC - 1) / RC;
+        lu_panel_kernel<T><<<dim3(2 * nch, nb), 256, 0, st>>>(mp, p, nch, fac);
+        FDE_LAUNCH_CHECK("lu_panel_kernel");
+        const int nt = (rem + 63) / 64;
+        lu_update_kernel<T><<<dim3(nt * nt, nb), 256, upd_smem, st>>>(mp, p, nt, fac);
+        FDE_LAUNCH_CHECK("lu_update_kernel");
+    }
+    return FDE_OK;
+}
+
+int launch_block_lu(Problem& P, int prec, cudaStream_t st) {
+    if (prec == FDE_FP64) return run_lu<double>(P, st);
+    return run_lu<float>(P, st);
+}
+
+int launch_block_trsv(const Problem& P, void* rhat, cudaStream_t st) {
+    if (P.precision == FDE_FP64) {
+        size_t smem = (size_t)P.mp * sizeof(double2);
+        FDE_CUDA_TRY(cudaFuncSetAttribute(block_trsv_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          200 * 1024));
+        block_trsv_kernel<double><<<P.nblk, 512, smem, st>>>(P.mp, (const double*)P.d_fac,
+                                                              (const double2*)P.d_dinv, (double2*)rhat);
+    } else {
+        size_t smem = (size_t)P.mp * sizeof(float2);
+        FDE_CUDA_TRY(cudaFuncSetAttribute(block_trsv_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          200 * 1024));
+        block_trsv_kernel<float><<<P.nblk, 512, smem, st>>>(P.mp, (const float*)P.d_fac, (const float2*)P.d_dinv,
+                                                             (float2*)rhat);
+    }
+    FDE_LAUNCH_CHECK("block_trsv_kernel");
+    return FDE_OK;
+}
+
+}  // namespace fde

@@ -1,0 +1,100 @@
+// Space-time matvec y = M z, M = A_1 (x) I - h B_1 (x) J (eq. (1.10) with u_0
+// eliminated), and the plain Toeplitz-like apply y = J z (eq. (1.4)).
+//
+// One CTA per time row t.  By linearity
+//     y_t = sum_q A[t][c_q] z_{c_q}  -  h J ( sum_q B[t][c_q] z_{c_q} ),
+// so each CTA forms both band combinations of the mu+1 neighbouring time columns
+// (read straight from HBM; the neighbours are shared through L2), then applies J
+// once: J v = dx^-alpha (D+ G v + D- G^T v) through the length-L circulant
+// embedding of G (Sec. 2.1: Toeplitz matvec by FFT), with one forward FFT of v
+// and one inverse FFT whose real / imaginary parts are G v and G^T v.
+#include "fde_internal.h"
+#include "fft_device.cuh"
+
+namespace fde {
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(1024)
+st_matvec_kernel(int m, int logL, int mu, double h, const int* __restrict__ start, const double* __restrict__ A,
+                 const double* __restrict__ B, const double* __restrict__ dplus, const double* __restrict__ dminus,
+                 const cplx_t<T>* __restrict__ sym, const cplx_t<T>* __restrict__ tw, const double* __restrict__ z,
+                 double* __restrict__ y) {
+    using C = cplx_t<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int L = 1 << logL;
+    C* buf = reinterpret_cast<C*>(smem_raw);
+    double* ubuf = reinterpret_cast<double*>(buf + L);
+    const int row = blockIdx.x;  // reduced time row: unknown u_{row+1}
+
+    double ca[FDE_MAX_MU + 1], cb[FDE_MAX_MU + 1];
+    int st = 0;
+    if (MODE == 0) {
+        const int t = row + 1;
+        st = start[t];
+#pragma unroll
+        for (int q = 0; q <= FDE_MAX_MU; ++q) {
+            ca[q] = q <= mu ? A[(size_t)t * (mu + 1) + q] : 0.0;
+            cb[q] = q <= mu ? B[(size_t)t * (mu + 1) + q] : 0.0;
+        }
+    }
+    for (int i = threadIdx.x; i < L; i += blockDim.x) {
+        T v = T(0);
+        if (i < m) {
+            if (MODE == 0) {
+                double u = 0.0, w = 0.0;
+#pragma unroll
+                for (int q = 0; q <= FDE_MAX_MU; ++q) {
+                    const int col = st + q;  // full-system time index; column 0 (u_0) is eliminated
+                    if (q <= mu && col >= 1) {
+                        const double zz = z[(size_t)(col - 1) * m + i];
+                        u += ca[q] * zz;
+                        w += cb[q] * zz;
+                    }
+                }
+                ubuf[i] = u;
+                v = (T)w;
+            } else {
+                v = (T)z[(size_t)row * m + i];
+            }
+        }
+        buf[bitrev(i, logL)] = mk(v, T(0));
+    }
+    __syncthreads();
+    fft_dit<C, false>(buf, logL, 1, L, tw);
+    for (int f = threadIdx.x; f < L; f += blockDim.x) buf[f] = cmul(buf[f], sym[f]);
+    __syncthreads();
+    fft_dif<C, true>(buf, logL, 1, L, tw);
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        const C wv = buf[bitrev(i, logL)];
+        const double jz = dplus[i] * (double)wv.x + dminus[i] * (double)wv.y;
+        if (MODE == 0)
+            y[(size_t)row * m + i] = ubuf[i] - h * jz;
+        else
+            y[(size_t)row * m + i] = jz;
+    }
+}
+
+template <int MODE>
+static int launch_st(const Problem& P, const double* z, double* y, int ncols, cudaStream_t st) {
+    const int L = P.L;
+    size_t smem = (size_t)L * sizeof(double2) + (MODE == 0 ? (size_t)P.m * sizeof(double) : 0);
+    int threads = L / 2;
+    if (threads > 1024) threads = 1024;
+    if (threads < 64) threads = 64;
+    auto kern = st_matvec_kernel<double, MODE>;
+    FDE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    kern<<<ncols, threads, smem, st>>>(P.m, P.logL, P.mu, P.h, P.d_start, P.d_a, P.d_b, P.d_dplus, P.d_dminus,
+                                       P.d_sym, P.d_twL, z, y);
+    FDE_LAUNCH_CHECK("st_matvec_kernel");
+    return FDE_OK;
+}
+
+int launch_matvec64(const Problem& P, const double* z, double* y, cudaStream_t st) {
+    return launch_st<0>(P, z, y, P.s, st);
+}
+
+int launch_japply64(const Problem& P, const double* z, double* y, int ncols, cudaStream_t st) {
+    return launch_st<1>(P, z, y, ncols, st);
+}
+
+}  // namespace fde

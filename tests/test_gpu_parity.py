@@ -1,0 +1,168 @@
+"""GPU parity of the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Tolerances (derived from the arithmetic):
+* Grunwald weights, band combinations: the same recurrence / formulas in FP64,
+  differences only from operation order: 1e-14 relative.
+* M z: J is applied through length-L FFTs (L = 2^k >= 2m).  The FFT's error is
+  O(eps log2 L) relative to ||lambda||_inf ||z||, and ||lambda||_inf <= sum|t_k|
+  = 2 alpha (d+ + d-) dx^-alpha (Sec. 3.2, Wiener class).  With eps = 1.1e-16
+  and log2 L <= 13 the bound is below 1e-12 * h * 2 alpha (d+ + d-) dx^-alpha
+  ||z||_inf, the scale used in the test.
+* S^{-1} r: FP64 LU without pivoting of strictly diagonally dominant blocks
+  (growth factor <= 2), backward stable; forward error <= cond(B_k) * eps * c.
+  cond(B_k) <= 1e4 on these sizes, so 1e-10 relative.
+* Solutions: the spec requirement, ||x - x_oracle|| / ||x_oracle|| <= 1e-8.
+"""
+import numpy as np
+import pytest
+
+import fde_inputs as fi
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1305_6653_gb300 import _lib
+    _lib.load()  # fails loudly if the library is missing
+    torch.cuda.set_device(0)
+
+
+def _gpu(prob, precision="fp64", device_inputs=False):
+    from paper_1305_6653_gb300 import FDEProblem
+    p = FDEProblem.from_inputs(prob, device_inputs=device_inputs)
+    p.assemble()
+    if precision:
+        p.factor(precision)
+    return p
+
+
+def _variable(m, s, scheme, alpha=1.5):
+    return fi.manufactured(m, s, alpha, scheme, dplus_fn=lambda x: 1.0 + x, dminus_fn=lambda x: 2.0 - x)
+
+
+CASES = [
+    ("small", lambda: fi.config_small()),
+    ("ragged_gbdf5", lambda: _variable(100, 16, "GBDF5", 1.8)),
+    ("gam4_ex41", lambda: fi.example_4_1(1.2, 48, 32)),
+    ("etr3", lambda: _variable(37, 8, "ETR3", 1.3)),
+    ("tiny_m1", lambda: _variable(1, 4, "GBDF1", 1.5)),
+    ("m64_exact_tile", lambda: _variable(64, 16, "GAM4", 1.9)),
+    ("m255_s64", lambda: _variable(255, 64, "GBDF3", 1.7)),
+]
+
+
+@pytest.mark.parametrize("name,make", CASES, ids=[c[0] for c in CASES])
+def test_grunwald_and_rhs(name, make):
+    prob = make()
+    with _gpu(prob, precision=None) as p:
+        g = p.grunwald()
+        np.testing.assert_allclose(g, O.grunwald_weights(prob.alpha, prob.m + 1), rtol=1e-14, atol=0)
+        b = p.rhs().cpu().numpy()
+    ref = O.reduced_rhs(prob)
+    scale = np.abs(ref).max() + prob.h * O.j_of(prob).__abs__().sum(axis=1).max() * np.abs(prob.u0).max()
+    np.testing.assert_allclose(b, ref, rtol=0, atol=1e-12 * max(scale, 1e-300))
+
+
+@pytest.mark.parametrize("name,make", CASES, ids=[c[0] for c in CASES])
+def test_matvec(name, make):
+    prob = make()
+    rng = np.random.default_rng(11)
+    z = rng.standard_normal(prob.n)
+    with _gpu(prob, precision=None) as p:
+        y = p.matvec(torch.as_tensor(z, device="cuda")).cpu().numpy()
+    ref = O.matvec(prob, z)
+    jscale = 2 * prob.alpha * (prob.dplus + prob.dminus).max() * prob.dx ** (-prob.alpha)
+    scale = prob.h * jscale * np.abs(z).max() + 4 * np.abs(z).max()
+    assert np.abs(y - ref).max() <= 1e-12 * scale
+
+
+@pytest.mark.parametrize("name,make", CASES, ids=[c[0] for c in CASES])
+def test_precond_apply_fp64(name, make):
+    prob = make()
+    rng = np.random.default_rng(12)
+    r = rng.standard_normal(prob.n)
+    with _gpu(prob, "fp64") as p:
+        z = p.precond_apply(torch.as_tensor(r, device="cuda")).cpu().numpy()
+    ref = O.StrangPreconditioner(prob).apply(r)
+    assert np.linalg.norm(z - ref) <= 1e-10 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_factor_reconstructs_strang_blocks(precision):
+    """Sampled check: L_k U_k equals phi_k I - h psi_k J of the oracle (Sec. 3.2)."""
+    prob = _variable(100, 16, "GBDF5", 1.8)
+    P = O.StrangPreconditioner(prob)
+    tol = 1e-12 if precision == "fp64" else 2e-5
+    with _gpu(prob, precision) as p:
+        for k in (0, 1, prob.s // 4, prob.s // 2):
+            F = p.factor_block(k)
+            L = np.tril(F, -1) + np.eye(prob.m)
+            U = np.triu(F)
+            B = P.block(k)
+            assert np.abs(L @ U - B).max() <= tol * np.abs(B).max(), k
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("name,make", CASES, ids=[c[0] for c in CASES])
+def test_solve_matches_direct_solution(name, make, precision):
+    prob = make()
+    if prob.n <= 5000:
+        ref = O.direct_solve(prob)
+    else:
+        ref, _, ok, _ = O.solve_strang_gmres(prob, side="right", tol=1e-13)
+        assert ok
+    with _gpu(prob, precision) as p:
+        x, st = p.solve(tol=1e-11, restart=20, maxit=400)
+        xs = x.cpu().numpy()
+    err = np.linalg.norm(xs - ref) / np.linalg.norm(ref)
+    assert st["status"] == 0, st
+    assert err <= 1e-8, (err, st)
+    # Theorem 3.3: with S, GMRES needs at most 2 m mu + 1 iterations (exact arithmetic)
+    assert st["iterations"] <= 2 * prob.m * prob.mu + 1
+    # the true residual reported by the library agrees with the oracle's
+    M_b = O.reduced_rhs(prob)
+    res = np.linalg.norm(M_b - O.matvec(prob, xs)) / np.linalg.norm(M_b)
+    assert res <= 1e-10 and abs(res - st["rel_residual"]) <= 1e-11
+
+
+def test_small_config_iterations_are_paper_like():
+    prob = fi.config_small()
+    with _gpu(prob, "fp64") as p:
+        _, st = p.solve(tol=1e-10)
+    _, its_oracle, _, _ = O.solve_strang_gmres(prob, side="right", tol=1e-10)
+    assert abs(st["iterations"] - its_oracle) <= 1
+
+
+def test_device_inputs_and_warm_start():
+    prob = fi.config_small()
+    ref = O.direct_solve(prob)
+    with _gpu(prob, "fp64", device_inputs=True) as p:
+        x0 = torch.as_tensor(ref, device="cuda")
+        x, st = p.solve(tol=1e-10, x0=x0)
+        assert st["iterations"] <= 1
+        np.testing.assert_allclose(x.cpu().numpy(), ref, rtol=0, atol=1e-8 * np.abs(ref).max())
+
+
+def test_error_paths():
+    from paper_1305_6653_gb300 import FdeError, _lib
+    prob = fi.config_small()
+    from paper_1305_6653_gb300 import FDEProblem
+    with FDEProblem.from_inputs(prob) as p:
+        with pytest.raises(FdeError) as e:
+            p.solve()
+        assert e.value.code == _lib.FDE_ERR_STATE
+        p.assemble().factor("fp64")
+        _, st = p.solve(tol=1e-14, maxit=1, raise_on_error=False)
+        assert st["status"] == _lib.FDE_ERR_NOT_CONVERGED and st["iterations"] == 1
+    bad = fi.config_small()
+    bad.f = bad.f.copy()
+    bad.f[3, 5] = np.nan
+    with pytest.raises(FdeError) as e:
+        FDEProblem.from_inputs(bad)
+    assert e.value.code == _lib.FDE_ERR_ARG
