@@ -1,0 +1,419 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the Strang-preconditioned BVM/GMRES solver on GB300.
+
+Metric: space-time FDE solves/s at rel.err 1e-8.  One step = one complete solve
+of the space-time system of a problem whose inputs (u0, f, d+, d-) are already
+resident in HBM: bvm_assemble (Grunwald weights, symbols, right-hand side) +
+strang_precond_factor (129 complex 2047 x 2047 block LUs) + pgmres_solve
+(flexible GMRES(20) to a true FP64 relative residual of --tol).
+
+Default workload: m=2047 interior points, s=256 time steps, alpha=1.8,
+d+(x)=1+x, d-(x)=2-x, 5-step GBDF, manufactured source (exact solution
+exp(-t) x^2 (1-x)^2); 524,032 unknowns.  Synthetic, seeded-free (deterministic).
+
+Multi-GPU: one process per GPU (torchrun), each solving its own instance; the
+instances are independent, so there is no data-path collective (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "space-time FDE solves/s at rel.err 1e-8: mixed+batched vs plain FP64 PGMRES"
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "tf32", "bf16"])
+    ap.add_argument("--m", type=int, default=2047)
+    ap.add_argument("--s", type=int, default=256)
+    ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--fp64-steps", type=int, default=1, help="plain FP64 solves timed for comparison (0: skip)")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+
+def peaks():
+    try:
+        with open(MEASURED_PEAKS) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1900.0), d.get("bf16_tflops_sustained", 1700.0), \
+            "measured"
+    except OSError:
+        return 6800.0, 1900.0, 1700.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def lu_update_flops(mp: int, nblk: int, nb: int = 32) -> float:
+    """Algorithmic FP flops of the trailing complex updates: sum_p 8 NB rem_p^2 per block."""
+    tot = 0.0
+    p = 0
+    while (p + 1) * nb < mp:
+        rem = mp - (p + 1) * nb
+        tot += 8.0 * nb * rem * rem
+        p += 1
+    return tot * nblk
+
+
+def trsv_bytes(mp: int, nblk: int, esz: int) -> float:
+    """Algorithmic bytes of one block-substitution launch: every factor entry once
+    (L below, U on/above the diagonal; Re and Im planes) + the RHS in and out."""
+    return nblk * (2.0 * mp * mp * esz + 4.0 * mp * esz)
+
+
+# ---------------------------------------------------------------------------
+# the CPU oracle baseline (bounded sample)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(prob, iterations: int) -> dict:
+    """Time the FP64 oracle on a bounded sample of one solve and compose the time
+    of a full solve (the oracle is slow; a full m=2047 / s=256 solve takes minutes).
+
+    Sample: with the same m, alpha, d and scheme, an s=16 instance (9 distinct
+    Strang blocks: their dense LUs and one preconditioner apply), plus the
+    full-size right-hand side, matvec and the time DFT pair at s=256.  Composition:
+    t = t_rhs + nblk/9 * t_factor(9) + its * (t_matvec + s/16 * t_blocksolve(16) + t_dft + t_gs)."""
+    import numpy as np
+
+    import fde_inputs
+    import oracle as O
+
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
+    except Exception:
+        cores = os.cpu_count() or 1
+    s, m = prob.s, prob.m
+    t0 = time.perf_counter()
+    J = O.j_of(prob)
+    b = O.reduced_rhs(prob, J=J)
+    t_rhs = time.perf_counter() - t0
+    AB = O.bvm_matrices(prob.family, prob.mu, s)
+    z = np.random.default_rng(0).standard_normal(prob.n)
+    t0 = time.perf_counter()
+    O.matvec(prob, z, J=J, AB=AB)
+    t_mv = time.perf_counter() - t0
+    small = fde_inputs.manufactured(m, 16, prob.alpha, prob.scheme,
+                                    dplus_fn=lambda x: prob.dplus, dminus_fn=lambda x: prob.dminus)
+    t0 = time.perf_counter()
+    P = O.StrangPreconditioner(small, J=J)
+    t_fac = time.perf_counter() - t0
+    nb_small = len(P.lu)
+    r = np.random.default_rng(1).standard_normal(small.n)
+    t0 = time.perf_counter()
+    P.apply(r)
+    t_app = time.perf_counter() - t0
+    n_ = np.arange(s)
+    F = np.exp(-2j * np.pi * np.outer(n_, n_) / s)
+    R = z.reshape(s, m)
+    t0 = time.perf_counter()
+    Xh = F @ R
+    (np.conj(F) @ Xh).real
+    t_dft = time.perf_counter() - t0
+    V = np.random.default_rng(2).standard_normal((21, prob.n))
+    t0 = time.perf_counter()
+    for i in range(10):
+        V[i] @ V[20]
+    t_gs = (time.perf_counter() - t0) * 2.0  # MGS on ~10 vectors, both passes
+    nblk = s // 2 + 1
+    t_solve = (t_rhs + nblk / nb_small * t_fac
+               + iterations * (t_mv + s / 16.0 * t_app + t_dft + t_gs))
+    sampled = t_rhs + t_mv + t_fac + t_app + t_dft + t_gs
+    return {
+        "value": 1.0 / t_solve, "unit": "solves/s", "cores": int(cores), "kind": "oracle",
+        "sample": (f"m={m}: {nb_small} dense Strang-block LUs + one preconditioner apply of an s=16 instance "
+                   f"(same alpha, d, scheme), full-size rhs/matvec/time-DFT at s={s}; composed to {nblk} "
+                   f"block LUs and {iterations} GMRES iterations; {sampled:.1f} s of CPU work"),
+        "seconds_per_solve": t_solve,
+    }
+
+
+# ---------------------------------------------------------------------------
+# main
+# ---------------------------------------------------------------------------
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    import fde_inputs
+
+    prob = fde_inputs.config_scale(args.m, args.s)
+    workload = {"workload": f"scale_m{args.m}_s{args.s}_gbdf5_alpha1.8_variable_d", "m": args.m, "s": args.s,
+                "unknowns": args.m * args.s, "scheme": "GBDF5", "alpha": 1.8, "d": "d+=1+x, d-=2-x",
+                "tol_true_residual": args.tol, "restart": 20, "precision": args.precision,
+                "l2": "flushed (512 MiB write) before every timed step; factors (4.3 GB fp32) exceed L2"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        steps = []
+        sample = None
+        for i in range(args.warmup + args.steps):
+            sample = oracle_sample(prob, iterations=12)
+            if i >= args.warmup:
+                steps.append(sample["seconds_per_solve"])
+        t = sum(steps) / len(steps)
+        v = 1.0 / t
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload,
+                "cpu_baseline": {"value": v, "unit": "solves/s", "cores": sample["cores"], "kind": "oracle",
+                                 "sample": sample["sample"]},
+                "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import numpy as np
+    import torch
+
+    import paper_1305_6653_gb300 as fde
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (the solver has no CPU path)")
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    hbm_peak, bf16_peak, _, peak_kind = peaks()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    xbuf = torch.empty(prob.n, dtype=torch.float64, device="cuda")
+
+    p = fde.FDEProblem.from_inputs(prob, device_inputs=True)
+
+    def step(precision):
+        p.assemble()
+        p.factor(precision)
+        _, st = p.solve(tol=args.tol, restart=20, maxit=400, out=xbuf)
+        return st
+
+    for _ in range(args.warmup):
+        step(args.precision)
+    barrier()
+
+    sampler = ClockSampler(local_rank)
+    if not args.no_clocks:
+        sampler.start()
+    p.profile(True)
+    launches0 = fde.fde_launch_count()
+    per_step = []
+    stats = []
+    barrier()
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        stats.append(step(args.precision))
+        e1.record()
+        e1.synchronize()
+        per_step.append(e0.elapsed_time(e1))
+    barrier()
+    launches = fde.fde_launch_count() - launches0
+    prof = p.profile_read()
+    p.profile(False)
+    clocks = sampler.stop() if not args.no_clocks else None
+
+    total_ms = sum(per_step)
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * args.steps / (total_ms / 1e3)
+
+    # roofline of the dominant kernel
+    mp = (prob.m + 63) // 64 * 64
+    nblk = prob.s // 2 + 1
+    esz = 8 if args.precision == "fp64" else 4
+    dom = max(prof.items(), key=lambda kv: kv[1][0])
+    name, (dom_ms, dom_n) = dom
+    roof = None
+    if name == "trsv":
+        per_launch = trsv_bytes(mp, nblk, esz)
+        ach = per_launch / (dom_ms / dom_n / 1e3) / 1e9
+        roof = {"kernel": "block_trsv_kernel", "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                "frac": ach / hbm_peak, "traffic": None, "peak_kind": peak_kind,
+                "algorithmic_bytes_per_launch": per_launch}
+    elif name == "lu_update":
+        flops = lu_update_flops(mp, nblk) * args.steps
+        ach = flops / (dom_ms / 1e3) / 1e12
+        if args.precision in ("fp32", "fp64"):
+            peak = FP32_ALU_PEAK_TFLOPS if args.precision == "fp32" else 1.25
+            roof = {"kernel": "lu_update_kernel", "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                    "frac": ach / peak, "traffic": None,
+                    "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz" if args.precision == "fp32"
+                    else "nominal FP64", "algorithmic_flops_per_launch": flops / max(dom_n, 1)}
+        else:
+            ratio = 1.1 / 2.25 if args.precision == "tf32" else 1.0
+            peak = bf16_peak * ratio
+            roof = {"kernel": "lu_update_tc_kernel", "bound": "tensor", "achieved": ach, "peak": peak,
+                    "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                    "peak_kind": f"{peak_kind} bf16 x nominal {args.precision}/bf16 ratio",
+                    "algorithmic_flops_per_launch": flops / max(dom_n, 1)}
+    stage_ms = {k: round(v[0] / args.steps, 4) for k, v in prof.items()}
+    stage_n = {k: v[1] // args.steps for k, v in prof.items()}
+
+    # accuracy of the last solution: true residual with the oracle's independent matvec
+    import oracle as O
+    xs = xbuf.cpu().numpy()
+    J = O.j_of(prob)
+    bor = O.reduced_rhs(prob, J=J)
+    res_oracle = float(np.linalg.norm(bor - O.matvec(prob, xs, J=J)) / np.linalg.norm(bor))
+
+    # plain FP64 PGMRES on the same workload (the comparison the metric names)
+    plain = None
+    if args.fp64_steps > 0:
+        tms, st64 = [], None
+        for _ in range(args.fp64_steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            st64 = step("fp64")
+            e1.record()
+            e1.synchronize()
+            tms.append(e0.elapsed_time(e1))
+        plain = {"value": 1e3 / (sum(tms) / len(tms)), "unit": "solves/s", "ms_per_step": sum(tms) / len(tms),
+                 "steps": len(tms), "iterations": st64["iterations"], "rel_residual": st64["rel_residual"]}
+    p.close()
+
+    # end-to-end through the public API from pinned host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        host = {k: torch.from_numpy(np.ascontiguousarray(getattr(prob, k))).pin_memory()
+                for k in ("dplus", "dminus", "u0", "f")}
+        xh = torch.empty(prob.n, dtype=torch.float64).pin_memory()
+        h2d = sum(t.numel() * 8 for t in host.values())
+        d2h = prob.n * 8
+
+        def e2e_step():
+            q = fde.FDEProblem(m=prob.m, s=prob.s, alpha=prob.alpha, xL=prob.xL, xR=prob.xR, t0=prob.t0, T=prob.T,
+                               dplus=host["dplus"].numpy(), dminus=host["dminus"].numpy(), u0=host["u0"].numpy(),
+                               f=host["f"].numpy(), family=prob.family, mu=prob.mu, device_inputs=False)
+            q.assemble().factor(args.precision)
+            x, _ = q.solve(tol=args.tol, restart=20, maxit=400)
+            xh.copy_(x, non_blocking=True)
+            torch.cuda.synchronize()
+            q.close()
+
+        e2e_step()
+        barrier()
+        t0 = time.perf_counter()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        e1.record()
+        e1.synchronize()
+        wall = time.perf_counter() - t0
+        ev = e0.elapsed_time(e1) / 1e3
+        e2e = {"value": world * args.e2e_steps / max(ev, wall), "unit": "solves/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "steps": args.e2e_steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        its = int(np.median([s["iterations"] for s in stats]))
+        cpu = oracle_sample(prob, iterations=its)
+        cpu.pop("seconds_per_solve", None)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64" if args.precision != "fp64" else "f64", "data": "synthetic",
+            "config": workload, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clocks, "iterations": [s["iterations"] for s in stats],
+            "rel_residual": stats[-1]["rel_residual"], "rel_residual_oracle_matvec": res_oracle,
+            "plain_fp64": plain, "stage_ms_per_step": stage_ms, "stage_launches_per_step": stage_n,
+            "per_step_ms": per_step,
+        }
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -178,6 +178,34 @@ int fde_get_grunwald(fde_problem* p, double* g);
 /* Sizes of a created problem: n = s*m unknowns, number of Strang blocks s/2+1. */
 int fde_problem_sizes(const fde_problem* p, int* m, int* s, int* nblocks);
 
+/* ---- measurement ---------------------------------------------------------- */
+
+/* Stages timed by the per-problem profiler. */
+#define FDE_STAGE_ASSEMBLE 0   /* Grunwald weights, twiddles, symbols, J u0, b */
+#define FDE_STAGE_FORM 1       /* forming the Strang blocks phi_k I - h psi_k J */
+#define FDE_STAGE_LU_DIAG 2    /* LU of the diagonal NB x NB blocks */
+#define FDE_STAGE_LU_PANEL 3   /* panel triangular solves */
+#define FDE_STAGE_LU_UPDATE 4  /* trailing complex GEMM updates (CUDA or tensor cores) */
+#define FDE_STAGE_TFFT_FWD 5   /* FFT along time */
+#define FDE_STAGE_TRSV 6       /* block forward / backward substitution */
+#define FDE_STAGE_TFFT_INV 7   /* inverse FFT along time */
+#define FDE_STAGE_MATVEC 8     /* M z */
+#define FDE_STAGE_KRYLOV 9     /* Gram-Schmidt, norms, Givens, updates */
+#define FDE_NUM_STAGES 10
+
+/* on != 0: record a CUDA event pair around every kernel launch of this problem
+ * (on its stream) and clear previous records; on == 0: stop recording.
+ * Errors: FDE_ERR_ARG. */
+int fde_profile_enable(fde_problem* p, int on);
+
+/* Total device time (ms, summed over launches) and number of launches recorded
+ * for one stage since fde_profile_enable.  Synchronises the problem's stream.
+ * Errors: FDE_ERR_ARG, FDE_ERR_CUDA. */
+int fde_profile_read(fde_problem* p, int stage, double* total_ms, int* launches);
+
+/* Number of kernels this library has launched in this process (all problems). */
+long long fde_launch_count(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -60,6 +60,7 @@ __all__ = [
     "strang_symbols",
     "strang_circulant",
     "strang_matrix",
+    "strang_matvec",
     "StrangPreconditioner",
     "gmres",
     "solve_strang_gmres",
@@ -318,6 +319,18 @@ def strang_matrix(prob) -> np.ndarray:
     sB = strang_circulant(b, nu, prob.s)
     J = j_of(prob)
     return np.kron(sA, np.eye(prob.m)) - prob.h * np.kron(sB, J)
+
+
+def strang_matvec(prob, z: np.ndarray, J=None) -> np.ndarray:
+    """S z with S = s(A) (x) I - h s(B) (x) J of eq. (1.11), by its Kronecker form."""
+    if J is None:
+        J = j_of(prob)
+    nu = nu_of(prob.family, prob.mu)
+    a, b = lmf_coefficients(prob.family, prob.mu, nu)
+    sA = strang_circulant(a, nu, prob.s)
+    sB = strang_circulant(b, nu, prob.s)
+    Z = z.reshape(prob.s, prob.m)
+    return (sA @ Z - prob.h * (sB @ Z) @ J.T).reshape(-1)
 
 
 class StrangPreconditioner:

@@ -60,6 +60,10 @@ def pgmres_solve(h, opts: FdePgmresOpts, x0_ptr: int | None, x_ptr: int, raise_o
     return st
 
 
+def fde_launch_count() -> int:
+    return int(_lib.load().fde_launch_count())
+
+
 def fde_problem_destroy(h) -> None:
     if h:
         _lib.load().fde_problem_destroy(h)
@@ -170,6 +174,19 @@ class FDEProblem:
         _lib.check(_lib.load().fde_get_factor_block(self.h, int(k), C.c_void_p(re.ctypes.data),
                                                      C.c_void_p(im.ctypes.data)), "fde_get_factor_block")
         return re + 1j * im
+
+    def profile(self, on: bool = True):
+        _lib.check(_lib.load().fde_profile_enable(self.h, 1 if on else 0), "fde_profile_enable")
+        return self
+
+    def profile_read(self) -> dict:
+        out = {}
+        for i, name in enumerate(_lib.STAGES):
+            ms = C.c_double()
+            cnt = C.c_int()
+            _lib.check(_lib.load().fde_profile_read(self.h, i, C.byref(ms), C.byref(cnt)), "fde_profile_read")
+            out[name] = (ms.value, cnt.value)
+        return out
 
     def close(self):
         if getattr(self, "h", None):

@@ -1,6 +1,7 @@
 // C ABI of libfde (declared in include/fde.h): problem lifecycle, BVM coefficient
 // derivation, and the host driver of the flexible GMRES iteration.  All numerical
 // work of the path runs in the kernels of the other translation units.
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -25,6 +26,35 @@ int set_error(int code, const std::string& msg) {
 int cuda_error(cudaError_t e, const char* what) {
     g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
     return FDE_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// launch counter and per-stage profiler
+// ---------------------------------------------------------------------------
+static std::atomic<long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+static cudaEvent_t next_event(Problem& P) {
+    if (P.ev_used == P.ev_pool.size()) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        P.ev_pool.push_back(e);
+    }
+    return P.ev_pool[P.ev_used++];
+}
+
+StageTimer::StageTimer(Problem& P, int stage) : P_(&P), stage_(stage) {
+    if (!P.prof) return;
+    e0_ = next_event(P);
+    if (e0_) cudaEventRecord(e0_, P.stream);
+}
+
+StageTimer::~StageTimer() {
+    if (!P_->prof || !e0_) return;
+    cudaEvent_t e1 = next_event(*P_);
+    if (!e1) return;
+    cudaEventRecord(e1, P_->stream);
+    P_->prof_rec[stage_].push_back({e0_, e1});
 }
 
 // ---------------------------------------------------------------------------
@@ -166,9 +196,21 @@ static int ensure_workspace(Problem& P, int restart) {
 
 static int apply_precond(Problem& P, const double* r, double* z) {
     int rc;
-    if ((rc = launch_time_fft_fwd(P, r, P.d_rhat, P.precision, P.stream))) return rc;
-    if ((rc = launch_block_trsv(P, P.d_rhat, P.stream))) return rc;
+    {
+        StageTimer t(P, FDE_STAGE_TFFT_FWD);
+        if ((rc = launch_time_fft_fwd(P, r, P.d_rhat, P.precision, P.stream))) return rc;
+    }
+    {
+        StageTimer t(P, FDE_STAGE_TRSV);
+        if ((rc = launch_block_trsv(P, P.d_rhat, P.stream))) return rc;
+    }
+    StageTimer t(P, FDE_STAGE_TFFT_INV);
     return launch_time_fft_inv(P, P.d_rhat, z, P.precision, P.stream);
+}
+
+static int matvec(Problem& P, const double* z, double* y) {
+    StageTimer t(P, FDE_STAGE_MATVEC);
+    return launch_matvec64(P, z, y, P.stream);
 }
 
 // ||v||^2 on the device into d_scal[slot]; optionally returned to the host (synchronises).
@@ -367,7 +409,36 @@ void fde_problem_destroy(fde_problem* h) {
                     P.d_fac, P.d_dinv, P.d_info, P.d_scal, P.d_partial, P.d_counter};
     for (void* b : bufs) dfree(b);
     if (h->pinned) cudaFreeHost(h->pinned);
+    for (cudaEvent_t e : P.ev_pool) cudaEventDestroy(e);
     delete h;
+}
+
+long long fde_launch_count(void) { return g_launches.load(); }
+
+int fde_profile_enable(fde_problem* h, int on) {
+    if (!h) return set_error(FDE_ERR_ARG, "NULL problem");
+    Problem& P = h->P;
+    if (P.stream) cudaStreamSynchronize(P.stream);
+    else cudaDeviceSynchronize();
+    for (auto& r : P.prof_rec) r.clear();
+    P.ev_used = 0;
+    P.prof = on != 0;
+    return FDE_OK;
+}
+
+int fde_profile_read(fde_problem* h, int stage, double* total_ms, int* launches) {
+    if (!h || stage < 0 || stage >= FDE_NUM_STAGES) return set_error(FDE_ERR_ARG, "bad problem or stage");
+    Problem& P = h->P;
+    FDE_CUDA_TRY(cudaStreamSynchronize(P.stream));
+    double tot = 0.0;
+    for (auto& pr : P.prof_rec[stage]) {
+        float ms = 0.f;
+        FDE_CUDA_TRY(cudaEventElapsedTime(&ms, pr.first, pr.second));
+        tot += ms;
+    }
+    if (total_ms) *total_ms = tot;
+    if (launches) *launches = (int)P.prof_rec[stage].size();
+    return FDE_OK;
 }
 
 int fde_problem_sizes(const fde_problem* h, int* m, int* s, int* nblocks) {
@@ -384,6 +455,7 @@ int bvm_assemble(fde_problem* h) {
     Problem& P = h->P;
     int rc;
     double* d_main = nullptr;
+    StageTimer timer(P, FDE_STAGE_ASSEMBLE);
     if ((rc = launch_grunwald(P.alpha, P.m + 2, P.d_g, P.stream))) return rc;
     if ((rc = launch_twiddles(P.L, P.d_twL, P.d_twL32, P.stream))) return rc;
     if ((rc = launch_twiddles(P.s, P.d_tws, P.d_tws32, P.stream))) return rc;
@@ -462,7 +534,7 @@ int fde_matvec(fde_problem* h, const double* z, double* y) {
     g_last_error.clear();
     if (!h || !z || !y) return set_error(FDE_ERR_ARG, "NULL argument");
     if (!h->P.assembled) return set_error(FDE_ERR_STATE, "bvm_assemble must run first");
-    return launch_matvec64(h->P, z, y, h->P.stream);
+    return matvec(h->P, z, y);
 }
 
 int fde_precond_apply(fde_problem* h, const double* r, double* z) {
@@ -575,7 +647,7 @@ int pgmres_solve(fde_problem* h, const fde_pgmres_opts* opts, const double* x0, 
     }
     // r = b - M x -> V_0
     if (x0) {
-        if ((rc = launch_matvec64(P, x, P.d_work, st))) return finish(rc);
+        if ((rc = matvec(P, x, P.d_work))) return finish(rc);
         if ((rc = launch_sub(P.d_b_rhs, P.d_work, V, n, st))) return finish(rc);
     } else {
         cudaError_t e = cudaMemcpyAsync(V, P.d_b_rhs, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
@@ -604,7 +676,8 @@ int pgmres_solve(fde_problem* h, const fde_pgmres_opts* opts, const double* x0, 
             double* w = V + (size_t)(j + 1) * n;
             double* zj = Z + (size_t)j * n;
             if ((rc = apply_precond(P, vj, zj))) return finish(rc);
-            if ((rc = launch_matvec64(P, zj, w, st))) return finish(rc);
+            if ((rc = matvec(P, zj, w))) return finish(rc);
+            StageTimer kt(P, FDE_STAGE_KRYLOV);
             if ((rc = launch_dots(V, j + 1, w, n, sc, P.d_partial, P.d_counter, st))) return finish(rc);
             if ((rc = launch_update(V, j + 1, sc, -1.0, w, n, st))) return finish(rc);
             if (o.reorth) {
@@ -636,7 +709,7 @@ int pgmres_solve(fde_problem* h, const fde_pgmres_opts* opts, const double* x0, 
         if ((rc = launch_update(Z, k, P.d_y, 1.0, x, n, st))) return finish(rc);
         ++S.restarts;
         S.rel_residual_estimate = est / bnorm;
-        if ((rc = launch_matvec64(P, x, P.d_work, st))) return finish(rc);
+        if ((rc = matvec(P, x, P.d_work))) return finish(rc);
         if ((rc = launch_sub(P.d_b_rhs, P.d_work, V, n, st))) return finish(rc);
         if ((rc = norm2(P, V, 132, &beta2, pin))) return finish(rc);
     }

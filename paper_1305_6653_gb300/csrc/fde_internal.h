@@ -5,6 +5,8 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "../../include/fde.h"
 
@@ -22,8 +24,11 @@ int cuda_error(cudaError_t e, const char* what);
         if (e_ != cudaSuccess) return ::fde::cuda_error(e_, #call); \
     } while (0)
 
+void note_launch();
+
 #define FDE_LAUNCH_CHECK(what)                               \
     do {                                                     \
+        ::fde::note_launch();                                \
         cudaError_t e_ = cudaGetLastError();                 \
         if (e_ != cudaSuccess) return ::fde::cuda_error(e_, what); \
     } while (0)
@@ -34,22 +39,6 @@ inline int ilog2(int v) {
     return r;
 }
 inline int round_up(int v, int q) { return (v + q - 1) / q * q; }
-
-// ---------------------------------------------------------------------------
-// Per-problem constants used by the kernels (kept in device memory).
-// ---------------------------------------------------------------------------
-struct BandRow {
-    int start;  // first full-system column (0..s-mu) of the formula for this row
-};
-
-// Row t = 1..s of (A, B) (eqs. (1.7)-(1.9)): mu+1 coefficients starting at column start[t].
-struct DeviceBand {
-    int mu;
-    int s;
-    const int* start;      // [s+1]
-    const double* a;       // [(s+1) * (mu+1)]
-    const double* b;       // [(s+1) * (mu+1)]
-};
 
 // ---------------------------------------------------------------------------
 // kernel launchers (defined in the .cu files)
@@ -148,6 +137,25 @@ struct Problem {
     bool assembled = false;
     bool factored = false;
     int precision = -1;
+
+    // per-stage CUDA-event profiler (fde_profile_enable)
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_rec[FDE_NUM_STAGES];
+};
+
+// Records a CUDA event pair around the launches made in its scope when the
+// problem's profiler is on.
+class StageTimer {
+  public:
+    StageTimer(Problem& P, int stage);
+    ~StageTimer();
+
+  private:
+    Problem* P_;
+    int stage_;
+    cudaEvent_t e0_ = nullptr;
 };
 
 }  // namespace fde

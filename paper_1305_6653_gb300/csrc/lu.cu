@@ -359,6 +359,7 @@ static int run_lu(Problem& P, cudaStream_t st) {
     const int mp = P.mp, nb = P.nblk;
     {
         dim3 grid(nb >= 1216 ? 1 : 1216 / nb, nb);
+        StageTimer t(P, FDE_STAGE_FORM);
         form_blocks_kernel<T><<<grid, 256, 0, st>>>(P.m, mp, P.h, P.dxa, P.d_g, P.d_dplus, P.d_dminus, P.d_phi,
                                                    P.d_psi, fac);
         FDE_LAUNCH_CHECK("form_blocks_kernel");
@@ -367,14 +368,21 @@ static int run_lu(Problem& P, cudaStream_t st) {
     FDE_CUDA_TRY(cudaFuncSetAttribute(lu_update_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)upd_smem));
     const int steps = mp / NB;
     for (int p = 0; p < steps; ++p) {
-        lu_diag_kernel<T><<<nb, 256, 0, st>>>(mp, p, fac, dinv, P.d_info);
-        FDE_LAUNCH_CHECK("lu_diag_kernel");
+        {
+            StageTimer t(P, FDE_STAGE_LU_DIAG);
+            lu_diag_kernel<T><<<nb, 256, 0, st>>>(mp, p, fac, dinv, P.d_info);
+            FDE_LAUNCH_CHECK("lu_diag_kernel");
+        }
         const int rem = mp - (p + 1) * NB;
         if (rem <= 0) break;
         const int nch = (rem + RC - 1) / RC;
-        lu_panel_kernel<T><<<dim3(2 * nch, nb), 256, 0, st>>>(mp, p, nch, fac);
-        FDE_LAUNCH_CHECK("lu_panel_kernel");
+        {
+            StageTimer t(P, FDE_STAGE_LU_PANEL);
+            lu_panel_kernel<T><<<dim3(2 * nch, nb), 256, 0, st>>>(mp, p, nch, fac);
+            FDE_LAUNCH_CHECK("lu_panel_kernel");
+        }
         const int nt = (rem + 63) / 64;
+        StageTimer t(P, FDE_STAGE_LU_UPDATE);
         lu_update_kernel<T><<<dim3(nt * nt, nb), 256, upd_smem, st>>>(mp, p, nt, fac);
         FDE_LAUNCH_CHECK("lu_update_kernel");
     }

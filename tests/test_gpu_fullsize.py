@@ -1,0 +1,78 @@
+"""Parity at the benchmarked size (m=2047, s=256, 5-step GBDF, alpha=1.8,
+d+=1+x, d-=2-x; 524,032 unknowns, 129 complex 2047 x 2047 Strang blocks), in the
+launch configuration bench.py times.
+
+* Full solution against the oracle's FP64 Strang-preconditioned FGMRES
+  (dense LAPACK LU per frequency, tol 1e-12): ||x - x_oracle|| / ||x_oracle|| <= 1e-8.
+* Properties that hold at any size, with the oracle's independent Kronecker
+  matvecs: the true residual ||b - M x|| / ||b||, and S z = r for the
+  preconditioner output (S is invertible, Theorem 3.1, so z is unique).
+* Sampled factors: L_k U_k = phi_k I - h psi_k J on sampled rows / columns.
+"""
+import numpy as np
+import pytest
+
+import fde_inputs as fi
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def setup():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    prob = fi.config_scale()
+    J = O.j_of(prob)
+    b = O.reduced_rhs(prob, J=J)
+    return prob, J, b
+
+
+@pytest.fixture(scope="module")
+def oracle_solution(setup):
+    prob, J, b = setup
+    x, its, ok, _ = O.solve_strang_gmres(prob, side="right", tol=1e-12)
+    assert ok
+    return x
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_fullsize_solve(setup, oracle_solution, precision):
+    from paper_1305_6653_gb300 import FDEProblem
+    prob, J, b = setup
+    with FDEProblem.from_inputs(prob, device_inputs=True) as p:
+        p.assemble().factor(precision)
+        x, st = p.solve(tol=1e-10, restart=20, maxit=400)
+        xs = x.cpu().numpy()
+        # preconditioner output satisfies S z = r (oracle Kronecker S)
+        r = np.random.default_rng(3).standard_normal(prob.n)
+        z = p.precond_apply(torch.as_tensor(r, device="cuda")).cpu().numpy()
+    assert st["status"] == 0
+    res = np.linalg.norm(b - O.matvec(prob, xs, J=J)) / np.linalg.norm(b)
+    assert res <= 1e-10
+    err = np.linalg.norm(xs - oracle_solution) / np.linalg.norm(oracle_solution)
+    assert err <= 1e-8, err
+    srel = np.linalg.norm(O.strang_matvec(prob, z, J=J) - r) / np.linalg.norm(r)
+    assert srel <= (1e-11 if precision == "fp64" else 1e-3), srel
+
+
+def test_fullsize_factor_samples(setup):
+    from paper_1305_6653_gb300 import FDEProblem
+    prob, J, b = setup
+    phi, psi = O.strang_symbols(prob.family, prob.mu, prob.s)
+    rng = np.random.default_rng(9)
+    with FDEProblem.from_inputs(prob) as p:
+        p.assemble().factor("fp32")
+        for k in (0, 1, 64, 128):
+            F = p.factor_block(k)
+            rows = rng.choice(prob.m, 6, replace=False)
+            cols = rng.choice(prob.m, 6, replace=False)
+            Lr = np.tril(F[rows], -1)
+            Lr[np.arange(6), rows] = 1.0
+            Uc = np.triu(F[:, cols])
+            LU = Lr @ Uc
+            B = phi[k] * (rows[:, None] == cols[None, :]) - prob.h * psi[k] * J[np.ix_(rows, cols)]
+            scale = np.abs(phi[k]) + prob.h * np.abs(psi[k]) * np.abs(J).max()
+            assert np.abs(LU - B).max() <= 3e-5 * scale, k

@@ -65,6 +65,13 @@ def test_strang_apply_equals_dense_inverse(m, s, scheme, sym):
     np.testing.assert_allclose(P.apply(r), np.linalg.solve(S, r), rtol=1e-11, atol=1e-13)
 
 
+@pytest.mark.parametrize("m,s,scheme", [(5, 12, "GBDF3"), (6, 16, "GBDF5"), (7, 8, "GAM4")])
+def test_strang_matvec_matches_dense(m, s, scheme):
+    p = _tiny(m, s, scheme)
+    z = np.random.default_rng(4).standard_normal(m * s)
+    np.testing.assert_allclose(O.strang_matvec(p, z), O.strang_matrix(p) @ z, rtol=1e-12, atol=1e-10)
+
+
 @pytest.mark.parametrize("m,s,scheme", [(5, 12, "GBDF3"), (6, 16, "GBDF5"), (5, 12, "GAM4"), (4, 10, "ETR3")])
 def test_theorem_3_3_rank_and_iterations(m, s, scheme):
     """S^{-1} M = I + L with rank L <= 2 m mu; full GMRES converges in <= rank + 1 steps."""
