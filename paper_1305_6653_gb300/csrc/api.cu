@@ -365,6 +365,7 @@ int fde_problem_create(const fde_problem_desc* d, void* stream, fde_problem** ou
     TRY(dalloc(&P.d_partial, (size_t)304 * 64));
     TRY(dalloc(&P.d_counter, 4));
     TRY(dalloc(&P.d_info, (size_t)P.nblk));
+    TRY(dalloc(&P.d_err, 1));
     if (cudaMallocHost((void**)&h->pinned, 64 * sizeof(double)) != cudaSuccess) {
         h->pinned = nullptr;
         fde_problem_destroy(h);
@@ -406,7 +407,7 @@ void fde_problem_destroy(fde_problem* h) {
     free_workspace(P);
     void* bufs[] = {P.d_start, P.d_a, P.d_b, P.d_dplus, P.d_dminus, P.d_u0, P.d_f, P.d_g, P.d_twL, P.d_twL32,
                     P.d_sym, P.d_sym32, P.d_tws, P.d_tws32, P.d_phi, P.d_psi, P.d_b_rhs, P.d_work, P.d_rhat,
-                    P.d_fac, P.d_dinv, P.d_info, P.d_scal, P.d_partial, P.d_counter};
+                    P.d_fac, P.d_dinv, P.d_info, P.d_err, P.d_pack, P.d_scal, P.d_partial, P.d_counter};
     for (void* b : bufs) dfree(b);
     if (h->pinned) cudaFreeHost(h->pinned);
     for (cudaEvent_t e : P.ev_pool) cudaEventDestroy(e);
@@ -492,8 +493,8 @@ int strang_precond_factor(fde_problem* h, int precision) {
     if (!h) return set_error(FDE_ERR_ARG, "NULL problem");
     Problem& P = h->P;
     if (!P.assembled) return set_error(FDE_ERR_STATE, "bvm_assemble must run before strang_precond_factor");
-    if (precision != FDE_FP64 && precision != FDE_FP32)
-        return set_error(FDE_ERR_ARG, "precision not supported by this build");
+    if (precision != FDE_FP64 && precision != FDE_FP32 && precision != FDE_TF32 && precision != FDE_BF16)
+        return set_error(FDE_ERR_ARG, "precision must be FDE_FP64, FDE_FP32, FDE_TF32 or FDE_BF16");
     const size_t esz = precision == FDE_FP64 ? sizeof(double) : sizeof(float);
     const size_t fac_bytes = (size_t)P.nblk * 2 * P.mp * P.mp * esz;
     int rc;
@@ -516,10 +517,14 @@ int strang_precond_factor(fde_problem* h, int precision) {
     P.factored = false;
     P.precision = precision;
     FDE_CUDA_TRY(cudaMemsetAsync(P.d_info, 0, P.nblk * sizeof(int), P.stream));
+    FDE_CUDA_TRY(cudaMemsetAsync(P.d_err, 0, sizeof(int), P.stream));
     if ((rc = launch_block_lu(P, precision, P.stream))) return rc;
     std::vector<int> info(P.nblk);
+    int derr = 0;
     FDE_CUDA_TRY(cudaMemcpyAsync(info.data(), P.d_info, P.nblk * sizeof(int), cudaMemcpyDeviceToHost, P.stream));
+    FDE_CUDA_TRY(cudaMemcpyAsync(&derr, P.d_err, sizeof(int), cudaMemcpyDeviceToHost, P.stream));
     FDE_CUDA_TRY(cudaStreamSynchronize(P.stream));
+    if (derr) return set_error(FDE_ERR_TIMEOUT, "a bounded wait in the tensor-core LU update ran out");
     for (int k = 0; k < P.nblk; ++k)
         if (info[k]) {
             char buf[128];

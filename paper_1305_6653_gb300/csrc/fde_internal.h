@@ -119,7 +119,10 @@ struct Problem {
     void* d_fac = nullptr;      // nblk * 2 * mp * mp (planar re/im), FP64 or FP32
     void* d_dinv = nullptr;     // nblk * mp complex: 1 / U_ii
     int* d_info = nullptr;      // nblk: first singular pivot (+1) or 0
+    int* d_err = nullptr;       // device error flag of bounded waits (0 = none)
     size_t fac_bytes = 0;
+    void* d_pack = nullptr;     // packed tensor-core operand tiles of the LU panels
+    size_t pack_bytes = 0;
 
     // Krylov workspace
     int restart_cap = 0;

@@ -16,6 +16,7 @@
 //                 variant lives in lu_tc.cu)
 #include "fde_internal.h"
 #include "fft_device.cuh"
+#include "lu_tc.cuh"
 
 namespace fde {
 
@@ -110,9 +111,12 @@ lu_diag_kernel(int mp, int p, T* __restrict__ fac, cplx_t<T>* __restrict__ dinv,
 // Panel solves.  blockIdx.x < nrow: a chunk of RC rows of A21 -> L21 = A21 U11^{-1};
 // otherwise a chunk of RC columns of A12 -> U12 = L11^{-1} A12.
 constexpr int RC = 32;
-template <typename T>
+// PACK < 0: plain; PACK = 0 / 1: also write the panels as packed TF32 / BF16
+// tensor-core operand tiles (A' from L21 rows, B' from U12 columns; see lu_tc.cuh).
+template <typename T, int PACK>
 __global__ void __launch_bounds__(256)
-lu_panel_kernel(int mp, int p, int nrow, T* __restrict__ fac) {
+lu_panel_kernel(int mp, int p, int nrow, T* __restrict__ fac, unsigned char* __restrict__ apack,
+                unsigned char* __restrict__ bpack, int ntile_max) {
     using C = cplx_t<T>;
     __shared__ C D[NB][NB + 1];
     __shared__ C X[RC][NB + 1];
@@ -182,6 +186,22 @@ lu_panel_kernel(int mp, int p, int nrow, T* __restrict__ fac) {
         if (b0 + q < mp) {
             re[idx] = X[q][c].x;
             im[idx] = X[q][c].y;
+        }
+        if constexpr (PACK >= 0) {
+            const int tile = chunk >> 2;
+            const int rt = (chunk & 3) * RC + q;  // row of the operand tile (A': output row, B': output column)
+            const float vr = (float)X[q][c].x, vi = (float)X[q][c].y;
+            if (rows) {
+                unsigned char* t = apack + ((size_t)k * ntile_max + tile) * TcCfg<PACK>::A_BYTES;
+                pack_store<PACK>(t, rt, c, vr);
+                pack_store<PACK>(t, rt, NB + c, vi);
+            } else {
+                unsigned char* t = bpack + ((size_t)k * ntile_max + tile) * TcCfg<PACK>::B_BYTES;
+                pack_store<PACK>(t, rt, c, vr);            // Re part of the product: Re L Re U - Im L Im U
+                pack_store<PACK>(t, rt, NB + c, -vi);
+                pack_store<PACK>(t, TC_BN + rt, c, vi);    // Im part: Re L Im U + Im L Re U
+                pack_store<PACK>(t, TC_BN + rt, NB + c, vr);
+            }
         }
     }
 }
@@ -378,7 +398,7 @@ static int run_lu(Problem& P, cudaStream_t st) {
         const int nch = (rem + RC - 1) / RC;
         {
             StageTimer t(P, FDE_STAGE_LU_PANEL);
-            lu_panel_kernel<T><<<dim3(2 * nch, nb), 256, 0, st>>>(mp, p, nch, fac);
+            lu_panel_kernel<T, -1><<<dim3(2 * nch, nb), 256, 0, st>>>(mp, p, nch, fac, nullptr, nullptr, 0);
             FDE_LAUNCH_CHECK("lu_panel_kernel");
         }
         const int nt = (rem + 63) / 64;
@@ -389,8 +409,67 @@ static int run_lu(Problem& P, cudaStream_t st) {
     return FDE_OK;
 }
 
+// FP32 factors whose trailing updates run on the tcgen05 tensor cores.
+template <int KIND>
+static int run_lu_tc(Problem& P, cudaStream_t st) {
+    using Cfg = TcCfg<KIND>;
+    static_assert(TC_KP == 2 * NB, "packed K' must be 2 NB");
+    float* fac = reinterpret_cast<float*>(P.d_fac);
+    float2* dinv = reinterpret_cast<float2*>(P.d_dinv);
+    const int mp = P.mp, nb = P.nblk;
+    const int ntile_max = (mp - NB + TC_BM - 1) / TC_BM;
+    const size_t abytes = (size_t)nb * ntile_max * Cfg::A_BYTES;
+    const size_t bbytes = (size_t)nb * ntile_max * Cfg::B_BYTES;
+    if (P.pack_bytes < abytes + bbytes) {
+        if (P.d_pack) cudaFree(P.d_pack);
+        P.d_pack = nullptr;
+        P.pack_bytes = 0;
+        FDE_CUDA_TRY(cudaMalloc(&P.d_pack, abytes + bbytes));
+        P.pack_bytes = abytes + bbytes;
+        FDE_CUDA_TRY(cudaMemsetAsync(P.d_pack, 0, abytes + bbytes, st));
+    }
+    unsigned char* apack = reinterpret_cast<unsigned char*>(P.d_pack);
+    unsigned char* bpack = apack + abytes;
+    {
+        dim3 grid(nb >= 1216 ? 1 : 1216 / nb, nb);
+        StageTimer t(P, FDE_STAGE_FORM);
+        form_blocks_kernel<float><<<grid, 256, 0, st>>>(P.m, mp, P.h, P.dxa, P.d_g, P.d_dplus, P.d_dminus,
+                                                        P.d_phi, P.d_psi, fac);
+        FDE_LAUNCH_CHECK("form_blocks_kernel");
+    }
+    // at most 2 CTAs per SM: each holds 256 of the SM's 512 TMEM columns
+    const int smem = (Cfg::A_BYTES + Cfg::B_BYTES) > 100 * 1024 ? (Cfg::A_BYTES + Cfg::B_BYTES) : 100 * 1024;
+    FDE_CUDA_TRY(cudaFuncSetAttribute(lu_update_tc_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    const int steps = mp / NB;
+    for (int p = 0; p < steps; ++p) {
+        {
+            StageTimer t(P, FDE_STAGE_LU_DIAG);
+            lu_diag_kernel<float><<<nb, 256, 0, st>>>(mp, p, fac, dinv, P.d_info);
+            FDE_LAUNCH_CHECK("lu_diag_kernel");
+        }
+        const int rest = (p + 1) * NB;
+        const int rem = mp - rest;
+        if (rem <= 0) break;
+        const int nch = (rem + RC - 1) / RC;
+        {
+            StageTimer t(P, FDE_STAGE_LU_PANEL);
+            lu_panel_kernel<float, KIND><<<dim3(2 * nch, nb), 256, 0, st>>>(mp, p, nch, fac, apack, bpack,
+                                                                            ntile_max);
+            FDE_LAUNCH_CHECK("lu_panel_kernel");
+        }
+        const int nt = (rem + TC_BM - 1) / TC_BM;
+        StageTimer t(P, FDE_STAGE_LU_UPDATE);
+        lu_update_tc_kernel<KIND><<<dim3(nt * nt, nb), 128, smem, st>>>(mp, rest, nt, ntile_max, fac, apack, bpack,
+                                                                        P.d_err);
+        FDE_LAUNCH_CHECK("lu_update_tc_kernel");
+    }
+    return FDE_OK;
+}
+
 int launch_block_lu(Problem& P, int prec, cudaStream_t st) {
     if (prec == FDE_FP64) return run_lu<double>(P, st);
+    if (prec == FDE_TF32) return run_lu_tc<0>(P, st);
+    if (prec == FDE_BF16) return run_lu_tc<1>(P, st);
     return run_lu<float>(P, st);
 }
 
