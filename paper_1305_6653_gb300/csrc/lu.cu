@@ -268,103 +268,142 @@ lu_update_kernel(int mp, int p, int ntile, T* __restrict__ fac) {
 }
 
 // Forward (unit lower L) then backward (U) substitution for one block per CTA,
-// in place on rhat[k] (length mp).  Rows in tiles of 32: 16 warps form the partial
-// products of a tile against the solved part (coalesced row reads of the factor
-// planes), then warp 0 resolves the 32 x 32 diagonal tile with shuffles.
+// in place on rhat[k] (length mp), column-oriented ("right-looking"): for each
+// 32-row diagonal tile, warp 0 resolves the tile from shared memory, then all
+// warps subtract the tile's 32-column strip of L (or U) times the new 32 values
+// from the remaining right-hand side.  In the strip update eight threads share a
+// row (one contiguous 32-value segment per plane), every load is independent of
+// the others, and the next diagonal tile is prefetched into shared memory, so
+// the factor planes stream at full memory-level parallelism.
+template <typename T> struct vec4;
+template <> struct vec4<float> { using type = float4; };
+template <> struct vec4<double> { using type = double4; };
+
 template <typename T>
-__global__ void __launch_bounds__(512)
+__device__ __forceinline__ typename vec4<T>::type ld4(const T* p) {
+    return *reinterpret_cast<const typename vec4<T>::type*>(p);
+}
+
+constexpr int TRSV_THREADS = 512;
+constexpr int TRSV_TPR = 8;                              // threads per row in the strip update
+constexpr int TRSV_RPP = TRSV_THREADS / TRSV_TPR;        // rows per pass
+
+template <typename T>
+__device__ __forceinline__ void load_diag_tile(cplx_t<T> (*D)[33], const T* re, const T* im, int mp, int r0) {
+    for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+        const int q = e >> 5, c = e & 31;
+        const size_t idx = (size_t)(r0 + q) * mp + r0 + c;
+        D[q][c] = mk(re[idx], im[idx]);
+    }
+}
+
+// y[rows] -= strip[rows][c0 .. c0+32) * xs[0..32), rows in [rbeg, rend)
+template <typename T>
+__device__ __forceinline__ void strip_update(cplx_t<T>* y, const cplx_t<T>* xs, const T* re, const T* im, int mp,
+                                             int c0, int rbeg, int rend) {
+    using C = cplx_t<T>;
+    const int sub = threadIdx.x & (TRSV_TPR - 1);
+    const int c = c0 + sub * 4;
+    const C x0 = xs[sub * 4], x1 = xs[sub * 4 + 1], x2 = xs[sub * 4 + 2], x3 = xs[sub * 4 + 3];
+    for (int rb = rbeg + (int)(threadIdx.x / TRSV_TPR); rb < rend; rb += 4 * TRSV_RPP) {
+        typename vec4<T>::type ar[4], ai[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int r = rb + u * TRSV_RPP;
+            if (r < rend) {
+                ar[u] = ld4(re + (size_t)r * mp + c);
+                ai[u] = ld4(im + (size_t)r * mp + c);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int r = rb + u * TRSV_RPP;
+            T sx = ar[u].x * x0.x - ai[u].x * x0.y + ar[u].y * x1.x - ai[u].y * x1.y + ar[u].z * x2.x -
+                   ai[u].z * x2.y + ar[u].w * x3.x - ai[u].w * x3.y;
+            T sy = ar[u].x * x0.y + ai[u].x * x0.x + ar[u].y * x1.y + ai[u].y * x1.x + ar[u].z * x2.y +
+                   ai[u].z * x2.x + ar[u].w * x3.y + ai[u].w * x3.x;
+#pragma unroll
+            for (int off = 1; off < TRSV_TPR; off <<= 1) {
+                sx += __shfl_xor_sync(0xffffffffu, sx, off);
+                sy += __shfl_xor_sync(0xffffffffu, sy, off);
+            }
+            if (sub == 0 && r < rend) {
+                C v = y[r];
+                v.x -= sx;
+                v.y -= sy;
+                y[r] = v;
+            }
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TRSV_THREADS)
 block_trsv_kernel(int mp, const T* __restrict__ fac, const cplx_t<T>* __restrict__ dinv, cplx_t<T>* __restrict__ rhat) {
     using C = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* y = reinterpret_cast<C*>(smem_raw);  // mp
-    __shared__ C part[32];
+    C* y = reinterpret_cast<C*>(smem_raw);                        // mp
+    C (*D)[32][33] = reinterpret_cast<C (*)[32][33]>(y + mp);     // 2 diagonal tiles (double buffer)
+    __shared__ C xs[32];
     const int k = blockIdx.x;
     const T* re = fac + (size_t)k * 2 * mp * mp;
     const T* im = re + (size_t)mp * mp;
     C* x = rhat + (size_t)k * mp;
     const C* dv = dinv + (size_t)k * mp;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nt = mp / 32;
     for (int i = threadIdx.x; i < mp; i += blockDim.x) y[i] = x[i];
+    load_diag_tile<T>(D[0], re, im, mp, 0);
     __syncthreads();
     // forward: y <- L^{-1} y
-    for (int r0 = 0; r0 < mp; r0 += 32) {
-        for (int q = warp; q < 32; q += nwarp) {
-            const int r = r0 + q;
-            const T* lr = re + (size_t)r * mp;
-            const T* li = im + (size_t)r * mp;
-            T ax = 0, ay = 0;
-#pragma unroll 8
-            for (int j = lane; j < r0; j += 32) {
-                const T a = lr[j], b = li[j];
-                const C v = y[j];
-                ax += a * v.x - b * v.y;
-                ay += a * v.y + b * v.x;
-            }
-#pragma unroll
-            for (int off = 16; off; off >>= 1) {
-                ax += __shfl_xor_sync(0xffffffffu, ax, off);
-                ay += __shfl_xor_sync(0xffffffffu, ay, off);
-            }
-            if (lane == 0) part[q] = mk(ax, ay);
-        }
-        __syncthreads();
+    for (int t = 0; t < nt; ++t) {
+        const int r0 = t * 32;
         if (warp == 0) {
-            const int r = r0 + lane;
-            C a = csub(y[r], part[lane]);
-            const T* lr = re + (size_t)r * mp + r0;
-            const T* li = im + (size_t)r * mp + r0;
+            C a = y[r0 + lane];
             for (int c = 0; c < 32; ++c) {
                 const T yx = __shfl_sync(0xffffffffu, a.x, c);
                 const T yy = __shfl_sync(0xffffffffu, a.y, c);
                 if (lane > c) {
-                    const T lx = lr[c], ly = li[c];
-                    a.x -= lx * yx - ly * yy;
-                    a.y -= lx * yy + ly * yx;
+                    const C l = D[t & 1][lane][c];
+                    a.x -= l.x * yx - l.y * yy;
+                    a.y -= l.x * yy + l.y * yx;
                 }
             }
-            y[r] = a;
+            y[r0 + lane] = a;
+            xs[lane] = a;
+        }
+        __syncthreads();
+        if (t + 1 < nt) {
+            load_diag_tile<T>(D[(t + 1) & 1], re, im, mp, r0 + 32);
+            strip_update<T>(y, xs, re, im, mp, r0, r0 + 32, mp);
         }
         __syncthreads();
     }
     // backward: y <- U^{-1} y
-    for (int r0 = mp - 32; r0 >= 0; r0 -= 32) {
-        for (int q = warp; q < 32; q += nwarp) {
-            const int r = r0 + q;
-            const T* ur = re + (size_t)r * mp;
-            const T* ui = im + (size_t)r * mp;
-            T ax = 0, ay = 0;
-#pragma unroll 8
-            for (int j = r0 + 32 + lane; j < mp; j += 32) {
-                const T a = ur[j], b = ui[j];
-                const C v = y[j];
-                ax += a * v.x - b * v.y;
-                ay += a * v.y + b * v.x;
-            }
-#pragma unroll
-            for (int off = 16; off; off >>= 1) {
-                ax += __shfl_xor_sync(0xffffffffu, ax, off);
-                ay += __shfl_xor_sync(0xffffffffu, ay, off);
-            }
-            if (lane == 0) part[q] = mk(ax, ay);
-        }
-        __syncthreads();
+    load_diag_tile<T>(D[(nt - 1) & 1], re, im, mp, (nt - 1) * 32);
+    __syncthreads();
+    for (int t = nt - 1; t >= 0; --t) {
+        const int r0 = t * 32;
         if (warp == 0) {
-            const int r = r0 + lane;
-            C a = csub(y[r], part[lane]);
-            const T* ur = re + (size_t)r * mp + r0;
-            const T* ui = im + (size_t)r * mp + r0;
-            const C di = dv[r];
+            C a = y[r0 + lane];
+            const C di = dv[r0 + lane];
             for (int c = 31; c >= 0; --c) {
                 if (lane == c) a = cmul(a, di);
                 const T yx = __shfl_sync(0xffffffffu, a.x, c);
                 const T yy = __shfl_sync(0xffffffffu, a.y, c);
                 if (lane < c) {
-                    const T ux = ur[c], uy = ui[c];
-                    a.x -= ux * yx - uy * yy;
-                    a.y -= ux * yy + uy * yx;
+                    const C u = D[t & 1][lane][c];
+                    a.x -= u.x * yx - u.y * yy;
+                    a.y -= u.x * yy + u.y * yx;
                 }
             }
-            y[r] = a;
+            y[r0 + lane] = a;
+            xs[lane] = a;
+        }
+        __syncthreads();
+        if (t > 0) {
+            load_diag_tile<T>(D[(t - 1) & 1], re, im, mp, r0 - 32);
+            strip_update<T>(y, xs, re, im, mp, r0, 0, r0);
         }
         __syncthreads();
     }
@@ -475,17 +514,17 @@ int launch_block_lu(Problem& P, int prec, cudaStream_t st) {
 
 int launch_block_trsv(const Problem& P, void* rhat, cudaStream_t st) {
     if (P.precision == FDE_FP64) {
-        size_t smem = (size_t)P.mp * sizeof(double2);
+        size_t smem = ((size_t)P.mp + 2 * 32 * 33) * sizeof(double2);
         FDE_CUDA_TRY(cudaFuncSetAttribute(block_trsv_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          200 * 1024));
-        block_trsv_kernel<double><<<P.nblk, 512, smem, st>>>(P.mp, (const double*)P.d_fac,
-                                                              (const double2*)P.d_dinv, (double2*)rhat);
+                                          (int)smem));
+        block_trsv_kernel<double><<<P.nblk, TRSV_THREADS, smem, st>>>(P.mp, (const double*)P.d_fac,
+                                                                       (const double2*)P.d_dinv, (double2*)rhat);
     } else {
-        size_t smem = (size_t)P.mp * sizeof(float2);
+        size_t smem = ((size_t)P.mp + 2 * 32 * 33) * sizeof(float2);
         FDE_CUDA_TRY(cudaFuncSetAttribute(block_trsv_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          200 * 1024));
-        block_trsv_kernel<float><<<P.nblk, 512, smem, st>>>(P.mp, (const float*)P.d_fac, (const float2*)P.d_dinv,
-                                                             (float2*)rhat);
+                                          (int)smem));
+        block_trsv_kernel<float><<<P.nblk, TRSV_THREADS, smem, st>>>(P.mp, (const float*)P.d_fac,
+                                                                      (const float2*)P.d_dinv, (float2*)rhat);
     }
     FDE_LAUNCH_CHECK("block_trsv_kernel");
     return FDE_OK;

@@ -3,7 +3,7 @@ d+=1+x, d-=2-x; 524,032 unknowns, 129 complex 2047 x 2047 Strang blocks), in the
 launch configuration bench.py times.
 
 * Full solution against the oracle's FP64 Strang-preconditioned FGMRES
-  (dense LAPACK LU per frequency, tol 1e-12): ||x - x_oracle|| / ||x_oracle|| <= 1e-8.
+  (dense LAPACK LU per frequency, tol 1e-11): ||x - x_oracle|| / ||x_oracle|| <= 1e-8.
 * Properties that hold at any size, with the oracle's independent Kronecker
   matvecs: the true residual ||b - M x|| / ||b||, and S z = r for the
   preconditioner output (S is invertible, Theorem 3.1, so z is unique).
@@ -33,12 +33,13 @@ def setup():
 @pytest.fixture(scope="module")
 def oracle_solution(setup):
     prob, J, b = setup
-    x, its, ok, _ = O.solve_strang_gmres(prob, side="right", tol=1e-12)
+    # the oracle's FP64 FGMRES floors near 5e-12 at this size; 1e-11 takes ~24 iterations
+    x, its, ok, _ = O.solve_strang_gmres(prob, side="right", tol=1e-11, maxit=80)
     assert ok
     return x
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("precision", ["fp32", "fp64", "tf32"])
 def test_fullsize_solve(setup, oracle_solution, precision):
     from paper_1305_6653_gb300 import FDEProblem
     prob, J, b = setup
@@ -55,7 +56,7 @@ def test_fullsize_solve(setup, oracle_solution, precision):
     err = np.linalg.norm(xs - oracle_solution) / np.linalg.norm(oracle_solution)
     assert err <= 1e-8, err
     srel = np.linalg.norm(O.strang_matvec(prob, z, J=J) - r) / np.linalg.norm(r)
-    assert srel <= (1e-11 if precision == "fp64" else 1e-3), srel
+    assert srel <= {"fp64": 1e-11, "fp32": 1e-3, "tf32": 5e-2}[precision], srel
 
 
 def test_fullsize_factor_samples(setup):
