@@ -161,6 +161,24 @@ int fde_matvec(fde_problem* p, const double* z, double* y);
  * strang_precond_factor.  Errors: FDE_ERR_STATE, FDE_ERR_CUDA. */
 int fde_precond_apply(fde_problem* p, const double* r, double* z);
 
+/* z = S^{-1} r like fde_precond_apply, for callers that cannot allocate device
+ * memory at the time of the call: applications whose memory manager owns the
+ * whole device after start-up, or code that must not risk the implicit device
+ * synchronisation of cudaMalloc.  The paper has no counterpart; this is a
+ * deployment variant.  It allocates nothing: the frequency-domain scratch (the
+ * s/2+1 transformed right-hand sides, (s/2+1) * mp complex values in the factor
+ * precision) lives in a file-scope static device array of 8 MiB that every GPU
+ * loading the library holds until exit.  Problems whose scratch would exceed
+ * 8 MiB are rejected with FDE_ERR_ARG (FP64: (s/2+1)*mp <= 524288, FP32/TF32/BF16:
+ * <= 1048576).  The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one array and it keeps the last
+ * call's contents (each call overwrites everything it reads), so calls whose GPU
+ * work overlaps -- on different streams or problems -- race and must be
+ * serialised by the caller.  r, z: device, length s*m (may alias).  Requires
+ * strang_precond_factor.  Errors: FDE_ERR_ARG, FDE_ERR_STATE, FDE_ERR_CUDA. */
+int fde_precond_apply_noalloc(fde_problem* p, const double* r, double* z);
+
 /* Copy the assembled right-hand side b (device, length s*m).  Requires
  * bvm_assemble.  Errors: FDE_ERR_STATE, FDE_ERR_CUDA. */
 int fde_get_rhs(fde_problem* p, double* b);

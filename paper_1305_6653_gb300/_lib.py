@@ -35,6 +35,7 @@ EXPORTED = [
     "fde_problem_create", "bvm_assemble", "strang_precond_factor", "pgmres_solve", "fde_problem_destroy",
     "fde_last_error", "fde_matvec", "fde_precond_apply", "fde_get_rhs", "fde_get_factor_block",
     "fde_get_grunwald", "fde_problem_sizes", "fde_profile_enable", "fde_profile_read", "fde_launch_count",
+    "fde_precond_apply_noalloc",
 ]
 STAGES = ["assemble", "form", "lu_diag", "lu_panel", "lu_update", "tfft_fwd", "trsv", "tfft_inv", "matvec",
           "krylov"]
@@ -98,6 +99,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "fde_profile_enable": (i32, [vp, i32]),
         "fde_profile_read": (i32, [vp, i32, C.POINTER(f64), C.POINTER(i32)]),
         "fde_launch_count": (C.c_longlong, []),
+        "fde_precond_apply_noalloc": (i32, [vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

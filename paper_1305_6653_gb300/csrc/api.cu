@@ -234,6 +234,10 @@ struct fde_problem {
     double* pinned = nullptr;  // small pinned host buffer for device -> host scalars
 };
 
+namespace fde {
+Problem* problem_of(fde_problem* h) { return h ? &h->P : nullptr; }
+}  // namespace fde
+
 extern "C" {
 
 const char* fde_last_error(void) { return g_last_error.c_str(); }

@@ -148,6 +148,9 @@ struct Problem {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_rec[FDE_NUM_STAGES];
 };
 
+// The problem behind a C-ABI handle (defined in api.cu).
+Problem* problem_of(fde_problem* h);
+
 // Records a CUDA event pair around the launches made in its scope when the
 // problem's profiler is on.
 class StageTimer {
