@@ -38,6 +38,9 @@ __device__ __forceinline__ double j_entry(int i, int j, double dxa, const double
     return dxa * v;
 }
 
+// One CTA row-loop per matrix row, threads along the columns (no index division).
+// FP64 blocks are formed in FP64; FP32 blocks in FP32 from FP32 copies of the
+// per-row coefficients dx^-alpha d+_i, dx^-alpha d-_i and of h psi_k.
 template <typename T>
 __global__ void form_blocks_kernel(int m, int mp, double h, double dxa, const double* __restrict__ g,
                                    const double* __restrict__ dp, const double* __restrict__ dm,
@@ -45,23 +48,37 @@ __global__ void form_blocks_kernel(int m, int mp, double h, double dxa, const do
     const int k = blockIdx.y;
     const double2 ph = phi[k];
     const double2 ps = psi[k];
+    const T hpr = (T)(h * ps.x), hpi = (T)(h * ps.y);
     T* re = plane_re(fac, k, mp);
     T* im = plane_im(fac, k, mp);
-    const size_t total = (size_t)mp * mp;
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-        const int i = (int)(e / mp);
-        const int j = (int)(e - (size_t)i * mp);
-        double vr, vi;
-        if (i < m && j < m) {
-            const double jv = j_entry(i, j, dxa, g, dp, dm);
-            vr = (i == j ? ph.x : 0.0) - h * ps.x * jv;
-            vi = (i == j ? ph.y : 0.0) - h * ps.y * jv;
-        } else {
-            vr = (i == j) ? 1.0 : 0.0;
-            vi = 0.0;
+    for (int i = blockIdx.x; i < mp; i += gridDim.x) {
+        T* rr = re + (size_t)i * mp;
+        T* ri = im + (size_t)i * mp;
+        if (i >= m) {
+            for (int j = threadIdx.x; j < mp; j += blockDim.x) {
+                rr[j] = (i == j) ? T(1) : T(0);
+                ri[j] = T(0);
+            }
+            continue;
         }
-        re[e] = (T)vr;
-        im[e] = (T)vi;
+        const T rp = (T)(dxa * dp[i]), rm = (T)(dxa * dm[i]);
+        for (int j = threadIdx.x; j < mp; j += blockDim.x) {
+            T vr = T(0), vi = T(0);
+            if (j < m) {
+                const int a = i - j + 1, b = j - i + 1;
+                T jv = T(0);
+                if (a >= 0) jv += rp * (T)g[a];
+                if (b >= 0) jv += rm * (T)g[b];
+                vr = -hpr * jv;
+                vi = -hpi * jv;
+                if (i == j) {
+                    vr += (T)ph.x;
+                    vi += (T)ph.y;
+                }
+            }
+            rr[j] = vr;
+            ri[j] = vi;
+        }
     }
 }
 
@@ -109,22 +126,27 @@ lu_diag_kernel(int mp, int p, T* __restrict__ fac, cplx_t<T>* __restrict__ dinv,
 }
 
 // Panel solves.  blockIdx.x < nrow: a chunk of RC rows of A21 -> L21 = A21 U11^{-1};
-// otherwise a chunk of RC columns of A12 -> U12 = L11^{-1} A12.
-constexpr int RC = 32;
+// otherwise a chunk of RC columns of A12 -> U12 = L11^{-1} A12.  One thread per
+// row (column): the NB values live in registers and the triangular solve against
+// the factored diagonal block (shared memory, broadcast reads) needs no barrier.
+// Loads and stores go through shared memory so that global accesses stay coalesced.
 // PACK < 0: plain; PACK = 0 / 1: also write the panels as packed TF32 / BF16
 // tensor-core operand tiles (A' from L21 rows, B' from U12 columns; see lu_tc.cuh).
+constexpr int RC = 128;
 template <typename T, int PACK>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(RC)
 lu_panel_kernel(int mp, int p, int nrow, T* __restrict__ fac, unsigned char* __restrict__ apack,
                 unsigned char* __restrict__ bpack, int ntile_max) {
     using C = cplx_t<T>;
     __shared__ C D[NB][NB + 1];
-    __shared__ C X[RC][NB + 1];
+    __shared__ C dinv_s[NB];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C (*X)[NB + 1] = reinterpret_cast<C (*)[NB + 1]>(smem_raw);  // [RC][NB+1]
     const int k = blockIdx.y;
     T* re = plane_re(fac, k, mp);
     T* im = plane_im(fac, k, mp);
     const int o = p * NB;
-    const int rest = o + NB;  // first row / column after the panel
+    const int rest = o + NB;
     for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
         const int r = e / NB, c = e % NB;
         const size_t idx = (size_t)(o + r) * mp + o + c;
@@ -147,50 +169,53 @@ lu_panel_kernel(int mp, int p, int nrow, T* __restrict__ fac, unsigned char* __r
         X[q][c] = (b0 + q < mp) ? mk(re[idx], im[idx]) : mk(T(0), T(0));
     }
     __syncthreads();
+    if (rows && threadIdx.x < NB) {
+        const C piv = D[threadIdx.x][threadIdx.x];
+        const T den = piv.x * piv.x + piv.y * piv.y;
+        dinv_s[threadIdx.x] = den > T(0) ? mk(piv.x / den, -piv.y / den) : mk(T(0), T(0));
+    }
+    __syncthreads();
+    const int q = threadIdx.x;
+    C x[NB];
+#pragma unroll
+    for (int c = 0; c < NB; ++c) x[c] = X[q][c];
     if (rows) {
-        // x U11 = a: for c: x_c = (a_c - sum_{c'<c} x_c' U[c'][c]) / U[c][c]  (right-looking form)
+        // x U11 = a: x_c = (a_c - sum_{c'<c} x_c' U[c'][c]) / U[c][c]
+#pragma unroll
         for (int c = 0; c < NB; ++c) {
-            const C piv = D[c][c];
-            const T den = piv.x * piv.x + piv.y * piv.y;
-            const C inv = den > T(0) ? mk(piv.x / den, -piv.y / den) : mk(T(0), T(0));
-            for (int q = threadIdx.x; q < RC; q += blockDim.x) X[q][c] = cmul(X[q][c], inv);
-            __syncthreads();
-            const int w = NB - c - 1;
-            for (int e = threadIdx.x; e < RC * w; e += blockDim.x) {
-                const int q = e / w, cc = c + 1 + e % w;
-                X[q][cc] = csub(X[q][cc], cmul(X[q][c], D[c][cc]));
-            }
-            __syncthreads();
+            x[c] = cmul(x[c], dinv_s[c]);
+#pragma unroll
+            for (int cc = c + 1; cc < NB; ++cc) x[cc] = csub(x[cc], cmul(x[c], D[c][cc]));
         }
     } else {
-        // L11 u = a (unit lower): for c: a_rr -= L[rr][c] a_c, rr > c
+        // L11 u = a (unit lower): u_rr -= L[rr][c] u_c, rr > c
+#pragma unroll
         for (int c = 0; c < NB; ++c) {
-            const int w = NB - c - 1;
-            for (int e = threadIdx.x; e < RC * w; e += blockDim.x) {
-                const int q = e / w, rr = c + 1 + e % w;
-                X[q][rr] = csub(X[q][rr], cmul(D[rr][c], X[q][c]));
-            }
-            __syncthreads();
+#pragma unroll
+            for (int rr = c + 1; rr < NB; ++rr) x[rr] = csub(x[rr], cmul(D[rr][c], x[c]));
         }
     }
+#pragma unroll
+    for (int c = 0; c < NB; ++c) X[q][c] = x[c];
+    __syncthreads();
     for (int e = threadIdx.x; e < RC * NB; e += blockDim.x) {
-        int q, c;
+        int qq, c;
         size_t idx;
         if (rows) {
-            q = e / NB; c = e % NB;
-            idx = (size_t)(b0 + q) * mp + o + c;
+            qq = e / NB; c = e % NB;
+            idx = (size_t)(b0 + qq) * mp + o + c;
         } else {
-            c = e / RC; q = e % RC;
-            idx = (size_t)(o + c) * mp + b0 + q;
+            c = e / RC; qq = e % RC;
+            idx = (size_t)(o + c) * mp + b0 + qq;
         }
-        if (b0 + q < mp) {
-            re[idx] = X[q][c].x;
-            im[idx] = X[q][c].y;
+        if (b0 + qq < mp) {
+            re[idx] = X[qq][c].x;
+            im[idx] = X[qq][c].y;
         }
         if constexpr (PACK >= 0) {
-            const int tile = chunk >> 2;
-            const int rt = (chunk & 3) * RC + q;  // row of the operand tile (A': output row, B': output column)
-            const float vr = (float)X[q][c].x, vi = (float)X[q][c].y;
+            const int tile = (chunk * RC + qq) / TC_BM;
+            const int rt = (chunk * RC + qq) % TC_BM;  // row of the operand tile (A': output row, B': output column)
+            const float vr = (float)X[qq][c].x, vi = (float)X[qq][c].y;
             if (rows) {
                 unsigned char* t = apack + ((size_t)k * ntile_max + tile) * TcCfg<PACK>::A_BYTES;
                 pack_store<PACK>(t, rt, c, vr);
@@ -417,12 +442,15 @@ static int run_lu(Problem& P, cudaStream_t st) {
     C* dinv = reinterpret_cast<C*>(P.d_dinv);
     const int mp = P.mp, nb = P.nblk;
     {
-        dim3 grid(nb >= 1216 ? 1 : 1216 / nb, nb);
+        dim3 grid(mp < 64 ? mp : 64, nb);
         StageTimer t(P, FDE_STAGE_FORM);
         form_blocks_kernel<T><<<grid, 256, 0, st>>>(P.m, mp, P.h, P.dxa, P.d_g, P.d_dplus, P.d_dminus, P.d_phi,
                                                    P.d_psi, fac);
         FDE_LAUNCH_CHECK("form_blocks_kernel");
     }
+    const size_t panel_smem = (size_t)RC * (NB + 1) * sizeof(C);
+    FDE_CUDA_TRY(cudaFuncSetAttribute(lu_panel_kernel<T, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)panel_smem));
     const size_t upd_smem = (64 * (NB + 1) + NB * 65) * sizeof(C);
     FDE_CUDA_TRY(cudaFuncSetAttribute(lu_update_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)upd_smem));
     const int steps = mp / NB;
@@ -437,7 +465,7 @@ static int run_lu(Problem& P, cudaStream_t st) {
         const int nch = (rem + RC - 1) / RC;
         {
             StageTimer t(P, FDE_STAGE_LU_PANEL);
-            lu_panel_kernel<T, -1><<<dim3(2 * nch, nb), 256, 0, st>>>(mp, p, nch, fac, nullptr, nullptr, 0);
+            lu_panel_kernel<T, -1><<<dim3(2 * nch, nb), RC, panel_smem, st>>>(mp, p, nch, fac, nullptr, nullptr, 0);
             FDE_LAUNCH_CHECK("lu_panel_kernel");
         }
         const int nt = (rem + 63) / 64;
@@ -470,7 +498,7 @@ static int run_lu_tc(Problem& P, cudaStream_t st) {
     unsigned char* apack = reinterpret_cast<unsigned char*>(P.d_pack);
     unsigned char* bpack = apack + abytes;
     {
-        dim3 grid(nb >= 1216 ? 1 : 1216 / nb, nb);
+        dim3 grid(mp < 64 ? mp : 64, nb);
         StageTimer t(P, FDE_STAGE_FORM);
         form_blocks_kernel<float><<<grid, 256, 0, st>>>(P.m, mp, P.h, P.dxa, P.d_g, P.d_dplus, P.d_dminus,
                                                         P.d_phi, P.d_psi, fac);
@@ -479,6 +507,9 @@ static int run_lu_tc(Problem& P, cudaStream_t st) {
     // at most 2 CTAs per SM: each holds 256 of the SM's 512 TMEM columns
     const int smem = (Cfg::A_BYTES + Cfg::B_BYTES) > 100 * 1024 ? (Cfg::A_BYTES + Cfg::B_BYTES) : 100 * 1024;
     FDE_CUDA_TRY(cudaFuncSetAttribute(lu_update_tc_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    const size_t panel_smem = (size_t)RC * (NB + 1) * sizeof(float2);
+    FDE_CUDA_TRY(cudaFuncSetAttribute(lu_panel_kernel<float, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)panel_smem));
     const int steps = mp / NB;
     for (int p = 0; p < steps; ++p) {
         {
@@ -492,8 +523,8 @@ static int run_lu_tc(Problem& P, cudaStream_t st) {
         const int nch = (rem + RC - 1) / RC;
         {
             StageTimer t(P, FDE_STAGE_LU_PANEL);
-            lu_panel_kernel<float, KIND><<<dim3(2 * nch, nb), 256, 0, st>>>(mp, p, nch, fac, apack, bpack,
-                                                                            ntile_max);
+            lu_panel_kernel<float, KIND><<<dim3(2 * nch, nb), RC, panel_smem, st>>>(mp, p, nch, fac, apack, bpack,
+                                                                                ntile_max);
             FDE_LAUNCH_CHECK("lu_panel_kernel");
         }
         const int nt = (rem + TC_BM - 1) / TC_BM;

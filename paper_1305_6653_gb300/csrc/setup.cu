@@ -6,16 +6,30 @@
 
 namespace fde {
 
-// g_0 = 1, g_{k+1} = (1 - (alpha+1)/(k+1)) g_k (eq. (1.2)); a sequential recurrence
-// of m+2 terms, run once per problem by a single thread.
+// g_0 = 1, g_{k+1} = (1 - (alpha+1)/(k+1)) g_k (eq. (1.2)).  One warp: lane l runs
+// the recurrence over its own contiguous chunk of factors starting from 1, the
+// chunk products are scanned across lanes (multiplicative prefix), and each lane
+// rescales its chunk.  The result is the same product of the same factors as the
+// sequential recurrence, associated differently (a few ulps apart).
 __global__ void grunwald_kernel(double alpha, int count, double* __restrict__ g) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double v = 1.0;
-    g[0] = v;
-    for (int k = 0; k + 1 < count; ++k) {
-        v = (1.0 - (alpha + 1.0) / (double)(k + 1)) * v;
-        g[k + 1] = v;
+    const int lane = threadIdx.x;
+    const int chunk = (count + 31) / 32;
+    const int k0 = lane * chunk;  // this lane produces g[k0+1 .. k0+chunk]
+    double prod = 1.0;
+    for (int k = k0; k < k0 + chunk && k + 1 < count; ++k) {
+        prod *= (1.0 - (alpha + 1.0) / (double)(k + 1));
+        g[k + 1] = prod;  // partial product, rescaled below
     }
+    double pre = prod;  // inclusive scan of chunk products
+    for (int off = 1; off < 32; off <<= 1) {
+        const double v = __shfl_up_sync(0xffffffffu, pre, off);
+        if (lane >= off) pre *= v;
+    }
+    double excl = __shfl_up_sync(0xffffffffu, pre, 1);
+    if (lane == 0) excl = 1.0;
+    __syncwarp();
+    for (int k = k0; k < k0 + chunk && k + 1 < count; ++k) g[k + 1] *= excl;
+    if (lane == 0) g[0] = 1.0;
 }
 
 // tw[k] = exp(-2 pi i k / L), k < L/2

@@ -1,8 +1,8 @@
 """GPU parity of the CUDA path (through the C ABI) against the FP64 CPU oracle.
 
 Tolerances (derived from the arithmetic):
-* Grunwald weights, band combinations: the same recurrence / formulas in FP64,
-  differences only from operation order: 1e-14 relative.
+* Grunwald weights: the same factors (1 - (alpha+1)/(k+1)) multiplied in FP64 in a
+  different association (warp scan): relative difference <= ~(m+2) eps.
 * M z: J is applied through length-L FFTs (L = 2^k >= 2m).  The FFT's error is
   O(eps log2 L) relative to ||lambda||_inf ||z||, and ||lambda||_inf <= sum|t_k|
   = 2 alpha (d+ + d-) dx^-alpha (Sec. 3.2, Wiener class).  With eps = 1.1e-16
@@ -62,7 +62,10 @@ def test_grunwald_and_rhs(name, make):
     prob = make()
     with _gpu(prob, precision=None) as p:
         g = p.grunwald()
-        np.testing.assert_allclose(g, O.grunwald_weights(prob.alpha, prob.m + 1), rtol=1e-14, atol=0)
+        # the device forms the same product of the same factors, associated by a warp scan:
+        # relative difference bounded by ~(m+2) eps in the worst case, a few eps in practice
+        np.testing.assert_allclose(g, O.grunwald_weights(prob.alpha, prob.m + 1), rtol=max(1e-14, 4e-16 * (prob.m + 2)),
+                                   atol=0)
         b = p.rhs().cpu().numpy()
     ref = O.reduced_rhs(prob)
     scale = np.abs(ref).max() + prob.h * O.j_of(prob).__abs__().sum(axis=1).max() * np.abs(prob.u0).max()
