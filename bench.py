@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--config", choices=["scale", "batch"], default="scale",
+                    help="scale: one m=2047/s=256 instance per step; batch: 64 uneven instances per step")
     return ap.parse_args()
 
 
@@ -201,6 +203,83 @@ def oracle_sample(prob, iterations: int) -> dict:
 
 
 # ---------------------------------------------------------------------------
+# batched workload: 64 independent instances per step
+# ---------------------------------------------------------------------------
+
+def bench_batch(args, world, rank, local_rank):
+    import numpy as np
+    import torch
+
+    import fde_inputs
+    import paper_1305_6653_gb300 as fde
+
+    torch.cuda.set_device(local_rank)
+    probs = fde_inputs.config_batch()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    outs = [torch.empty(p.n, dtype=torch.float64, device="cuda") for p in probs]
+    b = fde.FDEBatch(probs)
+
+    def step():
+        b.assemble().factor(args.precision)
+        _, st = b.solve(tol=args.tol, restart=20, maxit=400, outs=outs)
+        return st
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local_rank)
+    if not args.no_clocks:
+        sampler.start()
+    l0 = fde.fde_launch_count()
+    times, stats = [], None
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        stats = step()
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    launches = fde.fde_launch_count() - l0
+    clocks = sampler.stop() if not args.no_clocks else None
+    b.close()
+    ms = sum(times) / len(times)
+    value = world * len(probs) / (ms / 1e3)
+    # the same 64 instances one at a time through the single-problem API
+    t0 = time.perf_counter()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for pr, out in zip(probs, outs):
+        with fde.FDEProblem.from_inputs(pr) as p:
+            p.assemble().factor(args.precision)
+            p.solve(tol=args.tol, restart=20, maxit=400, out=out)
+    e1.record()
+    e1.synchronize()
+    seq_s = max(e0.elapsed_time(e1) / 1e3, time.perf_counter() - t0)
+    import oracle as O
+    worst = 0.0
+    for pr, out in zip(probs, outs):
+        xs = out.cpu().numpy()
+        bb = O.reduced_rhs(pr)
+        worst = max(worst, float(np.linalg.norm(bb - O.matvec(pr, xs)) / np.linalg.norm(bb)))
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+                "config": {"workload": "batch64_m255-2047_s64-256_etr3_gbdf3_gam4", "instances": len(probs),
+                           "unknowns_total": int(sum(p.n for p in probs)), "precision": args.precision,
+                           "tol_true_residual": args.tol, "restart": 20,
+                           "l2": "flushed (512 MiB write) before every timed step"},
+                "roofline": None, "gpu_launches": launches, "clocks": clocks,
+                "iterations": [s_["iterations"] for s_ in stats],
+                "sequential_single_api": {"value": len(probs) / seq_s, "unit": "solves/s", "seconds": seq_s},
+                "worst_rel_residual_oracle_matvec": worst, "per_step_ms": times}
+        print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------
 # main
 # ---------------------------------------------------------------------------
 
@@ -212,6 +291,8 @@ def main():
 
     import fde_inputs
 
+    if args.config == "batch" and args.impl == "ours":
+        return bench_batch(args, world, rank, local_rank)
     prob = fde_inputs.config_scale(args.m, args.s)
     workload = {"workload": f"scale_m{args.m}_s{args.s}_gbdf5_alpha1.8_variable_d", "m": args.m, "s": args.s,
                 "unknowns": args.m * args.s, "scheme": "GBDF5", "alpha": 1.8, "d": "d+=1+x, d-=2-x",

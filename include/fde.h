@@ -148,6 +148,41 @@ void fde_problem_destroy(fde_problem* p);
 /* Message of the last error on this thread ("" if none).  Owned by the library. */
 const char* fde_last_error(void);
 
+/* ---- batches of independent problems -------------------------------------- */
+
+/* A batch of independent instances of eq. (1.1) (uneven m, s, alpha, d and BVM
+ * scheme) solved together: the Strang-block LUs of all instances run as one set of
+ * launches per panel step, and flexible GMRES runs in lock-stepped restart rounds
+ * whose kernels cover all active instances at once (Sec. 3.2 per instance). */
+typedef struct fde_batch fde_batch;
+
+/* Create count problems (each validated and copied as by fde_problem_create) on
+ * one stream.  Errors: as fde_problem_create (message names the instance). */
+int fde_batch_create(const fde_problem_desc* descs, int count, void* stream, fde_batch** out);
+
+/* bvm_assemble for every instance.  Errors: as bvm_assemble. */
+int fde_batch_assemble(fde_batch* b);
+
+/* Factor the Strang blocks of every instance in FDE_FP32, FDE_TF32 or FDE_BF16
+ * (FP32 factor storage).  Errors: FDE_ERR_ARG, FDE_ERR_STATE, FDE_ERR_ALLOC,
+ * FDE_ERR_SINGULAR, FDE_ERR_TIMEOUT, FDE_ERR_CUDA. */
+int fde_batch_factor(fde_batch* b, int precision);
+
+/* Solve every instance from a zero initial guess.  x_out: host array of count
+ * device pointers, entry i of length s_i*m_i, written with u_1..u_s.  stats: host
+ * array of count entries (may be NULL); ms_solve is the batch's total time.
+ * Returns FDE_OK when every instance met the tolerance, else the first failing
+ * code (each instance's own code is in stats[i].status). */
+int fde_batch_solve(fde_batch* b, const fde_pgmres_opts* opts, double* const* x_out, fde_stats* stats);
+
+/* Number of instances, and the problem handle of instance i (owned by the
+ * batch; usable with the step-level entry points; NULL if out of range). */
+int fde_batch_size(const fde_batch* b);
+fde_problem* fde_batch_problem(fde_batch* b, int i);
+
+/* Release the batch and all its instances.  NULL is ignored. */
+void fde_batch_destroy(fde_batch* b);
+
 /* ---- step-level entry points (the same kernels the solver runs) ---------- */
 
 /* y = M z (eq. (1.10), u_0 eliminated) in FP64 on the device: the band of A and B

@@ -17,7 +17,7 @@ from . import _lib
 from ._lib import (FDE_BF16, FDE_ETR, FDE_FP32, FDE_FP64, FDE_GAM, FDE_GBDF, FDE_TF32, FdeError,  # noqa: F401
                    FdePgmresOpts, FdeProblemDesc, FdeStats, PRECISIONS, FAMILIES)
 
-__all__ = ["FDEProblem", "fde_problem_create", "bvm_assemble", "strang_precond_factor", "pgmres_solve",
+__all__ = ["FDEProblem", "FDEBatch", "fde_problem_create", "bvm_assemble", "strang_precond_factor", "pgmres_solve",
            "fde_problem_destroy", "fde_matvec", "fde_precond_apply", "FdeError", "PRECISIONS"]
 
 
@@ -191,6 +191,68 @@ class FDEProblem:
     def close(self):
         if getattr(self, "h", None):
             fde_problem_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class FDEBatch:
+    """A batch of independent instances solved together (fde_batch_* entry points).
+
+    problems: list of fde_inputs.Problem (or objects with the same fields); the
+    arrays are host memory, copied by the library."""
+
+    def __init__(self, problems, stream=None):
+        import numpy as np
+        self.count = len(problems)
+        self.sizes = [(p.m, p.s) for p in problems]
+        self._keep = []
+        descs = (FdeProblemDesc * self.count)()
+        for i, p in enumerate(problems):
+            arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (p.dplus, p.dminus, p.u0, p.f)]
+            self._keep.extend(arrs)
+            descs[i] = FdeProblemDesc(p.m, p.s, float(p.alpha), float(p.xL), float(p.xR), float(p.t0), float(p.T),
+                                      arrs[0].ctypes.data, arrs[1].ctypes.data, 0.0, 0.0, FAMILIES[p.family],
+                                      int(p.mu), arrs[2].ctypes.data, arrs[3].ctypes.data, 0)
+        self.h = C.c_void_p()
+        _lib.check(_lib.load().fde_batch_create(descs, self.count, _stream_handle(stream), C.byref(self.h)),
+                   "fde_batch_create")
+        self._keep = []
+
+    def assemble(self):
+        _lib.check(_lib.load().fde_batch_assemble(self.h), "fde_batch_assemble")
+        return self
+
+    def factor(self, precision="fp32"):
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        _lib.check(_lib.load().fde_batch_factor(self.h, prec), "fde_batch_factor")
+        return self
+
+    def solve(self, tol=1e-10, restart=20, maxit=1000, reorth=1, outs=None, raise_on_error=True):
+        torch = _torch()
+        if outs is None:
+            outs = [torch.empty(m * s, dtype=torch.float64, device="cuda") for m, s in self.sizes]
+        ptrs = (C.c_void_p * self.count)(*[o.data_ptr() for o in outs])
+        stats = (FdeStats * self.count)()
+        opts = FdePgmresOpts(float(tol), int(restart), int(maxit), int(reorth))
+        rc = _lib.load().fde_batch_solve(self.h, C.byref(opts), ptrs, stats)
+        if raise_on_error:
+            _lib.check(rc, "fde_batch_solve")
+        return outs, [st.as_dict() for st in stats]
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.load().fde_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):

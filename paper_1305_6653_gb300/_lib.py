@@ -35,7 +35,8 @@ EXPORTED = [
     "fde_problem_create", "bvm_assemble", "strang_precond_factor", "pgmres_solve", "fde_problem_destroy",
     "fde_last_error", "fde_matvec", "fde_precond_apply", "fde_get_rhs", "fde_get_factor_block",
     "fde_get_grunwald", "fde_problem_sizes", "fde_profile_enable", "fde_profile_read", "fde_launch_count",
-    "fde_precond_apply_noalloc",
+    "fde_precond_apply_noalloc", "fde_batch_create", "fde_batch_assemble", "fde_batch_factor",
+    "fde_batch_solve", "fde_batch_size", "fde_batch_problem", "fde_batch_destroy",
 ]
 STAGES = ["assemble", "form", "lu_diag", "lu_panel", "lu_update", "tfft_fwd", "trsv", "tfft_inv", "matvec",
           "krylov"]
@@ -100,6 +101,13 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "fde_profile_read": (i32, [vp, i32, C.POINTER(f64), C.POINTER(i32)]),
         "fde_launch_count": (C.c_longlong, []),
         "fde_precond_apply_noalloc": (i32, [vp, vp, vp]),
+        "fde_batch_create": (i32, [C.POINTER(FdeProblemDesc), i32, vp, C.POINTER(vp)]),
+        "fde_batch_assemble": (i32, [vp]),
+        "fde_batch_factor": (i32, [vp, i32]),
+        "fde_batch_solve": (i32, [vp, C.POINTER(FdePgmresOpts), C.POINTER(vp), C.POINTER(FdeStats)]),
+        "fde_batch_size": (i32, [vp]),
+        "fde_batch_problem": (vp, [vp, i32]),
+        "fde_batch_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

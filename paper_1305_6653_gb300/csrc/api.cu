@@ -179,7 +179,7 @@ static void free_workspace(Problem& P) {
     P.restart_cap = 0;
 }
 
-static int ensure_workspace(Problem& P, int restart) {
+int ensure_workspace(Problem& P, int restart) {
     if (P.restart_cap >= restart) return FDE_OK;
     free_workspace(P);
     int rc;
@@ -191,6 +191,32 @@ static int ensure_workspace(Problem& P, int restart) {
     if ((rc = dalloc(&P.d_gv, (size_t)restart + 1))) return rc;
     if ((rc = dalloc(&P.d_y, (size_t)restart))) return rc;
     P.restart_cap = restart;
+    return FDE_OK;
+}
+
+// Factor planes, 1/U_ii and the frequency-domain vector in the precision's storage
+// type (FP64 for FDE_FP64, FP32 otherwise); reallocated when the size changes.
+int ensure_factor_buffers(Problem& P, int precision) {
+    const size_t esz = precision == FDE_FP64 ? sizeof(double) : sizeof(float);
+    const size_t fac_bytes = (size_t)P.nblk * 2 * P.mp * P.mp * esz;
+    int rc;
+    if (P.d_fac && P.fac_bytes != fac_bytes) {
+        dfree(P.d_fac); dfree(P.d_dinv); dfree(P.d_rhat);
+        P.d_fac = P.d_dinv = P.d_rhat = nullptr;
+        P.fac_bytes = 0;
+    }
+    if (!P.d_fac) {
+        unsigned char* f = nullptr;
+        if ((rc = dalloc(&f, fac_bytes))) return rc;
+        P.d_fac = f;
+        P.fac_bytes = fac_bytes;
+        unsigned char* dv = nullptr;
+        if ((rc = dalloc(&dv, (size_t)P.nblk * P.mp * 2 * esz))) return rc;
+        P.d_dinv = dv;
+        unsigned char* rh = nullptr;
+        if ((rc = dalloc(&rh, (size_t)P.nblk * P.mp * 2 * esz))) return rc;
+        P.d_rhat = rh;
+    }
     return FDE_OK;
 }
 
@@ -499,25 +525,8 @@ int strang_precond_factor(fde_problem* h, int precision) {
     if (!P.assembled) return set_error(FDE_ERR_STATE, "bvm_assemble must run before strang_precond_factor");
     if (precision != FDE_FP64 && precision != FDE_FP32 && precision != FDE_TF32 && precision != FDE_BF16)
         return set_error(FDE_ERR_ARG, "precision must be FDE_FP64, FDE_FP32, FDE_TF32 or FDE_BF16");
-    const size_t esz = precision == FDE_FP64 ? sizeof(double) : sizeof(float);
-    const size_t fac_bytes = (size_t)P.nblk * 2 * P.mp * P.mp * esz;
-    int rc;
-    if (P.d_fac && (P.fac_bytes != fac_bytes || P.precision != precision)) {
-        dfree(P.d_fac); dfree(P.d_dinv); dfree(P.d_rhat);
-        P.d_fac = P.d_dinv = P.d_rhat = nullptr;
-    }
-    if (!P.d_fac) {
-        unsigned char* f = nullptr;
-        if ((rc = dalloc(&f, fac_bytes))) return rc;
-        P.d_fac = f;
-        P.fac_bytes = fac_bytes;
-        unsigned char* dv = nullptr;
-        if ((rc = dalloc(&dv, (size_t)P.nblk * P.mp * 2 * esz))) return rc;
-        P.d_dinv = dv;
-        unsigned char* rh = nullptr;
-        if ((rc = dalloc(&rh, (size_t)P.nblk * P.mp * 2 * esz))) return rc;
-        P.d_rhat = rh;
-    }
+    int rc = ensure_factor_buffers(P, precision);
+    if (rc) return rc;
     P.factored = false;
     P.precision = precision;
     FDE_CUDA_TRY(cudaMemsetAsync(P.d_info, 0, P.nblk * sizeof(int), P.stream));

@@ -1,0 +1,404 @@
+// Batched solve of many independent problems (uneven m, s, alpha, d and BVM
+// scheme) with one set of kernel launches per step for the whole batch.
+//
+// Each instance keeps its own buffers (it is an ordinary fde_problem); the batch
+// adds device descriptor tables (InstDev per instance, BlkDev per Strang block)
+// that the batched kernels index by blockIdx.y:
+//   * LU: the block table of every instance, sorted by m_p, so the blocks still
+//     being factored at step p are a prefix of the table (one launch per kernel
+//     and step for the whole batch);
+//   * GMRES: flexible GMRES(restart) in lock-stepped restart rounds.  Within a
+//     round all active instances take iteration j together; an instance whose
+//     residual estimate meets the tolerance drops out of the active list (its
+//     kernels are no longer launched) until the round ends; then every instance
+//     of the round forms x += Z y and its true FP64 residual, and the unconverged
+//     ones start the next round.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "fde_internal.h"
+#include "lu_tc.cuh"
+
+namespace fde {
+constexpr int TC_A_BYTES[2] = {TcCfg<0>::A_BYTES, TcCfg<1>::A_BYTES};
+constexpr int TC_B_BYTES[2] = {TcCfg<0>::B_BYTES, TcCfg<1>::B_BYTES};
+}  // namespace fde
+
+using namespace fde;
+
+struct fde_batch {
+    std::vector<fde_problem*> probs;
+    cudaStream_t stream = nullptr;
+    int precision = -1;
+    bool assembled = false, factored = false;
+    BlkDev* d_blk = nullptr;
+    std::vector<int> blk_mp;
+    InstDev* d_inst = nullptr;
+    int* d_act = nullptr;
+    int* d_kvec = nullptr;
+    int* d_err = nullptr;
+    double* d_gather = nullptr;
+    double* h_gather = nullptr;  // pinned
+    int* h_act = nullptr;        // pinned
+    int* h_kvec = nullptr;       // pinned
+    unsigned char* d_pack = nullptr;
+    size_t pack_bytes = 0;
+    int max_mp = 0, max_s = 0, max_L = 0, max_m = 0, max_nblk = 0;
+    long max_n = 0;
+};
+
+namespace {
+
+int upload_list(fde_batch* b, const std::vector<int>& v, int* host, int* dev) {
+    if (v.empty()) return FDE_OK;
+    std::memcpy(host, v.data(), v.size() * sizeof(int));
+    FDE_CUDA_TRY(cudaMemcpyAsync(dev, host, v.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream));
+    return FDE_OK;
+}
+
+int gather(fde_batch* b) {
+    const int n = (int)b->probs.size();
+    int rc = launch_gather_scalars(b->d_inst, n, b->d_gather, b->stream);
+    if (rc) return rc;
+    FDE_CUDA_TRY(cudaMemcpyAsync(b->h_gather, b->d_gather, 4 * n * sizeof(double), cudaMemcpyDeviceToHost,
+                                 b->stream));
+    FDE_CUDA_TRY(cudaStreamSynchronize(b->stream));
+    return FDE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void fde_batch_destroy(fde_batch* b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    else cudaDeviceSynchronize();
+    for (fde_problem* p : b->probs) fde_problem_destroy(p);
+    void* dev[] = {b->d_blk, b->d_inst, b->d_act, b->d_kvec, b->d_err, b->d_gather, b->d_pack};
+    for (void* d : dev)
+        if (d) cudaFree(d);
+    if (b->h_gather) cudaFreeHost(b->h_gather);
+    if (b->h_act) cudaFreeHost(b->h_act);
+    if (b->h_kvec) cudaFreeHost(b->h_kvec);
+    delete b;
+}
+
+int fde_batch_create(const fde_problem_desc* descs, int count, void* stream, fde_batch** out) {
+    if (!descs || !out || count < 1) return set_error(FDE_ERR_ARG, "need descs, out and count >= 1");
+    *out = nullptr;
+    fde_batch* b = new (std::nothrow) fde_batch();
+    if (!b) return set_error(FDE_ERR_ALLOC, "host allocation failed");
+    b->stream = (cudaStream_t)stream;
+    for (int i = 0; i < count; ++i) {
+        fde_problem* p = nullptr;
+        int rc = fde_problem_create(&descs[i], stream, &p);
+        if (rc) {
+            std::string msg = std::string("instance ") + std::to_string(i) + ": " + fde_last_error();
+            fde_batch_destroy(b);
+            return set_error(rc, msg);
+        }
+        b->probs.push_back(p);
+        const Problem& P = *problem_of(p);
+        b->max_mp = std::max(b->max_mp, P.mp);
+        b->max_s = std::max(b->max_s, P.s);
+        b->max_L = std::max(b->max_L, P.L);
+        b->max_m = std::max(b->max_m, P.m);
+        b->max_nblk = std::max(b->max_nblk, P.nblk);
+        b->max_n = std::max(b->max_n, P.n);
+    }
+    bool ok = cudaMalloc(&b->d_act, count * sizeof(int)) == cudaSuccess &&
+              cudaMalloc(&b->d_kvec, count * sizeof(int)) == cudaSuccess &&
+              cudaMalloc(&b->d_err, sizeof(int)) == cudaSuccess &&
+              cudaMalloc(&b->d_gather, 4 * count * sizeof(double)) == cudaSuccess &&
+              cudaMalloc(&b->d_inst, count * sizeof(InstDev)) == cudaSuccess &&
+              cudaMallocHost(&b->h_gather, 4 * count * sizeof(double)) == cudaSuccess &&
+              cudaMallocHost(&b->h_act, count * sizeof(int)) == cudaSuccess &&
+              cudaMallocHost(&b->h_kvec, count * sizeof(int)) == cudaSuccess;
+    if (!ok) {
+        fde_batch_destroy(b);
+        return set_error(FDE_ERR_ALLOC, "batch allocation failed");
+    }
+    *out = b;
+    return FDE_OK;
+}
+
+int fde_batch_size(const fde_batch* b) { return b ? (int)b->probs.size() : 0; }
+
+fde_problem* fde_batch_problem(fde_batch* b, int i) {
+    if (!b || i < 0 || i >= (int)b->probs.size()) return nullptr;
+    return b->probs[i];
+}
+
+int fde_batch_assemble(fde_batch* b) {
+    if (!b) return set_error(FDE_ERR_ARG, "NULL batch");
+    for (size_t i = 0; i < b->probs.size(); ++i) {
+        int rc = bvm_assemble(b->probs[i]);
+        if (rc) return rc;
+    }
+    b->assembled = true;
+    return FDE_OK;
+}
+
+int fde_batch_factor(fde_batch* b, int precision) {
+    if (!b) return set_error(FDE_ERR_ARG, "NULL batch");
+    if (!b->assembled) return set_error(FDE_ERR_STATE, "fde_batch_assemble must run first");
+    if (precision != FDE_FP32 && precision != FDE_TF32 && precision != FDE_BF16)
+        return set_error(FDE_ERR_ARG, "batched factorisation supports FDE_FP32, FDE_TF32 and FDE_BF16");
+    const int kind = precision == FDE_TF32 ? 0 : (precision == FDE_BF16 ? 1 : -1);
+    // buffers and the block table
+    std::vector<BlkDev> blks;
+    size_t pack_total = 0;
+    for (size_t i = 0; i < b->probs.size(); ++i) {
+        Problem& P = *problem_of(b->probs[i]);
+        int rc = ensure_factor_buffers(P, precision);
+        if (rc) return rc;
+        P.factored = false;
+        P.precision = precision;
+        const int ntile_max = (P.mp - LU_NB + TC_BM - 1) / TC_BM;
+        for (int k = 0; k < P.nblk; ++k) {
+            BlkDev d{};
+            d.inst = (int)i;
+            d.k = k;
+            d.m = P.m;
+            d.mp = P.mp;
+            d.ntile_max = ntile_max;
+            d.h = P.h;
+            d.dxa = P.dxa;
+            d.phi = P.d_phi + k;
+            d.psi = P.d_psi + k;
+            d.g = P.d_g;
+            d.dplus = P.d_dplus;
+            d.dminus = P.d_dminus;
+            d.fac = (float*)P.d_fac + (size_t)k * 2 * P.mp * P.mp;
+            d.dinv = (float2*)P.d_dinv + (size_t)k * P.mp;
+            d.info = P.d_info + k;
+            if (kind >= 0) {
+                d.apack = (unsigned char*)pack_total;  // offset, rebased below
+                pack_total += (size_t)ntile_max * (TC_A_BYTES[kind] + TC_B_BYTES[kind]);
+            }
+            blks.push_back(d);
+        }
+        FDE_CUDA_TRY(cudaMemsetAsync(P.d_info, 0, P.nblk * sizeof(int), b->stream));
+    }
+    if (kind >= 0 && b->pack_bytes < pack_total) {
+        if (b->d_pack) cudaFree(b->d_pack);
+        b->d_pack = nullptr;
+        b->pack_bytes = 0;
+        FDE_CUDA_TRY(cudaMalloc(&b->d_pack, pack_total));
+        b->pack_bytes = pack_total;
+        FDE_CUDA_TRY(cudaMemsetAsync(b->d_pack, 0, pack_total, b->stream));
+    }
+    if (kind >= 0) {
+        for (BlkDev& d : blks) {
+            const size_t off = (size_t)d.apack;
+            d.apack = b->d_pack + off;
+            d.bpack = d.apack + (size_t)d.ntile_max * TC_A_BYTES[kind];
+        }
+    }
+    std::stable_sort(blks.begin(), blks.end(), [](const BlkDev& a, const BlkDev& c) { return a.mp > c.mp; });
+    b->blk_mp.resize(blks.size());
+    for (size_t i = 0; i < blks.size(); ++i) b->blk_mp[i] = blks[i].mp;
+    if (b->d_blk) cudaFree(b->d_blk);
+    b->d_blk = nullptr;
+    FDE_CUDA_TRY(cudaMalloc(&b->d_blk, blks.size() * sizeof(BlkDev)));
+    FDE_CUDA_TRY(cudaMemcpyAsync(b->d_blk, blks.data(), blks.size() * sizeof(BlkDev), cudaMemcpyHostToDevice,
+                                 b->stream));
+    FDE_CUDA_TRY(cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream));
+    int rc = launch_lu_batched(b->d_blk, b->blk_mp, precision, b->d_err, b->stream);
+    if (rc) return rc;
+    // pivots and bounded waits
+    int derr = 0;
+    FDE_CUDA_TRY(cudaMemcpyAsync(&derr, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+    std::vector<std::vector<int>> infos(b->probs.size());
+    for (size_t i = 0; i < b->probs.size(); ++i) {
+        Problem& P = *problem_of(b->probs[i]);
+        infos[i].resize(P.nblk);
+        FDE_CUDA_TRY(cudaMemcpyAsync(infos[i].data(), P.d_info, P.nblk * sizeof(int), cudaMemcpyDeviceToHost,
+                                     b->stream));
+    }
+    FDE_CUDA_TRY(cudaStreamSynchronize(b->stream));
+    if (derr) return set_error(FDE_ERR_TIMEOUT, "a bounded wait in the tensor-core LU update ran out");
+    for (size_t i = 0; i < b->probs.size(); ++i)
+        for (int k = 0; k < (int)infos[i].size(); ++k)
+            if (infos[i][k])
+                return set_error(FDE_ERR_SINGULAR, "zero or non-finite pivot in instance " + std::to_string(i) +
+                                                       ", block " + std::to_string(k));
+    for (fde_problem* p : b->probs) problem_of(p)->factored = true;
+    b->precision = precision;
+    b->factored = true;
+    return FDE_OK;
+}
+
+int fde_batch_solve(fde_batch* b, const fde_pgmres_opts* opts, double* const* x_out, fde_stats* stats) {
+    if (!b || !x_out) return set_error(FDE_ERR_ARG, "NULL argument");
+    if (!b->factored) return set_error(FDE_ERR_STATE, "fde_batch_factor must run first");
+    fde_pgmres_opts o{1e-10, 20, 1000, 1};
+    if (opts) o = *opts;
+    if (!(o.tol > 0.0) || o.restart < 1 || o.restart > 63 || o.maxit < 1)
+        return set_error(FDE_ERR_ARG, "need tol > 0, 1 <= restart <= 63, maxit >= 1");
+    const int n = (int)b->probs.size();
+    cudaStream_t st = b->stream;
+    cudaEvent_t ev0, ev1;
+    FDE_CUDA_TRY(cudaEventCreate(&ev0));
+    FDE_CUDA_TRY(cudaEventCreate(&ev1));
+    FDE_CUDA_TRY(cudaEventRecord(ev0, st));
+    std::vector<InstDev> inst(n);
+    for (int i = 0; i < n; ++i) {
+        if (!x_out[i]) return set_error(FDE_ERR_ARG, "x_out has a NULL entry");
+        Problem& P = *problem_of(b->probs[i]);
+        int rc = ensure_workspace(P, o.restart);
+        if (rc) return rc;
+        InstDev d{};
+        d.m = P.m; d.s = P.s; d.mp = P.mp; d.L = P.L; d.logL = P.logL; d.logs = P.logs; d.mu = P.mu;
+        d.nblk = P.nblk; d.n = P.n; d.h = P.h; d.dxa = P.dxa;
+        d.start = P.d_start; d.A = P.d_a; d.B = P.d_b; d.dplus = P.d_dplus; d.dminus = P.d_dminus;
+        d.sym = P.d_sym; d.twL = P.d_twL; d.tws32 = P.d_tws32; d.tws = P.d_tws;
+        d.rhat = P.d_rhat; d.fac = P.d_fac; d.dinv = P.d_dinv;
+        d.b = P.d_b_rhs; d.x = x_out[i]; d.V = P.d_V; d.Z = P.d_Z; d.work = P.d_work; d.H = P.d_H;
+        d.cs = P.d_cs; d.sn = P.d_sn; d.gv = P.d_gv; d.y = P.d_y; d.scal = P.d_scal;
+        d.partial = P.d_partial; d.counter = P.d_counter;
+        inst[i] = d;
+        FDE_CUDA_TRY(cudaMemsetAsync(x_out[i], 0, P.n * sizeof(double), st));
+    }
+    FDE_CUDA_TRY(cudaMemcpyAsync(b->d_inst, inst.data(), n * sizeof(InstDev), cudaMemcpyHostToDevice, st));
+    const int ldh = o.restart + 1;
+    std::vector<int> all(n);
+    std::iota(all.begin(), all.end(), 0);
+    int rc;
+    auto fail = [&](int code) {
+        cudaEventDestroy(ev0);
+        cudaEventDestroy(ev1);
+        return code;
+    };
+    // r_0 = b - M x_0 (x_0 = 0) into V_0, |b|^2 and |r_0|^2
+    if ((rc = upload_list(b, all, b->h_act, b->d_act))) return fail(rc);
+    if ((rc = launch_matvec_batched(b->d_inst, b->d_act, n, b->max_s, b->max_L, b->max_m, 1, 0, st))) return fail(rc);
+    if ((rc = launch_residual_batched(b->d_inst, b->d_act, n, b->max_n, st))) return fail(rc);
+    if ((rc = launch_dots_batched(b->d_inst, b->d_act, n, 4, 0, st))) return fail(rc);
+    if ((rc = launch_dots_batched(b->d_inst, b->d_act, n, 3, 0, st))) return fail(rc);
+    std::vector<double> bnorm(n), beta(n), est(n, 0.0);
+    // |b|^2 sits in scal[131]; gather it through a one-off copy per instance
+    for (int i = 0; i < n; ++i) {
+        Problem& P = *problem_of(b->probs[i]);
+        FDE_CUDA_TRY(cudaMemcpyAsync(b->h_gather + 4 * i, P.d_scal + 131, sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
+    FDE_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int i = 0; i < n; ++i) bnorm[i] = std::sqrt(b->h_gather[4 * i]);
+    if ((rc = gather(b))) return fail(rc);
+    for (int i = 0; i < n; ++i) beta[i] = std::sqrt(b->h_gather[4 * i + 3]);
+    std::vector<int> its(n, 0), restarts(n, 0), status(n, FDE_OK), kk(n, 0);
+    std::vector<char> done(n, 0);
+    for (int i = 0; i < n; ++i) {
+        if (!std::isfinite(beta[i]) || !std::isfinite(bnorm[i])) { status[i] = FDE_ERR_NAN; done[i] = 1; }
+        else if (bnorm[i] == 0.0 || beta[i] <= o.tol * bnorm[i]) done[i] = 1;
+    }
+    for (;;) {
+        std::vector<int> round;
+        for (int i = 0; i < n; ++i)
+            if (!done[i]) round.push_back(i);
+        if (round.empty()) break;
+        const int nr = (int)round.size();
+        if ((rc = upload_list(b, round, b->h_act, b->d_act))) return fail(rc);
+        if ((rc = launch_scale_batched(b->d_inst, b->d_act, nr, 1, 0, o.restart, b->max_n, st))) return fail(rc);
+        std::vector<char> in_cycle(n, 0);
+        for (int i : round) { in_cycle[i] = 1; kk[i] = 0; }
+        for (int j = 0; j < o.restart; ++j) {
+            std::vector<int> cyc;
+            for (int i : round)
+                if (in_cycle[i]) cyc.push_back(i);
+            if (cyc.empty()) break;
+            const int nc = (int)cyc.size();
+            if ((rc = upload_list(b, cyc, b->h_act, b->d_act))) return fail(rc);
+            if ((rc = launch_time_fft_batched(b->d_inst, b->d_act, nc, b->max_mp, b->max_s, j, st))) return fail(rc);
+            if ((rc = launch_trsv_batched(b->d_inst, b->d_act, nc, b->max_nblk, b->max_mp, st))) return fail(rc);
+            if ((rc = launch_time_ifft_batched(b->d_inst, b->d_act, nc, b->max_mp, b->max_s, j, st))) return fail(rc);
+            if ((rc = launch_matvec_batched(b->d_inst, b->d_act, nc, b->max_s, b->max_L, b->max_m, 0, j, st)))
+                return fail(rc);
+            if ((rc = launch_dots_batched(b->d_inst, b->d_act, nc, 0, j, st))) return fail(rc);
+            if ((rc = launch_update_batched(b->d_inst, b->d_act, nc, 0, j, b->d_kvec, b->max_n, st))) return fail(rc);
+            if (o.reorth) {
+                if ((rc = launch_dots_batched(b->d_inst, b->d_act, nc, 1, j, st))) return fail(rc);
+                if ((rc = launch_update_batched(b->d_inst, b->d_act, nc, 1, j, b->d_kvec, b->max_n, st)))
+                    return fail(rc);
+            }
+            if ((rc = launch_dots_batched(b->d_inst, b->d_act, nc, 2, j, st))) return fail(rc);
+            if ((rc = launch_finish_batched(b->d_inst, b->d_act, nc, j, ldh, o.reorth, st))) return fail(rc);
+            if ((rc = launch_scale_batched(b->d_inst, b->d_act, nc, 0, j, o.restart, b->max_n, st))) return fail(rc);
+            if ((rc = gather(b))) return fail(rc);
+            for (int i : cyc) {
+                ++its[i];
+                kk[i] = j + 1;
+                est[i] = b->h_gather[4 * i + 1];
+                const double hn = std::fabs(b->h_gather[4 * i + 2]);
+                if (!std::isfinite(est[i]) || !std::isfinite(b->h_gather[4 * i])) {
+                    status[i] = FDE_ERR_NAN;
+                    in_cycle[i] = 0;
+                    continue;
+                }
+                if (est[i] <= o.tol * bnorm[i] || its[i] >= o.maxit || hn <= 1e-300) in_cycle[i] = 0;
+            }
+        }
+        // end of the round: x += Z y, true residual
+        std::vector<int> upd;
+        for (int i : round)
+            if (status[i] == FDE_OK && kk[i] > 0) upd.push_back(i);
+        for (int i : round)
+            if (status[i] != FDE_OK) done[i] = 1;
+        if (upd.empty()) continue;
+        const int nu = (int)upd.size();
+        for (int i = 0; i < n; ++i) b->h_kvec[i] = kk[i];
+        FDE_CUDA_TRY(cudaMemcpyAsync(b->d_kvec, b->h_kvec, n * sizeof(int), cudaMemcpyHostToDevice, st));
+        if ((rc = upload_list(b, upd, b->h_act, b->d_act))) return fail(rc);
+        if ((rc = launch_lsq_batched(b->d_inst, b->d_act, nu, b->d_kvec, ldh, st))) return fail(rc);
+        if ((rc = launch_update_batched(b->d_inst, b->d_act, nu, 2, 0, b->d_kvec, b->max_n, st))) return fail(rc);
+        if ((rc = launch_matvec_batched(b->d_inst, b->d_act, nu, b->max_s, b->max_L, b->max_m, 1, 0, st)))
+            return fail(rc);
+        if ((rc = launch_residual_batched(b->d_inst, b->d_act, nu, b->max_n, st))) return fail(rc);
+        if ((rc = launch_dots_batched(b->d_inst, b->d_act, nu, 3, 0, st))) return fail(rc);
+        if ((rc = gather(b))) return fail(rc);
+        for (int i : upd) {
+            ++restarts[i];
+            beta[i] = std::sqrt(b->h_gather[4 * i + 3]);
+            if (!std::isfinite(beta[i])) {
+                status[i] = FDE_ERR_NAN;
+                done[i] = 1;
+            } else if (beta[i] <= o.tol * bnorm[i]) {
+                done[i] = 1;
+            } else if (its[i] >= o.maxit) {
+                status[i] = FDE_ERR_NOT_CONVERGED;
+                done[i] = 1;
+            }
+        }
+    }
+    FDE_CUDA_TRY(cudaEventRecord(ev1, st));
+    FDE_CUDA_TRY(cudaEventSynchronize(ev1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev0, ev1);
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    int worst = FDE_OK;
+    for (int i = 0; i < n; ++i) {
+        if (stats) {
+            fde_stats& S = stats[i];
+            std::memset(&S, 0, sizeof S);
+            S.status = status[i];
+            S.iterations = its[i];
+            S.restarts = restarts[i];
+            S.precision = b->precision;
+            S.rel_residual = bnorm[i] > 0 ? beta[i] / bnorm[i] : 0.0;
+            S.rel_residual_estimate = bnorm[i] > 0 ? est[i] / bnorm[i] : 0.0;
+            S.ms_solve = ms;
+        }
+        if (status[i] != FDE_OK && worst == FDE_OK) worst = status[i];
+    }
+    if (worst == FDE_ERR_NOT_CONVERGED) return set_error(worst, "some instances reached maxit");
+    if (worst == FDE_ERR_NAN) return set_error(worst, "non-finite residual in some instance");
+    return FDE_OK;
+}
+
+}  // extern "C"

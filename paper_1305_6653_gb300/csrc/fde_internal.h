@@ -40,6 +40,59 @@ inline int ilog2(int v) {
 }
 inline int round_up(int v, int q) { return (v + q - 1) / q * q; }
 
+constexpr int LU_NB = 32;  // panel width of the blocked Strang-block LU
+
+// ---------------------------------------------------------------------------
+// Device descriptors of a batch of independent problems (batch.cu).  One InstDev
+// per instance (sizes, coefficient / symbol pointers, factor and Krylov buffers),
+// one BlkDev per Strang block of every instance.
+// ---------------------------------------------------------------------------
+struct InstDev {
+    int m, s, mp, L, logL, logs, mu, nblk;
+    long n;
+    double h, dxa;
+    const int* start;
+    const double* A;
+    const double* B;
+    const double* dplus;
+    const double* dminus;
+    const double2* sym;
+    const double2* twL;
+    const float2* tws32;
+    const double2* tws;
+    void* rhat;
+    void* fac;
+    void* dinv;
+    double* b;
+    double* x;
+    double* V;
+    double* Z;
+    double* work;
+    double* H;
+    double* cs;
+    double* sn;
+    double* gv;
+    double* y;
+    double* scal;          // [0..63] h1, [64..127] h2, [128] |w|^2, [129] est, [130] H(j+1,j), [132] beta^2
+    double* partial;       // RED_CTAS x 64
+    unsigned int* counter;
+};
+
+struct BlkDev {
+    int inst, k, m, mp, ntile_max;
+    double h, dxa;
+    const double2* phi;  // &phi_k, &psi_k of the instance
+    const double2* psi;
+    const double* g;
+    const double* dplus;
+    const double* dminus;
+    void* fac;    // this block's planes (Re then Im, mp x mp each)
+    void* dinv;   // this block's 1/U_ii (mp complex)
+    unsigned char* apack;  // this block's packed operand tiles (tensor-core paths)
+    unsigned char* bpack;
+    int* info;
+};
+
 // ---------------------------------------------------------------------------
 // kernel launchers (defined in the .cu files)
 // ---------------------------------------------------------------------------
@@ -150,6 +203,28 @@ struct Problem {
 
 // The problem behind a C-ABI handle (defined in api.cu).
 Problem* problem_of(fde_problem* h);
+int ensure_factor_buffers(Problem& P, int precision);
+int ensure_workspace(Problem& P, int restart);
+
+// batched launchers (lu.cu, timefft.cu, matvec.cu, krylov.cu)
+int launch_lu_batched(const BlkDev* d_blk, const std::vector<int>& mp_sorted, int precision, int* err,
+                      cudaStream_t st);
+int launch_trsv_batched(const InstDev* I, const int* act, int nact, int max_nblk, int max_mp, cudaStream_t st);
+int launch_time_fft_batched(const InstDev* I, const int* act, int nact, int max_mp, int max_s, int j,
+                            cudaStream_t st);
+int launch_time_ifft_batched(const InstDev* I, const int* act, int nact, int max_mp, int max_s, int j,
+                             cudaStream_t st);
+int launch_matvec_batched(const InstDev* I, const int* act, int nact, int max_s, int max_L, int max_m, int which,
+                          int j, cudaStream_t st);
+int launch_dots_batched(const InstDev* I, const int* act, int nact, int mode, int j, cudaStream_t st);
+int launch_update_batched(const InstDev* I, const int* act, int nact, int mode, int j, const int* kvec, long max_n,
+                          cudaStream_t st);
+int launch_scale_batched(const InstDev* I, const int* act, int nact, int mode, int j, int restart, long max_n,
+                         cudaStream_t st);
+int launch_residual_batched(const InstDev* I, const int* act, int nact, long max_n, cudaStream_t st);
+int launch_finish_batched(const InstDev* I, const int* act, int nact, int j, int ldh, int reorth, cudaStream_t st);
+int launch_lsq_batched(const InstDev* I, const int* act, int nact, const int* kvec, int ldh, cudaStream_t st);
+int launch_gather_scalars(const InstDev* I, int ninst, double* out, cudaStream_t st);
 
 // Records a CUDA event pair around the launches made in its scope when the
 // problem's profiler is on.

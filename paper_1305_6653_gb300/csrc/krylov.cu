@@ -15,16 +15,16 @@ constexpr int RED_THREADS = 256;
 constexpr int KMAX = 64;       // max Krylov vectors per multi-dot
 
 template <int KC>
-__global__ void __launch_bounds__(RED_THREADS)
-dots_kernel(const double* __restrict__ V, int k, const double* __restrict__ w, long n, double* __restrict__ out,
-            double* __restrict__ partial, unsigned int* __restrict__ counter) {
+__device__ __forceinline__ void dots_body(const double* __restrict__ V, int k, const double* __restrict__ w, long n,
+                                          double* __restrict__ out, double* __restrict__ partial,
+                                          unsigned int* __restrict__ counter, int bx, int nblocks) {
     __shared__ double red[RED_THREADS / 32][KC];
     __shared__ bool last;
     double acc[KC];
 #pragma unroll
     for (int i = 0; i < KC; ++i) acc[i] = 0.0;
-    const long stride = (long)gridDim.x * blockDim.x;
-    for (long x = (long)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += stride) {
+    const long stride = (long)nblocks * blockDim.x;
+    for (long x = (long)bx * blockDim.x + threadIdx.x; x < n; x += stride) {
         const double wx = w[x];
 #pragma unroll
         for (int i = 0; i < KC; ++i)
@@ -41,21 +41,28 @@ dots_kernel(const double* __restrict__ V, int k, const double* __restrict__ w, l
     for (int i = threadIdx.x; i < k; i += blockDim.x) {
         double v = 0.0;
         for (int q = 0; q < RED_THREADS / 32; ++q) v += red[q][i];
-        partial[(size_t)blockIdx.x * KMAX + i] = v;
+        partial[(size_t)bx * KMAX + i] = v;
     }
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == (unsigned)nblocks - 1);
     __syncthreads();
     if (last) {
         __threadfence();
         for (int i = threadIdx.x; i < k; i += blockDim.x) {
             double v = 0.0;
-            for (int c = 0; c < (int)gridDim.x; ++c) v += ((volatile double*)partial)[(size_t)c * KMAX + i];
+            for (int c = 0; c < nblocks; ++c) v += ((volatile double*)partial)[(size_t)c * KMAX + i];
             out[i] = v;
         }
         if (threadIdx.x == 0) *counter = 0u;
     }
+}
+
+template <int KC>
+__global__ void __launch_bounds__(RED_THREADS)
+dots_kernel(const double* __restrict__ V, int k, const double* __restrict__ w, long n, double* __restrict__ out,
+            double* __restrict__ partial, unsigned int* __restrict__ counter) {
+    dots_body<KC>(V, k, w, n, out, partial, counter, blockIdx.x, gridDim.x);
 }
 
 // w += sign * sum_i coef[i] V_i
@@ -131,6 +138,198 @@ __global__ void lsq_solve_kernel(const double* __restrict__ H, int ldh, int k, c
         for (int c = i + 1; c < k; ++c) v -= H[(size_t)c * ldh + i] * y[c];
         y[i] = v / H[(size_t)i * ldh + i];
     }
+}
+
+// ---------------------------------------------------------------------------
+// Batched variants over the active instances act[0..gridDim.y) of a batch.
+// Each instance owns its vectors, scalars, partial sums and reduction ticket.
+// ---------------------------------------------------------------------------
+constexpr int RED_CTAS_B = 32;  // reduction CTAs per instance in a batch
+
+// mode 0 / 1: h1 / h2 = V_{0..j}^T V_{j+1};  mode 2: |V_{j+1}|^2 -> scal[128];
+// mode 3: |V_0|^2 -> scal[132];  mode 4: |b|^2 -> scal[131]
+template <int KC>
+__global__ void __launch_bounds__(RED_THREADS)
+dots_batched(const InstDev* __restrict__ I, const int* __restrict__ act, int mode, int j) {
+    const InstDev& d = I[act[blockIdx.y]];
+    const double* w;
+    const double* V;
+    int k;
+    double* out;
+    if (mode <= 1) {
+        V = d.V; k = j + 1; w = d.V + (size_t)(j + 1) * d.n; out = d.scal + (mode == 0 ? 0 : 64);
+    } else if (mode == 2) {
+        V = w = d.V + (size_t)(j + 1) * d.n; k = 1; out = d.scal + 128;
+    } else if (mode == 3) {
+        V = w = d.V; k = 1; out = d.scal + 132;
+    } else {
+        V = w = d.b; k = 1; out = d.scal + 131;
+    }
+    dots_body<KC>(V, k, w, d.n, out, d.partial, d.counter, blockIdx.x, gridDim.x);
+}
+
+// mode 0 / 1: V_{j+1} -= V_{0..j} h1 / h2;  mode 2: x += Z_{0..k-1} y with k = kvec[instance]
+__global__ void update_batched(const InstDev* __restrict__ I, const int* __restrict__ act, int mode, int j,
+                               const int* __restrict__ kvec) {
+    __shared__ double c[KMAX];
+    const int inst = act[blockIdx.y];
+    const InstDev& d = I[inst];
+    const double* V;
+    double* w;
+    const double* coef;
+    int k;
+    double sign;
+    if (mode <= 1) {
+        V = d.V; w = d.V + (size_t)(j + 1) * d.n; coef = d.scal + (mode == 0 ? 0 : 64); k = j + 1; sign = -1.0;
+    } else {
+        V = d.Z; w = d.x; coef = d.y; k = kvec[inst]; sign = 1.0;
+    }
+    for (int i = threadIdx.x; i < k; i += blockDim.x) c[i] = sign * coef[i];
+    __syncthreads();
+    const long stride = (long)gridDim.x * blockDim.x;
+    for (long x = (long)blockIdx.x * blockDim.x + threadIdx.x; x < d.n; x += stride) {
+        double acc = w[x];
+        for (int i = 0; i < k; ++i) acc += c[i] * V[(size_t)i * d.n + x];
+        w[x] = acc;
+    }
+}
+
+// mode 0: V_{j+1} /= sqrt(scal[128]);  mode 1: V_0 /= sqrt(scal[132]) and g = (sqrt(scal[132]), 0, ...)
+__global__ void scale_batched(const InstDev* __restrict__ I, const int* __restrict__ act, int mode, int j,
+                              int restart) {
+    const InstDev& d = I[act[blockIdx.y]];
+    double* v = mode == 0 ? d.V + (size_t)(j + 1) * d.n : d.V;
+    const double nr = sqrt(d.scal[mode == 0 ? 128 : 132]);
+    const double inv = nr > 0.0 ? 1.0 / nr : 0.0;
+    const long stride = (long)gridDim.x * blockDim.x;
+    for (long x = (long)blockIdx.x * blockDim.x + threadIdx.x; x < d.n; x += stride) v[x] *= inv;
+    if (mode == 1 && blockIdx.x == 0)
+        for (int i = threadIdx.x; i <= restart; i += blockDim.x) d.gv[i] = i == 0 ? nr : 0.0;
+}
+
+// V_0 = b - work (work = M x)
+__global__ void residual_batched(const InstDev* __restrict__ I, const int* __restrict__ act) {
+    const InstDev& d = I[act[blockIdx.y]];
+    const long stride = (long)gridDim.x * blockDim.x;
+    for (long x = (long)blockIdx.x * blockDim.x + threadIdx.x; x < d.n; x += stride) d.V[x] = d.b[x] - d.work[x];
+}
+
+// one thread per active instance
+__global__ void finish_batched(const InstDev* __restrict__ I, const int* __restrict__ act, int nact, int j, int ldh,
+                               int reorth) {
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= nact) return;
+    const InstDev& d = I[act[a]];
+    double* col = d.H + (size_t)j * ldh;
+    const double* h1 = d.scal;
+    const double* h2 = d.scal + 64;
+    for (int i = 0; i <= j; ++i) col[i] = h1[i] + (reorth ? h2[i] : 0.0);
+    col[j + 1] = sqrt(d.scal[128]);
+    for (int i = 0; i < j; ++i) {
+        const double t = d.cs[i] * col[i] + d.sn[i] * col[i + 1];
+        col[i + 1] = -d.sn[i] * col[i] + d.cs[i] * col[i + 1];
+        col[i] = t;
+    }
+    const double aa = col[j], bb = col[j + 1];
+    const double r = hypot(aa, bb);
+    const double c = r > 0.0 ? aa / r : 1.0;
+    const double sn = r > 0.0 ? bb / r : 0.0;
+    d.cs[j] = c;
+    d.sn[j] = sn;
+    col[j] = r;
+    col[j + 1] = 0.0;
+    d.gv[j + 1] = -sn * d.gv[j];
+    d.gv[j] = c * d.gv[j];
+    d.scal[129] = fabs(d.gv[j + 1]);
+    d.scal[130] = bb;
+}
+
+__global__ void lsq_batched(const InstDev* __restrict__ I, const int* __restrict__ act, int nact,
+                            const int* __restrict__ kvec, int ldh) {
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= nact) return;
+    const int inst = act[a];
+    const InstDev& d = I[inst];
+    const int k = kvec[inst];
+    for (int i = k - 1; i >= 0; --i) {
+        double v = d.gv[i];
+        for (int c = i + 1; c < k; ++c) v -= d.H[(size_t)c * ldh + i] * d.y[c];
+        d.y[i] = v / d.H[(size_t)i * ldh + i];
+    }
+}
+
+// out[4*i + q] = scal[128 + q] of instance i (q = 0..3), and out[4*i+3] = scal[132]
+__global__ void gather_scalars(const InstDev* __restrict__ I, int ninst, double* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ninst) return;
+    const double* sc = I[i].scal;
+    out[4 * i + 0] = sc[128];
+    out[4 * i + 1] = sc[129];
+    out[4 * i + 2] = sc[130];
+    out[4 * i + 3] = sc[132];
+}
+
+static int grid_for(long n);
+
+int launch_dots_batched(const InstDev* I, const int* act, int nact, int mode, int j, cudaStream_t st) {
+    if (nact <= 0) return FDE_OK;
+    const int k = mode <= 1 ? j + 1 : 1;
+    const dim3 grid(RED_CTAS_B, nact);
+    if (k <= 8) dots_batched<8><<<grid, RED_THREADS, 0, st>>>(I, act, mode, j);
+    else if (k <= 16) dots_batched<16><<<grid, RED_THREADS, 0, st>>>(I, act, mode, j);
+    else if (k <= 32) dots_batched<32><<<grid, RED_THREADS, 0, st>>>(I, act, mode, j);
+    else dots_batched<64><<<grid, RED_THREADS, 0, st>>>(I, act, mode, j);
+    FDE_LAUNCH_CHECK("dots_batched");
+    return FDE_OK;
+}
+
+int launch_update_batched(const InstDev* I, const int* act, int nact, int mode, int j, const int* kvec, long max_n,
+                          cudaStream_t st) {
+    if (nact <= 0) return FDE_OK;
+    int g = (int)((max_n + 255) / 256);
+    if (g > 64) g = 64;
+    update_batched<<<dim3(g, nact), 256, 0, st>>>(I, act, mode, j, kvec);
+    FDE_LAUNCH_CHECK("update_batched");
+    return FDE_OK;
+}
+
+int launch_scale_batched(const InstDev* I, const int* act, int nact, int mode, int j, int restart, long max_n,
+                         cudaStream_t st) {
+    if (nact <= 0) return FDE_OK;
+    int g = (int)((max_n + 255) / 256);
+    if (g > 64) g = 64;
+    scale_batched<<<dim3(g, nact), 256, 0, st>>>(I, act, mode, j, restart);
+    FDE_LAUNCH_CHECK("scale_batched");
+    return FDE_OK;
+}
+
+int launch_residual_batched(const InstDev* I, const int* act, int nact, long max_n, cudaStream_t st) {
+    if (nact <= 0) return FDE_OK;
+    int g = (int)((max_n + 255) / 256);
+    if (g > 64) g = 64;
+    residual_batched<<<dim3(g, nact), 256, 0, st>>>(I, act);
+    FDE_LAUNCH_CHECK("residual_batched");
+    return FDE_OK;
+}
+
+int launch_finish_batched(const InstDev* I, const int* act, int nact, int j, int ldh, int reorth, cudaStream_t st) {
+    if (nact <= 0) return FDE_OK;
+    finish_batched<<<(nact + 63) / 64, 64, 0, st>>>(I, act, nact, j, ldh, reorth);
+    FDE_LAUNCH_CHECK("finish_batched");
+    return FDE_OK;
+}
+
+int launch_lsq_batched(const InstDev* I, const int* act, int nact, const int* kvec, int ldh, cudaStream_t st) {
+    if (nact <= 0) return FDE_OK;
+    lsq_batched<<<(nact + 63) / 64, 64, 0, st>>>(I, act, nact, kvec, ldh);
+    FDE_LAUNCH_CHECK("lsq_batched");
+    return FDE_OK;
+}
+
+int launch_gather_scalars(const InstDev* I, int ninst, double* out, cudaStream_t st) {
+    gather_scalars<<<(ninst + 63) / 64, 64, 0, st>>>(I, ninst, out);
+    FDE_LAUNCH_CHECK("gather_scalars");
+    return FDE_OK;
 }
 
 static int grid_for(long n) {

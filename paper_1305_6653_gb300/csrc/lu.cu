@@ -20,7 +20,7 @@
 
 namespace fde {
 
-constexpr int NB = 32;
+constexpr int NB = LU_NB;
 
 template <typename T>
 __device__ __forceinline__ T* plane_re(T* fac, int k, int mp) { return fac + (size_t)k * 2 * mp * mp; }
@@ -42,16 +42,12 @@ __device__ __forceinline__ double j_entry(int i, int j, double dxa, const double
 // FP64 blocks are formed in FP64; FP32 blocks in FP32 from FP32 copies of the
 // per-row coefficients dx^-alpha d+_i, dx^-alpha d-_i and of h psi_k.
 template <typename T>
-__global__ void form_blocks_kernel(int m, int mp, double h, double dxa, const double* __restrict__ g,
-                                   const double* __restrict__ dp, const double* __restrict__ dm,
-                                   const double2* __restrict__ phi, const double2* __restrict__ psi, T* __restrict__ fac) {
-    const int k = blockIdx.y;
-    const double2 ph = phi[k];
-    const double2 ps = psi[k];
+__device__ __forceinline__ void form_body(int m, int mp, double h, double dxa, const double* __restrict__ g,
+                                          const double* __restrict__ dp, const double* __restrict__ dm, double2 ph,
+                                          double2 ps, T* __restrict__ re, int row0, int rowstride) {
     const T hpr = (T)(h * ps.x), hpi = (T)(h * ps.y);
-    T* re = plane_re(fac, k, mp);
-    T* im = plane_im(fac, k, mp);
-    for (int i = blockIdx.x; i < mp; i += gridDim.x) {
+    T* im = re + (size_t)mp * mp;
+    for (int i = row0; i < mp; i += rowstride) {
         T* rr = re + (size_t)i * mp;
         T* ri = im + (size_t)i * mp;
         if (i >= m) {
@@ -82,15 +78,28 @@ __global__ void form_blocks_kernel(int m, int mp, double h, double dxa, const do
     }
 }
 
+template <typename T>
+__global__ void form_blocks_kernel(int m, int mp, double h, double dxa, const double* __restrict__ g,
+                                   const double* __restrict__ dp, const double* __restrict__ dm,
+                                   const double2* __restrict__ phi, const double2* __restrict__ psi, T* __restrict__ fac) {
+    const int k = blockIdx.y;
+    form_body<T>(m, mp, h, dxa, g, dp, dm, phi[k], psi[k], plane_re(fac, k, mp), blockIdx.x, gridDim.x);
+}
+
+// Batched: grid.y runs over the block table of every instance.
+template <typename T>
+__global__ void form_blocks_batched(const BlkDev* __restrict__ B) {
+    const BlkDev& d = B[blockIdx.y];
+    form_body<T>(d.m, d.mp, d.h, d.dxa, d.g, d.dplus, d.dminus, *d.phi, *d.psi, (T*)d.fac, blockIdx.x, gridDim.x);
+}
+
 // Unblocked LU (no pivoting) of the NB x NB diagonal block of every matrix.
 template <typename T>
-__global__ void __launch_bounds__(256)
-lu_diag_kernel(int mp, int p, T* __restrict__ fac, cplx_t<T>* __restrict__ dinv, int* __restrict__ info) {
+__device__ __forceinline__ void diag_body(int mp, int p, T* __restrict__ re, cplx_t<T>* __restrict__ dinv,
+                                          int* __restrict__ info) {
     using C = cplx_t<T>;
     __shared__ C D[NB][NB + 1];
-    const int k = blockIdx.x;
-    T* re = plane_re(fac, k, mp);
-    T* im = plane_im(fac, k, mp);
+    T* im = re + (size_t)mp * mp;
     const int o = p * NB;
     for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
         const int r = e / NB, c = e % NB;
@@ -102,7 +111,7 @@ lu_diag_kernel(int mp, int p, T* __restrict__ fac, cplx_t<T>* __restrict__ dinv,
         const C piv = D[c][c];
         const T den = piv.x * piv.x + piv.y * piv.y;
         const bool bad = !(den > T(0)) || !isfinite((double)den);
-        if (bad && threadIdx.x == 0) atomicCAS(info + k, 0, o + c + 1);
+        if (bad && threadIdx.x == 0) atomicCAS(info, 0, o + c + 1);
         C inv = mk(piv.x / den, -piv.y / den);
         if (bad) inv = mk(T(0), T(0));
         __syncthreads();
@@ -114,7 +123,7 @@ lu_diag_kernel(int mp, int p, T* __restrict__ fac, cplx_t<T>* __restrict__ dinv,
             const int r = c + 1 + e / w, cc = c + 1 + e % w;
             D[r][cc] = csub(D[r][cc], cmul(D[r][c], D[c][cc]));
         }
-        if (threadIdx.x == 0) dinv[(size_t)k * mp + o + c] = inv;
+        if (threadIdx.x == 0) dinv[o + c] = inv;
         __syncthreads();
     }
     for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
@@ -123,6 +132,20 @@ lu_diag_kernel(int mp, int p, T* __restrict__ fac, cplx_t<T>* __restrict__ dinv,
         re[idx] = D[r][c].x;
         im[idx] = D[r][c].y;
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+lu_diag_kernel(int mp, int p, T* __restrict__ fac, cplx_t<T>* __restrict__ dinv, int* __restrict__ info) {
+    const int k = blockIdx.x;
+    diag_body<T>(mp, p, plane_re(fac, k, mp), dinv + (size_t)k * mp, info + k);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) lu_diag_batched(const BlkDev* __restrict__ B, int p) {
+    const BlkDev& d = B[blockIdx.x];
+    if (p * NB >= d.mp) return;
+    diag_body<T>(d.mp, p, (T*)d.fac, (cplx_t<T>*)d.dinv, d.info);
 }
 
 // Panel solves.  blockIdx.x < nrow: a chunk of RC rows of A21 -> L21 = A21 U11^{-1};
@@ -134,17 +157,14 @@ lu_diag_kernel(int mp, int p, T* __restrict__ fac, cplx_t<T>* __restrict__ dinv,
 // tensor-core operand tiles (A' from L21 rows, B' from U12 columns; see lu_tc.cuh).
 constexpr int RC = 128;
 template <typename T, int PACK>
-__global__ void __launch_bounds__(RC)
-lu_panel_kernel(int mp, int p, int nrow, T* __restrict__ fac, unsigned char* __restrict__ apack,
-                unsigned char* __restrict__ bpack, int ntile_max) {
+__device__ __forceinline__ void panel_body(int mp, int p, int nrow, T* __restrict__ re, unsigned char* __restrict__ apack,
+                                           unsigned char* __restrict__ bpack, int bx) {
     using C = cplx_t<T>;
     __shared__ C D[NB][NB + 1];
     __shared__ C dinv_s[NB];
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C (*X)[NB + 1] = reinterpret_cast<C (*)[NB + 1]>(smem_raw);  // [RC][NB+1]
-    const int k = blockIdx.y;
-    T* re = plane_re(fac, k, mp);
-    T* im = plane_im(fac, k, mp);
+    T* im = re + (size_t)mp * mp;
     const int o = p * NB;
     const int rest = o + NB;
     for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
@@ -152,8 +172,8 @@ lu_panel_kernel(int mp, int p, int nrow, T* __restrict__ fac, unsigned char* __r
         const size_t idx = (size_t)(o + r) * mp + o + c;
         D[r][c] = mk(re[idx], im[idx]);
     }
-    const bool rows = blockIdx.x < nrow;
-    const int chunk = rows ? blockIdx.x : blockIdx.x - nrow;
+    const bool rows = bx < nrow;
+    const int chunk = rows ? bx : bx - nrow;
     const int b0 = rest + chunk * RC;
     // X[q][c]: rows mode -> A21[b0+q][o+c]; columns mode -> A12[o+c][b0+q] (stored transposed)
     for (int e = threadIdx.x; e < RC * NB; e += blockDim.x) {
@@ -217,11 +237,11 @@ lu_panel_kernel(int mp, int p, int nrow, T* __restrict__ fac, unsigned char* __r
             const int rt = (chunk * RC + qq) % TC_BM;  // row of the operand tile (A': output row, B': output column)
             const float vr = (float)X[qq][c].x, vi = (float)X[qq][c].y;
             if (rows) {
-                unsigned char* t = apack + ((size_t)k * ntile_max + tile) * TcCfg<PACK>::A_BYTES;
+                unsigned char* t = apack + (size_t)tile * TcCfg<PACK>::A_BYTES;
                 pack_store<PACK>(t, rt, c, vr);
                 pack_store<PACK>(t, rt, NB + c, vi);
             } else {
-                unsigned char* t = bpack + ((size_t)k * ntile_max + tile) * TcCfg<PACK>::B_BYTES;
+                unsigned char* t = bpack + (size_t)tile * TcCfg<PACK>::B_BYTES;
                 pack_store<PACK>(t, rt, c, vr);            // Re part of the product: Re L Re U - Im L Im U
                 pack_store<PACK>(t, rt, NB + c, -vi);
                 pack_store<PACK>(t, TC_BN + rt, c, vi);    // Im part: Re L Im U + Im L Re U
@@ -231,21 +251,42 @@ lu_panel_kernel(int mp, int p, int nrow, T* __restrict__ fac, unsigned char* __r
     }
 }
 
+template <int PACK>
+__device__ __forceinline__ size_t pack_stride(bool a_side, int ntile_max) {
+    if constexpr (PACK >= 0) return (size_t)ntile_max * (a_side ? TcCfg<PACK>::A_BYTES : TcCfg<PACK>::B_BYTES);
+    return 0;
+}
+
+template <typename T, int PACK>
+__global__ void __launch_bounds__(RC)
+lu_panel_kernel(int mp, int p, int nrow, T* __restrict__ fac, unsigned char* __restrict__ apack,
+                unsigned char* __restrict__ bpack, int ntile_max) {
+    const int k = blockIdx.y;
+    panel_body<T, PACK>(mp, p, nrow, plane_re(fac, k, mp), apack ? apack + k * pack_stride<PACK>(true, ntile_max) : nullptr,
+                        bpack ? bpack + k * pack_stride<PACK>(false, ntile_max) : nullptr, blockIdx.x);
+}
+
+template <typename T, int PACK>
+__global__ void __launch_bounds__(RC) lu_panel_batched(const BlkDev* __restrict__ B, int p) {
+    const BlkDev& d = B[blockIdx.y];
+    const int rem = d.mp - (p + 1) * NB;
+    if (rem <= 0) return;
+    const int nrow = (rem + RC - 1) / RC;
+    if ((int)blockIdx.x >= 2 * nrow) return;
+    panel_body<T, PACK>(d.mp, p, nrow, (T*)d.fac, d.apack, d.bpack, blockIdx.x);
+}
+
 // Trailing update A22 -= L21 U12 on CUDA cores: 64 x 64 output tile per CTA,
 // 4 x 4 complex outputs per thread, K = NB.
 template <typename T>
-__global__ void __launch_bounds__(256)
-lu_update_kernel(int mp, int p, int ntile, T* __restrict__ fac) {
+__device__ __forceinline__ void update_body(int mp, int p, T* __restrict__ re, int ti, int tj) {
     using C = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C (*Ls)[NB + 1] = reinterpret_cast<C (*)[NB + 1]>(smem_raw);                        // [64][NB+1]
     C (*Us)[64 + 1] = reinterpret_cast<C (*)[64 + 1]>(smem_raw + 64 * (NB + 1) * sizeof(C));  // [NB][65]
-    const int k = blockIdx.y;
-    T* re = plane_re(fac, k, mp);
-    T* im = plane_im(fac, k, mp);
+    T* im = re + (size_t)mp * mp;
     const int o = p * NB;
     const int rest = o + NB;
-    const int ti = blockIdx.x / ntile, tj = blockIdx.x % ntile;
     const int r0 = rest + ti * 64, c0 = rest + tj * 64;
     for (int e = threadIdx.x; e < 64 * NB; e += blockDim.x) {
         const int q = e / NB, c = e % NB;
@@ -292,6 +333,25 @@ lu_update_kernel(int mp, int p, int ntile, T* __restrict__ fac) {
     }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256)
+lu_update_kernel(int mp, int p, int ntile, T* __restrict__ fac) {
+    const int k = blockIdx.y;
+    update_body<T>(mp, p, plane_re(fac, k, mp), blockIdx.x / ntile, blockIdx.x % ntile);
+}
+
+// Batched: grid.x covers the tiles of the largest trailing matrix (ntile_grid^2).
+template <typename T>
+__global__ void __launch_bounds__(256) lu_update_batched(const BlkDev* __restrict__ B, int p, int ntile_grid) {
+    const BlkDev& d = B[blockIdx.y];
+    const int rem = d.mp - (p + 1) * NB;
+    if (rem <= 0) return;
+    const int nt = (rem + 63) / 64;
+    const int ti = blockIdx.x / ntile_grid, tj = blockIdx.x % ntile_grid;
+    if (ti >= nt || tj >= nt) return;
+    update_body<T>(d.mp, p, (T*)d.fac, ti, tj);
+}
+
 // Forward (unit lower L) then backward (U) substitution for one block per CTA,
 // in place on rhat[k] (length mp), column-oriented ("right-looking"): for each
 // 32-row diagonal tile, warp 0 resolves the tile from shared memory, then all
@@ -300,13 +360,18 @@ lu_update_kernel(int mp, int p, int ntile, T* __restrict__ fac) {
 // row (one contiguous 32-value segment per plane), every load is independent of
 // the others, and the next diagonal tile is prefetched into shared memory, so
 // the factor planes stream at full memory-level parallelism.
+struct dvec4 {
+    double x, y, z, w;
+};
 template <typename T> struct vec4;
 template <> struct vec4<float> { using type = float4; };
-template <> struct vec4<double> { using type = double4; };
+template <> struct vec4<double> { using type = dvec4; };
 
-template <typename T>
-__device__ __forceinline__ typename vec4<T>::type ld4(const T* p) {
-    return *reinterpret_cast<const typename vec4<T>::type*>(p);
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ dvec4 ld4(const double* p) {
+    const double2 a = reinterpret_cast<const double2*>(p)[0];
+    const double2 b = reinterpret_cast<const double2*>(p)[1];
+    return dvec4{a.x, a.y, b.x, b.y};
 }
 
 constexpr int TRSV_THREADS = 512;
@@ -363,18 +428,14 @@ __device__ __forceinline__ void strip_update(cplx_t<T>* y, const cplx_t<T>* xs, 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(TRSV_THREADS)
-block_trsv_kernel(int mp, const T* __restrict__ fac, const cplx_t<T>* __restrict__ dinv, cplx_t<T>* __restrict__ rhat) {
+__device__ __forceinline__ void trsv_body(int mp, const T* __restrict__ re, const cplx_t<T>* __restrict__ dv,
+                                          cplx_t<T>* __restrict__ x) {
     using C = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* y = reinterpret_cast<C*>(smem_raw);                        // mp
     C (*D)[32][33] = reinterpret_cast<C (*)[32][33]>(y + mp);     // 2 diagonal tiles (double buffer)
     __shared__ C xs[32];
-    const int k = blockIdx.x;
-    const T* re = fac + (size_t)k * 2 * mp * mp;
     const T* im = re + (size_t)mp * mp;
-    C* x = rhat + (size_t)k * mp;
-    const C* dv = dinv + (size_t)k * mp;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nt = mp / 32;
     for (int i = threadIdx.x; i < mp; i += blockDim.x) y[i] = x[i];
@@ -433,6 +494,25 @@ block_trsv_kernel(int mp, const T* __restrict__ fac, const cplx_t<T>* __restrict
         __syncthreads();
     }
     for (int i = threadIdx.x; i < mp; i += blockDim.x) x[i] = y[i];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TRSV_THREADS)
+block_trsv_kernel(int mp, const T* __restrict__ fac, const cplx_t<T>* __restrict__ dinv, cplx_t<T>* __restrict__ rhat) {
+    const int k = blockIdx.x;
+    trsv_body<T>(mp, fac + (size_t)k * 2 * mp * mp, dinv + (size_t)k * mp, rhat + (size_t)k * mp);
+}
+
+// Batched over the active instances act[0..gridDim.y): block k = blockIdx.x of instance act[blockIdx.y].
+template <typename T>
+__global__ void __launch_bounds__(TRSV_THREADS)
+block_trsv_batched(const InstDev* __restrict__ I, const int* __restrict__ act) {
+    const InstDev& d = I[act[blockIdx.y]];
+    const int k = blockIdx.x;
+    if (k >= d.nblk) return;
+    const size_t mp = d.mp;
+    trsv_body<T>(d.mp, (const T*)d.fac + (size_t)k * 2 * mp * mp, (const cplx_t<T>*)d.dinv + (size_t)k * mp,
+                 (cplx_t<T>*)d.rhat + (size_t)k * mp);
 }
 
 template <typename T>
@@ -533,6 +613,73 @@ static int run_lu_tc(Problem& P, cudaStream_t st) {
                                                                         P.d_err);
         FDE_LAUNCH_CHECK("lu_update_tc_kernel");
     }
+    return FDE_OK;
+}
+
+// Batched LU over a block table sorted by m_p (descending): at step p the blocks
+// still being factored form a prefix of the table.  FP32 storage; trailing
+// updates on CUDA cores (FDE_FP32) or tcgen05 (FDE_TF32 / FDE_BF16).
+template <int KIND>
+static int run_lu_batched(const BlkDev* d_blk, const std::vector<int>& mps, int* err, cudaStream_t st) {
+    const int nbt = (int)mps.size();
+    const int max_mp = mps[0];
+    {
+        form_blocks_batched<float><<<dim3(64, nbt), 256, 0, st>>>(d_blk);
+        FDE_LAUNCH_CHECK("form_blocks_batched");
+    }
+    const size_t panel_smem = (size_t)RC * (NB + 1) * sizeof(float2);
+    FDE_CUDA_TRY(cudaFuncSetAttribute(lu_panel_batched<float, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)panel_smem));
+    const size_t upd_smem = (64 * (NB + 1) + NB * 65) * sizeof(float2);
+    int tc_smem = 0;
+    if constexpr (KIND >= 0) {
+        using Cfg = TcCfg<KIND>;
+        tc_smem = (Cfg::A_BYTES + Cfg::B_BYTES) > 100 * 1024 ? (Cfg::A_BYTES + Cfg::B_BYTES) : 100 * 1024;
+        FDE_CUDA_TRY(cudaFuncSetAttribute(lu_update_tc_batched<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          tc_smem));
+    } else {
+        FDE_CUDA_TRY(cudaFuncSetAttribute(lu_update_batched<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)upd_smem));
+    }
+    for (int p = 0; p * NB < max_mp; ++p) {
+        int nd = 0, nu = 0;
+        while (nd < nbt && mps[nd] > p * NB) ++nd;
+        while (nu < nbt && mps[nu] > (p + 1) * NB) ++nu;
+        lu_diag_batched<float><<<nd, 256, 0, st>>>(d_blk, p);
+        FDE_LAUNCH_CHECK("lu_diag_batched");
+        if (nu == 0) break;
+        const int rem = max_mp - (p + 1) * NB;
+        const int nch = (rem + RC - 1) / RC;
+        lu_panel_batched<float, KIND><<<dim3(2 * nch, nu), RC, panel_smem, st>>>(d_blk, p);
+        FDE_LAUNCH_CHECK("lu_panel_batched");
+        if constexpr (KIND >= 0) {
+            const int ntg = (rem + TC_BM - 1) / TC_BM;
+            lu_update_tc_batched<KIND><<<dim3(ntg * ntg, nu), 128, tc_smem, st>>>(d_blk, p, NB, ntg, err);
+            FDE_LAUNCH_CHECK("lu_update_tc_batched");
+        } else {
+            const int ntg = (rem + 63) / 64;
+            lu_update_batched<float><<<dim3(ntg * ntg, nu), 256, upd_smem, st>>>(d_blk, p, ntg);
+            FDE_LAUNCH_CHECK("lu_update_batched");
+        }
+    }
+    return FDE_OK;
+}
+
+int launch_lu_batched(const BlkDev* d_blk, const std::vector<int>& mp_sorted, int precision, int* err,
+                      cudaStream_t st) {
+    if (mp_sorted.empty()) return FDE_OK;
+    if (precision == FDE_TF32) return run_lu_batched<0>(d_blk, mp_sorted, err, st);
+    if (precision == FDE_BF16) return run_lu_batched<1>(d_blk, mp_sorted, err, st);
+    return run_lu_batched<-1>(d_blk, mp_sorted, err, st);
+}
+
+int launch_trsv_batched(const InstDev* I, const int* act, int nact, int max_nblk, int max_mp, cudaStream_t st) {
+    if (nact <= 0) return FDE_OK;
+    const size_t smem = ((size_t)max_mp + 2 * 32 * 33) * sizeof(float2);
+    FDE_CUDA_TRY(cudaFuncSetAttribute(block_trsv_batched<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+    block_trsv_batched<float><<<dim3(max_nblk, nact), TRSV_THREADS, smem, st>>>(I, act);
+    FDE_LAUNCH_CHECK("block_trsv_batched");
     return FDE_OK;
 }
 

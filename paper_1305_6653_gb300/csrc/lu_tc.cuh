@@ -52,12 +52,14 @@ __device__ __forceinline__ void pack_store(unsigned char* tile, int row, int kp,
     }
 }
 
-// grid: (ntile * ntile, nblk); 128 threads.  err: first failure code (bounded waits).
+// One 128 x 128 complex output tile (ti, tj) of one block; 128 threads.
+// re: the block's Re plane (Im follows); apack / bpack: the block's packed
+// operand tiles.  err: first failure code of a bounded wait.
 template <int KIND>
-__global__ void __launch_bounds__(128)
-lu_update_tc_kernel(int mp, int rest, int ntile, int ntile_max, float* __restrict__ fac,
-                    const unsigned char* __restrict__ apack, const unsigned char* __restrict__ bpack,
-                    int* __restrict__ err) {
+__device__ __forceinline__ void tc_update_body(int mp, int rest, float* __restrict__ re_plane,
+                                               const unsigned char* __restrict__ apack,
+                                               const unsigned char* __restrict__ bpack, int* __restrict__ err, int ti,
+                                               int tj) {
     using Cfg = TcCfg<KIND>;
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* sA = smem;
@@ -66,8 +68,6 @@ lu_update_tc_kernel(int mp, int rest, int ntile, int ntile_max, float* __restric
     __shared__ uint32_t tmem_base;
     __shared__ int ok_flag;
 
-    const int k = blockIdx.y;
-    const int ti = blockIdx.x / ntile, tj = blockIdx.x % ntile;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (warp == 0) tc::tmem_alloc(&tmem_base, TC_TMEM_COLS);
@@ -83,8 +83,8 @@ lu_update_tc_kernel(int mp, int rest, int ntile, int ntile_max, float* __restric
     const uint32_t tbase = tmem_base;
 
     if (threadIdx.x == 0) {
-        const unsigned char* ga = apack + ((size_t)k * ntile_max + ti) * Cfg::A_BYTES;
-        const unsigned char* gb = bpack + ((size_t)k * ntile_max + tj) * Cfg::B_BYTES;
+        const unsigned char* ga = apack + (size_t)ti * Cfg::A_BYTES;
+        const unsigned char* gb = bpack + (size_t)tj * Cfg::B_BYTES;
         tc::mbar_arrive_expect_tx(&bar_load, Cfg::A_BYTES + Cfg::B_BYTES);
         tc::bulk_g2s(sA, ga, Cfg::A_BYTES, &bar_load);
         tc::bulk_g2s(sB, gb, Cfg::B_BYTES, &bar_load);
@@ -118,7 +118,7 @@ lu_update_tc_kernel(int mp, int rest, int ntile, int ntile_max, float* __restric
     if (ok && mma_done) {
         const int r = rest + ti * TC_BM + warp * 32 + lane;
         const uint32_t lane_addr = tbase + ((uint32_t)(warp * 32) << 16);
-        float* re = fac + (size_t)k * 2 * mp * mp;
+        float* re = re_plane;
         float* im = re + (size_t)mp * mp;
 #pragma unroll 1
         for (int ch = 0; ch < TC_BN / 16; ++ch) {
@@ -146,6 +146,33 @@ lu_update_tc_kernel(int mp, int rest, int ntile, int ntile_max, float* __restric
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tbase, TC_TMEM_COLS);
+}
+
+// grid: (ntile * ntile, nblk)
+template <int KIND>
+__global__ void __launch_bounds__(128)
+lu_update_tc_kernel(int mp, int rest, int ntile, int ntile_max, float* __restrict__ fac,
+                    const unsigned char* __restrict__ apack, const unsigned char* __restrict__ bpack,
+                    int* __restrict__ err) {
+    using Cfg = TcCfg<KIND>;
+    const int k = blockIdx.y;
+    tc_update_body<KIND>(mp, rest, fac + (size_t)k * 2 * mp * mp, apack + (size_t)k * ntile_max * Cfg::A_BYTES,
+                         bpack + (size_t)k * ntile_max * Cfg::B_BYTES, err, blockIdx.x / ntile, blockIdx.x % ntile);
+}
+
+// Batched over the block table: grid (ntile_grid^2, blocks); tiles outside a
+// smaller block's trailing matrix exit at once.
+template <int KIND>
+__global__ void __launch_bounds__(128)
+lu_update_tc_batched(const BlkDev* __restrict__ B, int p, int nb, int ntile_grid, int* __restrict__ err) {
+    const BlkDev& d = B[blockIdx.y];
+    const int rest = (p + 1) * nb;
+    const int rem = d.mp - rest;
+    if (rem <= 0) return;
+    const int nt = (rem + TC_BM - 1) / TC_BM;
+    const int ti = blockIdx.x / ntile_grid, tj = blockIdx.x % ntile_grid;
+    if (ti >= nt || tj >= nt) return;
+    tc_update_body<KIND>(d.mp, rest, (float*)d.fac, d.apack, d.bpack, err, ti, tj);
 }
 
 }  // namespace fde

@@ -14,17 +14,16 @@
 namespace fde {
 
 template <typename T, int MODE>
-__global__ void __launch_bounds__(1024)
-st_matvec_kernel(int m, int logL, int mu, double h, const int* __restrict__ start, const double* __restrict__ A,
-                 const double* __restrict__ B, const double* __restrict__ dplus, const double* __restrict__ dminus,
-                 const cplx_t<T>* __restrict__ sym, const cplx_t<T>* __restrict__ tw, const double* __restrict__ z,
-                 double* __restrict__ y) {
+__device__ __forceinline__ void matvec_body(int m, int logL, int mu, double h, const int* __restrict__ start,
+                                            const double* __restrict__ A, const double* __restrict__ B,
+                                            const double* __restrict__ dplus, const double* __restrict__ dminus,
+                                            const cplx_t<T>* __restrict__ sym, const cplx_t<T>* __restrict__ tw,
+                                            const double* __restrict__ z, double* __restrict__ y, int row) {
     using C = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int L = 1 << logL;
     C* buf = reinterpret_cast<C*>(smem_raw);
-    double* ubuf = reinterpret_cast<double*>(buf + L);
-    const int row = blockIdx.x;  // reduced time row: unknown u_{row+1}
+    double* ubuf = reinterpret_cast<double*>(buf + L);  // row = reduced time row: unknown u_{row+1}
 
     double ca[FDE_MAX_MU + 1], cb[FDE_MAX_MU + 1];
     int st = 0;
@@ -72,6 +71,40 @@ st_matvec_kernel(int m, int logL, int mu, double h, const int* __restrict__ star
         else
             y[(size_t)row * m + i] = jz;
     }
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(1024)
+st_matvec_kernel(int m, int logL, int mu, double h, const int* __restrict__ start, const double* __restrict__ A,
+                 const double* __restrict__ B, const double* __restrict__ dplus, const double* __restrict__ dminus,
+                 const cplx_t<T>* __restrict__ sym, const cplx_t<T>* __restrict__ tw, const double* __restrict__ z,
+                 double* __restrict__ y) {
+    matvec_body<T, MODE>(m, logL, mu, h, start, A, B, dplus, dminus, sym, tw, z, y, blockIdx.x);
+}
+
+// Batched M z over the active instances: grid (max s, active count).
+// which = 0: z = Z_j, y = V_{j+1} (Arnoldi step); which = 1: z = x, y = work (residual).
+__global__ void __launch_bounds__(1024)
+st_matvec_batched(const InstDev* __restrict__ I, const int* __restrict__ act, int which, int j) {
+    const InstDev& d = I[act[blockIdx.y]];
+    if ((int)blockIdx.x >= d.s) return;
+    const double* z = which == 0 ? d.Z + (size_t)j * d.n : d.x;
+    double* y = which == 0 ? d.V + (size_t)(j + 1) * d.n : d.work;
+    matvec_body<double, 0>(d.m, d.logL, d.mu, d.h, d.start, d.A, d.B, d.dplus, d.dminus, d.sym, d.twL, z, y,
+                           blockIdx.x);
+}
+
+int launch_matvec_batched(const InstDev* I, const int* act, int nact, int max_s, int max_L, int max_m, int which,
+                          int j, cudaStream_t st) {
+    if (nact <= 0) return FDE_OK;
+    const size_t smem = (size_t)max_L * sizeof(double2) + (size_t)max_m * sizeof(double);
+    int threads = max_L / 2;
+    if (threads > 1024) threads = 1024;
+    if (threads < 64) threads = 64;
+    FDE_CUDA_TRY(cudaFuncSetAttribute(st_matvec_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    st_matvec_batched<<<dim3(max_s, nact), threads, smem, st>>>(I, act, which, j);
+    FDE_LAUNCH_CHECK("st_matvec_batched");
+    return FDE_OK;
 }
 
 template <int MODE>

@@ -16,14 +16,13 @@ constexpr int XW = 16;      // spatial indices per CTA
 constexpr int NCOL = XW / 2; // packed complex columns per CTA
 
 template <typename T>
-__global__ void __launch_bounds__(256)
-time_fft_fwd_kernel(int m, int mp, int logs, const double* __restrict__ r, const cplx_t<T>* __restrict__ tw,
-                    cplx_t<T>* __restrict__ rhat) {
+__device__ __forceinline__ void fwd_body(int m, int mp, int logs, const double* __restrict__ r,
+                                         const cplx_t<T>* __restrict__ tw, cplx_t<T>* __restrict__ rhat, int bx) {
     using C = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf = reinterpret_cast<C*>(smem_raw);  // NCOL columns of length s
     const int s = 1 << logs;
-    const int x0 = blockIdx.x * XW;
+    const int x0 = bx * XW;
     for (int e = threadIdx.x; e < s * XW; e += blockDim.x) {
         const int t = e / XW;
         const int xx = e - t * XW;
@@ -52,13 +51,19 @@ time_fft_fwd_kernel(int m, int mp, int logs, const double* __restrict__ r, const
 
 template <typename T>
 __global__ void __launch_bounds__(256)
-time_fft_inv_kernel(int m, int mp, int logs, const cplx_t<T>* __restrict__ xhat, const cplx_t<T>* __restrict__ tw,
-                    double* __restrict__ z) {
+time_fft_fwd_kernel(int m, int mp, int logs, const double* __restrict__ r, const cplx_t<T>* __restrict__ tw,
+                    cplx_t<T>* __restrict__ rhat) {
+    fwd_body<T>(m, mp, logs, r, tw, rhat, blockIdx.x);
+}
+
+template <typename T>
+__device__ __forceinline__ void inv_body(int m, int mp, int logs, const cplx_t<T>* __restrict__ xhat,
+                                         const cplx_t<T>* __restrict__ tw, double* __restrict__ z, int bx) {
     using C = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf = reinterpret_cast<C*>(smem_raw);
     const int s = 1 << logs;
-    const int x0 = blockIdx.x * XW;
+    const int x0 = bx * XW;
     const int nk = s / 2 + 1;
     for (int e = threadIdx.x; e < nk * NCOL; e += blockDim.x) {
         const int k = e / NCOL;
@@ -86,6 +91,52 @@ time_fft_inv_kernel(int m, int mp, int logs, const cplx_t<T>* __restrict__ xhat,
             z[(size_t)t * m + x] = (double)src[xx & 1] * inv;
         }
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+time_fft_inv_kernel(int m, int mp, int logs, const cplx_t<T>* __restrict__ xhat, const cplx_t<T>* __restrict__ tw,
+                    double* __restrict__ z) {
+    inv_body<T>(m, mp, logs, xhat, tw, z, blockIdx.x);
+}
+
+// Batched over the active instances act[]: grid (max x-tiles, active count), FP32
+// transforms (the batched path uses FP32/TF32/BF16 preconditioners).  The forward
+// transform reads the Krylov vector V_j, the inverse one writes Z_j.
+__global__ void __launch_bounds__(256)
+time_fft_fwd_batched(const InstDev* __restrict__ I, const int* __restrict__ act, int j) {
+    const InstDev& d = I[act[blockIdx.y]];
+    if ((int)blockIdx.x * XW >= d.mp) return;
+    fwd_body<float>(d.m, d.mp, d.logs, d.V + (size_t)j * d.n, d.tws32, (float2*)d.rhat, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(256)
+time_fft_inv_batched(const InstDev* __restrict__ I, const int* __restrict__ act, int j) {
+    const InstDev& d = I[act[blockIdx.y]];
+    if ((int)blockIdx.x * XW >= d.mp) return;
+    inv_body<float>(d.m, d.mp, d.logs, (const float2*)d.rhat, d.tws32, d.Z + (size_t)j * d.n, blockIdx.x);
+}
+
+int launch_time_fft_batched(const InstDev* I, const int* act, int nact, int max_mp, int max_s, int j,
+                            cudaStream_t st) {
+    if (nact <= 0) return FDE_OK;
+    const dim3 grid((max_mp + XW - 1) / XW, nact);
+    const size_t smem = (size_t)NCOL * max_s * sizeof(float2);
+    FDE_CUDA_TRY(cudaFuncSetAttribute(time_fft_fwd_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    time_fft_fwd_batched<<<grid, 256, smem, st>>>(I, act, j);
+    FDE_LAUNCH_CHECK("time_fft_fwd_batched");
+    return FDE_OK;
+}
+
+int launch_time_ifft_batched(const InstDev* I, const int* act, int nact, int max_mp, int max_s, int j,
+                             cudaStream_t st) {
+    if (nact <= 0) return FDE_OK;
+    const dim3 grid((max_mp + XW - 1) / XW, nact);
+    const size_t smem = (size_t)NCOL * max_s * sizeof(float2);
+    FDE_CUDA_TRY(cudaFuncSetAttribute(time_fft_inv_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    time_fft_inv_batched<<<grid, 256, smem, st>>>(I, act, j);
+    FDE_LAUNCH_CHECK("time_fft_inv_batched");
+    return FDE_OK;
 }
 
 int launch_time_fft_fwd(const Problem& P, const double* r, void* rhat, int prec, cudaStream_t st) {

@@ -22,7 +22,7 @@ def lib():
 def _declared_functions():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    names = re.findall(r"^\s*(?:int|void|long long|const char\*)\s+\**(\w+)\s*\(", text, flags=re.M)
+    names = re.findall(r"^\s*(?:int|void|long long|const char\*|fde_problem\*)\s+\**(\w+)\s*\(", text, flags=re.M)
     return sorted(set(names))
 
 

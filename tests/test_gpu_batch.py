@@ -1,0 +1,99 @@
+"""Batched solves (fde_batch_*) against the FP64 oracle.
+
+Every instance of a batch must match the oracle's solution of its own system to
+rel.err <= 1e-8 (the same bar as single solves), whatever the other instances
+are.  The batch mixes m (ragged sizes included), s, alpha, d and BVM schemes so
+that the block table, the LU step prefixes and the per-instance convergence
+masks are all exercised.  At the full 64-instance workload the check is the true
+residual of every instance under the oracle's own Kronecker matvec.
+"""
+import numpy as np
+import pytest
+
+import fde_inputs as fi
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+
+
+def _mixed_batch():
+    probs = [
+        fi.config_small(),
+        fi.random_modes(100, 16, "GAM4", seed=fi.instance_seed(1)),
+        fi.random_modes(37, 32, "ETR3", seed=fi.instance_seed(2), random_u0=True),
+        fi.manufactured(130, 64, 1.8, "GBDF5", dplus_fn=lambda x: 1 + x, dminus_fn=lambda x: 2 - x),
+        fi.random_modes(255, 16, "GBDF3", seed=fi.instance_seed(3)),
+        fi.random_modes(1, 8, "GBDF1", seed=fi.instance_seed(4)),
+    ]
+    return probs
+
+
+def _reference(prob):
+    if prob.n <= 5000:
+        return O.direct_solve(prob)
+    x, _, ok, _ = O.solve_strang_gmres(prob, side="right", tol=1e-12)
+    assert ok
+    return x
+
+
+@pytest.mark.parametrize("precision", ["fp32", "tf32", "bf16"])
+def test_batch_matches_oracle(precision):
+    from paper_1305_6653_gb300 import FDEBatch
+    probs = _mixed_batch()
+    with FDEBatch(probs) as b:
+        b.assemble().factor(precision)
+        xs, stats = b.solve(tol=1e-11, restart=20, maxit=400)
+        xs = [x.cpu().numpy() for x in xs]
+    for prob, x, st in zip(probs, xs, stats):
+        ref = _reference(prob)
+        err = np.linalg.norm(x - ref) / np.linalg.norm(ref)
+        assert st["status"] == 0, (prob.name, st)
+        assert err <= 1e-8, (prob.name, err, st)
+        assert st["iterations"] <= 2 * prob.m * prob.mu + 1  # Theorem 3.3 bound
+
+
+def test_batch_iterations_match_single_solves():
+    from paper_1305_6653_gb300 import FDEBatch, FDEProblem
+    probs = _mixed_batch()
+    with FDEBatch(probs) as b:
+        b.assemble().factor("fp32")
+        _, stats = b.solve(tol=1e-10)
+    for prob, st in zip(probs, stats):
+        with FDEProblem.from_inputs(prob) as p:
+            p.assemble().factor("fp32")
+            _, s1 = p.solve(tol=1e-10)
+        # same kernels per instance; only the reduction split of the dot products differs
+        assert abs(st["iterations"] - s1["iterations"]) <= 2, (prob.name, st, s1)
+
+
+def test_batch_reports_per_instance_status():
+    from paper_1305_6653_gb300 import FDEBatch, _lib
+    probs = _mixed_batch()[:3]
+    with FDEBatch(probs) as b:
+        b.assemble().factor("fp32")
+        _, stats = b.solve(tol=1e-14, maxit=2, raise_on_error=False)
+    assert all(st["status"] == _lib.FDE_ERR_NOT_CONVERGED and st["iterations"] == 2 for st in stats)
+
+
+def test_batch_full_workload_residuals():
+    """The 64-instance workload (m in {255..2047}, s in {64,128,256}, ETR3 / GBDF3 /
+    GAM4): every instance's true residual under the oracle's matvec."""
+    from paper_1305_6653_gb300 import FDEBatch
+    probs = fi.config_batch()
+    with FDEBatch(probs) as b:
+        b.assemble().factor("tf32")
+        xs, stats = b.solve(tol=1e-10, restart=20, maxit=400)
+        xs = [x.cpu().numpy() for x in xs]
+    for prob, x, st in zip(probs, xs, stats):
+        assert st["status"] == 0, (prob.name, st)
+        bb = O.reduced_rhs(prob)
+        res = np.linalg.norm(bb - O.matvec(prob, x)) / np.linalg.norm(bb)
+        assert res <= 2e-10, (prob.name, res)
