@@ -46,8 +46,12 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
-    ap.add_argument("--config", choices=["scale", "batch"], default="scale",
-                    help="scale: one m=2047/s=256 instance per step; batch: 64 uneven instances per step")
+    ap.add_argument("--config", choices=["scale", "batch", "learned"], default="scale",
+                    help="scale: one m=2047/s=256 instance per step; batch: 64 uneven instances per step; "
+                         "learned: train the warm-start operator on m=1023/s=256 solves, then compare guesses")
+    ap.add_argument("--train", type=int, default=4096, help="learned: method-generated training solves")
+    ap.add_argument("--epochs", type=int, default=6, help="learned: passes over the training set")
+    ap.add_argument("--eval", type=int, default=32, help="learned: held-out instances")
     return ap.parse_args()
 
 
@@ -280,6 +284,86 @@ def bench_batch(args, world, rank, local_rank):
 
 
 # ---------------------------------------------------------------------------
+# learned warm start: train on method-generated solves, compare initial guesses
+# ---------------------------------------------------------------------------
+
+def bench_learned(args, world, rank, local_rank):
+    import numpy as np
+    import torch
+
+    import fde_inputs
+    import paper_1305_6653_gb300 as fde
+
+    torch.cuda.set_device(local_rank)
+    m, s = 1023, 256
+    net = fde.FDENop(m, s, width=64, layers=6, ksize=5, seed=1305)
+    X = torch.empty((args.train, net.cin * m), dtype=torch.float32, device="cuda")
+    Y = torch.empty((args.train, s * m), dtype=torch.float32, device="cuda")
+    t0 = time.perf_counter()
+    its_train = []
+    for c0 in range(0, args.train, 64):
+        chunk = [fde_inputs.config_learned_family(seed=i, m=m, s=s) for i in range(c0, min(c0 + 64, args.train))]
+        with fde.FDEBatch(chunk) as b:
+            b.assemble().factor(args.precision)
+            xs, st = b.solve(tol=args.tol)
+            its_train += [x_["iterations"] for x_ in st]
+            for i, x in enumerate(xs):
+                net.features(b.problem(i), X[c0 + i])
+                Y[c0 + i].copy_(x)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t0
+    B = 32
+    steps = args.epochs * (args.train // B)
+    t0 = time.perf_counter()
+    loss = None
+    for step in range(steps):
+        i0 = (step * B) % (args.train - B + 1)
+        lr = 2e-3 if step < 0.6 * steps else (6e-4 if step < 0.85 * steps else 2e-4)
+        loss, _ = net.loss_grad(X[i0:i0 + B].reshape(-1), Y[i0:i0 + B].reshape(-1), B)
+        net.adam_step(lr)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    res = {"zero": {"its": [], "ms": []}, "learned": {"its": [], "ms": [], "rejected": 0}}
+    x0 = torch.empty(s * m, dtype=torch.float64, device="cuda")
+    for k in range(args.eval):
+        prob = fde_inputs.config_learned_family(seed=10**6 + k, m=m, s=s)
+        with fde.FDEProblem.from_inputs(prob, device_inputs=True) as p:
+            for mode in ("zero", "learned"):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                p.assemble().factor(args.precision)
+                if mode == "learned":
+                    net.warm_start(p.h, x0)
+                    _, st = p.solve(tol=args.tol, x0=x0)
+                    res[mode]["rejected"] += st["x0_rejected"]
+                else:
+                    _, st = p.solve(tol=args.tol)
+                e1.record()
+                e1.synchronize()
+                res[mode]["its"].append(st["iterations"])
+                res[mode]["ms"].append(e0.elapsed_time(e1))
+    out = {}
+    for mode in ("zero", "learned"):
+        ms = float(np.mean(res[mode]["ms"]))
+        out[mode] = {"solves_per_s": 1e3 / ms, "mean_iterations": float(np.mean(res[mode]["its"])),
+                     "iterations": res[mode]["its"], "ms_per_solve": ms}
+    out["learned"]["x0_rejected"] = res["learned"]["rejected"]
+    if rank == 0:
+        line = {"metric": METRIC, "value": out["learned"]["solves_per_s"], "unit": "solves/s", "n_gpus": world,
+                "steps": args.eval, "warmup": 0, "ms_per_step": out["learned"]["ms_per_solve"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64+f16",
+                "data": "synthetic",
+                "config": {"workload": "learned_family_m1023_s256_gbdf3", "train_solves": args.train,
+                           "epochs": args.epochs, "batch": B, "network": "6 conv1d layers, width 64, kernel 5",
+                           "precision": args.precision, "tol_true_residual": args.tol},
+                "training": {"data_gen_s": t_gen, "train_s": t_train, "final_loss": loss, "steps": steps,
+                             "mean_train_iterations": float(np.mean(its_train))},
+                "zero_x0": out["zero"], "learned_x0": out["learned"]}
+        print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------
 # main
 # ---------------------------------------------------------------------------
 
@@ -293,6 +377,8 @@ def main():
 
     if args.config == "batch" and args.impl == "ours":
         return bench_batch(args, world, rank, local_rank)
+    if args.config == "learned" and args.impl == "ours":
+        return bench_learned(args, world, rank, local_rank)
     prob = fde_inputs.config_scale(args.m, args.s)
     workload = {"workload": f"scale_m{args.m}_s{args.s}_gbdf5_alpha1.8_variable_d", "m": args.m, "s": args.s,
                 "unknowns": args.m * args.s, "scheme": "GBDF5", "alpha": 1.8, "d": "d+=1+x, d-=2-x",

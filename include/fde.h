@@ -107,6 +107,8 @@ typedef struct {
     double rel_residual; /* final ||b - M x|| / ||b|| (FP64, recomputed) */
     double rel_residual_estimate; /* final Givens estimate of the last cycle */
     double ms_solve;     /* device time of the solve (CUDA events) */
+    int x0_rejected;     /* 1: the initial guess had ||b - M x0|| > ||b|| and x = 0 was used */
+    int reserved;
 } fde_stats;
 
 typedef struct fde_problem fde_problem;
@@ -135,7 +137,8 @@ int bvm_assemble(fde_problem* p);
 int strang_precond_factor(fde_problem* p, int precision);
 
 /* Solve M u = b by flexible GMRES(restart) right-preconditioned with S.
- * x0: device, length s*m initial guess, or NULL for zero.  x_out: device, length
+ * x0: device, length s*m initial guess, or NULL for zero; a guess whose residual
+ * exceeds ||b|| (or is not finite) is replaced by zero (stats->x0_rejected).  x_out: device, length
  * s*m (may alias x0).  st: host, may be NULL.  On FDE_ERR_NOT_CONVERGED x_out
  * holds the last iterate.  Requires strang_precond_factor.  Errors: FDE_ERR_ARG,
  * FDE_ERR_STATE, FDE_ERR_NOT_CONVERGED, FDE_ERR_NAN, FDE_ERR_CUDA. */
@@ -182,6 +185,39 @@ fde_problem* fde_batch_problem(fde_batch* b, int i);
 
 /* Release the batch and all its instances.  NULL is ignored. */
 void fde_batch_destroy(fde_batch* b);
+
+/* ---- learned warm start ----------------------------------------------------
+ * A 1-D convolutional neural operator over x (the paper has no counterpart): its
+ * input channels for one problem are u0(x_i), f(x_i, t_n) for n = 0..s, and the
+ * normalised (alpha - 1.5)/0.4, (d+(x_i) - 1.25)/0.75, (d-(x_i) - 1.25)/0.75 (s+5
+ * channels); its s output channels are u_1..u_s(x_i) -- a space-time initial guess
+ * for pgmres_solve.  Layers: `layers` convolutions of odd size `ksize` (<= 7),
+ * zero padding, width `width`, ReLU after all but the last.  Parameters (FP32,
+ * flat, per layer W (C_out, C_in, K) then b (C_out)) are initialised He-uniform
+ * from `seed` with a counter-based splitmix64 generator.  Activations are
+ * [batch][channel][x] float arrays on the device. */
+typedef struct fde_nop fde_nop;
+int fde_nop_create(int m, int s, int width, int layers, int ksize, unsigned long long seed, void* stream,
+                   fde_nop** out);
+long long fde_nop_num_params(const fde_nop* n);
+int fde_nop_in_channels(const fde_nop* n);
+/* Copy the flat parameter vector from / to host memory. */
+int fde_nop_set_params(fde_nop* n, const float* params);
+int fde_nop_get_params(fde_nop* n, float* params);
+/* FP32 forward of `batch` samples: in (device, batch x (s+5) x m) -> out (device, batch x s x m). */
+int fde_nop_forward(fde_nop* n, const float* in, float* out, int batch);
+/* Forward, mean-squared-error loss against target (device, batch x s x m) and
+ * backpropagated gradients (kept on the device for fde_nop_adam_step; also copied
+ * to grad_host when not NULL).  *loss (host) receives the loss. */
+int fde_nop_loss_grad(fde_nop* n, const float* in, const float* target, int batch, double* loss, float* grad_host);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) with the last gradients. */
+int fde_nop_adam_step(fde_nop* n, float lr);
+/* Input channels of problem p (device, (s+5) x m); p must have the network's m and s. */
+int fde_nop_features(fde_nop* n, fde_problem* p, float* in);
+/* Predict a space-time initial guess for p (device, s*m doubles) by the FP16
+ * inference path (FP16 weights and activations, FP32 accumulation). */
+int fde_nop_warm_start(fde_nop* n, fde_problem* p, double* x0);
+void fde_nop_destroy(fde_nop* n);
 
 /* ---- step-level entry points (the same kernels the solver runs) ---------- */
 

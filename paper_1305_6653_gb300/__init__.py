@@ -17,7 +17,7 @@ from . import _lib
 from ._lib import (FDE_BF16, FDE_ETR, FDE_FP32, FDE_FP64, FDE_GAM, FDE_GBDF, FDE_TF32, FdeError,  # noqa: F401
                    FdePgmresOpts, FdeProblemDesc, FdeStats, PRECISIONS, FAMILIES)
 
-__all__ = ["FDEProblem", "FDEBatch", "fde_problem_create", "bvm_assemble", "strang_precond_factor", "pgmres_solve",
+__all__ = ["FDEProblem", "FDEBatch", "FDENop", "fde_problem_create", "bvm_assemble", "strang_precond_factor", "pgmres_solve",
            "fde_problem_destroy", "fde_matvec", "fde_precond_apply", "FdeError", "PRECISIONS"]
 
 
@@ -250,6 +250,10 @@ class FDEBatch:
             _lib.check(rc, "fde_batch_solve")
         return outs, [st.as_dict() for st in stats]
 
+    def problem(self, i):
+        """Problem handle of instance i (owned by the batch)."""
+        return C.c_void_p(_lib.load().fde_batch_problem(self.h, int(i)))
+
     def close(self):
         if getattr(self, "h", None):
             _lib.load().fde_batch_destroy(self.h)
@@ -266,3 +270,67 @@ class FDEBatch:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class FDENop:
+    """Learned warm start (fde_nop_* entry points): a 1-D convolutional neural
+    operator over x, trained and run by the library's own kernels."""
+
+    def __init__(self, m, s, width=64, layers=6, ksize=5, seed=1305, stream=None):
+        self.m, self.s = int(m), int(s)
+        self.h = C.c_void_p()
+        _lib.check(_lib.load().fde_nop_create(self.m, self.s, int(width), int(layers), int(ksize), int(seed),
+                                              _stream_handle(stream), C.byref(self.h)), "fde_nop_create")
+        self.nparam = int(_lib.load().fde_nop_num_params(self.h))
+        self.cin = int(_lib.load().fde_nop_in_channels(self.h))
+
+    def set_params(self, params):
+        import numpy as np
+        a = np.ascontiguousarray(params, dtype=np.float32)
+        assert a.size == self.nparam
+        _lib.check(_lib.load().fde_nop_set_params(self.h, C.c_void_p(a.ctypes.data)), "fde_nop_set_params")
+
+    def get_params(self):
+        import numpy as np
+        a = np.empty(self.nparam, dtype=np.float32)
+        _lib.check(_lib.load().fde_nop_get_params(self.h, C.c_void_p(a.ctypes.data)), "fde_nop_get_params")
+        return a
+
+    def forward(self, x, batch):
+        torch = _torch()
+        out = torch.empty(batch * self.s * self.m, dtype=torch.float32, device="cuda")
+        _lib.check(_lib.load().fde_nop_forward(self.h, C.c_void_p(x.data_ptr()), C.c_void_p(out.data_ptr()),
+                                                int(batch)), "fde_nop_forward")
+        return out
+
+    def loss_grad(self, x, target, batch, want_grad=False):
+        import numpy as np
+        loss = C.c_double()
+        g = np.empty(self.nparam, dtype=np.float32) if want_grad else None
+        _lib.check(_lib.load().fde_nop_loss_grad(self.h, C.c_void_p(x.data_ptr()), C.c_void_p(target.data_ptr()),
+                                                  int(batch), C.byref(loss),
+                                                  C.c_void_p(g.ctypes.data) if want_grad else None),
+                   "fde_nop_loss_grad")
+        return loss.value, g
+
+    def adam_step(self, lr):
+        _lib.check(_lib.load().fde_nop_adam_step(self.h, C.c_float(lr)), "fde_nop_adam_step")
+
+    def features(self, problem_handle, out):
+        _lib.check(_lib.load().fde_nop_features(self.h, problem_handle, C.c_void_p(out.data_ptr())),
+                   "fde_nop_features")
+
+    def warm_start(self, problem_handle, x0):
+        _lib.check(_lib.load().fde_nop_warm_start(self.h, problem_handle, C.c_void_p(x0.data_ptr())),
+                   "fde_nop_warm_start")
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.load().fde_nop_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -37,6 +37,9 @@ EXPORTED = [
     "fde_get_grunwald", "fde_problem_sizes", "fde_profile_enable", "fde_profile_read", "fde_launch_count",
     "fde_precond_apply_noalloc", "fde_batch_create", "fde_batch_assemble", "fde_batch_factor",
     "fde_batch_solve", "fde_batch_size", "fde_batch_problem", "fde_batch_destroy",
+    "fde_nop_create", "fde_nop_num_params", "fde_nop_in_channels", "fde_nop_set_params", "fde_nop_get_params",
+    "fde_nop_forward", "fde_nop_loss_grad", "fde_nop_adam_step", "fde_nop_features", "fde_nop_warm_start",
+    "fde_nop_destroy",
 ]
 STAGES = ["assemble", "form", "lu_diag", "lu_panel", "lu_update", "tfft_fwd", "trsv", "tfft_inv", "matvec",
           "krylov"]
@@ -59,6 +62,7 @@ class FdeStats(C.Structure):
     _fields_ = [
         ("status", C.c_int), ("iterations", C.c_int), ("restarts", C.c_int), ("precision", C.c_int),
         ("rel_residual", C.c_double), ("rel_residual_estimate", C.c_double), ("ms_solve", C.c_double),
+        ("x0_rejected", C.c_int), ("reserved", C.c_int),
     ]
 
     def as_dict(self) -> dict:
@@ -108,6 +112,17 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "fde_batch_size": (i32, [vp]),
         "fde_batch_problem": (vp, [vp, i32]),
         "fde_batch_destroy": (None, [vp]),
+        "fde_nop_create": (i32, [i32, i32, i32, i32, i32, C.c_ulonglong, vp, C.POINTER(vp)]),
+        "fde_nop_num_params": (C.c_longlong, [vp]),
+        "fde_nop_in_channels": (i32, [vp]),
+        "fde_nop_set_params": (i32, [vp, vp]),
+        "fde_nop_get_params": (i32, [vp, vp]),
+        "fde_nop_forward": (i32, [vp, vp, vp, i32]),
+        "fde_nop_loss_grad": (i32, [vp, vp, vp, i32, C.POINTER(f64), vp]),
+        "fde_nop_adam_step": (i32, [vp, C.c_float]),
+        "fde_nop_features": (i32, [vp, vp, vp]),
+        "fde_nop_warm_start": (i32, [vp, vp, vp]),
+        "fde_nop_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

@@ -672,6 +672,13 @@ int pgmres_solve(fde_problem* h, const fde_pgmres_opts* opts, const double* x0, 
         if (e != cudaSuccess) return finish(cuda_error(e, "copy of b"));
     }
     if ((rc = norm2(P, V, 132, &beta2, pin))) return finish(rc);
+    if (x0 && !(beta2 <= bnorm2)) {
+        // the initial guess is worse than zero (or not finite): start from x = 0
+        FDE_CUDA_TRY(cudaMemsetAsync(x, 0, n * sizeof(double), st));
+        FDE_CUDA_TRY(cudaMemcpyAsync(V, P.d_b_rhs, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        if ((rc = norm2(P, V, 132, &beta2, pin))) return finish(rc);
+        S.x0_rejected = 1;
+    }
     int its = 0;
     std::vector<double> g0(o.restart + 1, 0.0);
     double est = 0.0;

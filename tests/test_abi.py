@@ -48,7 +48,7 @@ def test_struct_layouts_match_header():
     # fde_problem_desc: 2 ints, 5 doubles, 2 pointers, 2 doubles, 2 ints, 2 pointers, 1 int (+ padding)
     assert ctypes.sizeof(_lib.FdeProblemDesc) == 8 + 40 + 16 + 16 + 8 + 16 + 8
     assert ctypes.sizeof(_lib.FdePgmresOpts) == 24
-    assert ctypes.sizeof(_lib.FdeStats) == 16 + 24
+    assert ctypes.sizeof(_lib.FdeStats) == 16 + 24 + 8
 
 
 def test_argument_validation_needs_no_gpu(lib):
