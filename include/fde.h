@@ -215,8 +215,13 @@ int fde_nop_adam_step(fde_nop* n, float lr);
 /* Input channels of problem p (device, (s+5) x m); p must have the network's m and s. */
 int fde_nop_features(fde_nop* n, fde_problem* p, float* in);
 /* Predict a space-time initial guess for p (device, s*m doubles) by the FP16
- * inference path (FP16 weights and activations, FP32 accumulation). */
+ * inference path (FP16 weights and activations, FP32 accumulation), then keep
+ * only its first `modes` grid sine modes along x per time level (see
+ * fde_nop_set_filter; default 8, the mode count of the synthetic families' data): rough
+ * components of the prediction error would be amplified by M in the residual. */
 int fde_nop_warm_start(fde_nop* n, fde_problem* p, double* x0);
+/* Number of sine modes kept by fde_nop_warm_start (0: no projection). */
+int fde_nop_set_filter(fde_nop* n, int modes);
 void fde_nop_destroy(fde_nop* n);
 
 /* ---- step-level entry points (the same kernels the solver runs) ---------- */

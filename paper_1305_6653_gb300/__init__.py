@@ -320,6 +320,9 @@ class FDENop:
         _lib.check(_lib.load().fde_nop_features(self.h, problem_handle, C.c_void_p(out.data_ptr())),
                    "fde_nop_features")
 
+    def set_filter(self, modes):
+        _lib.check(_lib.load().fde_nop_set_filter(self.h, int(modes)), "fde_nop_set_filter")
+
     def warm_start(self, problem_handle, x0):
         _lib.check(_lib.load().fde_nop_warm_start(self.h, problem_handle, C.c_void_p(x0.data_ptr())),
                    "fde_nop_warm_start")

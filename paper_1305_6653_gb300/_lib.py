@@ -39,7 +39,7 @@ EXPORTED = [
     "fde_batch_solve", "fde_batch_size", "fde_batch_problem", "fde_batch_destroy",
     "fde_nop_create", "fde_nop_num_params", "fde_nop_in_channels", "fde_nop_set_params", "fde_nop_get_params",
     "fde_nop_forward", "fde_nop_loss_grad", "fde_nop_adam_step", "fde_nop_features", "fde_nop_warm_start",
-    "fde_nop_destroy",
+    "fde_nop_destroy", "fde_nop_set_filter",
 ]
 STAGES = ["assemble", "form", "lu_diag", "lu_panel", "lu_update", "tfft_fwd", "trsv", "tfft_inv", "matvec",
           "krylov"]
@@ -123,6 +123,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "fde_nop_features": (i32, [vp, vp, vp]),
         "fde_nop_warm_start": (i32, [vp, vp, vp]),
         "fde_nop_destroy": (None, [vp]),
+        "fde_nop_set_filter": (i32, [vp, i32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

@@ -215,6 +215,30 @@ __global__ void to_double_kernel(const float* __restrict__ a, double* __restrict
         b[i] = (double)a[i];
 }
 
+// Projection of each time level onto the first `modes` grid sine modes
+// phi_j(x_i) = sqrt(2/(m+1)) sin(j pi (i+1)/(m+1)) (orthonormal on the grid): the
+// guess keeps only smooth components, whose residual under M is not amplified by
+// the fractional operator.  One CTA per time level.
+__global__ void sine_filter_kernel(const float* __restrict__ y, int m, int modes, double* __restrict__ x0) {
+    extern __shared__ double coef[];  // modes
+    const int t = blockIdx.x;
+    const float* yt = y + (size_t)t * m;
+    const double nrm = sqrt(2.0 / (double)(m + 1));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    for (int j = warp; j < modes; j += nwarp) {
+        double c = 0.0;
+        for (int i = lane; i < m; i += 32) c += (double)yt[i] * sinpi((double)(j + 1) * (i + 1) / (double)(m + 1));
+        for (int off = 16; off; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
+        if (lane == 0) coef[j] = c * nrm;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        double v = 0.0;
+        for (int j = 0; j < modes; ++j) v += coef[j] * sinpi((double)(j + 1) * (i + 1) / (double)(m + 1));
+        x0[(size_t)t * m + i] = v * nrm;
+    }
+}
+
 static int grid1(long n) {
     long g = (n + 255) / 256;
     return (int)(g > 1216 ? 1216 : (g < 1 ? 1 : g));
@@ -242,6 +266,7 @@ struct fde_nop {
     float* out1 = nullptr;           // output of one inference (s x m)
     double* d_loss = nullptr;
     double* h_loss = nullptr;        // pinned
+    int modes = 8;                   // sine modes kept in the warm start (0: no projection)
 };
 
 namespace {
@@ -470,8 +495,20 @@ int fde_nop_warm_start(fde_nop* n, fde_problem* h, double* x0) {
         if (rc) return rc;
         xh = dst;
     }
-    to_double_kernel<<<grid1((long)n->s * m), 256, 0, n->stream>>>(n->out1, x0, (long)n->s * m);
-    FDE_LAUNCH_CHECK("to_double_kernel");
+    if (n->modes > 0) {
+        const int md = std::min(n->modes, m);
+        sine_filter_kernel<<<n->s, 256, md * sizeof(double), n->stream>>>(n->out1, m, md, x0);
+        FDE_LAUNCH_CHECK("sine_filter_kernel");
+    } else {
+        to_double_kernel<<<grid1((long)n->s * m), 256, 0, n->stream>>>(n->out1, x0, (long)n->s * m);
+        FDE_LAUNCH_CHECK("to_double_kernel");
+    }
+    return FDE_OK;
+}
+
+int fde_nop_set_filter(fde_nop* n, int modes) {
+    if (!n || modes < 0) return set_error(FDE_ERR_ARG, "need a network and modes >= 0");
+    n->modes = modes;
     return FDE_OK;
 }
 

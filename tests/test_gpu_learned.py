@@ -82,10 +82,19 @@ def test_features_and_fp16_inference():
                               ((prob.dplus - 1.25) / 0.75)[None], ((prob.dminus - 1.25) / 0.75)[None]])
         np.testing.assert_allclose(f, ref.astype(np.float32), rtol=0, atol=0)
         x0 = torch.empty(prob.n, dtype=torch.float64, device="cuda")
+        net.set_filter(0)
         net.warm_start(p.h, x0)
         y32 = net.forward(feat, 1).cpu().numpy()
         y16 = x0.cpu().numpy()
         assert np.abs(y16 - y32).max() <= 1e-2 * max(np.abs(y32).max(), 1e-3)
+        # with the sine projection: the orthogonal projection of the FP16 prediction
+        net.set_filter(8)
+        net.warm_start(p.h, x0)
+        i = np.arange(1, prob.m + 1)
+        Phi = np.sqrt(2.0 / (prob.m + 1)) * np.sin(np.pi * np.outer(np.arange(1, 9), i) / (prob.m + 1))
+        proj = (y16.reshape(prob.s, prob.m) @ Phi.T) @ Phi
+        np.testing.assert_allclose(x0.cpu().numpy().reshape(prob.s, prob.m), proj, rtol=0,
+                                   atol=1e-9 * max(np.abs(proj).max(), 1e-3))
 
 
 def _dataset(net, probs, precision="fp32"):
@@ -115,10 +124,10 @@ def test_trained_warm_start_saves_iterations():
     train = [fi.config_learned_family(seed=i, m=m, s=s) for i in range(256)]
     X, Y = _dataset(net, train)
     B = 32
-    for step in range(600):
+    for step in range(1500):
         i0 = (step * B) % len(train)
         loss, _ = net.loss_grad(X[i0:i0 + B].reshape(-1), Y[i0:i0 + B].reshape(-1), B)
-        net.adam_step(3e-3 if step < 400 else 1e-3)
+        net.adam_step(3e-3 if step < 900 else (1e-3 if step < 1300 else 3e-4))
     zero_its, warm_its = [], []
     for seed in range(10**6, 10**6 + 12):
         prob = fi.config_learned_family(seed=seed, m=m, s=s)
@@ -132,6 +141,7 @@ def test_trained_warm_start_saves_iterations():
             xs = x.cpu().numpy()
         assert st1["status"] == 0
         assert np.linalg.norm(xs - ref) / np.linalg.norm(ref) <= 1e-8
+        assert st1["x0_rejected"] == 0
         zero_its.append(st0["iterations"])
         warm_its.append(st1["iterations"])
     assert np.mean(warm_its) < np.mean(zero_its), (zero_its, warm_its, loss)
