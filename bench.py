@@ -50,7 +50,7 @@ def parse():
                     help="scale: one m=2047/s=256 instance per step; batch: 64 uneven instances per step; "
                          "learned: train the warm-start operator on m=1023/s=256 solves, then compare guesses")
     ap.add_argument("--train", type=int, default=4096, help="learned: method-generated training solves")
-    ap.add_argument("--epochs", type=int, default=6, help="learned: passes over the training set")
+    ap.add_argument("--epochs", type=int, default=40, help="learned: passes over the training set")
     ap.add_argument("--eval", type=int, default=32, help="learned: held-out instances")
     return ap.parse_args()
 
@@ -295,10 +295,10 @@ def bench_learned(args, world, rank, local_rank):
     import paper_1305_6653_gb300 as fde
 
     torch.cuda.set_device(local_rank)
-    m, s = 1023, 256
-    net = fde.FDENop(m, s, width=64, layers=6, ksize=5, seed=1305)
-    X = torch.empty((args.train, net.cin * m), dtype=torch.float32, device="cuda")
-    Y = torch.empty((args.train, s * m), dtype=torch.float32, device="cuda")
+    m, s, modes = 1023, 256, 16
+    net = fde.FDENop(m, s, modes=modes, width=64, layers=6, ksize=5, seed=1305)
+    X = torch.empty((args.train, net.cin * modes), dtype=torch.float32, device="cuda")
+    Y = torch.empty((args.train, s * modes), dtype=torch.float32, device="cuda")
     t0 = time.perf_counter()
     its_train = []
     for c0 in range(0, args.train, 64):
@@ -309,7 +309,7 @@ def bench_learned(args, world, rank, local_rank):
             its_train += [x_["iterations"] for x_ in st]
             for i, x in enumerate(xs):
                 net.features(b.problem(i), X[c0 + i])
-                Y[c0 + i].copy_(x)
+                net.coefficients(x, Y[c0 + i])
     torch.cuda.synchronize()
     t_gen = time.perf_counter() - t0
     B = 32
@@ -355,7 +355,8 @@ def bench_learned(args, world, rank, local_rank):
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64+f16",
                 "data": "synthetic",
                 "config": {"workload": "learned_family_m1023_s256_gbdf3", "train_solves": args.train,
-                           "epochs": args.epochs, "batch": B, "network": "6 conv1d layers, width 64, kernel 5",
+                           "epochs": args.epochs, "batch": B,
+                           "network": "6 conv1d layers along 16 sine modes, width 64, kernel 5",
                            "precision": args.precision, "tol_true_residual": args.tol},
                 "training": {"data_gen_s": t_gen, "train_s": t_train, "final_loss": loss, "steps": steps,
                              "mean_train_iterations": float(np.mean(its_train))},

@@ -187,41 +187,41 @@ fde_problem* fde_batch_problem(fde_batch* b, int i);
 void fde_batch_destroy(fde_batch* b);
 
 /* ---- learned warm start ----------------------------------------------------
- * A 1-D convolutional neural operator over x (the paper has no counterpart): its
- * input channels for one problem are u0(x_i), f(x_i, t_n) for n = 0..s, and the
- * normalised (alpha - 1.5)/0.4, (d+(x_i) - 1.25)/0.75, (d-(x_i) - 1.25)/0.75 (s+5
- * channels); its s output channels are u_1..u_s(x_i) -- a space-time initial guess
- * for pgmres_solve.  Layers: `layers` convolutions of odd size `ksize` (<= 7),
- * zero padding, width `width`, ReLU after all but the last.  Parameters (FP32,
- * flat, per layer W (C_out, C_in, K) then b (C_out)) are initialised He-uniform
- * from `seed` with a counter-based splitmix64 generator.  Activations are
- * [batch][channel][x] float arrays on the device. */
+ * A 1-D convolutional neural operator (the paper has no counterpart) that predicts
+ * a space-time initial guess for pgmres_solve.  It works in the grid sine basis
+ * phi_j(x_i) = sqrt(2/(m+1)) sin(j pi i/(m+1)), j = 1..modes: the convolution runs
+ * along the mode index over s+6 input channels [<u0,phi_j>, <f(.,t_n),phi_j> for
+ * n = 0..s, (alpha-1.5)/0.4, (mean d+ - 1.25)/0.75, (mean d- - 1.25)/0.75, j/modes]
+ * and its s output channels are the sine coefficients of u_1..u_s.  Layers:
+ * `layers` convolutions of odd size `ksize` (<= 7), zero padding, width `width`,
+ * ReLU after all but the last.  Parameters (FP32, flat, per layer W (C_out, C_in,
+ * K) then b (C_out)) start He-uniform from `seed` (counter-based splitmix64).
+ * Activations are [batch][channel][mode] float arrays on the device. */
 typedef struct fde_nop fde_nop;
-int fde_nop_create(int m, int s, int width, int layers, int ksize, unsigned long long seed, void* stream,
+int fde_nop_create(int m, int s, int modes, int width, int layers, int ksize, unsigned long long seed, void* stream,
                    fde_nop** out);
 long long fde_nop_num_params(const fde_nop* n);
 int fde_nop_in_channels(const fde_nop* n);
 /* Copy the flat parameter vector from / to host memory. */
 int fde_nop_set_params(fde_nop* n, const float* params);
 int fde_nop_get_params(fde_nop* n, float* params);
-/* FP32 forward of `batch` samples: in (device, batch x (s+5) x m) -> out (device, batch x s x m). */
+/* FP32 forward of `batch` samples: in (device, batch x (s+6) x modes) -> out (device, batch x s x modes). */
 int fde_nop_forward(fde_nop* n, const float* in, float* out, int batch);
-/* Forward, mean-squared-error loss against target (device, batch x s x m) and
+/* Forward, mean-squared-error loss against target (device, batch x s x modes) and
  * backpropagated gradients (kept on the device for fde_nop_adam_step; also copied
  * to grad_host when not NULL).  *loss (host) receives the loss. */
 int fde_nop_loss_grad(fde_nop* n, const float* in, const float* target, int batch, double* loss, float* grad_host);
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) with the last gradients. */
 int fde_nop_adam_step(fde_nop* n, float lr);
-/* Input channels of problem p (device, (s+5) x m); p must have the network's m and s. */
+/* Input channels of problem p (device, (s+6) x modes); p must have the network's m and s. */
 int fde_nop_features(fde_nop* n, fde_problem* p, float* in);
-/* Predict a space-time initial guess for p (device, s*m doubles) by the FP16
- * inference path (FP16 weights and activations, FP32 accumulation), then keep
- * only its first `modes` grid sine modes along x per time level (see
- * fde_nop_set_filter; default 8, the mode count of the synthetic families' data): rough
- * components of the prediction error would be amplified by M in the residual. */
+/* Sine coefficients (device, s x modes) of a space-time vector x (device, s*m): training targets. */
+int fde_nop_coefficients(fde_nop* n, const double* x, float* coef);
+/* Space-time vector x (device, s*m) from sine coefficients (device, s x modes). */
+int fde_nop_synthesize(fde_nop* n, const float* coef, double* x);
+/* Predict the initial guess for p (device, s*m doubles): features, FP16 inference
+ * (FP16 weights and activations, FP32 accumulation), synthesis on the grid. */
 int fde_nop_warm_start(fde_nop* n, fde_problem* p, double* x0);
-/* Number of sine modes kept by fde_nop_warm_start (0: no projection). */
-int fde_nop_set_filter(fde_nop* n, int modes);
 void fde_nop_destroy(fde_nop* n);
 
 /* ---- step-level entry points (the same kernels the solver runs) ---------- */

@@ -274,13 +274,13 @@ class FDEBatch:
 
 class FDENop:
     """Learned warm start (fde_nop_* entry points): a 1-D convolutional neural
-    operator over x, trained and run by the library's own kernels."""
+    operator along the sine-mode axis, trained and run by the library's own kernels."""
 
-    def __init__(self, m, s, width=64, layers=6, ksize=5, seed=1305, stream=None):
-        self.m, self.s = int(m), int(s)
+    def __init__(self, m, s, modes=16, width=64, layers=6, ksize=5, seed=1305, stream=None):
+        self.m, self.s, self.modes = int(m), int(s), int(modes)
         self.h = C.c_void_p()
-        _lib.check(_lib.load().fde_nop_create(self.m, self.s, int(width), int(layers), int(ksize), int(seed),
-                                              _stream_handle(stream), C.byref(self.h)), "fde_nop_create")
+        _lib.check(_lib.load().fde_nop_create(self.m, self.s, self.modes, int(width), int(layers), int(ksize),
+                                              int(seed), _stream_handle(stream), C.byref(self.h)), "fde_nop_create")
         self.nparam = int(_lib.load().fde_nop_num_params(self.h))
         self.cin = int(_lib.load().fde_nop_in_channels(self.h))
 
@@ -298,7 +298,7 @@ class FDENop:
 
     def forward(self, x, batch):
         torch = _torch()
-        out = torch.empty(batch * self.s * self.m, dtype=torch.float32, device="cuda")
+        out = torch.empty(batch * self.s * self.modes, dtype=torch.float32, device="cuda")
         _lib.check(_lib.load().fde_nop_forward(self.h, C.c_void_p(x.data_ptr()), C.c_void_p(out.data_ptr()),
                                                 int(batch)), "fde_nop_forward")
         return out
@@ -320,8 +320,13 @@ class FDENop:
         _lib.check(_lib.load().fde_nop_features(self.h, problem_handle, C.c_void_p(out.data_ptr())),
                    "fde_nop_features")
 
-    def set_filter(self, modes):
-        _lib.check(_lib.load().fde_nop_set_filter(self.h, int(modes)), "fde_nop_set_filter")
+    def coefficients(self, x, out):
+        _lib.check(_lib.load().fde_nop_coefficients(self.h, C.c_void_p(x.data_ptr()), C.c_void_p(out.data_ptr())),
+                   "fde_nop_coefficients")
+
+    def synthesize(self, coef, out):
+        _lib.check(_lib.load().fde_nop_synthesize(self.h, C.c_void_p(coef.data_ptr()), C.c_void_p(out.data_ptr())),
+                   "fde_nop_synthesize")
 
     def warm_start(self, problem_handle, x0):
         _lib.check(_lib.load().fde_nop_warm_start(self.h, problem_handle, C.c_void_p(x0.data_ptr())),

@@ -39,7 +39,7 @@ EXPORTED = [
     "fde_batch_solve", "fde_batch_size", "fde_batch_problem", "fde_batch_destroy",
     "fde_nop_create", "fde_nop_num_params", "fde_nop_in_channels", "fde_nop_set_params", "fde_nop_get_params",
     "fde_nop_forward", "fde_nop_loss_grad", "fde_nop_adam_step", "fde_nop_features", "fde_nop_warm_start",
-    "fde_nop_destroy", "fde_nop_set_filter",
+    "fde_nop_destroy", "fde_nop_coefficients", "fde_nop_synthesize",
 ]
 STAGES = ["assemble", "form", "lu_diag", "lu_panel", "lu_update", "tfft_fwd", "trsv", "tfft_inv", "matvec",
           "krylov"]
@@ -112,7 +112,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "fde_batch_size": (i32, [vp]),
         "fde_batch_problem": (vp, [vp, i32]),
         "fde_batch_destroy": (None, [vp]),
-        "fde_nop_create": (i32, [i32, i32, i32, i32, i32, C.c_ulonglong, vp, C.POINTER(vp)]),
+        "fde_nop_create": (i32, [i32, i32, i32, i32, i32, i32, C.c_ulonglong, vp, C.POINTER(vp)]),
         "fde_nop_num_params": (C.c_longlong, [vp]),
         "fde_nop_in_channels": (i32, [vp]),
         "fde_nop_set_params": (i32, [vp, vp]),
@@ -123,7 +123,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "fde_nop_features": (i32, [vp, vp, vp]),
         "fde_nop_warm_start": (i32, [vp, vp, vp]),
         "fde_nop_destroy": (None, [vp]),
-        "fde_nop_set_filter": (i32, [vp, i32]),
+        "fde_nop_coefficients": (i32, [vp, vp, vp]),
+        "fde_nop_synthesize": (i32, [vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

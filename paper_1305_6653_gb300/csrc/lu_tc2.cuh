@@ -1,0 +1,235 @@
+// Two-level blocked LU of the Strang blocks for the tensor-core precisions.
+//
+// Outer panels of TB = 128 columns.  Inside an outer panel the NB = 32 steps run
+// on CUDA cores restricted to the panel (diagonal LU, L21 rows over the whole
+// height, U12 columns inside the panel, rank-32 updates inside the panel), then the
+// outer row panel U12 = L11^{-1} A12 is formed by four 32-row solves and
+// rank-32 updates of the panel rows.  The outer trailing matrix then receives the
+// whole rank-128 update A22 -= L21 U12 in ONE complex GEMM with K' = 2 x 128 on
+// tcgen05 -- four times fewer passes over the trailing matrix than NB = 32.
+//
+// Complex product as one real GEMM (N' = 2 x 128 outputs side by side):
+//   A' = [Re L21 | Im L21]                                  128 rows x K' = 256
+//   B' = [[Re U12 ; -Im U12] | [Im U12 ; Re U12]]^T        256 rows x K'
+//   D  = A' B'^T:  D[:, 0:128] = Re(L21 U12),  D[:, 128:256] = Im(L21 U12).
+// The panel kernels write A' and B' pre-packed as K-chunks of 64 bytes per row,
+// each chunk in the canonical no-swizzle K-major core-matrix layout (8 rows x 16 B
+// core matrices, LBO = 128 B along K, SBO = 512 B between 8-row groups), so one
+// bulk copy lands a chunk of a tile in shared memory.
+//
+// The update kernel (one 128 x 128 complex output tile per CTA, 128 threads):
+//   * issues bulk copies of its C tile (Re and Im rows) into shared memory at
+//     once, so the read of C overlaps the whole main loop;
+//   * streams the K-chunks through a 3-stage full / empty mbarrier ring, one
+//     thread issuing the MMAs (M = 128, N = 256, accumulator in 256 TMEM columns);
+//   * subtracts D (tcgen05.ld) from the C tile in shared memory and writes the
+//     tile back with bulk copies.
+// Every mbarrier wait is bounded; on timeout the CTA records an error, waits
+// (bounded) for its own copies and MMAs, frees its TMEM and returns.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "tc_ptx.cuh"
+
+namespace fde {
+
+constexpr int TB = 128;             // outer panel width (complex K of the tensor-core update)
+constexpr int T2_BM = 128;          // output rows per CTA
+constexpr int T2_BN = 128;          // complex output columns per CTA (N' = 256)
+constexpr int T2_KP = 2 * TB;       // K' = 256 real
+constexpr int T2_STAGES = 3;
+constexpr int T2_CROW = 528;        // bytes per C-tile row in shared memory (512 + 16 pad, 16-B aligned)
+constexpr int T2_C_BYTES = T2_BM * T2_CROW;  // one plane
+
+template <int KIND>  // 0: TF32, 1: BF16
+struct Tc2 {
+    static constexpr int ESZ = KIND == 0 ? 4 : 2;
+    static constexpr int PER_CORE = 16 / ESZ;   // elements per core-matrix row
+    static constexpr int KCH = 64 / ESZ;        // elements per 64-byte K-chunk
+    static constexpr int NCH = T2_KP / KCH;     // chunks per tile
+    static constexpr int A_CHUNK = T2_BM * 64;  // bytes
+    static constexpr int B_CHUNK = 2 * T2_BN * 64;
+    static constexpr int A_TILE = NCH * A_CHUNK;
+    static constexpr int B_TILE = NCH * B_CHUNK;
+    static constexpr int STAGE = A_CHUNK + B_CHUNK;
+    static constexpr int SMEM = 2 * T2_C_BYTES + T2_STAGES * STAGE;
+    static constexpr int KSTEP = KIND == 0 ? 8 : 16;          // K per MMA = 32 bytes = 2 core matrices
+    static constexpr int MMAS = KCH / KSTEP;                  // MMAs per chunk (2)
+    static constexpr uint32_t IDESC = tc::instr_desc(KIND == 0 ? 2u : 1u, T2_BM, 2 * T2_BN);
+};
+
+// Byte offset of element (row, kp) of a packed tile whose chunks hold `rows` rows.
+template <int KIND>
+__device__ __forceinline__ uint32_t pack2_off(int rows, int row, int kp) {
+    using C = Tc2<KIND>;
+    return (uint32_t)((kp / C::KCH) * rows * 64 + (row >> 3) * 512 + ((kp % C::KCH) / C::PER_CORE) * 128 +
+                      (row & 7) * 16 + (kp % C::PER_CORE) * C::ESZ);
+}
+
+template <int KIND>
+__device__ __forceinline__ void pack2_store(unsigned char* tile, int rows, int row, int kp, float v) {
+    unsigned char* p = tile + pack2_off<KIND>(rows, row, kp);
+    if (KIND == 0)
+        *reinterpret_cast<float*>(p) = tc::to_tf32(v);
+    else
+        *reinterpret_cast<__nv_bfloat16*>(p) = __float2bfloat16_rn(v);
+}
+
+__device__ __forceinline__ void bulk_s2g(void* dst_gmem, const void* src_smem, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst_gmem),
+                 "r"(tc::smem_u32(src_smem)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Outer trailing update of one 128 x 128 complex tile (ti, tj) of one block:
+// C[r0.., c0..] -= D, r0 = R0 + 128 ti, c0 = R0 + 128 tj.
+template <int KIND>
+__device__ __forceinline__ void tc2_update_body(int mp, int R0, float* __restrict__ re_plane,
+                                                const unsigned char* __restrict__ apack,
+                                                const unsigned char* __restrict__ bpack, int* __restrict__ err, int ti,
+                                                int tj) {
+    using Cfg = Tc2<KIND>;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* sCr = smem;
+    unsigned char* sCi = smem + T2_C_BYTES;
+    unsigned char* sStage = smem + 2 * T2_C_BYTES;
+    __shared__ __align__(8) uint64_t bar_c, bar_mma, bar_full[T2_STAGES], bar_empty[T2_STAGES];
+    __shared__ uint32_t tmem_base;
+    __shared__ int ok_flag;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r0 = R0 + ti * T2_BM, c0 = R0 + tj * T2_BN;
+    const int nrows = min(T2_BM, mp - r0);
+    const int ncols = min(T2_BN, mp - c0);  // multiple of 64 (mp and R0 are)
+    const uint32_t row_bytes = (uint32_t)ncols * 4;
+    float* gre = re_plane;
+    float* gim = re_plane + (size_t)mp * mp;
+    const unsigned char* ga = apack + (size_t)ti * Cfg::A_TILE;
+    const unsigned char* gb = bpack + (size_t)tj * Cfg::B_TILE;
+
+    if (warp == 0) tc::tmem_alloc(&tmem_base, 256);
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&bar_c, 1);
+        tc::mbar_init(&bar_mma, 1);
+        for (int s = 0; s < T2_STAGES; ++s) {
+            tc::mbar_init(&bar_full[s], 1);
+            tc::mbar_init(&bar_empty[s], 1);
+        }
+        tc::fence_barrier_init();
+        ok_flag = 1;
+        // the C tile: every valid row of both planes
+        tc::mbar_arrive_expect_tx(&bar_c, 2u * (uint32_t)nrows * row_bytes);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tbase = tmem_base;
+    {
+        const int r = threadIdx.x;
+        if (r < nrows) {
+            tc::bulk_g2s(sCr + r * T2_CROW, gre + (size_t)(r0 + r) * mp + c0, row_bytes, &bar_c);
+            tc::bulk_g2s(sCi + r * T2_CROW, gim + (size_t)(r0 + r) * mp + c0, row_bytes, &bar_c);
+        }
+    }
+    if (threadIdx.x == 0) {
+        auto load_chunk = [&](int c) {
+            const int s = c % T2_STAGES;
+            unsigned char* sa = sStage + s * Cfg::STAGE;
+            tc::mbar_arrive_expect_tx(&bar_full[s], Cfg::STAGE);
+            tc::bulk_g2s(sa, ga + (size_t)c * Cfg::A_CHUNK, Cfg::A_CHUNK, &bar_full[s]);
+            tc::bulk_g2s(sa + Cfg::A_CHUNK, gb + (size_t)c * Cfg::B_CHUNK, Cfg::B_CHUNK, &bar_full[s]);
+        };
+        for (int c = 0; c < T2_STAGES - 1 && c < Cfg::NCH; ++c) load_chunk(c);
+        bool ok = true;
+        for (int c = 0; c < Cfg::NCH && ok; ++c) {
+            const int s = c % T2_STAGES;
+            if (!tc::mbar_wait(&bar_full[s], (c / T2_STAGES) & 1)) {
+                ok = false;
+                break;
+            }
+            const uint32_t a0 = tc::smem_u32(sStage + s * Cfg::STAGE);
+            const uint32_t b0 = a0 + Cfg::A_CHUNK;
+#pragma unroll
+            for (int j = 0; j < Cfg::MMAS; ++j) {
+                const uint64_t ad = tc::smem_desc(a0 + j * 256, 128, 512);
+                const uint64_t bd = tc::smem_desc(b0 + j * 256, 128, 512);
+                if (KIND == 0)
+                    tc::mma_tf32(tbase, ad, bd, Cfg::IDESC, (c > 0 || j > 0) ? 1u : 0u);
+                else
+                    tc::mma_f16(tbase, ad, bd, Cfg::IDESC, (c > 0 || j > 0) ? 1u : 0u);
+            }
+            tc::mma_commit(&bar_empty[s]);
+            // refill the stage freed by chunk c-1 with chunk c + STAGES - 1
+            const int nxt = c + T2_STAGES - 1;
+            if (nxt < Cfg::NCH) {
+                if (c >= 1) {
+                    const int sp = (c - 1) % T2_STAGES;
+                    if (!tc::mbar_wait(&bar_empty[sp], ((c - 1) / T2_STAGES) & 1)) {
+                        ok = false;
+                        break;
+                    }
+                }
+                load_chunk(nxt);
+            }
+        }
+        // bar_mma tracks every MMA this thread issued, also after a failed wait
+        tc::mma_commit(&bar_mma);
+        if (!ok) {
+            ok_flag = 0;
+            atomicCAS(err, 0, 1);
+        }
+    }
+    __syncthreads();
+    const bool ok = ok_flag != 0;
+    bool mine = false;
+    if (ok) {
+        mine = tc::mbar_wait(&bar_mma, 0) && tc::mbar_wait(&bar_c, 0);
+        if (!mine && lane == 0) atomicCAS(err, 0, 2);
+    }
+    const bool done = __syncthreads_and(mine) != 0;  // uniform across the CTA
+    tc::fence_after_sync();
+    if (ok && done) {
+        const int r = warp * 32 + lane;  // TMEM lane = tile row
+        const uint32_t lane_addr = tbase + ((uint32_t)(warp * 32) << 16);
+        float4* cr = reinterpret_cast<float4*>(sCr + r * T2_CROW);
+        float4* ci = reinterpret_cast<float4*>(sCi + r * T2_CROW);
+#pragma unroll 1
+        for (int ch = 0; ch < T2_BN / 16; ++ch) {
+            float dr[16], di[16];
+            tc::tmem_ld16(lane_addr + ch * 16, dr);
+            tc::tmem_ld16(lane_addr + T2_BN + ch * 16, di);
+            tc::tmem_ld_wait();
+            if (ch * 16 < ncols) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    float4 a = cr[ch * 4 + q], b = ci[ch * 4 + q];
+                    a.x -= dr[4 * q]; a.y -= dr[4 * q + 1]; a.z -= dr[4 * q + 2]; a.w -= dr[4 * q + 3];
+                    b.x -= di[4 * q]; b.y -= di[4 * q + 1]; b.z -= di[4 * q + 2]; b.w -= di[4 * q + 3];
+                    cr[ch * 4 + q] = a;
+                    ci[ch * 4 + q] = b;
+                }
+            }
+        }
+        fence_async_shared();
+        __syncthreads();
+        if (r < nrows) {
+            bulk_s2g(gre + (size_t)(r0 + r) * mp + c0, sCr + r * T2_CROW, row_bytes);
+            bulk_s2g(gim + (size_t)(r0 + r) * mp + c0, sCi + r * T2_CROW, row_bytes);
+            bulk_commit();
+            bulk_wait_all();
+        }
+    } else {
+        // bounded: let in-flight copies and MMAs land before TMEM is released
+        tc::mbar_wait(&bar_c, 0);
+        tc::mbar_wait(&bar_mma, 0);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tbase, 256);
+}
+
+}  // namespace fde

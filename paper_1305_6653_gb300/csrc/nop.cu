@@ -1,9 +1,13 @@
-// Learned warm start: a small 1-D convolutional neural operator over the spatial
-// index x that maps the per-point problem data of eq. (1.1) -- u0(x_i), f(x_i, t_n)
-// for n = 0..s, alpha, d+(x_i), d-(x_i) -- to the s time levels u_1..u_s(x_i), used
-// as the initial guess of the space-time GMRES solve.  The paper has no learned
-// component; the solve is still judged by its true FP64 residual, and pgmres_solve
-// falls back to the zero guess when the predicted guess is worse than zero.
+// Learned warm start: a small 1-D convolutional neural operator that maps the data
+// of eq. (1.1) -- u0, f(., t_n) for n = 0..s, alpha, d+, d- -- to a space-time
+// initial guess u_1..u_s of the GMRES solve.  It works in the grid sine basis
+// phi_j(x_i) = sqrt(2/(m+1)) sin(j pi i/(m+1)), j = 1..K: the convolution runs
+// along the mode index (length K) over channels [<u0,phi_j>, <f_n,phi_j> for
+// n = 0..s, (alpha-1.5)/0.4, (mean d+ - 1.25)/0.75, (mean d- - 1.25)/0.75, j/K], and
+// its s output channels are the sine coefficients of u_1..u_s, synthesised back
+// to the grid.  The paper has no learned component; the solve is still judged by
+// its true FP64 residual, and pgmres_solve falls back to the zero guess when the
+// predicted guess is worse than zero.
 //
 // Network: L convolution layers (kernel K, zero padding, same length), ReLU after
 // all but the last; parameters flat per layer: W (C_out, C_in, K) then b (C_out).
@@ -192,49 +196,58 @@ __global__ void to_half_kernel(const float* __restrict__ a, __half* __restrict__
         b[i] = __float2half_rn(a[i]);
 }
 
-// Input channels of one problem: u0, f(t_0..t_s), (alpha-1.5)/0.4, (d+ - 1.25)/0.75, (d- - 1.25)/0.75
-__global__ void features_kernel(int m, int s, const double* __restrict__ u0, const double* __restrict__ f,
-                                 double alpha, const double* __restrict__ dp, const double* __restrict__ dm,
-                                 float* __restrict__ in) {
-    const int C = s + 5;
-    const long total = (long)C * m;
-    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
-        const int c = (int)(e / m), x = (int)(e % m);
-        double v;
-        if (c == 0) v = u0[x];
-        else if (c <= s + 1) v = f[(size_t)(c - 1) * m + x];
-        else if (c == s + 2) v = (alpha - 1.5) / 0.4;
-        else if (c == s + 3) v = (dp[x] - 1.25) / 0.75;
-        else v = (dm[x] - 1.25) / 0.75;
-        in[e] = (float)v;
-    }
+// Sine coefficients c[r][j] = <v_r, phi_j> of `rows` grid vectors v_r (stride m):
+// one warp per (row, mode).
+__global__ void sine_analysis_kernel(const double* __restrict__ v, int rows, int m, int K, float* __restrict__ out,
+                                     int out_stride, int out_off) {
+    const int lane = threadIdx.x & 31;
+    const long w = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= (long)rows * K) return;
+    const int r = (int)(w / K), j = (int)(w % K);
+    const double* vr = v + (size_t)r * m;
+    double c = 0.0;
+    for (int i = lane; i < m; i += 32) c += vr[i] * sinpi((double)(j + 1) * (i + 1) / (double)(m + 1));
+    for (int off = 16; off; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
+    if (lane == 0) out[(size_t)(out_off + r) * out_stride + j] = (float)(c * sqrt(2.0 / (double)(m + 1)));
 }
 
-__global__ void to_double_kernel(const float* __restrict__ a, double* __restrict__ b, long n) {
-    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
-        b[i] = (double)a[i];
-}
-
-// Projection of each time level onto the first `modes` grid sine modes
-// phi_j(x_i) = sqrt(2/(m+1)) sin(j pi (i+1)/(m+1)) (orthonormal on the grid): the
-// guess keeps only smooth components, whose residual under M is not amplified by
-// the fractional operator.  One CTA per time level.
-__global__ void sine_filter_kernel(const float* __restrict__ y, int m, int modes, double* __restrict__ x0) {
-    extern __shared__ double coef[];  // modes
-    const int t = blockIdx.x;
-    const float* yt = y + (size_t)t * m;
-    const double nrm = sqrt(2.0 / (double)(m + 1));
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    for (int j = warp; j < modes; j += nwarp) {
-        double c = 0.0;
-        for (int i = lane; i < m; i += 32) c += (double)yt[i] * sinpi((double)(j + 1) * (i + 1) / (double)(m + 1));
-        for (int off = 16; off; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
-        if (lane == 0) coef[j] = c * nrm;
+// Scalar channels of the spectral input: (alpha-1.5)/0.4, mean d+, mean d- (normalised), j/K.
+__global__ void scalar_channels_kernel(int m, int K, int c0, double alpha, const double* __restrict__ dp,
+                                       const double* __restrict__ dm, float* __restrict__ in) {
+    __shared__ double sp[256], sm[256];
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        a += dp[i];
+        b += dm[i];
     }
+    sp[threadIdx.x] = a;
+    sm[threadIdx.x] = b;
     __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            sp[threadIdx.x] += sp[threadIdx.x + w];
+            sm[threadIdx.x] += sm[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    for (int j = threadIdx.x; j < K; j += blockDim.x) {
+        in[(size_t)(c0 + 0) * K + j] = (float)((alpha - 1.5) / 0.4);
+        in[(size_t)(c0 + 1) * K + j] = (float)((sp[0] / m - 1.25) / 0.75);
+        in[(size_t)(c0 + 2) * K + j] = (float)((sm[0] / m - 1.25) / 0.75);
+        in[(size_t)(c0 + 3) * K + j] = (float)(j + 1) / (float)K;
+    }
+}
+
+// x0[t][i] = sum_j c[t][j] phi_j(x_i): one CTA per time level.
+__global__ void sine_synthesis_kernel(const float* __restrict__ c, int m, int K, double* __restrict__ x0) {
+    extern __shared__ double coef[];
+    const int t = blockIdx.x;
+    for (int j = threadIdx.x; j < K; j += blockDim.x) coef[j] = (double)c[(size_t)t * K + j];
+    __syncthreads();
+    const double nrm = sqrt(2.0 / (double)(m + 1));
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
         double v = 0.0;
-        for (int j = 0; j < modes; ++j) v += coef[j] * sinpi((double)(j + 1) * (i + 1) / (double)(m + 1));
+        for (int j = 0; j < K; ++j) v += coef[j] * sinpi((double)(j + 1) * (i + 1) / (double)(m + 1));
         x0[(size_t)t * m + i] = v * nrm;
     }
 }
@@ -250,6 +263,7 @@ using namespace fde;
 
 struct fde_nop {
     int m = 0, s = 0, cin = 0, cout = 0, width = 0, layers = 0, K = 0;
+    int modes = 0;                   // length of the convolution axis (sine modes)
     cudaStream_t stream = nullptr;
     std::vector<int> din, dout;      // per layer
     std::vector<long> woff, boff;    // offsets in the flat parameter vector
@@ -266,7 +280,6 @@ struct fde_nop {
     float* out1 = nullptr;           // output of one inference (s x m)
     double* d_loss = nullptr;
     double* h_loss = nullptr;        // pinned
-    int modes = 8;                   // sine modes kept in the warm start (0: no projection)
 };
 
 namespace {
@@ -289,11 +302,11 @@ int ensure_batch(fde_nop* n, int B) {
     n->act.assign(n->layers + 1, nullptr);
     int cmax = n->cin;
     for (int l = 0; l < n->layers; ++l) {
-        FDE_CUDA_TRY(cudaMalloc(&n->act[l + 1], (size_t)B * n->dout[l] * n->m * sizeof(float)));
+        FDE_CUDA_TRY(cudaMalloc(&n->act[l + 1], (size_t)B * n->dout[l] * n->modes * sizeof(float)));
         cmax = std::max(cmax, n->dout[l]);
     }
-    FDE_CUDA_TRY(cudaMalloc(&n->ga, (size_t)B * cmax * n->m * sizeof(float)));
-    FDE_CUDA_TRY(cudaMalloc(&n->gb, (size_t)B * cmax * n->m * sizeof(float)));
+    FDE_CUDA_TRY(cudaMalloc(&n->ga, (size_t)B * cmax * n->modes * sizeof(float)));
+    FDE_CUDA_TRY(cudaMalloc(&n->gb, (size_t)B * cmax * n->modes * sizeof(float)));
     n->bcap = B;
     return FDE_OK;
 }
@@ -304,7 +317,7 @@ int forward32(fde_nop* n, const float* in, int B) {
     const float* x = in;
     for (int l = 0; l < n->layers; ++l) {
         rc = conv<float, float, float, false>(x, n->din[l], n->p + n->woff[l], n->p + n->boff[l], n->dout[l], n->K,
-                                              n->m, B, l < n->layers - 1, nullptr, n->act[l + 1], n->stream);
+                                              n->modes, B, l < n->layers - 1, nullptr, n->act[l + 1], n->stream);
         if (rc) return rc;
         x = n->act[l + 1];
     }
@@ -327,14 +340,16 @@ void fde_nop_destroy(fde_nop* n) {
     delete n;
 }
 
-int fde_nop_create(int m, int s, int width, int layers, int ksize, unsigned long long seed, void* stream,
+int fde_nop_create(int m, int s, int modes, int width, int layers, int ksize, unsigned long long seed, void* stream,
                    fde_nop** out) {
-    if (!out || m < 1 || s < 1 || width < 1 || layers < 1 || ksize < 1 || ksize > CV_KMAX || ksize % 2 == 0)
-        return set_error(FDE_ERR_ARG, "need m, s, width, layers >= 1 and an odd kernel size <= 7");
+    if (!out || m < 1 || s < 1 || modes < 1 || modes > m || width < 1 || layers < 1 || ksize < 1 ||
+        ksize > CV_KMAX || ksize % 2 == 0)
+        return set_error(FDE_ERR_ARG, "need m, s, width, layers >= 1, 1 <= modes <= m, odd kernel size <= 7");
     *out = nullptr;
     fde_nop* n = new (std::nothrow) fde_nop();
     if (!n) return set_error(FDE_ERR_ALLOC, "host allocation failed");
-    n->m = m; n->s = s; n->cin = s + 5; n->cout = s; n->width = width; n->layers = layers; n->K = ksize;
+    n->m = m; n->s = s; n->modes = modes; n->cin = s + 6; n->cout = s; n->width = width; n->layers = layers;
+    n->K = ksize;
     n->stream = (cudaStream_t)stream;
     for (int l = 0; l < layers; ++l) {
         n->din.push_back(l == 0 ? n->cin : width);
@@ -348,10 +363,10 @@ int fde_nop_create(int m, int s, int width, int layers, int ksize, unsigned long
     bool ok = cudaMalloc(&n->p, pb) == cudaSuccess && cudaMalloc(&n->g, pb) == cudaSuccess &&
               cudaMalloc(&n->m1, pb) == cudaSuccess && cudaMalloc(&n->m2, pb) == cudaSuccess &&
               cudaMalloc(&n->p16, (size_t)n->nparam * sizeof(__half)) == cudaSuccess &&
-              cudaMalloc(&n->h_a, (size_t)std::max(n->cin, width) * m * sizeof(__half)) == cudaSuccess &&
-              cudaMalloc(&n->h_b, (size_t)std::max(n->cin, width) * m * sizeof(__half)) == cudaSuccess &&
-              cudaMalloc(&n->feat, (size_t)n->cin * m * sizeof(float)) == cudaSuccess &&
-              cudaMalloc(&n->out1, (size_t)s * m * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&n->h_a, (size_t)std::max(n->cin, width) * modes * sizeof(__half)) == cudaSuccess &&
+              cudaMalloc(&n->h_b, (size_t)std::max(n->cin, width) * modes * sizeof(__half)) == cudaSuccess &&
+              cudaMalloc(&n->feat, (size_t)n->cin * modes * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&n->out1, (size_t)s * modes * sizeof(float)) == cudaSuccess &&
               cudaMalloc(&n->d_loss, sizeof(double)) == cudaSuccess &&
               cudaMallocHost(&n->h_loss, sizeof(double)) == cudaSuccess;
     if (!ok) {
@@ -400,7 +415,7 @@ int fde_nop_forward(fde_nop* n, const float* in, float* out, int batch) {
     if (!n || !in || !out || batch < 1) return set_error(FDE_ERR_ARG, "bad argument");
     int rc = forward32(n, in, batch);
     if (rc) return rc;
-    FDE_CUDA_TRY(cudaMemcpyAsync(out, n->act[n->layers], (size_t)batch * n->cout * n->m * sizeof(float),
+    FDE_CUDA_TRY(cudaMemcpyAsync(out, n->act[n->layers], (size_t)batch * n->cout * n->modes * sizeof(float),
                                  cudaMemcpyDeviceToDevice, n->stream));
     return FDE_OK;
 }
@@ -409,7 +424,7 @@ int fde_nop_loss_grad(fde_nop* n, const float* in, const float* target, int batc
     if (!n || !in || !target || batch < 1) return set_error(FDE_ERR_ARG, "bad argument");
     int rc = forward32(n, in, batch);
     if (rc) return rc;
-    const int L = n->layers, m = n->m, B = batch;
+    const int L = n->layers, m = n->modes, B = batch;
     const long ny = (long)B * n->cout * m;
     FDE_CUDA_TRY(cudaMemsetAsync(n->d_loss, 0, sizeof(double), n->stream));
     FDE_CUDA_TRY(cudaMemsetAsync(n->g, 0, n->nparam * sizeof(float), n->stream));
@@ -457,9 +472,22 @@ int fde_nop_features(fde_nop* n, fde_problem* h, float* in) {
     if (!n || !h || !in) return set_error(FDE_ERR_ARG, "NULL argument");
     Problem& P = *problem_of(h);
     if (P.m != n->m || P.s != n->s) return set_error(FDE_ERR_ARG, "problem size differs from the network's");
-    features_kernel<<<grid1((long)n->cin * n->m), 256, 0, n->stream>>>(P.m, P.s, P.d_u0, P.d_f, P.alpha, P.d_dplus,
-                                                                       P.d_dminus, in);
-    FDE_LAUNCH_CHECK("features_kernel");
+    const int K = n->modes;
+    const long w0 = (long)1 * K * 32, w1 = (long)(P.s + 1) * K * 32;
+    sine_analysis_kernel<<<(int)((w0 + 255) / 256), 256, 0, n->stream>>>(P.d_u0, 1, P.m, K, in, K, 0);
+    FDE_LAUNCH_CHECK("sine_analysis_kernel(u0)");
+    sine_analysis_kernel<<<(int)((w1 + 255) / 256), 256, 0, n->stream>>>(P.d_f, P.s + 1, P.m, K, in, K, 1);
+    FDE_LAUNCH_CHECK("sine_analysis_kernel(f)");
+    scalar_channels_kernel<<<1, 256, 0, n->stream>>>(P.m, K, P.s + 2, P.alpha, P.d_dplus, P.d_dminus, in);
+    FDE_LAUNCH_CHECK("scalar_channels_kernel");
+    return FDE_OK;
+}
+
+int fde_nop_coefficients(fde_nop* n, const double* x, float* coef) {
+    if (!n || !x || !coef) return set_error(FDE_ERR_ARG, "NULL argument");
+    const long w = (long)n->s * n->modes * 32;
+    sine_analysis_kernel<<<(int)((w + 255) / 256), 256, 0, n->stream>>>(x, n->s, n->m, n->modes, coef, n->modes, 0);
+    FDE_LAUNCH_CHECK("sine_analysis_kernel(x)");
     return FDE_OK;
 }
 
@@ -473,7 +501,7 @@ int fde_nop_warm_start(fde_nop* n, fde_problem* h, double* x0) {
         n->p16_valid = true;
     }
     // FP16 storage of weights and activations, FP32 accumulation and biases
-    const int L = n->layers, m = n->m;
+    const int L = n->layers, m = n->modes;
     const __half* xh = nullptr;
     for (int l = 0; l < L; ++l) {
         __half* dst = (l % 2 == 0) ? n->h_a : n->h_b;
@@ -495,20 +523,15 @@ int fde_nop_warm_start(fde_nop* n, fde_problem* h, double* x0) {
         if (rc) return rc;
         xh = dst;
     }
-    if (n->modes > 0) {
-        const int md = std::min(n->modes, m);
-        sine_filter_kernel<<<n->s, 256, md * sizeof(double), n->stream>>>(n->out1, m, md, x0);
-        FDE_LAUNCH_CHECK("sine_filter_kernel");
-    } else {
-        to_double_kernel<<<grid1((long)n->s * m), 256, 0, n->stream>>>(n->out1, x0, (long)n->s * m);
-        FDE_LAUNCH_CHECK("to_double_kernel");
-    }
+    sine_synthesis_kernel<<<n->s, 256, n->modes * sizeof(double), n->stream>>>(n->out1, n->m, n->modes, x0);
+    FDE_LAUNCH_CHECK("sine_synthesis_kernel");
     return FDE_OK;
 }
 
-int fde_nop_set_filter(fde_nop* n, int modes) {
-    if (!n || modes < 0) return set_error(FDE_ERR_ARG, "need a network and modes >= 0");
-    n->modes = modes;
+int fde_nop_synthesize(fde_nop* n, const float* coef, double* x) {
+    if (!n || !coef || !x) return set_error(FDE_ERR_ARG, "NULL argument");
+    sine_synthesis_kernel<<<n->s, 256, n->modes * sizeof(double), n->stream>>>(coef, n->m, n->modes, x);
+    FDE_LAUNCH_CHECK("sine_synthesis_kernel");
     return FDE_OK;
 }
 
