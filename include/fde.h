@@ -188,11 +188,12 @@ void fde_batch_destroy(fde_batch* b);
 
 /* ---- learned warm start ----------------------------------------------------
  * A 1-D convolutional neural operator (the paper has no counterpart) that predicts
- * a space-time initial guess for pgmres_solve.  It works in the grid sine basis
- * phi_j(x_i) = sqrt(2/(m+1)) sin(j pi i/(m+1)), j = 1..modes: the convolution runs
- * along the mode index over s+6 input channels [<u0,phi_j>, <f(.,t_n),phi_j> for
- * n = 0..s, (alpha-1.5)/0.4, (mean d+ - 1.25)/0.75, (mean d- - 1.25)/0.75, j/modes]
- * and its s output channels are the sine coefficients of u_1..u_s.  Layers:
+ * a space-time initial guess for pgmres_solve.  It works with sine-series
+ * coefficients c_j = 2/(m+1) sum_i v(x_i) sin(j pi i/(m+1)), j = 1..modes: the
+ * convolution runs along the mode index over s+6 input channels [c_j(u0),
+ * c_j(f(.,t_n)) for n = 0..s, (alpha-1.5)/0.4, (mean d+ - 1.25)/0.75,
+ * (mean d- - 1.25)/0.75, j/modes] and its s output channels are the coefficients
+ * of u_1..u_s (v(x_i) = sum_j c_j sin(j pi i/(m+1))).  Layers:
  * `layers` convolutions of odd size `ksize` (<= 7), zero padding, width `width`,
  * ReLU after all but the last.  Parameters (FP32, flat, per layer W (C_out, C_in,
  * K) then b (C_out)) start He-uniform from `seed` (counter-based splitmix64).

@@ -21,12 +21,6 @@
 #include <vector>
 
 #include "fde_internal.h"
-#include "lu_tc.cuh"
-
-namespace fde {
-constexpr int TC_A_BYTES[2] = {TcCfg<0>::A_BYTES, TcCfg<1>::A_BYTES};
-constexpr int TC_B_BYTES[2] = {TcCfg<0>::B_BYTES, TcCfg<1>::B_BYTES};
-}  // namespace fde
 
 using namespace fde;
 
@@ -159,14 +153,15 @@ int fde_batch_factor(fde_batch* b, int precision) {
         if (rc) return rc;
         P.factored = false;
         P.precision = precision;
-        const int ntile_max = (P.mp - LU_NB + TC_BM - 1) / TC_BM;
+        const size_t pack_a = tc_pack_a_bytes_per_block(precision, P.mp);
+        const size_t pack_all = tc_pack_bytes_per_block(precision, P.mp);
         for (int k = 0; k < P.nblk; ++k) {
             BlkDev d{};
             d.inst = (int)i;
             d.k = k;
             d.m = P.m;
             d.mp = P.mp;
-            d.ntile_max = ntile_max;
+            d.ntile_max = (int)pack_a;  // bytes of this block's A' tiles (B' tiles follow)
             d.h = P.h;
             d.dxa = P.dxa;
             d.phi = P.d_phi + k;
@@ -179,7 +174,7 @@ int fde_batch_factor(fde_batch* b, int precision) {
             d.info = P.d_info + k;
             if (kind >= 0) {
                 d.apack = (unsigned char*)pack_total;  // offset, rebased below
-                pack_total += (size_t)ntile_max * (TC_A_BYTES[kind] + TC_B_BYTES[kind]);
+                pack_total += pack_all;
             }
             blks.push_back(d);
         }
@@ -197,7 +192,7 @@ int fde_batch_factor(fde_batch* b, int precision) {
         for (BlkDev& d : blks) {
             const size_t off = (size_t)d.apack;
             d.apack = b->d_pack + off;
-            d.bpack = d.apack + (size_t)d.ntile_max * TC_A_BYTES[kind];
+            d.bpack = d.apack + (size_t)d.ntile_max;
         }
     }
     std::stable_sort(blks.begin(), blks.end(), [](const BlkDev& a, const BlkDev& c) { return a.mp > c.mp; });

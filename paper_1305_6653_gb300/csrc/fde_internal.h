@@ -79,7 +79,7 @@ struct InstDev {
 };
 
 struct BlkDev {
-    int inst, k, m, mp, ntile_max;
+    int inst, k, m, mp, ntile_max;  // ntile_max: bytes of the block's A' tiles (tensor-core paths)
     double h, dxa;
     const double2* phi;  // &phi_k, &psi_k of the instance
     const double2* psi;
@@ -209,6 +209,8 @@ int ensure_workspace(Problem& P, int restart);
 // batched launchers (lu.cu, timefft.cu, matvec.cu, krylov.cu)
 int launch_lu_batched(const BlkDev* d_blk, const std::vector<int>& mp_sorted, int precision, int* err,
                       cudaStream_t st);
+size_t tc_pack_bytes_per_block(int precision, int mp);    // packed tensor-core operands of one block
+size_t tc_pack_a_bytes_per_block(int precision, int mp);  // the A' part (B' follows)
 int launch_trsv_batched(const InstDev* I, const int* act, int nact, int max_nblk, int max_mp, cudaStream_t st);
 int launch_time_fft_batched(const InstDev* I, const int* act, int nact, int max_mp, int max_s, int j,
                             cudaStream_t st);

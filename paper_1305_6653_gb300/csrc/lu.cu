@@ -16,7 +16,7 @@
 //                 variant lives in lu_tc.cu)
 #include "fde_internal.h"
 #include "fft_device.cuh"
-#include "lu_tc.cuh"
+#include "lu_tc2.cuh"
 
 namespace fde {
 
@@ -154,19 +154,23 @@ __global__ void __launch_bounds__(256) lu_diag_batched(const BlkDev* __restrict_
 // the factored diagonal block (shared memory, broadcast reads) needs no barrier.
 // Loads and stores go through shared memory so that global accesses stay coalesced.
 // PACK < 0: plain; PACK = 0 / 1: also write the panels as packed TF32 / BF16
-// tensor-core operand tiles (A' from L21 rows, B' from U12 columns; see lu_tc.cuh).
+// tensor-core operand tiles (A' from L21 rows, B' from U12 columns; see lu_tc2.cuh).
 constexpr int RC = 128;
+// Ranges: rows mode over rows [rb, rend) against the diagonal block at (od, od);
+// columns mode over columns [cb, cend).  Tensor-core packing (PACK >= 0): rows r >= R0
+// of L21 go to A' tiles, columns >= R0 of U12 to B' tiles, at K' offset kq (Re) and
+// TB + kq (Im) -- the layout of lu_tc2.cuh.
 template <typename T, int PACK>
-__device__ __forceinline__ void panel_body(int mp, int p, int nrow, T* __restrict__ re, unsigned char* __restrict__ apack,
-                                           unsigned char* __restrict__ bpack, int bx) {
+__device__ __forceinline__ void panel_body(int mp, int od, int rb, int rend, int cb, int cend, int nrow,
+                                           T* __restrict__ re, unsigned char* __restrict__ apack,
+                                           unsigned char* __restrict__ bpack, int R0, int kq, int bx) {
     using C = cplx_t<T>;
     __shared__ C D[NB][NB + 1];
     __shared__ C dinv_s[NB];
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C (*X)[NB + 1] = reinterpret_cast<C (*)[NB + 1]>(smem_raw);  // [RC][NB+1]
     T* im = re + (size_t)mp * mp;
-    const int o = p * NB;
-    const int rest = o + NB;
+    const int o = od;
     for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
         const int r = e / NB, c = e % NB;
         const size_t idx = (size_t)(o + r) * mp + o + c;
@@ -174,7 +178,8 @@ __device__ __forceinline__ void panel_body(int mp, int p, int nrow, T* __restric
     }
     const bool rows = bx < nrow;
     const int chunk = rows ? bx : bx - nrow;
-    const int b0 = rest + chunk * RC;
+    const int b0 = (rows ? rb : cb) + chunk * RC;
+    const int bend = rows ? rend : cend;
     // X[q][c]: rows mode -> A21[b0+q][o+c]; columns mode -> A12[o+c][b0+q] (stored transposed)
     for (int e = threadIdx.x; e < RC * NB; e += blockDim.x) {
         int q, c;
@@ -186,7 +191,7 @@ __device__ __forceinline__ void panel_body(int mp, int p, int nrow, T* __restric
             c = e / RC; q = e % RC;
             idx = (size_t)(o + c) * mp + b0 + q;
         }
-        X[q][c] = (b0 + q < mp) ? mk(re[idx], im[idx]) : mk(T(0), T(0));
+        X[q][c] = (b0 + q < bend) ? mk(re[idx], im[idx]) : mk(T(0), T(0));
     }
     __syncthreads();
     if (rows && threadIdx.x < NB) {
@@ -228,73 +233,98 @@ __device__ __forceinline__ void panel_body(int mp, int p, int nrow, T* __restric
             c = e / RC; qq = e % RC;
             idx = (size_t)(o + c) * mp + b0 + qq;
         }
-        if (b0 + qq < mp) {
+        if (b0 + qq < bend) {
             re[idx] = X[qq][c].x;
             im[idx] = X[qq][c].y;
-        }
-        if constexpr (PACK >= 0) {
-            const int tile = (chunk * RC + qq) / TC_BM;
-            const int rt = (chunk * RC + qq) % TC_BM;  // row of the operand tile (A': output row, B': output column)
-            const float vr = (float)X[qq][c].x, vi = (float)X[qq][c].y;
-            if (rows) {
-                unsigned char* t = apack + (size_t)tile * TcCfg<PACK>::A_BYTES;
-                pack_store<PACK>(t, rt, c, vr);
-                pack_store<PACK>(t, rt, NB + c, vi);
-            } else {
-                unsigned char* t = bpack + (size_t)tile * TcCfg<PACK>::B_BYTES;
-                pack_store<PACK>(t, rt, c, vr);            // Re part of the product: Re L Re U - Im L Im U
-                pack_store<PACK>(t, rt, NB + c, -vi);
-                pack_store<PACK>(t, TC_BN + rt, c, vi);    // Im part: Re L Im U + Im L Re U
-                pack_store<PACK>(t, TC_BN + rt, NB + c, vr);
+            if constexpr (PACK >= 0) {
+                using Cfg = Tc2<PACK>;
+                const int g = b0 + qq - R0;  // position in the outer trailing matrix
+                if (g >= 0) {
+                    const int tile = g / T2_BM, rt = g % T2_BM;
+                    const float vr = (float)X[qq][c].x, vi = (float)X[qq][c].y;
+                    if (rows) {
+                        unsigned char* t = apack + (size_t)tile * Cfg::A_TILE;
+                        pack2_store<PACK>(t, T2_BM, rt, kq + c, vr);
+                        pack2_store<PACK>(t, T2_BM, rt, TB + kq + c, vi);
+                    } else {
+                        unsigned char* t = bpack + (size_t)tile * Cfg::B_TILE;
+                        pack2_store<PACK>(t, 2 * T2_BN, rt, kq + c, vr);  // Re output: Re L Re U - Im L Im U
+                        pack2_store<PACK>(t, 2 * T2_BN, rt, TB + kq + c, -vi);
+                        pack2_store<PACK>(t, 2 * T2_BN, T2_BN + rt, kq + c, vi);  // Im output
+                        pack2_store<PACK>(t, 2 * T2_BN, T2_BN + rt, TB + kq + c, vr);
+                    }
+                }
             }
         }
     }
 }
 
-template <int PACK>
-__device__ __forceinline__ size_t pack_stride(bool a_side, int ntile_max) {
-    if constexpr (PACK >= 0) return (size_t)ntile_max * (a_side ? TcCfg<PACK>::A_BYTES : TcCfg<PACK>::B_BYTES);
-    return 0;
+template <typename T>
+__global__ void __launch_bounds__(RC)
+lu_panel_kernel(int mp, int p, int nrow, T* __restrict__ fac) {
+    const int k = blockIdx.y;
+    const int rest = (p + 1) * NB;
+    panel_body<T, -1>(mp, p * NB, rest, mp, rest, mp, nrow, plane_re(fac, k, mp), nullptr, nullptr, 0, 0, blockIdx.x);
 }
 
+// General ranges (two-level LU): grid (nrow + ncol, nblk).
 template <typename T, int PACK>
 __global__ void __launch_bounds__(RC)
-lu_panel_kernel(int mp, int p, int nrow, T* __restrict__ fac, unsigned char* __restrict__ apack,
-                unsigned char* __restrict__ bpack, int ntile_max) {
+lu_panel_range_kernel(int mp, int od, int rb, int rend, int cb, int cend, int nrow, T* __restrict__ fac,
+                      unsigned char* __restrict__ apack, unsigned char* __restrict__ bpack, size_t pack_a_stride,
+                      size_t pack_b_stride, int R0, int kq) {
     const int k = blockIdx.y;
-    panel_body<T, PACK>(mp, p, nrow, plane_re(fac, k, mp), apack ? apack + k * pack_stride<PACK>(true, ntile_max) : nullptr,
-                        bpack ? bpack + k * pack_stride<PACK>(false, ntile_max) : nullptr, blockIdx.x);
+    panel_body<T, PACK>(mp, od, rb, rend, cb, cend, nrow, plane_re(fac, k, mp),
+                        apack ? apack + k * pack_a_stride : nullptr, bpack ? bpack + k * pack_b_stride : nullptr, R0,
+                        kq, blockIdx.x);
 }
 
 template <typename T, int PACK>
 __global__ void __launch_bounds__(RC) lu_panel_batched(const BlkDev* __restrict__ B, int p) {
     const BlkDev& d = B[blockIdx.y];
-    const int rem = d.mp - (p + 1) * NB;
+    const int rest = (p + 1) * NB;
+    const int rem = d.mp - rest;
     if (rem <= 0) return;
     const int nrow = (rem + RC - 1) / RC;
     if ((int)blockIdx.x >= 2 * nrow) return;
-    panel_body<T, PACK>(d.mp, p, nrow, (T*)d.fac, d.apack, d.bpack, blockIdx.x);
+    panel_body<T, PACK>(d.mp, p * NB, rest, d.mp, rest, d.mp, nrow, (T*)d.fac, d.apack, d.bpack, 0, 0, blockIdx.x);
+}
+
+// Batched general ranges; the ranges are relative to the outer step offset o and
+// clipped to each block's m_p.
+template <typename T, int PACK>
+__global__ void __launch_bounds__(RC)
+lu_panel_range_batched(const BlkDev* __restrict__ B, int od, int rows_from, int cols_from, int cols_to, int R0,
+                       int kq) {
+    const BlkDev& d = B[blockIdx.y];
+    if (od + NB > d.mp) return;
+    const int rend = d.mp, cend = cols_to < d.mp ? cols_to : d.mp;
+    const int nrow = rows_from < rend ? (rend - rows_from + RC - 1) / RC : 0;
+    const int ncol = cols_from < cend ? (cend - cols_from + RC - 1) / RC : 0;
+    if ((int)blockIdx.x >= nrow + ncol) return;
+    panel_body<T, PACK>(d.mp, od, rows_from, rend, cols_from, cend, nrow, (T*)d.fac, d.apack, d.bpack, R0, kq,
+                        blockIdx.x);
 }
 
 // Trailing update A22 -= L21 U12 on CUDA cores: 64 x 64 output tile per CTA,
 // 4 x 4 complex outputs per thread, K = NB.
+// C[r][c] -= sum_{k<NB} L[r][kb+k] U[kb+k][c] over the 64 x 64 tile at (r0, c0),
+// rows < rend, columns < cend.
 template <typename T>
-__device__ __forceinline__ void update_body(int mp, int p, T* __restrict__ re, int ti, int tj) {
+__device__ __forceinline__ void update_body(int mp, int kb, int r0, int c0, int rend, int cend, T* __restrict__ re) {
     using C = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C (*Ls)[NB + 1] = reinterpret_cast<C (*)[NB + 1]>(smem_raw);                        // [64][NB+1]
     C (*Us)[64 + 1] = reinterpret_cast<C (*)[64 + 1]>(smem_raw + 64 * (NB + 1) * sizeof(C));  // [NB][65]
     T* im = re + (size_t)mp * mp;
-    const int o = p * NB;
-    const int rest = o + NB;
-    const int r0 = rest + ti * 64, c0 = rest + tj * 64;
+    const int o = kb;
     for (int e = threadIdx.x; e < 64 * NB; e += blockDim.x) {
         const int q = e / NB, c = e % NB;
         const int r = r0 + q;
-        Ls[q][c] = r < mp ? mk(re[(size_t)r * mp + o + c], im[(size_t)r * mp + o + c]) : mk(T(0), T(0));
+        Ls[q][c] = r < rend ? mk(re[(size_t)r * mp + o + c], im[(size_t)r * mp + o + c]) : mk(T(0), T(0));
         const int c2 = e / 64, q2 = e % 64;
         const int cc = c0 + q2;
-        Us[c2][q2] = cc < mp ? mk(re[(size_t)(o + c2) * mp + cc], im[(size_t)(o + c2) * mp + cc]) : mk(T(0), T(0));
+        Us[c2][q2] = cc < cend ? mk(re[(size_t)(o + c2) * mp + cc], im[(size_t)(o + c2) * mp + cc]) : mk(T(0), T(0));
     }
     __syncthreads();
     const int tr = threadIdx.x / 16, tc = threadIdx.x % 16;
@@ -321,11 +351,11 @@ __device__ __forceinline__ void update_body(int mp, int p, T* __restrict__ re, i
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
         const int r = r0 + tr + 16 * a;
-        if (r >= mp) continue;
+        if (r >= rend) continue;
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
             const int c = c0 + tc + 16 * b;
-            if (c >= mp) continue;
+            if (c >= cend) continue;
             const size_t idx = (size_t)r * mp + c;
             re[idx] -= acc[a][b].x;
             im[idx] -= acc[a][b].y;
@@ -337,7 +367,29 @@ template <typename T>
 __global__ void __launch_bounds__(256)
 lu_update_kernel(int mp, int p, int ntile, T* __restrict__ fac) {
     const int k = blockIdx.y;
-    update_body<T>(mp, p, plane_re(fac, k, mp), blockIdx.x / ntile, blockIdx.x % ntile);
+    const int rest = (p + 1) * NB;
+    update_body<T>(mp, p * NB, rest + (blockIdx.x / ntile) * 64, rest + (blockIdx.x % ntile) * 64, mp, mp,
+                   plane_re(fac, k, mp));
+}
+
+// General ranges: rows [rb, rend) x columns [cb, cend), K block [kb, kb+NB); grid (ntr * ntc, nblk).
+template <typename T>
+__global__ void __launch_bounds__(256)
+lu_update_range_kernel(int mp, int kb, int rb, int rend, int cb, int cend, int ntc, T* __restrict__ fac) {
+    const int k = blockIdx.y;
+    update_body<T>(mp, kb, rb + (blockIdx.x / ntc) * 64, cb + (blockIdx.x % ntc) * 64, rend, cend,
+                   plane_re(fac, k, mp));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+lu_update_range_batched(const BlkDev* __restrict__ B, int kb, int rb, int rend_max, int cb, int cend_max, int ntc) {
+    const BlkDev& d = B[blockIdx.y];
+    const int rend = rend_max < d.mp ? rend_max : d.mp;
+    const int cend = cend_max < d.mp ? cend_max : d.mp;
+    const int r0 = rb + (blockIdx.x / ntc) * 64, c0 = cb + (blockIdx.x % ntc) * 64;
+    if (kb + NB > d.mp || r0 >= rend || c0 >= cend) return;
+    update_body<T>(d.mp, kb, r0, c0, rend, cend, (T*)d.fac);
 }
 
 // Batched: grid.x covers the tiles of the largest trailing matrix (ntile_grid^2).
@@ -349,7 +401,7 @@ __global__ void __launch_bounds__(256) lu_update_batched(const BlkDev* __restric
     const int nt = (rem + 63) / 64;
     const int ti = blockIdx.x / ntile_grid, tj = blockIdx.x % ntile_grid;
     if (ti >= nt || tj >= nt) return;
-    update_body<T>(d.mp, p, (T*)d.fac, ti, tj);
+    update_body<T>(d.mp, p * NB, (p + 1) * NB + ti * 64, (p + 1) * NB + tj * 64, d.mp, d.mp, (T*)d.fac);
 }
 
 // Forward (unit lower L) then backward (U) substitution for one block per CTA,
@@ -529,7 +581,7 @@ static int run_lu(Problem& P, cudaStream_t st) {
         FDE_LAUNCH_CHECK("form_blocks_kernel");
     }
     const size_t panel_smem = (size_t)RC * (NB + 1) * sizeof(C);
-    FDE_CUDA_TRY(cudaFuncSetAttribute(lu_panel_kernel<T, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    FDE_CUDA_TRY(cudaFuncSetAttribute(lu_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)panel_smem));
     const size_t upd_smem = (64 * (NB + 1) + NB * 65) * sizeof(C);
     FDE_CUDA_TRY(cudaFuncSetAttribute(lu_update_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)upd_smem));
@@ -545,7 +597,7 @@ static int run_lu(Problem& P, cudaStream_t st) {
         const int nch = (rem + RC - 1) / RC;
         {
             StageTimer t(P, FDE_STAGE_LU_PANEL);
-            lu_panel_kernel<T, -1><<<dim3(2 * nch, nb), RC, panel_smem, st>>>(mp, p, nch, fac, nullptr, nullptr, 0);
+            lu_panel_kernel<T><<<dim3(2 * nch, nb), RC, panel_smem, st>>>(mp, p, nch, fac);
             FDE_LAUNCH_CHECK("lu_panel_kernel");
         }
         const int nt = (rem + 63) / 64;
@@ -556,91 +608,155 @@ static int run_lu(Problem& P, cudaStream_t st) {
     return FDE_OK;
 }
 
-// FP32 factors whose trailing updates run on the tcgen05 tensor cores.
+// ---------------------------------------------------------------------------
+// Two-level LU for the tensor-core precisions (see lu_tc2.cuh)
+// ---------------------------------------------------------------------------
+template <int KIND>
+__global__ void __launch_bounds__(128)
+lu_update_tc2_kernel(int mp, int R0, int nt, float* __restrict__ fac, const unsigned char* __restrict__ apack,
+                     const unsigned char* __restrict__ bpack, size_t pa, size_t pb, int* __restrict__ err) {
+    const int k = blockIdx.y;
+    tc2_update_body<KIND>(mp, R0, fac + (size_t)k * 2 * mp * mp, apack + k * pa, bpack + k * pb, err,
+                          blockIdx.x / nt, blockIdx.x % nt);
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(128)
+lu_update_tc2_batched(const BlkDev* __restrict__ B, int R0, int ntg, int* __restrict__ err) {
+    const BlkDev& d = B[blockIdx.y];
+    if (R0 >= d.mp) return;
+    const int nt = (d.mp - R0 + T2_BM - 1) / T2_BM;
+    const int ti = blockIdx.x / ntg, tj = blockIdx.x % ntg;
+    if (ti >= nt || tj >= nt) return;
+    tc2_update_body<KIND>(d.mp, R0, (float*)d.fac, d.apack, d.bpack, err, ti, tj);
+}
+
+static inline int cdiv(int a, int b) { return a > 0 ? (a + b - 1) / b : 0; }
+
+template <int KIND>
+static int set_tc_attrs() {
+    const size_t panel_smem = (size_t)RC * (NB + 1) * sizeof(float2);
+    const size_t upd_smem = (64 * (NB + 1) + NB * 65) * sizeof(float2);
+    FDE_CUDA_TRY(cudaFuncSetAttribute(lu_panel_range_kernel<float, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)panel_smem));
+    FDE_CUDA_TRY(cudaFuncSetAttribute(lu_panel_range_batched<float, KIND>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_smem));
+    FDE_CUDA_TRY(cudaFuncSetAttribute(lu_update_range_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)upd_smem));
+    FDE_CUDA_TRY(cudaFuncSetAttribute(lu_update_range_batched<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)upd_smem));
+    FDE_CUDA_TRY(cudaFuncSetAttribute(lu_update_tc2_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      Tc2<KIND>::SMEM));
+    FDE_CUDA_TRY(cudaFuncSetAttribute(lu_update_tc2_batched<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      Tc2<KIND>::SMEM));
+    return FDE_OK;
+}
+
+// Packed operand bytes per block (A' tiles then B' tiles) for a block of size mp.
+template <int KIND>
+static void tc2_pack_sizes(int mp, size_t* pa, size_t* pb) {
+    const int ntile = mp > TB ? (mp - TB + T2_BM - 1) / T2_BM : 0;
+    *pa = (size_t)ntile * Tc2<KIND>::A_TILE;
+    *pb = (size_t)ntile * Tc2<KIND>::B_TILE;
+}
+
 template <int KIND>
 static int run_lu_tc(Problem& P, cudaStream_t st) {
-    using Cfg = TcCfg<KIND>;
-    static_assert(TC_KP == 2 * NB, "packed K' must be 2 NB");
+    using Cfg = Tc2<KIND>;
     float* fac = reinterpret_cast<float*>(P.d_fac);
     float2* dinv = reinterpret_cast<float2*>(P.d_dinv);
     const int mp = P.mp, nb = P.nblk;
-    const int ntile_max = (mp - NB + TC_BM - 1) / TC_BM;
-    const size_t abytes = (size_t)nb * ntile_max * Cfg::A_BYTES;
-    const size_t bbytes = (size_t)nb * ntile_max * Cfg::B_BYTES;
-    if (P.pack_bytes < abytes + bbytes) {
+    size_t pa, pb;
+    tc2_pack_sizes<KIND>(mp, &pa, &pb);
+    const size_t need = (size_t)nb * (pa + pb);
+    if (need > 0 && P.pack_bytes < need) {
         if (P.d_pack) cudaFree(P.d_pack);
         P.d_pack = nullptr;
         P.pack_bytes = 0;
-        FDE_CUDA_TRY(cudaMalloc(&P.d_pack, abytes + bbytes));
-        P.pack_bytes = abytes + bbytes;
-        FDE_CUDA_TRY(cudaMemsetAsync(P.d_pack, 0, abytes + bbytes, st));
+        FDE_CUDA_TRY(cudaMalloc(&P.d_pack, need));
+        P.pack_bytes = need;
+        FDE_CUDA_TRY(cudaMemsetAsync(P.d_pack, 0, need, st));
     }
     unsigned char* apack = reinterpret_cast<unsigned char*>(P.d_pack);
-    unsigned char* bpack = apack + abytes;
+    unsigned char* bpack = apack ? apack + (size_t)nb * pa : nullptr;
     {
         dim3 grid(mp < 64 ? mp : 64, nb);
         StageTimer t(P, FDE_STAGE_FORM);
-        form_blocks_kernel<float><<<grid, 256, 0, st>>>(P.m, mp, P.h, P.dxa, P.d_g, P.d_dplus, P.d_dminus,
-                                                        P.d_phi, P.d_psi, fac);
+        form_blocks_kernel<float><<<grid, 256, 0, st>>>(P.m, mp, P.h, P.dxa, P.d_g, P.d_dplus, P.d_dminus, P.d_phi,
+                                                        P.d_psi, fac);
         FDE_LAUNCH_CHECK("form_blocks_kernel");
     }
-    // at most 2 CTAs per SM: each holds 256 of the SM's 512 TMEM columns
-    const int smem = (Cfg::A_BYTES + Cfg::B_BYTES) > 100 * 1024 ? (Cfg::A_BYTES + Cfg::B_BYTES) : 100 * 1024;
-    FDE_CUDA_TRY(cudaFuncSetAttribute(lu_update_tc_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    int rc = set_tc_attrs<KIND>();
+    if (rc) return rc;
     const size_t panel_smem = (size_t)RC * (NB + 1) * sizeof(float2);
-    FDE_CUDA_TRY(cudaFuncSetAttribute(lu_panel_kernel<float, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)panel_smem));
-    const int steps = mp / NB;
-    for (int p = 0; p < steps; ++p) {
-        {
-            StageTimer t(P, FDE_STAGE_LU_DIAG);
-            lu_diag_kernel<float><<<nb, 256, 0, st>>>(mp, p, fac, dinv, P.d_info);
-            FDE_LAUNCH_CHECK("lu_diag_kernel");
+    const size_t upd_smem = (64 * (NB + 1) + NB * 65) * sizeof(float2);
+    for (int o = 0; o < mp; o += TB) {
+        const int W = mp - o < TB ? mp - o : TB;
+        const int R0 = o + W;  // start of the outer trailing matrix
+        for (int q = 0; q < W / NB; ++q) {
+            const int oi = o + q * NB;
+            {
+                StageTimer t(P, FDE_STAGE_LU_DIAG);
+                lu_diag_kernel<float><<<nb, 256, 0, st>>>(mp, oi / NB, fac, dinv, P.d_info);
+                FDE_LAUNCH_CHECK("lu_diag_kernel");
+            }
+            const int nrow = cdiv(mp - (oi + NB), RC), ncol = cdiv(R0 - (oi + NB), RC);
+            if (nrow + ncol > 0) {
+                StageTimer t(P, FDE_STAGE_LU_PANEL);
+                lu_panel_range_kernel<float, KIND><<<dim3(nrow + ncol, nb), RC, panel_smem, st>>>(
+                    mp, oi, oi + NB, mp, oi + NB, R0, nrow, fac, apack, bpack, pa, pb, R0, q * NB);
+                FDE_LAUNCH_CHECK("lu_panel_range_kernel");
+            }
+            const int ntr = cdiv(mp - (oi + NB), 64), ntc = cdiv(R0 - (oi + NB), 64);
+            if (ntr * ntc > 0) {
+                StageTimer t(P, FDE_STAGE_LU_UPDATE);
+                lu_update_range_kernel<float><<<dim3(ntr * ntc, nb), 256, upd_smem, st>>>(mp, oi, oi + NB, mp, oi + NB,
+                                                                                        R0, ntc, fac);
+                FDE_LAUNCH_CHECK("lu_update_range_kernel");
+            }
         }
-        const int rest = (p + 1) * NB;
-        const int rem = mp - rest;
-        if (rem <= 0) break;
-        const int nch = (rem + RC - 1) / RC;
-        {
-            StageTimer t(P, FDE_STAGE_LU_PANEL);
-            lu_panel_kernel<float, KIND><<<dim3(2 * nch, nb), RC, panel_smem, st>>>(mp, p, nch, fac, apack, bpack,
-                                                                                ntile_max);
-            FDE_LAUNCH_CHECK("lu_panel_kernel");
+        if (R0 >= mp) continue;
+        // outer row panel U12 = L11^{-1} A12, 32 rows at a time
+        for (int q = 0; q < W / NB; ++q) {
+            const int oi = o + q * NB;
+            {
+                StageTimer t(P, FDE_STAGE_LU_PANEL);
+                const int ncol = cdiv(mp - R0, RC);
+                lu_panel_range_kernel<float, KIND><<<dim3(ncol, nb), RC, panel_smem, st>>>(
+                    mp, oi, 0, 0, R0, mp, 0, fac, apack, bpack, pa, pb, R0, q * NB);
+                FDE_LAUNCH_CHECK("lu_panel_range_kernel");
+            }
+            const int ntr = cdiv(R0 - (oi + NB), 64), ntc = cdiv(mp - R0, 64);
+            if (ntr * ntc > 0) {
+                StageTimer t(P, FDE_STAGE_LU_UPDATE);
+                lu_update_range_kernel<float><<<dim3(ntr * ntc, nb), 256, upd_smem, st>>>(mp, oi, oi + NB, R0, R0, mp,
+                                                                                        ntc, fac);
+                FDE_LAUNCH_CHECK("lu_update_range_kernel");
+            }
         }
-        const int nt = (rem + TC_BM - 1) / TC_BM;
+        const int nt = cdiv(mp - R0, T2_BM);
         StageTimer t(P, FDE_STAGE_LU_UPDATE);
-        lu_update_tc_kernel<KIND><<<dim3(nt * nt, nb), 128, smem, st>>>(mp, rest, nt, ntile_max, fac, apack, bpack,
-                                                                        P.d_err);
-        FDE_LAUNCH_CHECK("lu_update_tc_kernel");
+        lu_update_tc2_kernel<KIND><<<dim3(nt * nt, nb), 128, Cfg::SMEM, st>>>(mp, R0, nt, fac, apack, bpack, pa, pb,
+                                                                             P.d_err);
+        FDE_LAUNCH_CHECK("lu_update_tc2_kernel");
     }
     return FDE_OK;
 }
 
-// Batched LU over a block table sorted by m_p (descending): at step p the blocks
-// still being factored form a prefix of the table.  FP32 storage; trailing
-// updates on CUDA cores (FDE_FP32) or tcgen05 (FDE_TF32 / FDE_BF16).
-template <int KIND>
-static int run_lu_batched(const BlkDev* d_blk, const std::vector<int>& mps, int* err, cudaStream_t st) {
+// Batched LU over a block table sorted by m_p (descending): blocks still being
+// factored form a prefix of the table.  FP32 storage; trailing updates on CUDA
+// cores (FDE_FP32, NB = 32 steps) or two-level with tcgen05 (FDE_TF32 / FDE_BF16).
+static int run_lu_batched_simt(const BlkDev* d_blk, const std::vector<int>& mps, cudaStream_t st) {
     const int nbt = (int)mps.size();
     const int max_mp = mps[0];
-    {
-        form_blocks_batched<float><<<dim3(64, nbt), 256, 0, st>>>(d_blk);
-        FDE_LAUNCH_CHECK("form_blocks_batched");
-    }
+    form_blocks_batched<float><<<dim3(64, nbt), 256, 0, st>>>(d_blk);
+    FDE_LAUNCH_CHECK("form_blocks_batched");
     const size_t panel_smem = (size_t)RC * (NB + 1) * sizeof(float2);
-    FDE_CUDA_TRY(cudaFuncSetAttribute(lu_panel_batched<float, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)panel_smem));
     const size_t upd_smem = (64 * (NB + 1) + NB * 65) * sizeof(float2);
-    int tc_smem = 0;
-    if constexpr (KIND >= 0) {
-        using Cfg = TcCfg<KIND>;
-        tc_smem = (Cfg::A_BYTES + Cfg::B_BYTES) > 100 * 1024 ? (Cfg::A_BYTES + Cfg::B_BYTES) : 100 * 1024;
-        FDE_CUDA_TRY(cudaFuncSetAttribute(lu_update_tc_batched<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          tc_smem));
-    } else {
-        FDE_CUDA_TRY(cudaFuncSetAttribute(lu_update_batched<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)upd_smem));
-    }
+    FDE_CUDA_TRY(cudaFuncSetAttribute(lu_panel_batched<float, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)panel_smem));
+    FDE_CUDA_TRY(cudaFuncSetAttribute(lu_update_batched<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)upd_smem));
     for (int p = 0; p * NB < max_mp; ++p) {
         int nd = 0, nu = 0;
         while (nd < nbt && mps[nd] > p * NB) ++nd;
@@ -650,17 +766,72 @@ static int run_lu_batched(const BlkDev* d_blk, const std::vector<int>& mps, int*
         if (nu == 0) break;
         const int rem = max_mp - (p + 1) * NB;
         const int nch = (rem + RC - 1) / RC;
-        lu_panel_batched<float, KIND><<<dim3(2 * nch, nu), RC, panel_smem, st>>>(d_blk, p);
+        lu_panel_batched<float, -1><<<dim3(2 * nch, nu), RC, panel_smem, st>>>(d_blk, p);
         FDE_LAUNCH_CHECK("lu_panel_batched");
-        if constexpr (KIND >= 0) {
-            const int ntg = (rem + TC_BM - 1) / TC_BM;
-            lu_update_tc_batched<KIND><<<dim3(ntg * ntg, nu), 128, tc_smem, st>>>(d_blk, p, NB, ntg, err);
-            FDE_LAUNCH_CHECK("lu_update_tc_batched");
-        } else {
-            const int ntg = (rem + 63) / 64;
-            lu_update_batched<float><<<dim3(ntg * ntg, nu), 256, upd_smem, st>>>(d_blk, p, ntg);
-            FDE_LAUNCH_CHECK("lu_update_batched");
+        const int ntg = (rem + 63) / 64;
+        lu_update_batched<float><<<dim3(ntg * ntg, nu), 256, upd_smem, st>>>(d_blk, p, ntg);
+        FDE_LAUNCH_CHECK("lu_update_batched");
+    }
+    return FDE_OK;
+}
+
+template <int KIND>
+static int run_lu_batched_tc(const BlkDev* d_blk, const std::vector<int>& mps, int* err, cudaStream_t st) {
+    using Cfg = Tc2<KIND>;
+    const int nbt = (int)mps.size();
+    const int max_mp = mps[0];
+    form_blocks_batched<float><<<dim3(64, nbt), 256, 0, st>>>(d_blk);
+    FDE_LAUNCH_CHECK("form_blocks_batched");
+    int rc = set_tc_attrs<KIND>();
+    if (rc) return rc;
+    const size_t panel_smem = (size_t)RC * (NB + 1) * sizeof(float2);
+    const size_t upd_smem = (64 * (NB + 1) + NB * 65) * sizeof(float2);
+    auto active = [&](int lim) {  // blocks with m_p > lim (a prefix of the sorted table)
+        int n = 0;
+        while (n < nbt && mps[n] > lim) ++n;
+        return n;
+    };
+    for (int o = 0; o < max_mp; o += TB) {
+        const int R0 = o + TB;
+        for (int q = 0; q < TB / NB; ++q) {
+            const int oi = o + q * NB;
+            const int nd = active(oi);
+            if (nd == 0) break;
+            lu_diag_batched<float><<<nd, 256, 0, st>>>(d_blk, oi / NB);
+            FDE_LAUNCH_CHECK("lu_diag_batched");
+            const int top = mps[0];  // largest active block bounds the grids
+            const int nrow = cdiv(top - (oi + NB), RC), ncol = cdiv((R0 < top ? R0 : top) - (oi + NB), RC);
+            if (nrow + ncol > 0) {
+                lu_panel_range_batched<float, KIND><<<dim3(nrow + ncol, nd), RC, panel_smem, st>>>(
+                    d_blk, oi, oi + NB, oi + NB, R0, R0, q * NB);
+                FDE_LAUNCH_CHECK("lu_panel_range_batched");
+            }
+            const int ntr = cdiv(top - (oi + NB), 64), ntc = cdiv((R0 < top ? R0 : top) - (oi + NB), 64);
+            if (ntr * ntc > 0) {
+                lu_update_range_batched<float><<<dim3(ntr * ntc, nd), 256, upd_smem, st>>>(d_blk, oi, oi + NB, 1 << 30,
+                                                                                         oi + NB, R0, ntc);
+                FDE_LAUNCH_CHECK("lu_update_range_batched");
+            }
         }
+        const int nt_blocks = active(R0);
+        if (nt_blocks == 0) continue;
+        const int top = mps[0];
+        for (int q = 0; q < TB / NB; ++q) {
+            const int oi = o + q * NB;
+            const int ncol = cdiv(top - R0, RC);
+            lu_panel_range_batched<float, KIND><<<dim3(ncol, nt_blocks), RC, panel_smem, st>>>(d_blk, oi, 1 << 30, R0,
+                                                                                               1 << 30, R0, q * NB);
+            FDE_LAUNCH_CHECK("lu_panel_range_batched");
+            const int ntr = cdiv(R0 - (oi + NB), 64), ntc = cdiv(top - R0, 64);
+            if (ntr * ntc > 0) {
+                lu_update_range_batched<float><<<dim3(ntr * ntc, nt_blocks), 256, upd_smem, st>>>(
+                    d_blk, oi, oi + NB, R0, R0, 1 << 30, ntc);
+                FDE_LAUNCH_CHECK("lu_update_range_batched");
+            }
+        }
+        const int ntg = cdiv(top - R0, T2_BM);
+        lu_update_tc2_batched<KIND><<<dim3(ntg * ntg, nt_blocks), 128, Cfg::SMEM, st>>>(d_blk, R0, ntg, err);
+        FDE_LAUNCH_CHECK("lu_update_tc2_batched");
     }
     return FDE_OK;
 }
@@ -668,9 +839,23 @@ static int run_lu_batched(const BlkDev* d_blk, const std::vector<int>& mps, int*
 int launch_lu_batched(const BlkDev* d_blk, const std::vector<int>& mp_sorted, int precision, int* err,
                       cudaStream_t st) {
     if (mp_sorted.empty()) return FDE_OK;
-    if (precision == FDE_TF32) return run_lu_batched<0>(d_blk, mp_sorted, err, st);
-    if (precision == FDE_BF16) return run_lu_batched<1>(d_blk, mp_sorted, err, st);
-    return run_lu_batched<-1>(d_blk, mp_sorted, err, st);
+    if (precision == FDE_TF32) return run_lu_batched_tc<0>(d_blk, mp_sorted, err, st);
+    if (precision == FDE_BF16) return run_lu_batched_tc<1>(d_blk, mp_sorted, err, st);
+    return run_lu_batched_simt(d_blk, mp_sorted, st);
+}
+
+size_t tc_pack_bytes_per_block(int precision, int mp) {
+    size_t pa = 0, pb = 0;
+    if (precision == FDE_TF32) tc2_pack_sizes<0>(mp, &pa, &pb);
+    else if (precision == FDE_BF16) tc2_pack_sizes<1>(mp, &pa, &pb);
+    return pa + pb;
+}
+
+size_t tc_pack_a_bytes_per_block(int precision, int mp) {
+    size_t pa = 0, pb = 0;
+    if (precision == FDE_TF32) tc2_pack_sizes<0>(mp, &pa, &pb);
+    else if (precision == FDE_BF16) tc2_pack_sizes<1>(mp, &pa, &pb);
+    return pa;
 }
 
 int launch_trsv_batched(const InstDev* I, const int* act, int nact, int max_nblk, int max_mp, cudaStream_t st) {

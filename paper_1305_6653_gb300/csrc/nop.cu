@@ -1,11 +1,11 @@
 // Learned warm start: a small 1-D convolutional neural operator that maps the data
 // of eq. (1.1) -- u0, f(., t_n) for n = 0..s, alpha, d+, d- -- to a space-time
-// initial guess u_1..u_s of the GMRES solve.  It works in the grid sine basis
-// phi_j(x_i) = sqrt(2/(m+1)) sin(j pi i/(m+1)), j = 1..K: the convolution runs
-// along the mode index (length K) over channels [<u0,phi_j>, <f_n,phi_j> for
+// initial guess u_1..u_s of the GMRES solve.  It works with sine-series
+// coefficients c_j (v(x_i) = sum_j c_j sin(j pi x_i), j = 1..K): the convolution runs
+// along the mode index (length K) over channels [c_j(u0), c_j(f(., t_n)) for
 // n = 0..s, (alpha-1.5)/0.4, (mean d+ - 1.25)/0.75, (mean d- - 1.25)/0.75, j/K], and
-// its s output channels are the sine coefficients of u_1..u_s, synthesised back
-// to the grid.  The paper has no learned component; the solve is still judged by
+// its s output channels are the coefficients of u_1..u_s, synthesised back to the
+// grid.  The paper has no learned component; the solve is still judged by
 // its true FP64 residual, and pgmres_solve falls back to the zero guess when the
 // predicted guess is worse than zero.
 //
@@ -196,8 +196,9 @@ __global__ void to_half_kernel(const float* __restrict__ a, __half* __restrict__
         b[i] = __float2half_rn(a[i]);
 }
 
-// Sine coefficients c[r][j] = <v_r, phi_j> of `rows` grid vectors v_r (stride m):
-// one warp per (row, mode).
+// Sine-series coefficients c[r][j] = 2/(m+1) sum_i v_r[i] sin(j pi (i+1)/(m+1)) of
+// `rows` grid vectors v_r (stride m), so that v_r[i] = sum_j c[r][j] sin(j pi (i+1)/(m+1))
+// on the first modes: one warp per (row, mode).
 __global__ void sine_analysis_kernel(const double* __restrict__ v, int rows, int m, int K, float* __restrict__ out,
                                      int out_stride, int out_off) {
     const int lane = threadIdx.x & 31;
@@ -208,7 +209,7 @@ __global__ void sine_analysis_kernel(const double* __restrict__ v, int rows, int
     double c = 0.0;
     for (int i = lane; i < m; i += 32) c += vr[i] * sinpi((double)(j + 1) * (i + 1) / (double)(m + 1));
     for (int off = 16; off; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
-    if (lane == 0) out[(size_t)(out_off + r) * out_stride + j] = (float)(c * sqrt(2.0 / (double)(m + 1)));
+    if (lane == 0) out[(size_t)(out_off + r) * out_stride + j] = (float)(c * (2.0 / (double)(m + 1)));
 }
 
 // Scalar channels of the spectral input: (alpha-1.5)/0.4, mean d+, mean d- (normalised), j/K.
@@ -238,17 +239,16 @@ __global__ void scalar_channels_kernel(int m, int K, int c0, double alpha, const
     }
 }
 
-// x0[t][i] = sum_j c[t][j] phi_j(x_i): one CTA per time level.
+// x0[t][i] = sum_j c[t][j] sin(j pi (i+1)/(m+1)): one CTA per time level.
 __global__ void sine_synthesis_kernel(const float* __restrict__ c, int m, int K, double* __restrict__ x0) {
     extern __shared__ double coef[];
     const int t = blockIdx.x;
     for (int j = threadIdx.x; j < K; j += blockDim.x) coef[j] = (double)c[(size_t)t * K + j];
     __syncthreads();
-    const double nrm = sqrt(2.0 / (double)(m + 1));
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
         double v = 0.0;
         for (int j = 0; j < K; ++j) v += coef[j] * sinpi((double)(j + 1) * (i + 1) / (double)(m + 1));
-        x0[(size_t)t * m + i] = v * nrm;
+        x0[(size_t)t * m + i] = v;
     }
 }
 

@@ -35,9 +35,9 @@ def _small_net(m=37, s=8, modes=13, width=8, layers=3, K=5, seed=3):
     return net, shapes
 
 
-def _phi(m, K):
+def _sin(m, K):
     i = np.arange(1, m + 1)
-    return np.sqrt(2.0 / (m + 1)) * np.sin(np.pi * np.outer(np.arange(1, K + 1), i) / (m + 1))
+    return np.sin(np.pi * np.outer(np.arange(1, K + 1), i) / (m + 1))  # K x m
 
 
 def test_forward_and_gradients_match_oracle():
@@ -79,13 +79,14 @@ def test_features_coefficients_and_fp16_inference():
     prob = fi.config_learned_family(seed=11, m=63, s=16)
     K = 12
     net, shapes = _small_net(m=63, s=16, modes=K, width=16, layers=4)
-    Phi = _phi(prob.m, K)
+    S = _sin(prob.m, K)
+    an = 2.0 / (prob.m + 1)  # series coefficients c = an * v S^T, synthesis v = c S
     with FDEProblem.from_inputs(prob) as p:
         p.assemble()
         feat = torch.empty(net.cin * K, dtype=torch.float32, device="cuda")
         net.features(p.h, feat)
         f = feat.cpu().numpy().reshape(net.cin, K)
-        spec = np.concatenate([prob.u0[None], prob.f]) @ Phi.T  # (s+2) x K sine coefficients
+        spec = an * np.concatenate([prob.u0[None], prob.f]) @ S.T  # (s+2) x K sine-series coefficients
         ref = np.concatenate([spec, np.full((1, K), (prob.alpha - 1.5) / 0.4),
                               np.full((1, K), (prob.dplus.mean() - 1.25) / 0.75),
                               np.full((1, K), (prob.dminus.mean() - 1.25) / 0.75),
@@ -96,14 +97,14 @@ def test_features_coefficients_and_fp16_inference():
         coef = torch.empty(prob.s * K, dtype=torch.float32, device="cuda")
         net.coefficients(xv, coef)
         X = xv.cpu().numpy().reshape(prob.s, prob.m)
-        np.testing.assert_allclose(coef.cpu().numpy().reshape(prob.s, K), X @ Phi.T, rtol=1e-5, atol=1e-5)
+        np.testing.assert_allclose(coef.cpu().numpy().reshape(prob.s, K), an * X @ S.T, rtol=1e-5, atol=1e-5)
         back = torch.empty(prob.n, dtype=torch.float64, device="cuda")
         net.synthesize(coef, back)
-        np.testing.assert_allclose(back.cpu().numpy().reshape(prob.s, prob.m), (X @ Phi.T) @ Phi, rtol=0, atol=1e-5)
+        np.testing.assert_allclose(back.cpu().numpy().reshape(prob.s, prob.m), an * (X @ S.T) @ S, rtol=0, atol=1e-5)
         # FP16 inference path against the FP32 forward, both synthesised on the grid
         x0 = torch.empty(prob.n, dtype=torch.float64, device="cuda")
         net.warm_start(p.h, x0)
-        y32 = net.forward(feat, 1).cpu().numpy().reshape(prob.s, K) @ Phi
+        y32 = net.forward(feat, 1).cpu().numpy().reshape(prob.s, K) @ S
         y16 = x0.cpu().numpy().reshape(prob.s, prob.m)
         assert np.abs(y16 - y32).max() <= 1e-2 * max(np.abs(y32).max(), 1e-3)
 
