@@ -38,7 +38,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "tf32", "bf16"])
+    ap.add_argument("--precision", default="tf32", choices=["fp64", "fp32", "tf32", "bf16", "tf32x3"])
     ap.add_argument("--m", type=int, default=2047)
     ap.add_argument("--s", type=int, default=256)
     ap.add_argument("--tol", type=float, default=1e-10)
@@ -130,6 +130,28 @@ def lu_update_flops(mp: int, nblk: int, nb: int = 32) -> float:
         rem = mp - (p + 1) * nb
         tot += 8.0 * nb * rem * rem
         p += 1
+    return tot * nblk
+
+
+def tc_update_flops(mp: int, nblk: int, tb: int = 128) -> float:
+    """Algorithmic flops of the rank-128 tensor-core updates: sum_o 8 TB R_o^2 per block, R_o = mp - o - TB."""
+    tot = 0.0
+    o = 0
+    while o + tb < mp:
+        r = mp - o - tb
+        tot += 8.0 * tb * r * r
+        o += tb
+    return tot * nblk
+
+
+def tc_update_bytes(mp: int, nblk: int, tb: int = 128) -> float:
+    """Algorithmic HBM bytes of the same updates: each trailing C entry (Re, Im FP32) read and written once."""
+    tot = 0.0
+    o = 0
+    while o + tb < mp:
+        r = mp - o - tb
+        tot += 16.0 * r * r
+        o += tb
     return tot * nblk
 
 
@@ -484,22 +506,35 @@ def main():
         roof = {"kernel": "block_trsv_kernel", "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
                 "frac": ach / hbm_peak, "traffic": None, "peak_kind": peak_kind,
                 "algorithmic_bytes_per_launch": per_launch}
-    elif name == "lu_update":
+    elif name == "lu_update" and args.precision in ("fp32", "fp64"):
         flops = lu_update_flops(mp, nblk) * args.steps
         ach = flops / (dom_ms / 1e3) / 1e12
-        if args.precision in ("fp32", "fp64"):
-            peak = FP32_ALU_PEAK_TFLOPS if args.precision == "fp32" else 1.25
-            roof = {"kernel": "lu_update_kernel", "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                    "frac": ach / peak, "traffic": None,
-                    "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz" if args.precision == "fp32"
-                    else "nominal FP64", "algorithmic_flops_per_launch": flops / max(dom_n, 1)}
-        else:
-            ratio = 1.1 / 2.25 if args.precision == "tf32" else 1.0
-            peak = bf16_peak * ratio
-            roof = {"kernel": "lu_update_tc_kernel", "bound": "tensor", "achieved": ach, "peak": peak,
-                    "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
-                    "peak_kind": f"{peak_kind} bf16 x nominal {args.precision}/bf16 ratio",
-                    "algorithmic_flops_per_launch": flops / max(dom_n, 1)}
+        peak = FP32_ALU_PEAK_TFLOPS if args.precision == "fp32" else 1.25
+        roof = {"kernel": "lu_update_kernel", "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None,
+                "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz" if args.precision == "fp32"
+                else "nominal FP64", "algorithmic_flops_per_launch": flops / max(dom_n, 1)}
+    elif name == "lu_tc":
+        flops = tc_update_flops(mp, nblk) * args.steps
+        ach = flops / (dom_ms / 1e3) / 1e12
+        ratio = 1.1 / 2.25 if args.precision in ("tf32", "tf32x3") else 1.0
+        peak = bf16_peak * ratio
+        if args.precision == "tf32x3":
+            flops *= 3  # three TF32 products per complex multiply-add
+        roof = {"kernel": "lu_update_tc2_kernel", "bound": "tensor", "achieved": ach, "peak": peak,
+                "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                "peak_kind": f"{peak_kind} bf16 x nominal {args.precision}/bf16 ratio",
+                "algorithmic_flops_per_launch": flops / max(dom_n, 1)}
+    # the tensor-core update is reported beside the dominant kernel whenever it ran
+    tc_line = None
+    if prof.get("lu_tc", (0, 0))[0] > 0:
+        tms, tn = prof["lu_tc"]
+        tfl = tc_update_flops(mp, nblk) * args.steps * (3 if args.precision == "tf32x3" else 1)
+        ratio = 1.1 / 2.25 if args.precision in ("tf32", "tf32x3") else 1.0
+        tbytes = tc_update_bytes(mp, nblk) * args.steps
+        tc_line = {"kernel": "lu_update_tc2_kernel", "launches_per_step": tn // args.steps,
+                   "ms_per_step": tms / args.steps, "tflops": tfl / (tms / 1e3) / 1e12,
+                   "tensor_peak": bf16_peak * ratio, "c_tile_gbs": tbytes / (tms / 1e3) / 1e9, "hbm_peak": hbm_peak}
     stage_ms = {k: round(v[0] / args.steps, 4) for k, v in prof.items()}
     stage_n = {k: v[1] // args.steps for k, v in prof.items()}
 
@@ -575,7 +610,8 @@ def main():
             "config": workload, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clocks, "iterations": [s["iterations"] for s in stats],
             "rel_residual": stats[-1]["rel_residual"], "rel_residual_oracle_matvec": res_oracle,
-            "plain_fp64": plain, "stage_ms_per_step": stage_ms, "stage_launches_per_step": stage_n,
+            "plain_fp64": plain, "tensor_core_update": tc_line, "stage_ms_per_step": stage_ms,
+            "stage_launches_per_step": stage_n,
             "per_step_ms": per_step,
         }
         print(json.dumps(line))

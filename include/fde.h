@@ -66,6 +66,7 @@ extern "C" {
 #define FDE_FP32 1 /* FP32 factors computed on CUDA cores */
 #define FDE_TF32 2 /* FP32 factors, trailing updates on tcgen05 tensor cores (TF32 in, FP32 acc) */
 #define FDE_BF16 3 /* FP32 factors, trailing updates on tcgen05 tensor cores (BF16 in, FP32 acc) */
+#define FDE_TF32X3 4 /* as FDE_TF32 with split operands (hi + lo): three TF32 products, FP32-level accuracy */
 
 /* Limits of this implementation. */
 #define FDE_MAX_MU 6      /* BVM steps */
@@ -130,7 +131,7 @@ int bvm_assemble(fde_problem* p);
 /* Form and factor the s/2+1 distinct Strang blocks phi_k I - h psi_k J
  * (eq. (1.11), Sec. 3.2) by blocked complex LU without pivoting (the blocks are
  * strictly row diagonally dominant), in the given precision (FDE_FP64, FDE_FP32,
- * FDE_TF32, FDE_BF16).  The library owns the factors (FP64: 16*(s/2+1)*mp^2
+ * FDE_TF32, FDE_BF16, FDE_TF32X3).  The library owns the factors (FP64: 16*(s/2+1)*mp^2
  * bytes, otherwise 8*(s/2+1)*mp^2, mp = m rounded up to 64).  Requires
  * bvm_assemble.  Errors: FDE_ERR_ARG, FDE_ERR_ALLOC, FDE_ERR_SINGULAR,
  * FDE_ERR_STATE, FDE_ERR_CUDA. */
@@ -166,8 +167,8 @@ int fde_batch_create(const fde_problem_desc* descs, int count, void* stream, fde
 /* bvm_assemble for every instance.  Errors: as bvm_assemble. */
 int fde_batch_assemble(fde_batch* b);
 
-/* Factor the Strang blocks of every instance in FDE_FP32, FDE_TF32 or FDE_BF16
- * (FP32 factor storage).  Errors: FDE_ERR_ARG, FDE_ERR_STATE, FDE_ERR_ALLOC,
+/* Factor the Strang blocks of every instance in FDE_FP32, FDE_TF32, FDE_BF16 or
+ * FDE_TF32X3 (FP32 factor storage).  Errors: FDE_ERR_ARG, FDE_ERR_STATE, FDE_ERR_ALLOC,
  * FDE_ERR_SINGULAR, FDE_ERR_TIMEOUT, FDE_ERR_CUDA. */
 int fde_batch_factor(fde_batch* b, int precision);
 
@@ -280,13 +281,14 @@ int fde_problem_sizes(const fde_problem* p, int* m, int* s, int* nblocks);
 #define FDE_STAGE_FORM 1       /* forming the Strang blocks phi_k I - h psi_k J */
 #define FDE_STAGE_LU_DIAG 2    /* LU of the diagonal NB x NB blocks */
 #define FDE_STAGE_LU_PANEL 3   /* panel triangular solves */
-#define FDE_STAGE_LU_UPDATE 4  /* trailing complex GEMM updates (CUDA or tensor cores) */
+#define FDE_STAGE_LU_UPDATE 4  /* complex rank-32 updates on CUDA cores */
 #define FDE_STAGE_TFFT_FWD 5   /* FFT along time */
 #define FDE_STAGE_TRSV 6       /* block forward / backward substitution */
 #define FDE_STAGE_TFFT_INV 7   /* inverse FFT along time */
 #define FDE_STAGE_MATVEC 8     /* M z */
 #define FDE_STAGE_KRYLOV 9     /* Gram-Schmidt, norms, Givens, updates */
-#define FDE_NUM_STAGES 10
+#define FDE_STAGE_LU_TC 10     /* rank-128 trailing updates on tcgen05 (FDE_TF32 / FDE_BF16) */
+#define FDE_NUM_STAGES 11
 
 /* on != 0: record a CUDA event pair around every kernel launch of this problem
  * (on its stream) and clear previous records; on == 0: stop recording.

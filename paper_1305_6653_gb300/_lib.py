@@ -20,8 +20,8 @@ FDE_ERR_STATE = -7
 FDE_ERR_TIMEOUT = -8
 
 FDE_GBDF, FDE_GAM, FDE_ETR = 1, 2, 3
-FDE_FP64, FDE_FP32, FDE_TF32, FDE_BF16 = 0, 1, 2, 3
-PRECISIONS = {"fp64": FDE_FP64, "fp32": FDE_FP32, "tf32": FDE_TF32, "bf16": FDE_BF16}
+FDE_FP64, FDE_FP32, FDE_TF32, FDE_BF16, FDE_TF32X3 = 0, 1, 2, 3, 4
+PRECISIONS = {"fp64": FDE_FP64, "fp32": FDE_FP32, "tf32": FDE_TF32, "bf16": FDE_BF16, "tf32x3": FDE_TF32X3}
 FAMILIES = {"GBDF": FDE_GBDF, "GAM": FDE_GAM, "ETR": FDE_ETR}
 
 ERROR_NAMES = {
@@ -42,7 +42,7 @@ EXPORTED = [
     "fde_nop_destroy", "fde_nop_coefficients", "fde_nop_synthesize",
 ]
 STAGES = ["assemble", "form", "lu_diag", "lu_panel", "lu_update", "tfft_fwd", "trsv", "tfft_inv", "matvec",
-          "krylov"]
+          "krylov", "lu_tc"]
 
 
 class FdeProblemDesc(C.Structure):

@@ -523,8 +523,9 @@ int strang_precond_factor(fde_problem* h, int precision) {
     if (!h) return set_error(FDE_ERR_ARG, "NULL problem");
     Problem& P = h->P;
     if (!P.assembled) return set_error(FDE_ERR_STATE, "bvm_assemble must run before strang_precond_factor");
-    if (precision != FDE_FP64 && precision != FDE_FP32 && precision != FDE_TF32 && precision != FDE_BF16)
-        return set_error(FDE_ERR_ARG, "precision must be FDE_FP64, FDE_FP32, FDE_TF32 or FDE_BF16");
+    if (precision != FDE_FP64 && precision != FDE_FP32 && precision != FDE_TF32 && precision != FDE_BF16 &&
+        precision != FDE_TF32X3)
+        return set_error(FDE_ERR_ARG, "precision must be FDE_FP64, FDE_FP32, FDE_TF32, FDE_BF16 or FDE_TF32X3");
     int rc = ensure_factor_buffers(P, precision);
     if (rc) return rc;
     P.factored = false;

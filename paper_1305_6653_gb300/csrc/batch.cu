@@ -141,9 +141,9 @@ int fde_batch_assemble(fde_batch* b) {
 int fde_batch_factor(fde_batch* b, int precision) {
     if (!b) return set_error(FDE_ERR_ARG, "NULL batch");
     if (!b->assembled) return set_error(FDE_ERR_STATE, "fde_batch_assemble must run first");
-    if (precision != FDE_FP32 && precision != FDE_TF32 && precision != FDE_BF16)
-        return set_error(FDE_ERR_ARG, "batched factorisation supports FDE_FP32, FDE_TF32 and FDE_BF16");
-    const int kind = precision == FDE_TF32 ? 0 : (precision == FDE_BF16 ? 1 : -1);
+    if (precision != FDE_FP32 && precision != FDE_TF32 && precision != FDE_BF16 && precision != FDE_TF32X3)
+        return set_error(FDE_ERR_ARG, "batched factorisation supports FDE_FP32, FDE_TF32, FDE_BF16 and FDE_TF32X3");
+    const int kind = precision == FDE_FP32 ? -1 : 0;  // >= 0: tensor-core path with packed operands
     // buffers and the block table
     std::vector<BlkDev> blks;
     size_t pack_total = 0;

@@ -244,14 +244,14 @@ __device__ __forceinline__ void panel_body(int mp, int od, int rb, int rend, int
                     const float vr = (float)X[qq][c].x, vi = (float)X[qq][c].y;
                     if (rows) {
                         unsigned char* t = apack + (size_t)tile * Cfg::A_TILE;
-                        pack2_store<PACK>(t, T2_BM, rt, kq + c, vr);
-                        pack2_store<PACK>(t, T2_BM, rt, TB + kq + c, vi);
+                        pack2_store<PACK>(t, T2_BM, rt, kq + c, vr, false);
+                        pack2_store<PACK>(t, T2_BM, rt, TB + kq + c, vi, false);
                     } else {
                         unsigned char* t = bpack + (size_t)tile * Cfg::B_TILE;
-                        pack2_store<PACK>(t, 2 * T2_BN, rt, kq + c, vr);  // Re output: Re L Re U - Im L Im U
-                        pack2_store<PACK>(t, 2 * T2_BN, rt, TB + kq + c, -vi);
-                        pack2_store<PACK>(t, 2 * T2_BN, T2_BN + rt, kq + c, vi);  // Im output
-                        pack2_store<PACK>(t, 2 * T2_BN, T2_BN + rt, TB + kq + c, vr);
+                        pack2_store<PACK>(t, 2 * T2_BN, rt, kq + c, vr, true);  // Re output: Re L Re U - Im L Im U
+                        pack2_store<PACK>(t, 2 * T2_BN, rt, TB + kq + c, -vi, true);
+                        pack2_store<PACK>(t, 2 * T2_BN, T2_BN + rt, kq + c, vi, true);  // Im output
+                        pack2_store<PACK>(t, 2 * T2_BN, T2_BN + rt, TB + kq + c, vr, true);
                     }
                 }
             }
@@ -735,7 +735,7 @@ static int run_lu_tc(Problem& P, cudaStream_t st) {
             }
         }
         const int nt = cdiv(mp - R0, T2_BM);
-        StageTimer t(P, FDE_STAGE_LU_UPDATE);
+        StageTimer t(P, FDE_STAGE_LU_TC);
         lu_update_tc2_kernel<KIND><<<dim3(nt * nt, nb), 128, Cfg::SMEM, st>>>(mp, R0, nt, fac, apack, bpack, pa, pb,
                                                                              P.d_err);
         FDE_LAUNCH_CHECK("lu_update_tc2_kernel");
@@ -841,6 +841,7 @@ int launch_lu_batched(const BlkDev* d_blk, const std::vector<int>& mp_sorted, in
     if (mp_sorted.empty()) return FDE_OK;
     if (precision == FDE_TF32) return run_lu_batched_tc<0>(d_blk, mp_sorted, err, st);
     if (precision == FDE_BF16) return run_lu_batched_tc<1>(d_blk, mp_sorted, err, st);
+    if (precision == FDE_TF32X3) return run_lu_batched_tc<2>(d_blk, mp_sorted, err, st);
     return run_lu_batched_simt(d_blk, mp_sorted, st);
 }
 
@@ -848,6 +849,7 @@ size_t tc_pack_bytes_per_block(int precision, int mp) {
     size_t pa = 0, pb = 0;
     if (precision == FDE_TF32) tc2_pack_sizes<0>(mp, &pa, &pb);
     else if (precision == FDE_BF16) tc2_pack_sizes<1>(mp, &pa, &pb);
+    else if (precision == FDE_TF32X3) tc2_pack_sizes<2>(mp, &pa, &pb);
     return pa + pb;
 }
 
@@ -855,6 +857,7 @@ size_t tc_pack_a_bytes_per_block(int precision, int mp) {
     size_t pa = 0, pb = 0;
     if (precision == FDE_TF32) tc2_pack_sizes<0>(mp, &pa, &pb);
     else if (precision == FDE_BF16) tc2_pack_sizes<1>(mp, &pa, &pb);
+    else if (precision == FDE_TF32X3) tc2_pack_sizes<2>(mp, &pa, &pb);
     return pa;
 }
 
@@ -872,6 +875,7 @@ int launch_block_lu(Problem& P, int prec, cudaStream_t st) {
     if (prec == FDE_FP64) return run_lu<double>(P, st);
     if (prec == FDE_TF32) return run_lu_tc<0>(P, st);
     if (prec == FDE_BF16) return run_lu_tc<1>(P, st);
+    if (prec == FDE_TF32X3) return run_lu_tc<2>(P, st);
     return run_lu<float>(P, st);
 }
 

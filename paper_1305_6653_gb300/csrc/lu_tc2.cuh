@@ -37,26 +37,30 @@ namespace fde {
 constexpr int TB = 128;             // outer panel width (complex K of the tensor-core update)
 constexpr int T2_BM = 128;          // output rows per CTA
 constexpr int T2_BN = 128;          // complex output columns per CTA (N' = 256)
-constexpr int T2_KP = 2 * TB;       // K' = 256 real
+constexpr int T2_KP = 2 * TB;       // K' = 256 real (one product)
 constexpr int T2_STAGES = 3;
 constexpr int T2_CROW = 528;        // bytes per C-tile row in shared memory (512 + 16 pad, 16-B aligned)
 constexpr int T2_C_BYTES = T2_BM * T2_CROW;  // one plane
 
-template <int KIND>  // 0: TF32, 1: BF16
+// KIND 0: TF32; 1: BF16; 2: split TF32 -- every operand as hi + lo (both TF32) and
+// the product as A_hi B_hi + A_lo B_hi + A_hi B_lo (three K' = 256 segments), which
+// restores FP32-level accuracy at three times the tensor work.
+template <int KIND>
 struct Tc2 {
-    static constexpr int ESZ = KIND == 0 ? 4 : 2;
+    static constexpr int ESZ = KIND == 1 ? 2 : 4;
+    static constexpr int KP = KIND == 2 ? 3 * T2_KP : T2_KP;  // K' of the packed operands
     static constexpr int PER_CORE = 16 / ESZ;   // elements per core-matrix row
     static constexpr int KCH = 64 / ESZ;        // elements per 64-byte K-chunk
-    static constexpr int NCH = T2_KP / KCH;     // chunks per tile
+    static constexpr int NCH = KP / KCH;        // chunks per tile
     static constexpr int A_CHUNK = T2_BM * 64;  // bytes
     static constexpr int B_CHUNK = 2 * T2_BN * 64;
     static constexpr int A_TILE = NCH * A_CHUNK;
     static constexpr int B_TILE = NCH * B_CHUNK;
     static constexpr int STAGE = A_CHUNK + B_CHUNK;
     static constexpr int SMEM = 2 * T2_C_BYTES + T2_STAGES * STAGE;
-    static constexpr int KSTEP = KIND == 0 ? 8 : 16;          // K per MMA = 32 bytes = 2 core matrices
+    static constexpr int KSTEP = KIND == 1 ? 16 : 8;          // K per MMA = 32 bytes = 2 core matrices
     static constexpr int MMAS = KCH / KSTEP;                  // MMAs per chunk (2)
-    static constexpr uint32_t IDESC = tc::instr_desc(KIND == 0 ? 2u : 1u, T2_BM, 2 * T2_BN);
+    static constexpr uint32_t IDESC = tc::instr_desc(KIND == 1 ? 1u : 2u, T2_BM, 2 * T2_BN);
 };
 
 // Byte offset of element (row, kp) of a packed tile whose chunks hold `rows` rows.
@@ -68,12 +72,26 @@ __device__ __forceinline__ uint32_t pack2_off(int rows, int row, int kp) {
 }
 
 template <int KIND>
-__device__ __forceinline__ void pack2_store(unsigned char* tile, int rows, int row, int kp, float v) {
+__device__ __forceinline__ void pack2_raw(unsigned char* tile, int rows, int row, int kp, float v) {
     unsigned char* p = tile + pack2_off<KIND>(rows, row, kp);
-    if (KIND == 0)
-        *reinterpret_cast<float*>(p) = tc::to_tf32(v);
-    else
+    if (KIND == 1)
         *reinterpret_cast<__nv_bfloat16*>(p) = __float2bfloat16_rn(v);
+    else
+        *reinterpret_cast<float*>(p) = tc::to_tf32(v);
+}
+
+// Store value v at K' position kp (< 256) of an A' (b_side = false) or B' tile.
+template <int KIND>
+__device__ __forceinline__ void pack2_store(unsigned char* tile, int rows, int row, int kp, float v, bool b_side) {
+    if constexpr (KIND == 2) {
+        const float hi = tc::to_tf32(v);
+        const float lo = tc::to_tf32(v - hi);
+        pack2_raw<KIND>(tile, rows, row, kp, hi);
+        pack2_raw<KIND>(tile, rows, row, T2_KP + kp, b_side ? hi : lo);
+        pack2_raw<KIND>(tile, rows, row, 2 * T2_KP + kp, b_side ? lo : hi);
+    } else {
+        pack2_raw<KIND>(tile, rows, row, kp, v);
+    }
 }
 
 __device__ __forceinline__ void bulk_s2g(void* dst_gmem, const void* src_smem, uint32_t bytes) {
@@ -157,10 +175,10 @@ __device__ __forceinline__ void tc2_update_body(int mp, int R0, float* __restric
             for (int j = 0; j < Cfg::MMAS; ++j) {
                 const uint64_t ad = tc::smem_desc(a0 + j * 256, 128, 512);
                 const uint64_t bd = tc::smem_desc(b0 + j * 256, 128, 512);
-                if (KIND == 0)
-                    tc::mma_tf32(tbase, ad, bd, Cfg::IDESC, (c > 0 || j > 0) ? 1u : 0u);
-                else
+                if (KIND == 1)
                     tc::mma_f16(tbase, ad, bd, Cfg::IDESC, (c > 0 || j > 0) ? 1u : 0u);
+                else
+                    tc::mma_tf32(tbase, ad, bd, Cfg::IDESC, (c > 0 || j > 0) ? 1u : 0u);
             }
             tc::mma_commit(&bar_empty[s]);
             // refill the stage freed by chunk c-1 with chunk c + STAGES - 1

@@ -44,7 +44,7 @@ def _reference(prob):
     return x
 
 
-@pytest.mark.parametrize("precision", ["fp32", "tf32", "bf16"])
+@pytest.mark.parametrize("precision", ["fp32", "tf32", "bf16", "tf32x3"])
 def test_batch_matches_oracle(precision):
     from paper_1305_6653_gb300 import FDEBatch
     probs = _mixed_batch()
