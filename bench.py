@@ -516,11 +516,11 @@ def main():
                 else "nominal FP64", "algorithmic_flops_per_launch": flops / max(dom_n, 1)}
     elif name == "lu_tc":
         flops = tc_update_flops(mp, nblk) * args.steps
+        if args.precision == "tf32x3":
+            flops *= 3  # three TF32 products per complex multiply-add
         ach = flops / (dom_ms / 1e3) / 1e12
         ratio = 1.1 / 2.25 if args.precision in ("tf32", "tf32x3") else 1.0
         peak = bf16_peak * ratio
-        if args.precision == "tf32x3":
-            flops *= 3  # three TF32 products per complex multiply-add
         roof = {"kernel": "lu_update_tc2_kernel", "bound": "tensor", "achieved": ach, "peak": peak,
                 "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
                 "peak_kind": f"{peak_kind} bf16 x nominal {args.precision}/bf16 ratio",
