@@ -240,8 +240,7 @@ __device__ __forceinline__ void panel_body(int mp, int od, int rb, int rend, int
                 using Cfg = Tc2<PACK>;
                 const int g = b0 + qq - R0;  // position in the outer trailing matrix
                 if (g >= 0) {
-                    const int tw = rows ? T2_BM : T2_BN;  // A' tiles hold 128 rows, B' tiles 64 columns
-                    const int tile = g / tw, rt = g % tw;
+                    const int tile = g / T2_BM, rt = g % T2_BM;
                     const float vr = (float)X[qq][c].x, vi = (float)X[qq][c].y;
                     if (rows) {
                         unsigned char* t = apack + (size_t)tile * Cfg::A_TILE;
@@ -614,21 +613,21 @@ static int run_lu(Problem& P, cudaStream_t st) {
 // ---------------------------------------------------------------------------
 template <int KIND>
 __global__ void __launch_bounds__(128)
-lu_update_tc2_kernel(int mp, int R0, int ntc, float* __restrict__ fac, const unsigned char* __restrict__ apack,
+lu_update_tc2_kernel(int mp, int R0, int nt, float* __restrict__ fac, const unsigned char* __restrict__ apack,
                      const unsigned char* __restrict__ bpack, size_t pa, size_t pb, int* __restrict__ err) {
     const int k = blockIdx.y;
     tc2_update_body<KIND>(mp, R0, fac + (size_t)k * 2 * mp * mp, apack + k * pa, bpack + k * pb, err,
-                          blockIdx.x / ntc, blockIdx.x % ntc);
+                          blockIdx.x / nt, blockIdx.x % nt);
 }
 
 template <int KIND>
 __global__ void __launch_bounds__(128)
-lu_update_tc2_batched(const BlkDev* __restrict__ B, int R0, int ntgc, int* __restrict__ err) {
+lu_update_tc2_batched(const BlkDev* __restrict__ B, int R0, int ntg, int* __restrict__ err) {
     const BlkDev& d = B[blockIdx.y];
     if (R0 >= d.mp) return;
-    const int ntr = (d.mp - R0 + T2_BM - 1) / T2_BM, ntc = (d.mp - R0 + T2_BN - 1) / T2_BN;
-    const int ti = blockIdx.x / ntgc, tj = blockIdx.x % ntgc;
-    if (ti >= ntr || tj >= ntc) return;
+    const int nt = (d.mp - R0 + T2_BM - 1) / T2_BM;
+    const int ti = blockIdx.x / ntg, tj = blockIdx.x % ntg;
+    if (ti >= nt || tj >= nt) return;
     tc2_update_body<KIND>(d.mp, R0, (float*)d.fac, d.apack, d.bpack, err, ti, tj);
 }
 
@@ -656,10 +655,9 @@ static int set_tc_attrs() {
 // Packed operand bytes per block (A' tiles then B' tiles) for a block of size mp.
 template <int KIND>
 static void tc2_pack_sizes(int mp, size_t* pa, size_t* pb) {
-    const int ntr = mp > TB ? (mp - TB + T2_BM - 1) / T2_BM : 0;
-    const int ntc = mp > TB ? (mp - TB + T2_BN - 1) / T2_BN : 0;
-    *pa = (size_t)ntr * Tc2<KIND>::A_TILE;
-    *pb = (size_t)ntc * Tc2<KIND>::B_TILE;
+    const int ntile = mp > TB ? (mp - TB + T2_BM - 1) / T2_BM : 0;
+    *pa = (size_t)ntile * Tc2<KIND>::A_TILE;
+    *pb = (size_t)ntile * Tc2<KIND>::B_TILE;
 }
 
 template <int KIND>
@@ -736,10 +734,10 @@ static int run_lu_tc(Problem& P, cudaStream_t st) {
                 FDE_LAUNCH_CHECK("lu_update_range_kernel");
             }
         }
-        const int ntr = cdiv(mp - R0, T2_BM), ntc = cdiv(mp - R0, T2_BN);
+        const int nt = cdiv(mp - R0, T2_BM);
         StageTimer t(P, FDE_STAGE_LU_TC);
-        lu_update_tc2_kernel<KIND><<<dim3(ntr * ntc, nb), 128, Cfg::SMEM, st>>>(mp, R0, ntc, fac, apack, bpack, pa,
-                                                                               pb, P.d_err);
+        lu_update_tc2_kernel<KIND><<<dim3(nt * nt, nb), 128, Cfg::SMEM, st>>>(mp, R0, nt, fac, apack, bpack, pa, pb,
+                                                                             P.d_err);
         FDE_LAUNCH_CHECK("lu_update_tc2_kernel");
     }
     return FDE_OK;
@@ -831,8 +829,8 @@ static int run_lu_batched_tc(const BlkDev* d_blk, const std::vector<int>& mps, i
                 FDE_LAUNCH_CHECK("lu_update_range_batched");
             }
         }
-        const int ntgr = cdiv(top - R0, T2_BM), ntgc = cdiv(top - R0, T2_BN);
-        lu_update_tc2_batched<KIND><<<dim3(ntgr * ntgc, nt_blocks), 128, Cfg::SMEM, st>>>(d_blk, R0, ntgc, err);
+        const int ntg = cdiv(top - R0, T2_BM);
+        lu_update_tc2_batched<KIND><<<dim3(ntg * ntg, nt_blocks), 128, Cfg::SMEM, st>>>(d_blk, R0, ntg, err);
         FDE_LAUNCH_CHECK("lu_update_tc2_batched");
     }
     return FDE_OK;

@@ -8,21 +8,20 @@
 // whole rank-128 update A22 -= L21 U12 in ONE complex GEMM with K' = 2 x 128 on
 // tcgen05 -- four times fewer passes over the trailing matrix than NB = 32.
 //
-// Complex product as one real GEMM (N' = 2 x 64 outputs side by side):
+// Complex product as one real GEMM (N' = 2 x 128 outputs side by side):
 //   A' = [Re L21 | Im L21]                                  128 rows x K' = 256
-//   B' = [[Re U12 ; -Im U12] | [Im U12 ; Re U12]]^T        128 rows x K' (64 columns)
-//   D  = A' B'^T:  D[:, 0:64] = Re(L21 U12),  D[:, 64:128] = Im(L21 U12).
+//   B' = [[Re U12 ; -Im U12] | [Im U12 ; Re U12]]^T        256 rows x K'
+//   D  = A' B'^T:  D[:, 0:128] = Re(L21 U12),  D[:, 128:256] = Im(L21 U12).
 // The panel kernels write A' and B' pre-packed as K-chunks of 64 bytes per row,
 // each chunk in the canonical no-swizzle K-major core-matrix layout (8 rows x 16 B
 // core matrices, LBO = 128 B along K, SBO = 512 B between 8-row groups), so one
 // bulk copy lands a chunk of a tile in shared memory.
 //
-// The update kernel (one 128 x 64 complex output tile per CTA, 128 threads, two
-// CTAs per SM):
+// The update kernel (one 128 x 128 complex output tile per CTA, 128 threads):
 //   * issues bulk copies of its C tile (Re and Im rows) into shared memory at
 //     once, so the read of C overlaps the whole main loop;
-//   * streams the K-chunks through a 2-stage full / empty mbarrier ring, one
-//     thread issuing the MMAs (M = 128, N = 128, accumulator in 128 TMEM columns);
+//   * streams the K-chunks through a 3-stage full / empty mbarrier ring, one
+//     thread issuing the MMAs (M = 128, N = 256, accumulator in 256 TMEM columns);
 //   * subtracts D (tcgen05.ld) from the C tile in shared memory and writes the
 //     tile back with bulk copies.
 // Every mbarrier wait is bounded; on timeout the CTA records an error, waits
@@ -37,11 +36,10 @@ namespace fde {
 
 constexpr int TB = 128;             // outer panel width (complex K of the tensor-core update)
 constexpr int T2_BM = 128;          // output rows per CTA
-constexpr int T2_BN = 64;           // complex output columns per CTA (N' = 128)
+constexpr int T2_BN = 128;          // complex output columns per CTA (N' = 256)
 constexpr int T2_KP = 2 * TB;       // K' = 256 real (one product)
-constexpr int T2_STAGES = 2;
-constexpr int T2_CROW = T2_BN * 4 + 16;  // bytes per C-tile row in shared memory (+16 pad: conflict-free, 16-B aligned)
-constexpr int T2_TMEM = 2 * T2_BN;       // accumulator columns (Re | Im)
+constexpr int T2_STAGES = 3;
+constexpr int T2_CROW = 528;        // bytes per C-tile row in shared memory (512 + 16 pad, 16-B aligned)
 constexpr int T2_C_BYTES = T2_BM * T2_CROW;  // one plane
 
 // KIND 0: TF32; 1: BF16; 2: split TF32 -- every operand as hi + lo (both TF32) and
@@ -105,8 +103,8 @@ __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.comm
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// Outer trailing update of one 128 x 64 complex tile (ti, tj) of one block:
-// C[r0.., c0..] -= D, r0 = R0 + 128 ti, c0 = R0 + 64 tj.
+// Outer trailing update of one 128 x 128 complex tile (ti, tj) of one block:
+// C[r0.., c0..] -= D, r0 = R0 + 128 ti, c0 = R0 + 128 tj.
 template <int KIND>
 __device__ __forceinline__ void tc2_update_body(int mp, int R0, float* __restrict__ re_plane,
                                                 const unsigned char* __restrict__ apack,
@@ -131,7 +129,7 @@ __device__ __forceinline__ void tc2_update_body(int mp, int R0, float* __restric
     const unsigned char* ga = apack + (size_t)ti * Cfg::A_TILE;
     const unsigned char* gb = bpack + (size_t)tj * Cfg::B_TILE;
 
-    if (warp == 0) tc::tmem_alloc(&tmem_base, T2_TMEM);
+    if (warp == 0) tc::tmem_alloc(&tmem_base, 256);
     if (threadIdx.x == 0) {
         tc::mbar_init(&bar_c, 1);
         tc::mbar_init(&bar_mma, 1);
@@ -249,7 +247,7 @@ __device__ __forceinline__ void tc2_update_body(int mp, int R0, float* __restric
     }
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tbase, T2_TMEM);
+    if (warp == 0) tc::tmem_dealloc(tbase, 256);
 }
 
 }  // namespace fde
