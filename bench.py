@@ -46,9 +46,10 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
-    ap.add_argument("--config", choices=["scale", "batch", "learned"], default="scale",
+    ap.add_argument("--config", choices=["scale", "batch", "learned", "precision"], default="scale",
                     help="scale: one m=2047/s=256 instance per step; batch: 64 uneven instances per step; "
-                         "learned: train the warm-start operator on m=1023/s=256 solves, then compare guesses")
+                         "learned: train the warm-start operator on m=1023/s=256 solves, then compare guesses; "
+                         "precision: m=4095/s=128, alpha=1.9, every preconditioner precision")
     ap.add_argument("--train", type=int, default=4096, help="learned: method-generated training solves")
     ap.add_argument("--epochs", type=int, default=40, help="learned: passes over the training set")
     ap.add_argument("--eval", type=int, default=32, help="learned: held-out instances")
@@ -306,6 +307,72 @@ def bench_batch(args, world, rank, local_rank):
 
 
 # ---------------------------------------------------------------------------
+# precision study: one m=4095/s=128 instance, every preconditioner precision
+# ---------------------------------------------------------------------------
+
+def bench_precision(args, world, rank, local_rank):
+    import numpy as np
+    import torch
+
+    import fde_inputs
+    import paper_1305_6653_gb300 as fde
+
+    torch.cuda.set_device(local_rank)
+    prob = fde_inputs.config_precision()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    xbuf = torch.empty(prob.n, dtype=torch.float64, device="cuda")
+    p = fde.FDEProblem.from_inputs(prob, device_inputs=True)
+
+    def step(precision):
+        p.assemble().factor(precision)
+        _, st = p.solve(tol=args.tol, restart=20, maxit=400, out=xbuf)
+        return st
+
+    variants, sols = {}, {}
+    l0 = fde.fde_launch_count()
+    sampler = ClockSampler(local_rank)
+    if not args.no_clocks:
+        sampler.start()
+    for prec in ("fp64", "fp32", "tf32", "tf32x3", "bf16"):
+        for _ in range(args.warmup):
+            step(prec)
+        times, st = [], None
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            st = step(prec)
+            e1.record()
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        ms = sum(times) / len(times)
+        sols[prec] = xbuf.cpu().numpy()
+        variants[prec] = {"solves_per_s": 1e3 / ms, "ms_per_step": ms, "iterations": st["iterations"],
+                          "rel_residual": st["rel_residual"]}
+    clocks = sampler.stop() if not args.no_clocks else None
+    launches = fde.fde_launch_count() - l0
+    p.close()
+    ref = sols["fp64"]
+    for prec, v in variants.items():
+        v["rel_diff_vs_gpu_fp64"] = float(np.linalg.norm(sols[prec] - ref) / np.linalg.norm(ref))
+    head = variants[args.precision]
+    if rank == 0:
+        line = {"metric": METRIC, "value": world * head["solves_per_s"], "unit": "solves/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+                "data": "synthetic",
+                "config": {"workload": f"precision_m{prob.m}_s{prob.s}_gbdf3_alpha1.9", "m": prob.m, "s": prob.s,
+                           "unknowns": prob.n, "precision": args.precision, "tol_true_residual": args.tol,
+                           "restart": 20, "l2": "flushed (512 MiB write) before every timed step"},
+                "roofline": None, "gpu_launches": launches, "clocks": clocks,
+                "variants": variants,
+                "note": "rel_diff_vs_gpu_fp64 compares with the FP64 GPU solve of the same run; the error of "
+                        "every variant against the CPU oracle is checked by tests/test_gpu_precision.py"}
+        print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------
 # learned warm start: train on method-generated solves, compare initial guesses
 # ---------------------------------------------------------------------------
 
@@ -402,6 +469,8 @@ def main():
         return bench_batch(args, world, rank, local_rank)
     if args.config == "learned" and args.impl == "ours":
         return bench_learned(args, world, rank, local_rank)
+    if args.config == "precision" and args.impl == "ours":
+        return bench_precision(args, world, rank, local_rank)
     prob = fde_inputs.config_scale(args.m, args.s)
     workload = {"workload": f"scale_m{args.m}_s{args.s}_gbdf5_alpha1.8_variable_d", "m": args.m, "s": args.s,
                 "unknowns": args.m * args.s, "scheme": "GBDF5", "alpha": 1.8, "d": "d+=1+x, d-=2-x",

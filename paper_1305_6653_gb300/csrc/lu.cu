@@ -404,14 +404,28 @@ __global__ void __launch_bounds__(256) lu_update_batched(const BlkDev* __restric
     update_body<T>(d.mp, p * NB, (p + 1) * NB + ti * 64, (p + 1) * NB + tj * 64, d.mp, d.mp, (T*)d.fac);
 }
 
-// Forward (unit lower L) then backward (U) substitution for one block per CTA,
-// in place on rhat[k] (length mp), column-oriented ("right-looking"): for each
-// 32-row diagonal tile, warp 0 resolves the tile from shared memory, then all
-// warps subtract the tile's 32-column strip of L (or U) times the new 32 values
-// from the remaining right-hand side.  In the strip update eight threads share a
-// row (one contiguous 32-value segment per plane), every load is independent of
-// the others, and the next diagonal tile is prefetched into shared memory, so
-// the factor planes stream at full memory-level parallelism.
+// Forward (unit lower L) then backward (U) substitution for one block per CTA, in
+// place on rhat[k] (length mp), column-oriented over 32-row tiles.  Step d of a
+// sweep resolves tile T(d) (T(d) = d forward, nt-1-d backward) and subtracts the
+// 32-column strip of L (U) below (above) it, times the 32 new values, from the
+// remaining right-hand side.
+//
+// The dependency chain (tile d needs the strips of every earlier tile) is kept off
+// the warps that stream the factor planes:
+//   * warp 0, the solver, resolves the diagonal tiles.  Before solving tile d it
+//     applies strip d-1 to tile d's own rows itself (look-ahead), so it only needs
+//     the streaming warps to have finished tile d's rows of strips <= d-2.  Its
+//     diagonal and look-ahead tiles arrive by cp.async two steps ahead.
+//   * warps 1..15 stream strip d over the rows of tiles d+2, d+3, ... (tile d+2
+//     first), eight threads per row, each factor element read once with 16-byte
+//     streaming loads.  The loads of a strip's first batch are issued before the
+//     wait for its 32 values, so the memory pipe does not drain between strips.
+// The two sides hand over through named barriers (producer arrives, consumer
+// syncs): X[d&1] -- x_d is in shared memory; B[d&1] -- strip d has reached every
+// row of tile d+2.  A barrier id is reused only every other step, after its
+// previous phase has completed (the solver passes B of step d before it arrives on
+// X of step d+2; the streaming warps pass X of step d+2 before they arrive on B of
+// step d+2), so phases never mix.  All waits are hardware barriers of this CTA.
 struct dvec4 {
     double x, y, z, w;
 };
@@ -419,62 +433,194 @@ template <typename T> struct vec4;
 template <> struct vec4<float> { using type = float4; };
 template <> struct vec4<double> { using type = dvec4; };
 
-__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+// Streaming loads (the factor planes are read once per solve).
+__device__ __forceinline__ float4 ld4(const float* p) { return __ldcs(reinterpret_cast<const float4*>(p)); }
 __device__ __forceinline__ dvec4 ld4(const double* p) {
-    const double2 a = reinterpret_cast<const double2*>(p)[0];
-    const double2 b = reinterpret_cast<const double2*>(p)[1];
+    const double2 a = __ldcs(reinterpret_cast<const double2*>(p));
+    const double2 b = __ldcs(reinterpret_cast<const double2*>(p) + 1);
     return dvec4{a.x, a.y, b.x, b.y};
 }
 
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void named_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+__device__ __forceinline__ void named_arrive(int id, int n) {
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
 constexpr int TRSV_THREADS = 512;
-constexpr int TRSV_TPR = 8;                              // threads per row in the strip update
-constexpr int TRSV_RPP = TRSV_THREADS / TRSV_TPR;        // rows per pass
+constexpr int TRSV_TPR = 8;                                  // threads per row in the strip update
+constexpr int TRSV_GROUPS = (TRSV_THREADS - 32) / TRSV_TPR;  // 60 row groups in warps 1..15
+constexpr int TRSV_BAR_X = 1, TRSV_BAR_B = 3;                // named barrier ids (+ d & 1)
+// Rows per group whose loads are in flight together: 8 x 2 x 16 B per thread for
+// FP32 factors; FP64 rows are twice as wide per element, 4 keep it spill-free.
+template <typename T> struct trsv_unroll { static constexpr int value = sizeof(T) == 4 ? 8 : 4; };
+// Solver tiles in shared memory: planar, rows padded by 16 bytes (16-byte aligned
+// cp.async destinations); [buffer 2][D, L][Re, Im][32][LD].
+template <typename T> struct trsv_tile { static constexpr int LD = 32 + 16 / (int)sizeof(T); };
+
+static size_t trsv_smem_bytes(int mp, size_t elem) {
+    const size_t ld = 32 + 16 / elem;
+    return (size_t)mp * 2 * elem + 8 * 32 * ld * elem;
+}
 
 template <typename T>
-__device__ __forceinline__ void load_diag_tile(cplx_t<T> (*D)[33], const T* re, const T* im, int mp, int r0) {
-    for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
-        const int q = e >> 5, c = e & 31;
-        const size_t idx = (size_t)(r0 + q) * mp + r0 + c;
-        D[q][c] = mk(re[idx], im[idx]);
+__device__ __forceinline__ void tile_async(T* dst, const T* plane, int mp, int r0, int c0, int lane) {
+    constexpr int EPC = 16 / (int)sizeof(T), CPR = 32 / EPC, LD = trsv_tile<T>::LD;
+    for (int e = lane; e < 32 * CPR; e += 32) {
+        const int r = e / CPR, ch = e % CPR;
+        cp_async16(dst + r * LD + ch * EPC, plane + (size_t)(r0 + r) * mp + c0 + ch * EPC);
     }
 }
 
-// y[rows] -= strip[rows][c0 .. c0+32) * xs[0..32), rows in [rbeg, rend)
-template <typename T>
-__device__ __forceinline__ void strip_update(cplx_t<T>* y, const cplx_t<T>* xs, const T* re, const T* im, int mp,
-                                             int c0, int rbeg, int rend) {
+// Solver side of one sweep (warp 0).
+template <typename T, bool FWD>
+__device__ __forceinline__ void trsv_solver(int mp, int nt, const T* re, const T* im, const cplx_t<T>* dv,
+                                            cplx_t<T>* y, cplx_t<T> (*xs)[32], T* tiles, int lane) {
     using C = cplx_t<T>;
-    const int sub = threadIdx.x & (TRSV_TPR - 1);
-    const int c = c0 + sub * 4;
-    const C x0 = xs[sub * 4], x1 = xs[sub * 4 + 1], x2 = xs[sub * 4 + 2], x3 = xs[sub * 4 + 3];
-    for (int rb = rbeg + (int)(threadIdx.x / TRSV_TPR); rb < rend; rb += 4 * TRSV_RPP) {
-        typename vec4<T>::type ar[4], ai[4];
+    constexpr int LD = trsv_tile<T>::LD, TS = 32 * LD;
+    auto tile_of = [&](int d) { return FWD ? d : nt - 1 - d; };
+    auto issue = [&](int d) {
+        T* b = tiles + (d & 1) * 4 * TS;  // [D re, D im, L re, L im]
+        const int j = tile_of(d);
+        tile_async<T>(b, re, mp, 32 * j, 32 * j, lane);
+        tile_async<T>(b + TS, im, mp, 32 * j, 32 * j, lane);
+        if (d >= 1) {
+            tile_async<T>(b + 2 * TS, re, mp, 32 * j, 32 * tile_of(d - 1), lane);
+            tile_async<T>(b + 3 * TS, im, mp, 32 * j, 32 * tile_of(d - 1), lane);
+        }
+    };
+    issue(0);
+    cp_async_commit();
+    if (nt > 1) issue(1);
+    cp_async_commit();
+    for (int d = 0; d < nt; ++d) {
+        const int r0 = 32 * tile_of(d);
+        const T* Dre = tiles + (d & 1) * 4 * TS;
+        const T* Dim = Dre + TS;
+        const T* Lre = Dre + 2 * TS;
+        const T* Lim = Dre + 3 * TS;
+        cp_async_wait1();
+        __syncwarp();
+        if (d >= 2) named_sync(TRSV_BAR_B + (d & 1), TRSV_THREADS);  // strip d-2 has reached tile d
+        C a = y[r0 + lane];
+        if (d >= 1) {  // look-ahead: strip d-1 on tile d's rows
+            const C* xp = xs[(d - 1) & 1];
+            T sx0 = 0, sy0 = 0, sx1 = 0, sy1 = 0;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int r = rb + u * TRSV_RPP;
-            if (r < rend) {
-                ar[u] = ld4(re + (size_t)r * mp + c);
-                ai[u] = ld4(im + (size_t)r * mp + c);
+            for (int c = 0; c < 32; c += 2) {
+                const C x0 = xp[c], x1 = xp[c + 1];
+                const T l0r = Lre[lane * LD + c], l0i = Lim[lane * LD + c];
+                const T l1r = Lre[lane * LD + c + 1], l1i = Lim[lane * LD + c + 1];
+                sx0 += l0r * x0.x - l0i * x0.y;
+                sy0 += l0r * x0.y + l0i * x0.x;
+                sx1 += l1r * x1.x - l1i * x1.y;
+                sy1 += l1r * x1.y + l1i * x1.x;
+            }
+            a.x -= sx0 + sx1;
+            a.y -= sy0 + sy1;
+        }
+        if (FWD) {
+#pragma unroll 8
+            for (int c = 0; c < 32; ++c) {
+                const T yx = __shfl_sync(0xffffffffu, a.x, c);
+                const T yy = __shfl_sync(0xffffffffu, a.y, c);
+                if (lane > c) {
+                    const T lr = Dre[lane * LD + c], li = Dim[lane * LD + c];
+                    a.x -= lr * yx - li * yy;
+                    a.y -= lr * yy + li * yx;
+                }
+            }
+        } else {
+            const C di = dv[r0 + lane];
+#pragma unroll 8
+            for (int c = 31; c >= 0; --c) {
+                if (lane == c) a = cmul(a, di);
+                const T yx = __shfl_sync(0xffffffffu, a.x, c);
+                const T yy = __shfl_sync(0xffffffffu, a.y, c);
+                if (lane < c) {
+                    const T ur = Dre[lane * LD + c], ui = Dim[lane * LD + c];
+                    a.x -= ur * yx - ui * yy;
+                    a.y -= ur * yy + ui * yx;
+                }
             }
         }
+        y[r0 + lane] = a;
+        xs[d & 1][lane] = a;
+        __syncwarp();
+        if (d <= nt - 3) named_arrive(TRSV_BAR_X + (d & 1), TRSV_THREADS);
+        if (d + 2 < nt) issue(d + 2);  // buffer d & 1 is free again
+        cp_async_commit();
+    }
+}
+
+// Streaming side of one sweep (warps 1..15): strip d over rows of tiles >= d+2.
+// Row index q in [0, len) maps to row lo + q forward and hi - 1 - q backward, so
+// tile d+2's rows are q < 32 in both directions.  The four groups of a warp hold
+// q values of one aligned quartet and len is a multiple of 32, so loop exits and
+// the shuffles stay warp-uniform.
+template <typename T, bool FWD>
+__device__ __forceinline__ void trsv_stream(int mp, int nt, const T* re, const T* im, cplx_t<T>* y,
+                                            const cplx_t<T> (*xs)[32], int bt) {
+    using C = cplx_t<T>;
+    using V = typename vec4<T>::type;
+    constexpr int U = trsv_unroll<T>::value;
+    const int g = bt / TRSV_TPR, sub = bt % TRSV_TPR;
+    for (int d = 0; d + 2 < nt; ++d) {
+        const int col = 32 * (FWD ? d : nt - 1 - d) + sub * 4;
+        const int lo = FWD ? 32 * (d + 2) : 0;
+        const int hi = FWD ? mp : 32 * (nt - 2 - d);
+        const int len = hi - lo;
+        V ar[U], ai[U];
+        auto load = [&](int q0) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int r = rb + u * TRSV_RPP;
-            T sx = ar[u].x * x0.x - ai[u].x * x0.y + ar[u].y * x1.x - ai[u].y * x1.y + ar[u].z * x2.x -
-                   ai[u].z * x2.y + ar[u].w * x3.x - ai[u].w * x3.y;
-            T sy = ar[u].x * x0.y + ai[u].x * x0.x + ar[u].y * x1.y + ai[u].y * x1.x + ar[u].z * x2.y +
-                   ai[u].z * x2.x + ar[u].w * x3.y + ai[u].w * x3.x;
+            for (int u = 0; u < U; ++u) {
+                const int q = q0 + u * TRSV_GROUPS;
+                if (q < len) {
+                    const int r = FWD ? lo + q : hi - 1 - q;
+                    ar[u] = ld4(re + (size_t)r * mp + col);
+                    ai[u] = ld4(im + (size_t)r * mp + col);
+                }
+            }
+        };
+        C x0, x1, x2, x3;
+        auto apply = [&](int q0) {
 #pragma unroll
-            for (int off = 1; off < TRSV_TPR; off <<= 1) {
-                sx += __shfl_xor_sync(0xffffffffu, sx, off);
-                sy += __shfl_xor_sync(0xffffffffu, sy, off);
+            for (int u = 0; u < U; ++u) {
+                const int q = q0 + u * TRSV_GROUPS;
+                T sx = ar[u].x * x0.x - ai[u].x * x0.y + ar[u].y * x1.x - ai[u].y * x1.y + ar[u].z * x2.x -
+                       ai[u].z * x2.y + ar[u].w * x3.x - ai[u].w * x3.y;
+                T sy = ar[u].x * x0.y + ai[u].x * x0.x + ar[u].y * x1.y + ai[u].y * x1.x + ar[u].z * x2.y +
+                       ai[u].z * x2.x + ar[u].w * x3.y + ai[u].w * x3.x;
+#pragma unroll
+                for (int off = 1; off < TRSV_TPR; off <<= 1) {
+                    sx += __shfl_xor_sync(0xffffffffu, sx, off);
+                    sy += __shfl_xor_sync(0xffffffffu, sy, off);
+                }
+                if (sub == 0 && q < len) {
+                    const int r = FWD ? lo + q : hi - 1 - q;
+                    C v = y[r];
+                    v.x -= sx;
+                    v.y -= sy;
+                    y[r] = v;
+                }
             }
-            if (sub == 0 && r < rend) {
-                C v = y[r];
-                v.x -= sx;
-                v.y -= sy;
-                y[r] = v;
-            }
+        };
+        load(g);  // independent of x_d: in flight across the wait
+        named_sync(TRSV_BAR_X + (d & 1), TRSV_THREADS);
+        x0 = xs[d & 1][sub * 4];
+        x1 = xs[d & 1][sub * 4 + 1];
+        x2 = xs[d & 1][sub * 4 + 2];
+        x3 = xs[d & 1][sub * 4 + 3];
+        apply(g);  // covers q < 32 (tile d+2): groups 0..31, u = 0
+        named_arrive(TRSV_BAR_B + (d & 1), TRSV_THREADS);
+        for (int q0 = g + U * TRSV_GROUPS; q0 < len; q0 += U * TRSV_GROUPS) {
+            load(q0);
+            apply(q0);
         }
     }
 }
@@ -484,67 +630,20 @@ __device__ __forceinline__ void trsv_body(int mp, const T* __restrict__ re, cons
                                           cplx_t<T>* __restrict__ x) {
     using C = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* y = reinterpret_cast<C*>(smem_raw);                        // mp
-    C (*D)[32][33] = reinterpret_cast<C (*)[32][33]>(y + mp);     // 2 diagonal tiles (double buffer)
-    __shared__ C xs[32];
+    C* y = reinterpret_cast<C*>(smem_raw);        // mp
+    T* tiles = reinterpret_cast<T*>(y + mp);      // solver tiles
+    __shared__ C xs[2][32];
     const T* im = re + (size_t)mp * mp;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nt = mp / 32;
     for (int i = threadIdx.x; i < mp; i += blockDim.x) y[i] = x[i];
-    load_diag_tile<T>(D[0], re, im, mp, 0);
     __syncthreads();
-    // forward: y <- L^{-1} y
-    for (int t = 0; t < nt; ++t) {
-        const int r0 = t * 32;
-        if (warp == 0) {
-            C a = y[r0 + lane];
-            for (int c = 0; c < 32; ++c) {
-                const T yx = __shfl_sync(0xffffffffu, a.x, c);
-                const T yy = __shfl_sync(0xffffffffu, a.y, c);
-                if (lane > c) {
-                    const C l = D[t & 1][lane][c];
-                    a.x -= l.x * yx - l.y * yy;
-                    a.y -= l.x * yy + l.y * yx;
-                }
-            }
-            y[r0 + lane] = a;
-            xs[lane] = a;
-        }
-        __syncthreads();
-        if (t + 1 < nt) {
-            load_diag_tile<T>(D[(t + 1) & 1], re, im, mp, r0 + 32);
-            strip_update<T>(y, xs, re, im, mp, r0, r0 + 32, mp);
-        }
-        __syncthreads();
-    }
-    // backward: y <- U^{-1} y
-    load_diag_tile<T>(D[(nt - 1) & 1], re, im, mp, (nt - 1) * 32);
+    if (warp == 0) trsv_solver<T, true>(mp, nt, re, im, dv, y, xs, tiles, lane);
+    else trsv_stream<T, true>(mp, nt, re, im, y, xs, threadIdx.x - 32);
     __syncthreads();
-    for (int t = nt - 1; t >= 0; --t) {
-        const int r0 = t * 32;
-        if (warp == 0) {
-            C a = y[r0 + lane];
-            const C di = dv[r0 + lane];
-            for (int c = 31; c >= 0; --c) {
-                if (lane == c) a = cmul(a, di);
-                const T yx = __shfl_sync(0xffffffffu, a.x, c);
-                const T yy = __shfl_sync(0xffffffffu, a.y, c);
-                if (lane < c) {
-                    const C u = D[t & 1][lane][c];
-                    a.x -= u.x * yx - u.y * yy;
-                    a.y -= u.x * yy + u.y * yx;
-                }
-            }
-            y[r0 + lane] = a;
-            xs[lane] = a;
-        }
-        __syncthreads();
-        if (t > 0) {
-            load_diag_tile<T>(D[(t - 1) & 1], re, im, mp, r0 - 32);
-            strip_update<T>(y, xs, re, im, mp, r0, 0, r0);
-        }
-        __syncthreads();
-    }
+    if (warp == 0) trsv_solver<T, false>(mp, nt, re, im, dv, y, xs, tiles, lane);
+    else trsv_stream<T, false>(mp, nt, re, im, y, xs, threadIdx.x - 32);
+    __syncthreads();
     for (int i = threadIdx.x; i < mp; i += blockDim.x) x[i] = y[i];
 }
 
@@ -863,7 +962,7 @@ size_t tc_pack_a_bytes_per_block(int precision, int mp) {
 
 int launch_trsv_batched(const InstDev* I, const int* act, int nact, int max_nblk, int max_mp, cudaStream_t st) {
     if (nact <= 0) return FDE_OK;
-    const size_t smem = ((size_t)max_mp + 2 * 32 * 33) * sizeof(float2);
+    const size_t smem = trsv_smem_bytes(max_mp, sizeof(float));
     FDE_CUDA_TRY(cudaFuncSetAttribute(block_trsv_batched<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
     block_trsv_batched<float><<<dim3(max_nblk, nact), TRSV_THREADS, smem, st>>>(I, act);
@@ -881,13 +980,13 @@ int launch_block_lu(Problem& P, int prec, cudaStream_t st) {
 
 int launch_block_trsv(const Problem& P, void* rhat, cudaStream_t st) {
     if (P.precision == FDE_FP64) {
-        size_t smem = ((size_t)P.mp + 2 * 32 * 33) * sizeof(double2);
+        const size_t smem = trsv_smem_bytes(P.mp, sizeof(double));
         FDE_CUDA_TRY(cudaFuncSetAttribute(block_trsv_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)smem));
         block_trsv_kernel<double><<<P.nblk, TRSV_THREADS, smem, st>>>(P.mp, (const double*)P.d_fac,
                                                                        (const double2*)P.d_dinv, (double2*)rhat);
     } else {
-        size_t smem = ((size_t)P.mp + 2 * 32 * 33) * sizeof(float2);
+        const size_t smem = trsv_smem_bytes(P.mp, sizeof(float));
         FDE_CUDA_TRY(cudaFuncSetAttribute(block_trsv_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)smem));
         block_trsv_kernel<float><<<P.nblk, TRSV_THREADS, smem, st>>>(P.mp, (const float*)P.d_fac,
