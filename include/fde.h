@@ -279,7 +279,7 @@ int fde_problem_sizes(const fde_problem* p, int* m, int* s, int* nblocks);
 /* Stages timed by the per-problem profiler. */
 #define FDE_STAGE_ASSEMBLE 0   /* Grunwald weights, twiddles, symbols, J u0, b */
 #define FDE_STAGE_FORM 1       /* forming the Strang blocks phi_k I - h psi_k J */
-#define FDE_STAGE_LU_DIAG 2    /* LU of the diagonal NB x NB blocks */
+#define FDE_STAGE_LU_DIAG 2    /* LU of the diagonal blocks (NB x NB; 128 x 128 with inverses on tensor-core paths) */
 #define FDE_STAGE_LU_PANEL 3   /* panel triangular solves */
 #define FDE_STAGE_LU_UPDATE 4  /* complex rank-32 updates on CUDA cores */
 #define FDE_STAGE_TFFT_FWD 5   /* FFT along time */
@@ -288,7 +288,9 @@ int fde_problem_sizes(const fde_problem* p, int* m, int* s, int* nblocks);
 #define FDE_STAGE_MATVEC 8     /* M z */
 #define FDE_STAGE_KRYLOV 9     /* Gram-Schmidt, norms, Givens, updates */
 #define FDE_STAGE_LU_TC 10     /* rank-128 trailing updates on tcgen05 (FDE_TF32 / FDE_BF16) */
-#define FDE_NUM_STAGES 11
+#define FDE_STAGE_LU_PACK 11   /* packing panels into tensor-core operand tiles (tensor-core paths) */
+#define FDE_STAGE_LU_PANEL_TC 12 /* panel products L21 = A21 U11^-1, U12 = L11^-1 A12 on tcgen05 */
+#define FDE_NUM_STAGES 13
 
 /* on != 0: record a CUDA event pair around every kernel launch of this problem
  * (on its stream) and clear previous records; on == 0: stop recording.

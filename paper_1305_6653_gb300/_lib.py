@@ -42,7 +42,7 @@ EXPORTED = [
     "fde_nop_destroy", "fde_nop_coefficients", "fde_nop_synthesize",
 ]
 STAGES = ["assemble", "form", "lu_diag", "lu_panel", "lu_update", "tfft_fwd", "trsv", "tfft_inv", "matvec",
-          "krylov", "lu_tc"]
+          "krylov", "lu_tc", "lu_pack", "lu_panel_tc"]
 
 
 class FdeProblemDesc(C.Structure):

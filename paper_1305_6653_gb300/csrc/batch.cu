@@ -193,6 +193,7 @@ int fde_batch_factor(fde_batch* b, int precision) {
             const size_t off = (size_t)d.apack;
             d.apack = b->d_pack + off;
             d.bpack = d.apack + (size_t)d.ntile_max;
+            d.ipack = d.bpack + tc_pack_b_bytes_per_block(precision, d.mp);
         }
     }
     std::stable_sort(blks.begin(), blks.end(), [](const BlkDev& a, const BlkDev& c) { return a.mp > c.mp; });

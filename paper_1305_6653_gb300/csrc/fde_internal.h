@@ -90,6 +90,7 @@ struct BlkDev {
     void* dinv;   // this block's 1/U_ii (mp complex)
     unsigned char* apack;  // this block's packed operand tiles (tensor-core paths)
     unsigned char* bpack;
+    unsigned char* ipack;  // L11^{-1} (A') and U11^{-1} (B') tiles of the current panel
     int* info;
 };
 
@@ -211,6 +212,7 @@ int launch_lu_batched(const BlkDev* d_blk, const std::vector<int>& mp_sorted, in
                       cudaStream_t st);
 size_t tc_pack_bytes_per_block(int precision, int mp);    // packed tensor-core operands of one block
 size_t tc_pack_a_bytes_per_block(int precision, int mp);  // the A' part (B' follows)
+size_t tc_pack_b_bytes_per_block(int precision, int mp);  // the B' part (inverse tiles follow)
 int launch_trsv_batched(const InstDev* I, const int* act, int nact, int max_nblk, int max_mp, cudaStream_t st);
 int launch_time_fft_batched(const InstDev* I, const int* act, int nact, int max_mp, int max_s, int j,
                             cudaStream_t st);

@@ -14,6 +14,8 @@
 //   2. lu_panel:  L21 = A21 U11^{-1} and U12 = L11^{-1} A12 (row / column chunks)
 //   3. lu_update: A22 -= L21 U12 (complex GEMM on CUDA cores; the tensor-core
 //                 variant lives in lu_tc.cu)
+#include <algorithm>
+
 #include "fde_internal.h"
 #include "fft_device.cuh"
 #include "lu_tc2.cuh"
@@ -759,6 +761,301 @@ static void tc2_pack_sizes(int mp, size_t* pa, size_t* pb) {
     *pb = (size_t)ntile * Tc2<KIND>::B_TILE;
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-core panel level of the two-level LU (FDE_TF32 / FDE_BF16 / FDE_TF32X3).
+// Per outer step o (panel width W = 128, trailing matrix from R0 = o + W):
+//   lu_diag128_kernel    L11 U11 = A11 in shared memory; L11^{-1}, U11^{-1} packed
+//   lu_pack_panel_kernel A21 -> A' tiles, A12 -> B' tiles
+//   lu_panel_tc2_kernel  L21 = A21 U11^{-1}, U12 = L11^{-1} A12 (tcgen05, store mode)
+//   lu_pack_panel_kernel L21 -> A' tiles, U12 -> B' tiles
+//   lu_update_tc2_kernel A22 -= L21 U12 (tcgen05)
+// The triangular panel solves become products with the inverted diagonal
+// triangles, so every O(m^2 W) term of the step runs on the tensor cores.
+// ---------------------------------------------------------------------------
+constexpr int D128_LD = TB + 1;  // shared row pitch in floats (column reads conflict-free)
+constexpr int D128_THREADS = 512;
+
+static size_t diag128_smem() { return (size_t)2 * TB * D128_LD * sizeof(float) + (size_t)2 * TB * sizeof(float2); }
+
+// One CTA per Strang block: unblocked LU (no pivoting) of the W x W block at (o, o)
+// (W = 128, or 64 for a last panel), L\U and 1/U_ii written back.  With invert != 0
+// (a trailing matrix follows; W = 128) both triangles are then inverted in place,
+// column j of L^{-1} and row j of U^{-1} at step j = W-1 .. 0:
+//   L^{-1}[i][j] = -(L[i][j] + sum_{j<k<i} L^{-1}[i][k] L[k][j])             (i > j)
+//   U^{-1}[j][c] = -(1/U[j][j]) sum_{j<k<=c} U[j][k] U^{-1}[k][c]            (c > j)
+// and packed: L^{-1} (unit diagonal, zeros above) as the A' tile and U^{-1} (zeros
+// below) as the B' tile of the panel products (layout of lu_tc2.cuh).
+template <int KIND>
+__device__ __forceinline__ void diag128_body(int mp, int o, float* __restrict__ re, float2* __restrict__ dk,
+                                             int* __restrict__ info, unsigned char* __restrict__ pA, bool invert) {
+    using Cfg = Tc2<KIND>;
+    constexpr int LD = D128_LD;
+    extern __shared__ __align__(16) float dsm[];
+    float* Ar = dsm;
+    float* Ai = dsm + TB * LD;
+    float2* tx = reinterpret_cast<float2*>(dsm + 2 * TB * LD);
+    float2* ty = tx + TB;
+    float* im = re + (size_t)mp * mp;
+    const int W = mp - o < TB ? mp - o : TB;
+    const int t = threadIdx.x;
+    for (int e = t; e < W * W; e += blockDim.x) {
+        const int r = e / W, c = e % W;
+        const size_t g = (size_t)(o + r) * mp + o + c;
+        Ar[r * LD + c] = re[g];
+        Ai[r * LD + c] = im[g];
+    }
+    __syncthreads();
+    const int tcol = t & (TB - 1), trow = t >> 7;  // 128 columns x 4 row groups
+    for (int c = 0; c < W; ++c) {
+        const float pr = Ar[c * LD + c], pim = Ai[c * LD + c];
+        const float den = pr * pr + pim * pim;
+        const bool bad = !(den > 0.f) || !isfinite(den);
+        if (bad && t == 0) atomicCAS(info, 0, o + c + 1);
+        const float ir = bad ? 0.f : pr / den, ii = bad ? 0.f : -pim / den;
+        for (int r = c + 1 + t; r < W; r += blockDim.x) {
+            const float ar = Ar[r * LD + c], ai = Ai[r * LD + c];
+            Ar[r * LD + c] = ar * ir - ai * ii;
+            Ai[r * LD + c] = ar * ii + ai * ir;
+        }
+        if (t == 0) dk[o + c] = make_float2(ir, ii);
+        __syncthreads();
+        if (tcol > c && tcol < W) {
+            const float ur = Ar[c * LD + tcol], ui = Ai[c * LD + tcol];
+            for (int r = c + 1 + trow; r < W; r += D128_THREADS / TB) {
+                const float lr = Ar[r * LD + c], li = Ai[r * LD + c];
+                Ar[r * LD + tcol] -= lr * ur - li * ui;
+                Ai[r * LD + tcol] -= lr * ui + li * ur;
+            }
+        }
+        __syncthreads();
+    }
+    for (int e = t; e < W * W; e += blockDim.x) {
+        const int r = e / W, c = e % W;
+        const size_t g = (size_t)(o + r) * mp + o + c;
+        re[g] = Ar[r * LD + c];
+        im[g] = Ai[r * LD + c];
+    }
+    if (!invert || W != TB) return;
+    __syncthreads();
+    // in-place inversion: threads 0..255 own row i = t/2 of L^{-1}, threads 256..511
+    // column c = (t-256)/2 of U^{-1}; the two threads of a pair split the sum
+    const bool lower = t < 256;
+    const int idx = (t & 255) >> 1, half = t & 1;
+    float resr = 0.f, resi = 0.f;
+    for (int j = TB - 1; j >= -1; --j) {
+        // results of step j + 1, then column j of L / row j of U as they were
+        if (j + 1 < TB && half == 0) {
+            if (lower && idx > j + 1) {
+                Ar[idx * LD + j + 1] = resr;
+                Ai[idx * LD + j + 1] = resi;
+            } else if (!lower && idx >= j + 1) {
+                Ar[(j + 1) * LD + idx] = resr;
+                Ai[(j + 1) * LD + idx] = resi;
+            }
+        }
+        if (j < 0) break;
+        for (int q = t; q < TB; q += blockDim.x) {
+            tx[q] = q > j ? make_float2(Ar[q * LD + j], Ai[q * LD + j]) : make_float2(0.f, 0.f);
+            ty[q] = q > j ? make_float2(Ar[j * LD + q], Ai[j * LD + q]) : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        float sr = 0.f, si = 0.f;
+        if (lower) {
+            for (int kk = j + 1 + half; kk < idx; kk += 2) {
+                const float lr = Ar[idx * LD + kk], li = Ai[idx * LD + kk];
+                const float2 x = tx[kk];
+                sr += lr * x.x - li * x.y;
+                si += lr * x.y + li * x.x;
+            }
+            if (half == 0 && idx > j) {
+                sr += tx[idx].x;
+                si += tx[idx].y;
+            }
+        } else {
+            for (int kk = j + 1 + half; kk <= idx; kk += 2) {
+                const float ur = Ar[kk * LD + idx], ui = Ai[kk * LD + idx];
+                const float2 y = ty[kk];
+                sr += y.x * ur - y.y * ui;
+                si += y.x * ui + y.y * ur;
+            }
+        }
+        sr += __shfl_xor_sync(0xffffffffu, sr, 1);
+        si += __shfl_xor_sync(0xffffffffu, si, 1);
+        if (lower) {
+            resr = -sr;
+            resi = -si;
+        } else {
+            const float pr = Ar[j * LD + j], pim = Ai[j * LD + j];
+            const float den = pr * pr + pim * pim;
+            const float dr = den > 0.f ? pr / den : 0.f, di = den > 0.f ? -pim / den : 0.f;
+            if (idx == j) {
+                resr = dr;
+                resi = di;
+            } else {  // -(1/U_jj) * s
+                resr = -(dr * sr - di * si);
+                resi = -(dr * si + di * sr);
+            }
+        }
+        __syncthreads();
+    }
+    __syncthreads();
+    // pack: L^{-1} as A' (row i, K' = [Re | Im] of L^{-1}[i][:]), U^{-1} as B'
+    constexpr int EPS = Cfg::PER_CORE;
+    constexpr int SEGS = 2 * TB / EPS;  // segments per packed row
+    unsigned char* pB = pA + Cfg::A_TILE;
+    for (int e = t; e < TB * SEGS; e += blockDim.x) {
+        const int i = e / SEGS, kp0 = (e % SEGS) * EPS;
+        const bool imag = kp0 >= TB;
+        float v[EPS];
+#pragma unroll
+        for (int u = 0; u < EPS; ++u) {
+            const int kk = (kp0 + u) & (TB - 1);
+            v[u] = kk < i ? (imag ? Ai[i * LD + kk] : Ar[i * LD + kk]) : (kk == i && !imag ? 1.f : 0.f);
+        }
+        pack2_seg<KIND>(pA, T2_BM, i, kp0, v, false);
+    }
+    for (int e = t; e < 2 * TB * SEGS; e += blockDim.x) {
+        const int brow = e / SEGS, kp0 = (e % SEGS) * EPS;
+        const int j = brow & (TB - 1);
+        const bool im_out = brow >= TB, second = kp0 >= TB;
+        // Re output row: [Re U^{-1}[k][j] | -Im U^{-1}[k][j]]; Im output row: [Im | Re]
+        float v[EPS];
+#pragma unroll
+        for (int u = 0; u < EPS; ++u) {
+            const int kk = (kp0 + u) & (TB - 1);
+            float x = 0.f;
+            if (kk <= j) {
+                const bool take_im = im_out != second;
+                x = take_im ? Ai[kk * LD + j] : Ar[kk * LD + j];
+                if (!im_out && second) x = -x;
+            }
+            v[u] = x;
+        }
+        pack2_seg<KIND>(pB, 2 * T2_BN, brow, kp0, v, true);
+    }
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(D128_THREADS)
+lu_diag128_kernel(int mp, int o, float* __restrict__ fac, float2* __restrict__ dinv, int* __restrict__ info,
+                  unsigned char* __restrict__ ipack, size_t ipack_stride, int invert) {
+    const int k = blockIdx.x;
+    diag128_body<KIND>(mp, o, fac + (size_t)k * 2 * mp * mp, dinv + (size_t)k * mp, info + k,
+                       ipack ? ipack + (size_t)k * ipack_stride : nullptr, invert != 0);
+}
+
+// Batched: blocks with m_p > o (a prefix of the table sorted by m_p).
+template <int KIND>
+__global__ void __launch_bounds__(D128_THREADS) lu_diag128_batched(const BlkDev* __restrict__ B, int o) {
+    const BlkDev& d = B[blockIdx.x];
+    diag128_body<KIND>(d.mp, o, (float*)d.fac, (float2*)d.dinv, d.info, d.ipack, o + TB < d.mp);
+}
+
+// Operand tiles of the current panels: rows R0.. of columns o..o+128 (A21 or L21)
+// as A' tiles, rows o..o+128 of columns R0.. (A12 or U12) as B' tiles.  One thread
+// per 16-byte segment; A' segments read one contiguous row piece, B' segments one
+// column piece (consecutive threads take consecutive columns: coalesced).
+template <int KIND>
+__device__ __forceinline__ void pack_panel_body(int mp, int o, int R0, const float* __restrict__ re,
+                                                unsigned char* __restrict__ apack, unsigned char* __restrict__ bpack) {
+    using Cfg = Tc2<KIND>;
+    constexpr int EPS = Cfg::PER_CORE;
+    constexpr int GPR = TB / EPS;  // segments per plane row of a panel
+    const float* im = re + (size_t)mp * mp;
+    const int nr = mp - R0;
+    const long items = (long)nr * GPR;
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < 2 * items; e += (long)gridDim.x * blockDim.x) {
+        float vr[EPS], vi[EPS];
+        if (e < items) {
+            const int rl = (int)(e / GPR), g = (int)(e % GPR);
+            const size_t off = (size_t)(R0 + rl) * mp + o + g * EPS;
+#pragma unroll
+            for (int u = 0; u < EPS; u += 4) {
+                const float4 a = *reinterpret_cast<const float4*>(re + off + u);
+                const float4 b = *reinterpret_cast<const float4*>(im + off + u);
+                vr[u] = a.x; vr[u + 1] = a.y; vr[u + 2] = a.z; vr[u + 3] = a.w;
+                vi[u] = b.x; vi[u + 1] = b.y; vi[u + 2] = b.z; vi[u + 3] = b.w;
+            }
+            unsigned char* tile = apack + (size_t)(rl / T2_BM) * Cfg::A_TILE;
+            pack2_seg<KIND>(tile, T2_BM, rl % T2_BM, g * EPS, vr, false);
+            pack2_seg<KIND>(tile, T2_BM, rl % T2_BM, TB + g * EPS, vi, false);
+        } else {
+            const long e2 = e - items;
+            const int g = (int)(e2 / nr), jl = (int)(e2 % nr);
+            float nv[EPS];
+#pragma unroll
+            for (int u = 0; u < EPS; ++u) {
+                const size_t off = (size_t)(o + g * EPS + u) * mp + R0 + jl;
+                vr[u] = re[off];
+                vi[u] = im[off];
+                nv[u] = -vi[u];
+            }
+            unsigned char* tile = bpack + (size_t)(jl / T2_BN) * Cfg::B_TILE;
+            const int jr = jl % T2_BN;
+            pack2_seg<KIND>(tile, 2 * T2_BN, jr, g * EPS, vr, true);
+            pack2_seg<KIND>(tile, 2 * T2_BN, jr, TB + g * EPS, nv, true);
+            pack2_seg<KIND>(tile, 2 * T2_BN, T2_BN + jr, g * EPS, vi, true);
+            pack2_seg<KIND>(tile, 2 * T2_BN, T2_BN + jr, TB + g * EPS, vr, true);
+        }
+    }
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(256)
+lu_pack_panel_kernel(int mp, int o, int R0, const float* __restrict__ fac, unsigned char* __restrict__ apack,
+                     unsigned char* __restrict__ bpack, size_t pa, size_t pb) {
+    const int k = blockIdx.y;
+    pack_panel_body<KIND>(mp, o, R0, fac + (size_t)k * 2 * mp * mp, apack + (size_t)k * pa, bpack + (size_t)k * pb);
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(256) lu_pack_panel_batched(const BlkDev* __restrict__ B, int o, int R0) {
+    const BlkDev& d = B[blockIdx.y];
+    if (R0 >= d.mp) return;
+    pack_panel_body<KIND>(d.mp, o, R0, (const float*)d.fac, d.apack, d.bpack);
+}
+
+// Panel products in store mode: blockIdx.x < ntr -> L21 tile (rows R0 + 128 x,
+// columns o..o+128) = A21 tile x U11^{-1}; otherwise U12 tile (rows o..o+128,
+// columns R0 + 128 (x - ntr)) = L11^{-1} A12 tile.
+template <int KIND>
+__global__ void __launch_bounds__(128)
+lu_panel_tc2_kernel(int mp, int o, int R0, int ntr, float* __restrict__ fac, const unsigned char* __restrict__ apack,
+                    const unsigned char* __restrict__ bpack, const unsigned char* __restrict__ ipack, size_t pa,
+                    size_t pb, size_t pi, int* __restrict__ err) {
+    using Cfg = Tc2<KIND>;
+    const int k = blockIdx.y, x = blockIdx.x;
+    float* re = fac + (size_t)k * 2 * mp * mp;
+    const unsigned char* ip = ipack + (size_t)k * pi;
+    if (x < ntr)
+        tc2_tile_body<KIND, true>(mp, R0 + x * T2_BM, o, re, apack + (size_t)k * pa + (size_t)x * Cfg::A_TILE,
+                                  ip + Cfg::A_TILE, err);
+    else
+        tc2_tile_body<KIND, true>(mp, o, R0 + (x - ntr) * T2_BN, re, ip,
+                                  bpack + (size_t)k * pb + (size_t)(x - ntr) * Cfg::B_TILE, err);
+}
+
+// Batched: grid.x = 2 ntg covers the largest active block (ntg tiles per panel).
+template <int KIND>
+__global__ void __launch_bounds__(128)
+lu_panel_tc2_batched(const BlkDev* __restrict__ B, int o, int R0, int ntg, int* __restrict__ err) {
+    using Cfg = Tc2<KIND>;
+    const BlkDev& d = B[blockIdx.y];
+    if (R0 >= d.mp) return;
+    const int nt = (d.mp - R0 + T2_BM - 1) / T2_BM;
+    const int x = blockIdx.x;
+    float* re = (float*)d.fac;
+    if (x < ntg) {
+        if (x >= nt) return;
+        tc2_tile_body<KIND, true>(d.mp, R0 + x * T2_BM, o, re, d.apack + (size_t)x * Cfg::A_TILE,
+                                  d.ipack + Cfg::A_TILE, err);
+    } else {
+        if (x - ntg >= nt) return;
+        tc2_tile_body<KIND, true>(d.mp, o, R0 + (x - ntg) * T2_BN, re, d.ipack,
+                                  d.bpack + (size_t)(x - ntg) * Cfg::B_TILE, err);
+    }
+}
+
 template <int KIND>
 static int run_lu_tc(Problem& P, cudaStream_t st) {
     using Cfg = Tc2<KIND>;
@@ -767,7 +1064,8 @@ static int run_lu_tc(Problem& P, cudaStream_t st) {
     const int mp = P.mp, nb = P.nblk;
     size_t pa, pb;
     tc2_pack_sizes<KIND>(mp, &pa, &pb);
-    const size_t need = (size_t)nb * (pa + pb);
+    const size_t pi = (size_t)Cfg::A_TILE + Cfg::B_TILE;  // L11^{-1} (A') and U11^{-1} (B') per block
+    const size_t need = mp > TB ? (size_t)nb * (pa + pb + pi) : 0;
     if (need > 0 && P.pack_bytes < need) {
         if (P.d_pack) cudaFree(P.d_pack);
         P.d_pack = nullptr;
@@ -778,6 +1076,7 @@ static int run_lu_tc(Problem& P, cudaStream_t st) {
     }
     unsigned char* apack = reinterpret_cast<unsigned char*>(P.d_pack);
     unsigned char* bpack = apack ? apack + (size_t)nb * pa : nullptr;
+    unsigned char* ipack = apack ? bpack + (size_t)nb * pb : nullptr;
     {
         dim3 grid(mp < 64 ? mp : 64, nb);
         StageTimer t(P, FDE_STAGE_FORM);
@@ -787,53 +1086,40 @@ static int run_lu_tc(Problem& P, cudaStream_t st) {
     }
     int rc = set_tc_attrs<KIND>();
     if (rc) return rc;
-    const size_t panel_smem = (size_t)RC * (NB + 1) * sizeof(float2);
-    const size_t upd_smem = (64 * (NB + 1) + NB * 65) * sizeof(float2);
+    FDE_CUDA_TRY(cudaFuncSetAttribute(lu_diag128_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)diag128_smem()));
+    FDE_CUDA_TRY(cudaFuncSetAttribute(lu_panel_tc2_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      Cfg::SMEM_STORE));
     for (int o = 0; o < mp; o += TB) {
         const int W = mp - o < TB ? mp - o : TB;
-        const int R0 = o + W;  // start of the outer trailing matrix
-        for (int q = 0; q < W / NB; ++q) {
-            const int oi = o + q * NB;
-            {
-                StageTimer t(P, FDE_STAGE_LU_DIAG);
-                lu_diag_kernel<float><<<nb, 256, 0, st>>>(mp, oi / NB, fac, dinv, P.d_info);
-                FDE_LAUNCH_CHECK("lu_diag_kernel");
-            }
-            const int nrow = cdiv(mp - (oi + NB), RC), ncol = cdiv(R0 - (oi + NB), RC);
-            if (nrow + ncol > 0) {
-                StageTimer t(P, FDE_STAGE_LU_PANEL);
-                lu_panel_range_kernel<float, KIND><<<dim3(nrow + ncol, nb), RC, panel_smem, st>>>(
-                    mp, oi, oi + NB, mp, oi + NB, R0, nrow, fac, apack, bpack, pa, pb, R0, q * NB);
-                FDE_LAUNCH_CHECK("lu_panel_range_kernel");
-            }
-            const int ntr = cdiv(mp - (oi + NB), 64), ntc = cdiv(R0 - (oi + NB), 64);
-            if (ntr * ntc > 0) {
-                StageTimer t(P, FDE_STAGE_LU_UPDATE);
-                lu_update_range_kernel<float><<<dim3(ntr * ntc, nb), 256, upd_smem, st>>>(mp, oi, oi + NB, mp, oi + NB,
-                                                                                        R0, ntc, fac);
-                FDE_LAUNCH_CHECK("lu_update_range_kernel");
-            }
+        const int R0 = o + W;
+        const bool more = R0 < mp;
+        {
+            StageTimer t(P, FDE_STAGE_LU_DIAG);
+            lu_diag128_kernel<KIND><<<nb, D128_THREADS, diag128_smem(), st>>>(mp, o, fac, dinv, P.d_info, ipack, pi,
+                                                                              more ? 1 : 0);
+            FDE_LAUNCH_CHECK("lu_diag128_kernel");
         }
-        if (R0 >= mp) continue;
-        // outer row panel U12 = L11^{-1} A12, 32 rows at a time
-        for (int q = 0; q < W / NB; ++q) {
-            const int oi = o + q * NB;
-            {
-                StageTimer t(P, FDE_STAGE_LU_PANEL);
-                const int ncol = cdiv(mp - R0, RC);
-                lu_panel_range_kernel<float, KIND><<<dim3(ncol, nb), RC, panel_smem, st>>>(
-                    mp, oi, 0, 0, R0, mp, 0, fac, apack, bpack, pa, pb, R0, q * NB);
-                FDE_LAUNCH_CHECK("lu_panel_range_kernel");
-            }
-            const int ntr = cdiv(R0 - (oi + NB), 64), ntc = cdiv(mp - R0, 64);
-            if (ntr * ntc > 0) {
-                StageTimer t(P, FDE_STAGE_LU_UPDATE);
-                lu_update_range_kernel<float><<<dim3(ntr * ntc, nb), 256, upd_smem, st>>>(mp, oi, oi + NB, R0, R0, mp,
-                                                                                        ntc, fac);
-                FDE_LAUNCH_CHECK("lu_update_range_kernel");
-            }
-        }
+        if (!more) break;
         const int nt = cdiv(mp - R0, T2_BM);
+        const long items = 2L * (mp - R0) * (TB / Cfg::PER_CORE);
+        const int pgrid = (int)std::min<long>((items + 255) / 256, 1024);
+        {
+            StageTimer t(P, FDE_STAGE_LU_PACK);
+            lu_pack_panel_kernel<KIND><<<dim3(pgrid, nb), 256, 0, st>>>(mp, o, R0, fac, apack, bpack, pa, pb);
+            FDE_LAUNCH_CHECK("lu_pack_panel_kernel");
+        }
+        {
+            StageTimer t(P, FDE_STAGE_LU_PANEL_TC);
+            lu_panel_tc2_kernel<KIND><<<dim3(2 * nt, nb), 128, Cfg::SMEM_STORE, st>>>(mp, o, R0, nt, fac, apack, bpack,
+                                                                                    ipack, pa, pb, pi, P.d_err);
+            FDE_LAUNCH_CHECK("lu_panel_tc2_kernel");
+        }
+        {
+            StageTimer t(P, FDE_STAGE_LU_PACK);
+            lu_pack_panel_kernel<KIND><<<dim3(pgrid, nb), 256, 0, st>>>(mp, o, R0, fac, apack, bpack, pa, pb);
+            FDE_LAUNCH_CHECK("lu_pack_panel_kernel");
+        }
         StageTimer t(P, FDE_STAGE_LU_TC);
         lu_update_tc2_kernel<KIND><<<dim3(nt * nt, nb), 128, Cfg::SMEM, st>>>(mp, R0, nt, fac, apack, bpack, pa, pb,
                                                                              P.d_err);
@@ -883,53 +1169,34 @@ static int run_lu_batched_tc(const BlkDev* d_blk, const std::vector<int>& mps, i
     FDE_LAUNCH_CHECK("form_blocks_batched");
     int rc = set_tc_attrs<KIND>();
     if (rc) return rc;
-    const size_t panel_smem = (size_t)RC * (NB + 1) * sizeof(float2);
-    const size_t upd_smem = (64 * (NB + 1) + NB * 65) * sizeof(float2);
+    FDE_CUDA_TRY(cudaFuncSetAttribute(lu_diag128_batched<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)diag128_smem()));
+    FDE_CUDA_TRY(cudaFuncSetAttribute(lu_panel_tc2_batched<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      Cfg::SMEM_STORE));
     auto active = [&](int lim) {  // blocks with m_p > lim (a prefix of the sorted table)
         int n = 0;
         while (n < nbt && mps[n] > lim) ++n;
         return n;
     };
     for (int o = 0; o < max_mp; o += TB) {
+        const int nd = active(o);
+        if (nd == 0) break;
+        lu_diag128_batched<KIND><<<nd, D128_THREADS, diag128_smem(), st>>>(d_blk, o);
+        FDE_LAUNCH_CHECK("lu_diag128_batched");
         const int R0 = o + TB;
-        for (int q = 0; q < TB / NB; ++q) {
-            const int oi = o + q * NB;
-            const int nd = active(oi);
-            if (nd == 0) break;
-            lu_diag_batched<float><<<nd, 256, 0, st>>>(d_blk, oi / NB);
-            FDE_LAUNCH_CHECK("lu_diag_batched");
-            const int top = mps[0];  // largest active block bounds the grids
-            const int nrow = cdiv(top - (oi + NB), RC), ncol = cdiv((R0 < top ? R0 : top) - (oi + NB), RC);
-            if (nrow + ncol > 0) {
-                lu_panel_range_batched<float, KIND><<<dim3(nrow + ncol, nd), RC, panel_smem, st>>>(
-                    d_blk, oi, oi + NB, oi + NB, R0, R0, q * NB);
-                FDE_LAUNCH_CHECK("lu_panel_range_batched");
-            }
-            const int ntr = cdiv(top - (oi + NB), 64), ntc = cdiv((R0 < top ? R0 : top) - (oi + NB), 64);
-            if (ntr * ntc > 0) {
-                lu_update_range_batched<float><<<dim3(ntr * ntc, nd), 256, upd_smem, st>>>(d_blk, oi, oi + NB, 1 << 30,
-                                                                                         oi + NB, R0, ntc);
-                FDE_LAUNCH_CHECK("lu_update_range_batched");
-            }
-        }
-        const int nt_blocks = active(R0);
-        if (nt_blocks == 0) continue;
-        const int top = mps[0];
-        for (int q = 0; q < TB / NB; ++q) {
-            const int oi = o + q * NB;
-            const int ncol = cdiv(top - R0, RC);
-            lu_panel_range_batched<float, KIND><<<dim3(ncol, nt_blocks), RC, panel_smem, st>>>(d_blk, oi, 1 << 30, R0,
-                                                                                               1 << 30, R0, q * NB);
-            FDE_LAUNCH_CHECK("lu_panel_range_batched");
-            const int ntr = cdiv(R0 - (oi + NB), 64), ntc = cdiv(top - R0, 64);
-            if (ntr * ntc > 0) {
-                lu_update_range_batched<float><<<dim3(ntr * ntc, nt_blocks), 256, upd_smem, st>>>(
-                    d_blk, oi, oi + NB, R0, R0, 1 << 30, ntc);
-                FDE_LAUNCH_CHECK("lu_update_range_batched");
-            }
-        }
+        const int nact = active(R0);
+        if (nact == 0) continue;
+        const int top = mps[0];  // the largest active block bounds the grids
         const int ntg = cdiv(top - R0, T2_BM);
-        lu_update_tc2_batched<KIND><<<dim3(ntg * ntg, nt_blocks), 128, Cfg::SMEM, st>>>(d_blk, R0, ntg, err);
+        const long items = 2L * (top - R0) * (TB / Cfg::PER_CORE);
+        const int pgrid = (int)std::min<long>((items + 255) / 256, 1024);
+        lu_pack_panel_batched<KIND><<<dim3(pgrid, nact), 256, 0, st>>>(d_blk, o, R0);
+        FDE_LAUNCH_CHECK("lu_pack_panel_batched");
+        lu_panel_tc2_batched<KIND><<<dim3(2 * ntg, nact), 128, Cfg::SMEM_STORE, st>>>(d_blk, o, R0, ntg, err);
+        FDE_LAUNCH_CHECK("lu_panel_tc2_batched");
+        lu_pack_panel_batched<KIND><<<dim3(pgrid, nact), 256, 0, st>>>(d_blk, o, R0);
+        FDE_LAUNCH_CHECK("lu_pack_panel_batched");
+        lu_update_tc2_batched<KIND><<<dim3(ntg * ntg, nact), 128, Cfg::SMEM, st>>>(d_blk, R0, ntg, err);
         FDE_LAUNCH_CHECK("lu_update_tc2_batched");
     }
     return FDE_OK;
@@ -944,12 +1211,21 @@ int launch_lu_batched(const BlkDev* d_blk, const std::vector<int>& mp_sorted, in
     return run_lu_batched_simt(d_blk, mp_sorted, st);
 }
 
+// A' tiles, B' tiles, then the L11^{-1} / U11^{-1} tiles of the panel products.
 size_t tc_pack_bytes_per_block(int precision, int mp) {
+    size_t pa = 0, pb = 0, pi = 0;
+    if (precision == FDE_TF32) tc2_pack_sizes<0>(mp, &pa, &pb), pi = Tc2<0>::A_TILE + Tc2<0>::B_TILE;
+    else if (precision == FDE_BF16) tc2_pack_sizes<1>(mp, &pa, &pb), pi = Tc2<1>::A_TILE + Tc2<1>::B_TILE;
+    else if (precision == FDE_TF32X3) tc2_pack_sizes<2>(mp, &pa, &pb), pi = Tc2<2>::A_TILE + Tc2<2>::B_TILE;
+    return mp > TB ? pa + pb + pi : 0;
+}
+
+size_t tc_pack_b_bytes_per_block(int precision, int mp) {
     size_t pa = 0, pb = 0;
     if (precision == FDE_TF32) tc2_pack_sizes<0>(mp, &pa, &pb);
     else if (precision == FDE_BF16) tc2_pack_sizes<1>(mp, &pa, &pb);
     else if (precision == FDE_TF32X3) tc2_pack_sizes<2>(mp, &pa, &pb);
-    return pa + pb;
+    return pb;
 }
 
 size_t tc_pack_a_bytes_per_block(int precision, int mp) {

@@ -58,6 +58,9 @@ struct Tc2 {
     static constexpr int B_TILE = NCH * B_CHUNK;
     static constexpr int STAGE = A_CHUNK + B_CHUNK;
     static constexpr int SMEM = 2 * T2_C_BYTES + T2_STAGES * STAGE;
+    // Store mode (no C tile): the operand ring only, padded so that at most two CTAs
+    // (2 x 256 TMEM columns) share an SM.
+    static constexpr int SMEM_STORE = T2_STAGES * STAGE > 80 * 1024 ? T2_STAGES * STAGE : 80 * 1024;
     static constexpr int KSTEP = KIND == 1 ? 16 : 8;          // K per MMA = 32 bytes = 2 core matrices
     static constexpr int MMAS = KCH / KSTEP;                  // MMAs per chunk (2)
     static constexpr uint32_t IDESC = tc::instr_desc(KIND == 1 ? 1u : 2u, T2_BM, 2 * T2_BN);
@@ -94,6 +97,29 @@ __device__ __forceinline__ void pack2_store(unsigned char* tile, int rows, int r
     }
 }
 
+// Store the PER_CORE values v[0..PER_CORE) at K' positions kp0 .. kp0 + PER_CORE - 1
+// (kp0 a multiple of PER_CORE, < 256) of one row: one 16-byte core-matrix row
+// segment per product segment.
+template <int KIND>
+__device__ __forceinline__ void pack2_seg(unsigned char* tile, int rows, int row, int kp0, const float* v,
+                                          bool b_side) {
+    if constexpr (KIND == 1) {
+        __align__(16) __nv_bfloat16 hv[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) hv[t] = __float2bfloat16_rn(v[t]);
+        *reinterpret_cast<uint4*>(tile + pack2_off<KIND>(rows, row, kp0)) = *reinterpret_cast<const uint4*>(hv);
+    } else {
+        float4 hi = make_float4(tc::to_tf32(v[0]), tc::to_tf32(v[1]), tc::to_tf32(v[2]), tc::to_tf32(v[3]));
+        *reinterpret_cast<float4*>(tile + pack2_off<KIND>(rows, row, kp0)) = hi;
+        if constexpr (KIND == 2) {
+            const float4 lo = make_float4(tc::to_tf32(v[0] - hi.x), tc::to_tf32(v[1] - hi.y),
+                                          tc::to_tf32(v[2] - hi.z), tc::to_tf32(v[3] - hi.w));
+            *reinterpret_cast<float4*>(tile + pack2_off<KIND>(rows, row, T2_KP + kp0)) = b_side ? hi : lo;
+            *reinterpret_cast<float4*>(tile + pack2_off<KIND>(rows, row, 2 * T2_KP + kp0)) = b_side ? lo : hi;
+        }
+    }
+}
+
 __device__ __forceinline__ void bulk_s2g(void* dst_gmem, const void* src_smem, uint32_t bytes) {
     asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst_gmem),
                  "r"(tc::smem_u32(src_smem)), "r"(bytes)
@@ -103,31 +129,29 @@ __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.comm
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// Outer trailing update of one 128 x 128 complex tile (ti, tj) of one block:
-// C[r0.., c0..] -= D, r0 = R0 + 128 ti, c0 = R0 + 128 tj.
-template <int KIND>
-__device__ __forceinline__ void tc2_update_body(int mp, int R0, float* __restrict__ re_plane,
-                                                const unsigned char* __restrict__ apack,
-                                                const unsigned char* __restrict__ bpack, int* __restrict__ err, int ti,
-                                                int tj) {
+// One 128 x 128 complex output tile at (r0, c0) of one block, D = A' B'^T from the
+// packed tiles ga (A') and gb (B'):
+//   STORE = false: C[r0.., c0..] -= D (C staged in shared memory, read early);
+//   STORE = true:  C[r0.., c0..]  = D (no read of C; D goes from TMEM to HBM).
+template <int KIND, bool STORE>
+__device__ __forceinline__ void tc2_tile_body(int mp, int r0, int c0, float* __restrict__ re_plane,
+                                              const unsigned char* __restrict__ ga,
+                                              const unsigned char* __restrict__ gb, int* __restrict__ err) {
     using Cfg = Tc2<KIND>;
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* sCr = smem;
     unsigned char* sCi = smem + T2_C_BYTES;
-    unsigned char* sStage = smem + 2 * T2_C_BYTES;
+    unsigned char* sStage = STORE ? smem : smem + 2 * T2_C_BYTES;  // store mode: no C tile
     __shared__ __align__(8) uint64_t bar_c, bar_mma, bar_full[T2_STAGES], bar_empty[T2_STAGES];
     __shared__ uint32_t tmem_base;
     __shared__ int ok_flag;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int r0 = R0 + ti * T2_BM, c0 = R0 + tj * T2_BN;
     const int nrows = min(T2_BM, mp - r0);
     const int ncols = min(T2_BN, mp - c0);  // multiple of 64 (mp and R0 are)
     const uint32_t row_bytes = (uint32_t)ncols * 4;
     float* gre = re_plane;
     float* gim = re_plane + (size_t)mp * mp;
-    const unsigned char* ga = apack + (size_t)ti * Cfg::A_TILE;
-    const unsigned char* gb = bpack + (size_t)tj * Cfg::B_TILE;
 
     if (warp == 0) tc::tmem_alloc(&tmem_base, 256);
     if (threadIdx.x == 0) {
@@ -140,13 +164,13 @@ __device__ __forceinline__ void tc2_update_body(int mp, int R0, float* __restric
         tc::fence_barrier_init();
         ok_flag = 1;
         // the C tile: every valid row of both planes
-        tc::mbar_arrive_expect_tx(&bar_c, 2u * (uint32_t)nrows * row_bytes);
+        if (!STORE) tc::mbar_arrive_expect_tx(&bar_c, 2u * (uint32_t)nrows * row_bytes);
     }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tbase = tmem_base;
-    {
+    if (!STORE) {
         const int r = threadIdx.x;
         if (r < nrows) {
             tc::bulk_g2s(sCr + r * T2_CROW, gre + (size_t)(r0 + r) * mp + c0, row_bytes, &bar_c);
@@ -205,12 +229,33 @@ __device__ __forceinline__ void tc2_update_body(int mp, int R0, float* __restric
     const bool ok = ok_flag != 0;
     bool mine = false;
     if (ok) {
-        mine = tc::mbar_wait(&bar_mma, 0) && tc::mbar_wait(&bar_c, 0);
+        mine = tc::mbar_wait(&bar_mma, 0) && (STORE || tc::mbar_wait(&bar_c, 0));
         if (!mine && lane == 0) atomicCAS(err, 0, 2);
     }
     const bool done = __syncthreads_and(mine) != 0;  // uniform across the CTA
     tc::fence_after_sync();
-    if (ok && done) {
+    if (STORE && ok && done) {
+        const int r = warp * 32 + lane;  // TMEM lane = tile row
+        const uint32_t lane_addr = tbase + ((uint32_t)(warp * 32) << 16);
+        float* pr = gre + (size_t)(r0 + r) * mp + c0;
+        float* pi = gim + (size_t)(r0 + r) * mp + c0;
+#pragma unroll 1
+        for (int ch = 0; ch < T2_BN / 16; ++ch) {
+            float dr[16], di[16];
+            tc::tmem_ld16(lane_addr + ch * 16, dr);
+            tc::tmem_ld16(lane_addr + T2_BN + ch * 16, di);
+            tc::tmem_ld_wait();
+            if (r < nrows && ch * 16 < ncols) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    reinterpret_cast<float4*>(pr + ch * 16)[q] =
+                        make_float4(dr[4 * q], dr[4 * q + 1], dr[4 * q + 2], dr[4 * q + 3]);
+                    reinterpret_cast<float4*>(pi + ch * 16)[q] =
+                        make_float4(di[4 * q], di[4 * q + 1], di[4 * q + 2], di[4 * q + 3]);
+                }
+            }
+        }
+    } else if (!STORE && ok && done) {
         const int r = warp * 32 + lane;  // TMEM lane = tile row
         const uint32_t lane_addr = tbase + ((uint32_t)(warp * 32) << 16);
         float4* cr = reinterpret_cast<float4*>(sCr + r * T2_CROW);
@@ -240,14 +285,25 @@ __device__ __forceinline__ void tc2_update_body(int mp, int R0, float* __restric
             bulk_commit();
             bulk_wait_all();
         }
-    } else {
+    } else if (!(ok && done)) {
         // bounded: let in-flight copies and MMAs land before TMEM is released
-        tc::mbar_wait(&bar_c, 0);
+        if (!STORE) tc::mbar_wait(&bar_c, 0);
         tc::mbar_wait(&bar_mma, 0);
     }
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tbase, 256);
+}
+
+// Outer trailing update of tile (ti, tj): C[R0 + 128 ti.., R0 + 128 tj..] -= D.
+template <int KIND>
+__device__ __forceinline__ void tc2_update_body(int mp, int R0, float* __restrict__ re_plane,
+                                                const unsigned char* __restrict__ apack,
+                                                const unsigned char* __restrict__ bpack, int* __restrict__ err, int ti,
+                                                int tj) {
+    using Cfg = Tc2<KIND>;
+    tc2_tile_body<KIND, false>(mp, R0 + ti * T2_BM, R0 + tj * T2_BN, re_plane, apack + (size_t)ti * Cfg::A_TILE,
+                               bpack + (size_t)tj * Cfg::B_TILE, err);
 }
 
 }  // namespace fde
