@@ -774,16 +774,26 @@ static void tc2_pack_sizes(int mp, size_t* pa, size_t* pb) {
 // ---------------------------------------------------------------------------
 constexpr int D128_LD = TB + 1;  // shared row pitch in floats (column reads conflict-free)
 constexpr int D128_THREADS = 512;
+constexpr int DB = 32;           // leaf block of the blocked LU and inversion
 
-static size_t diag128_smem() { return (size_t)2 * TB * D128_LD * sizeof(float) + (size_t)2 * TB * sizeof(float2); }
+// planes [128][129] x 2 | T [32][33] x 2 | per-warp vectors [8][32] complex | 1/U_cc of a leaf [32] complex
+static size_t diag128_smem() {
+    return (size_t)(2 * TB * D128_LD + 2 * DB * (DB + 1)) * sizeof(float) + (size_t)(8 * DB + DB) * sizeof(float2);
+}
 
-// One CTA per Strang block: unblocked LU (no pivoting) of the W x W block at (o, o)
-// (W = 128, or 64 for a last panel), L\U and 1/U_ii written back.  With invert != 0
-// (a trailing matrix follows; W = 128) both triangles are then inverted in place,
-// column j of L^{-1} and row j of U^{-1} at step j = W-1 .. 0:
-//   L^{-1}[i][j] = -(L[i][j] + sum_{j<k<i} L^{-1}[i][k] L[k][j])             (i > j)
-//   U^{-1}[j][c] = -(1/U[j][j]) sum_{j<k<=c} U[j][k] U^{-1}[k][c]            (c > j)
-// and packed: L^{-1} (unit diagonal, zeros above) as the A' tile and U^{-1} (zeros
+// One CTA per Strang block: LU (no pivoting) of the W x W block at (o, o), W = 128
+// (or 64 for a last panel), blocked over 32 x 32 leaves in shared memory:
+//   leaf LU by one warp; panel solves X U_pp = A (rows) and L_pp X = A (columns)
+//   with one thread per row / column and the 32 values in registers; rank-32
+//   trailing update with 4 x 4 complex register tiles.
+// L\U and 1/U_ii are written back.  With invert (a trailing matrix follows, W = 128)
+// both triangles are then inverted in place:
+//   phase 0: the eight diagonal 32 x 32 triangles, one warp each, column by column;
+//   phase d = 1..3: the blocks at distance d from the diagonal,
+//     X_ij = -X_ii sum_{j<=k<i} L_ik X_kj   (L^{-1}, i = j + d),
+//     Y_ij = -Y_ii sum_{i<k<=j} U_ik Y_kj   (U^{-1}, j = i + d),
+//   with the original L_ik, U_ik read back from the factor just written (L2).
+// L^{-1} (unit diagonal, zeros above) is packed as the A' tile and U^{-1} (zeros
 // below) as the B' tile of the panel products (layout of lu_tc2.cuh).
 template <int KIND>
 __device__ __forceinline__ void diag128_body(int mp, int o, float* __restrict__ re, float2* __restrict__ dk,
@@ -793,11 +803,13 @@ __device__ __forceinline__ void diag128_body(int mp, int o, float* __restrict__ 
     extern __shared__ __align__(16) float dsm[];
     float* Ar = dsm;
     float* Ai = dsm + TB * LD;
-    float2* tx = reinterpret_cast<float2*>(dsm + 2 * TB * LD);
-    float2* ty = tx + TB;
+    float* Tr = dsm + 2 * TB * LD;
+    float* Ti = Tr + DB * (DB + 1);
+    float2* vec = reinterpret_cast<float2*>(Ti + DB * (DB + 1));  // [8][32]
+    float2* pinv = vec + 8 * DB;                                   // [32]
     float* im = re + (size_t)mp * mp;
     const int W = mp - o < TB ? mp - o : TB;
-    const int t = threadIdx.x;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     for (int e = t; e < W * W; e += blockDim.x) {
         const int r = e / W, c = e % W;
         const size_t g = (size_t)(o + r) * mp + o + c;
@@ -805,27 +817,103 @@ __device__ __forceinline__ void diag128_body(int mp, int o, float* __restrict__ 
         Ai[r * LD + c] = im[g];
     }
     __syncthreads();
-    const int tcol = t & (TB - 1), trow = t >> 7;  // 128 columns x 4 row groups
-    for (int c = 0; c < W; ++c) {
-        const float pr = Ar[c * LD + c], pim = Ai[c * LD + c];
-        const float den = pr * pr + pim * pim;
-        const bool bad = !(den > 0.f) || !isfinite(den);
-        if (bad && t == 0) atomicCAS(info, 0, o + c + 1);
-        const float ir = bad ? 0.f : pr / den, ii = bad ? 0.f : -pim / den;
-        for (int r = c + 1 + t; r < W; r += blockDim.x) {
-            const float ar = Ar[r * LD + c], ai = Ai[r * LD + c];
-            Ar[r * LD + c] = ar * ir - ai * ii;
-            Ai[r * LD + c] = ar * ii + ai * ir;
-        }
-        if (t == 0) dk[o + c] = make_float2(ir, ii);
-        __syncthreads();
-        if (tcol > c && tcol < W) {
-            const float ur = Ar[c * LD + tcol], ui = Ai[c * LD + tcol];
-            for (int r = c + 1 + trow; r < W; r += D128_THREADS / TB) {
-                const float lr = Ar[r * LD + c], li = Ai[r * LD + c];
-                Ar[r * LD + tcol] -= lr * ur - li * ui;
-                Ai[r * LD + tcol] -= lr * ui + li * ur;
+    for (int P0 = 0; P0 < W; P0 += DB) {
+        if (warp == 0) {  // leaf LU, lane = row
+            const int ri = (P0 + lane) * LD + P0;
+            for (int c = 0; c < DB; ++c) {
+                const int ci = (P0 + c) * LD + P0;
+                const float pr = Ar[ci + c], pim = Ai[ci + c];
+                const float den = pr * pr + pim * pim;
+                const bool bad = !(den > 0.f) || !isfinite(den);
+                const float ir = bad ? 0.f : pr / den, ii = bad ? 0.f : -pim / den;
+                if (lane == c) {
+                    if (bad) atomicCAS(info, 0, o + P0 + c + 1);
+                    pinv[c] = make_float2(ir, ii);
+                    dk[o + P0 + c] = make_float2(ir, ii);
+                }
+                if (lane > c) {
+                    const float ar = Ar[ri + c], ai = Ai[ri + c];
+                    const float lr = ar * ir - ai * ii, li = ar * ii + ai * ir;
+                    Ar[ri + c] = lr;
+                    Ai[ri + c] = li;
+                    for (int cc = c + 1; cc < DB; ++cc) {
+                        const float ur = Ar[ci + cc], ui = Ai[ci + cc];
+                        Ar[ri + cc] -= lr * ur - li * ui;
+                        Ai[ri + cc] -= lr * ui + li * ur;
+                    }
+                }
+                __syncwarp();
             }
+        }
+        __syncthreads();
+        const int Q0 = P0 + DB, nrest = W - Q0;
+        if (nrest <= 0) break;
+        // panel solves in place in shared memory (row pitch 129: a warp's rows or
+        // columns fall in distinct banks)
+        if (t < nrest) {  // row Q0 + t of the column panel: x U_pp = a
+            const int ri = (Q0 + t) * LD + P0;
+            for (int c = 0; c < DB; ++c) {
+                const float2 pv = pinv[c];
+                const float xr = Ar[ri + c], xi = Ai[ri + c];
+                const float a = xr * pv.x - xi * pv.y, b = xr * pv.y + xi * pv.x;
+                Ar[ri + c] = a;
+                Ai[ri + c] = b;
+                const int ci = (P0 + c) * LD + P0;
+#pragma unroll 8
+                for (int cc = c + 1; cc < DB; ++cc) {
+                    const float ur = Ar[ci + cc], ui = Ai[ci + cc];
+                    Ar[ri + cc] -= a * ur - b * ui;
+                    Ai[ri + cc] -= a * ui + b * ur;
+                }
+            }
+        } else if (t >= 256 && t - 256 < nrest) {  // column Q0 + t - 256 of the row panel: L_pp x = a
+            const int j = Q0 + t - 256;
+            for (int c = 0; c < DB; ++c) {
+                const float xr = Ar[(P0 + c) * LD + j], xi = Ai[(P0 + c) * LD + j];
+#pragma unroll 8
+                for (int rr = c + 1; rr < DB; ++rr) {
+                    const float lr = Ar[(P0 + rr) * LD + P0 + c], li = Ai[(P0 + rr) * LD + P0 + c];
+                    Ar[(P0 + rr) * LD + j] -= lr * xr - li * xi;
+                    Ai[(P0 + rr) * LD + j] -= lr * xi + li * xr;
+                }
+            }
+        }
+        __syncthreads();
+        // rank-32 trailing update; a task owns rows Q0 + tr + q n4 and columns Q0 + tc + w n4
+        const int n4 = nrest / 4;
+        for (int task = t; task < n4 * n4; task += blockDim.x) {
+            const int tr = task / n4, tc = task % n4;
+            float accr[4][4], acci[4][4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int w = 0; w < 4; ++w) accr[q][w] = acci[q][w] = 0.f;
+#pragma unroll 4
+            for (int k = 0; k < DB; ++k) {
+                float ar[4], ai[4], br[4], bi[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    ar[q] = Ar[(Q0 + tr + q * n4) * LD + P0 + k];
+                    ai[q] = Ai[(Q0 + tr + q * n4) * LD + P0 + k];
+                    br[q] = Ar[(P0 + k) * LD + Q0 + tc + q * n4];
+                    bi[q] = Ai[(P0 + k) * LD + Q0 + tc + q * n4];
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+#pragma unroll
+                    for (int w = 0; w < 4; ++w) {
+                        accr[q][w] += ar[q] * br[w] - ai[q] * bi[w];
+                        acci[q][w] += ar[q] * bi[w] + ai[q] * br[w];
+                    }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int w = 0; w < 4; ++w) {
+                    const int idx = (Q0 + tr + q * n4) * LD + Q0 + tc + w * n4;
+                    Ar[idx] -= accr[q][w];
+                    Ai[idx] -= acci[q][w];
+                }
         }
         __syncthreads();
     }
@@ -836,69 +924,132 @@ __device__ __forceinline__ void diag128_body(int mp, int o, float* __restrict__ 
         im[g] = Ai[r * LD + c];
     }
     if (!invert || W != TB) return;
-    __syncthreads();
-    // in-place inversion: threads 0..255 own row i = t/2 of L^{-1}, threads 256..511
-    // column c = (t-256)/2 of U^{-1}; the two threads of a pair split the sum
-    const bool lower = t < 256;
-    const int idx = (t & 255) >> 1, half = t & 1;
-    float resr = 0.f, resi = 0.f;
-    for (int j = TB - 1; j >= -1; --j) {
-        // results of step j + 1, then column j of L / row j of U as they were
-        if (j + 1 < TB && half == 0) {
-            if (lower && idx > j + 1) {
-                Ar[idx * LD + j + 1] = resr;
-                Ai[idx * LD + j + 1] = resi;
-            } else if (!lower && idx >= j + 1) {
-                Ar[(j + 1) * LD + idx] = resr;
-                Ai[(j + 1) * LD + idx] = resi;
-            }
-        }
-        if (j < 0) break;
-        for (int q = t; q < TB; q += blockDim.x) {
-            tx[q] = q > j ? make_float2(Ar[q * LD + j], Ai[q * LD + j]) : make_float2(0.f, 0.f);
-            ty[q] = q > j ? make_float2(Ar[j * LD + q], Ai[j * LD + q]) : make_float2(0.f, 0.f);
-        }
-        __syncthreads();
-        float sr = 0.f, si = 0.f;
-        if (lower) {
-            for (int kk = j + 1 + half; kk < idx; kk += 2) {
-                const float lr = Ar[idx * LD + kk], li = Ai[idx * LD + kk];
-                const float2 x = tx[kk];
-                sr += lr * x.x - li * x.y;
-                si += lr * x.y + li * x.x;
-            }
-            if (half == 0 && idx > j) {
-                sr += tx[idx].x;
-                si += tx[idx].y;
+    __syncthreads();  // the factor in HBM is read back below by other threads of this CTA
+    // phase 0: diagonal triangles, warps 0-3 invert L_pp (lane = row), 4-7 U_pp (lane = column)
+    if (warp < 8) {
+        const int P0 = (warp & 3) * DB;
+        float2* v = vec + warp * DB;
+        if (warp < 4) {
+            const int ri = (P0 + lane) * LD + P0;
+            for (int j = DB - 1; j >= 0; --j) {
+                v[lane] = lane > j ? make_float2(Ar[ri + j], Ai[ri + j]) : make_float2(0.f, 0.f);
+                __syncwarp();
+                float sr = 0.f, si = 0.f;
+                if (lane > j) {
+                    sr = v[lane].x;
+                    si = v[lane].y;
+                    for (int k = j + 1; k < lane; ++k) {
+                        const float xr = Ar[ri + k], xi = Ai[ri + k];
+                        const float2 x = v[k];
+                        sr += xr * x.x - xi * x.y;
+                        si += xr * x.y + xi * x.x;
+                    }
+                }
+                __syncwarp();
+                if (lane > j) {
+                    Ar[ri + j] = -sr;
+                    Ai[ri + j] = -si;
+                }
+                __syncwarp();
             }
         } else {
-            for (int kk = j + 1 + half; kk <= idx; kk += 2) {
-                const float ur = Ar[kk * LD + idx], ui = Ai[kk * LD + idx];
-                const float2 y = ty[kk];
-                sr += y.x * ur - y.y * ui;
-                si += y.x * ui + y.y * ur;
+            for (int j = DB - 1; j >= 0; --j) {
+                const int ji = (P0 + j) * LD + P0;
+                v[lane] = lane > j ? make_float2(Ar[ji + lane], Ai[ji + lane]) : make_float2(0.f, 0.f);
+                const float pr = Ar[ji + j], pim = Ai[ji + j];
+                __syncwarp();
+                const float den = pr * pr + pim * pim;
+                const float dr = den > 0.f ? pr / den : 0.f, di = den > 0.f ? -pim / den : 0.f;
+                float nr = dr, ni = di;
+                if (lane > j) {
+                    float sr = 0.f, si = 0.f;
+                    for (int k = j + 1; k <= lane; ++k) {
+                        const float2 y = v[k];
+                        const float ur = Ar[(P0 + k) * LD + P0 + lane], ui = Ai[(P0 + k) * LD + P0 + lane];
+                        sr += y.x * ur - y.y * ui;
+                        si += y.x * ui + y.y * ur;
+                    }
+                    nr = -(dr * sr - di * si);
+                    ni = -(dr * si + di * sr);
+                }
+                __syncwarp();
+                if (lane >= j) {
+                    Ar[ji + lane] = nr;
+                    Ai[ji + lane] = ni;
+                }
+                __syncwarp();
             }
         }
-        sr += __shfl_xor_sync(0xffffffffu, sr, 1);
-        si += __shfl_xor_sync(0xffffffffu, si, 1);
-        if (lower) {
-            resr = -sr;
-            resi = -si;
-        } else {
-            const float pr = Ar[j * LD + j], pim = Ai[j * LD + j];
-            const float den = pr * pr + pim * pim;
-            const float dr = den > 0.f ? pr / den : 0.f, di = den > 0.f ? -pim / den : 0.f;
-            if (idx == j) {
-                resr = dr;
-                resi = di;
-            } else {  // -(1/U_jj) * s
-                resr = -(dr * sr - di * si);
-                resi = -(dr * si + di * sr);
-            }
-        }
-        __syncthreads();
     }
     __syncthreads();
+    // phases d = 1..3: one 32 x 32 target at a time, two outputs (r, c) and (r, c + 16) per thread
+    const int r = t >> 4, c = t & 15;
+    for (int d = 1; d < TB / DB; ++d) {
+        for (int side = 0; side < 2; ++side) {
+            const int ib = side == 0 ? d : 0, ie = side == 0 ? TB / DB : TB / DB - d;
+            for (int i = ib; i < ie; ++i) {
+                const int j = side == 0 ? i - d : i + d;
+                const int kb0 = side == 0 ? j : i + 1, kb1 = side == 0 ? i - 1 : j;
+                float t0r = 0.f, t0i = 0.f, t1r = 0.f, t1i = 0.f;
+                for (int kb = kb0; kb <= kb1; ++kb) {
+                    const float* gr = re + (size_t)(o + DB * i + r) * mp + o + DB * kb;
+                    const float* gi = im + (size_t)(o + DB * i + r) * mp + o + DB * kb;
+                    const bool dz = kb == j;  // the inverted diagonal block of column block j
+#pragma unroll 8
+                    for (int kk = 0; kk < DB; ++kk) {
+                        const float sr = __ldcg(gr + kk), si = __ldcg(gi + kk);  // L2: written above
+                        const int zi = (DB * kb + kk) * LD + DB * j;
+                        float z0r = Ar[zi + c], z0i = Ai[zi + c], z1r = Ar[zi + c + 16], z1i = Ai[zi + c + 16];
+                        if (dz) {  // L side: unit lower; U side: upper with the inverted diagonal
+                            if (side == 0) {
+                                if (kk < c) z0r = z0i = 0.f;
+                                else if (kk == c) z0r = 1.f, z0i = 0.f;
+                                if (kk < c + 16) z1r = z1i = 0.f;
+                                else if (kk == c + 16) z1r = 1.f, z1i = 0.f;
+                            } else {
+                                if (kk > c) z0r = z0i = 0.f;
+                                if (kk > c + 16) z1r = z1i = 0.f;
+                            }
+                        }
+                        t0r += sr * z0r - si * z0i;
+                        t0i += sr * z0i + si * z0r;
+                        t1r += sr * z1r - si * z1i;
+                        t1i += sr * z1i + si * z1r;
+                    }
+                }
+                Tr[r * (DB + 1) + c] = t0r;
+                Ti[r * (DB + 1) + c] = t0i;
+                Tr[r * (DB + 1) + c + 16] = t1r;
+                Ti[r * (DB + 1) + c + 16] = t1i;
+                __syncthreads();
+                // Z_ij = -Z_ii T: L side unit lower (kk <= r), U side upper (kk >= r)
+                float o0r = 0.f, o0i = 0.f, o1r = 0.f, o1i = 0.f;
+                const int k0 = side == 0 ? 0 : r, k1 = side == 0 ? r : DB - 1;
+                for (int kk = k0; kk <= k1; ++kk) {
+                    float zr, zi;
+                    if (side == 0 && kk == r) {
+                        zr = 1.f;
+                        zi = 0.f;
+                    } else {
+                        zr = Ar[(DB * i + r) * LD + DB * i + kk];
+                        zi = Ai[(DB * i + r) * LD + DB * i + kk];
+                    }
+                    const float a0r = Tr[kk * (DB + 1) + c], a0i = Ti[kk * (DB + 1) + c];
+                    const float a1r = Tr[kk * (DB + 1) + c + 16], a1i = Ti[kk * (DB + 1) + c + 16];
+                    o0r += zr * a0r - zi * a0i;
+                    o0i += zr * a0i + zi * a0r;
+                    o1r += zr * a1r - zi * a1i;
+                    o1i += zr * a1i + zi * a1r;
+                }
+                const int oi = (DB * i + r) * LD + DB * j;
+                Ar[oi + c] = -o0r;
+                Ai[oi + c] = -o0i;
+                Ar[oi + c + 16] = -o1r;
+                Ai[oi + c + 16] = -o1i;
+                __syncthreads();
+            }
+        }
+    }
     // pack: L^{-1} as A' (row i, K' = [Re | Im] of L^{-1}[i][:]), U^{-1} as B'
     constexpr int EPS = Cfg::PER_CORE;
     constexpr int SEGS = 2 * TB / EPS;  // segments per packed row
