@@ -1,29 +1,26 @@
-// Two-level blocked LU of the Strang blocks for the tensor-core precisions.
-//
-// Outer panels of TB = 128 columns.  Inside an outer panel the NB = 32 steps run
-// on CUDA cores restricted to the panel (diagonal LU, L21 rows over the whole
-// height, U12 columns inside the panel, rank-32 updates inside the panel), then the
-// outer row panel U12 = L11^{-1} A12 is formed by four 32-row solves and
-// rank-32 updates of the panel rows.  The outer trailing matrix then receives the
-// whole rank-128 update A22 -= L21 U12 in ONE complex GEMM with K' = 2 x 128 on
-// tcgen05 -- four times fewer passes over the trailing matrix than NB = 32.
+// Tensor-core tiles of the two-level blocked LU of the Strang blocks (FDE_TF32,
+// FDE_BF16, FDE_TF32X3).  Outer panels of TB = 128 columns; per panel the
+// diagonal block is factored and its triangles inverted on CUDA cores, and the
+// panel products L21 = A21 U11^{-1}, U12 = L11^{-1} A12 and the rank-128 trailing
+// update A22 -= L21 U12 run here, each as complex GEMMs with K' = 2 x 128.
 //
 // Complex product as one real GEMM (N' = 2 x 128 outputs side by side):
-//   A' = [Re L21 | Im L21]                                  128 rows x K' = 256
-//   B' = [[Re U12 ; -Im U12] | [Im U12 ; Re U12]]^T        256 rows x K'
-//   D  = A' B'^T:  D[:, 0:128] = Re(L21 U12),  D[:, 128:256] = Im(L21 U12).
-// The panel kernels write A' and B' pre-packed as K-chunks of 64 bytes per row,
-// each chunk in the canonical no-swizzle K-major core-matrix layout (8 rows x 16 B
-// core matrices, LBO = 128 B along K, SBO = 512 B between 8-row groups), so one
-// bulk copy lands a chunk of a tile in shared memory.
+//   A' = [Re L | Im L]                                      128 rows x K' = 256
+//   B' = [[Re U ; -Im U] | [Im U ; Re U]]^T                256 rows x K'
+//   D  = A' B'^T:  D[:, 0:128] = Re(L U),  D[:, 128:256] = Im(L U).
+// Operands are pre-packed as K-chunks of 64 bytes per row, each chunk in the
+// canonical no-swizzle K-major core-matrix layout (8 rows x 16 B core matrices,
+// LBO = 128 B along K, SBO = 512 B between 8-row groups), so one bulk copy lands
+// a chunk of a tile in shared memory.
 //
-// The update kernel (one 128 x 128 complex output tile per CTA, 128 threads):
-//   * issues bulk copies of its C tile (Re and Im rows) into shared memory at
-//     once, so the read of C overlaps the whole main loop;
-//   * streams the K-chunks through a 3-stage full / empty mbarrier ring, one
-//     thread issuing the MMAs (M = 128, N = 256, accumulator in 256 TMEM columns);
-//   * subtracts D (tcgen05.ld) from the C tile in shared memory and writes the
-//     tile back with bulk copies.
+// The tile kernel (one 128 x 128 complex output tile per CTA, 128 threads):
+//   * streams the K-chunks through a full / empty mbarrier ring, one thread
+//     issuing the MMAs (M = 128, N = 256, accumulator in 256 TMEM columns);
+//   * update mode (C -= D): prefetches its C rows into L2 at the start, runs an
+//     8-stage ring (192 KB in flight), then copies C from L2 into the freed ring,
+//     subtracts D (tcgen05.ld) and writes the tile back with bulk copies;
+//   * store mode (C = D): a 3-stage ring (two CTAs per SM) and D goes from TMEM
+//     straight to HBM; C is never read.
 // Every mbarrier wait is bounded; on timeout the CTA records an error, waits
 // (bounded) for its own copies and MMAs, frees its TMEM and returns.
 #pragma once
@@ -38,7 +35,9 @@ constexpr int TB = 128;             // outer panel width (complex K of the tenso
 constexpr int T2_BM = 128;          // output rows per CTA
 constexpr int T2_BN = 128;          // complex output columns per CTA (N' = 256)
 constexpr int T2_KP = 2 * TB;       // K' = 256 real (one product)
-constexpr int T2_STAGES = 3;
+constexpr int T2_STAGES = 3;       // store mode
+constexpr int T2_STAGES_UPD = 8;   // update mode
+constexpr int T2_STAGES_MAX = 8;
 constexpr int T2_CROW = 528;        // bytes per C-tile row in shared memory (512 + 16 pad, 16-B aligned)
 constexpr int T2_C_BYTES = T2_BM * T2_CROW;  // one plane
 
@@ -57,7 +56,8 @@ struct Tc2 {
     static constexpr int A_TILE = NCH * A_CHUNK;
     static constexpr int B_TILE = NCH * B_CHUNK;
     static constexpr int STAGE = A_CHUNK + B_CHUNK;
-    static constexpr int SMEM = 2 * T2_C_BYTES + T2_STAGES * STAGE;
+    static constexpr int SMEM = T2_STAGES_UPD * STAGE;  // the C tile reuses the ring after the main loop
+    static_assert(SMEM >= 2 * T2_C_BYTES, "C tile must fit the freed operand ring");
     // Store mode (no C tile): the operand ring only, padded so that at most two CTAs
     // (2 x 256 TMEM columns) share an SM.
     static constexpr int SMEM_STORE = T2_STAGES * STAGE > 80 * 1024 ? T2_STAGES * STAGE : 80 * 1024;
@@ -125,13 +125,17 @@ __device__ __forceinline__ void bulk_s2g(void* dst_gmem, const void* src_smem, u
                  "r"(tc::smem_u32(src_smem)), "r"(bytes)
                  : "memory");
 }
+__device__ __forceinline__ void bulk_prefetch_l2(const void* gmem, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(gmem), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 // One 128 x 128 complex output tile at (r0, c0) of one block, D = A' B'^T from the
 // packed tiles ga (A') and gb (B'):
-//   STORE = false: C[r0.., c0..] -= D (C staged in shared memory, read early);
+//   STORE = false: C[r0.., c0..] -= D (C prefetched into L2 at the start, staged
+//                  in the freed operand ring after the last MMA);
 //   STORE = true:  C[r0.., c0..]  = D (no read of C; D goes from TMEM to HBM).
 template <int KIND, bool STORE>
 __device__ __forceinline__ void tc2_tile_body(int mp, int r0, int c0, float* __restrict__ re_plane,
@@ -139,10 +143,11 @@ __device__ __forceinline__ void tc2_tile_body(int mp, int r0, int c0, float* __r
                                               const unsigned char* __restrict__ gb, int* __restrict__ err) {
     using Cfg = Tc2<KIND>;
     extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char* sCr = smem;
+    constexpr int NS = STORE ? T2_STAGES : T2_STAGES_UPD;
+    unsigned char* sStage = smem;
+    unsigned char* sCr = smem;  // update mode: the C tile, after the last MMA
     unsigned char* sCi = smem + T2_C_BYTES;
-    unsigned char* sStage = STORE ? smem : smem + 2 * T2_C_BYTES;  // store mode: no C tile
-    __shared__ __align__(8) uint64_t bar_c, bar_mma, bar_full[T2_STAGES], bar_empty[T2_STAGES];
+    __shared__ __align__(8) uint64_t bar_c, bar_mma, bar_full[T2_STAGES_MAX], bar_empty[T2_STAGES_MAX];
     __shared__ uint32_t tmem_base;
     __shared__ int ok_flag;
 
@@ -157,39 +162,37 @@ __device__ __forceinline__ void tc2_tile_body(int mp, int r0, int c0, float* __r
     if (threadIdx.x == 0) {
         tc::mbar_init(&bar_c, 1);
         tc::mbar_init(&bar_mma, 1);
-        for (int s = 0; s < T2_STAGES; ++s) {
+        for (int s = 0; s < NS; ++s) {
             tc::mbar_init(&bar_full[s], 1);
             tc::mbar_init(&bar_empty[s], 1);
         }
         tc::fence_barrier_init();
         ok_flag = 1;
-        // the C tile: every valid row of both planes
-        if (!STORE) tc::mbar_arrive_expect_tx(&bar_c, 2u * (uint32_t)nrows * row_bytes);
     }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tbase = tmem_base;
-    if (!STORE) {
+    if (!STORE) {  // C rows towards L2 while the operands stream
         const int r = threadIdx.x;
         if (r < nrows) {
-            tc::bulk_g2s(sCr + r * T2_CROW, gre + (size_t)(r0 + r) * mp + c0, row_bytes, &bar_c);
-            tc::bulk_g2s(sCi + r * T2_CROW, gim + (size_t)(r0 + r) * mp + c0, row_bytes, &bar_c);
+            bulk_prefetch_l2(gre + (size_t)(r0 + r) * mp + c0, row_bytes);
+            bulk_prefetch_l2(gim + (size_t)(r0 + r) * mp + c0, row_bytes);
         }
     }
     if (threadIdx.x == 0) {
         auto load_chunk = [&](int c) {
-            const int s = c % T2_STAGES;
+            const int s = c % NS;
             unsigned char* sa = sStage + s * Cfg::STAGE;
             tc::mbar_arrive_expect_tx(&bar_full[s], Cfg::STAGE);
             tc::bulk_g2s(sa, ga + (size_t)c * Cfg::A_CHUNK, Cfg::A_CHUNK, &bar_full[s]);
             tc::bulk_g2s(sa + Cfg::A_CHUNK, gb + (size_t)c * Cfg::B_CHUNK, Cfg::B_CHUNK, &bar_full[s]);
         };
-        for (int c = 0; c < T2_STAGES - 1 && c < Cfg::NCH; ++c) load_chunk(c);
+        for (int c = 0; c < NS - 1 && c < Cfg::NCH; ++c) load_chunk(c);
         bool ok = true;
         for (int c = 0; c < Cfg::NCH && ok; ++c) {
-            const int s = c % T2_STAGES;
-            if (!tc::mbar_wait(&bar_full[s], (c / T2_STAGES) & 1)) {
+            const int s = c % NS;
+            if (!tc::mbar_wait(&bar_full[s], (c / NS) & 1)) {
                 ok = false;
                 break;
             }
@@ -206,11 +209,11 @@ __device__ __forceinline__ void tc2_tile_body(int mp, int r0, int c0, float* __r
             }
             tc::mma_commit(&bar_empty[s]);
             // refill the stage freed by chunk c-1 with chunk c + STAGES - 1
-            const int nxt = c + T2_STAGES - 1;
+            const int nxt = c + NS - 1;
             if (nxt < Cfg::NCH) {
                 if (c >= 1) {
-                    const int sp = (c - 1) % T2_STAGES;
-                    if (!tc::mbar_wait(&bar_empty[sp], ((c - 1) / T2_STAGES) & 1)) {
+                    const int sp = (c - 1) % NS;
+                    if (!tc::mbar_wait(&bar_empty[sp], ((c - 1) / NS) & 1)) {
                         ok = false;
                         break;
                     }
@@ -229,11 +232,26 @@ __device__ __forceinline__ void tc2_tile_body(int mp, int r0, int c0, float* __r
     const bool ok = ok_flag != 0;
     bool mine = false;
     if (ok) {
-        mine = tc::mbar_wait(&bar_mma, 0) && (STORE || tc::mbar_wait(&bar_c, 0));
+        mine = tc::mbar_wait(&bar_mma, 0);
         if (!mine && lane == 0) atomicCAS(err, 0, 2);
     }
-    const bool done = __syncthreads_and(mine) != 0;  // uniform across the CTA
+    bool done = __syncthreads_and(mine) != 0;  // uniform across the CTA
     tc::fence_after_sync();
+    bool staged = false;  // update mode: C copies in flight into the ring
+    if (!STORE && ok && done) {
+        // every MMA has completed, so the operand ring is free for the C tile
+        if (threadIdx.x == 0) tc::mbar_arrive_expect_tx(&bar_c, 2u * (uint32_t)nrows * row_bytes);
+        __syncthreads();
+        const int r = threadIdx.x;
+        if (r < nrows) {
+            tc::bulk_g2s(sCr + r * T2_CROW, gre + (size_t)(r0 + r) * mp + c0, row_bytes, &bar_c);
+            tc::bulk_g2s(sCi + r * T2_CROW, gim + (size_t)(r0 + r) * mp + c0, row_bytes, &bar_c);
+        }
+        staged = true;
+        const bool cok = tc::mbar_wait(&bar_c, 0);
+        if (!cok && lane == 0) atomicCAS(err, 0, 2);
+        done = __syncthreads_and(cok) != 0;
+    }
     if (STORE && ok && done) {
         const int r = warp * 32 + lane;  // TMEM lane = tile row
         const uint32_t lane_addr = tbase + ((uint32_t)(warp * 32) << 16);
@@ -287,7 +305,7 @@ __device__ __forceinline__ void tc2_tile_body(int mp, int r0, int c0, float* __r
         }
     } else if (!(ok && done)) {
         // bounded: let in-flight copies and MMAs land before TMEM is released
-        if (!STORE) tc::mbar_wait(&bar_c, 0);
+        if (staged) tc::mbar_wait(&bar_c, 0);
         tc::mbar_wait(&bar_mma, 0);
     }
     tc::fence_before_sync();
