@@ -43,17 +43,18 @@ static cudaEvent_t next_event(Problem& P) {
     return P.ev_pool[P.ev_used++];
 }
 
-StageTimer::StageTimer(Problem& P, int stage) : P_(&P), stage_(stage) {
+StageTimer::StageTimer(Problem& P, int stage, cudaStream_t on)
+    : P_(&P), stage_(stage), st_(on ? on : P.stream) {
     if (!P.prof) return;
     e0_ = next_event(P);
-    if (e0_) cudaEventRecord(e0_, P.stream);
+    if (e0_) cudaEventRecord(e0_, st_);
 }
 
 StageTimer::~StageTimer() {
     if (!P_->prof || !e0_) return;
     cudaEvent_t e1 = next_event(*P_);
     if (!e1) return;
-    cudaEventRecord(e1, P_->stream);
+    cudaEventRecord(e1, st_);
     P_->prof_rec[stage_].push_back({e0_, e1});
 }
 
@@ -434,6 +435,8 @@ void fde_problem_destroy(fde_problem* h) {
     Problem& P = h->P;
     if (P.stream) cudaStreamSynchronize(P.stream);
     else cudaDeviceSynchronize();
+    if (P.lu_hi) cudaStreamSynchronize(P.lu_hi);
+    if (P.lu_lo) cudaStreamSynchronize(P.lu_lo);
     free_workspace(P);
     void* bufs[] = {P.d_start, P.d_a, P.d_b, P.d_dplus, P.d_dminus, P.d_u0, P.d_f, P.d_g, P.d_twL, P.d_twL32,
                     P.d_sym, P.d_sym32, P.d_tws, P.d_tws32, P.d_phi, P.d_psi, P.d_b_rhs, P.d_work, P.d_rhat,
@@ -441,6 +444,10 @@ void fde_problem_destroy(fde_problem* h) {
     for (void* b : bufs) dfree(b);
     if (h->pinned) cudaFreeHost(h->pinned);
     for (cudaEvent_t e : P.ev_pool) cudaEventDestroy(e);
+    for (cudaEvent_t e : P.lu_ev)
+        if (e) cudaEventDestroy(e);
+    if (P.lu_hi) cudaStreamDestroy(P.lu_hi);
+    if (P.lu_lo) cudaStreamDestroy(P.lu_lo);
     delete h;
 }
 

@@ -177,6 +177,9 @@ struct Problem {
     size_t fac_bytes = 0;
     void* d_pack = nullptr;     // packed tensor-core operand tiles of the LU panels
     size_t pack_bytes = 0;
+    // tensor-core LU look-ahead: panel chain on lu_hi, interior updates on lu_lo
+    cudaStream_t lu_hi = nullptr, lu_lo = nullptr;
+    cudaEvent_t lu_ev[3] = {nullptr, nullptr, nullptr};  // fork / cross done / interior done
 
     // Krylov workspace
     int restart_cap = 0;
@@ -234,12 +237,13 @@ int launch_gather_scalars(const InstDev* I, int ninst, double* out, cudaStream_t
 // problem's profiler is on.
 class StageTimer {
   public:
-    StageTimer(Problem& P, int stage);
+    StageTimer(Problem& P, int stage, cudaStream_t on = nullptr);  // on: default P.stream
     ~StageTimer();
 
   private:
     Problem* P_;
     int stage_;
+    cudaStream_t st_;
     cudaEvent_t e0_ = nullptr;
 };
 
