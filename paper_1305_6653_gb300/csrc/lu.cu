@@ -42,11 +42,17 @@ __device__ __forceinline__ double j_entry(int i, int j, double dxa, const double
 
 // One CTA row-loop per matrix row, threads along the columns (no index division).
 // FP64 blocks are formed in FP64; FP32 blocks in FP32 from FP32 copies of the
-// per-row coefficients dx^-alpha d+_i, dx^-alpha d-_i and of h psi_k.
+// per-row coefficients dx^-alpha d+_i, dx^-alpha d-_i and of h psi_k.  The CTA
+// stages g_0..g_{m+1} in shared memory in the block's precision (dynamic shared
+// memory of (m + 2) elements), so no element converts FP64 values.
 template <typename T>
 __device__ __forceinline__ void form_body(int m, int mp, double h, double dxa, const double* __restrict__ g,
                                           const double* __restrict__ dp, const double* __restrict__ dm, double2 ph,
                                           double2 ps, T* __restrict__ re, int row0, int rowstride) {
+    extern __shared__ __align__(16) unsigned char form_smem[];
+    T* gs = reinterpret_cast<T*>(form_smem);
+    for (int q = threadIdx.x; q < m + 2; q += blockDim.x) gs[q] = (T)g[q];
+    __syncthreads();
     const T hpr = (T)(h * ps.x), hpi = (T)(h * ps.y);
     T* im = re + (size_t)mp * mp;
     for (int i = row0; i < mp; i += rowstride) {
@@ -65,8 +71,8 @@ __device__ __forceinline__ void form_body(int m, int mp, double h, double dxa, c
             if (j < m) {
                 const int a = i - j + 1, b = j - i + 1;
                 T jv = T(0);
-                if (a >= 0) jv += rp * (T)g[a];
-                if (b >= 0) jv += rm * (T)g[b];
+                if (a >= 0) jv += rp * gs[a];
+                if (b >= 0) jv += rm * gs[b];
                 vr = -hpr * jv;
                 vi = -hpi * jv;
                 if (i == j) {
@@ -677,8 +683,9 @@ static int run_lu(Problem& P, cudaStream_t st) {
     {
         dim3 grid(mp < 64 ? mp : 64, nb);
         StageTimer t(P, FDE_STAGE_FORM);
-        form_blocks_kernel<T><<<grid, 256, 0, st>>>(P.m, mp, P.h, P.dxa, P.d_g, P.d_dplus, P.d_dminus, P.d_phi,
-                                                   P.d_psi, fac);
+        const size_t gsm = (size_t)(P.m + 2) * sizeof(T);
+        form_blocks_kernel<T><<<grid, 256, gsm, st>>>(P.m, mp, P.h, P.dxa, P.d_g, P.d_dplus, P.d_dminus, P.d_phi,
+                                                      P.d_psi, fac);
         FDE_LAUNCH_CHECK("form_blocks_kernel");
     }
     const size_t panel_smem = (size_t)RC * (NB + 1) * sizeof(C);
@@ -714,11 +721,24 @@ static int run_lu(Problem& P, cudaStream_t st) {
 // ---------------------------------------------------------------------------
 template <int KIND>
 __global__ void __launch_bounds__(128)
-lu_update_tc2_kernel(int mp, int R0, int nt, float* __restrict__ fac, const unsigned char* __restrict__ apack,
-                     const unsigned char* __restrict__ bpack, size_t pa, size_t pb, int* __restrict__ err) {
-    const int k = blockIdx.y;
-    tc2_update_body<KIND>(mp, R0, fac + (size_t)k * 2 * mp * mp, apack + k * pa, bpack + k * pb, err,
-                          blockIdx.x / nt, blockIdx.x % nt);
+lu_update_tc2_kernel(int mp, int R0, int nt, int part, float* __restrict__ fac,
+                     const unsigned char* __restrict__ apack, const unsigned char* __restrict__ bpack, size_t pa,
+                     size_t pb, int* __restrict__ err) {
+    // part 0: all nt^2 tiles; 1: the cross ti = 0 or tj = 0 (2 nt - 1 tiles: the next
+    // panel's rows and columns); 2: the interior ti, tj >= 1 ((nt - 1)^2 tiles)
+    const int k = blockIdx.y, x = blockIdx.x;
+    int ti, tj;
+    if (part == 0) {
+        ti = x / nt;
+        tj = x % nt;
+    } else if (part == 1) {
+        ti = x < nt ? 0 : x - nt + 1;
+        tj = x < nt ? x : 0;
+    } else {
+        ti = 1 + x / (nt - 1);
+        tj = 1 + x % (nt - 1);
+    }
+    tc2_update_body<KIND>(mp, R0, fac + (size_t)k * 2 * mp * mp, apack + k * pa, bpack + k * pb, err, ti, tj);
 }
 
 template <int KIND>
@@ -776,14 +796,14 @@ constexpr int D128_LD = TB + 1;  // shared row pitch in floats (column reads con
 constexpr int D128_THREADS = 512;
 constexpr int DB = 32;           // leaf block of the blocked LU and inversion
 
-// planes [128][129] x 2 | T [32][33] x 2 | per-warp vectors [8][32] complex | 1/U_cc of a leaf [32] complex
+// planes [128][129] x 2 | T [2 targets][32][33] x 2 | per-warp vectors [8][32] complex | 1/U_cc of a leaf [32]
 static size_t diag128_smem() {
-    return (size_t)(2 * TB * D128_LD + 2 * DB * (DB + 1)) * sizeof(float) + (size_t)(8 * DB + DB) * sizeof(float2);
+    return (size_t)(2 * TB * D128_LD + 4 * DB * (DB + 1)) * sizeof(float) + (size_t)(8 * DB + DB) * sizeof(float2);
 }
 
 // One CTA per Strang block: LU (no pivoting) of the W x W block at (o, o), W = 128
 // (or 64 for a last panel), blocked over 32 x 32 leaves in shared memory:
-//   leaf LU by one warp; panel solves X U_pp = A (rows) and L_pp X = A (columns)
+//   leaf LU by four warps; panel solves X U_pp = A (rows) and L_pp X = A (columns)
 //   with one thread per row / column and the 32 values in registers; rank-32
 //   trailing update with 4 x 4 complex register tiles.
 // L\U and 1/U_ii are written back.  With invert (a trailing matrix follows, W = 128)
@@ -803,9 +823,9 @@ __device__ __forceinline__ void diag128_body(int mp, int o, float* __restrict__ 
     extern __shared__ __align__(16) float dsm[];
     float* Ar = dsm;
     float* Ai = dsm + TB * LD;
-    float* Tr = dsm + 2 * TB * LD;
-    float* Ti = Tr + DB * (DB + 1);
-    float2* vec = reinterpret_cast<float2*>(Ti + DB * (DB + 1));  // [8][32]
+    float* Tr = dsm + 2 * TB * LD;          // [2][32][33]
+    float* Ti = Tr + 2 * DB * (DB + 1);     // [2][32][33]
+    float2* vec = reinterpret_cast<float2*>(Ti + 2 * DB * (DB + 1));  // [8][32]
     float2* pinv = vec + 8 * DB;                                   // [32]
     float* im = re + (size_t)mp * mp;
     const int W = mp - o < TB ? mp - o : TB;
@@ -818,31 +838,36 @@ __device__ __forceinline__ void diag128_body(int mp, int o, float* __restrict__ 
     }
     __syncthreads();
     for (int P0 = 0; P0 < W; P0 += DB) {
-        if (warp == 0) {  // leaf LU, lane = row
+        if (warp < 4) {  // leaf LU: lane = row; warp 0 scales column c, warp w updates columns c+1+w, c+5+w, ..
             const int ri = (P0 + lane) * LD + P0;
             for (int c = 0; c < DB; ++c) {
                 const int ci = (P0 + c) * LD + P0;
-                const float pr = Ar[ci + c], pim = Ai[ci + c];
-                const float den = pr * pr + pim * pim;
-                const bool bad = !(den > 0.f) || !isfinite(den);
-                const float ir = bad ? 0.f : pr / den, ii = bad ? 0.f : -pim / den;
-                if (lane == c) {
-                    if (bad) atomicCAS(info, 0, o + P0 + c + 1);
-                    pinv[c] = make_float2(ir, ii);
-                    dk[o + P0 + c] = make_float2(ir, ii);
+                if (warp == 0) {
+                    const float pr = Ar[ci + c], pim = Ai[ci + c];
+                    const float den = pr * pr + pim * pim;
+                    const bool bad = !(den > 0.f) || !isfinite(den);
+                    const float ir = bad ? 0.f : pr / den, ii = bad ? 0.f : -pim / den;
+                    if (lane == c) {
+                        if (bad) atomicCAS(info, 0, o + P0 + c + 1);
+                        pinv[c] = make_float2(ir, ii);
+                        dk[o + P0 + c] = make_float2(ir, ii);
+                    }
+                    if (lane > c) {
+                        const float ar = Ar[ri + c], ai = Ai[ri + c];
+                        Ar[ri + c] = ar * ir - ai * ii;
+                        Ai[ri + c] = ar * ii + ai * ir;
+                    }
                 }
+                named_sync(1, 128);  // multipliers of column c
                 if (lane > c) {
-                    const float ar = Ar[ri + c], ai = Ai[ri + c];
-                    const float lr = ar * ir - ai * ii, li = ar * ii + ai * ir;
-                    Ar[ri + c] = lr;
-                    Ai[ri + c] = li;
-                    for (int cc = c + 1; cc < DB; ++cc) {
+                    const float lr = Ar[ri + c], li = Ai[ri + c];
+                    for (int cc = c + 1 + warp; cc < DB; cc += 4) {
                         const float ur = Ar[ci + cc], ui = Ai[ci + cc];
                         Ar[ri + cc] -= lr * ur - li * ui;
                         Ai[ri + cc] -= lr * ui + li * ur;
                     }
                 }
-                __syncwarp();
+                named_sync(1, 128);  // step c complete before the next pivot
             }
         }
         __syncthreads();
@@ -982,70 +1007,95 @@ __device__ __forceinline__ void diag128_body(int mp, int o, float* __restrict__ 
         }
     }
     __syncthreads();
-    // phases d = 1..3: one 32 x 32 target at a time, two outputs (r, c) and (r, c + 16) per thread
-    const int r = t >> 4, c = t & 15;
-    for (int d = 1; d < TB / DB; ++d) {
-        for (int side = 0; side < 2; ++side) {
-            const int ib = side == 0 ? d : 0, ie = side == 0 ? TB / DB : TB / DB - d;
-            for (int i = ib; i < ie; ++i) {
-                const int j = side == 0 ? i - d : i + d;
-                const int kb0 = side == 0 ? j : i + 1, kb1 = side == 0 ? i - 1 : j;
-                float t0r = 0.f, t0i = 0.f, t1r = 0.f, t1i = 0.f;
-                for (int kb = kb0; kb <= kb1; ++kb) {
-                    const float* gr = re + (size_t)(o + DB * i + r) * mp + o + DB * kb;
-                    const float* gi = im + (size_t)(o + DB * i + r) * mp + o + DB * kb;
-                    const bool dz = kb == j;  // the inverted diagonal block of column block j
-#pragma unroll 8
+    // phases d = 1..3: in round q the L-side target (i, i-d), i = d + q, runs on threads
+    // 0..255 and the U-side target (q, q+d) on threads 256..511; a thread owns row r
+    // and the four columns c + 8u of its target
+    {
+        const bool lower = t < 256;
+        const int lt = t & 255, r = lt >> 3, c = lt & 7;
+        float* Th_r = Tr + (lower ? 0 : DB * (DB + 1));
+        float* Th_i = Ti + (lower ? 0 : DB * (DB + 1));
+        for (int d = 1; d < TB / DB; ++d) {
+            for (int q = 0; q < TB / DB - d; ++q) {
+                const int i = lower ? d + q : q;
+                const int j = lower ? i - d : i + d;
+                float tr[4] = {0.f, 0.f, 0.f, 0.f}, tim[4] = {0.f, 0.f, 0.f, 0.f};
+                // off-diagonal source blocks (L side kb in (j, i), U side kb in (i, j)): their
+                // originals were overwritten by earlier phases, so each is staged from the
+                // factor in L2 into this half's T buffer (free until T is stored)
+                for (int kq = 0; kq < d - 1; ++kq) {
+                    const int kb = lower ? j + 1 + kq : i + 1 + kq;
+                    for (int e = lt; e < DB * DB; e += 256) {
+                        const int rr = e >> 5, cc = e & 31;
+                        const size_t g = (size_t)(o + DB * i + rr) * mp + o + DB * kb + cc;
+                        Th_r[rr * (DB + 1) + cc] = __ldcg(re + g);
+                        Th_i[rr * (DB + 1) + cc] = __ldcg(im + g);
+                    }
+                    __syncthreads();
+#pragma unroll 4
                     for (int kk = 0; kk < DB; ++kk) {
-                        const float sr = __ldcg(gr + kk), si = __ldcg(gi + kk);  // L2: written above
-                        const int zi = (DB * kb + kk) * LD + DB * j;
-                        float z0r = Ar[zi + c], z0i = Ai[zi + c], z1r = Ar[zi + c + 16], z1i = Ai[zi + c + 16];
-                        if (dz) {  // L side: unit lower; U side: upper with the inverted diagonal
-                            if (side == 0) {
-                                if (kk < c) z0r = z0i = 0.f;
-                                else if (kk == c) z0r = 1.f, z0i = 0.f;
-                                if (kk < c + 16) z1r = z1i = 0.f;
-                                else if (kk == c + 16) z1r = 1.f, z1i = 0.f;
-                            } else {
-                                if (kk > c) z0r = z0i = 0.f;
-                                if (kk > c + 16) z1r = z1i = 0.f;
-                            }
+                        const float sr = Th_r[r * (DB + 1) + kk], si = Th_i[r * (DB + 1) + kk];
+                        const int zi = (DB * kb + kk) * LD + DB * j + c;
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const float zr = Ar[zi + 8 * u], zm = Ai[zi + 8 * u];
+                            tr[u] += sr * zr - si * zm;
+                            tim[u] += sr * zm + si * zr;
                         }
-                        t0r += sr * z0r - si * z0i;
-                        t0i += sr * z0i + si * z0r;
-                        t1r += sr * z1r - si * z1i;
-                        t1i += sr * z1i + si * z1r;
+                    }
+                    __syncthreads();
+                }
+                // the diagonal term: the target's own original block (still in place) times
+                // the inverted diagonal block of column block j, unit lower (L) / upper (U)
+                const int srow = (DB * i + r) * LD + DB * j;
+#pragma unroll 4
+                for (int kk = 0; kk < DB; ++kk) {
+                    const float sr = Ar[srow + kk], si = Ai[srow + kk];
+                    const int zi = (DB * j + kk) * LD + DB * j + c;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int col = c + 8 * u;
+                        float zr = Ar[zi + 8 * u], zm = Ai[zi + 8 * u];
+                        if (lower) {
+                            if (kk < col) zr = zm = 0.f;
+                            else if (kk == col) zr = 1.f, zm = 0.f;
+                        } else if (kk > col) {
+                            zr = zm = 0.f;
+                        }
+                        tr[u] += sr * zr - si * zm;
+                        tim[u] += sr * zm + si * zr;
                     }
                 }
-                Tr[r * (DB + 1) + c] = t0r;
-                Ti[r * (DB + 1) + c] = t0i;
-                Tr[r * (DB + 1) + c + 16] = t1r;
-                Ti[r * (DB + 1) + c + 16] = t1i;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    Th_r[r * (DB + 1) + c + 8 * u] = tr[u];
+                    Th_i[r * (DB + 1) + c + 8 * u] = tim[u];
+                }
                 __syncthreads();
-                // Z_ij = -Z_ii T: L side unit lower (kk <= r), U side upper (kk >= r)
-                float o0r = 0.f, o0i = 0.f, o1r = 0.f, o1i = 0.f;
-                const int k0 = side == 0 ? 0 : r, k1 = side == 0 ? r : DB - 1;
-                for (int kk = k0; kk <= k1; ++kk) {
-                    float zr, zi;
-                    if (side == 0 && kk == r) {
-                        zr = 1.f;
-                        zi = 0.f;
-                    } else {
-                        zr = Ar[(DB * i + r) * LD + DB * i + kk];
-                        zi = Ai[(DB * i + r) * LD + DB * i + kk];
-                    }
-                    const float a0r = Tr[kk * (DB + 1) + c], a0i = Ti[kk * (DB + 1) + c];
-                    const float a1r = Tr[kk * (DB + 1) + c + 16], a1i = Ti[kk * (DB + 1) + c + 16];
-                    o0r += zr * a0r - zi * a0i;
-                    o0i += zr * a0i + zi * a0r;
-                    o1r += zr * a1r - zi * a1i;
-                    o1i += zr * a1i + zi * a1r;
+                // Z_ij = -Z_ii T: L side unit lower (kk < r, plus T[r]), U side upper (kk >= r)
+                float orr[4], oii[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    orr[u] = lower ? Th_r[r * (DB + 1) + c + 8 * u] : 0.f;
+                    oii[u] = lower ? Th_i[r * (DB + 1) + c + 8 * u] : 0.f;
                 }
-                const int oi = (DB * i + r) * LD + DB * j;
-                Ar[oi + c] = -o0r;
-                Ai[oi + c] = -o0i;
-                Ar[oi + c + 16] = -o1r;
-                Ai[oi + c + 16] = -o1i;
+                const int zrow = (DB * i + r) * LD + DB * i;
+                const int k0 = lower ? 0 : r, k1 = lower ? r : DB;
+                for (int kk = k0; kk < k1; ++kk) {
+                    const float zr = Ar[zrow + kk], zm = Ai[zrow + kk];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const float ar = Th_r[kk * (DB + 1) + c + 8 * u], ai = Th_i[kk * (DB + 1) + c + 8 * u];
+                        orr[u] += zr * ar - zm * ai;
+                        oii[u] += zr * ai + zm * ar;
+                    }
+                }
+                const int oi = (DB * i + r) * LD + DB * j + c;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    Ar[oi + 8 * u] = -orr[u];
+                    Ai[oi + 8 * u] = -oii[u];
+                }
                 __syncthreads();
             }
         }
@@ -1207,6 +1257,23 @@ lu_panel_tc2_batched(const BlkDev* __restrict__ B, int o, int R0, int ntg, int* 
     }
 }
 
+static int ensure_lu_streams(Problem& P) {
+    if (P.lu_hi) return FDE_OK;
+    int least = 0, greatest = 0;
+    FDE_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    FDE_CUDA_TRY(cudaStreamCreateWithPriority(&P.lu_hi, cudaStreamNonBlocking, greatest));
+    FDE_CUDA_TRY(cudaStreamCreateWithPriority(&P.lu_lo, cudaStreamNonBlocking, least));
+    for (cudaEvent_t& e : P.lu_ev) FDE_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    return FDE_OK;
+}
+
+// Two-level tensor-core LU with look-ahead.  The panel chain (diagonal block,
+// packing, panel products) and the part of each trailing update that the next
+// panel needs (its rows and columns: the cross tiles) run on a high-priority
+// stream; the interior of the trailing update runs on a low-priority stream
+// alongside the next panel's chain.  The packed L21 / U12 operands alternate
+// between two buffers by step parity, so the interior update of step o keeps
+// reading its operands while step o + 1 packs its own.
 template <int KIND>
 static int run_lu_tc(Problem& P, cudaStream_t st) {
     using Cfg = Tc2<KIND>;
@@ -1216,7 +1283,7 @@ static int run_lu_tc(Problem& P, cudaStream_t st) {
     size_t pa, pb;
     tc2_pack_sizes<KIND>(mp, &pa, &pb);
     const size_t pi = (size_t)Cfg::A_TILE + Cfg::B_TILE;  // L11^{-1} (A') and U11^{-1} (B') per block
-    const size_t need = mp > TB ? (size_t)nb * (pa + pb + pi) : 0;
+    const size_t need = mp > TB ? (size_t)nb * (2 * (pa + pb) + pi) : 0;
     if (need > 0 && P.pack_bytes < need) {
         if (P.d_pack) cudaFree(P.d_pack);
         P.d_pack = nullptr;
@@ -1225,58 +1292,96 @@ static int run_lu_tc(Problem& P, cudaStream_t st) {
         P.pack_bytes = need;
         FDE_CUDA_TRY(cudaMemsetAsync(P.d_pack, 0, need, st));
     }
-    unsigned char* apack = reinterpret_cast<unsigned char*>(P.d_pack);
-    unsigned char* bpack = apack ? apack + (size_t)nb * pa : nullptr;
-    unsigned char* ipack = apack ? bpack + (size_t)nb * pb : nullptr;
-    {
-        dim3 grid(mp < 64 ? mp : 64, nb);
-        StageTimer t(P, FDE_STAGE_FORM);
-        form_blocks_kernel<float><<<grid, 256, 0, st>>>(P.m, mp, P.h, P.dxa, P.d_g, P.d_dplus, P.d_dminus, P.d_phi,
-                                                        P.d_psi, fac);
-        FDE_LAUNCH_CHECK("form_blocks_kernel");
-    }
+    unsigned char* base = reinterpret_cast<unsigned char*>(P.d_pack);
+    auto apk = [&](int o) { return base ? base + (size_t)((o / TB) & 1) * nb * (pa + pb) : nullptr; };
+    auto bpk = [&](int o) { return base ? apk(o) + (size_t)nb * pa : nullptr; };
+    unsigned char* ipack = base ? base + (size_t)2 * nb * (pa + pb) : nullptr;
     int rc = set_tc_attrs<KIND>();
     if (rc) return rc;
     FDE_CUDA_TRY(cudaFuncSetAttribute(lu_diag128_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)diag128_smem()));
     FDE_CUDA_TRY(cudaFuncSetAttribute(lu_panel_tc2_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       Cfg::SMEM_STORE));
-    for (int o = 0; o < mp; o += TB) {
-        const int W = mp - o < TB ? mp - o : TB;
-        const int R0 = o + W;
+    if ((rc = ensure_lu_streams(P))) return rc;
+    cudaStream_t sh = P.lu_hi, sl = P.lu_lo;
+    FDE_CUDA_TRY(cudaEventRecord(P.lu_ev[0], st));  // fork after the work already queued on st
+    FDE_CUDA_TRY(cudaStreamWaitEvent(sh, P.lu_ev[0], 0));
+    FDE_CUDA_TRY(cudaStreamWaitEvent(sl, P.lu_ev[0], 0));
+
+    // diagonal block, then (if a trailing matrix follows) packing and panel products
+    auto panel = [&](int o) -> int {
+        const int R0 = o + (mp - o < TB ? mp - o : TB);
         const bool more = R0 < mp;
         {
-            StageTimer t(P, FDE_STAGE_LU_DIAG);
-            lu_diag128_kernel<KIND><<<nb, D128_THREADS, diag128_smem(), st>>>(mp, o, fac, dinv, P.d_info, ipack, pi,
+            StageTimer t(P, FDE_STAGE_LU_DIAG, sh);
+            lu_diag128_kernel<KIND><<<nb, D128_THREADS, diag128_smem(), sh>>>(mp, o, fac, dinv, P.d_info, ipack, pi,
                                                                               more ? 1 : 0);
             FDE_LAUNCH_CHECK("lu_diag128_kernel");
         }
-        if (!more) break;
+        if (!more) return FDE_OK;
         const int nt = cdiv(mp - R0, T2_BM);
         const long items = 2L * (mp - R0) * (TB / Cfg::PER_CORE);
         const int pgrid = (int)std::min<long>((items + 255) / 256, 1024);
         {
-            StageTimer t(P, FDE_STAGE_LU_PACK);
-            lu_pack_panel_kernel<KIND><<<dim3(pgrid, nb), 256, 0, st>>>(mp, o, R0, fac, apack, bpack, pa, pb);
+            StageTimer t(P, FDE_STAGE_LU_PACK, sh);
+            lu_pack_panel_kernel<KIND><<<dim3(pgrid, nb), 256, 0, sh>>>(mp, o, R0, fac, apk(o), bpk(o), pa, pb);
             FDE_LAUNCH_CHECK("lu_pack_panel_kernel");
         }
         {
-            StageTimer t(P, FDE_STAGE_LU_PANEL_TC);
-            lu_panel_tc2_kernel<KIND><<<dim3(2 * nt, nb), 128, Cfg::SMEM_STORE, st>>>(mp, o, R0, nt, fac, apack, bpack,
-                                                                                    ipack, pa, pb, pi, P.d_err);
+            StageTimer t(P, FDE_STAGE_LU_PANEL_TC, sh);
+            lu_panel_tc2_kernel<KIND><<<dim3(2 * nt, nb), 128, Cfg::SMEM_STORE, sh>>>(mp, o, R0, nt, fac, apk(o),
+                                                                                    bpk(o), ipack, pa, pb, pi,
+                                                                                    P.d_err);
             FDE_LAUNCH_CHECK("lu_panel_tc2_kernel");
         }
         {
-            StageTimer t(P, FDE_STAGE_LU_PACK);
-            lu_pack_panel_kernel<KIND><<<dim3(pgrid, nb), 256, 0, st>>>(mp, o, R0, fac, apack, bpack, pa, pb);
+            StageTimer t(P, FDE_STAGE_LU_PACK, sh);
+            lu_pack_panel_kernel<KIND><<<dim3(pgrid, nb), 256, 0, sh>>>(mp, o, R0, fac, apk(o), bpk(o), pa, pb);
             FDE_LAUNCH_CHECK("lu_pack_panel_kernel");
         }
-        StageTimer t(P, FDE_STAGE_LU_TC);
-        lu_update_tc2_kernel<KIND><<<dim3(nt * nt, nb), 128, Cfg::SMEM, st>>>(mp, R0, nt, fac, apack, bpack, pa, pb,
-                                                                             P.d_err);
-        FDE_LAUNCH_CHECK("lu_update_tc2_kernel");
-    }
-    return FDE_OK;
+        return FDE_OK;
+    };
+    auto body = [&]() -> int {
+        {
+            dim3 grid(mp < 64 ? mp : 64, nb);
+            StageTimer t(P, FDE_STAGE_FORM, sh);
+            const size_t gsm = (size_t)(P.m + 2) * sizeof(float);
+            form_blocks_kernel<float><<<grid, 256, gsm, sh>>>(P.m, mp, P.h, P.dxa, P.d_g, P.d_dplus, P.d_dminus,
+                                                              P.d_phi, P.d_psi, fac);
+            FDE_LAUNCH_CHECK("form_blocks_kernel");
+        }
+        int r = panel(0);
+        if (r) return r;
+        for (int o = 0; o + TB < mp; o += TB) {
+            const int R0 = o + TB;
+            const int nt = cdiv(mp - R0, T2_BM);
+            if (o > 0) FDE_CUDA_TRY(cudaStreamWaitEvent(sh, P.lu_ev[2], 0));  // interior of step o - TB
+            {
+                StageTimer t(P, FDE_STAGE_LU_TC, sh);
+                lu_update_tc2_kernel<KIND><<<dim3(2 * nt - 1, nb), 128, Cfg::SMEM, sh>>>(
+                    mp, R0, nt, 1, fac, apk(o), bpk(o), pa, pb, P.d_err);
+                FDE_LAUNCH_CHECK("lu_update_tc2_kernel");
+            }
+            FDE_CUDA_TRY(cudaEventRecord(P.lu_ev[1], sh));
+            FDE_CUDA_TRY(cudaStreamWaitEvent(sl, P.lu_ev[1], 0));
+            if (nt > 1) {
+                StageTimer t(P, FDE_STAGE_LU_TC, sl);
+                lu_update_tc2_kernel<KIND><<<dim3((nt - 1) * (nt - 1), nb), 128, Cfg::SMEM, sl>>>(
+                    mp, R0, nt, 2, fac, apk(o), bpk(o), pa, pb, P.d_err);
+                FDE_LAUNCH_CHECK("lu_update_tc2_kernel");
+            }
+            FDE_CUDA_TRY(cudaEventRecord(P.lu_ev[2], sl));
+            if ((r = panel(R0))) return r;
+        }
+        return FDE_OK;
+    };
+    rc = body();
+    // join: st continues after both streams
+    cudaEventRecord(P.lu_ev[1], sl);
+    cudaStreamWaitEvent(st, P.lu_ev[1], 0);
+    cudaEventRecord(P.lu_ev[1], sh);
+    cudaStreamWaitEvent(st, P.lu_ev[1], 0);
+    return rc;
 }
 
 // Batched LU over a block table sorted by m_p (descending): blocks still being
@@ -1285,7 +1390,7 @@ static int run_lu_tc(Problem& P, cudaStream_t st) {
 static int run_lu_batched_simt(const BlkDev* d_blk, const std::vector<int>& mps, cudaStream_t st) {
     const int nbt = (int)mps.size();
     const int max_mp = mps[0];
-    form_blocks_batched<float><<<dim3(64, nbt), 256, 0, st>>>(d_blk);
+    form_blocks_batched<float><<<dim3(64, nbt), 256, (size_t)(max_mp + 2) * sizeof(float), st>>>(d_blk);
     FDE_LAUNCH_CHECK("form_blocks_batched");
     const size_t panel_smem = (size_t)RC * (NB + 1) * sizeof(float2);
     const size_t upd_smem = (64 * (NB + 1) + NB * 65) * sizeof(float2);
@@ -1316,7 +1421,7 @@ static int run_lu_batched_tc(const BlkDev* d_blk, const std::vector<int>& mps, i
     using Cfg = Tc2<KIND>;
     const int nbt = (int)mps.size();
     const int max_mp = mps[0];
-    form_blocks_batched<float><<<dim3(64, nbt), 256, 0, st>>>(d_blk);
+    form_blocks_batched<float><<<dim3(64, nbt), 256, (size_t)(max_mp + 2) * sizeof(float), st>>>(d_blk);
     FDE_LAUNCH_CHECK("form_blocks_batched");
     int rc = set_tc_attrs<KIND>();
     if (rc) return rc;
