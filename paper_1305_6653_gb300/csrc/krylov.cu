@@ -5,7 +5,8 @@
 //
 // Reductions are deterministic: every CTA writes its partial sums, and the last
 // CTA to finish (atomic ticket after a fence; nothing waits) adds them in a fixed
-// order and resets the ticket.
+// order (one warp per vector, lanes over the partials, then a shuffle tree) and
+// resets the ticket.
 #include "fde_internal.h"
 
 namespace fde {
@@ -49,10 +50,13 @@ __device__ __forceinline__ void dots_body(const double* __restrict__ V, int k, c
     __syncthreads();
     if (last) {
         __threadfence();
-        for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        // warp q adds vectors i = q, q + 8, ..: its lanes split the CTA partials (fixed
+        // order, independent L2 loads), then a fixed shuffle tree
+        for (int i = warp; i < k; i += RED_THREADS / 32) {
             double v = 0.0;
-            for (int c = 0; c < nblocks; ++c) v += ((volatile double*)partial)[(size_t)c * KMAX + i];
-            out[i] = v;
+            for (int c = lane; c < nblocks; c += 32) v += __ldcg(partial + (size_t)c * KMAX + i);
+            for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+            if (lane == 0) out[i] = v;
         }
         if (threadIdx.x == 0) *counter = 0u;
     }
