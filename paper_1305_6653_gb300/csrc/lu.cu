@@ -830,11 +830,17 @@ __device__ __forceinline__ void diag128_body(int mp, int o, float* __restrict__ 
     float* im = re + (size_t)mp * mp;
     const int W = mp - o < TB ? mp - o : TB;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    for (int e = t; e < W * W; e += blockDim.x) {
-        const int r = e / W, c = e % W;
+    const int sh4 = W == TB ? 5 : 4;  // log2(W / 4): float4 columns per row
+#pragma unroll 4
+    for (int e = t; e < W * W / 4; e += blockDim.x) {
+        const int r = e >> sh4, c = (e & ((1 << sh4) - 1)) * 4;
         const size_t g = (size_t)(o + r) * mp + o + c;
-        Ar[r * LD + c] = re[g];
-        Ai[r * LD + c] = im[g];
+        const float4 a = *reinterpret_cast<const float4*>(re + g);
+        const float4 b = *reinterpret_cast<const float4*>(im + g);
+        float* pr = Ar + r * LD + c;
+        float* pi = Ai + r * LD + c;
+        pr[0] = a.x, pr[1] = a.y, pr[2] = a.z, pr[3] = a.w;
+        pi[0] = b.x, pi[1] = b.y, pi[2] = b.z, pi[3] = b.w;
     }
     __syncthreads();
     for (int P0 = 0; P0 < W; P0 += DB) {
@@ -942,11 +948,14 @@ __device__ __forceinline__ void diag128_body(int mp, int o, float* __restrict__ 
         }
         __syncthreads();
     }
-    for (int e = t; e < W * W; e += blockDim.x) {
-        const int r = e / W, c = e % W;
+#pragma unroll 4
+    for (int e = t; e < W * W / 4; e += blockDim.x) {
+        const int r = e >> sh4, c = (e & ((1 << sh4) - 1)) * 4;
         const size_t g = (size_t)(o + r) * mp + o + c;
-        re[g] = Ar[r * LD + c];
-        im[g] = Ai[r * LD + c];
+        const float* pr = Ar + r * LD + c;
+        const float* pi = Ai + r * LD + c;
+        *reinterpret_cast<float4*>(re + g) = make_float4(pr[0], pr[1], pr[2], pr[3]);
+        *reinterpret_cast<float4*>(im + g) = make_float4(pi[0], pi[1], pi[2], pi[3]);
     }
     if (!invert || W != TB) return;
     __syncthreads();  // the factor in HBM is read back below by other threads of this CTA
