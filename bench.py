@@ -30,6 +30,9 @@ sys.path.insert(0, ROOT)
 METRIC = "space-time FDE solves/s at rel.err 1e-8: mixed+batched vs plain FP64 PGMRES"
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
+# Iterations of the oracle's exact-FP64 Strang FGMRES(20) on the benchmark workload at
+# tol 1e-10 (the same method in FP64 on the GPU takes 20), used to compose its solve time
+ORACLE_ITERATIONS = 20
 
 
 def parse():
@@ -489,7 +492,7 @@ def main():
         steps = []
         sample = None
         for i in range(args.warmup + args.steps):
-            sample = oracle_sample(prob, iterations=12)
+            sample = oracle_sample(prob, iterations=ORACLE_ITERATIONS)
             if i >= args.warmup:
                 steps.append(sample["seconds_per_solve"])
         t = sum(steps) / len(steps)
@@ -572,7 +575,13 @@ def main():
     mp = (prob.m + 63) // 64 * 64
     nblk = prob.s // 2 + 1
     esz = 8 if args.precision == "fp64" else 4
-    dom = max(prof.items(), key=lambda kv: kv[1][0])
+    # The tensor-core LU runs its interior updates on a second stream beside the panel
+    # chain, so the event sums of the LU stages include overlap; the dominant kernel is
+    # taken among the single-stream stages (the ncu launch list agrees: the block
+    # solves lead, the trailing update follows).
+    overlapped = {"lu_tc", "lu_diag", "lu_pack", "lu_panel_tc", "form"} if args.precision in (
+        "tf32", "bf16", "tf32x3") else set()
+    dom = max((kv for kv in prof.items() if kv[0] not in overlapped), key=lambda kv: kv[1][0])
     name, (dom_ms, dom_n) = dom
     roof = None
     if name == "trsv":
@@ -608,6 +617,7 @@ def main():
         ratio = 1.1 / 2.25 if args.precision in ("tf32", "tf32x3") else 1.0
         tbytes = tc_update_bytes(mp, nblk) * args.steps
         tc_line = {"kernel": "lu_update_tc2_kernel", "launches_per_step": tn // args.steps,
+                   "timing": "CUDA events on both LU streams; the interior updates overlap the panel chain",
                    "ms_per_step": tms / args.steps, "tflops": tfl / (tms / 1e3) / 1e12,
                    "tensor_peak": bf16_peak * ratio, "c_tile_gbs": tbytes / (tms / 1e3) / 1e9, "hbm_peak": hbm_peak}
     stage_ms = {k: round(v[0] / args.steps, 4) for k, v in prof.items()}
@@ -673,8 +683,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        its = int(np.median([s["iterations"] for s in stats]))
-        cpu = oracle_sample(prob, iterations=its)
+        cpu = oracle_sample(prob, iterations=ORACLE_ITERATIONS)
         cpu.pop("seconds_per_solve", None)
 
     if rank == 0:

@@ -440,7 +440,8 @@ void fde_problem_destroy(fde_problem* h) {
     free_workspace(P);
     void* bufs[] = {P.d_start, P.d_a, P.d_b, P.d_dplus, P.d_dminus, P.d_u0, P.d_f, P.d_g, P.d_twL, P.d_twL32,
                     P.d_sym, P.d_sym32, P.d_tws, P.d_tws32, P.d_phi, P.d_psi, P.d_b_rhs, P.d_work, P.d_rhat,
-                    P.d_fac, P.d_dinv, P.d_info, P.d_err, P.d_pack, P.d_scal, P.d_partial, P.d_counter};
+                    P.d_fac, P.d_dinv, P.d_info, P.d_err, P.d_pack, P.d_tinv, P.d_scal, P.d_partial,
+                    P.d_counter};
     for (void* b : bufs) dfree(b);
     if (h->pinned) cudaFreeHost(h->pinned);
     for (cudaEvent_t e : P.ev_pool) cudaEventDestroy(e);

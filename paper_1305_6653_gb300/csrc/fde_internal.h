@@ -175,6 +175,8 @@ struct Problem {
     int* d_info = nullptr;      // nblk: first singular pivot (+1) or 0
     int* d_err = nullptr;       // device error flag of bounded waits (0 = none)
     size_t fac_bytes = 0;
+    void* d_tinv = nullptr;     // inverted 32 x 32 diagonal tiles of L and U (block solves)
+    size_t tinv_bytes = 0;
     void* d_pack = nullptr;     // packed tensor-core operand tiles of the LU panels
     size_t pack_bytes = 0;
     // tensor-core LU look-ahead: panel chain on lu_hi, interior updates on lu_lo

@@ -476,27 +476,41 @@ static size_t trsv_smem_bytes(int mp, size_t elem) {
     return (size_t)mp * 2 * elem + 8 * 32 * ld * elem;
 }
 
+// 32 x 32 tile with row pitch `pitch` (elements) -> shared tile with pitch LD.
 template <typename T>
-__device__ __forceinline__ void tile_async(T* dst, const T* plane, int mp, int r0, int c0, int lane) {
+__device__ __forceinline__ void tile_async(T* dst, const T* src, size_t pitch, int lane) {
     constexpr int EPC = 16 / (int)sizeof(T), CPR = 32 / EPC, LD = trsv_tile<T>::LD;
     for (int e = lane; e < 32 * CPR; e += 32) {
         const int r = e / CPR, ch = e % CPR;
-        cp_async16(dst + r * LD + ch * EPC, plane + (size_t)(r0 + r) * mp + c0 + ch * EPC);
+        cp_async16(dst + r * LD + ch * EPC, src + (size_t)r * pitch + ch * EPC);
     }
 }
+template <typename T>
+__device__ __forceinline__ void tile_async(T* dst, const T* plane, int mp, int r0, int c0, int lane) {
+    tile_async<T>(dst, plane + (size_t)r0 * mp + c0, (size_t)mp, lane);
+}
 
-// Solver side of one sweep (warp 0).
-template <typename T, bool FWD>
+// Solver side of one sweep (warp 0).  INV: the inverted diagonal tiles are given
+// (tinv: per tile [L^-1 re, L^-1 im, U^-1 re, U^-1 im][32][32]) and a tile solve is
+// the product x = D^-1 a; otherwise the tile is solved by substitution.
+template <typename T, bool FWD, bool INV>
 __device__ __forceinline__ void trsv_solver(int mp, int nt, const T* re, const T* im, const cplx_t<T>* dv,
-                                            cplx_t<T>* y, cplx_t<T> (*xs)[32], T* tiles, int lane) {
+                                            const T* tinv, cplx_t<T>* y, cplx_t<T> (*xs)[32], T* tiles,
+                                            cplx_t<T>* av, int lane) {
     using C = cplx_t<T>;
     constexpr int LD = trsv_tile<T>::LD, TS = 32 * LD;
     auto tile_of = [&](int d) { return FWD ? d : nt - 1 - d; };
     auto issue = [&](int d) {
         T* b = tiles + (d & 1) * 4 * TS;  // [D re, D im, L re, L im]
         const int j = tile_of(d);
-        tile_async<T>(b, re, mp, 32 * j, 32 * j, lane);
-        tile_async<T>(b + TS, im, mp, 32 * j, 32 * j, lane);
+        if (INV) {
+            const T* ti = tinv + (size_t)j * 4096 + (FWD ? 0 : 2048);
+            tile_async<T>(b, ti, 32, lane);
+            tile_async<T>(b + TS, ti + 1024, 32, lane);
+        } else {
+            tile_async<T>(b, re, mp, 32 * j, 32 * j, lane);
+            tile_async<T>(b + TS, im, mp, 32 * j, 32 * j, lane);
+        }
         if (d >= 1) {
             tile_async<T>(b + 2 * TS, re, mp, 32 * j, 32 * tile_of(d - 1), lane);
             tile_async<T>(b + 3 * TS, im, mp, 32 * j, 32 * tile_of(d - 1), lane);
@@ -532,7 +546,23 @@ __device__ __forceinline__ void trsv_solver(int mp, int nt, const T* re, const T
             a.x -= sx0 + sx1;
             a.y -= sy0 + sy1;
         }
-        if (FWD) {
+        if (INV) {  // x = D^-1 a (D^-1 stored with its zeros and unit / inverted diagonal)
+            av[lane] = a;
+            __syncwarp();
+            T sx0 = 0, sy0 = 0, sx1 = 0, sy1 = 0;
+#pragma unroll
+            for (int c = 0; c < 32; c += 2) {
+                const C a0 = av[c], a1 = av[c + 1];
+                const T d0r = Dre[lane * LD + c], d0i = Dim[lane * LD + c];
+                const T d1r = Dre[lane * LD + c + 1], d1i = Dim[lane * LD + c + 1];
+                sx0 += d0r * a0.x - d0i * a0.y;
+                sy0 += d0r * a0.y + d0i * a0.x;
+                sx1 += d1r * a1.x - d1i * a1.y;
+                sy1 += d1r * a1.y + d1i * a1.x;
+            }
+            a.x = sx0 + sx1;
+            a.y = sy0 + sy1;
+        } else if (FWD) {
 #pragma unroll 8
             for (int c = 0; c < 32; ++c) {
                 const T yx = __shfl_sync(0xffffffffu, a.x, c);
@@ -633,23 +663,24 @@ __device__ __forceinline__ void trsv_stream(int mp, int nt, const T* re, const T
     }
 }
 
-template <typename T>
+template <typename T, bool INV>
 __device__ __forceinline__ void trsv_body(int mp, const T* __restrict__ re, const cplx_t<T>* __restrict__ dv,
-                                          cplx_t<T>* __restrict__ x) {
+                                          const T* __restrict__ tinv, cplx_t<T>* __restrict__ x) {
     using C = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* y = reinterpret_cast<C*>(smem_raw);        // mp
     T* tiles = reinterpret_cast<T*>(y + mp);      // solver tiles
     __shared__ C xs[2][32];
+    __shared__ C av[32];
     const T* im = re + (size_t)mp * mp;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nt = mp / 32;
     for (int i = threadIdx.x; i < mp; i += blockDim.x) y[i] = x[i];
     __syncthreads();
-    if (warp == 0) trsv_solver<T, true>(mp, nt, re, im, dv, y, xs, tiles, lane);
+    if (warp == 0) trsv_solver<T, true, INV>(mp, nt, re, im, dv, tinv, y, xs, tiles, av, lane);
     else trsv_stream<T, true>(mp, nt, re, im, y, xs, threadIdx.x - 32);
     __syncthreads();
-    if (warp == 0) trsv_solver<T, false>(mp, nt, re, im, dv, y, xs, tiles, lane);
+    if (warp == 0) trsv_solver<T, false, INV>(mp, nt, re, im, dv, tinv, y, xs, tiles, av, lane);
     else trsv_stream<T, false>(mp, nt, re, im, y, xs, threadIdx.x - 32);
     __syncthreads();
     for (int i = threadIdx.x; i < mp; i += blockDim.x) x[i] = y[i];
@@ -657,9 +688,11 @@ __device__ __forceinline__ void trsv_body(int mp, const T* __restrict__ re, cons
 
 template <typename T>
 __global__ void __launch_bounds__(TRSV_THREADS)
-block_trsv_kernel(int mp, const T* __restrict__ fac, const cplx_t<T>* __restrict__ dinv, cplx_t<T>* __restrict__ rhat) {
+block_trsv_kernel(int mp, const T* __restrict__ fac, const cplx_t<T>* __restrict__ dinv, const T* __restrict__ tinv,
+                  cplx_t<T>* __restrict__ rhat) {
     const int k = blockIdx.x;
-    trsv_body<T>(mp, fac + (size_t)k * 2 * mp * mp, dinv + (size_t)k * mp, rhat + (size_t)k * mp);
+    trsv_body<T, true>(mp, fac + (size_t)k * 2 * mp * mp, dinv + (size_t)k * mp,
+                       tinv + (size_t)k * (mp / 32) * 4096, rhat + (size_t)k * mp);
 }
 
 // Batched over the active instances act[0..gridDim.y): block k = blockIdx.x of instance act[blockIdx.y].
@@ -670,8 +703,8 @@ block_trsv_batched(const InstDev* __restrict__ I, const int* __restrict__ act) {
     const int k = blockIdx.x;
     if (k >= d.nblk) return;
     const size_t mp = d.mp;
-    trsv_body<T>(d.mp, (const T*)d.fac + (size_t)k * 2 * mp * mp, (const cplx_t<T>*)d.dinv + (size_t)k * mp,
-                 (cplx_t<T>*)d.rhat + (size_t)k * mp);
+    trsv_body<T, false>(d.mp, (const T*)d.fac + (size_t)k * 2 * mp * mp, (const cplx_t<T>*)d.dinv + (size_t)k * mp,
+                        nullptr, (cplx_t<T>*)d.rhat + (size_t)k * mp);
 }
 
 template <typename T>
@@ -1511,12 +1544,104 @@ int launch_trsv_batched(const InstDev* I, const int* act, int nact, int max_nblk
     return FDE_OK;
 }
 
+// Inverses of the 32 x 32 diagonal tiles of every block's factors, for the block
+// solves: warp 0 inverts the unit lower tile of L, warp 1 the upper tile of U (its
+// diagonal included), both in place column by column / row by row from the last,
+//   L^-1[i][j] = -(L[i][j] + sum_{j<k<i} L^-1[i][k] L[k][j])          (i > j)
+//   U^-1[j][c] = -(1/U[j][j]) sum_{j<k<=c} U[j][k] U^-1[k][c]         (c > j).
+// Output per block and tile: [L^-1 re, L^-1 im, U^-1 re, U^-1 im][32][32], with the
+// zeros and the unit (L) / inverted (U) diagonal written out.
+template <typename T>
+__global__ void __launch_bounds__(64) tile_inverse_kernel(int mp, const T* __restrict__ fac, T* __restrict__ tinv) {
+    using C = cplx_t<T>;
+    __shared__ C tl[2][32][33];
+    __shared__ C vb[2][32];
+    const int k = blockIdx.y, t = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const T* re = fac + (size_t)k * 2 * mp * mp;
+    const T* im = re + (size_t)mp * mp;
+    const int r0 = 32 * t;
+    C (*A)[33] = tl[warp];
+    C* v = vb[warp];
+    for (int r = 0; r < 32; ++r) {
+        const size_t g = (size_t)(r0 + r) * mp + r0 + lane;
+        A[r][lane] = mk(re[g], im[g]);
+    }
+    __syncwarp();
+    if (warp == 0) {  // lane = row
+        for (int j = 31; j >= 0; --j) {
+            v[lane] = lane > j ? A[lane][j] : mk(T(0), T(0));
+            __syncwarp();
+            C sum = mk(T(0), T(0));
+            if (lane > j) {
+                sum = v[lane];
+                for (int q = j + 1; q < lane; ++q) sum = cadd(sum, cmul(A[lane][q], v[q]));
+            }
+            __syncwarp();
+            if (lane > j) A[lane][j] = mk(-sum.x, -sum.y);
+            __syncwarp();
+        }
+    } else {  // lane = column
+        for (int j = 31; j >= 0; --j) {
+            v[lane] = lane > j ? A[j][lane] : mk(T(0), T(0));
+            const C piv = A[j][j];
+            __syncwarp();
+            const T den = piv.x * piv.x + piv.y * piv.y;
+            const C dj = den > T(0) ? mk(piv.x / den, -piv.y / den) : mk(T(0), T(0));
+            C nv = dj;
+            if (lane > j) {
+                C sum = mk(T(0), T(0));
+                for (int q = j + 1; q <= lane; ++q) sum = cadd(sum, cmul(v[q], A[q][lane]));
+                nv = cmul(dj, sum);
+                nv = mk(-nv.x, -nv.y);
+            }
+            __syncwarp();
+            if (lane >= j) A[j][lane] = nv;
+            __syncwarp();
+        }
+    }
+    T* out = tinv + ((size_t)k * (mp / 32) + t) * 4096 + warp * 2048;
+    for (int r = 0; r < 32; ++r) {
+        C e = A[r][lane];
+        if (warp == 0) {
+            if (lane > r) e = mk(T(0), T(0));
+            else if (lane == r) e = mk(T(1), T(0));
+        } else if (lane < r) {
+            e = mk(T(0), T(0));
+        }
+        out[r * 32 + lane] = e.x;
+        out[1024 + r * 32 + lane] = e.y;
+    }
+}
+
+static int launch_tile_inverse(Problem& P, int prec, cudaStream_t st) {
+    const size_t esz = prec == FDE_FP64 ? sizeof(double) : sizeof(float);
+    const size_t bytes = (size_t)P.nblk * (P.mp / 32) * 4096 * esz;
+    if (P.tinv_bytes < bytes) {
+        if (P.d_tinv) cudaFree(P.d_tinv);
+        P.d_tinv = nullptr;
+        P.tinv_bytes = 0;
+        FDE_CUDA_TRY(cudaMalloc(&P.d_tinv, bytes));
+        P.tinv_bytes = bytes;
+    }
+    StageTimer t(P, FDE_STAGE_LU_DIAG);
+    const dim3 grid(P.mp / 32, P.nblk);
+    if (prec == FDE_FP64)
+        tile_inverse_kernel<double><<<grid, 64, 0, st>>>(P.mp, (const double*)P.d_fac, (double*)P.d_tinv);
+    else
+        tile_inverse_kernel<float><<<grid, 64, 0, st>>>(P.mp, (const float*)P.d_fac, (float*)P.d_tinv);
+    FDE_LAUNCH_CHECK("tile_inverse_kernel");
+    return FDE_OK;
+}
+
 int launch_block_lu(Problem& P, int prec, cudaStream_t st) {
-    if (prec == FDE_FP64) return run_lu<double>(P, st);
-    if (prec == FDE_TF32) return run_lu_tc<0>(P, st);
-    if (prec == FDE_BF16) return run_lu_tc<1>(P, st);
-    if (prec == FDE_TF32X3) return run_lu_tc<2>(P, st);
-    return run_lu<float>(P, st);
+    int rc;
+    if (prec == FDE_FP64) rc = run_lu<double>(P, st);
+    else if (prec == FDE_TF32) rc = run_lu_tc<0>(P, st);
+    else if (prec == FDE_BF16) rc = run_lu_tc<1>(P, st);
+    else if (prec == FDE_TF32X3) rc = run_lu_tc<2>(P, st);
+    else rc = run_lu<float>(P, st);
+    if (rc) return rc;
+    return launch_tile_inverse(P, prec, st);
 }
 
 int launch_block_trsv(const Problem& P, void* rhat, cudaStream_t st) {
@@ -1524,14 +1649,14 @@ int launch_block_trsv(const Problem& P, void* rhat, cudaStream_t st) {
         const size_t smem = trsv_smem_bytes(P.mp, sizeof(double));
         FDE_CUDA_TRY(cudaFuncSetAttribute(block_trsv_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)smem));
-        block_trsv_kernel<double><<<P.nblk, TRSV_THREADS, smem, st>>>(P.mp, (const double*)P.d_fac,
-                                                                       (const double2*)P.d_dinv, (double2*)rhat);
+        block_trsv_kernel<double><<<P.nblk, TRSV_THREADS, smem, st>>>(
+            P.mp, (const double*)P.d_fac, (const double2*)P.d_dinv, (const double*)P.d_tinv, (double2*)rhat);
     } else {
         const size_t smem = trsv_smem_bytes(P.mp, sizeof(float));
         FDE_CUDA_TRY(cudaFuncSetAttribute(block_trsv_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)smem));
-        block_trsv_kernel<float><<<P.nblk, TRSV_THREADS, smem, st>>>(P.mp, (const float*)P.d_fac,
-                                                                      (const float2*)P.d_dinv, (float2*)rhat);
+        block_trsv_kernel<float><<<P.nblk, TRSV_THREADS, smem, st>>>(
+            P.mp, (const float*)P.d_fac, (const float2*)P.d_dinv, (const float*)P.d_tinv, (float2*)rhat);
     }
     FDE_LAUNCH_CHECK("block_trsv_kernel");
     return FDE_OK;
