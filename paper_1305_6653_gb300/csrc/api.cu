@@ -382,8 +382,8 @@ int fde_problem_create(const fde_problem_desc* d, void* stream, fde_problem** ou
     TRY(dalloc(&P.d_u0, m));
     TRY(dalloc(&P.d_f, (size_t)(P.s + 1) * m));
     TRY(dalloc(&P.d_g, m + 2));
-    TRY(dalloc(&P.d_twL, (size_t)P.L / 2 + 1));
-    TRY(dalloc(&P.d_twL32, (size_t)P.L / 2 + 1));
+    TRY(dalloc(&P.d_twL, (size_t)P.L + 1));
+    TRY(dalloc(&P.d_twL32, (size_t)P.L + 1));
     TRY(dalloc(&P.d_sym, (size_t)P.L));
     TRY(dalloc(&P.d_sym32, (size_t)P.L));
     TRY(dalloc(&P.d_tws, (size_t)P.s / 2 + 1));
@@ -496,8 +496,8 @@ int bvm_assemble(fde_problem* h) {
     double* d_main = nullptr;
     StageTimer timer(P, FDE_STAGE_ASSEMBLE);
     if ((rc = launch_grunwald(P.alpha, P.m + 2, P.d_g, P.stream))) return rc;
-    if ((rc = launch_twiddles(P.L, P.d_twL, P.d_twL32, P.stream))) return rc;
-    if ((rc = launch_twiddles(P.s, P.d_tws, P.d_tws32, P.stream))) return rc;
+    if ((rc = launch_twiddles(P.L, P.L, P.d_twL, P.d_twL32, P.stream))) return rc;      // L + 1 allocated
+    if ((rc = launch_twiddles(P.s, P.s / 2, P.d_tws, P.d_tws32, P.stream))) return rc;  // s/2 + 1 allocated
     if ((rc = launch_toeplitz_symbol(P.d_g, P.m, P.L, P.dxa, P.d_twL, P.d_sym, P.d_sym32, nullptr, P.stream)))
         return rc;
     // main-formula coefficients for the Strang symbols

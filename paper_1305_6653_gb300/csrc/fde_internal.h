@@ -101,7 +101,8 @@ struct Problem;
 
 // setup.cu
 int launch_grunwald(double alpha, int count, double* g, cudaStream_t st);
-int launch_twiddles(int L, double2* tw64, float2* tw32, cudaStream_t st);
+// tw[k] = exp(-2 pi i k / L) for k < count (count = the table's length)
+int launch_twiddles(int L, int count, double2* tw64, float2* tw32, cudaStream_t st);
 int launch_toeplitz_symbol(const double* g, int m, int L, double scale, const double2* tw, double2* sym64,
                            float2* sym32, double2* work, cudaStream_t st);
 int launch_strang_symbols(const double* a_main, const double* b_main, int mu, int nu, int s, double2* phi,
@@ -159,7 +160,7 @@ struct Problem {
     double* d_u0 = nullptr;     // m
     double* d_f = nullptr;      // (s+1)*m
     double* d_g = nullptr;      // m+2 Grunwald weights
-    double2* d_twL = nullptr;   // L/2 twiddles exp(-2 pi i k / L), FP64
+    double2* d_twL = nullptr;   // L twiddles exp(-2 pi i k / L), FP64
     float2* d_twL32 = nullptr;  // same, FP32
     double2* d_sym = nullptr;   // L: (lambda + i conj(lambda)) / L, lambda = FFT of the circulant embedding of G
     float2* d_sym32 = nullptr;

@@ -7,7 +7,8 @@
 // (read straight from HBM; the neighbours are shared through L2), then applies J
 // once: J v = dx^-alpha (D+ G v + D- G^T v) through the length-L circulant
 // embedding of G (Sec. 2.1: Toeplitz matvec by FFT), with one forward FFT of v
-// and one inverse FFT whose real / imaginary parts are G v and G^T v.
+// (real input: a half-length complex FFT and a split) and one inverse FFT whose
+// real / imaginary parts are G v and G^T v, both as radix-4 passes in FP64.
 #include "fde_internal.h"
 #include "fft_device.cuh"
 
@@ -19,9 +20,10 @@ __device__ __forceinline__ void matvec_body(int m, int logL, int mu, double h, c
                                             const double* __restrict__ dplus, const double* __restrict__ dminus,
                                             const cplx_t<T>* __restrict__ sym, const cplx_t<T>* __restrict__ tw,
                                             const double* __restrict__ z, double* __restrict__ y, int row) {
+    static_assert(sizeof(T) == 8, "the Toeplitz apply runs in FP64");
     using C = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int L = 1 << logL;
+    const int L = 1 << logL, N = L >> 1, logN = logL - 1;
     C* buf = reinterpret_cast<C*>(smem_raw);
     double* ubuf = reinterpret_cast<double*>(buf + L);  // row = reduced time row: unknown u_{row+1}
 
@@ -36,33 +38,57 @@ __device__ __forceinline__ void matvec_body(int m, int logL, int mu, double h, c
             cb[q] = q <= mu ? B[(size_t)t * (mu + 1) + q] : 0.0;
         }
     }
-    for (int i = threadIdx.x; i < L; i += blockDim.x) {
-        T v = T(0);
-        if (i < m) {
-            if (MODE == 0) {
-                double u = 0.0, w = 0.0;
+    // The input v of the Toeplitz apply is real: its length-L FFT comes from the
+    // length-N = L/2 FFT of zc[n] = v[2n] + i v[2n+1] (bit-reversed for the DIT).
+    for (int n = threadIdx.x; n < N; n += blockDim.x) {
+        double v2[2] = {0.0, 0.0};
 #pragma unroll
-                for (int q = 0; q <= FDE_MAX_MU; ++q) {
-                    const int col = st + q;  // full-system time index; column 0 (u_0) is eliminated
-                    if (q <= mu && col >= 1) {
-                        const double zz = z[(size_t)(col - 1) * m + i];
-                        u += ca[q] * zz;
-                        w += cb[q] * zz;
+        for (int e = 0; e < 2; ++e) {
+            const int i = 2 * n + e;
+            if (i < m) {
+                if (MODE == 0) {
+                    double u = 0.0, w = 0.0;
+#pragma unroll
+                    for (int q = 0; q <= FDE_MAX_MU; ++q) {
+                        const int col = st + q;  // full-system time index; column 0 (u_0) is eliminated
+                        if (q <= mu && col >= 1) {
+                            const double zz = z[(size_t)(col - 1) * m + i];
+                            u += ca[q] * zz;
+                            w += cb[q] * zz;
+                        }
                     }
+                    ubuf[i] = u;
+                    v2[e] = w;
+                } else {
+                    v2[e] = z[(size_t)row * m + i];
                 }
-                ubuf[i] = u;
-                v = (T)w;
-            } else {
-                v = (T)z[(size_t)row * m + i];
             }
         }
-        buf[bitrev(i, logL)] = mk(v, T(0));
+        buf[bitrev(n, logN)] = mk(v2[0], v2[1]);
     }
     __syncthreads();
-    fft_dit<C, false>(buf, logL, 1, L, tw);
-    for (int f = threadIdx.x; f < L; f += blockDim.x) buf[f] = cmul(buf[f], sym[f]);
+    fft_dit4<false>(buf, logN, tw, 2);  // tw holds W_L^k; stride 2 gives W_N^k
+    // Split Zc into V (length L) and multiply by the symbol, in place: the thread of
+    // pair (k, N-k) reads Zc[k], Zc[N-k] and writes V[k], V[k+N], V[N-k], V[2N-k] with
+    //   E = (Zc[k] + conj Zc[N-k]) / 2,  O = (Zc[k] - conj Zc[N-k]) / 2i,
+    //   V[k] = E + W_L^k O,  V[k+N] = E - W_L^k O.
+    for (int k = threadIdx.x; k <= N / 2; k += blockDim.x) {
+        const int kk = (N - k) & (N - 1);
+        const C zk = buf[k], zn = buf[kk];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            if (e == 1 && kk == k) break;
+            const int idx = e == 0 ? k : kk;
+            const C za = e == 0 ? zk : zn, zb = e == 0 ? zn : zk;
+            const C E = mk(0.5 * (za.x + zb.x), 0.5 * (za.y - zb.y));
+            const C O = mk(0.5 * (za.y + zb.y), -0.5 * (za.x - zb.x));
+            const C wo = cmul(tw[idx], O);
+            buf[idx] = cmul(cadd(E, wo), sym[idx]);
+            buf[idx + N] = cmul(csub(E, wo), sym[idx + N]);
+        }
+    }
     __syncthreads();
-    fft_dif<C, true>(buf, logL, 1, L, tw);
+    fft_dif4<true>(buf, logL, tw, 1);
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
         const C wv = buf[bitrev(i, logL)];
         const double jz = dplus[i] * (double)wv.x + dminus[i] * (double)wv.y;

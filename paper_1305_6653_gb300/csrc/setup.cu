@@ -32,10 +32,11 @@ __global__ void grunwald_kernel(double alpha, int count, double* __restrict__ g)
     if (lane == 0) g[0] = 1.0;
 }
 
-// tw[k] = exp(-2 pi i k / L), k < L/2
-__global__ void twiddle_kernel(int L, double2* __restrict__ tw64, float2* __restrict__ tw32) {
+// tw[k] = exp(-2 pi i k / L) for k < count (the caller's table length: L/2 for
+// radix-2 stages, L for the radix-4 passes, which read up to 3L/4).
+__global__ void twiddle_kernel(int L, int count, double2* __restrict__ tw64, float2* __restrict__ tw32) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= L / 2) return;
+    if (k >= count) return;
     double sn, cs;
     sincospi(-2.0 * (double)k / (double)L, &sn, &cs);
     if (tw64) tw64[k] = make_double2(cs, sn);
@@ -115,9 +116,9 @@ int launch_grunwald(double alpha, int count, double* g, cudaStream_t st) {
     return FDE_OK;
 }
 
-int launch_twiddles(int L, double2* tw64, float2* tw32, cudaStream_t st) {
-    int n = L / 2 > 0 ? L / 2 : 1;
-    twiddle_kernel<<<(n + 255) / 256, 256, 0, st>>>(L, tw64, tw32);
+int launch_twiddles(int L, int count, double2* tw64, float2* tw32, cudaStream_t st) {
+    if (count <= 0) return FDE_OK;
+    twiddle_kernel<<<(count + 255) / 256, 256, 0, st>>>(L, count, tw64, tw32);
     FDE_LAUNCH_CHECK("twiddle_kernel");
     return FDE_OK;
 }
