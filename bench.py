@@ -171,15 +171,16 @@ def trsv_bytes(mp: int, nblk: int, esz: int) -> float:
 
 def oracle_sample(prob, iterations: int) -> dict:
     """Time the FP64 oracle on a bounded sample of one solve and compose the time
-    of a full solve (the oracle is slow; a full m=2047 / s=256 solve takes minutes).
+    of a full solve (a complete oracle solve of the benchmark workload takes about
+    a minute of host time).
 
-    Sample: with the same m, alpha, d and scheme, an s=16 instance (9 distinct
-    Strang blocks: their dense LUs and one preconditioner apply), plus the
-    full-size right-hand side, matvec and the time DFT pair at s=256.  Composition:
-    t = t_rhs + nblk/9 * t_factor(9) + its * (t_matvec + s/16 * t_blocksolve(16) + t_dft + t_gs)."""
+    Sample, on the full workload: the right-hand side, the dense LUs of all s/2+1
+    Strang blocks, and the work of one FGMRES iteration (one preconditioner apply,
+    one matvec, classical Gram-Schmidt with re-orthogonalisation against the
+    mean basis size of GMRES(20), 10 vectors).  Composition:
+    t = t_rhs + t_factor + its * t_iteration."""
     import numpy as np
 
-    import fde_inputs
     import oracle as O
 
     try:
@@ -190,44 +191,30 @@ def oracle_sample(prob, iterations: int) -> dict:
     s, m = prob.s, prob.m
     t0 = time.perf_counter()
     J = O.j_of(prob)
-    b = O.reduced_rhs(prob, J=J)
+    O.reduced_rhs(prob, J=J)
     t_rhs = time.perf_counter() - t0
     AB = O.bvm_matrices(prob.family, prob.mu, s)
-    z = np.random.default_rng(0).standard_normal(prob.n)
     t0 = time.perf_counter()
-    O.matvec(prob, z, J=J, AB=AB)
-    t_mv = time.perf_counter() - t0
-    small = fde_inputs.manufactured(m, 16, prob.alpha, prob.scheme,
-                                    dplus_fn=lambda x: prob.dplus, dminus_fn=lambda x: prob.dminus)
-    t0 = time.perf_counter()
-    P = O.StrangPreconditioner(small, J=J)
+    P = O.StrangPreconditioner(prob, J=J)
     t_fac = time.perf_counter() - t0
-    nb_small = len(P.lu)
-    r = np.random.default_rng(1).standard_normal(small.n)
+    nblk = len(P.lu)
+    V = np.random.default_rng(2).standard_normal((11, prob.n))
     t0 = time.perf_counter()
-    P.apply(r)
-    t_app = time.perf_counter() - t0
-    n_ = np.arange(s)
-    F = np.exp(-2j * np.pi * np.outer(n_, n_) / s)
-    R = z.reshape(s, m)
-    t0 = time.perf_counter()
-    Xh = F @ R
-    (np.conj(F) @ Xh).real
-    t_dft = time.perf_counter() - t0
-    V = np.random.default_rng(2).standard_normal((21, prob.n))
-    t0 = time.perf_counter()
-    for i in range(10):
-        V[i] @ V[20]
-    t_gs = (time.perf_counter() - t0) * 2.0  # MGS on ~10 vectors, both passes
-    nblk = s // 2 + 1
-    t_solve = (t_rhs + nblk / nb_small * t_fac
-               + iterations * (t_mv + s / 16.0 * t_app + t_dft + t_gs))
-    sampled = t_rhs + t_mv + t_fac + t_app + t_dft + t_gs
+    z = P.apply(V[0])
+    w = O.matvec(prob, z, J=J, AB=AB)
+    for _ in range(2):  # CGS2: two passes of dots and updates against 10 vectors
+        h = V[:10] @ w
+        w = w - V[:10].T @ h
+    float(np.linalg.norm(w))
+    t_it = time.perf_counter() - t0
+    del P
+    t_solve = t_rhs + t_fac + iterations * t_it
+    sampled = t_rhs + t_fac + t_it
     return {
         "value": 1.0 / t_solve, "unit": "solves/s", "cores": int(cores), "kind": "oracle",
-        "sample": (f"m={m}: {nb_small} dense Strang-block LUs + one preconditioner apply of an s=16 instance "
-                   f"(same alpha, d, scheme), full-size rhs/matvec/time-DFT at s={s}; composed to {nblk} "
-                   f"block LUs and {iterations} GMRES iterations; {sampled:.1f} s of CPU work"),
+        "sample": (f"m={m}, s={s}: right-hand side, dense LUs of all {nblk} Strang blocks and one FGMRES "
+                   f"iteration (preconditioner apply, matvec, CGS2 against 10 vectors), composed to "
+                   f"{iterations} iterations; {sampled:.1f} s of CPU work"),
         "seconds_per_solve": t_solve,
     }
 

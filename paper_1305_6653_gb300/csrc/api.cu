@@ -712,13 +712,17 @@ int pgmres_solve(fde_problem* h, const fde_pgmres_opts* opts, const double* x0, 
             if ((rc = apply_precond(P, vj, zj))) return finish(rc);
             if ((rc = matvec(P, zj, w))) return finish(rc);
             StageTimer kt(P, FDE_STAGE_KRYLOV);
-            if ((rc = launch_dots(V, j + 1, w, n, sc, P.d_partial, P.d_counter, st))) return finish(rc);
-            if ((rc = launch_update(V, j + 1, sc, -1.0, w, n, st))) return finish(rc);
+            // CGS2 in three passes over V: h1 = V^T w; w -= V h1 and h2 = V^T w;
+            // w -= V h2 and |w|^2 (one pass fewer without re-orthogonalisation)
+            if ((rc = launch_cgs_pass(0, V, j + 1, nullptr, w, n, sc, P.d_partial, P.d_counter, st)))
+                return finish(rc);
             if (o.reorth) {
-                if ((rc = launch_dots(V, j + 1, w, n, sc + 64, P.d_partial, P.d_counter, st))) return finish(rc);
-                if ((rc = launch_update(V, j + 1, sc + 64, -1.0, w, n, st))) return finish(rc);
+                if ((rc = launch_cgs_pass(1, V, j + 1, sc, w, n, sc + 64, P.d_partial, P.d_counter, st)))
+                    return finish(rc);
             }
-            if ((rc = launch_norm(w, n, sc + 128, P.d_partial, P.d_counter, st))) return finish(rc);
+            if ((rc = launch_cgs_pass(2, V, j + 1, o.reorth ? sc + 64 : sc, w, n, sc + 128, P.d_partial,
+                                      P.d_counter, st)))
+                return finish(rc);
             if ((rc = launch_arnoldi_finish(P.d_H, ldh, j, sc, o.reorth ? sc + 64 : nullptr, sc + 128, P.d_cs,
                                             P.d_sn, P.d_gv, sc + 129, st)))
                 return finish(rc);

@@ -126,6 +126,10 @@ int launch_dots(const double* V, int k, const double* w, long n, double* out, do
                 unsigned int* counter, cudaStream_t st);
 int launch_update(const double* V, int k, const double* coef, double sign, double* w, long n, cudaStream_t st);
 int launch_norm(const double* w, long n, double* out, double* partial, unsigned int* counter, cudaStream_t st);
+// Fused classical Gram-Schmidt pass over V_0..V_{k-1} (V row-major [k][n], w length n):
+// mode 0: out = V^T w;  1: w -= V c, then out = V^T w;  2: w -= V c, then out[0] = |w|^2
+int launch_cgs_pass(int mode, const double* V, int k, const double* c, double* w, long n, double* out,
+                    double* partial, unsigned int* counter, cudaStream_t st);
 int launch_scale(const double* src, const double* nrm_sq, double* dst, long n, cudaStream_t st);
 int launch_arnoldi_finish(double* H, int ldh, int j, const double* h1, const double* h2, const double* nrm_sq,
                           double* cs, double* sn, double* g, double* est, cudaStream_t st);

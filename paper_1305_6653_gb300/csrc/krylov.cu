@@ -15,22 +15,14 @@ constexpr int RED_CTAS = 304;  // 2 per SM on 152 SMs
 constexpr int RED_THREADS = 256;
 constexpr int KMAX = 64;       // max Krylov vectors per multi-dot
 
+// Per-thread partial sums acc[0..k) -> out[0..k): each CTA stores its partials,
+// and the last CTA to finish adds them in a fixed order.
 template <int KC>
-__device__ __forceinline__ void dots_body(const double* __restrict__ V, int k, const double* __restrict__ w, long n,
-                                          double* __restrict__ out, double* __restrict__ partial,
-                                          unsigned int* __restrict__ counter, int bx, int nblocks) {
+__device__ __forceinline__ void reduce_partials(const double (&acc)[KC], int k, double* __restrict__ out,
+                                                double* __restrict__ partial, unsigned int* __restrict__ counter,
+                                                int bx, int nblocks) {
     __shared__ double red[RED_THREADS / 32][KC];
     __shared__ bool last;
-    double acc[KC];
-#pragma unroll
-    for (int i = 0; i < KC; ++i) acc[i] = 0.0;
-    const long stride = (long)nblocks * blockDim.x;
-    for (long x = (long)bx * blockDim.x + threadIdx.x; x < n; x += stride) {
-        const double wx = w[x];
-#pragma unroll
-        for (int i = 0; i < KC; ++i)
-            if (i < k) acc[i] += V[(size_t)i * n + x] * wx;
-    }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int i = 0; i < KC; ++i) {
@@ -60,6 +52,100 @@ __device__ __forceinline__ void dots_body(const double* __restrict__ V, int k, c
         }
         if (threadIdx.x == 0) *counter = 0u;
     }
+}
+
+template <int KC>
+__device__ __forceinline__ void dots_body(const double* __restrict__ V, int k, const double* __restrict__ w, long n,
+                                          double* __restrict__ out, double* __restrict__ partial,
+                                          unsigned int* __restrict__ counter, int bx, int nblocks) {
+    double acc[KC];
+#pragma unroll
+    for (int i = 0; i < KC; ++i) acc[i] = 0.0;
+    const long stride = (long)nblocks * blockDim.x;
+    for (long x = (long)bx * blockDim.x + threadIdx.x; x < n; x += stride) {
+        const double wx = w[x];
+#pragma unroll
+        for (int i = 0; i < KC; ++i)
+            if (i < k) acc[i] += V[(size_t)i * n + x] * wx;
+    }
+    reduce_partials<KC>(acc, k, out, partial, counter, bx, nblocks);
+}
+
+// One pass of classical Gram-Schmidt over the basis V_0..V_{k-1} (x: element):
+//   MODE 0: out[i] = sum_x V_i[x] w[x]
+//   MODE 1: w[x] -= sum_i c[i] V_i[x], then out[i] = sum_x V_i[x] w[x] of the new w
+//   MODE 2: w[x] -= sum_i c[i] V_i[x], then out[0] = sum_x w[x]^2
+// The V_i[x] of an element are loaded once and serve both the update and the
+// sums, so CGS2 (dots, update + dots, update + norm) reads V three times.
+// PAIR: two neighbouring elements per thread with 16-byte loads (n even, so every
+// V_i starts on a 16-byte boundary).
+template <int KC, int MODE, bool PAIR>
+__global__ void __launch_bounds__(RED_THREADS)
+cgs_pass_kernel(const double* __restrict__ V, int k, const double* __restrict__ c, double* __restrict__ w, long n,
+                double* __restrict__ out, double* __restrict__ partial, unsigned int* __restrict__ counter) {
+    constexpr int NA = MODE == 2 ? 1 : KC;
+    constexpr int E = PAIR ? 2 : 1;
+    __shared__ double cs[KC];
+    if (MODE > 0) {
+        for (int i = threadIdx.x; i < KC; i += blockDim.x) cs[i] = i < k ? c[i] : 0.0;
+        __syncthreads();
+    }
+    double acc[NA];
+#pragma unroll
+    for (int i = 0; i < NA; ++i) acc[i] = 0.0;
+    const long ne = n / E;
+    const long stride = (long)gridDim.x * blockDim.x;
+    for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < ne; q += stride) {
+        const long x = q * E;
+        double wx[E], v[KC][E];
+        if (PAIR) {
+            const double2 t = *reinterpret_cast<const double2*>(w + x);
+            wx[0] = t.x;
+            wx[E - 1] = t.y;
+        } else {
+            wx[0] = w[x];
+        }
+#pragma unroll
+        for (int i = 0; i < KC; ++i) {
+            if (i < k) {
+                if (PAIR) {
+                    const double2 t = *reinterpret_cast<const double2*>(V + (size_t)i * n + x);
+                    v[i][0] = t.x;
+                    v[i][E - 1] = t.y;
+                } else {
+                    v[i][0] = V[(size_t)i * n + x];
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < E; ++e) v[i][e] = 0.0;
+            }
+        }
+        if (MODE > 0) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                double a = wx[e];
+#pragma unroll
+                for (int i = 0; i < KC; ++i)
+                    if (i < k) a -= cs[i] * v[i][e];
+                wx[e] = a;
+            }
+            if (PAIR)
+                *reinterpret_cast<double2*>(w + x) = make_double2(wx[0], wx[E - 1]);
+            else
+                w[x] = wx[0];
+        }
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            if (MODE == 2) {
+                acc[0] += wx[e] * wx[e];
+            } else {
+#pragma unroll
+                for (int i = 0; i < NA; ++i)
+                    if (i < k) acc[i] += v[i][e] * wx[e];
+            }
+        }
+    }
+    reduce_partials<NA>(acc, MODE == 2 ? 1 : k, out, partial, counter, blockIdx.x, gridDim.x);
 }
 
 template <int KC>
@@ -356,6 +442,49 @@ int launch_dots(const double* V, int k, const double* w, long n, double* out, do
     else
         dots_kernel<64><<<RED_CTAS, RED_THREADS, 0, st>>>(V, k, w, n, out, partial, counter);
     FDE_LAUNCH_CHECK("dots_kernel");
+    return FDE_OK;
+}
+
+template <int KC, int MODE>
+static void cgs_pass_launch(const double* V, int k, const double* c, double* w, long n, double* out, double* partial,
+                            unsigned int* counter, cudaStream_t st) {
+    if constexpr (KC <= 24) {  // wider paired variants would spill
+        if ((n & 1) == 0) {
+            cgs_pass_kernel<KC, MODE, true><<<RED_CTAS, RED_THREADS, 0, st>>>(V, k, c, w, n, out, partial, counter);
+            return;
+        }
+    }
+    cgs_pass_kernel<KC, MODE, false><<<RED_CTAS, RED_THREADS, 0, st>>>(V, k, c, w, n, out, partial, counter);
+}
+
+template <int MODE>
+static void cgs_pass_dispatch(const double* V, int k, const double* c, double* w, long n, double* out,
+                              double* partial, unsigned int* counter, cudaStream_t st) {
+    if (k <= 8)
+        cgs_pass_launch<8, MODE>(V, k, c, w, n, out, partial, counter, st);
+    else if (k <= 16)
+        cgs_pass_launch<16, MODE>(V, k, c, w, n, out, partial, counter, st);
+    else if (k <= 24)
+        cgs_pass_launch<24, MODE>(V, k, c, w, n, out, partial, counter, st);
+    else if (k <= 32)
+        cgs_pass_launch<32, MODE>(V, k, c, w, n, out, partial, counter, st);
+    else
+        cgs_pass_launch<64, MODE>(V, k, c, w, n, out, partial, counter, st);
+}
+
+int launch_cgs_pass(int mode, const double* V, int k, const double* c, double* w, long n, double* out,
+                    double* partial, unsigned int* counter, cudaStream_t st) {
+    if (k <= 0 || n <= 0) return set_error(FDE_ERR_ARG, "empty Gram-Schmidt pass");
+    if (k > KMAX) return set_error(FDE_ERR_ARG, "too many Krylov vectors for one Gram-Schmidt pass");
+    if (mode == 0)
+        cgs_pass_dispatch<0>(V, k, c, w, n, out, partial, counter, st);
+    else if (mode == 1)
+        cgs_pass_dispatch<1>(V, k, c, w, n, out, partial, counter, st);
+    else if (mode == 2)
+        cgs_pass_dispatch<2>(V, k, c, w, n, out, partial, counter, st);
+    else
+        return set_error(FDE_ERR_ARG, "unknown Gram-Schmidt pass mode");
+    FDE_LAUNCH_CHECK("cgs_pass_kernel");
     return FDE_OK;
 }
 
