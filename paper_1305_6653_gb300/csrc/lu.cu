@@ -453,7 +453,12 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(src) : "memory");
 }
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(src) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 __device__ __forceinline__ void named_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
 __device__ __forceinline__ void named_arrive(int id, int n) {
@@ -829,9 +834,11 @@ constexpr int D128_LD = TB + 1;  // shared row pitch in floats (column reads con
 constexpr int D128_THREADS = 512;
 constexpr int DB = 32;           // leaf block of the blocked LU and inversion
 
-// planes [128][129] x 2 | T [2 targets][32][33] x 2 | per-warp vectors [8][32] complex | 1/U_cc of a leaf [32]
+// planes [128][129] x 2 | T [2 sides][3 targets][32][33] x 2 | per-warp vectors [8][32] complex | 1/U_cc of a leaf [32]
+constexpr int D128_NT = 3;  // inversion targets per side in one round (distance 1: three blocks)
 static size_t diag128_smem() {
-    return (size_t)(2 * TB * D128_LD + 4 * DB * (DB + 1)) * sizeof(float) + (size_t)(8 * DB + DB) * sizeof(float2);
+    return (size_t)(2 * TB * D128_LD + 4 * D128_NT * DB * (DB + 1)) * sizeof(float) +
+           (size_t)(8 * DB + DB) * sizeof(float2);
 }
 
 // One CTA per Strang block: LU (no pivoting) of the W x W block at (o, o), W = 128
@@ -856,24 +863,26 @@ __device__ __forceinline__ void diag128_body(int mp, int o, float* __restrict__ 
     extern __shared__ __align__(16) float dsm[];
     float* Ar = dsm;
     float* Ai = dsm + TB * LD;
-    float* Tr = dsm + 2 * TB * LD;          // [2][32][33]
-    float* Ti = Tr + 2 * DB * (DB + 1);     // [2][32][33]
-    float2* vec = reinterpret_cast<float2*>(Ti + 2 * DB * (DB + 1));  // [8][32]
+    float* Tr = dsm + 2 * TB * LD;                     // [2][3][32][33]
+    float* Ti = Tr + 2 * D128_NT * DB * (DB + 1);      // [2][3][32][33]
+    float2* vec = reinterpret_cast<float2*>(Ti + 2 * D128_NT * DB * (DB + 1));  // [8][32]
     float2* pinv = vec + 8 * DB;                                   // [32]
     float* im = re + (size_t)mp * mp;
     const int W = mp - o < TB ? mp - o : TB;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const int sh4 = W == TB ? 5 : 4;  // log2(W / 4): float4 columns per row
-#pragma unroll 4
-    for (int e = t; e < W * W / 4; e += blockDim.x) {
-        const int r = e >> sh4, c = (e & ((1 << sh4) - 1)) * 4;
-        const size_t g = (size_t)(o + r) * mp + o + c;
-        const float4 a = *reinterpret_cast<const float4*>(re + g);
-        const float4 b = *reinterpret_cast<const float4*>(im + g);
-        float* pr = Ar + r * LD + c;
-        float* pi = Ai + r * LD + c;
-        pr[0] = a.x, pr[1] = a.y, pr[2] = a.z, pr[3] = a.w;
-        pi[0] = b.x, pi[1] = b.y, pi[2] = b.z, pi[3] = b.w;
+    {
+        // 4-byte asynchronous copies straight into the padded planes, all in flight
+        // at once (the row pitch of 129 floats rules out 16-byte copies)
+        const int shw = sh4 + 2;
+        for (int e = t; e < W * W; e += blockDim.x) {
+            const int r = e >> shw, c = e & (W - 1);
+            const size_t g = (size_t)(o + r) * mp + o + c;
+            cp_async4(Ar + r * LD + c, re + g);
+            cp_async4(Ai + r * LD + c, im + g);
+        }
+        cp_async_commit();
+        cp_async_wait_all();
     }
     __syncthreads();
     for (int P0 = 0; P0 < W; P0 += DB) {
@@ -1049,46 +1058,64 @@ __device__ __forceinline__ void diag128_body(int mp, int o, float* __restrict__ 
         }
     }
     __syncthreads();
-    // phases d = 1..3: in round q the L-side target (i, i-d), i = d + q, runs on threads
-    // 0..255 and the U-side target (q, q+d) on threads 256..511; a thread owns row r
-    // and the four columns c + 8u of its target
+    // phases d = 1..3: every target at distance d in one round -- the L-side targets
+    // (q + d, q) on threads 0..255, the U-side targets (q, q + d) on threads 256..511,
+    // q = 0 .. 3 - d; a thread owns row r and the four columns c + 8u of each target
     {
+        constexpr int TS = DB * (DB + 1);
         const bool lower = t < 256;
         const int lt = t & 255, r = lt >> 3, c = lt & 7;
-        float* Th_r = Tr + (lower ? 0 : DB * (DB + 1));
-        float* Th_i = Ti + (lower ? 0 : DB * (DB + 1));
+        float* Th_r = Tr + (lower ? 0 : D128_NT * TS);
+        float* Th_i = Ti + (lower ? 0 : D128_NT * TS);
         for (int d = 1; d < TB / DB; ++d) {
-            for (int q = 0; q < TB / DB - d; ++q) {
-                const int i = lower ? d + q : q;
-                const int j = lower ? i - d : i + d;
-                float tr[4] = {0.f, 0.f, 0.f, 0.f}, tim[4] = {0.f, 0.f, 0.f, 0.f};
-                // off-diagonal source blocks (L side kb in (j, i), U side kb in (i, j)): their
-                // originals were overwritten by earlier phases, so each is staged from the
-                // factor in L2 into this half's T buffer (free until T is stored)
-                for (int kq = 0; kq < d - 1; ++kq) {
+            const int nq = TB / DB - d;
+            float tr[D128_NT][4], tim[D128_NT][4];
+#pragma unroll
+            for (int q = 0; q < D128_NT; ++q)
+#pragma unroll
+                for (int u = 0; u < 4; ++u) tr[q][u] = tim[q][u] = 0.f;
+            // off-diagonal source blocks (L side kb in (j, i), U side kb in (i, j)): their
+            // originals were overwritten by earlier rounds, so each is staged from the
+            // factor in L2 into the target's T buffer (free until T is stored)
+            for (int kq = 0; kq < d - 1; ++kq) {
+#pragma unroll
+                for (int q = 0; q < D128_NT; ++q) {
+                    if (q >= nq) break;
+                    const int i = lower ? d + q : q, j = lower ? q : q + d;
                     const int kb = lower ? j + 1 + kq : i + 1 + kq;
                     for (int e = lt; e < DB * DB; e += 256) {
                         const int rr = e >> 5, cc = e & 31;
                         const size_t g = (size_t)(o + DB * i + rr) * mp + o + DB * kb + cc;
-                        Th_r[rr * (DB + 1) + cc] = __ldcg(re + g);
-                        Th_i[rr * (DB + 1) + cc] = __ldcg(im + g);
+                        Th_r[q * TS + rr * (DB + 1) + cc] = __ldcg(re + g);
+                        Th_i[q * TS + rr * (DB + 1) + cc] = __ldcg(im + g);
                     }
-                    __syncthreads();
+                }
+                __syncthreads();
+#pragma unroll
+                for (int q = 0; q < D128_NT; ++q) {
+                    if (q >= nq) break;
+                    const int j = lower ? q : q + d;
+                    const int kb = lower ? j + 1 + kq : q + 1 + kq;
 #pragma unroll 4
                     for (int kk = 0; kk < DB; ++kk) {
-                        const float sr = Th_r[r * (DB + 1) + kk], si = Th_i[r * (DB + 1) + kk];
+                        const float sr = Th_r[q * TS + r * (DB + 1) + kk], si = Th_i[q * TS + r * (DB + 1) + kk];
                         const int zi = (DB * kb + kk) * LD + DB * j + c;
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
                             const float zr = Ar[zi + 8 * u], zm = Ai[zi + 8 * u];
-                            tr[u] += sr * zr - si * zm;
-                            tim[u] += sr * zm + si * zr;
+                            tr[q][u] += sr * zr - si * zm;
+                            tim[q][u] += sr * zm + si * zr;
                         }
                     }
-                    __syncthreads();
                 }
-                // the diagonal term: the target's own original block (still in place) times
-                // the inverted diagonal block of column block j, unit lower (L) / upper (U)
+                __syncthreads();
+            }
+            // the diagonal term: the target's own original block (still in place) times
+            // the inverted diagonal block of column block j, unit lower (L) / upper (U)
+#pragma unroll
+            for (int q = 0; q < D128_NT; ++q) {
+                if (q >= nq) break;
+                const int i = lower ? d + q : q, j = lower ? q : q + d;
                 const int srow = (DB * i + r) * LD + DB * j;
 #pragma unroll 4
                 for (int kk = 0; kk < DB; ++kk) {
@@ -1104,22 +1131,27 @@ __device__ __forceinline__ void diag128_body(int mp, int o, float* __restrict__ 
                         } else if (kk > col) {
                             zr = zm = 0.f;
                         }
-                        tr[u] += sr * zr - si * zm;
-                        tim[u] += sr * zm + si * zr;
+                        tr[q][u] += sr * zr - si * zm;
+                        tim[q][u] += sr * zm + si * zr;
                     }
                 }
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    Th_r[r * (DB + 1) + c + 8 * u] = tr[u];
-                    Th_i[r * (DB + 1) + c + 8 * u] = tim[u];
+                    Th_r[q * TS + r * (DB + 1) + c + 8 * u] = tr[q][u];
+                    Th_i[q * TS + r * (DB + 1) + c + 8 * u] = tim[q][u];
                 }
-                __syncthreads();
-                // Z_ij = -Z_ii T: L side unit lower (kk < r, plus T[r]), U side upper (kk >= r)
+            }
+            __syncthreads();
+            // Z_ij = -Z_ii T: L side unit lower (kk < r, plus T[r]), U side upper (kk >= r)
+#pragma unroll
+            for (int q = 0; q < D128_NT; ++q) {
+                if (q >= nq) break;
+                const int i = lower ? d + q : q, j = lower ? q : q + d;
                 float orr[4], oii[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    orr[u] = lower ? Th_r[r * (DB + 1) + c + 8 * u] : 0.f;
-                    oii[u] = lower ? Th_i[r * (DB + 1) + c + 8 * u] : 0.f;
+                    orr[u] = lower ? Th_r[q * TS + r * (DB + 1) + c + 8 * u] : 0.f;
+                    oii[u] = lower ? Th_i[q * TS + r * (DB + 1) + c + 8 * u] : 0.f;
                 }
                 const int zrow = (DB * i + r) * LD + DB * i;
                 const int k0 = lower ? 0 : r, k1 = lower ? r : DB;
@@ -1127,7 +1159,8 @@ __device__ __forceinline__ void diag128_body(int mp, int o, float* __restrict__ 
                     const float zr = Ar[zrow + kk], zm = Ai[zrow + kk];
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
-                        const float ar = Th_r[kk * (DB + 1) + c + 8 * u], ai = Th_i[kk * (DB + 1) + c + 8 * u];
+                        const float ar = Th_r[q * TS + kk * (DB + 1) + c + 8 * u];
+                        const float ai = Th_i[q * TS + kk * (DB + 1) + c + 8 * u];
                         orr[u] += zr * ar - zm * ai;
                         oii[u] += zr * ai + zm * ar;
                     }
@@ -1138,16 +1171,18 @@ __device__ __forceinline__ void diag128_body(int mp, int o, float* __restrict__ 
                     Ar[oi + 8 * u] = -orr[u];
                     Ai[oi + 8 * u] = -oii[u];
                 }
-                __syncthreads();
             }
+            __syncthreads();
         }
     }
-    // pack: L^{-1} as A' (row i, K' = [Re | Im] of L^{-1}[i][:]), U^{-1} as B'
+    // pack: L^{-1} as A' (row i, K' = [Re | Im] of L^{-1}[i][:]), U^{-1} as B'.
+    // Consecutive threads take consecutive rows of one segment column: eight threads
+    // fill one 128-byte core-matrix group, and a warp's shared reads hit 32 banks.
     constexpr int EPS = Cfg::PER_CORE;
     constexpr int SEGS = 2 * TB / EPS;  // segments per packed row
     unsigned char* pB = pA + Cfg::A_TILE;
     for (int e = t; e < TB * SEGS; e += blockDim.x) {
-        const int i = e / SEGS, kp0 = (e % SEGS) * EPS;
+        const int i = e % TB, kp0 = (e / TB) * EPS;
         const bool imag = kp0 >= TB;
         float v[EPS];
 #pragma unroll
@@ -1158,7 +1193,7 @@ __device__ __forceinline__ void diag128_body(int mp, int o, float* __restrict__ 
         pack2_seg<KIND>(pA, T2_BM, i, kp0, v, false);
     }
     for (int e = t; e < 2 * TB * SEGS; e += blockDim.x) {
-        const int brow = e / SEGS, kp0 = (e % SEGS) * EPS;
+        const int brow = e % (2 * TB), kp0 = (e / (2 * TB)) * EPS;
         const int j = brow & (TB - 1);
         const bool im_out = brow >= TB, second = kp0 >= TB;
         // Re output row: [Re U^{-1}[k][j] | -Im U^{-1}[k][j]]; Im output row: [Im | Re]
