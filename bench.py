@@ -49,10 +49,13 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
-    ap.add_argument("--config", choices=["scale", "batch", "learned", "precision"], default="scale",
+    ap.add_argument("--config", choices=["scale", "batch", "learned", "precision", "bccb", "example41"],
+                    default="scale",
                     help="scale: one m=2047/s=256 instance per step; batch: 64 uneven instances per step; "
                          "learned: train the warm-start operator on m=1023/s=256 solves, then compare guesses; "
-                         "precision: m=4095/s=128, alpha=1.9, every preconditioner precision")
+                         "precision: m=4095/s=128, alpha=1.9, every preconditioner precision; "
+                         "bccb: the scale workload with the Strang-type BCCB preconditioners; "
+                         "example41: every row of Tables 1-2 with the columns I, S, S^(2), S~^(2)")
     ap.add_argument("--train", type=int, default=4096, help="learned: method-generated training solves")
     ap.add_argument("--epochs", type=int, default=40, help="learned: passes over the training set")
     ap.add_argument("--eval", type=int, default=32, help="learned: held-out instances")
@@ -157,6 +160,25 @@ def tc_update_bytes(mp: int, nblk: int, tb: int = 128) -> float:
         tot += 16.0 * r * r
         o += tb
     return tot * nblk
+
+
+def matvec_flops(m: int, s: int, L: int, mu: int) -> float:
+    """Algorithmic FP64 flops of one space-time matvec launch (s time rows).  Per row:
+    the real-input forward FFT as a length-L/2 complex FFT (radix-4 passes of L/8
+    butterflies at 34 flops, one radix-2 pass of L/4 at 4 flops when log2(L/2) is
+    odd), the split and symbol product (30 flops per output), the length-L inverse
+    radix-4 FFT, the (mu+1)-tap band (4 flops per tap and point) and the output
+    combination (8 flops per point)."""
+    import math
+    n = L // 2
+    ln = int(math.log2(n))
+    fwd = (ln // 2) * (n // 4) * 34 + (ln % 2) * (n // 2) * 4
+    lL = int(math.log2(L))
+    inv = (lL // 2) * (L // 4) * 34 + (lL % 2) * (L // 2) * 4
+    return float(s) * (fwd + 30 * n + inv + 4 * (mu + 1) * m + 8 * m)
+
+
+FP64_PEAK_TFLOPS = 1.25  # GB300 nominal FP64 (no measured FP64 figure in MEASURED_PEAKS.json)
 
 
 def trsv_bytes(mp: int, nblk: int, esz: int) -> float:
@@ -369,6 +391,152 @@ def bench_precision(args, world, rank, local_rank):
 
 
 # ---------------------------------------------------------------------------
+# Strang-type BCCB preconditioners S^(2) / S~^(2) on the benchmark workload
+# ---------------------------------------------------------------------------
+
+def bench_bccb(args, world, rank, local_rank):
+    import numpy as np
+    import torch
+
+    import fde_inputs
+    import paper_1305_6653_gb300 as fde
+
+    torch.cuda.set_device(local_rank)
+    prob = fde_inputs.config_scale(args.m, args.s)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    xbuf = torch.empty(prob.n, dtype=torch.float64, device="cuda")
+    p = fde.FDEProblem.from_inputs(prob, device_inputs=True)
+    bprec = "fp32" if args.precision in ("fp32", "tf32", "bf16", "tf32x3") else "fp64"
+
+    def step(modified):
+        p.assemble().bccb(modified=modified, precision=bprec)
+        _, st = p.solve(tol=args.tol, restart=20, maxit=20000, out=xbuf, raise_on_error=False)
+        return st
+
+    variants = {}
+    l0 = fde.fde_launch_count()
+    sampler = ClockSampler(local_rank)
+    if not args.no_clocks:
+        sampler.start()
+    mv_ms, mv_launches = 0.0, 0
+    for name, modified in (("S2", False), ("S2_modified", True)):
+        for _ in range(args.warmup):
+            step(modified)
+        times, st = [], None
+        p.profile(True)
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            st = step(modified)
+            e1.record()
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        prof = p.profile_read()
+        p.profile(False)
+        ms = sum(times) / len(times)
+        stages = {k: v[0] / args.steps for k, v in prof.items() if v[1]}
+        variants[name] = {"solves_per_s": 1e3 / ms, "ms_per_step": ms, "iterations": st["iterations"],
+                          "rel_residual": st["rel_residual"], "converged": st["status"] == 0,
+                          "stage_ms_per_step": stages}
+        if name == "S2":
+            mv_ms, mv_launches = prof["matvec"]
+    clocks = sampler.stop() if not args.no_clocks else None
+    launches = fde.fde_launch_count() - l0
+    p.close()
+    conv = [k for k, v in variants.items() if v["converged"]]
+    best = max(conv, key=lambda k: variants[k]["solves_per_s"]) if conv else "S2"
+    head = variants[best]
+    flops = matvec_flops(prob.m, prob.s, 1 << (2 * prob.m - 1).bit_length(), prob.mu)
+    per_launch_s = mv_ms / max(mv_launches, 1) / 1e3
+    achieved = flops / per_launch_s / 1e12 if per_launch_s > 0 else None
+    roof = {"kernel": "st_matvec_kernel", "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+            "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS if achieved else None, "traffic": None,
+            "peak_kind": "nominal FP64 (152 SMs x 2 FP64 FMA per clock x 2.07 GHz)",
+            "algorithmic_flops_per_launch": flops}
+    if rank == 0:
+        line = {"metric": METRIC, "value": world * head["solves_per_s"], "unit": "solves/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if bprec == "fp64" else "f32+f64", "data": "synthetic",
+                "config": {"workload": f"bccb_scale_m{prob.m}_s{prob.s}_gbdf5_alpha1.8_variable_d", "m": prob.m,
+                           "s": prob.s, "unknowns": prob.n, "preconditioner": best, "apply_precision": bprec,
+                           "tol_true_residual": args.tol, "restart": 20,
+                           "l2": "flushed (512 MiB write) before every timed step"},
+                "roofline": roof, "gpu_launches": launches, "clocks": clocks, "variants": variants}
+        print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------
+# Example 4.1 (Sec. 4, Tables 1-2): every row with the columns I, S, S^(2), S~^(2)
+# ---------------------------------------------------------------------------
+
+def bench_example41(args, world, rank, local_rank):
+    import os
+
+    import torch
+
+    import fde_inputs
+    import paper_1305_6653_gb300 as fde
+
+    torch.cuda.set_device(local_rank)
+    golden = {}
+    for fn, cols in (("paper_tables_its.txt", ("I", "S")), ("paper_tables_bccb_its.txt", ("S2", "S2_modified"))):
+        for line in open(os.path.join(ROOT, "tests", "golden", fn)):
+            if line.strip() and not line.startswith("#"):
+                a, n, s_, c1, c2 = line.split()
+                golden.setdefault((float(a), int(n), int(s_)), {}).update({cols[0]: int(c1), cols[1]: int(c2)})
+    setups = {"I": lambda p: p.no_precond(), "S": lambda p: p.factor("fp64"), "S2": lambda p: p.bccb(),
+              "S2_modified": lambda p: p.bccb(modified=True)}
+    rows, total_ms, nsolves = [], 0.0, 0
+    l0 = fde.fde_launch_count()
+    sampler = ClockSampler(local_rank)
+    if not args.no_clocks:
+        sampler.start()
+    for (alpha, n, s_), paper in sorted(golden.items()):
+        prob = fde_inputs.example_4_1(alpha, n, s_)
+        xbuf = torch.empty(prob.n, dtype=torch.float64, device="cuda")
+        row = {"alpha": alpha, "n": n, "s": s_}
+        with fde.FDEProblem.from_inputs(prob, device_inputs=True) as p:
+            for name, setup in setups.items():
+                def step():
+                    setup(p.assemble())
+                    return p.solve(tol=1e-8, restart=20, maxit=5000, out=xbuf, raise_on_error=False)[1]
+                for _ in range(args.warmup):
+                    step()
+                times, st = [], None
+                for _ in range(args.steps):
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    st = step()
+                    e1.record()
+                    e1.synchronize()
+                    times.append(e0.elapsed_time(e1))
+                ms = sum(times) / len(times)
+                total_ms += ms
+                nsolves += 1
+                row[name] = {"its": st["iterations"], "paper_its": paper[name], "ms": ms,
+                             "converged": st["status"] == 0}
+        rows.append(row)
+    clocks = sampler.stop() if not args.no_clocks else None
+    launches = fde.fde_launch_count() - l0
+    if rank == 0:
+        line = {"metric": METRIC, "value": world * nsolves * 1e3 / total_ms, "unit": "solves/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / nsolves,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic",
+                "config": {"workload": "example_4_1_tables_1_2", "rows": len(rows),
+                           "preconditioners": list(setups), "tol": 1e-8, "restart": 20,
+                           "stopping": "true residual relative to ||b|| (x0 = 0, so ||r0|| = ||b||); the paper's "
+                                       "counts use the left-preconditioned residual",
+                           "l2": "inputs of a few MB; every solve re-assembles and re-sets up its preconditioner"},
+                "roofline": None, "gpu_launches": launches, "clocks": clocks, "rows": rows}
+        print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------
 # learned warm start: train on method-generated solves, compare initial guesses
 # ---------------------------------------------------------------------------
 
@@ -465,6 +633,10 @@ def main():
         return bench_batch(args, world, rank, local_rank)
     if args.config == "learned" and args.impl == "ours":
         return bench_learned(args, world, rank, local_rank)
+    if args.config == "example41" and args.impl == "ours":
+        return bench_example41(args, world, rank, local_rank)
+    if args.config == "bccb" and args.impl == "ours":
+        return bench_bccb(args, world, rank, local_rank)
     if args.config == "precision" and args.impl == "ours":
         return bench_precision(args, world, rank, local_rank)
     prob = fde_inputs.config_scale(args.m, args.s)

@@ -137,11 +137,34 @@ int bvm_assemble(fde_problem* p);
  * FDE_ERR_STATE, FDE_ERR_CUDA. */
 int strang_precond_factor(fde_problem* p, int precision);
 
-/* Solve M u = b by flexible GMRES(restart) right-preconditioned with S.
+/* Set up the Strang-type BCCB preconditioner S^(2) = s(A) (x) I - h s(B) (x) s(J)
+ * (eq. (x1), Sec. 3.1), or with modified != 0 the preconditioner S~^(2) of eq. (xc),
+ * whose eigenvalue phi_0 = 0 of s(A) is replaced by Re(phi_{s-1}).  s(J) =
+ * dx^-alpha (mean(d+) s(G) + mean(d-) s(G)^T), s(G) the Strang circulant of G with
+ * first column [g_1, .., g_K, 0, .., 0, g_0], K = floor((m+1)/2).  It is applied by
+ * the two-dimensional Fourier diagonalisation of Sec. 3.3: the FFT along time, one
+ * circulant solve per time frequency (a length-L FFT convolution with the first
+ * column of the circulant inverse), the inverse FFT along time.  precision:
+ * FDE_FP64 or FDE_FP32 arithmetic of the apply (the set-up is FP64).  After this
+ * call pgmres_solve and fde_precond_apply use S^(2) (or S~^(2)) until
+ * strang_precond_factor selects S again; no block LU is formed.  The library owns
+ * the spectra (16 (s/2+1) L + 8 (s/2+1) L bytes, L = the power of two >= 2m).
+ * Requires bvm_assemble.  Errors: FDE_ERR_ARG, FDE_ERR_STATE, FDE_ERR_ALLOC,
+ * FDE_ERR_SINGULAR (a zero eigenvalue of the preconditioner), FDE_ERR_CUDA. */
+int bccb_precond_setup(fde_problem* p, int modified, int precision);
+
+/* Select no preconditioner (the column "I" of Tables 1-2, Sec. 4): pgmres_solve then
+ * runs plain restarted GMRES on M u = b (z_j = v_j).  Requires bvm_assemble.
+ * strang_precond_factor or bccb_precond_setup select a preconditioner again.
+ * Errors: FDE_ERR_ARG, FDE_ERR_STATE. */
+int fde_precond_none(fde_problem* p);
+
+/* Solve M u = b by flexible GMRES(restart) right-preconditioned with S (or with the
+ * BCCB preconditioner after bccb_precond_setup, or none after fde_precond_none).
  * x0: device, length s*m initial guess, or NULL for zero; a guess whose residual
  * exceeds ||b|| (or is not finite) is replaced by zero (stats->x0_rejected).  x_out: device, length
  * s*m (may alias x0).  st: host, may be NULL.  On FDE_ERR_NOT_CONVERGED x_out
- * holds the last iterate.  Requires strang_precond_factor.  Errors: FDE_ERR_ARG,
+ * holds the last iterate.  Requires strang_precond_factor or bccb_precond_setup.  Errors: FDE_ERR_ARG,
  * FDE_ERR_STATE, FDE_ERR_NOT_CONVERGED, FDE_ERR_NAN, FDE_ERR_CUDA. */
 int pgmres_solve(fde_problem* p, const fde_pgmres_opts* opts, const double* x0, double* x_out,
                  fde_stats* st);

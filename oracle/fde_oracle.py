@@ -33,6 +33,15 @@ Readings of points the paper leaves open (each is listed in the design notes):
   iterations across restarts; the stopping test there is the preconditioned
   residual relative to the initial one.
 
+Strang-type BCCB preconditioners (eqs. x1 and xc, Sec. 3.1), readings:
+
+* s(G) is the circulant whose first column the paper displays: g_1 .. g_K on
+  the diagonal and the first K-1 subdiagonals (K = floor((N+1)/2)), g_0 on the
+  superdiagonal that wraps to the last row; s(G^T) is its transpose (the
+  display of its first column is garbled in its last entry).
+* The modified preconditioner replaces the zero eigenvalue phi_0 of s(A) by
+  Re(phi_{s-1}) (the paper's "phi_s", the last eigenvalue in its indexing).
+
 Parity pins: every function below is checked in ``tests/test_oracle_*.py``
 against something other than itself (closed forms, invariants, the paper's
 printed tables, brute force); there is no "parity unpinned" function.
@@ -64,6 +73,12 @@ __all__ = [
     "StrangPreconditioner",
     "gmres",
     "solve_strang_gmres",
+    "strang_g_column",
+    "circulant",
+    "strang_j_matrix",
+    "bccb_matrix",
+    "BCCBPreconditioner",
+    "solve_bccb_gmres",
 ]
 
 
@@ -482,3 +497,98 @@ def solve_strang_gmres(prob, *, side: str = "right", restart: int = 20, tol: flo
                              side=side, restart=restart, tol=tol, maxit=maxit,
                              reference=reference, x0=x0)
     return x, its, ok, hist
+
+
+# ---------------------------------------------------------------------------
+# Sec. 3.1, eqs. (x1) and (xc): Strang-type BCCB preconditioners
+# ---------------------------------------------------------------------------
+
+def strang_g_column(alpha: float, m: int) -> np.ndarray:
+    """First column of the m x m Strang circulant s(G_alpha) as the paper displays it:
+    [g_1, ..., g_K, 0, ..., 0, g_0] with K = floor((m+1)/2)."""
+    g = grunwald_weights(alpha, m + 1)
+    c = np.zeros(m)
+    K = (m + 1) // 2
+    for i in range(K):
+        c[i] += g[i + 1]
+    c[m - 1] += g[0]
+    return c
+
+
+def circulant(c: np.ndarray) -> np.ndarray:
+    """Dense circulant with first column c: C[i, j] = c[(i - j) mod n]."""
+    n = len(c)
+    C = np.empty((n, n), dtype=np.result_type(c, np.float64))
+    for i in range(n):
+        for j in range(n):
+            C[i, j] = c[(i - j) % n]
+    return C
+
+
+def strang_j_matrix(prob) -> np.ndarray:
+    """Dense s(J_N) = dx^-alpha (mean(d+) s(G) + mean(d-) s(G)^T) (Sec. 3.1, below eq. x1)."""
+    m = prob.m
+    dp = float(np.mean(np.broadcast_to(np.asarray(prob.dplus, dtype=np.float64), (m,))))
+    dm = float(np.mean(np.broadcast_to(np.asarray(prob.dminus, dtype=np.float64), (m,))))
+    sG = circulant(strang_g_column(prob.alpha, m))
+    return prob.dx ** (-prob.alpha) * (dp * sG + dm * sG.T)
+
+
+def _s_of_a_modified(prob) -> np.ndarray:
+    """s~(A) (eq. xc): s(A) with its eigenvalue phi_0 = 0 moved to Re(phi_{s-1}).
+    As a matrix: s(A) + (phi~_0 - phi_0) / s * ones (the rank-one change of the
+    eigenvalue that belongs to the constant eigenvector)."""
+    nu = nu_of(prob.family, prob.mu)
+    a, _ = lmf_coefficients(prob.family, prob.mu, nu)
+    sA = strang_circulant(a, nu, prob.s)
+    phi, _ = strang_symbols(prob.family, prob.mu, prob.s)
+    return sA + (phi[-1].real - phi[0].real) / prob.s * np.ones((prob.s, prob.s))
+
+
+def bccb_matrix(prob, modified: bool = False) -> np.ndarray:
+    """Dense S^(2) = s(A) (x) I - h s(B) (x) s(J) (eq. x1), or S~^(2) with s~(A) (eq. xc)."""
+    nu = nu_of(prob.family, prob.mu)
+    a, b = lmf_coefficients(prob.family, prob.mu, nu)
+    sA = _s_of_a_modified(prob) if modified else strang_circulant(a, nu, prob.s)
+    sB = strang_circulant(b, nu, prob.s)
+    return np.kron(sA, np.eye(prob.m)) - prob.h * np.kron(sB, strang_j_matrix(prob))
+
+
+class BCCBPreconditioner:
+    """(S^(2))^{-1} r or (S~^(2))^{-1} r by the two-dimensional DFT diagonalisation
+    of Sec. 3.3: F along time and F_N along space, division by the eigenvalues
+    phi_j - h psi_j lambda_k(s(J)) (eq. 1.13), inverse transforms.
+
+    lambda_k(s(J)) = sum_i c_i exp(-2 pi i i k / N) for the first column c of
+    s(J); numpy.fft uses the same sign, so fft(c) pairs with fft(x) along space.
+    """
+
+    def __init__(self, prob, modified: bool = False):
+        self.s, self.m, self.h = prob.s, prob.m, prob.h
+        phi, psi = strang_symbols(prob.family, prob.mu, prob.s)
+        if modified:
+            phi = phi.copy()
+            phi[0] = phi[-1].real
+        m = prob.m
+        dp = float(np.mean(np.broadcast_to(np.asarray(prob.dplus, dtype=np.float64), (m,))))
+        dm = float(np.mean(np.broadcast_to(np.asarray(prob.dminus, dtype=np.float64), (m,))))
+        cG = strang_g_column(prob.alpha, m)
+        cGT = np.roll(cG[::-1], 1)  # first column of s(G)^T: c[(-i) mod m]
+        self.lam_J = np.fft.fft(prob.dx ** (-prob.alpha) * (dp * cG + dm * cGT))
+        self.D = phi[:, None] - prob.h * psi[:, None] * self.lam_J[None, :]
+
+    def apply(self, r: np.ndarray) -> np.ndarray:
+        R = r.reshape(self.s, self.m)
+        X = np.fft.fft2(R) / self.D
+        return np.fft.ifft2(X).real.reshape(-1)
+
+
+def solve_bccb_gmres(prob, *, modified: bool = False, side: str = "right", restart: int = 20,
+                     tol: float = 1e-12, maxit: int = 5000, reference: str = "b", x0=None):
+    """GMRES on the reduced system with the BCCB preconditioner (FP64 throughout)."""
+    J = j_of(prob)
+    AB = bvm_matrices(prob.family, prob.mu, prob.s)
+    P = BCCBPreconditioner(prob, modified=modified)
+    b = reduced_rhs(prob, J=J)
+    return gmres(lambda z: matvec(prob, z, J=J, AB=AB), b, precond=P.apply, side=side, restart=restart,
+                 tol=tol, maxit=maxit, reference=reference, x0=x0)

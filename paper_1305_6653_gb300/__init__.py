@@ -17,7 +17,8 @@ from . import _lib
 from ._lib import (FDE_BF16, FDE_ETR, FDE_FP32, FDE_FP64, FDE_GAM, FDE_GBDF, FDE_TF32, FdeError,  # noqa: F401
                    FdePgmresOpts, FdeProblemDesc, FdeStats, PRECISIONS, FAMILIES)
 
-__all__ = ["FDEProblem", "FDEBatch", "FDENop", "fde_problem_create", "bvm_assemble", "strang_precond_factor", "pgmres_solve",
+__all__ = ["FDEProblem", "FDEBatch", "FDENop", "fde_problem_create", "bvm_assemble", "strang_precond_factor",
+           "bccb_precond_setup", "pgmres_solve",
            "fde_problem_destroy", "fde_matvec", "fde_precond_apply", "FdeError", "PRECISIONS"]
 
 
@@ -49,6 +50,11 @@ def bvm_assemble(h) -> None:
 def strang_precond_factor(h, precision) -> None:
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     _lib.check(_lib.load().strang_precond_factor(h, prec), "strang_precond_factor")
+
+
+def bccb_precond_setup(h, modified: bool = False, precision="fp64") -> None:
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    _lib.check(_lib.load().bccb_precond_setup(h, 1 if modified else 0, prec), "bccb_precond_setup")
 
 
 def pgmres_solve(h, opts: FdePgmresOpts, x0_ptr: int | None, x_ptr: int, raise_on_error: bool = True) -> FdeStats:
@@ -133,6 +139,16 @@ class FDEProblem:
 
     def factor(self, precision="fp64"):
         strang_precond_factor(self.h, precision)
+        return self
+
+    def no_precond(self):
+        """Plain GMRES (no preconditioner) for the solves."""
+        _lib.check(_lib.load().fde_precond_none(self.h), "fde_precond_none")
+        return self
+
+    def bccb(self, modified=False, precision="fp64"):
+        """Select the Strang-type BCCB preconditioner S^(2) (or S~^(2)) for the solves."""
+        bccb_precond_setup(self.h, modified, precision)
         return self
 
     def solve(self, tol=1e-10, restart=20, maxit=1000, reorth=1, x0=None, out=None, raise_on_error=True):

@@ -32,7 +32,9 @@ ERROR_NAMES = {
 
 # Every symbol declared in include/fde.h (checked by the CPU tests).
 EXPORTED = [
-    "fde_problem_create", "bvm_assemble", "strang_precond_factor", "pgmres_solve", "fde_problem_destroy",
+    "fde_problem_create", "bvm_assemble", "strang_precond_factor", "bccb_precond_setup", "fde_precond_none",
+    "pgmres_solve",
+    "fde_problem_destroy",
     "fde_last_error", "fde_matvec", "fde_precond_apply", "fde_get_rhs", "fde_get_factor_block",
     "fde_get_grunwald", "fde_problem_sizes", "fde_profile_enable", "fde_profile_read", "fde_launch_count",
     "fde_precond_apply_noalloc", "fde_batch_create", "fde_batch_assemble", "fde_batch_factor",
@@ -92,6 +94,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "fde_problem_create": (i32, [C.POINTER(FdeProblemDesc), vp, C.POINTER(vp)]),
         "bvm_assemble": (i32, [vp]),
         "strang_precond_factor": (i32, [vp, i32]),
+        "bccb_precond_setup": (i32, [vp, i32, i32]),
+        "fde_precond_none": (i32, [vp]),
         "pgmres_solve": (i32, [vp, C.POINTER(FdePgmresOpts), vp, vp, C.POINTER(FdeStats)]),
         "fde_problem_destroy": (None, [vp]),
         "fde_last_error": (C.c_char_p, []),

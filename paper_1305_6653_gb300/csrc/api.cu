@@ -223,6 +223,23 @@ int ensure_factor_buffers(Problem& P, int precision) {
 
 static int apply_precond(Problem& P, const double* r, double* z) {
     int rc;
+    if (P.precond == FDE_PRECOND_NONE) {  // plain GMRES: z = r
+        StageTimer t(P, FDE_STAGE_TRSV);
+        FDE_CUDA_TRY(cudaMemcpyAsync(z, r, (size_t)P.n * sizeof(double), cudaMemcpyDeviceToDevice, P.stream));
+        return FDE_OK;
+    }
+    if (P.precond != FDE_PRECOND_STRANG) {  // S^(2) / S~^(2): time FFT, circulant solves, inverse
+        {
+            StageTimer t(P, FDE_STAGE_TFFT_FWD);
+            if ((rc = launch_time_fft_fwd(P, r, P.d_rhat_b, P.bccb_precision, P.stream))) return rc;
+        }
+        {
+            StageTimer t(P, FDE_STAGE_TRSV);
+            if ((rc = launch_bccb_solve(P, P.d_rhat_b, P.bccb_precision, P.stream))) return rc;
+        }
+        StageTimer t(P, FDE_STAGE_TFFT_INV);
+        return launch_time_fft_inv(P, P.d_rhat_b, z, P.bccb_precision, P.stream);
+    }
     {
         StageTimer t(P, FDE_STAGE_TFFT_FWD);
         if ((rc = launch_time_fft_fwd(P, r, P.d_rhat, P.precision, P.stream))) return rc;
@@ -441,7 +458,7 @@ void fde_problem_destroy(fde_problem* h) {
     void* bufs[] = {P.d_start, P.d_a, P.d_b, P.d_dplus, P.d_dminus, P.d_u0, P.d_f, P.d_g, P.d_twL, P.d_twL32,
                     P.d_sym, P.d_sym32, P.d_tws, P.d_tws32, P.d_phi, P.d_psi, P.d_b_rhs, P.d_work, P.d_rhat,
                     P.d_fac, P.d_dinv, P.d_info, P.d_err, P.d_pack, P.d_tinv, P.d_scal, P.d_partial,
-                    P.d_counter};
+                    P.d_counter, P.d_bccb_K64, P.d_bccb_K32, P.d_rhat_b};
     for (void* b : bufs) dfree(b);
     if (h->pinned) cudaFreeHost(h->pinned);
     for (cudaEvent_t e : P.ev_pool) cudaEventDestroy(e);
@@ -554,6 +571,70 @@ int strang_precond_factor(fde_problem* h, int precision) {
             return set_error(FDE_ERR_SINGULAR, buf);
         }
     P.factored = true;
+    P.precond = FDE_PRECOND_STRANG;
+    return FDE_OK;
+}
+
+int bccb_precond_setup(fde_problem* h, int modified, int precision) {
+    g_last_error.clear();
+    if (!h) return set_error(FDE_ERR_ARG, "NULL problem");
+    Problem& P = h->P;
+    if (!P.assembled) return set_error(FDE_ERR_STATE, "bvm_assemble must run before bccb_precond_setup");
+    if (precision != FDE_FP64 && precision != FDE_FP32)
+        return set_error(FDE_ERR_ARG, "the BCCB apply runs in FDE_FP64 or FDE_FP32");
+    if (P.L < 2 * P.m) return set_error(FDE_ERR_ARG, "the BCCB apply needs the FFT length L >= 2m");
+    const int nk = P.nblk, m = P.m;
+    int rc;
+    P.factored = false;
+    if (!P.d_bccb_K64) {
+        if ((rc = dalloc(&P.d_bccb_K64, (size_t)nk * P.L))) return rc;
+        if ((rc = dalloc(&P.d_bccb_K32, (size_t)nk * P.L))) return rc;
+    }
+    if (P.d_rhat_b && P.rhat_b_prec != precision) {
+        dfree(P.d_rhat_b);
+        P.d_rhat_b = nullptr;
+    }
+    if (!P.d_rhat_b) {
+        unsigned char* rb = nullptr;
+        const size_t esz = precision == FDE_FP64 ? sizeof(double) : sizeof(float);
+        if ((rc = dalloc(&rb, (size_t)nk * P.mp * 2 * esz))) return rc;
+        FDE_CUDA_TRY(cudaMemsetAsync(rb, 0, (size_t)nk * P.mp * 2 * esz, P.stream));
+        P.d_rhat_b = rb;
+        P.rhat_b_prec = precision;
+    }
+    // Re(phi_{s-1}) = Re(phi_1) = sum_r alpha_{r+nu} cos(2 pi r / s) (Sec. 3.1)
+    double phi0_mod = 0.0;
+    for (int r = -P.nu; r <= P.mu - P.nu; ++r) phi0_mod += P.h_a_main[r + P.nu] * std::cos(2.0 * M_PI * r / P.s);
+    double* c = nullptr;
+    double2 *tw = nullptr, *mu = nullptr, *cinv = nullptr;
+    if ((rc = dalloc(&c, m)) || (rc = dalloc(&tw, m)) || (rc = dalloc(&mu, m)) ||
+        (rc = dalloc(&cinv, (size_t)nk * m))) {
+        dfree(c); dfree(tw); dfree(mu); dfree(cinv);
+        return rc;
+    }
+    FDE_CUDA_TRY(cudaMemsetAsync(P.d_err, 0, sizeof(int), P.stream));
+    rc = launch_bccb_setup(P, modified ? 1 : 0, phi0_mod, c, tw, mu, cinv, P.d_bccb_K64, P.d_bccb_K32, P.d_err,
+                           P.stream);
+    int singular = 0;
+    cudaError_t e = cudaMemcpyAsync(&singular, P.d_err, sizeof(int), cudaMemcpyDeviceToHost, P.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(P.stream);
+    dfree(c); dfree(tw); dfree(mu); dfree(cinv);
+    if (rc) return rc;
+    if (e != cudaSuccess) return cuda_error(e, "bccb_precond_setup");
+    if (singular) return set_error(FDE_ERR_SINGULAR, "the BCCB preconditioner has a zero eigenvalue");
+    P.bccb_precision = precision;
+    P.precond = modified ? FDE_PRECOND_BCCB_MODIFIED : FDE_PRECOND_BCCB;
+    P.factored = true;
+    return FDE_OK;
+}
+
+int fde_precond_none(fde_problem* h) {
+    g_last_error.clear();
+    if (!h) return set_error(FDE_ERR_ARG, "NULL problem");
+    Problem& P = h->P;
+    if (!P.assembled) return set_error(FDE_ERR_STATE, "bvm_assemble must run before fde_precond_none");
+    P.precond = FDE_PRECOND_NONE;
+    P.factored = true;
     return FDE_OK;
 }
 
@@ -592,7 +673,8 @@ int fde_get_factor_block(fde_problem* h, int k, double* re, double* im) {
     g_last_error.clear();
     if (!h || !re || !im) return set_error(FDE_ERR_ARG, "NULL argument");
     Problem& P = h->P;
-    if (!P.factored) return set_error(FDE_ERR_STATE, "strang_precond_factor must run first");
+    if (!P.factored || P.precond != FDE_PRECOND_STRANG)
+        return set_error(FDE_ERR_STATE, "strang_precond_factor must run first");
     if (k < 0 || k >= P.nblk) return set_error(FDE_ERR_ARG, "block index out of range");
     const size_t mp2 = (size_t)P.mp * P.mp;
     const bool f64 = P.precision == FDE_FP64;

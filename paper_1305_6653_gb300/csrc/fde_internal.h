@@ -184,6 +184,14 @@ struct Problem {
     size_t tinv_bytes = 0;
     void* d_pack = nullptr;     // packed tensor-core operand tiles of the LU panels
     size_t pack_bytes = 0;
+    // Strang-type BCCB preconditioner (bccb_precond_setup): the spectra K_k of the
+    // circulant inverses, k = 0..s/2, length L each, and its frequency-side vectors
+    int precond = 0;            // FDE_PRECOND_STRANG or FDE_PRECOND_BCCB / FDE_PRECOND_BCCB_MODIFIED
+    int bccb_precision = -1;    // FDE_FP64 or FDE_FP32 arithmetic of the apply
+    double2* d_bccb_K64 = nullptr;
+    float2* d_bccb_K32 = nullptr;
+    void* d_rhat_b = nullptr;   // nblk * mp complex (FP64 or FP32 by bccb_precision)
+    int rhat_b_prec = -1;
     // tensor-core LU look-ahead: panel chain on lu_hi, interior updates on lu_lo
     cudaStream_t lu_hi = nullptr, lu_lo = nullptr;
     cudaEvent_t lu_ev[3] = {nullptr, nullptr, nullptr};  // fork / cross done / interior done
@@ -211,6 +219,19 @@ struct Problem {
     size_t ev_used = 0;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_rec[FDE_NUM_STAGES];
 };
+
+// preconditioner in use by pgmres_solve / fde_precond_apply
+constexpr int FDE_PRECOND_STRANG = 0;         // block-circulant S (eq. 1.11), block LU
+constexpr int FDE_PRECOND_BCCB = 1;           // S^(2) (eq. x1)
+constexpr int FDE_PRECOND_BCCB_MODIFIED = 2;  // S~^(2) (eq. xc)
+constexpr int FDE_PRECOND_NONE = 3;           // plain GMRES (column I of Tables 1-2)
+
+// bccb.cu: set-up of the BCCB spectra (scratch: c, tw, mu of length m, cinv of nblk * m;
+// *singular set to 1 on a zero or non-finite eigenvalue of the preconditioner)
+// and the per-frequency circulant solves in place on rhat ([nblk][mp] complex)
+int launch_bccb_setup(const Problem& P, int modified, double phi0_mod, double* c, double2* tw, double2* mu,
+                      double2* cinv, double2* K64, float2* K32, int* singular, cudaStream_t st);
+int launch_bccb_solve(const Problem& P, void* rhat, int prec, cudaStream_t st);
 
 // The problem behind a C-ABI handle (defined in api.cu).
 Problem* problem_of(fde_problem* h);

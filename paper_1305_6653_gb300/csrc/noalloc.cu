@@ -48,7 +48,8 @@ extern "C" int fde_precond_apply_noalloc(fde_problem* h, const double* r, double
     if (need > NOALLOC_SCRATCH_BYTES)
         return set_error(FDE_ERR_ARG, "fde_precond_apply_noalloc: (s/2+1) * mp complex values exceed the 8 MiB "
                                       "static scratch; use fde_precond_apply");
-    if (!P.factored) return set_error(FDE_ERR_STATE, "strang_precond_factor must run first");
+    if (!P.factored || P.precond != FDE_PRECOND_STRANG)
+        return set_error(FDE_ERR_STATE, "strang_precond_factor must run first");
     void* scratch = nullptr;
     int rc = scratch_address(&scratch);
     if (rc) return rc;
