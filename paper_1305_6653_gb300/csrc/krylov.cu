@@ -7,6 +7,8 @@
 // CTA to finish (atomic ticket after a fence; nothing waits) adds them in a fixed
 // order (one warp per vector, lanes over the partials, then a shuffle tree) and
 // resets the ticket.
+#include <algorithm>
+
 #include "fde_internal.h"
 
 namespace fde {
@@ -445,16 +447,35 @@ int launch_dots(const double* V, int k, const double* w, long n, double* out, do
     return FDE_OK;
 }
 
+// One wave: as many CTAs as fit on the device at once (the wide variants hold
+// their basis values in registers and fit one CTA per SM), at most RED_CTAS.
+template <int KC, int MODE, bool PAIR>
+static int one_wave_grid() {
+    static int grid = 0;  // per kernel instantiation
+    if (grid == 0) {
+        auto kernel = cgs_pass_kernel<KC, MODE, PAIR>;
+        int dev = 0, sms = 0, occ = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, RED_THREADS, 0) != cudaSuccess || occ < 1)
+            return RED_CTAS;
+        grid = std::min(RED_CTAS, sms * occ);
+    }
+    return grid;
+}
+
 template <int KC, int MODE>
 static void cgs_pass_launch(const double* V, int k, const double* c, double* w, long n, double* out, double* partial,
                             unsigned int* counter, cudaStream_t st) {
     if constexpr (KC <= 24) {  // wider paired variants would spill
         if ((n & 1) == 0) {
-            cgs_pass_kernel<KC, MODE, true><<<RED_CTAS, RED_THREADS, 0, st>>>(V, k, c, w, n, out, partial, counter);
+            auto kern = cgs_pass_kernel<KC, MODE, true>;
+            kern<<<one_wave_grid<KC, MODE, true>(), RED_THREADS, 0, st>>>(V, k, c, w, n, out, partial, counter);
             return;
         }
     }
-    cgs_pass_kernel<KC, MODE, false><<<RED_CTAS, RED_THREADS, 0, st>>>(V, k, c, w, n, out, partial, counter);
+    auto kern = cgs_pass_kernel<KC, MODE, false>;
+    kern<<<one_wave_grid<KC, MODE, false>(), RED_THREADS, 0, st>>>(V, k, c, w, n, out, partial, counter);
 }
 
 template <int MODE>
