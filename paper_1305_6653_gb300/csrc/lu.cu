@@ -779,6 +779,24 @@ lu_update_tc2_kernel(int mp, int R0, int nt, int part, float* __restrict__ fac,
     tc2_update_body<KIND>(mp, R0, fac + (size_t)k * 2 * mp * mp, apack + k * pa, bpack + k * pb, err, ti, tj);
 }
 
+// Interior of the trailing update (tiles ti, tj >= 1) in row pairs: CTA x takes
+// tiles (1 + 2p, tj) and (2 + 2p, tj), p = x / (nt - 1), tj = 1 + x % (nt - 1).
+template <int KIND>
+__global__ void __launch_bounds__(128)
+lu_update_tc2p_kernel(int mp, int R0, int nt, float* __restrict__ fac, const unsigned char* __restrict__ apack,
+                      const unsigned char* __restrict__ bpack, size_t pa, size_t pb, int* __restrict__ err) {
+    using Cfg = Tc2<KIND>;
+    const int k = blockIdx.y, x = blockIdx.x;
+    const int ncol = nt - 1;
+    const int p = x / ncol, tj = 1 + x % ncol;
+    const int ti0 = 1 + 2 * p;
+    const bool two = ti0 + 1 < nt;
+    const unsigned char* ab = apack + (size_t)k * pa;
+    tc2_pair_body<KIND>(mp, R0 + ti0 * T2_BM, R0 + tj * T2_BN, two, fac + (size_t)k * 2 * mp * mp,
+                        ab + (size_t)ti0 * Cfg::A_TILE, ab + (size_t)(two ? ti0 + 1 : ti0) * Cfg::A_TILE,
+                        bpack + (size_t)k * pb + (size_t)tj * Cfg::B_TILE, err);
+}
+
 template <int KIND>
 __global__ void __launch_bounds__(128)
 lu_update_tc2_batched(const BlkDev* __restrict__ B, int R0, int ntg, int* __restrict__ err) {
@@ -808,6 +826,8 @@ static int set_tc_attrs() {
                                       Tc2<KIND>::SMEM));
     FDE_CUDA_TRY(cudaFuncSetAttribute(lu_update_tc2_batched<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       Tc2<KIND>::SMEM));
+    FDE_CUDA_TRY(cudaFuncSetAttribute(lu_update_tc2p_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      Tc2p<KIND>::SMEM));
     return FDE_OK;
 }
 
@@ -1443,9 +1463,9 @@ static int run_lu_tc(Problem& P, cudaStream_t st) {
             FDE_CUDA_TRY(cudaStreamWaitEvent(sl, P.lu_ev[1], 0));
             if (nt > 1) {
                 StageTimer t(P, FDE_STAGE_LU_TC, sl);
-                lu_update_tc2_kernel<KIND><<<dim3((nt - 1) * (nt - 1), nb), 128, Cfg::SMEM, sl>>>(
-                    mp, R0, nt, 2, fac, apk(o), bpk(o), pa, pb, P.d_err);
-                FDE_LAUNCH_CHECK("lu_update_tc2_kernel");
+                lu_update_tc2p_kernel<KIND><<<dim3(((nt - 1 + 1) / 2) * (nt - 1), nb), 128, Tc2p<KIND>::SMEM, sl>>>(
+                    mp, R0, nt, fac, apk(o), bpk(o), pa, pb, P.d_err);
+                FDE_LAUNCH_CHECK("lu_update_tc2p_kernel");
             }
             FDE_CUDA_TRY(cudaEventRecord(P.lu_ev[2], sl));
             if ((r = panel(R0))) return r;

@@ -129,7 +129,9 @@ __device__ __forceinline__ void bulk_prefetch_l2(const void* gmem, uint32_t byte
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(gmem), "r"(bytes) : "memory");
 }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// Wait until the committed bulk stores have read their shared-memory source (all a
+// CTA needs before it exits or reuses the buffer; the global writes complete on their own).
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 // One 128 x 128 complex output tile at (r0, c0) of one block, D = A' B'^T from the
@@ -301,7 +303,7 @@ __device__ __forceinline__ void tc2_tile_body(int mp, int r0, int c0, float* __r
             bulk_s2g(gre + (size_t)(r0 + r) * mp + c0, sCr + r * T2_CROW, row_bytes);
             bulk_s2g(gim + (size_t)(r0 + r) * mp + c0, sCi + r * T2_CROW, row_bytes);
             bulk_commit();
-            bulk_wait_all();
+            bulk_wait_read_all();
         }
     } else if (!(ok && done)) {
         // bounded: let in-flight copies and MMAs land before TMEM is released
@@ -311,6 +313,202 @@ __device__ __forceinline__ void tc2_tile_body(int mp, int r0, int c0, float* __r
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tbase, 256);
+}
+
+// ---------------------------------------------------------------------------
+// Row-pair tile for the interior of the trailing update: two vertically adjacent
+// 128 x 128 complex tiles (rows r0 .. r0 + 256, columns c0 .. c0 + 128) share each
+// B' chunk, so a CTA brings 2 A' + 1 B' chunk per K step into shared memory for
+// two tiles of output (256 KB of operands per 128 x 128 tile instead of 384 KB; the
+// operand stream through L2 is what bounds the single-tile kernel).  Two MMAs per
+// K step (M = 128 each, N = 256) into two accumulators of 256 TMEM columns.  The
+// epilogue runs half by half: C rows staged in the freed operand ring with bulk
+// copies, D subtracted, rows written back with bulk copies; the second half reuses
+// the ring once the first half's stores have read it.  A missing second half (odd
+// tile count) is neither loaded nor computed.  Every wait is bounded.
+// ---------------------------------------------------------------------------
+constexpr int T2P_STAGES = 6;
+
+template <int KIND>
+struct Tc2p {
+    static constexpr int STAGE = 2 * Tc2<KIND>::A_CHUNK + Tc2<KIND>::B_CHUNK;
+    static constexpr int SMEM = T2P_STAGES * STAGE;
+    static_assert(SMEM >= 2 * T2_C_BYTES, "a half tile of C must fit the freed operand ring");
+};
+
+template <int KIND>
+__device__ __forceinline__ void tc2_pair_body(int mp, int r0, int c0, bool two, float* __restrict__ re_plane,
+                                              const unsigned char* __restrict__ ga0,
+                                              const unsigned char* __restrict__ ga1,
+                                              const unsigned char* __restrict__ gb, int* __restrict__ err) {
+    using Cfg = Tc2<KIND>;
+    using Pc = Tc2p<KIND>;
+    constexpr int NS = T2P_STAGES;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* sCr = smem;
+    unsigned char* sCi = smem + T2_C_BYTES;
+    __shared__ __align__(8) uint64_t bar_c, bar_mma, bar_full[NS], bar_empty[NS];
+    __shared__ uint32_t tmem_base;
+    __shared__ int ok_flag;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ncols = min(T2_BN, mp - c0);  // multiple of 64
+    const uint32_t row_bytes = (uint32_t)ncols * 4;
+    const int nrow0 = min(T2_BM, mp - r0);
+    const int nrow1 = two ? min(T2_BM, mp - r0 - T2_BM) : 0;
+    float* gre = re_plane;
+    float* gim = re_plane + (size_t)mp * mp;
+    const uint32_t stage_tx = (uint32_t)((two ? 2 : 1) * Cfg::A_CHUNK + Cfg::B_CHUNK);
+
+    if (warp == 0) tc::tmem_alloc(&tmem_base, 512);
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&bar_c, 1);
+        tc::mbar_init(&bar_mma, 1);
+        for (int st = 0; st < NS; ++st) {
+            tc::mbar_init(&bar_full[st], 1);
+            tc::mbar_init(&bar_empty[st], 1);
+        }
+        tc::fence_barrier_init();
+        ok_flag = 1;
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tbase = tmem_base;
+    {  // C rows of both halves towards L2 while the operands stream
+        const int r = threadIdx.x;
+        if (r < nrow0) {
+            bulk_prefetch_l2(gre + (size_t)(r0 + r) * mp + c0, row_bytes);
+            bulk_prefetch_l2(gim + (size_t)(r0 + r) * mp + c0, row_bytes);
+        }
+        if (r < nrow1) {
+            bulk_prefetch_l2(gre + (size_t)(r0 + T2_BM + r) * mp + c0, row_bytes);
+            bulk_prefetch_l2(gim + (size_t)(r0 + T2_BM + r) * mp + c0, row_bytes);
+        }
+    }
+    if (threadIdx.x == 0) {
+        auto load_chunk = [&](int c) {
+            const int st = c % NS;
+            unsigned char* sa = smem + st * Pc::STAGE;
+            tc::mbar_arrive_expect_tx(&bar_full[st], stage_tx);
+            tc::bulk_g2s(sa, ga0 + (size_t)c * Cfg::A_CHUNK, Cfg::A_CHUNK, &bar_full[st]);
+            if (two) tc::bulk_g2s(sa + Cfg::A_CHUNK, ga1 + (size_t)c * Cfg::A_CHUNK, Cfg::A_CHUNK, &bar_full[st]);
+            tc::bulk_g2s(sa + 2 * Cfg::A_CHUNK, gb + (size_t)c * Cfg::B_CHUNK, Cfg::B_CHUNK, &bar_full[st]);
+        };
+        for (int c = 0; c < NS - 1 && c < Cfg::NCH; ++c) load_chunk(c);
+        bool ok = true;
+        for (int c = 0; c < Cfg::NCH && ok; ++c) {
+            const int st = c % NS;
+            if (!tc::mbar_wait(&bar_full[st], (c / NS) & 1)) {
+                ok = false;
+                break;
+            }
+            const uint32_t a0 = tc::smem_u32(smem + st * Pc::STAGE);
+            const uint32_t a1 = a0 + Cfg::A_CHUNK;
+            const uint32_t b0 = a0 + 2 * Cfg::A_CHUNK;
+#pragma unroll
+            for (int j = 0; j < Cfg::MMAS; ++j) {
+                const uint64_t bd = tc::smem_desc(b0 + j * 256, 128, 512);
+                const uint64_t ad0 = tc::smem_desc(a0 + j * 256, 128, 512);
+                const uint32_t acc = (c > 0 || j > 0) ? 1u : 0u;
+                if (KIND == 1)
+                    tc::mma_f16(tbase, ad0, bd, Cfg::IDESC, acc);
+                else
+                    tc::mma_tf32(tbase, ad0, bd, Cfg::IDESC, acc);
+                if (two) {
+                    const uint64_t ad1 = tc::smem_desc(a1 + j * 256, 128, 512);
+                    if (KIND == 1)
+                        tc::mma_f16(tbase + 2u * T2_BN, ad1, bd, Cfg::IDESC, acc);
+                    else
+                        tc::mma_tf32(tbase + 2u * T2_BN, ad1, bd, Cfg::IDESC, acc);
+                }
+            }
+            tc::mma_commit(&bar_empty[st]);
+            const int nxt = c + NS - 1;
+            if (nxt < Cfg::NCH) {
+                if (c >= 1) {
+                    const int sp = (c - 1) % NS;
+                    if (!tc::mbar_wait(&bar_empty[sp], ((c - 1) / NS) & 1)) {
+                        ok = false;
+                        break;
+                    }
+                }
+                load_chunk(nxt);
+            }
+        }
+        tc::mma_commit(&bar_mma);  // tracks every MMA issued, also after a failed wait
+        if (!ok) {
+            ok_flag = 0;
+            atomicCAS(err, 0, 1);
+        }
+    }
+    __syncthreads();
+    const bool ok = ok_flag != 0;
+    bool mine = false;
+    if (ok) {
+        mine = tc::mbar_wait(&bar_mma, 0);
+        if (!mine && lane == 0) atomicCAS(err, 0, 2);
+    }
+    bool done = __syncthreads_and(mine) != 0;
+    tc::fence_after_sync();
+    bool staged = false;   // C copies of the current half in flight
+    uint32_t cphase = 0;   // bar_c phase of the current half
+    for (int h = 0; h < 2 && ok && done; ++h) {
+        const int nrows = h == 0 ? nrow0 : nrow1;
+        if (nrows <= 0) break;
+        const int rh = r0 + h * T2_BM;
+        if (threadIdx.x == 0) tc::mbar_arrive_expect_tx(&bar_c, 2u * (uint32_t)nrows * row_bytes);
+        __syncthreads();
+        const int r = threadIdx.x;
+        if (r < nrows) {
+            tc::bulk_g2s(sCr + r * T2_CROW, gre + (size_t)(rh + r) * mp + c0, row_bytes, &bar_c);
+            tc::bulk_g2s(sCi + r * T2_CROW, gim + (size_t)(rh + r) * mp + c0, row_bytes, &bar_c);
+        }
+        staged = true;
+        const bool cok = tc::mbar_wait(&bar_c, cphase);
+        if (!cok && lane == 0) atomicCAS(err, 0, 2);
+        done = __syncthreads_and(cok) != 0;
+        if (!done) break;
+        staged = false;
+        cphase ^= 1u;
+        const uint32_t lane_addr = tbase + (uint32_t)h * 2u * T2_BN + ((uint32_t)(warp * 32) << 16);
+        float4* cr = reinterpret_cast<float4*>(sCr + r * T2_CROW);
+        float4* ci = reinterpret_cast<float4*>(sCi + r * T2_CROW);
+#pragma unroll 1
+        for (int ch = 0; ch < T2_BN / 16; ++ch) {
+            float dr[16], di[16];
+            tc::tmem_ld16(lane_addr + ch * 16, dr);
+            tc::tmem_ld16(lane_addr + T2_BN + ch * 16, di);
+            tc::tmem_ld_wait();
+            if (ch * 16 < ncols) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    float4 a = cr[ch * 4 + q], b = ci[ch * 4 + q];
+                    a.x -= dr[4 * q]; a.y -= dr[4 * q + 1]; a.z -= dr[4 * q + 2]; a.w -= dr[4 * q + 3];
+                    b.x -= di[4 * q]; b.y -= di[4 * q + 1]; b.z -= di[4 * q + 2]; b.w -= di[4 * q + 3];
+                    cr[ch * 4 + q] = a;
+                    ci[ch * 4 + q] = b;
+                }
+            }
+        }
+        fence_async_shared();
+        __syncthreads();
+        if (r < nrows) {
+            bulk_s2g(gre + (size_t)(rh + r) * mp + c0, sCr + r * T2_CROW, row_bytes);
+            bulk_s2g(gim + (size_t)(rh + r) * mp + c0, sCi + r * T2_CROW, row_bytes);
+            bulk_commit();
+            bulk_wait_read_all();  // the next half reuses the buffer
+        }
+        __syncthreads();
+    }
+    if (!(ok && done)) {
+        // bounded: let in-flight copies and MMAs land before TMEM is released
+        if (staged) tc::mbar_wait(&bar_c, cphase);
+        tc::mbar_wait(&bar_mma, 0);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tbase, 512);
 }
 
 // Outer trailing update of tile (ti, tj): C[R0 + 128 ti.., R0 + 128 tj..] -= D.
