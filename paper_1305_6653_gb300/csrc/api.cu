@@ -160,19 +160,14 @@ static bool formula(int family, int mu, int ell, double* a, double* b) {
 // ---------------------------------------------------------------------------
 template <typename T>
 static int dalloc(T** p, size_t count) {
-    *p = nullptr;
-    if (count == 0) return FDE_OK;
-    cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
-    if (e != cudaSuccess) {
-        *p = nullptr;
-        return set_error(FDE_ERR_ALLOC, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
-    }
-    return FDE_OK;
+    void* q = nullptr;
+    const int rc = dev_alloc(&q, count * sizeof(T));
+    *p = static_cast<T*>(q);
+    return rc;
 }
 
-static void dfree(void* p) {
-    if (p) cudaFree(p);
-}
+// The caller makes sure that no queued GPU work still uses p.
+static void dfree(void* p) { dev_free(p); }
 
 static void free_workspace(Problem& P) {
     dfree(P.d_V); dfree(P.d_Z); dfree(P.d_H); dfree(P.d_cs); dfree(P.d_sn); dfree(P.d_gv); dfree(P.d_y);
@@ -182,6 +177,7 @@ static void free_workspace(Problem& P) {
 
 int ensure_workspace(Problem& P, int restart) {
     if (P.restart_cap >= restart) return FDE_OK;
+    if (P.d_V) FDE_CUDA_TRY(cudaStreamSynchronize(P.stream));
     free_workspace(P);
     int rc;
     if ((rc = dalloc(&P.d_V, (size_t)(restart + 1) * P.n))) return rc;
@@ -202,6 +198,7 @@ int ensure_factor_buffers(Problem& P, int precision) {
     const size_t fac_bytes = (size_t)P.nblk * 2 * P.mp * P.mp * esz;
     int rc;
     if (P.d_fac && P.fac_bytes != fac_bytes) {
+        FDE_CUDA_TRY(cudaStreamSynchronize(P.stream));
         dfree(P.d_fac); dfree(P.d_dinv); dfree(P.d_rhat);
         P.d_fac = P.d_dinv = P.d_rhat = nullptr;
         P.fac_bytes = 0;
@@ -591,6 +588,7 @@ int bccb_precond_setup(fde_problem* h, int modified, int precision) {
         if ((rc = dalloc(&P.d_bccb_K32, (size_t)nk * P.L))) return rc;
     }
     if (P.d_rhat_b && P.rhat_b_prec != precision) {
+        FDE_CUDA_TRY(cudaStreamSynchronize(P.stream));
         dfree(P.d_rhat_b);
         P.d_rhat_b = nullptr;
     }

@@ -233,6 +233,11 @@ int launch_bccb_setup(const Problem& P, int modified, double phi0_mod, double* c
                       double2* cinv, double2* K64, float2* K32, int* singular, cudaStream_t st);
 int launch_bccb_solve(const Problem& P, void* rhat, int prec, cudaStream_t st);
 
+// devmem.cu: device buffers through a cache of freed blocks (exact size, per device).
+// dev_free: no queued GPU work may still use the block.
+int dev_alloc(void** p, size_t bytes);
+void dev_free(void* p);
+
 // The problem behind a C-ABI handle (defined in api.cu).
 Problem* problem_of(fde_problem* h);
 int ensure_factor_buffers(Problem& P, int precision);

@@ -1382,10 +1382,14 @@ static int run_lu_tc(Problem& P, cudaStream_t st) {
     const size_t pi = (size_t)Cfg::A_TILE + Cfg::B_TILE;  // L11^{-1} (A') and U11^{-1} (B') per block
     const size_t need = mp > TB ? (size_t)nb * (2 * (pa + pb) + pi) : 0;
     if (need > 0 && P.pack_bytes < need) {
-        if (P.d_pack) cudaFree(P.d_pack);
+        if (P.d_pack) {
+            FDE_CUDA_TRY(cudaStreamSynchronize(st));
+            dev_free(P.d_pack);
+        }
         P.d_pack = nullptr;
         P.pack_bytes = 0;
-        FDE_CUDA_TRY(cudaMalloc(&P.d_pack, need));
+        int arc = dev_alloc(&P.d_pack, need);
+        if (arc) return arc;
         P.pack_bytes = need;
         FDE_CUDA_TRY(cudaMemsetAsync(P.d_pack, 0, need, st));
     }
@@ -1672,10 +1676,14 @@ static int launch_tile_inverse(Problem& P, int prec, cudaStream_t st) {
     const size_t esz = prec == FDE_FP64 ? sizeof(double) : sizeof(float);
     const size_t bytes = (size_t)P.nblk * (P.mp / 32) * 4096 * esz;
     if (P.tinv_bytes < bytes) {
-        if (P.d_tinv) cudaFree(P.d_tinv);
+        if (P.d_tinv) {
+            FDE_CUDA_TRY(cudaStreamSynchronize(st));
+            dev_free(P.d_tinv);
+        }
         P.d_tinv = nullptr;
         P.tinv_bytes = 0;
-        FDE_CUDA_TRY(cudaMalloc(&P.d_tinv, bytes));
+        int arc = dev_alloc(&P.d_tinv, bytes);
+        if (arc) return arc;
         P.tinv_bytes = bytes;
     }
     StageTimer t(P, FDE_STAGE_LU_DIAG);
