@@ -92,6 +92,10 @@ class Problem:
     scheme: str  # key of SCHEMES
     name: str = ""
     meta: dict = field(default_factory=dict)
+    # time-dependent coefficients d+-(x_i, t_n), (s+1, m), or None; when given, dplus /
+    # dminus hold their means over the unknown time levels n = 1..s
+    dplus_t: np.ndarray | None = None
+    dminus_t: np.ndarray | None = None
 
     @property
     def family(self) -> str:
@@ -176,6 +180,26 @@ def manufactured(m: int, s: int, alpha: float, scheme: str,
     return Problem(m=m, s=s, alpha=float(alpha), xL=xL, xR=xR, t0=t0, T=T,
                    dplus=dp, dminus=dm, u0=u0, f=np.ascontiguousarray(f),
                    scheme=scheme, name=name)
+
+
+def manufactured_time_varying(m: int, s: int, alpha: float, scheme: str,
+                              name: str = "manufactured_tv") -> Problem:
+    """As manufactured(), with coefficients that vary in space and time (eq. (1.1)
+    allows d+-(x, t)): d+(x,t) = (1+x)(1 + sin(pi t)/2), d-(x,t) = (2-x)(1 + t/2)."""
+    xL, xR, t0, T = 0.0, 1.0, 0.0, 1.0
+    x = _grid(m, xL, xR)
+    t = t0 + (T - t0) / s * np.arange(s + 1, dtype=np.float64)
+    dpt = (1.0 + x)[None, :] * (1.0 + 0.5 * np.sin(np.pi * t))[:, None]
+    dmt = (2.0 - x)[None, :] * (1.0 + 0.5 * t)[:, None]
+    prof = x ** 2 * (1.0 - x) ** 2
+    left = _rl_profile(x, alpha)
+    right = _rl_profile(1.0 - x, alpha)
+    et = np.exp(-t)[:, None]
+    f = -et * prof[None, :] - et * (dpt * left[None, :] + dmt * right[None, :])
+    return Problem(m=m, s=s, alpha=float(alpha), xL=xL, xR=xR, t0=t0, T=T,
+                   dplus=dpt[1:].mean(axis=0), dminus=dmt[1:].mean(axis=0), u0=prof.copy(),
+                   f=np.ascontiguousarray(f), scheme=scheme, name=name,
+                   dplus_t=np.ascontiguousarray(dpt), dminus_t=np.ascontiguousarray(dmt))
 
 
 def random_modes(m: int, s: int, scheme: str, seed: int, *, random_u0: bool = False,

@@ -88,7 +88,15 @@ typedef struct {
     int mu;         /* number of steps, 1 <= mu <= FDE_MAX_MU (ETR: odd) */
     const double* u0; /* length m: u0(x_i) */
     const double* f;  /* length (s+1)*m, row-major [n][i]: f(x_i, t_n), n = 0..s */
-    int device_ptrs;  /* 0: dplus/dminus/u0/f are host pointers, 1: device pointers */
+    int device_ptrs;  /* 0: dplus/dminus/u0/f/dplus_t/dminus_t are host pointers, 1: device pointers */
+    /* Coefficients that vary in time, d+-(x_i, t_n) (eq. (1.1) allows them): NULL, or
+     * length (s+1)*m, row-major [n][i], n = 0..s.  Both or neither are given; when
+     * given, dplus/dminus/dplus_c/dminus_c are ignored, the matvec applies J_n =
+     * dx^-alpha (D+(t_n) G + D-(t_n) G^T) at each time level (the BVM on
+     * u' = J(t) u + f), and the Strang / BCCB preconditioners use the means of d+-
+     * over n = 1..s.  Not supported by fde_batch_create (FDE_ERR_ARG). */
+    const double* dplus_t;
+    const double* dminus_t;
 } fde_problem_desc;
 
 /* Options of pgmres_solve. */

@@ -58,6 +58,8 @@ __all__ = [
     "j_matrix",
     "j_of",
     "j_matrix_from_g",
+    "time_varying",
+    "j_at",
     "nu_of",
     "lmf_coefficients",
     "bvm_matrices",
@@ -141,9 +143,26 @@ def j_matrix_from_g(alpha: float, dx: float, dplus: np.ndarray, dminus: np.ndarr
 
 
 def j_of(prob) -> np.ndarray:
+    """J of eq. (1.4)/(1.5) with the problem's d+, d- (for time-dependent coefficients:
+    their means over the unknown time levels, the J of the Strang preconditioner)."""
     if prob.m <= 160:
         return j_matrix(prob.alpha, prob.dx, prob.dplus, prob.dminus)
     return j_matrix_from_g(prob.alpha, prob.dx, prob.dplus, prob.dminus)
+
+
+def time_varying(prob) -> bool:
+    return getattr(prob, "dplus_t", None) is not None
+
+
+def j_at(prob, n: int) -> np.ndarray:
+    """J_n = dx^-alpha (D+(t_n) G + D-(t_n) G^T): eq. (1.4) at time level n, for
+    coefficients d+-(x, t) (eq. (1.1)); the time-independent J otherwise."""
+    if not time_varying(prob):
+        return j_of(prob)
+    dp, dm = prob.dplus_t[n], prob.dminus_t[n]
+    if prob.m <= 160:
+        return j_matrix(prob.alpha, prob.dx, dp, dm)
+    return j_matrix_from_g(prob.alpha, prob.dx, dp, dm)
 
 
 # ---------------------------------------------------------------------------
@@ -243,12 +262,21 @@ def bvm_matrices(family: str, mu: int, s: int, exact: bool = False):
 # ---------------------------------------------------------------------------
 
 def full_system(prob):
-    """(A (x) I - h B (x) J) u = e_1 (x) u_0 + h (B (x) I) f, eq. (1.10); size (s+1) m."""
+    """(A (x) I - h B (x) J) u = e_1 (x) u_0 + h (B (x) I) f, eq. (1.10); size (s+1) m.
+
+    With time-dependent coefficients the BVM is applied to u' = J(t) u + f(t): the
+    term B (x) J becomes (B (x) I) blkdiag(J_0, .., J_s)."""
     m, s, h = prob.m, prob.s, prob.h
     A, B = bvm_matrices(prob.family, prob.mu, s)
-    J = j_of(prob)
     I = np.eye(m)
-    M = np.kron(A, I) - h * np.kron(B, J)
+    if time_varying(prob):
+        JB = np.zeros(((s + 1) * m, (s + 1) * m))
+        for n in range(s + 1):
+            JB[n * m:(n + 1) * m, n * m:(n + 1) * m] = j_at(prob, n)
+        M = np.kron(A, I) - h * np.kron(B, I) @ JB
+    else:
+        J = j_of(prob)
+        M = np.kron(A, I) - h * np.kron(B, J)
     e1 = np.zeros(s + 1)
     e1[0] = 1.0
     rhs = np.kron(e1, prob.u0) + h * np.kron(B, I) @ prob.f.reshape(-1)
@@ -269,9 +297,11 @@ def reduced_rhs(prob, J=None) -> np.ndarray:
     """b_red without forming M: b_t = h sum_j B[t,j] f_j - A[t,0] u_0 + h B[t,0] J u_0."""
     h = prob.h
     A, B = bvm_matrices(prob.family, prob.mu, prob.s)
-    if J is None:
-        J = j_of(prob)
-    b = h * (B[1:, :] @ prob.f) - np.outer(A[1:, 0], prob.u0) + h * np.outer(B[1:, 0], J @ prob.u0)
+    if time_varying(prob):
+        J0 = j_at(prob, 0)
+    else:
+        J0 = j_of(prob) if J is None else J
+    b = h * (B[1:, :] @ prob.f) - np.outer(A[1:, 0], prob.u0) + h * np.outer(B[1:, 0], J0 @ prob.u0)
     return b.reshape(-1)
 
 
@@ -283,6 +313,9 @@ def matvec(prob, z: np.ndarray, J=None, AB=None) -> np.ndarray:
         AB = bvm_matrices(prob.family, prob.mu, prob.s)
     A, B = AB
     Z = z.reshape(prob.s, prob.m)
+    if time_varying(prob):  # (A_1 (x) I) z - h (B_1 (x) I) [J_1 z_1; ..; J_s z_s]
+        JZ = np.stack([j_at(prob, n + 1) @ Z[n] for n in range(prob.s)])
+        return (A[1:, 1:] @ Z - prob.h * (B[1:, 1:] @ JZ)).reshape(-1)
     Y = A[1:, 1:] @ Z - prob.h * (B[1:, 1:] @ Z) @ J.T
     return Y.reshape(-1)
 

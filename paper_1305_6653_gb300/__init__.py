@@ -94,7 +94,7 @@ class FDEProblem:
     """
 
     def __init__(self, *, m, s, alpha, xL, xR, t0, T, dplus, dminus, u0, f, family, mu, stream=None,
-                 device_inputs: bool | None = None):
+                 device_inputs: bool | None = None, dplus_t=None, dminus_t=None):
         torch = _torch()
         self.m, self.s = int(m), int(s)
         self.n = self.m * self.s
@@ -118,7 +118,7 @@ class FDEProblem:
             device_inputs = isinstance(u0, torch.Tensor) and u0.is_cuda
         self.desc = FdeProblemDesc(self.m, self.s, float(alpha), float(xL), float(xR), float(t0), float(T),
                                    ptr(dplus), ptr(dminus), 0.0, 0.0, fam, int(mu), ptr(u0), ptr(f),
-                                   1 if device_inputs else 0)
+                                   1 if device_inputs else 0, ptr(dplus_t), ptr(dminus_t))
         self.h = fde_problem_create(self.desc, stream)
         del keep
 
@@ -128,6 +128,8 @@ class FDEProblem:
         torch = _torch()
         fam, mu = prob.family, prob.mu
         arrays = dict(dplus=prob.dplus, dminus=prob.dminus, u0=prob.u0, f=prob.f)
+        if getattr(prob, "dplus_t", None) is not None:
+            arrays.update(dplus_t=prob.dplus_t, dminus_t=prob.dminus_t)
         if device_inputs:
             arrays = {k: torch.as_tensor(v, dtype=torch.float64, device="cuda") for k, v in arrays.items()}
         return cls(m=prob.m, s=prob.s, alpha=prob.alpha, xL=prob.xL, xR=prob.xR, t0=prob.t0, T=prob.T,
@@ -240,6 +242,10 @@ class FDEBatch:
             descs[i] = FdeProblemDesc(p.m, p.s, float(p.alpha), float(p.xL), float(p.xR), float(p.t0), float(p.T),
                                       arrs[0].ctypes.data, arrs[1].ctypes.data, 0.0, 0.0, FAMILIES[p.family],
                                       int(p.mu), arrs[2].ctypes.data, arrs[3].ctypes.data, 0)
+            if getattr(p, "dplus_t", None) is not None:  # rejected by the library: not batched
+                tv = [np.ascontiguousarray(a, dtype=np.float64) for a in (p.dplus_t, p.dminus_t)]
+                self._keep.extend(tv)
+                descs[i].dplus_t, descs[i].dminus_t = tv[0].ctypes.data, tv[1].ctypes.data
         self.h = C.c_void_p()
         _lib.check(_lib.load().fde_batch_create(descs, self.count, _stream_handle(stream), C.byref(self.h)),
                    "fde_batch_create")

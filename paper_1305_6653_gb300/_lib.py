@@ -53,6 +53,7 @@ class FdeProblemDesc(C.Structure):
         ("t0", C.c_double), ("T", C.c_double), ("dplus", C.c_void_p), ("dminus", C.c_void_p),
         ("dplus_c", C.c_double), ("dminus_c", C.c_double), ("family", C.c_int), ("mu", C.c_int),
         ("u0", C.c_void_p), ("f", C.c_void_p), ("device_ptrs", C.c_int),
+        ("dplus_t", C.c_void_p), ("dminus_t", C.c_void_p),
     ]
 
 

@@ -362,7 +362,48 @@ int fde_problem_create(const fde_problem_desc* d, void* stream, fde_problem** ou
         return FDE_OK;
     };
     int rc;
-    if ((rc = fetch(d->dplus, d->dplus_c, dp)) || (rc = fetch(d->dminus, d->dminus_c, dm))) {
+    if ((d->dplus_t == nullptr) != (d->dminus_t == nullptr)) {
+        delete h;
+        return set_error(FDE_ERR_ARG, "give both dplus_t and dminus_t or neither");
+    }
+    P.timevar = d->dplus_t != nullptr;
+    std::vector<double> dpt, dmt;  // time-dependent coefficients, (s+1) x m
+    if (P.timevar) {
+        const size_t cnt = (size_t)(P.s + 1) * m;
+        dpt.resize(cnt);
+        dmt.resize(cnt);
+        for (int w = 0; w < 2; ++w) {
+            const double* src = w == 0 ? d->dplus_t : d->dminus_t;
+            double* dst = w == 0 ? dpt.data() : dmt.data();
+            if (d->device_ptrs) {
+                cudaError_t e = cudaMemcpy(dst, src, cnt * sizeof(double), cudaMemcpyDefault);
+                if (e != cudaSuccess) {
+                    delete h;
+                    return cuda_error(e, "copy of dplus_t/dminus_t");
+                }
+            } else {
+                std::memcpy(dst, src, cnt * sizeof(double));
+            }
+        }
+        for (size_t k = 0; k < cnt; ++k) {
+            if (!(dpt[k] >= 0.0) || !(dmt[k] >= 0.0) || !(dpt[k] + dmt[k] > 0.0) || !std::isfinite(dpt[k]) ||
+                !std::isfinite(dmt[k])) {
+                delete h;
+                return set_error(FDE_ERR_ARG,
+                                 "need d+ >= 0, d- >= 0, d+ + d- != 0 and finite at every point and time level");
+            }
+        }
+        // the preconditioners use the means over the unknown time levels n = 1..s
+        for (size_t i = 0; i < m; ++i) {
+            double sp = 0.0, sm = 0.0;
+            for (int n = 1; n <= P.s; ++n) {
+                sp += dpt[(size_t)n * m + i];
+                sm += dmt[(size_t)n * m + i];
+            }
+            dp[i] = sp / P.s;
+            dm[i] = sm / P.s;
+        }
+    } else if ((rc = fetch(d->dplus, d->dplus_c, dp)) || (rc = fetch(d->dminus, d->dminus_c, dm))) {
         delete h;
         return rc;
     }
@@ -411,6 +452,11 @@ int fde_problem_create(const fde_problem_desc* d, void* stream, fde_problem** ou
     TRY(dalloc(&P.d_counter, 4));
     TRY(dalloc(&P.d_info, (size_t)P.nblk));
     TRY(dalloc(&P.d_err, 1));
+    if (P.timevar) {
+        TRY(dalloc(&P.d_dplus_t, (size_t)(P.s + 1) * m));
+        TRY(dalloc(&P.d_dminus_t, (size_t)(P.s + 1) * m));
+        TRY(dalloc(&P.d_jz, (size_t)P.n));
+    }
     if (cudaMallocHost((void**)&h->pinned, 64 * sizeof(double)) != cudaSuccess) {
         h->pinned = nullptr;
         fde_problem_destroy(h);
@@ -434,6 +480,10 @@ int fde_problem_create(const fde_problem_desc* d, void* stream, fde_problem** ou
     CUTRY(cudaMemcpyAsync(P.d_dminus, dm.data(), m * sizeof(double), cudaMemcpyHostToDevice, st));
     CUTRY(cudaMemcpyAsync(P.d_u0, d->u0, m * sizeof(double), kind, st));
     CUTRY(cudaMemcpyAsync(P.d_f, d->f, (size_t)(P.s + 1) * m * sizeof(double), kind, st));
+    if (P.timevar) {
+        CUTRY(cudaMemcpyAsync(P.d_dplus_t, dpt.data(), dpt.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+        CUTRY(cudaMemcpyAsync(P.d_dminus_t, dmt.data(), dmt.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    }
     CUTRY(cudaMemsetAsync(P.d_counter, 0, 4 * sizeof(unsigned int), st));
     CUTRY(cudaMemsetAsync(P.d_scal, 0, 256 * sizeof(double), st));
     // host vectors go out of scope: wait for the copies
@@ -455,7 +505,8 @@ void fde_problem_destroy(fde_problem* h) {
     void* bufs[] = {P.d_start, P.d_a, P.d_b, P.d_dplus, P.d_dminus, P.d_u0, P.d_f, P.d_g, P.d_twL, P.d_twL32,
                     P.d_sym, P.d_sym32, P.d_tws, P.d_tws32, P.d_phi, P.d_psi, P.d_b_rhs, P.d_work, P.d_rhat,
                     P.d_fac, P.d_dinv, P.d_info, P.d_err, P.d_pack, P.d_tinv, P.d_scal, P.d_partial,
-                    P.d_counter, P.d_bccb_K64, P.d_bccb_K32, P.d_rhat_b};
+                    P.d_counter, P.d_bccb_K64, P.d_bccb_K32, P.d_rhat_b, P.d_dplus_t, P.d_dminus_t,
+                    P.d_jz};
     for (void* b : bufs) dfree(b);
     if (h->pinned) cudaFreeHost(h->pinned);
     for (cudaEvent_t e : P.ev_pool) cudaEventDestroy(e);
@@ -533,7 +584,12 @@ int bvm_assemble(fde_problem* h) {
     cudaFree(d_main);
     if (rc) return rc;
     // J u0 (one Toeplitz-like apply), then b
-    if ((rc = launch_japply64(P, P.d_u0, P.d_work, 1, P.stream))) return rc;
+    // J u_0 (with time-dependent coefficients: J_0, the coefficients of time level 0)
+    if (P.timevar)
+        rc = launch_japply64_d(P, P.d_u0, P.d_work, 1, P.d_dplus_t, P.d_dminus_t, 0, P.stream);
+    else
+        rc = launch_japply64(P, P.d_u0, P.d_work, 1, P.stream);
+    if (rc) return rc;
     if ((rc = launch_rhs(P, P.d_work, P.stream))) return rc;
     FDE_CUDA_TRY(cudaGetLastError());
     P.assembled = true;

@@ -89,6 +89,11 @@ int fde_batch_create(const fde_problem_desc* descs, int count, void* stream, fde
     if (!b) return set_error(FDE_ERR_ALLOC, "host allocation failed");
     b->stream = (cudaStream_t)stream;
     for (int i = 0; i < count; ++i) {
+        if (descs[i].dplus_t || descs[i].dminus_t) {
+            fde_batch_destroy(b);
+            return set_error(FDE_ERR_ARG, std::string("instance ") + std::to_string(i) +
+                                              ": time-dependent coefficients are not batched");
+        }
         fde_problem* p = nullptr;
         int rc = fde_problem_create(&descs[i], stream, &p);
         if (rc) {

@@ -112,6 +112,9 @@ int launch_rhs(const Problem& P, const double* Ju0, cudaStream_t st);
 // matvec.cu: y = M z (mode 0) or y = J z for ncols columns (mode 1)
 int launch_matvec64(const Problem& P, const double* z, double* y, cudaStream_t st);
 int launch_japply64(const Problem& P, const double* z, double* y, int ncols, cudaStream_t st);
+// J_n z for ncols columns with per-column coefficients dplus + c*dstride (dstride 0: shared)
+int launch_japply64_d(const Problem& P, const double* z, double* y, int ncols, const double* dplus,
+                      const double* dminus, int dstride, cudaStream_t st);
 
 // timefft.cu
 int launch_time_fft_fwd(const Problem& P, const double* r, void* rhat, int prec, cudaStream_t st);
@@ -159,8 +162,12 @@ struct Problem {
     int* d_start = nullptr;
     double* d_a = nullptr;      // (s+1)*(mu+1)
     double* d_b = nullptr;
-    double* d_dplus = nullptr;  // m
+    double* d_dplus = nullptr;  // m (time-dependent coefficients: their means over n = 1..s)
     double* d_dminus = nullptr; // m
+    bool timevar = false;        // d+-(x, t) given
+    double* d_dplus_t = nullptr;  // (s+1)*m, [n][i], when timevar
+    double* d_dminus_t = nullptr;
+    double* d_jz = nullptr;       // n: J_n z_n of the time-dependent matvec
     double* d_u0 = nullptr;     // m
     double* d_f = nullptr;      // (s+1)*m
     double* d_g = nullptr;      // m+2 Grunwald weights

@@ -19,7 +19,8 @@ __device__ __forceinline__ void matvec_body(int m, int logL, int mu, double h, c
                                             const double* __restrict__ A, const double* __restrict__ B,
                                             const double* __restrict__ dplus, const double* __restrict__ dminus,
                                             const cplx_t<T>* __restrict__ sym, const cplx_t<T>* __restrict__ tw,
-                                            const double* __restrict__ z, double* __restrict__ y, int row) {
+                                            const double* __restrict__ z, double* __restrict__ y, int row,
+                                            int dstride = 0) {
     static_assert(sizeof(T) == 8, "the Toeplitz apply runs in FP64");
     using C = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -89,9 +90,11 @@ __device__ __forceinline__ void matvec_body(int m, int logL, int mu, double h, c
     }
     __syncthreads();
     fft_dif4<true>(buf, logL, tw, 1);
+    const double* dp = dplus + (size_t)row * dstride;  // MODE 1 with per-column coefficients
+    const double* dm = dminus + (size_t)row * dstride;
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
         const C wv = buf[bitrev(i, logL)];
-        const double jz = dplus[i] * (double)wv.x + dminus[i] * (double)wv.y;
+        const double jz = dp[i] * (double)wv.x + dm[i] * (double)wv.y;
         if (MODE == 0)
             y[(size_t)row * m + i] = ubuf[i] - h * jz;
         else
@@ -104,8 +107,30 @@ __global__ void __launch_bounds__(1024)
 st_matvec_kernel(int m, int logL, int mu, double h, const int* __restrict__ start, const double* __restrict__ A,
                  const double* __restrict__ B, const double* __restrict__ dplus, const double* __restrict__ dminus,
                  const cplx_t<T>* __restrict__ sym, const cplx_t<T>* __restrict__ tw, const double* __restrict__ z,
-                 double* __restrict__ y) {
-    matvec_body<T, MODE>(m, logL, mu, h, start, A, B, dplus, dminus, sym, tw, z, y, blockIdx.x);
+                 double* __restrict__ y, int dstride) {
+    matvec_body<T, MODE>(m, logL, mu, h, start, A, B, dplus, dminus, sym, tw, z, y, blockIdx.x, dstride);
+}
+
+// Time-dependent coefficients: y_n = sum_q a_{n,q} z_q - h sum_q b_{n,q} (J_q z_q) over the
+// BVM band of row n (u_0 eliminated), with jz = [J_1 z_1; ..; J_s z_s] from the Toeplitz
+// apply; one CTA per time row, threads along x.
+__global__ void __launch_bounds__(256)
+st_band_kernel(int m, int mu, double h, const int* __restrict__ start, const double* __restrict__ A,
+               const double* __restrict__ B, const double* __restrict__ z, const double* __restrict__ jz,
+               double* __restrict__ y) {
+    const int row = blockIdx.x, t = row + 1;
+    const int st = start[t];
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        double u = 0.0, w = 0.0;
+        for (int q = 0; q <= mu; ++q) {
+            const int col = st + q;  // full-system time index; column 0 (u_0) is eliminated
+            if (col >= 1) {
+                u += A[(size_t)t * (mu + 1) + q] * z[(size_t)(col - 1) * m + i];
+                w += B[(size_t)t * (mu + 1) + q] * jz[(size_t)(col - 1) * m + i];
+            }
+        }
+        y[(size_t)row * m + i] = u - h * w;
+    }
 }
 
 // Batched M z over the active instances: grid (max s, active count).
@@ -134,7 +159,8 @@ int launch_matvec_batched(const InstDev* I, const int* act, int nact, int max_s,
 }
 
 template <int MODE>
-static int launch_st(const Problem& P, const double* z, double* y, int ncols, cudaStream_t st) {
+static int launch_st(const Problem& P, const double* z, double* y, int ncols, cudaStream_t st,
+                     const double* dplus = nullptr, const double* dminus = nullptr, int dstride = 0) {
     const int L = P.L;
     size_t smem = (size_t)L * sizeof(double2) + (MODE == 0 ? (size_t)P.m * sizeof(double) : 0);
     int threads = L / 2;
@@ -142,18 +168,30 @@ static int launch_st(const Problem& P, const double* z, double* y, int ncols, cu
     if (threads < 64) threads = 64;
     auto kern = st_matvec_kernel<double, MODE>;
     FDE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-    kern<<<ncols, threads, smem, st>>>(P.m, P.logL, P.mu, P.h, P.d_start, P.d_a, P.d_b, P.d_dplus, P.d_dminus,
-                                       P.d_sym, P.d_twL, z, y);
+    kern<<<ncols, threads, smem, st>>>(P.m, P.logL, P.mu, P.h, P.d_start, P.d_a, P.d_b,
+                                       dplus ? dplus : P.d_dplus, dminus ? dminus : P.d_dminus, P.d_sym, P.d_twL,
+                                       z, y, dstride);
     FDE_LAUNCH_CHECK("st_matvec_kernel");
     return FDE_OK;
 }
 
 int launch_matvec64(const Problem& P, const double* z, double* y, cudaStream_t st) {
-    return launch_st<0>(P, z, y, P.s, st);
+    if (!P.timevar) return launch_st<0>(P, z, y, P.s, st);
+    // J_q z_q for q = 1..s with the coefficients of time level q, then the BVM band
+    int rc = launch_st<1>(P, z, P.d_jz, P.s, st, P.d_dplus_t + P.m, P.d_dminus_t + P.m, P.m);
+    if (rc) return rc;
+    st_band_kernel<<<P.s, 256, 0, st>>>(P.m, P.mu, P.h, P.d_start, P.d_a, P.d_b, z, P.d_jz, y);
+    FDE_LAUNCH_CHECK("st_band_kernel");
+    return FDE_OK;
 }
 
 int launch_japply64(const Problem& P, const double* z, double* y, int ncols, cudaStream_t st) {
     return launch_st<1>(P, z, y, ncols, st);
+}
+
+int launch_japply64_d(const Problem& P, const double* z, double* y, int ncols, const double* dplus,
+                      const double* dminus, int dstride, cudaStream_t st) {
+    return launch_st<1>(P, z, y, ncols, st, dplus, dminus, dstride);
 }
 
 }  // namespace fde

@@ -45,8 +45,10 @@ def test_binding_lists_every_declared_symbol():
 
 def test_struct_layouts_match_header():
     from paper_1305_6653_gb300 import _lib
-    # fde_problem_desc: 2 ints, 5 doubles, 2 pointers, 2 doubles, 2 ints, 2 pointers, 1 int (+ padding)
-    assert ctypes.sizeof(_lib.FdeProblemDesc) == 8 + 40 + 16 + 16 + 8 + 16 + 8
+    # fde_problem_desc: 2 ints, 5 doubles, 2 pointers, 2 doubles, 2 ints, 2 pointers, 1 int (+ padding),
+    # 2 pointers (time-dependent coefficients)
+    assert ctypes.sizeof(_lib.FdeProblemDesc) == 8 + 40 + 16 + 16 + 8 + 16 + 8 + 16
+    assert _lib.FdeProblemDesc.dplus_t.offset == 112 and _lib.FdeProblemDesc.dminus_t.offset == 120
     assert ctypes.sizeof(_lib.FdePgmresOpts) == 24
     assert ctypes.sizeof(_lib.FdeStats) == 16 + 24 + 8
 
@@ -67,5 +69,12 @@ def test_argument_validation_needs_no_gpu(lib):
     assert L.fde_problem_create(ctypes.byref(d), None, ctypes.byref(h)) == _lib.FDE_ERR_ARG
     d.family, d.mu = 3, 4  # ETR needs odd mu
     assert L.fde_problem_create(ctypes.byref(d), None, ctypes.byref(h)) == _lib.FDE_ERR_ARG
+    d.family, d.mu = 1, 3
+    one = (ctypes.c_double * 1)(1.0)
+    d.u0 = d.f = ctypes.cast(one, ctypes.c_void_p)
+    d.dplus_t = ctypes.cast(one, ctypes.c_void_p)  # d+(x, t) without d-(x, t)
+    assert L.fde_problem_create(ctypes.byref(d), None, ctypes.byref(h)) == _lib.FDE_ERR_ARG
+    assert b"dminus_t" in L.fde_last_error()
+    d.dplus_t = None
     assert L.bvm_assemble(None) == _lib.FDE_ERR_ARG
     assert L.strang_precond_factor(None, 0) == _lib.FDE_ERR_ARG
