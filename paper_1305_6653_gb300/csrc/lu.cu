@@ -797,15 +797,23 @@ lu_update_tc2p_kernel(int mp, int R0, int nt, float* __restrict__ fac, const uns
                         bpack + (size_t)k * pb + (size_t)tj * Cfg::B_TILE, err);
 }
 
+// Batched, in row pairs over every tile of each active block: grid.x = ceil(ntg / 2) * ntg
+// covers the largest block (ntg tiles per dimension); CTA x takes tiles (2p, tj) and
+// (2p + 1, tj), p = x / ntg, tj = x % ntg.
 template <int KIND>
 __global__ void __launch_bounds__(128)
-lu_update_tc2_batched(const BlkDev* __restrict__ B, int R0, int ntg, int* __restrict__ err) {
+lu_update_tc2p_batched(const BlkDev* __restrict__ B, int R0, int ntg, int* __restrict__ err) {
+    using Cfg = Tc2<KIND>;
     const BlkDev& d = B[blockIdx.y];
     if (R0 >= d.mp) return;
     const int nt = (d.mp - R0 + T2_BM - 1) / T2_BM;
-    const int ti = blockIdx.x / ntg, tj = blockIdx.x % ntg;
-    if (ti >= nt || tj >= nt) return;
-    tc2_update_body<KIND>(d.mp, R0, (float*)d.fac, d.apack, d.bpack, err, ti, tj);
+    const int p = blockIdx.x / ntg, tj = blockIdx.x % ntg;
+    const int ti0 = 2 * p;
+    if (ti0 >= nt || tj >= nt) return;
+    const bool two = ti0 + 1 < nt;
+    tc2_pair_body<KIND>(d.mp, R0 + ti0 * T2_BM, R0 + tj * T2_BN, two, (float*)d.fac,
+                        d.apack + (size_t)ti0 * Cfg::A_TILE, d.apack + (size_t)(two ? ti0 + 1 : ti0) * Cfg::A_TILE,
+                        d.bpack + (size_t)tj * Cfg::B_TILE, err);
 }
 
 static inline int cdiv(int a, int b) { return a > 0 ? (a + b - 1) / b : 0; }
@@ -824,9 +832,9 @@ static int set_tc_attrs() {
                                       (int)upd_smem));
     FDE_CUDA_TRY(cudaFuncSetAttribute(lu_update_tc2_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       Tc2<KIND>::SMEM));
-    FDE_CUDA_TRY(cudaFuncSetAttribute(lu_update_tc2_batched<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      Tc2<KIND>::SMEM));
     FDE_CUDA_TRY(cudaFuncSetAttribute(lu_update_tc2p_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      Tc2p<KIND>::SMEM));
+    FDE_CUDA_TRY(cudaFuncSetAttribute(lu_update_tc2p_batched<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       Tc2p<KIND>::SMEM));
     return FDE_OK;
 }
@@ -1553,8 +1561,9 @@ static int run_lu_batched_tc(const BlkDev* d_blk, const std::vector<int>& mps, i
         FDE_LAUNCH_CHECK("lu_panel_tc2_batched");
         lu_pack_panel_batched<KIND><<<dim3(pgrid, nact), 256, 0, st>>>(d_blk, o, R0);
         FDE_LAUNCH_CHECK("lu_pack_panel_batched");
-        lu_update_tc2_batched<KIND><<<dim3(ntg * ntg, nact), 128, Cfg::SMEM, st>>>(d_blk, R0, ntg, err);
-        FDE_LAUNCH_CHECK("lu_update_tc2_batched");
+        lu_update_tc2p_batched<KIND><<<dim3(((ntg + 1) / 2) * ntg, nact), 128, Tc2p<KIND>::SMEM, st>>>(d_blk, R0,
+                                                                                                     ntg, err);
+        FDE_LAUNCH_CHECK("lu_update_tc2p_batched");
     }
     return FDE_OK;
 }
