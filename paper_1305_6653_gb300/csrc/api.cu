@@ -33,6 +33,7 @@ int cuda_error(cudaError_t e, const char* what) {
 // ---------------------------------------------------------------------------
 static std::atomic<long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void note_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 static cudaEvent_t next_event(Problem& P) {
     if (P.ev_used == P.ev_pool.size()) {
@@ -177,6 +178,7 @@ static void free_workspace(Problem& P) {
 
 int ensure_workspace(Problem& P, int restart) {
     if (P.restart_cap >= restart) return FDE_OK;
+    ++P.graph_gen;
     if (P.d_V) FDE_CUDA_TRY(cudaStreamSynchronize(P.stream));
     free_workspace(P);
     int rc;
@@ -198,6 +200,7 @@ int ensure_factor_buffers(Problem& P, int precision) {
     const size_t fac_bytes = (size_t)P.nblk * 2 * P.mp * P.mp * esz;
     int rc;
     if (P.d_fac && P.fac_bytes != fac_bytes) {
+        ++P.graph_gen;
         FDE_CUDA_TRY(cudaStreamSynchronize(P.stream));
         dfree(P.d_fac); dfree(P.d_dinv); dfree(P.d_rhat);
         P.d_fac = P.d_dinv = P.d_rhat = nullptr;
@@ -263,6 +266,92 @@ static int norm2(Problem& P, const double* v, int slot, double* host_out, double
         FDE_CUDA_TRY(cudaStreamSynchronize(P.stream));
         *host_out = *pinned;
     }
+    return FDE_OK;
+}
+
+static void drop_iter_graphs(Problem& P) {
+    for (cudaGraphExec_t g : P.iter_graph)
+        if (g) cudaGraphExecDestroy(g);
+    P.iter_graph.clear();
+    P.iter_graph_launches.clear();
+}
+
+// One inner iteration j of pgmres_solve as a stream of launches: z_j = P^{-1} v_j,
+// w = M z_j, CGS2 against v_0..v_j, Hessenberg column / Givens rotation, w /= |w|.
+static int iteration_launches(Problem& P, int j, int ldh, int reorth) {
+    const long n = P.n;
+    cudaStream_t st = P.stream;
+    double* V = P.d_V;
+    double* sc = P.d_scal;
+    double* vj = V + (size_t)j * n;
+    double* w = V + (size_t)(j + 1) * n;
+    double* zj = P.d_Z + (size_t)j * n;
+    int rc;
+    if ((rc = apply_precond(P, vj, zj))) return rc;
+    if ((rc = matvec(P, zj, w))) return rc;
+    StageTimer kt(P, FDE_STAGE_KRYLOV);
+    // CGS2 in three passes over V: h1 = V^T w; w -= V h1 and h2 = V^T w;
+    // w -= V h2 and |w|^2 (one pass fewer without re-orthogonalisation)
+    if ((rc = launch_cgs_pass(0, V, j + 1, nullptr, w, n, sc, P.d_partial, P.d_counter, st))) return rc;
+    if (reorth) {
+        if ((rc = launch_cgs_pass(1, V, j + 1, sc, w, n, sc + 64, P.d_partial, P.d_counter, st))) return rc;
+    }
+    if ((rc = launch_cgs_pass(2, V, j + 1, reorth ? sc + 64 : sc, w, n, sc + 128, P.d_partial, P.d_counter, st)))
+        return rc;
+    if ((rc = launch_arnoldi_finish(P.d_H, ldh, j, sc, reorth ? sc + 64 : nullptr, sc + 128, P.d_cs, P.d_sn,
+                                    P.d_gv, sc + 129, st)))
+        return rc;
+    return launch_scale(w, sc + 128, w, n, st);
+}
+
+// Run iteration j: replay its CUDA graph or launch the kernels directly.  Graphs are
+// captured only for a problem that is solved again (from its second pgmres_solve on),
+// so a one-shot solve pays no capture; the stage profiler always launches directly.
+static int run_iteration(Problem& P, int j, int ldh, int reorth, int restart) {
+    if (P.prof || P.solves < 1) return iteration_launches(P, j, ldh, reorth);
+    const long long key = ((((long long)P.graph_gen * 8 + P.precond) * 8 + (P.precision + 1)) * 8 +
+                           (P.bccb_precision + 1)) * 128 * 2 + (long long)ldh * 2 + (reorth ? 1 : 0);
+    if (key != P.graph_key) {
+        drop_iter_graphs(P);
+        P.graph_key = key;
+    }
+    if ((int)P.iter_graph.size() < restart) {
+        P.iter_graph.resize(restart, nullptr);
+        P.iter_graph_launches.resize(restart, 0);
+    }
+    if (!P.iter_graph[j]) {
+        if (!P.cap_stream) FDE_CUDA_TRY(cudaStreamCreateWithFlags(&P.cap_stream, cudaStreamNonBlocking));
+        // the capture stream follows the work already queued on P.stream
+        cudaEvent_t fork;
+        FDE_CUDA_TRY(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+        cudaEventRecord(fork, P.stream);
+        cudaStreamWaitEvent(P.cap_stream, fork, 0);
+        cudaEventDestroy(fork);
+        cudaStream_t user = P.stream;
+        P.stream = P.cap_stream;
+        const long long l0 = fde_launch_count();
+        cudaError_t e = cudaStreamBeginCapture(P.cap_stream, cudaStreamCaptureModeRelaxed);
+        int rc = e == cudaSuccess ? iteration_launches(P, j, ldh, reorth) : FDE_OK;
+        cudaGraph_t graph = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(P.cap_stream, &graph);
+        P.stream = user;
+        if (e != cudaSuccess) return cuda_error(e, "cudaStreamBeginCapture");
+        if (rc) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (e2 != cudaSuccess) return cuda_error(e2, "cudaStreamEndCapture");
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_error(e, "cudaGraphInstantiate");
+        P.iter_graph[j] = exec;
+        P.iter_graph_launches[j] = fde_launch_count() - l0;
+        // the launches were counted once while capturing; each replay adds them below
+        note_launches(-P.iter_graph_launches[j]);
+    }
+    FDE_CUDA_TRY(cudaGraphLaunch(P.iter_graph[j], P.stream));
+    note_launches(P.iter_graph_launches[j]);
     return FDE_OK;
 }
 
@@ -514,6 +603,8 @@ void fde_problem_destroy(fde_problem* h) {
         if (e) cudaEventDestroy(e);
     if (P.lu_hi) cudaStreamDestroy(P.lu_hi);
     if (P.lu_lo) cudaStreamDestroy(P.lu_lo);
+    drop_iter_graphs(P);
+    if (P.cap_stream) cudaStreamDestroy(P.cap_stream);
     delete h;
 }
 
@@ -644,6 +735,7 @@ int bccb_precond_setup(fde_problem* h, int modified, int precision) {
         if ((rc = dalloc(&P.d_bccb_K32, (size_t)nk * P.L))) return rc;
     }
     if (P.d_rhat_b && P.rhat_b_prec != precision) {
+        ++P.graph_gen;
         FDE_CUDA_TRY(cudaStreamSynchronize(P.stream));
         dfree(P.d_rhat_b);
         P.d_rhat_b = nullptr;
@@ -842,27 +934,7 @@ int pgmres_solve(fde_problem* h, const fde_pgmres_opts* opts, const double* x0, 
         FDE_CUDA_TRY(cudaMemcpyAsync(P.d_gv, g0.data(), g0.size() * sizeof(double), cudaMemcpyHostToDevice, st));
         int j = 0;
         for (; j < o.restart; ++j) {
-            double* vj = V + (size_t)j * n;
-            double* w = V + (size_t)(j + 1) * n;
-            double* zj = Z + (size_t)j * n;
-            if ((rc = apply_precond(P, vj, zj))) return finish(rc);
-            if ((rc = matvec(P, zj, w))) return finish(rc);
-            StageTimer kt(P, FDE_STAGE_KRYLOV);
-            // CGS2 in three passes over V: h1 = V^T w; w -= V h1 and h2 = V^T w;
-            // w -= V h2 and |w|^2 (one pass fewer without re-orthogonalisation)
-            if ((rc = launch_cgs_pass(0, V, j + 1, nullptr, w, n, sc, P.d_partial, P.d_counter, st)))
-                return finish(rc);
-            if (o.reorth) {
-                if ((rc = launch_cgs_pass(1, V, j + 1, sc, w, n, sc + 64, P.d_partial, P.d_counter, st)))
-                    return finish(rc);
-            }
-            if ((rc = launch_cgs_pass(2, V, j + 1, o.reorth ? sc + 64 : sc, w, n, sc + 128, P.d_partial,
-                                      P.d_counter, st)))
-                return finish(rc);
-            if ((rc = launch_arnoldi_finish(P.d_H, ldh, j, sc, o.reorth ? sc + 64 : nullptr, sc + 128, P.d_cs,
-                                            P.d_sn, P.d_gv, sc + 129, st)))
-                return finish(rc);
-            if ((rc = launch_scale(w, sc + 128, w, n, st))) return finish(rc);
+            if ((rc = run_iteration(P, j, ldh, o.reorth, o.restart))) return finish(rc);
             ++its;
             FDE_CUDA_TRY(cudaMemcpyAsync(pin, sc + 128, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
             FDE_CUDA_TRY(cudaStreamSynchronize(st));
@@ -888,6 +960,7 @@ int pgmres_solve(fde_problem* h, const fde_pgmres_opts* opts, const double* x0, 
         if ((rc = norm2(P, V, 132, &beta2, pin))) return finish(rc);
     }
     S.iterations = its;
+    ++P.solves;
     return finish(status);
 }
 

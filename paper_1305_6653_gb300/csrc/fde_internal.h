@@ -25,6 +25,7 @@ int cuda_error(cudaError_t e, const char* what);
     } while (0)
 
 void note_launch();
+void note_launches(long long k);  // k kernels launched at once (a graph replay; negative: uncount)
 
 #define FDE_LAUNCH_CHECK(what)                               \
     do {                                                     \
@@ -199,6 +200,15 @@ struct Problem {
     float2* d_bccb_K32 = nullptr;
     void* d_rhat_b = nullptr;   // nblk * mp complex (FP64 or FP32 by bccb_precision)
     int rhat_b_prec = -1;
+    // CUDA graphs of the GMRES inner iteration j (preconditioner apply, matvec, Gram-
+    // Schmidt passes, Givens update, normalisation), captured on first use and replayed;
+    // graph_key names the set-up they were captured for (stale graphs are destroyed)
+    cudaStream_t cap_stream = nullptr;
+    std::vector<cudaGraphExec_t> iter_graph;
+    std::vector<long long> iter_graph_launches;  // kernels per replay (launch counter)
+    long long graph_key = -1;
+    int graph_gen = 0;                           // bumped whenever a buffer the graphs use changes
+    int solves = 0;                              // completed pgmres_solve calls
     // tensor-core LU look-ahead: panel chain on lu_hi, interior updates on lu_lo
     cudaStream_t lu_hi = nullptr, lu_lo = nullptr;
     cudaEvent_t lu_ev[3] = {nullptr, nullptr, nullptr};  // fork / cross done / interior done

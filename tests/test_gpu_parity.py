@@ -176,3 +176,24 @@ def test_error_paths():
     with pytest.raises(FdeError) as e:
         FDEProblem.from_inputs(bad)
     assert e.value.code == _lib.FDE_ERR_ARG
+
+
+@pytest.mark.parametrize("precision", ["fp64", "tf32"])
+def test_repeated_solve_replays_graphs(precision):
+    # from its second solve on a problem replays the inner GMRES iteration as captured CUDA
+    # graphs: same iterates, same iteration count, same launch count as direct launches
+    from paper_1305_6653_gb300 import fde_launch_count
+    prob = _variable(255, 64, "GBDF3", 1.7)
+    with _gpu(prob, precision) as p:
+        counts, xs, its = [], [], []
+        for _ in range(3):
+            l0 = fde_launch_count()
+            x, st = p.solve(tol=1e-11, restart=20, maxit=400)
+            torch.cuda.synchronize()
+            counts.append(fde_launch_count() - l0)
+            xs.append(x.cpu().numpy())
+            its.append(st["iterations"])
+    assert its[0] == its[1] == its[2]
+    np.testing.assert_array_equal(xs[1], xs[0])
+    np.testing.assert_array_equal(xs[2], xs[0])
+    assert counts[0] == counts[1] == counts[2], counts
