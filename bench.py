@@ -49,13 +49,15 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
-    ap.add_argument("--config", choices=["scale", "batch", "learned", "precision", "bccb", "example41"],
+    ap.add_argument("--config", choices=["scale", "batch", "learned", "precision", "bccb", "example41", "rhs"],
                     default="scale",
                     help="scale: one m=2047/s=256 instance per step; batch: 64 uneven instances per step; "
                          "learned: train the warm-start operator on m=1023/s=256 solves, then compare guesses; "
                          "precision: m=4095/s=128, alpha=1.9, every preconditioner precision; "
                          "bccb: the scale workload with the Strang-type BCCB preconditioners; "
-                         "example41: every row of Tables 1-2 with the columns I, S, S^(2), S~^(2)")
+                         "example41: every row of Tables 1-2 with the columns I, S, S^(2), S~^(2); "
+                         "rhs: --rhs right-hand sides of the scale operator sharing one factorisation")
+    ap.add_argument("--rhs", type=int, default=16, help="rhs: number of right-hand sides")
     ap.add_argument("--train", type=int, default=4096, help="learned: method-generated training solves")
     ap.add_argument("--epochs", type=int, default=40, help="learned: passes over the training set")
     ap.add_argument("--eval", type=int, default=32, help="learned: held-out instances")
@@ -315,6 +317,85 @@ def bench_batch(args, world, rank, local_rank):
                 "iterations": [s_["iterations"] for s_ in stats],
                 "sequential_single_api": {"value": len(probs) / seq_s, "unit": "solves/s", "seconds": seq_s},
                 "worst_rel_residual_oracle_matvec": worst, "per_step_ms": times}
+        print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------
+# many right-hand sides of the benchmark operator: one factorisation, shared block solves
+# ---------------------------------------------------------------------------
+
+def bench_many_rhs(args, world, rank, local_rank):
+    import numpy as np
+    import torch
+
+    import fde_inputs
+    import paper_1305_6653_gb300 as fde
+
+    torch.cuda.set_device(local_rank)
+    count = args.rhs
+    probs = fde_inputs.config_many_rhs(count=count, m=args.m, s=args.s)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    outs = [torch.empty(p.n, dtype=torch.float64, device="cuda") for p in probs]
+    b = fde.FDEBatch(probs).share_operator()
+
+    def step():
+        b.assemble().factor(args.precision)
+        _, st = b.solve(tol=args.tol, restart=20, maxit=400, outs=outs)
+        return st
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local_rank)
+    if not args.no_clocks:
+        sampler.start()
+    l0 = fde.fde_launch_count()
+    times, stats = [], None
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        stats = step()
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    launches = fde.fde_launch_count() - l0
+    clocks = sampler.stop() if not args.no_clocks else None
+    b.close()
+    ms = sum(times) / len(times)
+    value = world * count / (ms / 1e3)
+    # the same right-hand sides one at a time through the single-problem API (own factors each)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for pr, out in zip(probs, outs):
+        with fde.FDEProblem.from_inputs(pr) as p:
+            p.assemble().factor(args.precision)
+            p.solve(tol=args.tol, restart=20, maxit=400, out=out)
+    e1.record()
+    e1.synchronize()
+    seq_s = e0.elapsed_time(e1) / 1e3
+    import oracle as O
+    J = O.j_of(probs[0])
+    AB = O.bvm_matrices(probs[0].family, probs[0].mu, probs[0].s)
+    worst = 0.0
+    for pr, out in zip(probs[:4], outs[:4]):  # bounded host check
+        xs = out.cpu().numpy()
+        bb = O.reduced_rhs(pr, J=J)
+        worst = max(worst, float(np.linalg.norm(bb - O.matvec(pr, xs, J=J, AB=AB)) / np.linalg.norm(bb)))
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+                "config": {"workload": f"many_rhs{count}_m{args.m}_s{args.s}_gbdf5_alpha1.8_variable_d",
+                           "right_hand_sides": count, "m": args.m, "s": args.s, "precision": args.precision,
+                           "tol_true_residual": args.tol, "restart": 20,
+                           "l2": "flushed (512 MiB write) before every timed step; factors (4.3 GB) exceed L2"},
+                "roofline": None, "gpu_launches": launches, "clocks": clocks,
+                "iterations": [st["iterations"] for st in stats],
+                "sequential_single_api": {"value": count / seq_s, "unit": "solves/s", "seconds": seq_s},
+                "worst_rel_residual_oracle_matvec_first4": worst}
         print(json.dumps(line))
 
 
@@ -633,6 +714,8 @@ def main():
         return bench_batch(args, world, rank, local_rank)
     if args.config == "learned" and args.impl == "ours":
         return bench_learned(args, world, rank, local_rank)
+    if args.config == "rhs" and args.impl == "ours":
+        return bench_many_rhs(args, world, rank, local_rank)
     if args.config == "example41" and args.impl == "ours":
         return bench_example41(args, world, rank, local_rank)
     if args.config == "bccb" and args.impl == "ours":

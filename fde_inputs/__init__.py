@@ -271,6 +271,26 @@ def config_batch(count: int = 64, m_choices=(255, 511, 1023, 2047), s_choices=(6
     return out
 
 
+def config_many_rhs(count: int = 16, m: int = 2047, s: int = 256, base_seed: int = 0) -> list[Problem]:
+    """Many right-hand sides of the benchmark operator (m, s, alpha = 1.8, d+ = 1+x,
+    d- = 2-x, GBDF5): instance r keeps the operator and takes the manufactured source
+    scaled by (1 + r/4) plus a seeded smooth source e^{-ct} sum_j a_j sin(j pi x),
+    and the manufactured u0 scaled by (1 - r/(2 count))."""
+    import dataclasses
+    base = config_scale(m, s)
+    x, t = base.x, base.t
+    modes = np.sin(np.pi * np.outer(x, np.arange(1, 9, dtype=np.float64)))
+    out = []
+    for r in range(count):
+        rng = np.random.default_rng(instance_seed(base_seed + r) + 9_000_000)
+        c = rng.uniform(0.5, 2.0)
+        a = rng.standard_normal(8)
+        f = base.f * (1.0 + 0.25 * r) + np.exp(-c * t)[:, None] * (modes @ a)[None, :]
+        out.append(dataclasses.replace(base, f=np.ascontiguousarray(f), u0=base.u0 * (1.0 - 0.5 * r / count),
+                                       name=f"rhs{r}_m{m}_s{s}", meta={"c": c, "a": a}))
+    return out
+
+
 def config_learned_family(seed: int, m: int = 1023, s: int = 256) -> Problem:
     """Learned-warm-start family member: random alpha, d, u0 and source; 3-step GBDF."""
     return random_modes(m, s, "GBDF3", seed, random_u0=True, name=f"family{seed}")

@@ -210,6 +210,17 @@ int fde_batch_factor(fde_batch* b, int precision);
  * code (each instance's own code is in stats[i].status). */
 int fde_batch_solve(fde_batch* b, const fde_pgmres_opts* opts, double* const* x_out, fde_stats* stats);
 
+/* Declare that every instance has the same operator M and preconditioner (m, s, alpha,
+ * interval, BVM scheme and coefficients d+, d- equal; only u0 and f differ): many
+ * right-hand sides of one problem.  fde_batch_factor then factors the Strang blocks
+ * once (instance 0, through strang_precond_factor) and every instance's block solves
+ * read those factors; the solve kernels of one block index run side by side, so each
+ * factor plane is read from HBM once per iteration for all right-hand sides.  Call after
+ * fde_batch_create and before fde_batch_factor.  Errors: FDE_ERR_ARG (an instance has
+ * another operator), FDE_ERR_STATE, FDE_ERR_CUDA.  (The paper solves one right-hand
+ * side; the factors depend on J, A and B only, Sec. 3.2.) */
+int fde_batch_share_operator(fde_batch* b);
+
 /* Number of instances, and the problem handle of instance i (owned by the
  * batch; usable with the step-level entry points; NULL if out of range). */
 int fde_batch_size(const fde_batch* b);

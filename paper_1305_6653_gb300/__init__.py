@@ -251,6 +251,11 @@ class FDEBatch:
                    "fde_batch_create")
         self._keep = []
 
+    def share_operator(self):
+        """All instances have one operator (only u0 and f differ): factor once, share the factors."""
+        _lib.check(_lib.load().fde_batch_share_operator(self.h), "fde_batch_share_operator")
+        return self
+
     def assemble(self):
         _lib.check(_lib.load().fde_batch_assemble(self.h), "fde_batch_assemble")
         return self

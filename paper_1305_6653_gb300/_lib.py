@@ -37,7 +37,8 @@ EXPORTED = [
     "fde_problem_destroy",
     "fde_last_error", "fde_matvec", "fde_precond_apply", "fde_get_rhs", "fde_get_factor_block",
     "fde_get_grunwald", "fde_problem_sizes", "fde_profile_enable", "fde_profile_read", "fde_launch_count",
-    "fde_precond_apply_noalloc", "fde_batch_create", "fde_batch_assemble", "fde_batch_factor",
+    "fde_precond_apply_noalloc", "fde_batch_create", "fde_batch_share_operator", "fde_batch_assemble",
+    "fde_batch_factor",
     "fde_batch_solve", "fde_batch_size", "fde_batch_problem", "fde_batch_destroy",
     "fde_nop_create", "fde_nop_num_params", "fde_nop_in_channels", "fde_nop_set_params", "fde_nop_get_params",
     "fde_nop_forward", "fde_nop_loss_grad", "fde_nop_adam_step", "fde_nop_features", "fde_nop_warm_start",
@@ -113,6 +114,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "fde_batch_create": (i32, [C.POINTER(FdeProblemDesc), i32, vp, C.POINTER(vp)]),
         "fde_batch_assemble": (i32, [vp]),
         "fde_batch_factor": (i32, [vp, i32]),
+        "fde_batch_share_operator": (i32, [vp]),
         "fde_batch_solve": (i32, [vp, C.POINTER(FdePgmresOpts), C.POINTER(vp), C.POINTER(FdeStats)]),
         "fde_batch_size": (i32, [vp]),
         "fde_batch_problem": (vp, [vp, i32]),

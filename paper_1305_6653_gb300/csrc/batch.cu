@@ -43,6 +43,11 @@ struct fde_batch {
     size_t pack_bytes = 0;
     int max_mp = 0, max_s = 0, max_L = 0, max_m = 0, max_nblk = 0;
     long max_n = 0;
+    // many right-hand sides of one operator (fde_batch_share_operator): instance 0
+    // holds the only factors; every instance solves against them with its own
+    // frequency-side vectors
+    bool shared = false;
+    void* d_rhat_shared = nullptr;  // count * nblk * mp complex FP32
 };
 
 namespace {
@@ -73,7 +78,8 @@ void fde_batch_destroy(fde_batch* b) {
     if (b->stream) cudaStreamSynchronize(b->stream);
     else cudaDeviceSynchronize();
     for (fde_problem* p : b->probs) fde_problem_destroy(p);
-    void* dev[] = {b->d_blk, b->d_inst, b->d_act, b->d_kvec, b->d_err, b->d_gather, b->d_pack};
+    void* dev[] = {b->d_blk, b->d_inst, b->d_act, b->d_kvec, b->d_err, b->d_gather, b->d_pack,
+                   b->d_rhat_shared};
     for (void* d : dev)
         if (d) cudaFree(d);
     if (b->h_gather) cudaFreeHost(b->h_gather);
@@ -126,6 +132,29 @@ int fde_batch_create(const fde_problem_desc* descs, int count, void* stream, fde
     return FDE_OK;
 }
 
+int fde_batch_share_operator(fde_batch* b) {
+    if (!b) return set_error(FDE_ERR_ARG, "NULL batch");
+    if (b->factored) return set_error(FDE_ERR_STATE, "fde_batch_share_operator must run before fde_batch_factor");
+    const Problem& P0 = *problem_of(b->probs[0]);
+    std::vector<double> d0(2 * (size_t)P0.m), di(2 * (size_t)P0.m);
+    FDE_CUDA_TRY(cudaMemcpy(d0.data(), P0.d_dplus, P0.m * sizeof(double), cudaMemcpyDeviceToHost));
+    FDE_CUDA_TRY(cudaMemcpy(d0.data() + P0.m, P0.d_dminus, P0.m * sizeof(double), cudaMemcpyDeviceToHost));
+    for (size_t i = 1; i < b->probs.size(); ++i) {
+        const Problem& P = *problem_of(b->probs[i]);
+        const bool same = P.m == P0.m && P.s == P0.s && P.mu == P0.mu && P.family == P0.family &&
+                          P.alpha == P0.alpha && P.xL == P0.xL && P.xR == P0.xR && P.t0 == P0.t0 && P.T == P0.T;
+        if (!same)
+            return set_error(FDE_ERR_ARG, "instance " + std::to_string(i) + " has another operator (m, s, alpha, "
+                                          "interval or BVM scheme)");
+        FDE_CUDA_TRY(cudaMemcpy(di.data(), P.d_dplus, P.m * sizeof(double), cudaMemcpyDeviceToHost));
+        FDE_CUDA_TRY(cudaMemcpy(di.data() + P.m, P.d_dminus, P.m * sizeof(double), cudaMemcpyDeviceToHost));
+        if (di != d0)
+            return set_error(FDE_ERR_ARG, "instance " + std::to_string(i) + " has other coefficients d+, d-");
+    }
+    b->shared = true;
+    return FDE_OK;
+}
+
 int fde_batch_size(const fde_batch* b) { return b ? (int)b->probs.size() : 0; }
 
 fde_problem* fde_batch_problem(fde_batch* b, int i) {
@@ -148,6 +177,22 @@ int fde_batch_factor(fde_batch* b, int precision) {
     if (!b->assembled) return set_error(FDE_ERR_STATE, "fde_batch_assemble must run first");
     if (precision != FDE_FP32 && precision != FDE_TF32 && precision != FDE_BF16 && precision != FDE_TF32X3)
         return set_error(FDE_ERR_ARG, "batched factorisation supports FDE_FP32, FDE_TF32, FDE_BF16 and FDE_TF32X3");
+    if (b->shared) {
+        // one factorisation (the single-problem path: look-ahead tensor-core LU), used by all
+        int rc = strang_precond_factor(b->probs[0], precision);
+        if (rc) return rc;
+        const Problem& P0 = *problem_of(b->probs[0]);
+        const size_t per = (size_t)P0.nblk * P0.mp * 2 * sizeof(float);
+        if (!b->d_rhat_shared) FDE_CUDA_TRY(cudaMalloc(&b->d_rhat_shared, per * b->probs.size()));
+        FDE_CUDA_TRY(cudaMemsetAsync(b->d_rhat_shared, 0, per * b->probs.size(), b->stream));
+        for (fde_problem* p : b->probs) {
+            problem_of(p)->factored = true;
+            problem_of(p)->precision = precision;
+        }
+        b->precision = precision;
+        b->factored = true;
+        return FDE_OK;
+    }
     const int kind = precision == FDE_FP32 ? -1 : 0;  // >= 0: tensor-core path with packed operands
     // buffers and the block table
     std::vector<BlkDev> blks;
@@ -259,7 +304,14 @@ int fde_batch_solve(fde_batch* b, const fde_pgmres_opts* opts, double* const* x_
         d.nblk = P.nblk; d.n = P.n; d.h = P.h; d.dxa = P.dxa;
         d.start = P.d_start; d.A = P.d_a; d.B = P.d_b; d.dplus = P.d_dplus; d.dminus = P.d_dminus;
         d.sym = P.d_sym; d.twL = P.d_twL; d.tws32 = P.d_tws32; d.tws = P.d_tws;
-        d.rhat = P.d_rhat; d.fac = P.d_fac; d.dinv = P.d_dinv;
+        if (b->shared) {  // the factors of instance 0, frequency vectors of its own
+            const Problem& P0 = *problem_of(b->probs[0]);
+            d.fac = P0.d_fac;
+            d.dinv = P0.d_dinv;
+            d.rhat = (unsigned char*)b->d_rhat_shared + (size_t)i * P0.nblk * P0.mp * 2 * sizeof(float);
+        } else {
+            d.rhat = P.d_rhat; d.fac = P.d_fac; d.dinv = P.d_dinv;
+        }
         d.b = P.d_b_rhs; d.x = x_out[i]; d.V = P.d_V; d.Z = P.d_Z; d.work = P.d_work; d.H = P.d_H;
         d.cs = P.d_cs; d.sn = P.d_sn; d.gv = P.d_gv; d.y = P.d_y; d.scal = P.d_scal;
         d.partial = P.d_partial; d.counter = P.d_counter;

@@ -700,12 +700,15 @@ block_trsv_kernel(int mp, const T* __restrict__ fac, const cplx_t<T>* __restrict
                        tinv + (size_t)k * (mp / 32) * 4096, rhat + (size_t)k * mp);
 }
 
-// Batched over the active instances act[0..gridDim.y): block k = blockIdx.x of instance act[blockIdx.y].
+// Batched over the active instances act[0..gridDim.x): block k = blockIdx.y of instance act[blockIdx.x].
+// The instance index runs fastest, so the CTAs of one block index are scheduled together:
+// when the instances share their factors (many right-hand sides of one operator) they
+// stream the same factor planes at the same time and HBM serves them once, through L2.
 template <typename T>
 __global__ void __launch_bounds__(TRSV_THREADS)
 block_trsv_batched(const InstDev* __restrict__ I, const int* __restrict__ act) {
-    const InstDev& d = I[act[blockIdx.y]];
-    const int k = blockIdx.x;
+    const InstDev& d = I[act[blockIdx.x]];
+    const int k = blockIdx.y;
     if (k >= d.nblk) return;
     const size_t mp = d.mp;
     trsv_body<T, false>(d.mp, (const T*)d.fac + (size_t)k * 2 * mp * mp, (const cplx_t<T>*)d.dinv + (size_t)k * mp,
@@ -1607,7 +1610,7 @@ int launch_trsv_batched(const InstDev* I, const int* act, int nact, int max_nblk
     const size_t smem = trsv_smem_bytes(max_mp, sizeof(float));
     FDE_CUDA_TRY(cudaFuncSetAttribute(block_trsv_batched<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
-    block_trsv_batched<float><<<dim3(max_nblk, nact), TRSV_THREADS, smem, st>>>(I, act);
+    block_trsv_batched<float><<<dim3(nact, max_nblk), TRSV_THREADS, smem, st>>>(I, act);
     FDE_LAUNCH_CHECK("block_trsv_batched");
     return FDE_OK;
 }
