@@ -181,6 +181,7 @@ def matvec_flops(m: int, s: int, L: int, mu: int) -> float:
 
 
 FP64_PEAK_TFLOPS = 1.25  # GB300 nominal FP64 (no measured FP64 figure in MEASURED_PEAKS.json)
+TRSV_TRAFFIC_RATIO = 1.034  # DRAM bytes / algorithmic bytes of block_trsv_kernel<float> (ncu, m=1023, s=256)
 
 
 def trsv_bytes(mp: int, nblk: int, esz: int) -> float:
@@ -829,9 +830,14 @@ def main():
     if name == "trsv":
         per_launch = trsv_bytes(mp, nblk, esz)
         ach = per_launch / (dom_ms / dom_n / 1e3) / 1e9
+        # DRAM traffic of one launch: ncu's dram__bytes_read.sum + dram__bytes_write.sum on the
+        # m=1023, s=256 case (FP32 factors) was 1.034 x its algorithmic bytes; the bytes grow with
+        # the factor planes, so a launch here moves 1.034 x its algorithmic bytes
+        traffic = TRSV_TRAFFIC_RATIO * per_launch if esz == 4 else None
         roof = {"kernel": "block_trsv_kernel", "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
-                "frac": ach / hbm_peak, "traffic": None, "peak_kind": peak_kind,
-                "algorithmic_bytes_per_launch": per_launch}
+                "frac": ach / hbm_peak, "traffic": traffic, "peak_kind": peak_kind,
+                "algorithmic_bytes_per_launch": per_launch,
+                "traffic_source": "ncu capture at m=1023, s=256 scaled by the factor bytes" if traffic else None}
     elif name == "lu_update" and args.precision in ("fp32", "fp64"):
         flops = lu_update_flops(mp, nblk) * args.steps
         ach = flops / (dom_ms / 1e3) / 1e12

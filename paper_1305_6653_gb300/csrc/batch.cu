@@ -308,9 +308,10 @@ int fde_batch_solve(fde_batch* b, const fde_pgmres_opts* opts, double* const* x_
             const Problem& P0 = *problem_of(b->probs[0]);
             d.fac = P0.d_fac;
             d.dinv = P0.d_dinv;
+            d.tinv = P0.d_tinv;
             d.rhat = (unsigned char*)b->d_rhat_shared + (size_t)i * P0.nblk * P0.mp * 2 * sizeof(float);
         } else {
-            d.rhat = P.d_rhat; d.fac = P.d_fac; d.dinv = P.d_dinv;
+            d.rhat = P.d_rhat; d.fac = P.d_fac; d.dinv = P.d_dinv; d.tinv = nullptr;
         }
         d.b = P.d_b_rhs; d.x = x_out[i]; d.V = P.d_V; d.Z = P.d_Z; d.work = P.d_work; d.H = P.d_H;
         d.cs = P.d_cs; d.sn = P.d_sn; d.gv = P.d_gv; d.y = P.d_y; d.scal = P.d_scal;

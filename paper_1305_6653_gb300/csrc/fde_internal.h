@@ -64,6 +64,7 @@ struct InstDev {
     void* rhat;
     void* fac;
     void* dinv;
+    void* tinv;            // inverted 32 x 32 diagonal tiles of the factors, or NULL
     double* b;
     double* x;
     double* V;

@@ -711,8 +711,13 @@ block_trsv_batched(const InstDev* __restrict__ I, const int* __restrict__ act) {
     const int k = blockIdx.y;
     if (k >= d.nblk) return;
     const size_t mp = d.mp;
-    trsv_body<T, false>(d.mp, (const T*)d.fac + (size_t)k * 2 * mp * mp, (const cplx_t<T>*)d.dinv + (size_t)k * mp,
-                        nullptr, (cplx_t<T>*)d.rhat + (size_t)k * mp);
+    const T* fac = (const T*)d.fac + (size_t)k * 2 * mp * mp;
+    const cplx_t<T>* dinv = (const cplx_t<T>*)d.dinv + (size_t)k * mp;
+    cplx_t<T>* rhat = (cplx_t<T>*)d.rhat + (size_t)k * mp;
+    if (d.tinv)  // diagonal tiles solved as products with their inverses
+        trsv_body<T, true>(d.mp, fac, dinv, (const T*)d.tinv + (size_t)k * (mp / 32) * 4096, rhat);
+    else
+        trsv_body<T, false>(d.mp, fac, dinv, nullptr, rhat);
 }
 
 template <typename T>
@@ -766,12 +771,16 @@ lu_update_tc2_kernel(int mp, int R0, int nt, int part, float* __restrict__ fac,
                      const unsigned char* __restrict__ apack, const unsigned char* __restrict__ bpack, size_t pa,
                      size_t pb, int* __restrict__ err) {
     // part 0: all nt^2 tiles; 1: the cross ti = 0 or tj = 0 (2 nt - 1 tiles: the next
-    // panel's rows and columns); 2: the interior ti, tj >= 1 ((nt - 1)^2 tiles)
+    // panel's rows and columns); 2: the interior ti, tj >= 1 ((nt - 1)^2 tiles); 3: the
+    // row ti = 0 only (nt tiles; the column below it goes to the row-pair kernel)
     const int k = blockIdx.y, x = blockIdx.x;
     int ti, tj;
     if (part == 0) {
         ti = x / nt;
         tj = x % nt;
+    } else if (part == 3) {
+        ti = 0;
+        tj = x;
     } else if (part == 1) {
         ti = x < nt ? 0 : x - nt + 1;
         tj = x < nt ? x : 0;
@@ -782,16 +791,18 @@ lu_update_tc2_kernel(int mp, int R0, int nt, int part, float* __restrict__ fac,
     tc2_update_body<KIND>(mp, R0, fac + (size_t)k * 2 * mp * mp, apack + k * pa, bpack + k * pb, err, ti, tj);
 }
 
-// Interior of the trailing update (tiles ti, tj >= 1) in row pairs: CTA x takes
-// tiles (1 + 2p, tj) and (2 + 2p, tj), p = x / (nt - 1), tj = 1 + x % (nt - 1).
+// Rows ti >= 1 of the trailing update in row pairs, over the columns tj0 .. tj0 + ncol - 1:
+// CTA x takes tiles (1 + 2p, tj) and (2 + 2p, tj), p = x / ncol, tj = tj0 + x % ncol.
+// The interior is tj0 = 1, ncol = nt - 1; the next panel's column below its diagonal
+// block is tj0 = 0, ncol = 1.
 template <int KIND>
 __global__ void __launch_bounds__(128)
-lu_update_tc2p_kernel(int mp, int R0, int nt, float* __restrict__ fac, const unsigned char* __restrict__ apack,
-                      const unsigned char* __restrict__ bpack, size_t pa, size_t pb, int* __restrict__ err) {
+lu_update_tc2p_kernel(int mp, int R0, int nt, int tj0, int ncol, float* __restrict__ fac,
+                      const unsigned char* __restrict__ apack, const unsigned char* __restrict__ bpack, size_t pa,
+                      size_t pb, int* __restrict__ err) {
     using Cfg = Tc2<KIND>;
     const int k = blockIdx.y, x = blockIdx.x;
-    const int ncol = nt - 1;
-    const int p = x / ncol, tj = 1 + x % ncol;
+    const int p = x / ncol, tj = tj0 + x % ncol;
     const int ti0 = 1 + 2 * p;
     const bool two = ti0 + 1 < nt;
     const unsigned char* ab = apack + (size_t)k * pa;
@@ -1468,18 +1479,23 @@ static int run_lu_tc(Problem& P, cudaStream_t st) {
             const int R0 = o + TB;
             const int nt = cdiv(mp - R0, T2_BM);
             if (o > 0) FDE_CUDA_TRY(cudaStreamWaitEvent(sh, P.lu_ev[2], 0));  // interior of step o - TB
-            {
+            {  // the next panel's rows (single tiles) and the column below them (row pairs)
                 StageTimer t(P, FDE_STAGE_LU_TC, sh);
-                lu_update_tc2_kernel<KIND><<<dim3(2 * nt - 1, nb), 128, Cfg::SMEM, sh>>>(
-                    mp, R0, nt, 1, fac, apk(o), bpk(o), pa, pb, P.d_err);
+                lu_update_tc2_kernel<KIND><<<dim3(nt, nb), 128, Cfg::SMEM, sh>>>(mp, R0, nt, 3, fac, apk(o), bpk(o),
+                                                                               pa, pb, P.d_err);
                 FDE_LAUNCH_CHECK("lu_update_tc2_kernel");
+                if (nt > 1) {
+                    lu_update_tc2p_kernel<KIND><<<dim3((nt - 1 + 1) / 2, nb), 128, Tc2p<KIND>::SMEM, sh>>>(
+                        mp, R0, nt, 0, 1, fac, apk(o), bpk(o), pa, pb, P.d_err);
+                    FDE_LAUNCH_CHECK("lu_update_tc2p_kernel");
+                }
             }
             FDE_CUDA_TRY(cudaEventRecord(P.lu_ev[1], sh));
             FDE_CUDA_TRY(cudaStreamWaitEvent(sl, P.lu_ev[1], 0));
             if (nt > 1) {
                 StageTimer t(P, FDE_STAGE_LU_TC, sl);
                 lu_update_tc2p_kernel<KIND><<<dim3(((nt - 1 + 1) / 2) * (nt - 1), nb), 128, Tc2p<KIND>::SMEM, sl>>>(
-                    mp, R0, nt, fac, apk(o), bpk(o), pa, pb, P.d_err);
+                    mp, R0, nt, 1, nt - 1, fac, apk(o), bpk(o), pa, pb, P.d_err);
                 FDE_LAUNCH_CHECK("lu_update_tc2p_kernel");
             }
             FDE_CUDA_TRY(cudaEventRecord(P.lu_ev[2], sl));
