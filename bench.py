@@ -35,6 +35,17 @@ FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FP32 lanes
 ORACLE_ITERATIONS = 20
 
 
+def rank_max_ms(total_ms: float, dist, device) -> float:
+    """The timed region of the slowest replica: the maximum of total_ms over the ranks
+    (one process per GPU, each solving its own instance; no data-path collective)."""
+    if dist is None:
+        return total_ms
+    import torch
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -806,11 +817,7 @@ def main():
     p.profile(False)
     clocks = sampler.stop() if not args.no_clocks else None
 
-    total_ms = sum(per_step)
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = rank_max_ms(sum(per_step), dist, "cuda")
     ms_per_step = total_ms / args.steps
     value = world * args.steps / (total_ms / 1e3)
 
