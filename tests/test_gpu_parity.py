@@ -11,7 +11,7 @@ Tolerances (derived from the arithmetic):
 * S^{-1} r: FP64 LU without pivoting of strictly diagonally dominant blocks
   (growth factor <= 2), backward stable; forward error <= cond(B_k) * eps * c.
   cond(B_k) <= 1e4 on these sizes, so 1e-10 relative.
-* Solutions: the spec requirement, ||x - x_oracle|| / ||x_oracle|| <= 1e-8.
+* Solutions: the accuracy target of the solver, ||x - x_oracle|| / ||x_oracle|| <= 1e-8.
 """
 import numpy as np
 import pytest
