@@ -883,6 +883,64 @@ static size_t diag128_smem() {
            (size_t)(8 * DB + DB) * sizeof(float2);
 }
 
+// Panel solves of the 128 x 128 diagonal block with the 32 values of one row
+// (x U_pp = a, U_pp the leaf's unit-free upper factor, 1/U_cc given) or one column
+// (L_pp x = a, L_pp unit lower) in registers; the leaf's factors are read from shared
+// memory (broadcast; row pitch D128_LD keeps a warp's rows / columns in distinct banks).
+__device__ __noinline__ void panel_row_solve(float* Ar, float* Ai, int row, int P0, const float2* pinv) {
+    constexpr int LD = D128_LD;
+    float xr[DB], xi[DB];
+    const int ri = row * LD + P0;
+#pragma unroll
+    for (int c = 0; c < DB; ++c) {
+        xr[c] = Ar[ri + c];
+        xi[c] = Ai[ri + c];
+    }
+#pragma unroll
+    for (int c = 0; c < DB; ++c) {
+        const float2 pv = pinv[c];
+        const float a = xr[c] * pv.x - xi[c] * pv.y, b = xr[c] * pv.y + xi[c] * pv.x;
+        xr[c] = a;
+        xi[c] = b;
+        const int ci = (P0 + c) * LD + P0;
+#pragma unroll
+        for (int cc = c + 1; cc < DB; ++cc) {
+            const float ur = Ar[ci + cc], ui = Ai[ci + cc];
+            xr[cc] -= a * ur - b * ui;
+            xi[cc] -= a * ui + b * ur;
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < DB; ++c) {
+        Ar[ri + c] = xr[c];
+        Ai[ri + c] = xi[c];
+    }
+}
+
+__device__ __noinline__ void panel_col_solve(float* Ar, float* Ai, int col, int P0) {
+    constexpr int LD = D128_LD;
+    float xr[DB], xi[DB];
+#pragma unroll
+    for (int c = 0; c < DB; ++c) {
+        xr[c] = Ar[(P0 + c) * LD + col];
+        xi[c] = Ai[(P0 + c) * LD + col];
+    }
+#pragma unroll
+    for (int c = 0; c < DB; ++c) {
+#pragma unroll
+        for (int rr = c + 1; rr < DB; ++rr) {
+            const float lr = Ar[(P0 + rr) * LD + P0 + c], li = Ai[(P0 + rr) * LD + P0 + c];
+            xr[rr] -= lr * xr[c] - li * xi[c];
+            xi[rr] -= lr * xi[c] + li * xr[c];
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < DB; ++c) {
+        Ar[(P0 + c) * LD + col] = xr[c];
+        Ai[(P0 + c) * LD + col] = xi[c];
+    }
+}
+
 // One CTA per Strang block: LU (no pivoting) of the W x W block at (o, o), W = 128
 // (or 64 for a last panel), blocked over 32 x 32 leaves in shared memory:
 //   leaf LU by four warps; panel solves X U_pp = A (rows) and L_pp X = A (columns)
@@ -963,36 +1021,11 @@ __device__ __forceinline__ void diag128_body(int mp, int o, float* __restrict__ 
         __syncthreads();
         const int Q0 = P0 + DB, nrest = W - Q0;
         if (nrest <= 0) break;
-        // panel solves in place in shared memory (row pitch 129: a warp's rows or
-        // columns fall in distinct banks)
-        if (t < nrest) {  // row Q0 + t of the column panel: x U_pp = a
-            const int ri = (Q0 + t) * LD + P0;
-            for (int c = 0; c < DB; ++c) {
-                const float2 pv = pinv[c];
-                const float xr = Ar[ri + c], xi = Ai[ri + c];
-                const float a = xr * pv.x - xi * pv.y, b = xr * pv.y + xi * pv.x;
-                Ar[ri + c] = a;
-                Ai[ri + c] = b;
-                const int ci = (P0 + c) * LD + P0;
-#pragma unroll 8
-                for (int cc = c + 1; cc < DB; ++cc) {
-                    const float ur = Ar[ci + cc], ui = Ai[ci + cc];
-                    Ar[ri + cc] -= a * ur - b * ui;
-                    Ai[ri + cc] -= a * ui + b * ur;
-                }
-            }
-        } else if (t >= 256 && t - 256 < nrest) {  // column Q0 + t - 256 of the row panel: L_pp x = a
-            const int j = Q0 + t - 256;
-            for (int c = 0; c < DB; ++c) {
-                const float xr = Ar[(P0 + c) * LD + j], xi = Ai[(P0 + c) * LD + j];
-#pragma unroll 8
-                for (int rr = c + 1; rr < DB; ++rr) {
-                    const float lr = Ar[(P0 + rr) * LD + P0 + c], li = Ai[(P0 + rr) * LD + P0 + c];
-                    Ar[(P0 + rr) * LD + j] -= lr * xr - li * xi;
-                    Ai[(P0 + rr) * LD + j] -= lr * xi + li * xr;
-                }
-            }
-        }
+        // panel solves with the 32 values of one row (x U_pp = a) or one column
+        // (L_pp x = a) in registers (separate functions: their register arrays stay
+        // out of the kernel's own allocation)
+        if (t < nrest) panel_row_solve(Ar, Ai, Q0 + t, P0, pinv);                     // column panel
+        else if (t >= 256 && t - 256 < nrest) panel_col_solve(Ar, Ai, Q0 + t - 256, P0);  // row panel
         __syncthreads();
         // rank-32 trailing update; a task owns rows Q0 + tr + q n4 and columns Q0 + tc + w n4
         const int n4 = nrest / 4;
