@@ -952,6 +952,10 @@ def main():
             "plain_fp64": plain, "tensor_core_update": tc_line, "stage_ms_per_step": stage_ms,
             "stage_launches_per_step": stage_n,
             "per_step_ms": per_step,
+            # setup-excluded rate: the GMRES phase alone (pgmres_solve's device time)
+            "gmres_phase": {"ms_per_solve": sum(s["ms_solve"] for s in stats) / len(stats),
+                            "iterations_per_s": sum(s["iterations"] for s in stats) /
+                            (sum(s["ms_solve"] for s in stats) / 1e3)},
         }
         print(json.dumps(line))
     if dist is not None:
