@@ -1380,12 +1380,14 @@ lu_panel_tc2_kernel(int mp, int o, int R0, int ntr, float* __restrict__ fac, con
     const int k = blockIdx.y, x = blockIdx.x;
     float* re = fac + (size_t)k * 2 * mp * mp;
     const unsigned char* ip = ipack + (size_t)k * pi;
-    if (x < ntr)
-        tc2_tile_body<KIND, true>(mp, R0 + x * T2_BM, o, re, apack + (size_t)k * pa + (size_t)x * Cfg::A_TILE,
-                                  ip + Cfg::A_TILE, err);
-    else
-        tc2_tile_body<KIND, true>(mp, o, R0 + (x - ntr) * T2_BN, re, ip,
-                                  bpack + (size_t)k * pb + (size_t)(x - ntr) * Cfg::B_TILE, err);
+    // D is packed over the operand tile it was computed from (A21 -> L21, A12 -> U12)
+    if (x < ntr) {
+        unsigned char* at = const_cast<unsigned char*>(apack) + (size_t)k * pa + (size_t)x * Cfg::A_TILE;
+        tc2_tile_body<KIND, true>(mp, R0 + x * T2_BM, o, re, at, ip + Cfg::A_TILE, err, at, 0);
+    } else {
+        unsigned char* bt = const_cast<unsigned char*>(bpack) + (size_t)k * pb + (size_t)(x - ntr) * Cfg::B_TILE;
+        tc2_tile_body<KIND, true>(mp, o, R0 + (x - ntr) * T2_BN, re, ip, bt, err, bt, 1);
+    }
 }
 
 // Batched: grid.x = 2 ntg covers the largest active block (ntg tiles per panel).
@@ -1400,12 +1402,12 @@ lu_panel_tc2_batched(const BlkDev* __restrict__ B, int o, int R0, int ntg, int* 
     float* re = (float*)d.fac;
     if (x < ntg) {
         if (x >= nt) return;
-        tc2_tile_body<KIND, true>(d.mp, R0 + x * T2_BM, o, re, d.apack + (size_t)x * Cfg::A_TILE,
-                                  d.ipack + Cfg::A_TILE, err);
+        unsigned char* at = d.apack + (size_t)x * Cfg::A_TILE;
+        tc2_tile_body<KIND, true>(d.mp, R0 + x * T2_BM, o, re, at, d.ipack + Cfg::A_TILE, err, at, 0);
     } else {
         if (x - ntg >= nt) return;
-        tc2_tile_body<KIND, true>(d.mp, o, R0 + (x - ntg) * T2_BN, re, d.ipack,
-                                  d.bpack + (size_t)(x - ntg) * Cfg::B_TILE, err);
+        unsigned char* bt = d.bpack + (size_t)(x - ntg) * Cfg::B_TILE;
+        tc2_tile_body<KIND, true>(d.mp, o, R0 + (x - ntg) * T2_BN, re, d.ipack, bt, err, bt, 1);
     }
 }
 
@@ -1483,17 +1485,12 @@ static int run_lu_tc(Problem& P, cudaStream_t st) {
             lu_pack_panel_kernel<KIND><<<dim3(pgrid, nb), 256, 0, sh>>>(mp, o, R0, fac, apk(o), bpk(o), pa, pb);
             FDE_LAUNCH_CHECK("lu_pack_panel_kernel");
         }
-        {
+        {  // the products also pack L21 / U12 as the update's operand tiles
             StageTimer t(P, FDE_STAGE_LU_PANEL_TC, sh);
             lu_panel_tc2_kernel<KIND><<<dim3(2 * nt, nb), 128, Cfg::SMEM_STORE, sh>>>(mp, o, R0, nt, fac, apk(o),
                                                                                     bpk(o), ipack, pa, pb, pi,
                                                                                     P.d_err);
             FDE_LAUNCH_CHECK("lu_panel_tc2_kernel");
-        }
-        {
-            StageTimer t(P, FDE_STAGE_LU_PACK, sh);
-            lu_pack_panel_kernel<KIND><<<dim3(pgrid, nb), 256, 0, sh>>>(mp, o, R0, fac, apk(o), bpk(o), pa, pb);
-            FDE_LAUNCH_CHECK("lu_pack_panel_kernel");
         }
         return FDE_OK;
     };
@@ -1610,9 +1607,7 @@ static int run_lu_batched_tc(const BlkDev* d_blk, const std::vector<int>& mps, i
         lu_pack_panel_batched<KIND><<<dim3(pgrid, nact), 256, 0, st>>>(d_blk, o, R0);
         FDE_LAUNCH_CHECK("lu_pack_panel_batched");
         lu_panel_tc2_batched<KIND><<<dim3(2 * ntg, nact), 128, Cfg::SMEM_STORE, st>>>(d_blk, o, R0, ntg, err);
-        FDE_LAUNCH_CHECK("lu_panel_tc2_batched");
-        lu_pack_panel_batched<KIND><<<dim3(pgrid, nact), 256, 0, st>>>(d_blk, o, R0);
-        FDE_LAUNCH_CHECK("lu_pack_panel_batched");
+        FDE_LAUNCH_CHECK("lu_panel_tc2_batched");  // also packs L21 / U12
         lu_update_tc2p_batched<KIND><<<dim3(((ntg + 1) / 2) * ntg, nact), 128, Tc2p<KIND>::SMEM, st>>>(d_blk, R0,
                                                                                                      ntg, err);
         FDE_LAUNCH_CHECK("lu_update_tc2p_batched");

@@ -139,10 +139,15 @@ __device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy
 //   STORE = false: C[r0.., c0..] -= D (C prefetched into L2 at the start, staged
 //                  in the freed operand ring after the last MMA);
 //   STORE = true:  C[r0.., c0..]  = D (no read of C; D goes from TMEM to HBM).
+// Store mode also packs D as an operand tile of the trailing update when pk is set:
+// pk_side 0 -- an A' tile (tile rows, K' = [Re | Im] of the 128 columns: L21);
+// pk_side 1 -- a B' tile (K' = the tile rows, output rows = its columns: U12).
+// The operand tile that D replaces is no longer read once the MMAs are complete.
 template <int KIND, bool STORE>
 __device__ __forceinline__ void tc2_tile_body(int mp, int r0, int c0, float* __restrict__ re_plane,
                                               const unsigned char* __restrict__ ga,
-                                              const unsigned char* __restrict__ gb, int* __restrict__ err) {
+                                              const unsigned char* __restrict__ gb, int* __restrict__ err,
+                                              unsigned char* __restrict__ pk = nullptr, int pk_side = 0) {
     using Cfg = Tc2<KIND>;
     extern __shared__ __align__(1024) unsigned char smem[];
     constexpr int NS = STORE ? T2_STAGES : T2_STAGES_UPD;
@@ -272,6 +277,25 @@ __device__ __forceinline__ void tc2_tile_body(int mp, int r0, int c0, float* __r
                         make_float4(dr[4 * q], dr[4 * q + 1], dr[4 * q + 2], dr[4 * q + 3]);
                     reinterpret_cast<float4*>(pi + ch * 16)[q] =
                         make_float4(di[4 * q], di[4 * q + 1], di[4 * q + 2], di[4 * q + 3]);
+                }
+                if (pk && pk_side == 0) {  // L21 row r: K' = column (Re), TB + column (Im)
+                    constexpr int EPS = Cfg::PER_CORE;
+#pragma unroll
+                    for (int u = 0; u < 16 / EPS; ++u) {
+                        pack2_seg<KIND>(pk, T2_BM, r, ch * 16 + u * EPS, dr + u * EPS, false);
+                        pack2_seg<KIND>(pk, T2_BM, r, TB + ch * 16 + u * EPS, di + u * EPS, false);
+                    }
+                } else if (pk) {  // U12 row r = K index: output rows j (Re) and T2_BN + j (Im)
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) {
+                        const int j = ch * 16 + e;
+                        if (j < ncols) {
+                            pack2_store<KIND>(pk, 2 * T2_BN, j, r, dr[e], true);
+                            pack2_store<KIND>(pk, 2 * T2_BN, j, TB + r, -di[e], true);
+                            pack2_store<KIND>(pk, 2 * T2_BN, T2_BN + j, r, di[e], true);
+                            pack2_store<KIND>(pk, 2 * T2_BN, T2_BN + j, TB + r, dr[e], true);
+                        }
+                    }
                 }
             }
         }
