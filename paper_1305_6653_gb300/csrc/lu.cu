@@ -769,7 +769,7 @@ template <int KIND>
 __global__ void __launch_bounds__(128)
 lu_update_tc2_kernel(int mp, int R0, int nt, int part, float* __restrict__ fac,
                      const unsigned char* __restrict__ apack, const unsigned char* __restrict__ bpack, size_t pa,
-                     size_t pb, int* __restrict__ err) {
+                     size_t pb, int* __restrict__ err, unsigned char* __restrict__ bpack_next = nullptr) {
     // part 0: all nt^2 tiles; 1: the cross ti = 0 or tj = 0 (2 nt - 1 tiles: the next
     // panel's rows and columns); 2: the interior ti, tj >= 1 ((nt - 1)^2 tiles); 3: the
     // row ti = 0 only (nt tiles; the column below it goes to the row-pair kernel)
@@ -788,7 +788,11 @@ lu_update_tc2_kernel(int mp, int R0, int nt, int part, float* __restrict__ fac,
         ti = 1 + x / (nt - 1);
         tj = 1 + x % (nt - 1);
     }
-    tc2_update_body<KIND>(mp, R0, fac + (size_t)k * 2 * mp * mp, apack + k * pa, bpack + k * pb, err, ti, tj);
+    // the next panel's row block (ti = 0, tj >= 1) is also packed as the next step's B' tile tj - 1
+    unsigned char* pkn = bpack_next && ti == 0 && tj >= 1
+                             ? bpack_next + (size_t)k * pb + (size_t)(tj - 1) * Tc2<KIND>::B_TILE
+                             : nullptr;
+    tc2_update_body<KIND>(mp, R0, fac + (size_t)k * 2 * mp * mp, apack + k * pa, bpack + k * pb, err, ti, tj, pkn);
 }
 
 // Rows ti >= 1 of the trailing update in row pairs, over the columns tj0 .. tj0 + ncol - 1:
@@ -799,16 +803,20 @@ template <int KIND>
 __global__ void __launch_bounds__(128)
 lu_update_tc2p_kernel(int mp, int R0, int nt, int tj0, int ncol, float* __restrict__ fac,
                       const unsigned char* __restrict__ apack, const unsigned char* __restrict__ bpack, size_t pa,
-                      size_t pb, int* __restrict__ err) {
+                      size_t pb, int* __restrict__ err, unsigned char* __restrict__ apack_next = nullptr) {
     using Cfg = Tc2<KIND>;
     const int k = blockIdx.y, x = blockIdx.x;
     const int p = x / ncol, tj = tj0 + x % ncol;
     const int ti0 = 1 + 2 * p;
     const bool two = ti0 + 1 < nt;
     const unsigned char* ab = apack + (size_t)k * pa;
+    // the next panel's column block (tj = 0) is also packed as the next step's A' tiles ti - 1
+    unsigned char* an = apack_next && tj == 0 ? apack_next + (size_t)k * pa : nullptr;
     tc2_pair_body<KIND>(mp, R0 + ti0 * T2_BM, R0 + tj * T2_BN, two, fac + (size_t)k * 2 * mp * mp,
                         ab + (size_t)ti0 * Cfg::A_TILE, ab + (size_t)(two ? ti0 + 1 : ti0) * Cfg::A_TILE,
-                        bpack + (size_t)k * pb + (size_t)tj * Cfg::B_TILE, err);
+                        bpack + (size_t)k * pb + (size_t)tj * Cfg::B_TILE, err,
+                        an ? an + (size_t)(ti0 - 1) * Cfg::A_TILE : nullptr,
+                        an && two ? an + (size_t)ti0 * Cfg::A_TILE : nullptr);
 }
 
 // Batched, in row pairs over every tile of each active block: grid.x = ceil(ntg / 2) * ntg
@@ -1480,7 +1488,7 @@ static int run_lu_tc(Problem& P, cudaStream_t st) {
         const int nt = cdiv(mp - R0, T2_BM);
         const long items = 2L * (mp - R0) * (TB / Cfg::PER_CORE);
         const int pgrid = (int)std::min<long>((items + 255) / 256, 1024);
-        {
+        if (o == 0) {  // later panels were packed by the previous step's update of their rows and columns
             StageTimer t(P, FDE_STAGE_LU_PACK, sh);
             lu_pack_panel_kernel<KIND><<<dim3(pgrid, nb), 256, 0, sh>>>(mp, o, R0, fac, apk(o), bpk(o), pa, pb);
             FDE_LAUNCH_CHECK("lu_pack_panel_kernel");
@@ -1509,14 +1517,17 @@ static int run_lu_tc(Problem& P, cudaStream_t st) {
             const int R0 = o + TB;
             const int nt = cdiv(mp - R0, T2_BM);
             if (o > 0) FDE_CUDA_TRY(cudaStreamWaitEvent(sh, P.lu_ev[2], 0));  // interior of step o - TB
-            {  // the next panel's rows (single tiles) and the column below them (row pairs)
+            {  // the next panel's rows (single tiles) and the column below them (row pairs); when
+               // that panel has a trailing matrix, they are packed as its operand tiles as well
                 StageTimer t(P, FDE_STAGE_LU_TC, sh);
+                const bool next = R0 + TB < mp;
                 lu_update_tc2_kernel<KIND><<<dim3(nt, nb), 128, Cfg::SMEM, sh>>>(mp, R0, nt, 3, fac, apk(o), bpk(o),
-                                                                               pa, pb, P.d_err);
+                                                                               pa, pb, P.d_err,
+                                                                               next ? bpk(R0) : nullptr);
                 FDE_LAUNCH_CHECK("lu_update_tc2_kernel");
                 if (nt > 1) {
                     lu_update_tc2p_kernel<KIND><<<dim3((nt - 1 + 1) / 2, nb), 128, Tc2p<KIND>::SMEM, sh>>>(
-                        mp, R0, nt, 0, 1, fac, apk(o), bpk(o), pa, pb, P.d_err);
+                        mp, R0, nt, 0, 1, fac, apk(o), bpk(o), pa, pb, P.d_err, next ? apk(R0) : nullptr);
                     FDE_LAUNCH_CHECK("lu_update_tc2p_kernel");
                 }
             }

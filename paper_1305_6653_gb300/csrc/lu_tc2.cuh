@@ -134,6 +134,54 @@ __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.comm
 __device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
+// Operand tiles of the next outer step packed from an updated C tile staged in shared
+// memory (row pitch T2_CROW), one thread per row (A') or column (B'):
+//   A' -- tile row r -> A' row r, K' = [Re | Im] of the tile's 128 columns (the next L21 source);
+//   B' -- tile column j -> B' rows j (Re outputs) and T2_BN + j (Im outputs), K' = the tile
+//         row (the next U12 source).
+template <int KIND>
+__device__ __forceinline__ void pack_staged_a(unsigned char* __restrict__ pk, const unsigned char* sCr,
+                                              const unsigned char* sCi, int nrows) {
+    constexpr int EPS = Tc2<KIND>::PER_CORE;
+    const int r = threadIdx.x;
+    if (r >= nrows) return;
+    const float* cr = reinterpret_cast<const float*>(sCr + r * T2_CROW);
+    const float* ci = reinterpret_cast<const float*>(sCi + r * T2_CROW);
+#pragma unroll 4
+    for (int kp0 = 0; kp0 < TB; kp0 += EPS) {
+        float vr[EPS], vi[EPS];
+#pragma unroll
+        for (int u = 0; u < EPS; ++u) {
+            vr[u] = cr[kp0 + u];
+            vi[u] = ci[kp0 + u];
+        }
+        pack2_seg<KIND>(pk, T2_BM, r, kp0, vr, false);
+        pack2_seg<KIND>(pk, T2_BM, r, TB + kp0, vi, false);
+    }
+}
+
+template <int KIND>
+__device__ __forceinline__ void pack_staged_b(unsigned char* __restrict__ pk, const unsigned char* sCr,
+                                              const unsigned char* sCi, int ncols) {
+    constexpr int EPS = Tc2<KIND>::PER_CORE;
+    const int j = threadIdx.x;
+    if (j >= ncols) return;
+#pragma unroll 2
+    for (int kp0 = 0; kp0 < TB; kp0 += EPS) {
+        float vr[EPS], vi[EPS], nv[EPS];
+#pragma unroll
+        for (int u = 0; u < EPS; ++u) {
+            vr[u] = reinterpret_cast<const float*>(sCr + (kp0 + u) * T2_CROW)[j];
+            vi[u] = reinterpret_cast<const float*>(sCi + (kp0 + u) * T2_CROW)[j];
+            nv[u] = -vi[u];
+        }
+        pack2_seg<KIND>(pk, 2 * T2_BN, j, kp0, vr, true);
+        pack2_seg<KIND>(pk, 2 * T2_BN, j, TB + kp0, nv, true);
+        pack2_seg<KIND>(pk, 2 * T2_BN, T2_BN + j, kp0, vi, true);
+        pack2_seg<KIND>(pk, 2 * T2_BN, T2_BN + j, TB + kp0, vr, true);
+    }
+}
+
 // One 128 x 128 complex output tile at (r0, c0) of one block, D = A' B'^T from the
 // packed tiles ga (A') and gb (B'):
 //   STORE = false: C[r0.., c0..] -= D (C prefetched into L2 at the start, staged
@@ -143,6 +191,8 @@ __device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy
 // pk_side 0 -- an A' tile (tile rows, K' = [Re | Im] of the 128 columns: L21);
 // pk_side 1 -- a B' tile (K' = the tile rows, output rows = its columns: U12).
 // The operand tile that D replaces is no longer read once the MMAs are complete.
+// Update mode with pk set packs the updated tile as a B' tile of the next outer step
+// (a tile of the next panel's row block).
 template <int KIND, bool STORE>
 __device__ __forceinline__ void tc2_tile_body(int mp, int r0, int c0, float* __restrict__ re_plane,
                                               const unsigned char* __restrict__ ga,
@@ -327,8 +377,9 @@ __device__ __forceinline__ void tc2_tile_body(int mp, int r0, int c0, float* __r
             bulk_s2g(gre + (size_t)(r0 + r) * mp + c0, sCr + r * T2_CROW, row_bytes);
             bulk_s2g(gim + (size_t)(r0 + r) * mp + c0, sCi + r * T2_CROW, row_bytes);
             bulk_commit();
-            bulk_wait_read_all();
         }
+        if (pk) pack_staged_b<KIND>(pk, sCr, sCi, ncols);  // reads the tile beside the bulk stores
+        if (r < nrows) bulk_wait_read_all();
     } else if (!(ok && done)) {
         // bounded: let in-flight copies and MMAs land before TMEM is released
         if (staged) tc::mbar_wait(&bar_c, 0);
@@ -360,11 +411,15 @@ struct Tc2p {
     static_assert(SMEM >= 2 * T2_C_BYTES, "a half tile of C must fit the freed operand ring");
 };
 
+// pk0 / pk1 (nullable): A' tiles of the next outer step to pack the updated halves into
+// (tiles of the next panel's column block).
 template <int KIND>
 __device__ __forceinline__ void tc2_pair_body(int mp, int r0, int c0, bool two, float* __restrict__ re_plane,
                                               const unsigned char* __restrict__ ga0,
                                               const unsigned char* __restrict__ ga1,
-                                              const unsigned char* __restrict__ gb, int* __restrict__ err) {
+                                              const unsigned char* __restrict__ gb, int* __restrict__ err,
+                                              unsigned char* __restrict__ pk0 = nullptr,
+                                              unsigned char* __restrict__ pk1 = nullptr) {
     using Cfg = Tc2<KIND>;
     using Pc = Tc2p<KIND>;
     constexpr int NS = T2P_STAGES;
@@ -521,8 +576,10 @@ __device__ __forceinline__ void tc2_pair_body(int mp, int r0, int c0, bool two, 
             bulk_s2g(gre + (size_t)(rh + r) * mp + c0, sCr + r * T2_CROW, row_bytes);
             bulk_s2g(gim + (size_t)(rh + r) * mp + c0, sCi + r * T2_CROW, row_bytes);
             bulk_commit();
-            bulk_wait_read_all();  // the next half reuses the buffer
         }
+        unsigned char* pkh = h == 0 ? pk0 : pk1;
+        if (pkh) pack_staged_a<KIND>(pkh, sCr, sCi, nrows);  // reads the half beside the bulk stores
+        if (r < nrows) bulk_wait_read_all();  // the next half reuses the buffer
         __syncthreads();
     }
     if (!(ok && done)) {
@@ -540,10 +597,10 @@ template <int KIND>
 __device__ __forceinline__ void tc2_update_body(int mp, int R0, float* __restrict__ re_plane,
                                                 const unsigned char* __restrict__ apack,
                                                 const unsigned char* __restrict__ bpack, int* __restrict__ err, int ti,
-                                                int tj) {
+                                                int tj, unsigned char* __restrict__ pk_next = nullptr) {
     using Cfg = Tc2<KIND>;
     tc2_tile_body<KIND, false>(mp, R0 + ti * T2_BM, R0 + tj * T2_BN, re_plane, apack + (size_t)ti * Cfg::A_TILE,
-                               bpack + (size_t)tj * Cfg::B_TILE, err);
+                               bpack + (size_t)tj * Cfg::B_TILE, err, pk_next, 1);
 }
 
 }  // namespace fde
