@@ -605,40 +605,44 @@ __device__ __forceinline__ void trsv_solver(int mp, int nt, const T* re, const T
 // Row index q in [0, len) maps to row lo + q forward and hi - 1 - q backward, so
 // tile d+2's rows are q < 32 in both directions.  The four groups of a warp hold
 // q values of one aligned quartet and len is a multiple of 32, so loop exits and
-// the shuffles stay warp-uniform.
+// the shuffles stay warp-uniform.  Two register buffers of H rows alternate: the
+// loads of one are in flight while the other is applied, so the load pipe does
+// not drain between batches.
 template <typename T, bool FWD>
 __device__ __forceinline__ void trsv_stream(int mp, int nt, const T* re, const T* im, cplx_t<T>* y,
                                             const cplx_t<T> (*xs)[32], int bt) {
     using C = cplx_t<T>;
     using V = typename vec4<T>::type;
-    constexpr int U = trsv_unroll<T>::value;
+    constexpr int H = trsv_unroll<T>::value / 2, HG = H * TRSV_GROUPS;
     const int g = bt / TRSV_TPR, sub = bt % TRSV_TPR;
     for (int d = 0; d + 2 < nt; ++d) {
         const int col = 32 * (FWD ? d : nt - 1 - d) + sub * 4;
         const int lo = FWD ? 32 * (d + 2) : 0;
         const int hi = FWD ? mp : 32 * (nt - 2 - d);
         const int len = hi - lo;
-        V ar[U], ai[U];
-        auto load = [&](int q0) {
+        V ar[2][H], ai[2][H];
+        auto load = [&](int b, int q0) {
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
+            for (int u = 0; u < H; ++u) {
                 const int q = q0 + u * TRSV_GROUPS;
                 if (q < len) {
                     const int r = FWD ? lo + q : hi - 1 - q;
-                    ar[u] = ld4(re + (size_t)r * mp + col);
-                    ai[u] = ld4(im + (size_t)r * mp + col);
+                    ar[b][u] = ld4(re + (size_t)r * mp + col);
+                    ai[b][u] = ld4(im + (size_t)r * mp + col);
                 }
             }
         };
         C x0, x1, x2, x3;
-        auto apply = [&](int q0) {
+        auto apply = [&](int b, int q0) {
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
+            for (int u = 0; u < H; ++u) {
                 const int q = q0 + u * TRSV_GROUPS;
-                T sx = ar[u].x * x0.x - ai[u].x * x0.y + ar[u].y * x1.x - ai[u].y * x1.y + ar[u].z * x2.x -
-                       ai[u].z * x2.y + ar[u].w * x3.x - ai[u].w * x3.y;
-                T sy = ar[u].x * x0.y + ai[u].x * x0.x + ar[u].y * x1.y + ai[u].y * x1.x + ar[u].z * x2.y +
-                       ai[u].z * x2.x + ar[u].w * x3.y + ai[u].w * x3.x;
+                const V& vr = ar[b][u];
+                const V& vi = ai[b][u];
+                T sx = vr.x * x0.x - vi.x * x0.y + vr.y * x1.x - vi.y * x1.y + vr.z * x2.x - vi.z * x2.y +
+                       vr.w * x3.x - vi.w * x3.y;
+                T sy = vr.x * x0.y + vi.x * x0.x + vr.y * x1.y + vi.y * x1.x + vr.z * x2.y + vi.z * x2.x +
+                       vr.w * x3.y + vi.w * x3.x;
 #pragma unroll
                 for (int off = 1; off < TRSV_TPR; off <<= 1) {
                     sx += __shfl_xor_sync(0xffffffffu, sx, off);
@@ -653,17 +657,21 @@ __device__ __forceinline__ void trsv_stream(int mp, int nt, const T* re, const T
                 }
             }
         };
-        load(g);  // independent of x_d: in flight across the wait
+        load(0, g);  // independent of x_d: in flight across the wait
+        load(1, g + HG);
         named_sync(TRSV_BAR_X + (d & 1), TRSV_THREADS);
         x0 = xs[d & 1][sub * 4];
         x1 = xs[d & 1][sub * 4 + 1];
         x2 = xs[d & 1][sub * 4 + 2];
         x3 = xs[d & 1][sub * 4 + 3];
-        apply(g);  // covers q < 32 (tile d+2): groups 0..31, u = 0
+        apply(0, g);  // covers q < 32 (tile d+2): groups 0..31, u = 0
         named_arrive(TRSV_BAR_B + (d & 1), TRSV_THREADS);
-        for (int q0 = g + U * TRSV_GROUPS; q0 < len; q0 += U * TRSV_GROUPS) {
-            load(q0);
-            apply(q0);
+        for (int q0 = g + HG; q0 < len; q0 += 2 * HG) {
+            load(0, q0 + HG);
+            apply(1, q0);
+            if (q0 + HG >= len) break;
+            load(1, q0 + 2 * HG);
+            apply(0, q0 + HG);
         }
     }
 }
