@@ -201,6 +201,23 @@ def trsv_bytes(mp: int, nblk: int, esz: int) -> float:
     return nblk * (2.0 * mp * mp * esz + 4.0 * mp * esz)
 
 
+def path_roofline(m: int, s: int, mp: int, esz: int, its: int, precision: str, bf16_peak: float,
+                  hbm_peak: float, ms_measured: float, restart: int = 20) -> dict:
+    """Whole-path roofline of one solve: the time it would take at the roofs over the
+    measured time.  The block LUs' (s/2+1)(8/3)m^3 real flops at the factor
+    precision's peak, plus, per iteration at Arnoldi step j, the factor stream
+    (trsv_bytes) and (4 + 4(j+1)) n FP64 vector reads and writes at the HBM peak."""
+    nblk = s // 2 + 1
+    n = m * s
+    setup_flops = nblk * (8.0 / 3.0) * float(m) ** 3
+    setup_peak = {"tf32": bf16_peak * 1.1 / 2.25, "tf32x3": bf16_peak * 1.1 / 2.25, "bf16": bf16_peak,
+                  "fp32": FP32_ALU_PEAK_TFLOPS, "fp64": FP64_PEAK_TFLOPS}[precision]
+    iter_bytes = sum(trsv_bytes(mp, nblk, esz) + (4 + 4 * (i % restart + 1)) * 8.0 * n for i in range(its))
+    roof_ms = setup_flops / (setup_peak * 1e12) * 1e3 + iter_bytes / (hbm_peak * 1e9) * 1e3
+    return {"setup_flops": setup_flops, "setup_peak_tflops": setup_peak, "iteration_bytes": iter_bytes,
+            "iterations": its, "ms_at_roofs": roof_ms, "ms_measured": ms_measured, "frac": roof_ms / ms_measured}
+
+
 # ---------------------------------------------------------------------------
 # the CPU oracle baseline (bounded sample)
 # ---------------------------------------------------------------------------
@@ -875,6 +892,8 @@ def main():
                    "timing": "CUDA events on both LU streams; the interior updates overlap the panel chain",
                    "ms_per_step": tms / args.steps, "tflops": tfl / (tms / 1e3) / 1e12,
                    "tensor_peak": bf16_peak * ratio, "c_tile_gbs": tbytes / (tms / 1e3) / 1e9, "hbm_peak": hbm_peak}
+    path_roof = path_roofline(prob.m, prob.s, mp, esz, stats[-1]["iterations"], args.precision, bf16_peak,
+                              hbm_peak, ms_per_step)
     stage_ms = {k: round(v[0] / args.steps, 4) for k, v in prof.items()}
     stage_n = {k: v[1] // args.steps for k, v in prof.items()}
 
@@ -949,7 +968,7 @@ def main():
             "config": workload, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clocks, "iterations": [s["iterations"] for s in stats],
             "rel_residual": stats[-1]["rel_residual"], "rel_residual_oracle_matvec": res_oracle,
-            "plain_fp64": plain, "tensor_core_update": tc_line, "stage_ms_per_step": stage_ms,
+            "plain_fp64": plain, "tensor_core_update": tc_line, "path_roofline": path_roof, "stage_ms_per_step": stage_ms,
             "stage_launches_per_step": stage_n,
             "per_step_ms": per_step,
             # setup-excluded rate: the GMRES phase alone (pgmres_solve's device time)

@@ -1,7 +1,7 @@
 """Host logic of the multi-GPU bench path on CPU: world_size 2 over gloo.  The solver
 runs one replica per GPU (independent instances, no data-path collective); the only
 exchange is the maximum over the ranks of the timed region, and the reference arm runs
-on rank 0 alone."""
+on rank 0 alone.  Also the bench's whole-path roofline arithmetic (host only)."""
 import os
 import socket
 import subprocess
@@ -58,3 +58,14 @@ def test_reference_arm_runs_on_rank_zero_only():
                         "--steps", "1", "--warmup", "0"], env=env, capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, r.stderr
     assert r.stdout.strip() == ""
+
+
+def test_path_roofline_counts():
+    import bench
+    r = bench.path_roofline(2047, 256, 2048, 4, 29, "tf32", 1947.8, 6789.6, 55.0)
+    # (s/2+1)(8/3)m^3 real flops of the 129 complex block LUs at m = 2047
+    assert abs(r["setup_flops"] - 2.9506e12) / 2.9506e12 < 1e-4
+    # 29 iterations: 20 + 9 Arnoldi steps, each the 4.333 GB factor stream plus its vectors
+    vec = sum(4 + 4 * (i % 20 + 1) for i in range(29)) * 8.0 * 2047 * 256
+    assert r["iteration_bytes"] == 29 * 129 * (2.0 * 2048 * 2048 * 4 + 4.0 * 2048 * 4) + vec
+    assert 0.0 < r["frac"] < 1.0
