@@ -11,6 +11,11 @@ Default workload: m=2047 interior points, s=256 time steps, alpha=1.8,
 d+(x)=1+x, d-(x)=2-x, 5-step GBDF, manufactured source (exact solution
 exp(-t) x^2 (1-x)^2); 524,032 unknowns.  Synthetic, seeded-free (deterministic).
 
+Other configurations (--config): batch (64 uneven instances in one call), rhs (many
+right-hand sides of one operator), precision (m=4095, s=128 factor precisions),
+learned (warm start), bccb (S^(2) and its modified form), example41 (Tables 1-2),
+timevar (the default shape with d+-(x, t) varying in time).
+
 Multi-GPU: one process per GPU (torchrun), each solving its own instance; the
 instances are independent, so there is no data-path collective (weak scaling).
 """
@@ -60,7 +65,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
-    ap.add_argument("--config", choices=["scale", "batch", "learned", "precision", "bccb", "example41", "rhs"],
+    ap.add_argument("--config", choices=["scale", "batch", "learned", "precision", "bccb", "example41", "rhs", "timevar"],
                     default="scale",
                     help="scale: one m=2047/s=256 instance per step; batch: 64 uneven instances per step; "
                          "learned: train the warm-start operator on m=1023/s=256 solves, then compare guesses; "
@@ -504,6 +509,87 @@ def bench_precision(args, world, rank, local_rank):
 # Strang-type BCCB preconditioners S^(2) / S~^(2) on the benchmark workload
 # ---------------------------------------------------------------------------
 
+def bench_timevar(args, world, rank, local_rank):
+    """Time-dependent coefficients d+-(x, t) (eq. (1.1) allows them): the default
+    workload's shape (m=2047, s=256, alpha=1.8, 5-step GBDF) with
+    d+(x,t) = (1+x)(1 + sin(pi t)/2), d-(x,t) = (2-x)(1 + t/2).  The matvec applies
+    J(t_n) on every time level; the block-circulant preconditioner uses the
+    time-averaged J.  The oracle's time-level matvec checks the last solution."""
+    import numpy as np
+    import torch
+
+    import fde_inputs
+    import oracle as O
+    import paper_1305_6653_gb300 as fde
+
+    torch.cuda.set_device(local_rank)
+    prob = fde_inputs.manufactured_time_varying(args.m, args.s, 1.8, "GBDF5", name=f"timevar_m{args.m}_s{args.s}")
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    xbuf = torch.empty(prob.n, dtype=torch.float64, device="cuda")
+    p = fde.FDEProblem.from_inputs(prob, device_inputs=True)
+
+    def step():
+        p.assemble().factor(args.precision)
+        _, st = p.solve(tol=args.tol, restart=20, maxit=400, out=xbuf)
+        return st
+
+    for _ in range(args.warmup):
+        step()
+    l0 = fde.fde_launch_count()
+    sampler = ClockSampler(local_rank)
+    if not args.no_clocks:
+        sampler.start()
+    p.profile(True)
+    times, stats = [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        stats.append(step())
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    prof = p.profile_read()
+    p.profile(False)
+    clocks = sampler.stop() if not args.no_clocks else None
+    launches = fde.fde_launch_count() - l0
+    p.close()
+    ms = rank_max_ms(sum(times), None, "cuda") / args.steps
+    mp = (prob.m + 63) // 64 * 64
+    nblk = prob.s // 2 + 1
+    esz = 8 if args.precision == "fp64" else 4
+    roof = None
+    if prof.get("trsv", (0, 0))[1] > 0:
+        tms, tn = prof["trsv"]
+        per_launch = trsv_bytes(mp, nblk, esz)
+        ach = per_launch / (tms / tn / 1e3) / 1e9
+        hbm_peak, _, _, peak_kind = peaks()
+        roof = {"kernel": "block_trsv_kernel", "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                "frac": ach / hbm_peak, "traffic": TRSV_TRAFFIC_RATIO * per_launch if esz == 4 else None,
+                "peak_kind": peak_kind, "algorithmic_bytes_per_launch": per_launch,
+                "traffic_source": "ncu capture at m=1023, s=256 scaled by the factor bytes" if esz == 4 else None}
+    xs = xbuf.cpu().numpy()
+    bor = O.reduced_rhs(prob)
+    res_oracle = float(np.linalg.norm(bor - O.matvec(prob, xs)) / np.linalg.norm(bor))
+    if rank == 0:
+        line = {"metric": METRIC, "value": world * 1e3 / ms, "unit": "solves/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32+f64" if args.precision != "fp64" else "f64", "data": "synthetic",
+                "config": {"workload": f"timevar_m{prob.m}_s{prob.s}_gbdf5_alpha1.8_d_of_x_t", "m": prob.m,
+                           "s": prob.s, "unknowns": prob.n, "scheme": "GBDF5", "alpha": 1.8,
+                           "d": "d+=(1+x)(1+sin(pi t)/2), d-=(2-x)(1+t/2)", "precision": args.precision,
+                           "tol_true_residual": args.tol, "restart": 20,
+                           "l2": "flushed (512 MiB write) before every timed step; factors exceed L2"},
+                "roofline": roof, "gpu_launches": launches, "clocks": clocks,
+                "iterations": [s["iterations"] for s in stats], "rel_residual": stats[-1]["rel_residual"],
+                "rel_residual_oracle_matvec": res_oracle,
+                "stage_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in prof.items()},
+                "stage_launches_per_step": {k: v[1] // args.steps for k, v in prof.items()}}
+        print(json.dumps(line))
+
+
 def bench_bccb(args, world, rank, local_rank):
     import numpy as np
     import torch
@@ -751,6 +837,8 @@ def main():
         return bench_bccb(args, world, rank, local_rank)
     if args.config == "precision" and args.impl == "ours":
         return bench_precision(args, world, rank, local_rank)
+    if args.config == "timevar" and args.impl == "ours":
+        return bench_timevar(args, world, rank, local_rank)
     prob = fde_inputs.config_scale(args.m, args.s)
     workload = {"workload": f"scale_m{args.m}_s{args.s}_gbdf5_alpha1.8_variable_d", "m": args.m, "s": args.s,
                 "unknowns": args.m * args.s, "scheme": "GBDF5", "alpha": 1.8, "d": "d+=1+x, d-=2-x",
