@@ -51,3 +51,26 @@ def test_time_averaged_strang_preconditioner_converges():
     # the preconditioner's J is the mean of J_1..J_s
     Jbar = np.mean([O.j_at(p, n) for n in range(1, p.s + 1)], axis=0)
     np.testing.assert_allclose(O.j_of(p), Jbar, rtol=1e-12, atol=1e-12 * np.abs(Jbar).max())
+
+
+def test_time_level_matvec_matches_fft_toeplitz_products():
+    """J_n z_n = dx^-alpha (D+(t_n) G z_n + D-(t_n) G^T z_n) (eq. (1.4) at each time
+    level), with G z and G^T z taken as Toeplitz products by scipy's FFT route and
+    the BVM band applied after: an evaluation independent of the oracle's dense J_n."""
+    from scipy.linalg import matmul_toeplitz
+
+    prob = fi.manufactured_time_varying(255, 32, 1.6, "GBDF3")
+    m, s = prob.m, prob.s
+    z = np.random.default_rng(5).standard_normal(m * s)
+    g = O.grunwald_weights(prob.alpha, m + 1)
+    col = g[1:m + 1]
+    row = np.zeros(m)
+    row[0], row[1] = g[1], g[0]
+    Z = z.reshape(s, m)
+    GZ = matmul_toeplitz((col, row), Z.T).T
+    GtZ = matmul_toeplitz((row, col), Z.T).T
+    JZ = (prob.dplus_t[1:] * GZ + prob.dminus_t[1:] * GtZ) / prob.dx ** prob.alpha
+    A, B = O.bvm_matrices(prob.family, prob.mu, s)
+    ref = (A[1:, 1:] @ Z - prob.h * (B[1:, 1:] @ JZ)).reshape(-1)
+    got = O.matvec(prob, z)
+    assert np.linalg.norm(got - ref) <= 1e-12 * np.linalg.norm(ref)
