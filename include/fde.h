@@ -347,6 +347,16 @@ int fde_profile_read(fde_problem* p, int stage, double* total_ms, int* launches)
 /* Number of kernels this library has launched in this process (all problems). */
 long long fde_launch_count(void);
 
+/* Return the library's cached device memory to the CUDA driver.  Buffers freed by
+ * fde_problem_destroy / fde_batch_destroy (and replaced workspaces) are kept in a
+ * process-wide cache of at most 16 GiB, keyed by exact size, so that the next
+ * problem of the same shape reuses them without cudaMalloc / cudaFree; the cache
+ * is also emptied for a device when an allocation on it fails.  This call frees
+ * every cached block on every device; buffers of live problems are not touched.
+ * Thread-safe.  Makes no CUDA call when the cache is empty.  Errors: FDE_ERR_CUDA
+ * (a cudaFree failed; the cache is emptied all the same). */
+int fde_release_cached_memory(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -19,7 +19,8 @@ from ._lib import (FDE_BF16, FDE_ETR, FDE_FP32, FDE_FP64, FDE_GAM, FDE_GBDF, FDE
 
 __all__ = ["FDEProblem", "FDEBatch", "FDENop", "fde_problem_create", "bvm_assemble", "strang_precond_factor",
            "bccb_precond_setup", "pgmres_solve",
-           "fde_problem_destroy", "fde_matvec", "fde_precond_apply", "FdeError", "PRECISIONS"]
+           "fde_problem_destroy", "fde_matvec", "fde_precond_apply", "fde_release_cached_memory", "FdeError",
+           "PRECISIONS"]
 
 
 def _torch():
@@ -68,6 +69,11 @@ def pgmres_solve(h, opts: FdePgmresOpts, x0_ptr: int | None, x_ptr: int, raise_o
 
 def fde_launch_count() -> int:
     return int(_lib.load().fde_launch_count())
+
+
+def fde_release_cached_memory() -> None:
+    """Return the library's cached device buffers to the CUDA driver."""
+    _lib.check(_lib.load().fde_release_cached_memory(), "fde_release_cached_memory")
 
 
 def fde_problem_destroy(h) -> None:

@@ -37,6 +37,7 @@ EXPORTED = [
     "fde_problem_destroy",
     "fde_last_error", "fde_matvec", "fde_precond_apply", "fde_get_rhs", "fde_get_factor_block",
     "fde_get_grunwald", "fde_problem_sizes", "fde_profile_enable", "fde_profile_read", "fde_launch_count",
+    "fde_release_cached_memory",
     "fde_precond_apply_noalloc", "fde_batch_create", "fde_batch_share_operator", "fde_batch_assemble",
     "fde_batch_factor",
     "fde_batch_solve", "fde_batch_size", "fde_batch_problem", "fde_batch_destroy",
@@ -110,6 +111,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "fde_profile_enable": (i32, [vp, i32]),
         "fde_profile_read": (i32, [vp, i32, C.POINTER(f64), C.POINTER(i32)]),
         "fde_launch_count": (C.c_longlong, []),
+        "fde_release_cached_memory": (C.c_int, []),
         "fde_precond_apply_noalloc": (i32, [vp, vp, vp]),
         "fde_batch_create": (i32, [C.POINTER(FdeProblemDesc), i32, vp, C.POINTER(vp)]),
         "fde_batch_assemble": (i32, [vp]),

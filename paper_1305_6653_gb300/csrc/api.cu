@@ -610,6 +610,8 @@ void fde_problem_destroy(fde_problem* h) {
 
 long long fde_launch_count(void) { return g_launches.load(); }
 
+int fde_release_cached_memory(void) { return dev_release_cached(); }
+
 int fde_profile_enable(fde_problem* h, int on) {
     if (!h) return set_error(FDE_ERR_ARG, "NULL problem");
     Problem& P = h->P;

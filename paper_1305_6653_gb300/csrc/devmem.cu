@@ -7,7 +7,8 @@
 // device.  Repeated create / solve / destroy cycles (the end-to-end use of the
 // API) therefore reuse the blocks of the previous problem.  The cache holds at
 // most DEVMEM_CACHE_LIMIT bytes (oldest blocks are released first) and is
-// emptied for the device when cudaMalloc runs out of memory.
+// emptied for the device when cudaMalloc runs out of memory, and entirely by
+// fde_release_cached_memory().
 //
 // dev_free() callers guarantee that no queued GPU work still uses the block
 // (every call site synchronises the problem's streams first); the block may be
@@ -100,6 +101,22 @@ void dev_free(void* p) {
         g_cached -= g_cache.front().bytes;
         g_cache.pop_front();
     }
+}
+
+int dev_release_cached() {
+    std::lock_guard<std::mutex> lock(g_mu);
+    cudaError_t first = cudaSuccess;
+    for (const Block& b : g_cache) {
+        const cudaError_t e = cudaFree(b.p);
+        if (e != cudaSuccess && first == cudaSuccess) first = e;
+    }
+    g_cache.clear();
+    g_cached = 0;
+    if (first != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(FDE_ERR_CUDA, std::string("cudaFree failed: ") + cudaGetErrorString(first));
+    }
+    return FDE_OK;
 }
 
 }  // namespace fde

@@ -255,6 +255,8 @@ int launch_bccb_solve(const Problem& P, void* rhat, int prec, cudaStream_t st);
 // dev_free: no queued GPU work may still use the block.
 int dev_alloc(void** p, size_t bytes);
 void dev_free(void* p);
+// Frees every cached block (blocks in use are not affected).
+int dev_release_cached();
 
 // The problem behind a C-ABI handle (defined in api.cu).
 Problem* problem_of(fde_problem* h);

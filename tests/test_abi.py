@@ -78,3 +78,10 @@ def test_argument_validation_needs_no_gpu(lib):
     d.dplus_t = None
     assert L.bvm_assemble(None) == _lib.FDE_ERR_ARG
     assert L.strang_precond_factor(None, 0) == _lib.FDE_ERR_ARG
+
+
+def test_release_of_an_empty_device_cache_needs_no_gpu(lib):
+    """With nothing cached, fde_release_cached_memory makes no CUDA call and succeeds."""
+    from paper_1305_6653_gb300 import _lib, fde_release_cached_memory
+    assert _lib.load().fde_release_cached_memory() == _lib.FDE_OK
+    fde_release_cached_memory()
