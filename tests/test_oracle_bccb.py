@@ -68,14 +68,19 @@ def test_eigenvalues_follow_eq_1_13():
 
 
 def test_modified_preconditioner_moves_only_phi0():
-    # S~^(2) - S^(2) = (phi~_0 / s) ones(s, s) (x) I_N with phi~_0 = Re(phi_{s-1}), phi_0 = 0
+    # eq. xc changes one eigenvalue of s(A), the one of the constant eigenvector (phi_0 = 0,
+    # the consistency condition rho(1) = 0): S~^(2) - S^(2) must be c * (ones(s, s) / s) (x) I_N
+    # for one scalar c != 0.  The value of c is the reading-dependent part; it is pinned
+    # against the printed iteration counts (test_paper_tables_modified_bccb_alpha_1_2).
     p = _tiny(5, 12, "GAM4", 1.4)
     phi, _ = O.strang_symbols(p.family, p.mu, p.s)
     assert abs(phi[0]) < 1e-14
     diff = O.bccb_matrix(p, modified=True) - O.bccb_matrix(p)
-    expect = np.kron(np.full((p.s, p.s), phi[-1].real / p.s), np.eye(p.m))
-    np.testing.assert_allclose(diff, expect, atol=1e-12)
-    # every eigenvalue of S~^(2) is away from zero, and those of the j = 0 slice moved by phi~_0
+    shape = np.kron(np.full((p.s, p.s), 1.0 / p.s), np.eye(p.m))
+    c = float(np.sum(diff * shape) / np.sum(shape * shape))
+    np.testing.assert_allclose(diff, c * shape, atol=1e-12)
+    assert abs(c) > 1e-3
+    # the singular eigenvalue phi_0 - h psi_0 lambda(s(J)) of the j = 0 slice is gone
     lam = np.linalg.eigvals(O.bccb_matrix(p, modified=True))
     assert np.abs(lam).min() > 1e-3
 
@@ -95,14 +100,7 @@ def _golden():
 MISPRINTS = {(1.5, 96, 16), (1.5, 96, 32), (1.5, 96, 64)}
 
 
-@pytest.mark.parametrize("row", _golden(), ids=lambda r: f"a{r[0]}-n{r[1]}-s{r[2]}")
-def test_paper_tables_bccb_iteration_counts(row):
-    """Tables 1-2 of Sec. 4, columns S^(2) and S~^(2) for Example 4.1.
-
-    S^(2): within max(2, 15%) of the printed count.  S~^(2): needs at least as many
-    iterations as S^(2) (the paper's ordering in every row) and stays within 40% of
-    the printed count (the modified eigenvalue is the paper's reading-dependent part)."""
-    alpha, n, s, its2, its2m = row
+def _bccb_counts(alpha, n, s):
     p = fi.example_4_1(alpha, n, s)
     J = O.j_of(p)
     AB = O.bvm_matrices(p.family, p.mu, p.s)
@@ -112,7 +110,38 @@ def test_paper_tables_bccb_iteration_counts(row):
     _, got2m, ok2m, _ = O.gmres(mv, b, precond=O.BCCBPreconditioner(p, modified=True).apply, side="left",
                                 restart=20, tol=1e-8)
     assert ok2 and ok2m
+    return got2, got2m
+
+
+@pytest.mark.parametrize("row", _golden(), ids=lambda r: f"a{r[0]}-n{r[1]}-s{r[2]}")
+def test_paper_tables_bccb_iteration_counts(row):
+    """Tables 1-2 of Sec. 4, columns S^(2) and S~^(2) for Example 4.1.
+
+    S^(2): within max(2, 15%) of the printed count.  S~^(2): needs at least as many
+    iterations as S^(2) (the paper's ordering in every row); its alpha = 1.2 column is
+    pinned tightly below, the alpha = 1.5 column (where the printed counts are 20-37 %
+    above those of this reading, a known reading-dependent gap) within 40%."""
+    alpha, n, s, its2, its2m = row
+    got2, got2m = _bccb_counts(alpha, n, s)
     if (alpha, n, s) not in MISPRINTS:
         assert abs(got2 - its2) <= max(2, 0.15 * its2), (got2, its2)
     assert got2m >= got2 - 1, (got2m, got2)
     assert abs(got2m - its2m) <= 0.4 * its2m, (got2m, its2m)
+
+
+def test_paper_tables_modified_bccb_alpha_1_2():
+    """The value of phi~_0 in eq. xc, pinned against Table 1 (alpha = 1.2), column S~^(2).
+
+    With phi~_0 = Re(phi_{s-1}) every row is within max(4, 15%) of the printed count and
+    the column's mean relative deviation is below 10% (measured: at most 4 iterations,
+    mean 7%).  The other readings one could take from the garbled display fail this:
+    phi~_0 = |phi_1| needs 24-45% more iterations than printed in every row, and
+    phi~_0 = Re(phi_{s/2}) (the Nyquist eigenvalue) 2.5-9 times as many."""
+    rows = [r for r in _golden() if r[0] == 1.2]
+    assert len(rows) == 12
+    devs = []
+    for alpha, n, s, _, its2m in rows:
+        _, got2m = _bccb_counts(alpha, n, s)
+        assert abs(got2m - its2m) <= max(4, 0.15 * its2m), (n, s, got2m, its2m)
+        devs.append(abs(got2m - its2m) / its2m)
+    assert np.mean(devs) <= 0.10, devs
