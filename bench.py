@@ -11,6 +11,15 @@ Default workload: m=2047 interior points, s=256 time steps, alpha=1.8,
 d+(x)=1+x, d-(x)=2-x, 5-step GBDF, manufactured source (exact solution
 exp(-t) x^2 (1-x)^2); 524,032 unknowns.  Synthetic, seeded-free (deterministic).
 
+The default run also reports, as extra keys of its JSON line: the plain FP64 PGMRES
+on the same workload (one warm-up, --fp64-steps timed), the same solve end to end
+through the C ABI from pinned host buffers (e2e), the 64-instance batched workload
+(batch64) and the m=4095 precision study (precision_m4095), the stage split of an
+untimed profiled pass, and cuBLAS-measured TF32 / FP32 / FP64 peaks.  The headline
+runs the product path (iteration CUDA graphs); the block solves are timed by event
+pairs recorded inside those graphs.  --impl reference times complete solves of the
+CPU oracle.
+
 Other configurations (--config): batch (64 uneven instances in one call), rhs (many
 right-hand sides of one operator), precision (m=4095, s=128 factor precisions),
 learned (warm start), bccb (S^(2) and its modified form), example41 (Tables 1-2),
@@ -35,9 +44,6 @@ sys.path.insert(0, ROOT)
 METRIC = "space-time FDE solves/s at rel.err 1e-8: mixed+batched vs plain FP64 PGMRES"
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
-# Iterations of the oracle's exact-FP64 Strang FGMRES(20) on the benchmark workload at
-# tol 1e-10 (the same method in FP64 on the GPU takes 20), used to compose its solve time
-ORACLE_ITERATIONS = 20
 
 
 def rank_max_ms(total_ms: float, dist, device) -> float:
@@ -58,11 +64,26 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", default="tf32", choices=["fp64", "fp32", "tf32", "bf16", "tf32x3"])
+    ap.add_argument("--matvec", default="fp64", choices=["fp64", "fp32"],
+                    help="precision of the Toeplitz apply in the Arnoldi products (the restart residual is FP64)")
+    ap.add_argument("--relax", type=float, default=0.0,
+                    help="--matvec fp32: FP32 products while the residual estimate is above this (0: always)")
+    ap.add_argument("--batch-precision", default="tf32", choices=["fp32", "tf32", "bf16", "tf32x3"],
+                    help="factor precision of the batched workload")
     ap.add_argument("--m", type=int, default=2047)
     ap.add_argument("--s", type=int, default=256)
     ap.add_argument("--tol", type=float, default=1e-10)
-    ap.add_argument("--fp64-steps", type=int, default=1, help="plain FP64 solves timed for comparison (0: skip)")
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--fp64-steps", type=int, default=3,
+                    help="plain FP64 solves timed for comparison, after one FP64 warm-up solve (0: skip)")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--profile-steps", type=int, default=2,
+                    help="untimed solves with the full stage profiler after the timed region (stage split)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched (64 instances) and precision (m=4095) legs of the default run")
+    ap.add_argument("--reference-budget", type=float, default=150.0,
+                    help="--impl reference: seconds of complete oracle solves (at least one solve)")
+    ap.add_argument("--oracle-single-thread", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--single-its", type=int, default=20, help=argparse.SUPPRESS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--config", choices=["scale", "batch", "learned", "precision", "bccb", "example41", "rhs", "timevar"],
@@ -207,7 +228,8 @@ def trsv_bytes(mp: int, nblk: int, esz: int) -> float:
 
 
 def path_roofline(m: int, s: int, mp: int, esz: int, its: int, precision: str, bf16_peak: float,
-                  hbm_peak: float, ms_measured: float, restart: int = 20) -> dict:
+                  hbm_peak: float, ms_measured: float, restart: int = 20, tf32_peak: float | None = None,
+                  fp64_peak: float | None = None) -> dict:
     """Whole-path roofline of one solve: the time it would take at the roofs over the
     measured time.  The block LUs' (s/2+1)(8/3)m^3 real flops at the factor
     precision's peak, plus, per iteration at Arnoldi step j, the factor stream
@@ -215,8 +237,9 @@ def path_roofline(m: int, s: int, mp: int, esz: int, its: int, precision: str, b
     nblk = s // 2 + 1
     n = m * s
     setup_flops = nblk * (8.0 / 3.0) * float(m) ** 3
-    setup_peak = {"tf32": bf16_peak * 1.1 / 2.25, "tf32x3": bf16_peak * 1.1 / 2.25, "bf16": bf16_peak,
-                  "fp32": FP32_ALU_PEAK_TFLOPS, "fp64": FP64_PEAK_TFLOPS}[precision]
+    tf32 = tf32_peak if tf32_peak else bf16_peak * 1.1 / 2.25
+    setup_peak = {"tf32": tf32, "tf32x3": tf32, "bf16": bf16_peak,
+                  "fp32": FP32_ALU_PEAK_TFLOPS, "fp64": fp64_peak if fp64_peak else FP64_PEAK_TFLOPS}[precision]
     iter_bytes = sum(trsv_bytes(mp, nblk, esz) + (4 + 4 * (i % restart + 1)) * 8.0 * n for i in range(its))
     roof_ms = setup_flops / (setup_peak * 1e12) * 1e3 + iter_bytes / (hbm_peak * 1e9) * 1e3
     return {"setup_flops": setup_flops, "setup_peak_tflops": setup_peak, "iteration_bytes": iter_bytes,
@@ -224,28 +247,37 @@ def path_roofline(m: int, s: int, mp: int, esz: int, its: int, precision: str, b
 
 
 # ---------------------------------------------------------------------------
-# the CPU oracle baseline (bounded sample)
+# the CPU oracle: bounded sample (cpu_baseline) and complete solves (--impl reference)
 # ---------------------------------------------------------------------------
 
-def oracle_sample(prob, iterations: int) -> dict:
-    """Time the FP64 oracle on a bounded sample of one solve and compose the time
-    of a full solve (a complete oracle solve of the benchmark workload takes about
-    a minute of host time).
+def oracle_cores() -> int:
+    """Threads the oracle's BLAS/LAPACK use (threadpoolctl where installed, else the
+    environment's OpenBLAS/OMP setting, else the host's core count)."""
+    try:
+        from threadpoolctl import threadpool_info
+        return max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
+    except Exception:
+        for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS"):
+            if os.environ.get(k, "").isdigit():
+                return int(os.environ[k])
+        return os.cpu_count() or 1
+
+
+def oracle_sample(prob, iterations: int, its_source: str) -> dict:
+    """Time the FP64 oracle on a bounded sample of one solve and compose the time of
+    a full solve from it (a complete oracle solve of the benchmark workload takes
+    about a minute of host time; the reference arm times complete solves).
 
     Sample, on the full workload: the right-hand side, the dense LUs of all s/2+1
     Strang blocks, and the work of one FGMRES iteration (one preconditioner apply,
-    one matvec, classical Gram-Schmidt with re-orthogonalisation against the
-    mean basis size of GMRES(20), 10 vectors).  Composition:
-    t = t_rhs + t_factor + its * t_iteration."""
+    one matvec, classical Gram-Schmidt with re-orthogonalisation against the mean
+    basis size of GMRES(20), 10 vectors).  Composition:
+    t = t_rhs + t_factor + its * t_iteration, its = `iterations` (`its_source` says
+    where that count comes from)."""
     import numpy as np
 
     import oracle as O
 
-    try:
-        from threadpoolctl import threadpool_info
-        cores = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
-    except Exception:
-        cores = os.cpu_count() or 1
     s, m = prob.s, prob.m
     t0 = time.perf_counter()
     J = O.j_of(prob)
@@ -269,45 +301,164 @@ def oracle_sample(prob, iterations: int) -> dict:
     t_solve = t_rhs + t_fac + iterations * t_it
     sampled = t_rhs + t_fac + t_it
     return {
-        "value": 1.0 / t_solve, "unit": "solves/s", "cores": int(cores), "kind": "oracle",
-        "sample": (f"m={m}, s={s}: right-hand side, dense LUs of all {nblk} Strang blocks and one FGMRES "
-                   f"iteration (preconditioner apply, matvec, CGS2 against 10 vectors), composed to "
-                   f"{iterations} iterations; {sampled:.1f} s of CPU work"),
+        "value": 1.0 / t_solve, "unit": "solves/s", "cores": oracle_cores(), "kind": "oracle", "composed": True,
+        "sample": (f"m={m}, s={s}: right-hand side ({t_rhs:.2f} s), dense LUs of all {nblk} Strang blocks "
+                   f"({t_fac:.1f} s) and one FGMRES iteration ({t_it:.2f} s: preconditioner apply, matvec, CGS2 "
+                   f"against 10 vectors), composed to {iterations} iterations ({its_source}); {sampled:.1f} s of "
+                   f"CPU work"),
         "seconds_per_solve": t_solve,
     }
+
+
+def oracle_complete_solve(prob, tol: float) -> dict:
+    """One complete solve by the oracle as it stands: right-hand side, the Strang
+    preconditioner (dense DFT along time, one LAPACK LU per frequency block), and its
+    right-preconditioned FGMRES(20) to a true relative residual of tol (the steps of
+    oracle.solve_strang_gmres, timed one by one)."""
+    import oracle as O
+
+    t0 = time.perf_counter()
+    J = O.j_of(prob)
+    AB = O.bvm_matrices(prob.family, prob.mu, prob.s)
+    b = O.reduced_rhs(prob, J=J)
+    t1 = time.perf_counter()
+    P = O.StrangPreconditioner(prob, J=J)
+    t2 = time.perf_counter()
+    _, its, ok, _ = O.gmres(lambda z: O.matvec(prob, z, J=J, AB=AB), b, precond=P.apply, side="right",
+                            restart=20, tol=tol, maxit=400, reference="b")
+    t3 = time.perf_counter()
+    return {"seconds": t3 - t0, "rhs_s": t1 - t0, "factor_s": t2 - t1, "fgmres_s": t3 - t2, "iterations": its,
+            "converged": bool(ok), "blocks": len(P.lu)}
+
+
+def oracle_single_thread_sample(prob, iterations: int) -> dict:
+    """Single-thread oracle (run in a child process with one BLAS thread): the right-
+    hand side and one matvec, DFT pair and Gram-Schmidt at full size, ONE dense block
+    LU and ONE block solve, composed to a full solve: t_rhs + nblk t_lu +
+    its (s t_blocksolve + t_rest)."""
+    import numpy as np
+    import scipy.linalg as sla
+
+    import oracle as O
+
+    s, m = prob.s, prob.m
+    t0 = time.perf_counter()
+    J = O.j_of(prob)
+    O.reduced_rhs(prob, J=J)
+    t_rhs = time.perf_counter() - t0
+    AB = O.bvm_matrices(prob.family, prob.mu, s)
+    phi, psi = O.strang_symbols(prob.family, prob.mu, s)
+    k = s // 4
+    Bk = phi[k] * np.eye(m) - prob.h * psi[k] * J
+    t0 = time.perf_counter()
+    lu = sla.lu_factor(Bk, check_finite=False)
+    t_lu = time.perf_counter() - t0
+    r = np.random.default_rng(3).standard_normal(m) + 0j
+    t0 = time.perf_counter()
+    sla.lu_solve(lu, r, check_finite=False)
+    t_bs = time.perf_counter() - t0
+    V = np.random.default_rng(2).standard_normal((11, prob.n))
+    n_ = np.arange(s)
+    F = np.exp(-2j * np.pi * np.outer(n_, n_) / s)
+    t0 = time.perf_counter()
+    R = F @ V[0].reshape(s, m)
+    z = (np.conj(F) @ R).real.reshape(-1) / s
+    w = O.matvec(prob, z, J=J, AB=AB)
+    for _ in range(2):
+        h = V[:10] @ w
+        w = w - V[:10].T @ h
+    t_rest = time.perf_counter() - t0
+    nblk = s // 2 + 1
+    t_solve = t_rhs + nblk * t_lu + iterations * (s * t_bs + t_rest)
+    return {"value": 1.0 / t_solve, "unit": "solves/s", "cores": 1, "composed": True,
+            "sample": (f"one thread: right-hand side {t_rhs:.2f} s, one {m}x{m} complex block LU {t_lu:.2f} s "
+                       f"(x {nblk}), one block solve {t_bs * 1e3:.1f} ms (x {s} per iteration), DFT pair + matvec "
+                       f"+ CGS2 {t_rest:.2f} s per iteration; composed to {iterations} iterations")}
+
+
+def bench_reference(args, rank, prob, workload):
+    """--impl reference: the CPU oracle (no GPU) timed on COMPLETE solves of the
+    workload, as many as fit in --reference-budget seconds (at least one, at most
+    --steps); `steps` is the number of complete solves timed.  A complete solve takes
+    about a minute, so --warmup is not run (the oracle has no warm-up effects beyond
+    the first numpy import, done before the clock starts)."""
+    if rank != 0:
+        return
+    import numpy  # noqa: F401  (import cost outside the timed solves)
+    solves = []
+    t_start = time.perf_counter()
+    while True:
+        r = oracle_complete_solve(prob, args.tol)
+        solves.append(r)
+        elapsed = time.perf_counter() - t_start
+        if len(solves) >= max(1, args.steps) or elapsed + r["seconds"] > args.reference_budget:
+            break
+    total = sum(r["seconds"] for r in solves)
+    t = total / len(solves)
+    v = 1.0 / t
+    cores = oracle_cores()
+    single = None
+    try:  # the single-thread leg, in a child process with one BLAS thread
+        env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+        out = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-single-thread",
+                              "--m", str(args.m), "--s", str(args.s), "--single-its", str(solves[-1]["iterations"])],
+                             env=env, capture_output=True, text=True, timeout=600)
+        single = json.loads(out.stdout.strip().splitlines()[-1])
+    except Exception as e:  # reported, never fatal
+        single = {"unavailable": f"{type(e).__name__}: {e}"}
+    stage = {k: round(sum(r[k] for r in solves) / len(solves), 3) for k in ("rhs_s", "factor_s", "fgmres_s")}
+    sample = (f"{len(solves)} complete oracle solve(s) of the workload (m={prob.m}, s={prob.s}): right-hand side, "
+              f"dense LAPACK LUs of all {solves[-1]['blocks']} Strang blocks, FGMRES(20) to a true residual of "
+              f"{args.tol:g} ({solves[-1]['iterations']} iterations); mean wall per stage {stage}")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": len(solves), "warmup": 0, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload,
+            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": sample,
+                             "composed": False},
+            "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "oracle_iterations": [r["iterations"] for r in solves],
+            "oracle_converged": all(r["converged"] for r in solves),
+            "oracle_stage_seconds": stage, "single_thread": single,
+            "note": (f"--steps {args.steps} / --warmup {args.warmup} requested; a complete oracle solve takes "
+                     f"{t:.0f} s, so the arm times complete solves for at most {args.reference_budget:.0f} s "
+                     f"(steps = solves timed) and runs no warm-up")}
+    print(json.dumps(line))
 
 
 # ---------------------------------------------------------------------------
 # batched workload: 64 independent instances per step
 # ---------------------------------------------------------------------------
 
-def bench_batch(args, world, rank, local_rank):
+def measure_batch(args, steps: int, warmup: int, sequential: bool = True, sample_clocks: bool = False,
+                  local_rank: int = 0) -> dict:
+    """The 64-instance batched workload (fde_inputs.config_batch): one step = assemble +
+    factor + solve of all instances in one fde_batch_* call sequence, inputs resident in
+    HBM.  Optionally the same instances one at a time through the single-problem API."""
     import numpy as np
     import torch
 
     import fde_inputs
     import paper_1305_6653_gb300 as fde
 
-    torch.cuda.set_device(local_rank)
     probs = fde_inputs.config_batch()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     outs = [torch.empty(p.n, dtype=torch.float64, device="cuda") for p in probs]
-    b = fde.FDEBatch(probs)
+    b = fde.FDEBatch(probs, device_inputs=True)
 
     def step():
-        b.assemble().factor(args.precision)
+        b.assemble().factor(args.batch_precision)
         _, st = b.solve(tol=args.tol, restart=20, maxit=400, outs=outs)
         return st
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     torch.cuda.synchronize()
     sampler = ClockSampler(local_rank)
-    if not args.no_clocks:
+    if sample_clocks:
         sampler.start()
     l0 = fde.fde_launch_count()
     times, stats = [], None
-    for _ in range(args.steps):
+    for _ in range(steps):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -317,40 +468,55 @@ def bench_batch(args, world, rank, local_rank):
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
     launches = fde.fde_launch_count() - l0
-    clocks = sampler.stop() if not args.no_clocks else None
+    clocks = sampler.stop() if sample_clocks else None
     b.close()
     ms = sum(times) / len(times)
-    value = world * len(probs) / (ms / 1e3)
-    # the same 64 instances one at a time through the single-problem API
-    t0 = time.perf_counter()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for pr, out in zip(probs, outs):
-        with fde.FDEProblem.from_inputs(pr) as p:
-            p.assemble().factor(args.precision)
-            p.solve(tol=args.tol, restart=20, maxit=400, out=out)
-    e1.record()
-    e1.synchronize()
-    seq_s = max(e0.elapsed_time(e1) / 1e3, time.perf_counter() - t0)
+    out = {"value": len(probs) / (ms / 1e3), "unit": "solves/s", "instances": len(probs), "steps": steps,
+           "warmup": warmup, "ms_per_step": ms, "per_step_ms": times, "precision": args.batch_precision,
+           "tol_true_residual": args.tol, "gpu_launches": launches, "clocks": clocks,
+           "iterations": [s_["iterations"] for s_ in stats],
+           "unknowns_total": int(sum(p.n for p in probs))}
+    if sequential:  # the same 64 instances one at a time through the single-problem API
+        t0 = time.perf_counter()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for pr, o in zip(probs, outs):
+            with fde.FDEProblem.from_inputs(pr, device_inputs=True) as p:
+                p.assemble().factor(args.batch_precision)
+                p.solve(tol=args.tol, restart=20, maxit=400, out=o)
+        e1.record()
+        e1.synchronize()
+        seq_s = max(e0.elapsed_time(e1) / 1e3, time.perf_counter() - t0)
+        out["sequential_single_api"] = {"value": len(probs) / seq_s, "unit": "solves/s", "seconds": seq_s}
     import oracle as O
     worst = 0.0
-    for pr, out in zip(probs, outs):
-        xs = out.cpu().numpy()
+    for pr, o in zip(probs, outs):
+        xs = o.cpu().numpy()
         bb = O.reduced_rhs(pr)
         worst = max(worst, float(np.linalg.norm(bb - O.matvec(pr, xs)) / np.linalg.norm(bb)))
+    out["worst_rel_residual_oracle_matvec"] = worst
+    return out
+
+
+def bench_batch(args, world, rank, local_rank):
+    import torch
+    torch.cuda.set_device(local_rank)
+    r = measure_batch(args, args.steps, args.warmup, sequential=True, sample_clocks=not args.no_clocks,
+                      local_rank=local_rank)
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-                "config": {"workload": "batch64_m255-2047_s64-256_etr3_gbdf3_gam4", "instances": len(probs),
-                           "unknowns_total": int(sum(p.n for p in probs)), "precision": args.precision,
+        line = {"metric": METRIC, "value": world * r["value"], "unit": "solves/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+                "data": "synthetic",
+                "config": {"workload": "batch64_m255-2047_s64-256_etr3_gbdf3_gam4", "instances": r["instances"],
+                           "unknowns_total": r["unknowns_total"], "precision": args.batch_precision,
                            "tol_true_residual": args.tol, "restart": 20,
                            "l2": "flushed (512 MiB write) before every timed step"},
-                "roofline": None, "gpu_launches": launches, "clocks": clocks,
-                "iterations": [s_["iterations"] for s_ in stats],
-                "sequential_single_api": {"value": len(probs) / seq_s, "unit": "solves/s", "seconds": seq_s},
-                "worst_rel_residual_oracle_matvec": worst, "per_step_ms": times}
+                "roofline": None, "gpu_launches": r["gpu_launches"], "clocks": r["clocks"],
+                "iterations": r["iterations"], "sequential_single_api": r["sequential_single_api"],
+                "worst_rel_residual_oracle_matvec": r["worst_rel_residual_oracle_matvec"],
+                "per_step_ms": r["per_step_ms"]}
         print(json.dumps(line))
 
 
@@ -370,7 +536,7 @@ def bench_many_rhs(args, world, rank, local_rank):
     probs = fde_inputs.config_many_rhs(count=count, m=args.m, s=args.s)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     outs = [torch.empty(p.n, dtype=torch.float64, device="cuda") for p in probs]
-    b = fde.FDEBatch(probs).share_operator()
+    b = fde.FDEBatch(probs, device_inputs=True).share_operator()
 
     def step():
         b.assemble().factor(args.precision)
@@ -404,7 +570,7 @@ def bench_many_rhs(args, world, rank, local_rank):
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record()
     for pr, out in zip(probs, outs):
-        with fde.FDEProblem.from_inputs(pr) as p:
+        with fde.FDEProblem.from_inputs(pr, device_inputs=True) as p:
             p.assemble().factor(args.precision)
             p.solve(tol=args.tol, restart=20, maxit=400, out=out)
     e1.record()
@@ -437,20 +603,23 @@ def bench_many_rhs(args, world, rank, local_rank):
 # precision study: one m=4095/s=128 instance, every preconditioner precision
 # ---------------------------------------------------------------------------
 
-def bench_precision(args, world, rank, local_rank):
+def measure_precision(args, steps: int, warmup: int, precisions=("fp64", "fp32", "tf32", "tf32x3", "bf16"),
+                      sample_clocks: bool = False, local_rank: int = 0) -> dict:
+    """The precision study: one m=4095, s=128, alpha=1.9, GBDF3 instance, solved to a true
+    residual of 1e-8 (the tolerance it is specified at) with each factor precision; one
+    step = assemble + factor + solve.  TF32 and BF16 factors do not precondition it
+    (kappa(B_k) u >> 1): they are run to maxit = 100 and reported as not converged."""
     import numpy as np
     import torch
 
     import fde_inputs
     import paper_1305_6653_gb300 as fde
 
-    torch.cuda.set_device(local_rank)
     prob = fde_inputs.config_precision()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     xbuf = torch.empty(prob.n, dtype=torch.float64, device="cuda")
     p = fde.FDEProblem.from_inputs(prob, device_inputs=True)
-
-    tol = 1e-8  # the tolerance this configuration is specified at
+    tol = 1e-8
 
     def step(precision):
         p.assemble().factor(precision)
@@ -460,13 +629,13 @@ def bench_precision(args, world, rank, local_rank):
     variants, sols = {}, {}
     l0 = fde.fde_launch_count()
     sampler = ClockSampler(local_rank)
-    if not args.no_clocks:
+    if sample_clocks:
         sampler.start()
-    for prec in ("fp64", "fp32", "tf32", "tf32x3", "bf16"):
-        for _ in range(args.warmup):
+    for prec in precisions:
+        for _ in range(warmup):
             step(prec)
         times, st = [], None
-        for _ in range(args.steps):
+        for _ in range(steps):
             flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -477,31 +646,41 @@ def bench_precision(args, world, rank, local_rank):
             times.append(e0.elapsed_time(e1))
         ms = sum(times) / len(times)
         sols[prec] = xbuf.cpu().numpy()
-        variants[prec] = {"solves_per_s": 1e3 / ms, "ms_per_step": ms, "iterations": st["iterations"],
-                          "rel_residual": st["rel_residual"], "converged": st["status"] == 0}
-    clocks = sampler.stop() if not args.no_clocks else None
+        variants[prec] = {"solves_per_s": 1e3 / ms, "ms_per_step": ms, "steps": steps, "warmup": warmup,
+                          "iterations": st["iterations"], "rel_residual": st["rel_residual"],
+                          "converged": st["status"] == 0}
+    clocks = sampler.stop() if sample_clocks else None
     launches = fde.fde_launch_count() - l0
     p.close()
-    ref = sols["fp64"]
-    for prec, v in variants.items():
-        v["rel_diff_vs_gpu_fp64"] = float(np.linalg.norm(sols[prec] - ref) / np.linalg.norm(ref))
-    # headline: the fastest variant that reached the tolerance (TF32 / BF16 factors do
-    # not precondition this configuration: kappa(B_k) u >> 1)
+    if "fp64" in sols:
+        ref = sols["fp64"]
+        for prec, v in variants.items():
+            v["rel_diff_vs_gpu_fp64"] = float(np.linalg.norm(sols[prec] - ref) / np.linalg.norm(ref))
     conv = [k for k, v in variants.items() if v["converged"]]
-    best = max(conv, key=lambda k: variants[k]["solves_per_s"]) if conv else "fp64"
-    head = variants[best]
+    best = max(conv, key=lambda k: variants[k]["solves_per_s"]) if conv else None
+    return {"workload": f"precision_m{prob.m}_s{prob.s}_gbdf3_alpha1.9", "m": prob.m, "s": prob.s,
+            "unknowns": prob.n, "tol_true_residual": tol, "variants": variants, "fastest_converged": best,
+            "gpu_launches": launches, "clocks": clocks,
+            "note": "rel_diff_vs_gpu_fp64 compares with the FP64 GPU solve of the same run; the error of every "
+                    "variant against the CPU oracle is checked by tests/test_gpu_precision.py"}
+
+
+def bench_precision(args, world, rank, local_rank):
+    import torch
+    torch.cuda.set_device(local_rank)
+    r = measure_precision(args, args.steps, args.warmup, sample_clocks=not args.no_clocks, local_rank=local_rank)
+    best = r["fastest_converged"] or "fp64"
+    head = r["variants"][best]
     if rank == 0:
         line = {"metric": METRIC, "value": world * head["solves_per_s"], "unit": "solves/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
                 "data": "synthetic",
-                "config": {"workload": f"precision_m{prob.m}_s{prob.s}_gbdf3_alpha1.9", "m": prob.m, "s": prob.s,
-                           "unknowns": prob.n, "precision": best, "tol_true_residual": tol,
-                           "restart": 20, "l2": "flushed (512 MiB write) before every timed step"},
-                "roofline": None, "gpu_launches": launches, "clocks": clocks,
-                "variants": variants,
-                "note": "rel_diff_vs_gpu_fp64 compares with the FP64 GPU solve of the same run; the error of "
-                        "every variant against the CPU oracle is checked by tests/test_gpu_precision.py"}
+                "config": {"workload": r["workload"], "m": r["m"], "s": r["s"], "unknowns": r["unknowns"],
+                           "precision": best, "tol_true_residual": r["tol_true_residual"], "restart": 20,
+                           "l2": "flushed (512 MiB write) before every timed step"},
+                "roofline": None, "gpu_launches": r["gpu_launches"], "clocks": r["clocks"],
+                "variants": r["variants"], "note": r["note"]}
         print(json.dumps(line))
 
 
@@ -752,7 +931,7 @@ def bench_learned(args, world, rank, local_rank):
     its_train = []
     for c0 in range(0, args.train, 64):
         chunk = [fde_inputs.config_learned_family(seed=i, m=m, s=s) for i in range(c0, min(c0 + 64, args.train))]
-        with fde.FDEBatch(chunk) as b:
+        with fde.FDEBatch(chunk, device_inputs=True) as b:
             b.assemble().factor(args.precision)
             xs, st = b.solve(tol=args.tol)
             its_train += [x_["iterations"] for x_ in st]
@@ -817,6 +996,42 @@ def bench_learned(args, world, rank, local_rank):
 # main
 # ---------------------------------------------------------------------------
 
+def measure_peaks() -> dict:
+    """Microbenchmarks of the peaks that MEASURED_PEAKS.json lacks, on this GPU: TF32
+    tensor-core GEMM (float32 matmul with TF32 allowed), FP32 CUDA-core GEMM (TF32
+    off) and FP64 GEMM, 8192^3 / 8192^3 / 4096^3, best of several CUDA-event timings
+    (2 N^3 flops).  cuBLAS through torch: a measurement of the hardware, not a part of
+    the solver."""
+    import torch
+
+    def best(n, dtype, reps, tf32):
+        old = torch.backends.cuda.matmul.allow_tf32
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        try:
+            a = torch.randn(n, n, device="cuda", dtype=dtype)
+            b = torch.randn(n, n, device="cuda", dtype=dtype)
+            c = a @ b
+            torch.cuda.synchronize()
+            t = []
+            for _ in range(reps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                torch.matmul(a, b, out=c)
+                e1.record()
+                e1.synchronize()
+                t.append(e0.elapsed_time(e1))
+            del a, b, c
+            return 2.0 * n ** 3 / (min(t) / 1e3) / 1e12
+        finally:
+            torch.backends.cuda.matmul.allow_tf32 = old
+
+    return {"tf32_tflops": best(8192, torch.float32, 8, True), "fp32_tflops": best(8192, torch.float32, 3, False),
+            "fp64_tflops": best(4096, torch.float64, 3, False),
+            "how": "torch.matmul (cuBLAS) best of 3-8 CUDA-event timings: float32 8192^3 with TF32 on / off, "
+                   "float64 4096^3; 2 N^3 flops"}
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -825,6 +1040,9 @@ def main():
 
     import fde_inputs
 
+    if args.oracle_single_thread:  # child process of the reference arm (one BLAS thread)
+        print(json.dumps(oracle_single_thread_sample(fde_inputs.config_scale(args.m, args.s), args.single_its)))
+        return
     if args.config == "batch" and args.impl == "ours":
         return bench_batch(args, world, rank, local_rank)
     if args.config == "learned" and args.impl == "ours":
@@ -843,27 +1061,11 @@ def main():
     workload = {"workload": f"scale_m{args.m}_s{args.s}_gbdf5_alpha1.8_variable_d", "m": args.m, "s": args.s,
                 "unknowns": args.m * args.s, "scheme": "GBDF5", "alpha": 1.8, "d": "d+=1+x, d-=2-x",
                 "tol_true_residual": args.tol, "restart": 20, "precision": args.precision,
+                "arnoldi_matvec": args.matvec if args.matvec == "fp64" else f"fp32 (relax {args.relax:g})",
                 "l2": "flushed (512 MiB write) before every timed step; factors (4.3 GB fp32) exceed L2"}
 
     if args.impl == "reference":
-        if rank != 0:
-            return
-        steps = []
-        sample = None
-        for i in range(args.warmup + args.steps):
-            sample = oracle_sample(prob, iterations=ORACLE_ITERATIONS)
-            if i >= args.warmup:
-                steps.append(sample["seconds_per_solve"])
-        t = sum(steps) / len(steps)
-        v = 1.0 / t
-        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload,
-                "cpu_baseline": {"value": v, "unit": "solves/s", "cores": sample["cores"], "kind": "oracle",
-                                 "sample": sample["sample"]},
-                "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-        print(json.dumps(line))
-        return
+        return bench_reference(args, rank, prob, workload)
 
     import numpy as np
     import torch
@@ -889,20 +1091,26 @@ def main():
 
     p = fde.FDEProblem.from_inputs(prob, device_inputs=True)
 
-    def step(precision):
+    def step(precision, matvec=None):
         p.assemble()
         p.factor(precision)
-        _, st = p.solve(tol=args.tol, restart=20, maxit=400, out=xbuf)
+        mv = args.matvec if matvec is None else matvec
+        _, st = p.solve(tol=args.tol, restart=20, maxit=400, out=xbuf, matvec=mv, relax=args.relax)
         return st
 
+    # the block-solve timer is selected before the warm-up, so that the iteration graphs
+    # the warm-up captures already carry its event-record nodes
+    p.profile_select(["trsv"])
     for _ in range(args.warmup):
         step(args.precision)
     barrier()
 
+    # ---- timed region: the product path (iteration graphs replayed), with CUDA-event
+    # pairs around the block solves only, recorded inside those graphs
     sampler = ClockSampler(local_rank)
     if not args.no_clocks:
         sampler.start()
-    p.profile(True)
+    p.profile_select(["trsv"])  # same selection (graphs kept): clears the warm-up's records
     launches0 = fde.fde_launch_count()
     per_step = []
     stats = []
@@ -918,72 +1126,83 @@ def main():
         per_step.append(e0.elapsed_time(e1))
     barrier()
     launches = fde.fde_launch_count() - launches0
-    prof = p.profile_read()
-    p.profile(False)
+    timed_prof = p.profile_read()
+    p.profile_select([])
     clocks = sampler.stop() if not args.no_clocks else None
 
     total_ms = rank_max_ms(sum(per_step), dist, "cuda")
     ms_per_step = total_ms / args.steps
     value = world * args.steps / (total_ms / 1e3)
 
-    # roofline of the dominant kernel
+    # ---- untimed profiled pass: every stage with its own event pair (direct launches)
+    prof = {}
+    if args.profile_steps > 0:
+        p.profile(True)
+        for _ in range(args.profile_steps):
+            flush.zero_()
+            step(args.precision)
+        torch.cuda.synchronize()
+        prof = p.profile_read()
+        p.profile(False)
+
+    measured = measure_peaks() if rank == 0 else None
+    tf32_peak = measured["tf32_tflops"] if measured else bf16_peak * 1.1 / 2.25
+    fp64_peak = measured["fp64_tflops"] if measured else FP64_PEAK_TFLOPS
+
+    # roofline of the dominant kernel, the block solves: algorithmic bytes per launch over
+    # their mean CUDA-event duration in the timed region
     mp = (prob.m + 63) // 64 * 64
     nblk = prob.s // 2 + 1
     esz = 8 if args.precision == "fp64" else 4
-    # The tensor-core LU runs its interior updates on a second stream beside the panel
-    # chain, so the event sums of the LU stages include overlap; the dominant kernel is
-    # taken among the single-stream stages (the ncu launch list agrees: the block
-    # solves lead, the trailing update follows).
-    overlapped = {"lu_tc", "lu_diag", "lu_pack", "lu_panel_tc", "form"} if args.precision in (
-        "tf32", "bf16", "tf32x3") else set()
-    dom = max((kv for kv in prof.items() if kv[0] not in overlapped), key=lambda kv: kv[1][0])
-    name, (dom_ms, dom_n) = dom
-    roof = None
-    if name == "trsv":
-        per_launch = trsv_bytes(mp, nblk, esz)
-        ach = per_launch / (dom_ms / dom_n / 1e3) / 1e9
-        # DRAM traffic of one launch: ncu's dram__bytes_read.sum + dram__bytes_write.sum on the
-        # m=1023, s=256 case (FP32 factors) was 1.034 x its algorithmic bytes; the bytes grow with
-        # the factor planes, so a launch here moves 1.034 x its algorithmic bytes
-        traffic = TRSV_TRAFFIC_RATIO * per_launch if esz == 4 else None
-        roof = {"kernel": "block_trsv_kernel", "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
-                "frac": ach / hbm_peak, "traffic": traffic, "peak_kind": peak_kind,
-                "algorithmic_bytes_per_launch": per_launch,
-                "traffic_source": "ncu capture at m=1023, s=256 scaled by the factor bytes" if traffic else None}
-    elif name == "lu_update" and args.precision in ("fp32", "fp64"):
-        flops = lu_update_flops(mp, nblk) * args.steps
-        ach = flops / (dom_ms / 1e3) / 1e12
-        peak = FP32_ALU_PEAK_TFLOPS if args.precision == "fp32" else 1.25
-        roof = {"kernel": "lu_update_kernel", "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": None,
-                "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz" if args.precision == "fp32"
-                else "nominal FP64", "algorithmic_flops_per_launch": flops / max(dom_n, 1)}
-    elif name == "lu_tc":
-        flops = tc_update_flops(mp, nblk) * args.steps
-        if args.precision == "tf32x3":
-            flops *= 3  # three TF32 products per complex multiply-add
-        ach = flops / (dom_ms / 1e3) / 1e12
-        ratio = 1.1 / 2.25 if args.precision in ("tf32", "tf32x3") else 1.0
-        peak = bf16_peak * ratio
-        roof = {"kernel": "lu_update_tc2_kernel + lu_update_tc2p_kernel", "bound": "tensor", "achieved": ach, "peak": peak,
-                "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
-                "peak_kind": f"{peak_kind} bf16 x nominal {args.precision}/bf16 ratio",
-                "algorithmic_flops_per_launch": flops / max(dom_n, 1)}
-    # the tensor-core update is reported beside the dominant kernel whenever it ran
+    dom_ms, dom_n = timed_prof["trsv"]
+    per_launch = trsv_bytes(mp, nblk, esz)
+    ach = per_launch / (dom_ms / dom_n / 1e3) / 1e9
+    # DRAM traffic of one launch: ncu's dram__bytes_read.sum + dram__bytes_write.sum on the
+    # m=1023, s=256 case (FP32 factors) was 1.034 x its algorithmic bytes; the bytes grow with
+    # the factor planes, so a launch here moves 1.034 x its algorithmic bytes
+    traffic = TRSV_TRAFFIC_RATIO * per_launch if esz == 4 else None
+    roof = {"kernel": "block_trsv_kernel", "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+            "frac": ach / hbm_peak, "traffic": traffic, "peak_kind": peak_kind,
+            "algorithmic_bytes_per_launch": per_launch, "launches_timed": dom_n,
+            "timing": "CUDA events recorded inside the replayed iteration graphs, over the timed region",
+            "traffic_source": "ncu capture at m=1023, s=256 scaled by the factor bytes" if traffic else None}
+    # the tensor-core update beside it (profiled pass)
     tc_line = None
     if prof.get("lu_tc", (0, 0))[0] > 0:
         tms, tn = prof["lu_tc"]
-        tfl = tc_update_flops(mp, nblk) * args.steps * (3 if args.precision == "tf32x3" else 1)
-        ratio = 1.1 / 2.25 if args.precision in ("tf32", "tf32x3") else 1.0
-        tbytes = tc_update_bytes(mp, nblk) * args.steps
-        tc_line = {"kernel": "lu_update_tc2_kernel (cross tiles) + lu_update_tc2p_kernel (interior row pairs)", "launches_per_step": tn // args.steps,
-                   "timing": "CUDA events on both LU streams; the interior updates overlap the panel chain",
-                   "ms_per_step": tms / args.steps, "tflops": tfl / (tms / 1e3) / 1e12,
-                   "tensor_peak": bf16_peak * ratio, "c_tile_gbs": tbytes / (tms / 1e3) / 1e9, "hbm_peak": hbm_peak}
+        nps = args.profile_steps
+        tfl = tc_update_flops(mp, nblk) * nps * (3 if args.precision == "tf32x3" else 1)
+        tpeak = tf32_peak if args.precision in ("tf32", "tf32x3") else bf16_peak
+        tbytes = tc_update_bytes(mp, nblk) * nps
+        tc_line = {"kernel": "lu_update_tc2_kernel (cross tiles) + lu_update_tc2p_kernel (interior row pairs)",
+                   "launches_per_step": tn // nps,
+                   "timing": "profiled pass; CUDA events on both LU streams (the interior updates overlap the "
+                             "panel chain)",
+                   "ms_per_step": tms / nps, "tflops": tfl / (tms / 1e3) / 1e12,
+                   "tensor_peak": tpeak, "tensor_peak_kind": "measured (cuBLAS TF32 GEMM, this run)" if measured
+                   and args.precision in ("tf32", "tf32x3") else "measured bf16",
+                   "c_tile_gbs": tbytes / (tms / 1e3) / 1e9, "hbm_peak": hbm_peak}
+    matvec_line = None
+    nps_ = max(args.profile_steps, 1)
+    if prof.get("matvec", (0, 0))[1] > 0:
+        mms, mn = prof["matvec"]
+        L = 1
+        while L < 2 * prob.m:
+            L *= 2
+        mfl = matvec_flops(prob.m, prob.s, L, prob.mu) * mn
+        matvec_line = {"kernel": "st_matvec_kernel", "ms_per_launch": mms / mn, "launches_per_step": mn // nps_,
+                       "tflops": mfl / (mms / 1e3) / 1e12, "timing": "profiled pass"}
+        if args.matvec == "fp64":  # every launch is the FP64 product: bound by the FP64 rate
+            matvec_line.update({"bound": "fp64 alu", "fp64_peak": fp64_peak,
+                                "frac": mfl / (mms / 1e3) / 1e12 / fp64_peak})
+        else:
+            matvec_line["note"] = ("mixed: FP32 Arnoldi products and FP64 restart residuals; no single-precision "
+                                   "roofline")
     path_roof = path_roofline(prob.m, prob.s, mp, esz, stats[-1]["iterations"], args.precision, bf16_peak,
-                              hbm_peak, ms_per_step)
-    stage_ms = {k: round(v[0] / args.steps, 4) for k, v in prof.items()}
-    stage_n = {k: v[1] // args.steps for k, v in prof.items()}
+                              hbm_peak, ms_per_step, tf32_peak=tf32_peak, fp64_peak=fp64_peak)
+    nps = max(args.profile_steps, 1)
+    stage_ms = {k: round(v[0] / nps, 4) for k, v in prof.items()}
+    stage_n = {k: v[1] // nps for k, v in prof.items()}
 
     # accuracy of the last solution: true residual with the oracle's independent matvec
     import oracle as O
@@ -992,24 +1211,30 @@ def main():
     bor = O.reduced_rhs(prob, J=J)
     res_oracle = float(np.linalg.norm(bor - O.matvec(prob, xs, J=J)) / np.linalg.norm(bor))
 
-    # plain FP64 PGMRES on the same workload (the comparison the metric names)
+    # plain FP64 PGMRES on the same workload (the comparison the metric names): one
+    # FP64 warm-up solve (allocates the 8.7 GB of FP64 factors), then timed solves
     plain = None
     if args.fp64_steps > 0:
+        step("fp64", "fp64")
         tms, st64 = [], None
         for _ in range(args.fp64_steps):
             flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record()
-            st64 = step("fp64")
+            st64 = step("fp64", "fp64")
             e1.record()
             e1.synchronize()
             tms.append(e0.elapsed_time(e1))
+        tms_sorted = sorted(tms)
         plain = {"value": 1e3 / (sum(tms) / len(tms)), "unit": "solves/s", "ms_per_step": sum(tms) / len(tms),
-                 "steps": len(tms), "iterations": st64["iterations"], "rel_residual": st64["rel_residual"]}
+                 "ms_median": tms_sorted[len(tms) // 2], "per_step_ms": tms, "steps": len(tms), "warmup": 1,
+                 "iterations": st64["iterations"], "rel_residual": st64["rel_residual"],
+                 "speedup_of_mixed": (sum(tms) / len(tms)) / ms_per_step}
     p.close()
 
-    # end-to-end through the public API from pinned host buffers
+    # end-to-end through the C ABI from pinned host buffers: create copies the inputs in,
+    # pgmres_solve copies the solution out (host x_out), destroy
     e2e = None
     if args.e2e_steps > 0:
         host = {k: torch.from_numpy(np.ascontiguousarray(getattr(prob, k))).pin_memory()
@@ -1023,9 +1248,8 @@ def main():
                                dplus=host["dplus"].numpy(), dminus=host["dminus"].numpy(), u0=host["u0"].numpy(),
                                f=host["f"].numpy(), family=prob.family, mu=prob.mu, device_inputs=False)
             q.assemble().factor(args.precision)
-            x, _ = q.solve(tol=args.tol, restart=20, maxit=400)
-            xh.copy_(x, non_blocking=True)
-            torch.cuda.synchronize()
+            q.solve(tol=args.tol, restart=20, maxit=400, out=xh, matvec=args.matvec,
+                    relax=args.relax)  # returns after the copy to xh
             q.close()
 
         e2e_step()
@@ -1041,11 +1265,23 @@ def main():
         wall = time.perf_counter() - t0
         ev = e0.elapsed_time(e1) / 1e3
         e2e = {"value": world * args.e2e_steps / max(ev, wall), "unit": "solves/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "steps": args.e2e_steps}
+               "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
+               "path": "fde_problem_create (host desc) -> bvm_assemble -> strang_precond_factor -> pgmres_solve "
+                       "(host x_out) -> fde_problem_destroy"}
+
+    # the batched and precision legs (the metric's "mixed+batched"), driver-visible
+    batch = precision = None
+    if not args.no_extras and world == 1:
+        batch = measure_batch(args, steps=3, warmup=1, sequential=False)
+        precision = measure_precision(args, steps=1, warmup=1,
+                                      precisions=("tf32x3", "fp32", "tf32", "bf16", "fp64"))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = oracle_sample(prob, iterations=ORACLE_ITERATIONS)
+        its = plain["iterations"] if plain else 20
+        cpu = oracle_sample(prob, iterations=its,
+                            its_source="the plain FP64 solve's iteration count in this run" if plain
+                            else "assumed")
         cpu.pop("seconds_per_solve", None)
 
     if rank == 0:
@@ -1055,9 +1291,14 @@ def main():
             "vs_baseline": None, "dtype": "f32+f64" if args.precision != "fp64" else "f64", "data": "synthetic",
             "config": workload, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clocks, "iterations": [s["iterations"] for s in stats],
+            "matvecs_fp32": [s["matvecs_fp32"] for s in stats],
             "rel_residual": stats[-1]["rel_residual"], "rel_residual_oracle_matvec": res_oracle,
-            "plain_fp64": plain, "tensor_core_update": tc_line, "path_roofline": path_roof, "stage_ms_per_step": stage_ms,
-            "stage_launches_per_step": stage_n,
+            "plain_fp64": plain, "batch64": batch, "precision_m4095": precision,
+            "tensor_core_update": tc_line, "matvec": matvec_line, "path_roofline": path_roof,
+            "peaks_measured": measured,
+            "stage_ms_per_step": stage_ms, "stage_launches_per_step": stage_n,
+            "stage_split_source": f"untimed profiled pass of {args.profile_steps} solves after the timed region "
+                                  "(every stage with its own event pair, direct launches)",
             "per_step_ms": per_step,
             # setup-excluded rate: the GMRES phase alone (pgmres_solve's device time)
             "gmres_phase": {"ms_per_solve": sum(s["ms_solve"] for s in stats) / len(stats),

@@ -52,6 +52,7 @@ __all__ = [
     "config_precision",
     "config_learned_family",
     "instance_seed",
+    "check_sample",
 ]
 
 # Scheme name -> (family, mu).  The family names follow the BVM literature the
@@ -289,6 +290,17 @@ def config_many_rhs(count: int = 16, m: int = 2047, s: int = 256, base_seed: int
         out.append(dataclasses.replace(base, f=np.ascontiguousarray(f), u0=base.u0 * (1.0 - 0.5 * r / count),
                                        name=f"rhs{r}_m{m}_s{s}", meta={"c": c, "a": a}))
     return out
+
+
+def check_sample(n: int, seed: int, count: int = 128, projections: int = 8):
+    """Seeded positions and probe vectors for comparing two length-n solutions that are
+    too large to store: `count` distinct indices in [0, n) and `projections` standard
+    normal vectors of length n (E <g, v>^2 = |v|^2, so the probes estimate the 2-norm
+    of a difference).  Plain random numbers; no arithmetic of the method."""
+    rng = np.random.default_rng(seed + 11_000_000)
+    idx = np.sort(rng.choice(n, size=min(count, n), replace=False))
+    probes = rng.standard_normal((projections, n))
+    return idx, probes
 
 
 def config_learned_family(seed: int, m: int = 1023, s: int = 256) -> Problem:

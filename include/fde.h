@@ -105,6 +105,13 @@ typedef struct {
     int restart;   /* Krylov subspace size per cycle (the paper uses 20) */
     int maxit;     /* cap on the total number of inner iterations */
     int reorth;    /* 1: classical Gram-Schmidt with one re-orthogonalisation (CGS2); 0: CGS */
+    int matvec_precision; /* FDE_FP64 (0): every product M z in FP64.  FDE_FP32: the Arnoldi
+                   * products w = M z_j apply the Toeplitz part J (Sec. 2.1, the FFT of the
+                   * circulant embedding) in FP32 while the cycle's Givens estimate of
+                   * ||r|| / ||b|| is above `relax`, in FP64 below it (an inexact-Krylov
+                   * relaxation: early products may be inexact, late ones may not); the
+                   * restart's true residual is always FP64. */
+    double relax;  /* the switch-over for FDE_FP32 (0: FP32 in every Arnoldi product) */
 } fde_pgmres_opts;
 
 /* Statistics returned by pgmres_solve. */
@@ -117,7 +124,7 @@ typedef struct {
     double rel_residual_estimate; /* final Givens estimate of the last cycle */
     double ms_solve;     /* device time of the solve (CUDA events) */
     int x0_rejected;     /* 1: the initial guess had ||b - M x0|| > ||b|| and x = 0 was used */
-    int reserved;
+    int matvecs_fp32;    /* Arnoldi products that used the FP32 Toeplitz apply */
 } fde_stats;
 
 typedef struct fde_problem fde_problem;
@@ -169,10 +176,14 @@ int fde_precond_none(fde_problem* p);
 
 /* Solve M u = b by flexible GMRES(restart) right-preconditioned with S (or with the
  * BCCB preconditioner after bccb_precond_setup, or none after fde_precond_none).
- * x0: device, length s*m initial guess, or NULL for zero; a guess whose residual
- * exceeds ||b|| (or is not finite) is replaced by zero (stats->x0_rejected).  x_out: device, length
- * s*m (may alias x0).  st: host, may be NULL.  On FDE_ERR_NOT_CONVERGED x_out
- * holds the last iterate.  Requires strang_precond_factor or bccb_precond_setup.  Errors: FDE_ERR_ARG,
+ * x0: length s*m initial guess (u_1..u_s of eq. (1.10), time-major), or NULL for
+ * zero; a guess whose residual exceeds ||b|| (or is not finite) is replaced by zero
+ * (stats->x0_rejected).  x_out: length s*m (may alias x0).  Both are device pointers
+ * when the problem was created with desc->device_ptrs = 1 and host pointers when it
+ * was created with 0; in the host case the library copies x0 in and the solution out
+ * on the problem's stream (a device copy of n doubles, allocated at the first such
+ * solve, is owned by the problem) and the call returns after the copy.  st: host,
+ * may be NULL.  On FDE_ERR_NOT_CONVERGED x_out holds the last iterate.  Requires strang_precond_factor or bccb_precond_setup.  Errors: FDE_ERR_ARG,
  * FDE_ERR_STATE, FDE_ERR_NOT_CONVERGED, FDE_ERR_NAN, FDE_ERR_CUDA. */
 int pgmres_solve(fde_problem* p, const fde_pgmres_opts* opts, const double* x0, double* x_out,
                  fde_stats* st);
@@ -204,7 +215,9 @@ int fde_batch_assemble(fde_batch* b);
 int fde_batch_factor(fde_batch* b, int precision);
 
 /* Solve every instance from a zero initial guess.  x_out: host array of count
- * device pointers, entry i of length s_i*m_i, written with u_1..u_s.  stats: host
+ * pointers, entry i of length s_i*m_i, written with u_1..u_s: a device pointer when
+ * instance i was created with device_ptrs = 1, a host pointer when with 0 (copied
+ * out on the batch's stream before the call returns).  stats: host
  * array of count entries (may be NULL); ms_solve is the batch's total time.
  * Returns FDE_OK when every instance met the tolerance, else the first failing
  * code (each instance's own code is in stats[i].status). */
@@ -276,6 +289,14 @@ void fde_nop_destroy(fde_nop* n);
  * Requires bvm_assemble.  Errors: FDE_ERR_STATE, FDE_ERR_CUDA. */
 int fde_matvec(fde_problem* p, const double* z, double* y);
 
+/* y = M z like fde_matvec, with the Toeplitz apply J w of every time row in FP32
+ * (Sec. 2.1: both FFTs of the circulant embedding and the symbol product); the BVM
+ * band sums, the A-band part and y are FP64.  The product pgmres_solve uses for the
+ * relaxed Arnoldi steps of opts->matvec_precision = FDE_FP32.  Problems with time-
+ * dependent coefficients use the FP64 product.  z, y: device, length s*m, must not
+ * alias.  Requires bvm_assemble.  Errors: FDE_ERR_STATE, FDE_ERR_CUDA. */
+int fde_matvec_fp32(fde_problem* p, const double* z, double* y);
+
 /* z = S^{-1} r with the current factors (Sec. 3.2): FFT along time, the s/2+1
  * block solves, inverse FFT.  r, z: device, length s*m (may alias).  Requires
  * strang_precond_factor.  Errors: FDE_ERR_STATE, FDE_ERR_CUDA. */
@@ -296,7 +317,8 @@ int fde_precond_apply(fde_problem* p, const double* r, double* z);
  * call's contents (each call overwrites everything it reads), so calls whose GPU
  * work overlaps -- on different streams or problems -- race and must be
  * serialised by the caller.  r, z: device, length s*m (may alias).  Requires
- * strang_precond_factor.  Errors: FDE_ERR_ARG, FDE_ERR_STATE, FDE_ERR_CUDA. */
+ * strang_precond_factor (checked first: FDE_ERR_STATE before the size check, which
+ * uses the factor precision).  Errors: FDE_ERR_ARG, FDE_ERR_STATE, FDE_ERR_CUDA. */
 int fde_precond_apply_noalloc(fde_problem* p, const double* r, double* z);
 
 /* Copy the assembled right-hand side b (device, length s*m).  Requires
@@ -339,8 +361,16 @@ int fde_problem_sizes(const fde_problem* p, int* m, int* s, int* nblocks);
  * Errors: FDE_ERR_ARG. */
 int fde_profile_enable(fde_problem* p, int on);
 
+/* Time only the stages whose bit (1 << FDE_STAGE_x) is set in stage_mask, without
+ * changing how the solver runs: the GMRES inner iterations keep replaying their
+ * CUDA graphs, and the event pairs around the selected stages are recorded inside
+ * those graphs (event-record nodes) and read after each replay.  Clears previous
+ * records and turns fde_profile_enable's full profiler off; stage_mask 0 stops
+ * recording.  Errors: FDE_ERR_ARG (NULL problem, bits beyond FDE_NUM_STAGES). */
+int fde_profile_select(fde_problem* p, unsigned stage_mask);
+
 /* Total device time (ms, summed over launches) and number of launches recorded
- * for one stage since fde_profile_enable.  Synchronises the problem's stream.
+ * for one stage since fde_profile_enable or fde_profile_select.  Synchronises the problem's stream.
  * Errors: FDE_ERR_ARG, FDE_ERR_CUDA. */
 int fde_profile_read(fde_problem* p, int stage, double* total_ms, int* launches);
 

@@ -91,12 +91,28 @@ def fde_precond_apply(h, r_ptr: int, z_ptr: int) -> None:
 
 # ---- convenience object ------------------------------------------------------
 
+def _as_host_vector(a, n):
+    """A contiguous float64 CPU tensor of length n (moved from the device if needed)."""
+    torch = _torch()
+    t = torch.as_tensor(a, dtype=torch.float64)
+    if t.is_cuda:
+        t = t.cpu()
+    t = t.contiguous().reshape(-1)
+    if t.numel() != n:
+        raise ValueError(f"expected {n} values, got {t.numel()}")
+    return t
+
+
 class FDEProblem:
     """One instance of eq. (1.1) on the device.
 
     Inputs (dplus, dminus, u0, f) may be numpy arrays (host, copied by the
-    library) or CUDA float64 tensors (device).  Vectors returned are CUDA
-    float64 tensors of length s*m, time-major (u_1 .. u_s).
+    library) or CUDA float64 tensors (device).  The solve vectors follow the
+    inputs (the desc's device_ptrs): a problem built from device tensors takes
+    and returns CUDA float64 tensors, one built from host arrays takes and
+    returns CPU float64 tensors (the library copies them on its stream).  The
+    step-level vectors (matvec, precond_apply, rhs) are CUDA tensors; all are
+    length s*m, time-major (u_1 .. u_s).
     """
 
     def __init__(self, *, m, s, alpha, xL, xR, t0, T, dplus, dminus, u0, f, family, mu, stream=None,
@@ -122,6 +138,7 @@ class FDEProblem:
 
         if device_inputs is None:
             device_inputs = isinstance(u0, torch.Tensor) and u0.is_cuda
+        self.device_ptrs = bool(device_inputs)
         self.desc = FdeProblemDesc(self.m, self.s, float(alpha), float(xL), float(xR), float(t0), float(T),
                                    ptr(dplus), ptr(dminus), 0.0, 0.0, fam, int(mu), ptr(u0), ptr(f),
                                    1 if device_inputs else 0, ptr(dplus_t), ptr(dminus_t))
@@ -159,10 +176,27 @@ class FDEProblem:
         bccb_precond_setup(self.h, modified, precision)
         return self
 
-    def solve(self, tol=1e-10, restart=20, maxit=1000, reorth=1, x0=None, out=None, raise_on_error=True):
+    def solve(self, tol=1e-10, restart=20, maxit=1000, reorth=1, x0=None, out=None, raise_on_error=True,
+              matvec="fp64", relax=0.0):
+        """pgmres_solve (matvec="fp32": the Arnoldi products' Toeplitz apply in FP32 while
+        the residual estimate is above relax, see fde_pgmres_opts).  Device problems: x0 / out are CUDA tensors.  Host problems:
+        x0 / out are CPU tensors (a CUDA x0 is copied to the host first, so that the
+        library receives the host pointer its desc declared)."""
         torch = _torch()
-        x = out if out is not None else torch.empty(self.n, dtype=torch.float64, device="cuda")
-        opts = FdePgmresOpts(float(tol), int(restart), int(maxit), int(reorth))
+        if self.device_ptrs:
+            x = out if out is not None else torch.empty(self.n, dtype=torch.float64, device="cuda")
+            if not x.is_cuda:
+                raise ValueError("this problem was created from device inputs: out must be a CUDA tensor")
+            if x0 is not None:
+                x0 = torch.as_tensor(x0, dtype=torch.float64, device="cuda").contiguous()
+        else:
+            x = out if out is not None else torch.empty(self.n, dtype=torch.float64)
+            if x.is_cuda:
+                raise ValueError("this problem was created from host inputs: its solve writes host memory, "
+                                 "pass a CPU tensor as out")
+            if x0 is not None:
+                x0 = _as_host_vector(x0, self.n)
+        opts = FdePgmresOpts(float(tol), int(restart), int(maxit), int(reorth), PRECISIONS[matvec], float(relax))
         st = pgmres_solve(self.h, opts, x0.data_ptr() if x0 is not None else None, x.data_ptr(),
                           raise_on_error=raise_on_error)
         return x, st.as_dict()
@@ -171,6 +205,14 @@ class FDEProblem:
         torch = _torch()
         y = torch.empty(self.n, dtype=torch.float64, device="cuda")
         fde_matvec(self.h, z.data_ptr(), y.data_ptr())
+        return y
+
+    def matvec_fp32(self, z):
+        """y = M z with the Toeplitz apply in FP32 (fde_matvec_fp32)."""
+        torch = _torch()
+        y = torch.empty(self.n, dtype=torch.float64, device="cuda")
+        _lib.check(_lib.load().fde_matvec_fp32(self.h, C.c_void_p(z.data_ptr()), C.c_void_p(y.data_ptr())),
+                   "fde_matvec_fp32")
         return y
 
     def precond_apply(self, r):
@@ -203,6 +245,15 @@ class FDEProblem:
         _lib.check(_lib.load().fde_profile_enable(self.h, 1 if on else 0), "fde_profile_enable")
         return self
 
+    def profile_select(self, stages=()):
+        """Time only the named stages (e.g. ["trsv"]) and keep the iteration graphs
+        (fde_profile_select); an empty list stops recording."""
+        mask = 0
+        for name in stages:
+            mask |= 1 << _lib.STAGES.index(name)
+        _lib.check(_lib.load().fde_profile_select(self.h, C.c_uint(mask)), "fde_profile_select")
+        return self
+
     def profile_read(self) -> dict:
         out = {}
         for i, name in enumerate(_lib.STAGES):
@@ -233,21 +284,34 @@ class FDEProblem:
 class FDEBatch:
     """A batch of independent instances solved together (fde_batch_* entry points).
 
-    problems: list of fde_inputs.Problem (or objects with the same fields); the
-    arrays are host memory, copied by the library."""
+    problems: list of fde_inputs.Problem (or objects with the same fields).  With
+    device_inputs the arrays are first placed in device memory (desc device_ptrs = 1)
+    and the solutions are CUDA tensors; otherwise the library copies host arrays and
+    the solutions are CPU tensors."""
 
-    def __init__(self, problems, stream=None):
+    def __init__(self, problems, stream=None, device_inputs: bool = False):
         import numpy as np
+        torch = _torch()
         self.count = len(problems)
         self.sizes = [(p.m, p.s) for p in problems]
+        self.device_ptrs = bool(device_inputs)
         self._keep = []
         descs = (FdeProblemDesc * self.count)()
+
+        def ptr(a):
+            if device_inputs:
+                t = torch.as_tensor(np.asarray(a, dtype=np.float64), device="cuda").contiguous()
+                self._keep.append(t)
+                return t.data_ptr()
+            arr = np.ascontiguousarray(a, dtype=np.float64)
+            self._keep.append(arr)
+            return arr.ctypes.data
+
         for i, p in enumerate(problems):
-            arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (p.dplus, p.dminus, p.u0, p.f)]
-            self._keep.extend(arrs)
+            arrs = [ptr(a) for a in (p.dplus, p.dminus, p.u0, p.f)]
             descs[i] = FdeProblemDesc(p.m, p.s, float(p.alpha), float(p.xL), float(p.xR), float(p.t0), float(p.T),
-                                      arrs[0].ctypes.data, arrs[1].ctypes.data, 0.0, 0.0, FAMILIES[p.family],
-                                      int(p.mu), arrs[2].ctypes.data, arrs[3].ctypes.data, 0)
+                                      arrs[0], arrs[1], 0.0, 0.0, FAMILIES[p.family],
+                                      int(p.mu), arrs[2], arrs[3], 1 if device_inputs else 0)
             if getattr(p, "dplus_t", None) is not None:  # rejected by the library: not batched
                 tv = [np.ascontiguousarray(a, dtype=np.float64) for a in (p.dplus_t, p.dminus_t)]
                 self._keep.extend(tv)
@@ -273,8 +337,12 @@ class FDEBatch:
 
     def solve(self, tol=1e-10, restart=20, maxit=1000, reorth=1, outs=None, raise_on_error=True):
         torch = _torch()
+        dev = "cuda" if self.device_ptrs else "cpu"
         if outs is None:
-            outs = [torch.empty(m * s, dtype=torch.float64, device="cuda") for m, s in self.sizes]
+            outs = [torch.empty(m * s, dtype=torch.float64, device=dev) for m, s in self.sizes]
+        if any(o.is_cuda != self.device_ptrs for o in outs):
+            raise ValueError(f"this batch's solutions are {'device' if self.device_ptrs else 'host'} memory: "
+                             f"pass {dev} tensors as outs")
         ptrs = (C.c_void_p * self.count)(*[o.data_ptr() for o in outs])
         stats = (FdeStats * self.count)()
         opts = FdePgmresOpts(float(tol), int(restart), int(maxit), int(reorth))

@@ -35,8 +35,8 @@ EXPORTED = [
     "fde_problem_create", "bvm_assemble", "strang_precond_factor", "bccb_precond_setup", "fde_precond_none",
     "pgmres_solve",
     "fde_problem_destroy",
-    "fde_last_error", "fde_matvec", "fde_precond_apply", "fde_get_rhs", "fde_get_factor_block",
-    "fde_get_grunwald", "fde_problem_sizes", "fde_profile_enable", "fde_profile_read", "fde_launch_count",
+    "fde_last_error", "fde_matvec", "fde_matvec_fp32", "fde_precond_apply", "fde_get_rhs", "fde_get_factor_block",
+    "fde_get_grunwald", "fde_problem_sizes", "fde_profile_enable", "fde_profile_select", "fde_profile_read", "fde_launch_count",
     "fde_release_cached_memory",
     "fde_precond_apply_noalloc", "fde_batch_create", "fde_batch_share_operator", "fde_batch_assemble",
     "fde_batch_factor",
@@ -60,14 +60,15 @@ class FdeProblemDesc(C.Structure):
 
 
 class FdePgmresOpts(C.Structure):
-    _fields_ = [("tol", C.c_double), ("restart", C.c_int), ("maxit", C.c_int), ("reorth", C.c_int)]
+    _fields_ = [("tol", C.c_double), ("restart", C.c_int), ("maxit", C.c_int), ("reorth", C.c_int),
+                ("matvec_precision", C.c_int), ("relax", C.c_double)]
 
 
 class FdeStats(C.Structure):
     _fields_ = [
         ("status", C.c_int), ("iterations", C.c_int), ("restarts", C.c_int), ("precision", C.c_int),
         ("rel_residual", C.c_double), ("rel_residual_estimate", C.c_double), ("ms_solve", C.c_double),
-        ("x0_rejected", C.c_int), ("reserved", C.c_int),
+        ("x0_rejected", C.c_int), ("matvecs_fp32", C.c_int),
     ]
 
     def as_dict(self) -> dict:
@@ -103,12 +104,14 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "fde_problem_destroy": (None, [vp]),
         "fde_last_error": (C.c_char_p, []),
         "fde_matvec": (i32, [vp, vp, vp]),
+        "fde_matvec_fp32": (i32, [vp, vp, vp]),
         "fde_precond_apply": (i32, [vp, vp, vp]),
         "fde_get_rhs": (i32, [vp, vp]),
         "fde_get_factor_block": (i32, [vp, i32, vp, vp]),
         "fde_get_grunwald": (i32, [vp, vp]),
         "fde_problem_sizes": (i32, [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]),
         "fde_profile_enable": (i32, [vp, i32]),
+        "fde_profile_select": (i32, [vp, C.c_uint]),
         "fde_profile_read": (i32, [vp, i32, C.POINTER(f64), C.POINTER(i32)]),
         "fde_launch_count": (C.c_longlong, []),
         "fde_release_cached_memory": (C.c_int, []),

@@ -46,17 +46,50 @@ static cudaEvent_t next_event(Problem& P) {
 
 StageTimer::StageTimer(Problem& P, int stage, cudaStream_t on)
     : P_(&P), stage_(stage), st_(on ? on : P.stream) {
-    if (!P.prof) return;
-    e0_ = next_event(P);
-    if (e0_) cudaEventRecord(e0_, st_);
+    if (P.prof) {
+        e0_ = next_event(P);
+        if (e0_) cudaEventRecord(e0_, st_);
+        return;
+    }
+    if (!(P.prof_mask & (1u << stage))) return;
+    if (P.capturing_events) {
+        // inside a stream capture: an event-record node of the graph (a plain record
+        // would only mark a capture dependency); the graph owns the event
+        if (cudaEventCreate(&e0_) != cudaSuccess) { e0_ = nullptr; return; }
+        graph_ = true;
+        cudaEventRecordWithFlags(e0_, st_, cudaEventRecordExternal);
+    } else {
+        e0_ = next_event(P);
+        if (e0_) cudaEventRecord(e0_, st_);
+    }
 }
 
 StageTimer::~StageTimer() {
-    if (!P_->prof || !e0_) return;
+    if (!e0_) return;
+    if (graph_) {
+        cudaEvent_t e1 = nullptr;
+        if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0_); return; }
+        cudaEventRecordWithFlags(e1, st_, cudaEventRecordExternal);
+        P_->capturing_events->push_back({stage_, e0_, e1});
+        return;
+    }
     cudaEvent_t e1 = next_event(*P_);
     if (!e1) return;
     cudaEventRecord(e1, st_);
     P_->prof_rec[stage_].push_back({e0_, e1});
+}
+
+// Sum the stage times recorded by the last replay of iteration graph gi (its stream
+// has been synchronised).
+static void harvest_graph_events(Problem& P, int gi) {
+    if (gi >= (int)P.iter_graph_events.size()) return;
+    for (const Problem::GraphEvent& g : P.iter_graph_events[gi]) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, g.e0, g.e1) == cudaSuccess) {
+            P.prof_acc_ms[g.stage] += ms;
+            P.prof_acc_n[g.stage] += 1;
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -193,6 +226,11 @@ int ensure_workspace(Problem& P, int restart) {
     return FDE_OK;
 }
 
+int ensure_solution_buffer(Problem& P) {
+    if (P.d_xsol) return FDE_OK;
+    return dalloc(&P.d_xsol, (size_t)P.n);
+}
+
 // Factor planes, 1/U_ii and the frequency-domain vector in the precision's storage
 // type (FP64 for FDE_FP64, FP32 otherwise); reallocated when the size changes.
 int ensure_factor_buffers(Problem& P, int precision) {
@@ -252,9 +290,9 @@ static int apply_precond(Problem& P, const double* r, double* z) {
     return launch_time_fft_inv(P, P.d_rhat, z, P.precision, P.stream);
 }
 
-static int matvec(Problem& P, const double* z, double* y) {
+static int matvec(Problem& P, const double* z, double* y, bool fp32 = false) {
     StageTimer t(P, FDE_STAGE_MATVEC);
-    return launch_matvec64(P, z, y, P.stream);
+    return fp32 ? launch_matvec32(P, z, y, P.stream) : launch_matvec64(P, z, y, P.stream);
 }
 
 // ||v||^2 on the device into d_scal[slot]; optionally returned to the host (synchronises).
@@ -274,11 +312,18 @@ static void drop_iter_graphs(Problem& P) {
         if (g) cudaGraphExecDestroy(g);
     P.iter_graph.clear();
     P.iter_graph_launches.clear();
+    for (auto& v : P.iter_graph_events)
+        for (const Problem::GraphEvent& g : v) {
+            cudaEventDestroy(g.e0);
+            cudaEventDestroy(g.e1);
+        }
+    P.iter_graph_events.clear();
 }
 
 // One inner iteration j of pgmres_solve as a stream of launches: z_j = P^{-1} v_j,
-// w = M z_j, CGS2 against v_0..v_j, Hessenberg column / Givens rotation, w /= |w|.
-static int iteration_launches(Problem& P, int j, int ldh, int reorth) {
+// w = M z_j (Toeplitz part in FP32 when fp32), CGS2 against v_0..v_j, Hessenberg
+// column / Givens rotation, w /= |w|.
+static int iteration_launches(Problem& P, int j, int ldh, int reorth, bool fp32) {
     const long n = P.n;
     cudaStream_t st = P.stream;
     double* V = P.d_V;
@@ -288,7 +333,7 @@ static int iteration_launches(Problem& P, int j, int ldh, int reorth) {
     double* zj = P.d_Z + (size_t)j * n;
     int rc;
     if ((rc = apply_precond(P, vj, zj))) return rc;
-    if ((rc = matvec(P, zj, w))) return rc;
+    if ((rc = matvec(P, zj, w, fp32))) return rc;
     StageTimer kt(P, FDE_STAGE_KRYLOV);
     // CGS2 in three passes over V: h1 = V^T w; w -= V h1 and h2 = V^T w;
     // w -= V h2 and |w|^2 (one pass fewer without re-orthogonalisation)
@@ -307,19 +352,23 @@ static int iteration_launches(Problem& P, int j, int ldh, int reorth) {
 // Run iteration j: replay its CUDA graph or launch the kernels directly.  Graphs are
 // captured only for a problem that is solved again (from its second pgmres_solve on),
 // so a one-shot solve pays no capture; the stage profiler always launches directly.
-static int run_iteration(Problem& P, int j, int ldh, int reorth, int restart) {
-    if (P.prof || P.solves < 1) return iteration_launches(P, j, ldh, reorth);
-    const long long key = ((((long long)P.graph_gen * 8 + P.precond) * 8 + (P.precision + 1)) * 8 +
-                           (P.bccb_precision + 1)) * 128 * 2 + (long long)ldh * 2 + (reorth ? 1 : 0);
+static int run_iteration(Problem& P, int j, int ldh, int reorth, int restart, bool fp32, bool* replayed) {
+    *replayed = false;
+    if (P.prof || P.solves < 1) return iteration_launches(P, j, ldh, reorth, fp32);
+    const int gi = j + (fp32 ? restart : 0);  // graph of iteration j with the FP64 / FP32 product
+    const long long key = (((((long long)P.graph_gen * 8 + P.precond) * 8 + (P.precision + 1)) * 8 +
+                            (P.bccb_precision + 1)) * 128 * 2 + (long long)ldh * 2 + (reorth ? 1 : 0)) *
+                              (1LL << FDE_NUM_STAGES) + (long long)P.prof_mask;
     if (key != P.graph_key) {
         drop_iter_graphs(P);
         P.graph_key = key;
     }
-    if ((int)P.iter_graph.size() < restart) {
-        P.iter_graph.resize(restart, nullptr);
-        P.iter_graph_launches.resize(restart, 0);
+    if ((int)P.iter_graph.size() < 2 * restart) {
+        P.iter_graph.resize(2 * restart, nullptr);
+        P.iter_graph_launches.resize(2 * restart, 0);
+        P.iter_graph_events.resize(2 * restart);
     }
-    if (!P.iter_graph[j]) {
+    if (!P.iter_graph[gi]) {
         if (!P.cap_stream) FDE_CUDA_TRY(cudaStreamCreateWithFlags(&P.cap_stream, cudaStreamNonBlocking));
         // the capture stream follows the work already queued on P.stream
         cudaEvent_t fork;
@@ -330,11 +379,19 @@ static int run_iteration(Problem& P, int j, int ldh, int reorth, int restart) {
         cudaStream_t user = P.stream;
         P.stream = P.cap_stream;
         const long long l0 = fde_launch_count();
+        std::vector<Problem::GraphEvent> events;
         cudaError_t e = cudaStreamBeginCapture(P.cap_stream, cudaStreamCaptureModeRelaxed);
-        int rc = e == cudaSuccess ? iteration_launches(P, j, ldh, reorth) : FDE_OK;
+        P.capturing_events = &events;
+        int rc = e == cudaSuccess ? iteration_launches(P, j, ldh, reorth, fp32) : FDE_OK;
+        P.capturing_events = nullptr;
         cudaGraph_t graph = nullptr;
         cudaError_t e2 = cudaStreamEndCapture(P.cap_stream, &graph);
         P.stream = user;
+        for (const Problem::GraphEvent& g : P.iter_graph_events[gi]) {
+            cudaEventDestroy(g.e0);
+            cudaEventDestroy(g.e1);
+        }
+        P.iter_graph_events[gi] = events;  // owned by graph gi from here on
         if (e != cudaSuccess) return cuda_error(e, "cudaStreamBeginCapture");
         if (rc) {
             if (graph) cudaGraphDestroy(graph);
@@ -345,13 +402,14 @@ static int run_iteration(Problem& P, int j, int ldh, int reorth, int restart) {
         e = cudaGraphInstantiate(&exec, graph, 0);
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) return cuda_error(e, "cudaGraphInstantiate");
-        P.iter_graph[j] = exec;
-        P.iter_graph_launches[j] = fde_launch_count() - l0;
+        P.iter_graph[gi] = exec;
+        P.iter_graph_launches[gi] = fde_launch_count() - l0;
         // the launches were counted once while capturing; each replay adds them below
-        note_launches(-P.iter_graph_launches[j]);
+        note_launches(-P.iter_graph_launches[gi]);
     }
-    FDE_CUDA_TRY(cudaGraphLaunch(P.iter_graph[j], P.stream));
-    note_launches(P.iter_graph_launches[j]);
+    FDE_CUDA_TRY(cudaGraphLaunch(P.iter_graph[gi], P.stream));
+    note_launches(P.iter_graph_launches[gi]);
+    *replayed = true;
     return FDE_OK;
 }
 
@@ -412,6 +470,7 @@ int fde_problem_create(const fde_problem_desc* d, void* stream, fde_problem** ou
     P.mp = round_up(P.m, 64);
     P.n = (long)P.m * P.s;
     P.stream = (cudaStream_t)stream;
+    P.device_ptrs = d->device_ptrs != 0;
 
     // BVM band rows t = 1..s (eqs. (1.7)-(1.9)); row 0 is the initial condition.
     std::vector<double> ha((size_t)(P.s + 1) * (P.mu + 1), 0.0), hb((size_t)(P.s + 1) * (P.mu + 1), 0.0);
@@ -595,7 +654,7 @@ void fde_problem_destroy(fde_problem* h) {
                     P.d_sym, P.d_sym32, P.d_tws, P.d_tws32, P.d_phi, P.d_psi, P.d_b_rhs, P.d_work, P.d_rhat,
                     P.d_fac, P.d_dinv, P.d_info, P.d_err, P.d_pack, P.d_tinv, P.d_scal, P.d_partial,
                     P.d_counter, P.d_bccb_K64, P.d_bccb_K32, P.d_rhat_b, P.d_dplus_t, P.d_dminus_t,
-                    P.d_jz};
+                    P.d_jz, P.d_xsol};
     for (void* b : bufs) dfree(b);
     if (h->pinned) cudaFreeHost(h->pinned);
     for (cudaEvent_t e : P.ev_pool) cudaEventDestroy(e);
@@ -612,14 +671,33 @@ long long fde_launch_count(void) { return g_launches.load(); }
 
 int fde_release_cached_memory(void) { return dev_release_cached(); }
 
-int fde_profile_enable(fde_problem* h, int on) {
-    if (!h) return set_error(FDE_ERR_ARG, "NULL problem");
-    Problem& P = h->P;
+static void profile_reset(Problem& P) {
     if (P.stream) cudaStreamSynchronize(P.stream);
     else cudaDeviceSynchronize();
     for (auto& r : P.prof_rec) r.clear();
     P.ev_used = 0;
+    for (int k = 0; k < FDE_NUM_STAGES; ++k) {
+        P.prof_acc_ms[k] = 0.0;
+        P.prof_acc_n[k] = 0;
+    }
+}
+
+int fde_profile_enable(fde_problem* h, int on) {
+    if (!h) return set_error(FDE_ERR_ARG, "NULL problem");
+    Problem& P = h->P;
+    profile_reset(P);
     P.prof = on != 0;
+    P.prof_mask = 0;
+    return FDE_OK;
+}
+
+int fde_profile_select(fde_problem* h, unsigned stage_mask) {
+    if (!h) return set_error(FDE_ERR_ARG, "NULL problem");
+    if (stage_mask >> FDE_NUM_STAGES) return set_error(FDE_ERR_ARG, "stage mask has bits beyond FDE_NUM_STAGES");
+    Problem& P = h->P;
+    profile_reset(P);
+    P.prof = false;
+    P.prof_mask = stage_mask;
     return FDE_OK;
 }
 
@@ -627,14 +705,14 @@ int fde_profile_read(fde_problem* h, int stage, double* total_ms, int* launches)
     if (!h || stage < 0 || stage >= FDE_NUM_STAGES) return set_error(FDE_ERR_ARG, "bad problem or stage");
     Problem& P = h->P;
     FDE_CUDA_TRY(cudaStreamSynchronize(P.stream));
-    double tot = 0.0;
+    double tot = P.prof_acc_ms[stage];
     for (auto& pr : P.prof_rec[stage]) {
         float ms = 0.f;
         FDE_CUDA_TRY(cudaEventElapsedTime(&ms, pr.first, pr.second));
         tot += ms;
     }
     if (total_ms) *total_ms = tot;
-    if (launches) *launches = (int)P.prof_rec[stage].size();
+    if (launches) *launches = (int)P.prof_rec[stage].size() + P.prof_acc_n[stage];
     return FDE_OK;
 }
 
@@ -793,6 +871,13 @@ int fde_matvec(fde_problem* h, const double* z, double* y) {
     return matvec(h->P, z, y);
 }
 
+int fde_matvec_fp32(fde_problem* h, const double* z, double* y) {
+    g_last_error.clear();
+    if (!h || !z || !y) return set_error(FDE_ERR_ARG, "NULL argument");
+    if (!h->P.assembled) return set_error(FDE_ERR_STATE, "bvm_assemble must run first");
+    return matvec(h->P, z, y, true);
+}
+
 int fde_precond_apply(fde_problem* h, const double* r, double* z) {
     g_last_error.clear();
     if (!h || !r || !z) return set_error(FDE_ERR_ARG, "NULL argument");
@@ -845,20 +930,36 @@ int fde_get_factor_block(fde_problem* h, int k, double* re, double* im) {
     return FDE_OK;
 }
 
-int pgmres_solve(fde_problem* h, const fde_pgmres_opts* opts, const double* x0, double* x, fde_stats* stats) {
+int pgmres_solve(fde_problem* h, const fde_pgmres_opts* opts, const double* x0_arg, double* x_arg,
+                 fde_stats* stats) {
     g_last_error.clear();
-    if (!h || !x) return set_error(FDE_ERR_ARG, "NULL argument");
+    if (!h || !x_arg) return set_error(FDE_ERR_ARG, "NULL argument");
     Problem& P = h->P;
     if (!P.factored) return set_error(FDE_ERR_STATE, "strang_precond_factor must run before pgmres_solve");
-    fde_pgmres_opts o{1e-10, 20, 1000, 1};
+    fde_pgmres_opts o{1e-10, 20, 1000, 1, FDE_FP64, 0.0};
     if (opts) o = *opts;
     if (!(o.tol > 0.0) || o.restart < 1 || o.restart > 63 || o.maxit < 1)
         return set_error(FDE_ERR_ARG, "need tol > 0, 1 <= restart <= 63, maxit >= 1");
+    if ((o.matvec_precision != FDE_FP64 && o.matvec_precision != FDE_FP32) || !(o.relax >= 0.0))
+        return set_error(FDE_ERR_ARG, "matvec_precision must be FDE_FP64 or FDE_FP32, relax >= 0");
     int rc = ensure_workspace(P, o.restart);
     if (rc) return rc;
     cudaStream_t st = P.stream;
     const long n = P.n;
     double* pin = h->pinned;
+    // Host solve vectors (desc->device_ptrs == 0): the iteration runs on the device copy
+    // d_xsol; x0 is copied in first and the solution copied out at the end, on the stream.
+    const bool host_x = !P.device_ptrs;
+    double* x = x_arg;
+    const double* x0 = x0_arg;
+    if (host_x) {
+        if ((rc = ensure_solution_buffer(P))) return rc;
+        x = P.d_xsol;
+        if (x0_arg) {
+            FDE_CUDA_TRY(cudaMemcpyAsync(P.d_xsol, x0_arg, n * sizeof(double), cudaMemcpyHostToDevice, st));
+            x0 = P.d_xsol;
+        }
+    }
     cudaEvent_t ev0, ev1;
     FDE_CUDA_TRY(cudaEventCreate(&ev0));
     FDE_CUDA_TRY(cudaEventCreate(&ev1));
@@ -875,6 +976,10 @@ int pgmres_solve(fde_problem* h, const fde_pgmres_opts* opts, const double* x0, 
     double bnorm2 = 0, beta2 = 0;
 
     auto finish = [&](int code) -> int {
+        if (host_x) {  // the solution (or last iterate) back to the caller's host array
+            cudaError_t e = cudaMemcpyAsync(x_arg, x, n * sizeof(double), cudaMemcpyDeviceToHost, st);
+            if (e != cudaSuccess && code == FDE_OK) code = cuda_error(e, "copy of the solution to the host");
+        }
         cudaEventRecord(ev1, st);
         cudaEventSynchronize(ev1);
         float ms = 0;
@@ -935,12 +1040,18 @@ int pgmres_solve(fde_problem* h, const fde_pgmres_opts* opts, const double* x0, 
         std::fill(g0.begin() + 1, g0.end(), 0.0);
         FDE_CUDA_TRY(cudaMemcpyAsync(P.d_gv, g0.data(), g0.size() * sizeof(double), cudaMemcpyHostToDevice, st));
         int j = 0;
+        double est_rel = beta / bnorm;  // residual estimate before iteration j
         for (; j < o.restart; ++j) {
-            if ((rc = run_iteration(P, j, ldh, o.reorth, o.restart))) return finish(rc);
+            bool replayed = false;
+            const bool fp32 = o.matvec_precision == FDE_FP32 && !P.timevar && (o.relax <= 0.0 || est_rel > o.relax);
+            if ((rc = run_iteration(P, j, ldh, o.reorth, o.restart, fp32, &replayed))) return finish(rc);
             ++its;
+            if (fp32) ++S.matvecs_fp32;
             FDE_CUDA_TRY(cudaMemcpyAsync(pin, sc + 128, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
             FDE_CUDA_TRY(cudaStreamSynchronize(st));
+            if (replayed && P.prof_mask) harvest_graph_events(P, j + (fp32 ? o.restart : 0));
             est = pin[1];
+            est_rel = est / bnorm;
             const double hnext = std::fabs(pin[2]);
             if (!std::isfinite(est) || !std::isfinite(pin[0])) {
                 status = set_error(FDE_ERR_NAN, "non-finite Hessenberg entry");

@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -23,6 +24,8 @@
 #include "fde_internal.h"
 
 using namespace fde;
+
+#include <cstdio>
 
 struct fde_batch {
     std::vector<fde_problem*> probs;
@@ -48,6 +51,12 @@ struct fde_batch {
     // frequency-side vectors
     bool shared = false;
     void* d_rhat_shared = nullptr;  // count * nblk * mp complex FP32
+    // batched GMRES: per-instance control words (InstDev::ctl, 4 ints each) and their
+    // host copy; restart cycles captured as CUDA graphs, keyed by the cycle's shape
+    int* d_ctl = nullptr;
+    int* h_ctl = nullptr;  // pinned
+    cudaStream_t cap_stream = nullptr;
+    std::map<std::string, std::pair<cudaGraphExec_t, long long>> cycle_graphs;  // key -> (graph, kernels)
 };
 
 namespace {
@@ -69,6 +78,66 @@ int gather(fde_batch* b) {
     return FDE_OK;
 }
 
+// One restart cycle of the batched flexible GMRES for the nr instances of the current
+// round list (b->d_act): iterations j = 0..restart-1, each a fixed sequence of launches
+// over the whole round.  An instance that meets its tolerance (or maxit, a breakdown,
+// a non-finite value) has its live flag cleared by finish_batched on the device, and
+// every later kernel of the cycle skips it; nothing returns to the host until the
+// cycle is over.
+int cycle_launches(fde_batch* b, int nr, const fde_pgmres_opts& o, cudaStream_t st) {
+    const int ldh = o.restart + 1;
+    int rc;
+    for (int j = 0; j < o.restart; ++j) {
+        if ((rc = launch_time_fft_batched(b->d_inst, b->d_act, nr, b->max_mp, b->max_s, j, st))) return rc;
+        if ((rc = launch_trsv_batched(b->d_inst, b->d_act, nr, b->max_nblk, b->max_mp, st))) return rc;
+        if ((rc = launch_time_ifft_batched(b->d_inst, b->d_act, nr, b->max_mp, b->max_s, j, st))) return rc;
+        if ((rc = launch_matvec_batched(b->d_inst, b->d_act, nr, b->max_s, b->max_L, b->max_m, 0, j, st))) return rc;
+        if ((rc = launch_dots_batched(b->d_inst, b->d_act, nr, 0, j, st))) return rc;
+        if ((rc = launch_update_batched(b->d_inst, b->d_act, nr, 0, j, b->d_kvec, b->max_n, st))) return rc;
+        if (o.reorth) {
+            if ((rc = launch_dots_batched(b->d_inst, b->d_act, nr, 1, j, st))) return rc;
+            if ((rc = launch_update_batched(b->d_inst, b->d_act, nr, 1, j, b->d_kvec, b->max_n, st))) return rc;
+        }
+        if ((rc = launch_dots_batched(b->d_inst, b->d_act, nr, 2, j, st))) return rc;
+        if ((rc = launch_finish_batched(b->d_inst, b->d_act, nr, j, ldh, o.reorth, o.tol, o.maxit, st))) return rc;
+        if ((rc = launch_scale_batched(b->d_inst, b->d_act, nr, 0, j, o.restart, b->max_n, st))) return rc;
+    }
+    return FDE_OK;
+}
+
+// Run the cycle: replay its CUDA graph (captured on first use for this shape: round
+// size, restart, re-orthogonalisation, tolerance and maxit, which enter as kernel
+// arguments; the round list itself is read from device memory when the graph runs).
+int run_cycle(fde_batch* b, int nr, const fde_pgmres_opts& o, cudaStream_t st) {
+    char key[128];
+    std::snprintf(key, sizeof key, "%d/%d/%d/%a/%d", nr, o.restart, o.reorth, o.tol, o.maxit);
+    auto it = b->cycle_graphs.find(key);
+    if (it == b->cycle_graphs.end()) {
+        if (!b->cap_stream) FDE_CUDA_TRY(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+        const long long l0 = fde_launch_count();
+        cudaError_t e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeRelaxed);
+        if (e != cudaSuccess) return cuda_error(e, "cudaStreamBeginCapture");
+        int rc = cycle_launches(b, nr, o, b->cap_stream);
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(b->cap_stream, &graph);
+        if (rc) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (e != cudaSuccess) return cuda_error(e, "cudaStreamEndCapture");
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_error(e, "cudaGraphInstantiate");
+        const long long k = fde_launch_count() - l0;
+        note_launches(-k);  // counted once while capturing; each replay adds them below
+        it = b->cycle_graphs.emplace(key, std::make_pair(exec, k)).first;
+    }
+    FDE_CUDA_TRY(cudaGraphLaunch(it->second.first, st));
+    note_launches(it->second.second);
+    return FDE_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -85,6 +154,10 @@ void fde_batch_destroy(fde_batch* b) {
     if (b->h_gather) cudaFreeHost(b->h_gather);
     if (b->h_act) cudaFreeHost(b->h_act);
     if (b->h_kvec) cudaFreeHost(b->h_kvec);
+    if (b->d_ctl) cudaFree(b->d_ctl);
+    if (b->h_ctl) cudaFreeHost(b->h_ctl);
+    for (auto& kv : b->cycle_graphs) cudaGraphExecDestroy(kv.second.first);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     delete b;
 }
 
@@ -123,7 +196,9 @@ int fde_batch_create(const fde_problem_desc* descs, int count, void* stream, fde
               cudaMalloc(&b->d_inst, count * sizeof(InstDev)) == cudaSuccess &&
               cudaMallocHost(&b->h_gather, 4 * count * sizeof(double)) == cudaSuccess &&
               cudaMallocHost(&b->h_act, count * sizeof(int)) == cudaSuccess &&
-              cudaMallocHost(&b->h_kvec, count * sizeof(int)) == cudaSuccess;
+              cudaMallocHost(&b->h_kvec, count * sizeof(int)) == cudaSuccess &&
+              cudaMalloc(&b->d_ctl, 4 * count * sizeof(int)) == cudaSuccess &&
+              cudaMallocHost(&b->h_ctl, 4 * count * sizeof(int)) == cudaSuccess;
     if (!ok) {
         fde_batch_destroy(b);
         return set_error(FDE_ERR_ALLOC, "batch allocation failed");
@@ -313,11 +388,19 @@ int fde_batch_solve(fde_batch* b, const fde_pgmres_opts* opts, double* const* x_
         } else {
             d.rhat = P.d_rhat; d.fac = P.d_fac; d.dinv = P.d_dinv; d.tinv = nullptr;
         }
-        d.b = P.d_b_rhs; d.x = x_out[i]; d.V = P.d_V; d.Z = P.d_Z; d.work = P.d_work; d.H = P.d_H;
+        // host solution arrays (the instance's desc->device_ptrs == 0): solve into the
+        // instance's device copy, copied out when the batch is done
+        double* xd = x_out[i];
+        if (!P.device_ptrs) {
+            if ((rc = ensure_solution_buffer(P))) return rc;
+            xd = P.d_xsol;
+        }
+        d.b = P.d_b_rhs; d.x = xd; d.V = P.d_V; d.Z = P.d_Z; d.work = P.d_work; d.H = P.d_H;
         d.cs = P.d_cs; d.sn = P.d_sn; d.gv = P.d_gv; d.y = P.d_y; d.scal = P.d_scal;
         d.partial = P.d_partial; d.counter = P.d_counter;
+        d.ctl = b->d_ctl + 4 * i;
         inst[i] = d;
-        FDE_CUDA_TRY(cudaMemsetAsync(x_out[i], 0, P.n * sizeof(double), st));
+        FDE_CUDA_TRY(cudaMemsetAsync(xd, 0, P.n * sizeof(double), st));
     }
     FDE_CUDA_TRY(cudaMemcpyAsync(b->d_inst, inst.data(), n * sizeof(InstDev), cudaMemcpyHostToDevice, st));
     const int ldh = o.restart + 1;
@@ -331,6 +414,7 @@ int fde_batch_solve(fde_batch* b, const fde_pgmres_opts* opts, double* const* x_
     };
     // r_0 = b - M x_0 (x_0 = 0) into V_0, |b|^2 and |r_0|^2
     if ((rc = upload_list(b, all, b->h_act, b->d_act))) return fail(rc);
+    if ((rc = launch_ctl_set_batched(b->d_inst, b->d_act, n, 1, 2, st))) return fail(rc);
     if ((rc = launch_matvec_batched(b->d_inst, b->d_act, n, b->max_s, b->max_L, b->max_m, 1, 0, st))) return fail(rc);
     if ((rc = launch_residual_batched(b->d_inst, b->d_act, n, b->max_n, st))) return fail(rc);
     if ((rc = launch_dots_batched(b->d_inst, b->d_act, n, 4, 0, st))) return fail(rc);
@@ -352,50 +436,25 @@ int fde_batch_solve(fde_batch* b, const fde_pgmres_opts* opts, double* const* x_
         else if (bnorm[i] == 0.0 || beta[i] <= o.tol * bnorm[i]) done[i] = 1;
     }
     for (;;) {
+        // a restart round: every unconverged instance runs one cycle of up to `restart`
+        // Arnoldi steps, leaving it on the device as soon as its estimate meets the tolerance
         std::vector<int> round;
         for (int i = 0; i < n; ++i)
             if (!done[i]) round.push_back(i);
         if (round.empty()) break;
         const int nr = (int)round.size();
         if ((rc = upload_list(b, round, b->h_act, b->d_act))) return fail(rc);
+        if ((rc = launch_ctl_set_batched(b->d_inst, b->d_act, nr, 1, 1, st))) return fail(rc);
         if ((rc = launch_scale_batched(b->d_inst, b->d_act, nr, 1, 0, o.restart, b->max_n, st))) return fail(rc);
-        std::vector<char> in_cycle(n, 0);
-        for (int i : round) { in_cycle[i] = 1; kk[i] = 0; }
-        for (int j = 0; j < o.restart; ++j) {
-            std::vector<int> cyc;
-            for (int i : round)
-                if (in_cycle[i]) cyc.push_back(i);
-            if (cyc.empty()) break;
-            const int nc = (int)cyc.size();
-            if ((rc = upload_list(b, cyc, b->h_act, b->d_act))) return fail(rc);
-            if ((rc = launch_time_fft_batched(b->d_inst, b->d_act, nc, b->max_mp, b->max_s, j, st))) return fail(rc);
-            if ((rc = launch_trsv_batched(b->d_inst, b->d_act, nc, b->max_nblk, b->max_mp, st))) return fail(rc);
-            if ((rc = launch_time_ifft_batched(b->d_inst, b->d_act, nc, b->max_mp, b->max_s, j, st))) return fail(rc);
-            if ((rc = launch_matvec_batched(b->d_inst, b->d_act, nc, b->max_s, b->max_L, b->max_m, 0, j, st)))
-                return fail(rc);
-            if ((rc = launch_dots_batched(b->d_inst, b->d_act, nc, 0, j, st))) return fail(rc);
-            if ((rc = launch_update_batched(b->d_inst, b->d_act, nc, 0, j, b->d_kvec, b->max_n, st))) return fail(rc);
-            if (o.reorth) {
-                if ((rc = launch_dots_batched(b->d_inst, b->d_act, nc, 1, j, st))) return fail(rc);
-                if ((rc = launch_update_batched(b->d_inst, b->d_act, nc, 1, j, b->d_kvec, b->max_n, st)))
-                    return fail(rc);
-            }
-            if ((rc = launch_dots_batched(b->d_inst, b->d_act, nc, 2, j, st))) return fail(rc);
-            if ((rc = launch_finish_batched(b->d_inst, b->d_act, nc, j, ldh, o.reorth, st))) return fail(rc);
-            if ((rc = launch_scale_batched(b->d_inst, b->d_act, nc, 0, j, o.restart, b->max_n, st))) return fail(rc);
-            if ((rc = gather(b))) return fail(rc);
-            for (int i : cyc) {
-                ++its[i];
-                kk[i] = j + 1;
-                est[i] = b->h_gather[4 * i + 1];
-                const double hn = std::fabs(b->h_gather[4 * i + 2]);
-                if (!std::isfinite(est[i]) || !std::isfinite(b->h_gather[4 * i])) {
-                    status[i] = FDE_ERR_NAN;
-                    in_cycle[i] = 0;
-                    continue;
-                }
-                if (est[i] <= o.tol * bnorm[i] || its[i] >= o.maxit || hn <= 1e-300) in_cycle[i] = 0;
-            }
+        if ((rc = run_cycle(b, nr, o, st))) return fail(rc);
+        FDE_CUDA_TRY(cudaMemcpyAsync(b->h_ctl, b->d_ctl, 4 * n * sizeof(int), cudaMemcpyDeviceToHost, st));
+        if ((rc = gather(b))) return fail(rc);  // synchronises
+        for (int i : round) {
+            const int* c = b->h_ctl + 4 * i;
+            kk[i] = c[1];
+            its[i] = c[2];
+            est[i] = b->h_gather[4 * i + 1];
+            if (c[3]) status[i] = FDE_ERR_NAN;
         }
         // end of the round: x += Z y, true residual
         std::vector<int> upd;
@@ -408,6 +467,7 @@ int fde_batch_solve(fde_batch* b, const fde_pgmres_opts* opts, double* const* x_
         for (int i = 0; i < n; ++i) b->h_kvec[i] = kk[i];
         FDE_CUDA_TRY(cudaMemcpyAsync(b->d_kvec, b->h_kvec, n * sizeof(int), cudaMemcpyHostToDevice, st));
         if ((rc = upload_list(b, upd, b->h_act, b->d_act))) return fail(rc);
+        if ((rc = launch_ctl_set_batched(b->d_inst, b->d_act, nu, 1, 0, st))) return fail(rc);
         if ((rc = launch_lsq_batched(b->d_inst, b->d_act, nu, b->d_kvec, ldh, st))) return fail(rc);
         if ((rc = launch_update_batched(b->d_inst, b->d_act, nu, 2, 0, b->d_kvec, b->max_n, st))) return fail(rc);
         if ((rc = launch_matvec_batched(b->d_inst, b->d_act, nu, b->max_s, b->max_L, b->max_m, 1, 0, st)))
@@ -428,6 +488,11 @@ int fde_batch_solve(fde_batch* b, const fde_pgmres_opts* opts, double* const* x_
                 done[i] = 1;
             }
         }
+    }
+    for (int i = 0; i < n; ++i) {
+        const Problem& P = *problem_of(b->probs[i]);
+        if (!P.device_ptrs)
+            FDE_CUDA_TRY(cudaMemcpyAsync(x_out[i], P.d_xsol, P.n * sizeof(double), cudaMemcpyDeviceToHost, st));
     }
     FDE_CUDA_TRY(cudaEventRecord(ev1, st));
     FDE_CUDA_TRY(cudaEventSynchronize(ev1));

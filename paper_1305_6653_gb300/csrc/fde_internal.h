@@ -78,6 +78,10 @@ struct InstDev {
     double* scal;          // [0..63] h1, [64..127] h2, [128] |w|^2, [129] est, [130] H(j+1,j), [132] beta^2
     double* partial;       // RED_CTAS x 64
     unsigned int* counter;
+    // per-instance control words of a batched solve: [0] live (the batched GMRES
+    // kernels skip an instance whose flag is 0), [1] Arnoldi steps taken in the
+    // current restart cycle, [2] total steps, [3] 1 = a non-finite value was met
+    int* ctl;
 };
 
 struct BlkDev {
@@ -113,6 +117,8 @@ int launch_rhs(const Problem& P, const double* Ju0, cudaStream_t st);
 
 // matvec.cu: y = M z (mode 0) or y = J z for ncols columns (mode 1)
 int launch_matvec64(const Problem& P, const double* z, double* y, cudaStream_t st);
+// y = M z with the Toeplitz apply in FP32 (the band, its A part and y in FP64)
+int launch_matvec32(const Problem& P, const double* z, double* y, cudaStream_t st);
 int launch_japply64(const Problem& P, const double* z, double* y, int ncols, cudaStream_t st);
 // J_n z for ncols columns with per-column coefficients dplus + c*dstride (dstride 0: shared)
 int launch_japply64_d(const Problem& P, const double* z, double* y, int ncols, const double* dplus,
@@ -155,6 +161,8 @@ struct Problem {
     int mp = 0;                 // m rounded up to the LU tile (64)
     long n = 0;                 // s*m unknowns
     cudaStream_t stream = nullptr;
+    bool device_ptrs = false;   // desc->device_ptrs: solve vectors (x0, x_out) are device pointers
+    double* d_xsol = nullptr;   // n: device copy of the solution when x0 / x_out are host pointers
 
     // host copies of the BVM band (rows 0..s of A and B)
     int h_start[FDE_MAX_S + 1];
@@ -231,11 +239,23 @@ struct Problem {
     bool factored = false;
     int precision = -1;
 
-    // per-stage CUDA-event profiler (fde_profile_enable)
+    // per-stage CUDA-event profiler (fde_profile_enable: every stage, direct launches)
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_rec[FDE_NUM_STAGES];
+    // selected-stage timer (fde_profile_select): event pairs around the stages in the
+    // mask; inside a captured iteration graph they become event-record nodes owned by
+    // that graph, read after each replay and summed into prof_acc
+    unsigned prof_mask = 0;
+    struct GraphEvent {
+        int stage;
+        cudaEvent_t e0, e1;
+    };
+    std::vector<GraphEvent>* capturing_events = nullptr;   // graph being captured
+    std::vector<std::vector<GraphEvent>> iter_graph_events;  // per iteration graph
+    double prof_acc_ms[FDE_NUM_STAGES] = {};
+    int prof_acc_n[FDE_NUM_STAGES] = {};
 };
 
 // preconditioner in use by pgmres_solve / fde_precond_apply
@@ -262,6 +282,7 @@ int dev_release_cached();
 Problem* problem_of(fde_problem* h);
 int ensure_factor_buffers(Problem& P, int precision);
 int ensure_workspace(Problem& P, int restart);
+int ensure_solution_buffer(Problem& P);  // d_xsol for problems whose solve vectors are host memory
 
 // batched launchers (lu.cu, timefft.cu, matvec.cu, krylov.cu)
 int launch_lu_batched(const BlkDev* d_blk, const std::vector<int>& mp_sorted, int precision, int* err,
@@ -282,7 +303,12 @@ int launch_update_batched(const InstDev* I, const int* act, int nact, int mode, 
 int launch_scale_batched(const InstDev* I, const int* act, int nact, int mode, int j, int restart, long max_n,
                          cudaStream_t st);
 int launch_residual_batched(const InstDev* I, const int* act, int nact, long max_n, cudaStream_t st);
-int launch_finish_batched(const InstDev* I, const int* act, int nact, int j, int ldh, int reorth, cudaStream_t st);
+// finish_batched also decides, on the device, whether the instance leaves the cycle
+// (estimate <= tol |b|, maxit total steps, breakdown or a non-finite value)
+int launch_finish_batched(const InstDev* I, const int* act, int nact, int j, int ldh, int reorth, double tol,
+                          int maxit, cudaStream_t st);
+// ctl[0] = live for the listed instances; reset: also zero ctl[1] (and ctl[2], ctl[3] when reset > 1)
+int launch_ctl_set_batched(const InstDev* I, const int* act, int nact, int live, int reset, cudaStream_t st);
 int launch_lsq_batched(const InstDev* I, const int* act, int nact, const int* kvec, int ldh, cudaStream_t st);
 int launch_gather_scalars(const InstDev* I, int ninst, double* out, cudaStream_t st);
 
@@ -298,6 +324,7 @@ class StageTimer {
     int stage_;
     cudaStream_t st_;
     cudaEvent_t e0_ = nullptr;
+    bool graph_ = false;  // recorded into the iteration graph being captured
 };
 
 }  // namespace fde

@@ -91,7 +91,7 @@ __device__ void fft_dif(C* buf, int logn, int ncol, int stride, const C* __restr
     }
 }
 
-// Radix-4 passes over one column of N = 2^logn FP64 points: each pass is the exact
+// Radix-4 passes over one column of N = 2^logn points (FP64 double2 or FP32 float2): each pass is the exact
 // regrouping of two consecutive radix-2 stages of fft_dit / fft_dif (same data order
 // in and out), with three twiddle products per four points instead of four and half
 // the passes through shared memory.  tw[k * ts] = exp(-2 pi i k / N) for k < N (ts:
@@ -100,13 +100,13 @@ __device__ void fft_dif(C* buf, int logn, int ncol, int stride, const C* __restr
 // DIT, stages s and s+1 (half = 2^(s-1)), w2 = W_{2^(s+1)}^pos, w1 = w2^2, w3 = w2^3:
 //   a = x0, b = w1 x1, c = w2 x2, d = w3 x3;
 //   y0 = a+b+c+d, y1 = a-b-i(c-d), y2 = a+b-c-d, y3 = a-b+i(c-d)   (i -> -i inverse).
-template <bool INVERSE>
-__device__ void fft_dit4(double2* buf, int logn, const double2* __restrict__ tw, int ts) {
+template <bool INVERSE, typename C>
+__device__ void fft_dit4(C* buf, int logn, const C* __restrict__ tw, int ts) {
     const int N = 1 << logn;
     int st = 1;
     if (logn & 1) {  // a first radix-2 stage (twiddle 1)
         for (int b = threadIdx.x; b < N / 2; b += blockDim.x) {
-            const double2 a = buf[2 * b], c = buf[2 * b + 1];
+            const C a = buf[2 * b], c = buf[2 * b + 1];
             buf[2 * b] = cadd(a, c);
             buf[2 * b + 1] = csub(a, c);
         }
@@ -119,19 +119,19 @@ __device__ void fft_dit4(double2* buf, int logn, const double2* __restrict__ tw,
         for (int g = threadIdx.x; g < N / 4; g += blockDim.x) {
             const int pos = g & (half - 1);
             const int i0 = ((g >> (st - 1)) << (st + 1)) + pos;
-            double2 w2 = tw[pos * tws], w1 = tw[2 * pos * tws], w3 = tw[3 * pos * tws];
+            C w2 = tw[pos * tws], w1 = tw[2 * pos * tws], w3 = tw[3 * pos * tws];
             if (INVERSE) {
                 w1.y = -w1.y;
                 w2.y = -w2.y;
                 w3.y = -w3.y;
             }
-            const double2 a = buf[i0];
-            const double2 b = cmul(w1, buf[i0 + half]);
-            const double2 c = cmul(w2, buf[i0 + 2 * half]);
-            const double2 d = cmul(w3, buf[i0 + 3 * half]);
-            const double2 apb = cadd(a, b), amb = csub(a, b), cpd = cadd(c, d), cmd = csub(c, d);
+            const C a = buf[i0];
+            const C b = cmul(w1, buf[i0 + half]);
+            const C c = cmul(w2, buf[i0 + 2 * half]);
+            const C d = cmul(w3, buf[i0 + 3 * half]);
+            const C apb = cadd(a, b), amb = csub(a, b), cpd = cadd(c, d), cmd = csub(c, d);
             // -i (c - d) forward, +i (c - d) inverse
-            const double2 rot = INVERSE ? make_double2(-cmd.y, cmd.x) : make_double2(cmd.y, -cmd.x);
+            const C rot = INVERSE ? mk(-cmd.y, cmd.x) : mk(cmd.y, -cmd.x);
             buf[i0] = cadd(apb, cpd);
             buf[i0 + half] = cadd(amb, rot);
             buf[i0 + 2 * half] = csub(apb, cpd);
@@ -144,8 +144,8 @@ __device__ void fft_dit4(double2* buf, int logn, const double2* __restrict__ tw,
 // DIF, stages S and S-1 (h = 2^(S-2)), u = W_{2^S}^pos:
 //   y0 = (x0+x2) + (x1+x3), y1 = ((x0+x2) - (x1+x3)) u^2,
 //   y2 = u ((x0-x2) - i(x1-x3)), y3 = u^3 ((x0-x2) + i(x1-x3))   (conjugates inverse).
-template <bool INVERSE>
-__device__ void fft_dif4(double2* buf, int logn, const double2* __restrict__ tw, int ts) {
+template <bool INVERSE, typename C>
+__device__ void fft_dif4(C* buf, int logn, const C* __restrict__ tw, int ts) {
     const int N = 1 << logn;
     int S = logn;
     for (; S >= 2; S -= 2) {
@@ -154,16 +154,16 @@ __device__ void fft_dif4(double2* buf, int logn, const double2* __restrict__ tw,
         for (int g = threadIdx.x; g < N / 4; g += blockDim.x) {
             const int pos = g & (h - 1);
             const int i0 = ((g >> (S - 2)) << S) + pos;
-            double2 u1 = tw[pos * tws], u2 = tw[2 * pos * tws], u3 = tw[3 * pos * tws];
+            C u1 = tw[pos * tws], u2 = tw[2 * pos * tws], u3 = tw[3 * pos * tws];
             if (INVERSE) {
                 u1.y = -u1.y;
                 u2.y = -u2.y;
                 u3.y = -u3.y;
             }
-            const double2 x0 = buf[i0], x1 = buf[i0 + h], x2 = buf[i0 + 2 * h], x3 = buf[i0 + 3 * h];
-            const double2 s02 = cadd(x0, x2), d02 = csub(x0, x2), s13 = cadd(x1, x3), d13 = csub(x1, x3);
+            const C x0 = buf[i0], x1 = buf[i0 + h], x2 = buf[i0 + 2 * h], x3 = buf[i0 + 3 * h];
+            const C s02 = cadd(x0, x2), d02 = csub(x0, x2), s13 = cadd(x1, x3), d13 = csub(x1, x3);
             // -i (x1 - x3) forward, +i (x1 - x3) inverse
-            const double2 rot = INVERSE ? make_double2(-d13.y, d13.x) : make_double2(d13.y, -d13.x);
+            const C rot = INVERSE ? mk(-d13.y, d13.x) : mk(d13.y, -d13.x);
             buf[i0] = cadd(s02, s13);
             buf[i0 + h] = cmul(csub(s02, s13), u2);
             buf[i0 + 2 * h] = cmul(cadd(d02, rot), u1);
@@ -173,7 +173,7 @@ __device__ void fft_dif4(double2* buf, int logn, const double2* __restrict__ tw,
     }
     if (S == 1) {  // a last radix-2 stage (twiddle 1)
         for (int b = threadIdx.x; b < N / 2; b += blockDim.x) {
-            const double2 a = buf[2 * b], c = buf[2 * b + 1];
+            const C a = buf[2 * b], c = buf[2 * b + 1];
             buf[2 * b] = cadd(a, c);
             buf[2 * b + 1] = csub(a, c);
         }

@@ -244,6 +244,7 @@ template <int KC>
 __global__ void __launch_bounds__(RED_THREADS)
 dots_batched(const InstDev* __restrict__ I, const int* __restrict__ act, int mode, int j) {
     const InstDev& d = I[act[blockIdx.y]];
+    if (!d.ctl[0]) return;  // the instance has left the cycle: no CTA of it takes part
     const double* w;
     const double* V;
     int k;
@@ -266,6 +267,7 @@ __global__ void update_batched(const InstDev* __restrict__ I, const int* __restr
     __shared__ double c[KMAX];
     const int inst = act[blockIdx.y];
     const InstDev& d = I[inst];
+    if (!d.ctl[0]) return;
     const double* V;
     double* w;
     const double* coef;
@@ -290,6 +292,7 @@ __global__ void update_batched(const InstDev* __restrict__ I, const int* __restr
 __global__ void scale_batched(const InstDev* __restrict__ I, const int* __restrict__ act, int mode, int j,
                               int restart) {
     const InstDev& d = I[act[blockIdx.y]];
+    if (!d.ctl[0]) return;
     double* v = mode == 0 ? d.V + (size_t)(j + 1) * d.n : d.V;
     const double nr = sqrt(d.scal[mode == 0 ? 128 : 132]);
     const double inv = nr > 0.0 ? 1.0 / nr : 0.0;
@@ -302,16 +305,18 @@ __global__ void scale_batched(const InstDev* __restrict__ I, const int* __restri
 // V_0 = b - work (work = M x)
 __global__ void residual_batched(const InstDev* __restrict__ I, const int* __restrict__ act) {
     const InstDev& d = I[act[blockIdx.y]];
+    if (!d.ctl[0]) return;
     const long stride = (long)gridDim.x * blockDim.x;
     for (long x = (long)blockIdx.x * blockDim.x + threadIdx.x; x < d.n; x += stride) d.V[x] = d.b[x] - d.work[x];
 }
 
 // one thread per active instance
 __global__ void finish_batched(const InstDev* __restrict__ I, const int* __restrict__ act, int nact, int j, int ldh,
-                               int reorth) {
+                               int reorth, double tol, int maxit) {
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= nact) return;
     const InstDev& d = I[act[a]];
+    if (!d.ctl[0]) return;
     double* col = d.H + (size_t)j * ldh;
     const double* h1 = d.scal;
     const double* h2 = d.scal + 64;
@@ -332,8 +337,32 @@ __global__ void finish_batched(const InstDev* __restrict__ I, const int* __restr
     col[j + 1] = 0.0;
     d.gv[j + 1] = -sn * d.gv[j];
     d.gv[j] = c * d.gv[j];
-    d.scal[129] = fabs(d.gv[j + 1]);
+    const double est = fabs(d.gv[j + 1]);
+    d.scal[129] = est;
     d.scal[130] = bb;
+    // leave the cycle: tolerance met (Givens estimate), maxit, breakdown, or non-finite
+    const int its = d.ctl[2] + 1;
+    d.ctl[2] = its;
+    d.ctl[1] = j + 1;
+    if (!isfinite(est) || !isfinite(d.scal[128])) {
+        d.ctl[3] = 1;
+        d.ctl[0] = 0;
+    } else if (est <= tol * sqrt(d.scal[131]) || its >= maxit || fabs(bb) <= 1e-300) {
+        d.ctl[0] = 0;
+    }
+}
+
+__global__ void ctl_set_batched(const InstDev* __restrict__ I, const int* __restrict__ act, int nact, int live,
+                                int reset) {
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= nact) return;
+    int* c = I[act[a]].ctl;
+    c[0] = live;
+    if (reset) c[1] = 0;
+    if (reset > 1) {
+        c[2] = 0;
+        c[3] = 0;
+    }
 }
 
 __global__ void lsq_batched(const InstDev* __restrict__ I, const int* __restrict__ act, int nact,
@@ -342,6 +371,7 @@ __global__ void lsq_batched(const InstDev* __restrict__ I, const int* __restrict
     if (a >= nact) return;
     const int inst = act[a];
     const InstDev& d = I[inst];
+    if (!d.ctl[0]) return;
     const int k = kvec[inst];
     for (int i = k - 1; i >= 0; --i) {
         double v = d.gv[i];
@@ -404,10 +434,18 @@ int launch_residual_batched(const InstDev* I, const int* act, int nact, long max
     return FDE_OK;
 }
 
-int launch_finish_batched(const InstDev* I, const int* act, int nact, int j, int ldh, int reorth, cudaStream_t st) {
+int launch_finish_batched(const InstDev* I, const int* act, int nact, int j, int ldh, int reorth, double tol,
+                          int maxit, cudaStream_t st) {
     if (nact <= 0) return FDE_OK;
-    finish_batched<<<(nact + 63) / 64, 64, 0, st>>>(I, act, nact, j, ldh, reorth);
+    finish_batched<<<(nact + 63) / 64, 64, 0, st>>>(I, act, nact, j, ldh, reorth, tol, maxit);
     FDE_LAUNCH_CHECK("finish_batched");
+    return FDE_OK;
+}
+
+int launch_ctl_set_batched(const InstDev* I, const int* act, int nact, int live, int reset, cudaStream_t st) {
+    if (nact <= 0) return FDE_OK;
+    ctl_set_batched<<<(nact + 63) / 64, 64, 0, st>>>(I, act, nact, live, reset);
+    FDE_LAUNCH_CHECK("ctl_set_batched");
     return FDE_OK;
 }
 

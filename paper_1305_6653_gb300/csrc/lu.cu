@@ -717,7 +717,7 @@ __global__ void __launch_bounds__(TRSV_THREADS)
 block_trsv_batched(const InstDev* __restrict__ I, const int* __restrict__ act) {
     const InstDev& d = I[act[blockIdx.x]];
     const int k = blockIdx.y;
-    if (k >= d.nblk) return;
+    if (k >= d.nblk || !d.ctl[0]) return;
     const size_t mp = d.mp;
     const T* fac = (const T*)d.fac + (size_t)k * 2 * mp * mp;
     const cplx_t<T>* dinv = (const cplx_t<T>*)d.dinv + (size_t)k * mp;

@@ -21,7 +21,9 @@ __device__ __forceinline__ void matvec_body(int m, int logL, int mu, double h, c
                                             const cplx_t<T>* __restrict__ sym, const cplx_t<T>* __restrict__ tw,
                                             const double* __restrict__ z, double* __restrict__ y, int row,
                                             int dstride = 0) {
-    static_assert(sizeof(T) == 8, "the Toeplitz apply runs in FP64");
+    // T = double: the FP64 product.  T = float: the band sums, the A-band part and the
+    // output stay FP64; only the Toeplitz apply J w (both FFTs and the symbol product)
+    // runs in FP32 (the inexact inner product of the flexible GMRES).
     using C = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int L = 1 << logL, N = L >> 1, logN = logL - 1;
@@ -65,7 +67,7 @@ __device__ __forceinline__ void matvec_body(int m, int logL, int mu, double h, c
                 }
             }
         }
-        buf[bitrev(n, logN)] = mk(v2[0], v2[1]);
+        buf[bitrev(n, logN)] = mk((T)v2[0], (T)v2[1]);
     }
     __syncthreads();
     fft_dit4<false>(buf, logN, tw, 2);  // tw holds W_L^k; stride 2 gives W_N^k
@@ -81,8 +83,9 @@ __device__ __forceinline__ void matvec_body(int m, int logL, int mu, double h, c
             if (e == 1 && kk == k) break;
             const int idx = e == 0 ? k : kk;
             const C za = e == 0 ? zk : zn, zb = e == 0 ? zn : zk;
-            const C E = mk(0.5 * (za.x + zb.x), 0.5 * (za.y - zb.y));
-            const C O = mk(0.5 * (za.y + zb.y), -0.5 * (za.x - zb.x));
+            const T half = T(0.5);
+            const C E = mk(half * (za.x + zb.x), half * (za.y - zb.y));
+            const C O = mk(half * (za.y + zb.y), -half * (za.x - zb.x));
             const C wo = cmul(tw[idx], O);
             buf[idx] = cmul(cadd(E, wo), sym[idx]);
             buf[idx + N] = cmul(csub(E, wo), sym[idx + N]);
@@ -138,7 +141,7 @@ st_band_kernel(int m, int mu, double h, const int* __restrict__ start, const dou
 __global__ void __launch_bounds__(1024)
 st_matvec_batched(const InstDev* __restrict__ I, const int* __restrict__ act, int which, int j) {
     const InstDev& d = I[act[blockIdx.y]];
-    if ((int)blockIdx.x >= d.s) return;
+    if ((int)blockIdx.x >= d.s || !d.ctl[0]) return;
     const double* z = which == 0 ? d.Z + (size_t)j * d.n : d.x;
     double* y = which == 0 ? d.V + (size_t)(j + 1) * d.n : d.work;
     matvec_body<double, 0>(d.m, d.logL, d.mu, d.h, d.start, d.A, d.B, d.dplus, d.dminus, d.sym, d.twL, z, y,
@@ -158,21 +161,35 @@ int launch_matvec_batched(const InstDev* I, const int* act, int nact, int max_s,
     return FDE_OK;
 }
 
-template <int MODE>
+template <int MODE, typename T = double>
 static int launch_st(const Problem& P, const double* z, double* y, int ncols, cudaStream_t st,
                      const double* dplus = nullptr, const double* dminus = nullptr, int dstride = 0) {
     const int L = P.L;
-    size_t smem = (size_t)L * sizeof(double2) + (MODE == 0 ? (size_t)P.m * sizeof(double) : 0);
+    size_t smem = (size_t)L * sizeof(cplx_t<T>) + (MODE == 0 ? (size_t)P.m * sizeof(double) : 0);
     int threads = L / 2;
     if (threads > 1024) threads = 1024;
     if (threads < 64) threads = 64;
-    auto kern = st_matvec_kernel<double, MODE>;
+    auto kern = st_matvec_kernel<T, MODE>;
     FDE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    const cplx_t<T>* sym;
+    const cplx_t<T>* tw;
+    if constexpr (sizeof(T) == 8) {
+        sym = P.d_sym;
+        tw = P.d_twL;
+    } else {
+        sym = P.d_sym32;
+        tw = P.d_twL32;
+    }
     kern<<<ncols, threads, smem, st>>>(P.m, P.logL, P.mu, P.h, P.d_start, P.d_a, P.d_b,
-                                       dplus ? dplus : P.d_dplus, dminus ? dminus : P.d_dminus, P.d_sym, P.d_twL,
-                                       z, y, dstride);
+                                       dplus ? dplus : P.d_dplus, dminus ? dminus : P.d_dminus, sym, tw, z, y,
+                                       dstride);
     FDE_LAUNCH_CHECK("st_matvec_kernel");
     return FDE_OK;
+}
+
+int launch_matvec32(const Problem& P, const double* z, double* y, cudaStream_t st) {
+    if (P.timevar) return launch_matvec64(P, z, y, st);  // the time-level products stay FP64
+    return launch_st<0, float>(P, z, y, P.s, st);
 }
 
 int launch_matvec64(const Problem& P, const double* z, double* y, cudaStream_t st) {

@@ -43,13 +43,14 @@ extern "C" int fde_precond_apply_noalloc(fde_problem* h, const double* r, double
     set_error(FDE_OK, "");
     if (!h || !r || !z) return set_error(FDE_ERR_ARG, "NULL argument");
     Problem& P = *problem_of(h);
+    // The state comes first: the scratch size depends on the precision of the factors.
+    if (!P.factored || P.precond != FDE_PRECOND_STRANG)
+        return set_error(FDE_ERR_STATE, "strang_precond_factor must run first");
     const size_t esz = P.precision == FDE_FP64 ? sizeof(double) : sizeof(float);
-    const size_t need = (size_t)P.nblk * P.mp * 2 * (P.precision < 0 ? sizeof(double) : esz);
+    const size_t need = (size_t)P.nblk * P.mp * 2 * esz;
     if (need > NOALLOC_SCRATCH_BYTES)
         return set_error(FDE_ERR_ARG, "fde_precond_apply_noalloc: (s/2+1) * mp complex values exceed the 8 MiB "
                                       "static scratch; use fde_precond_apply");
-    if (!P.factored || P.precond != FDE_PRECOND_STRANG)
-        return set_error(FDE_ERR_STATE, "strang_precond_factor must run first");
     void* scratch = nullptr;
     int rc = scratch_address(&scratch);
     if (rc) return rc;

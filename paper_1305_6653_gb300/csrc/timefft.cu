@@ -106,14 +106,14 @@ time_fft_inv_kernel(int m, int mp, int logs, const cplx_t<T>* __restrict__ xhat,
 __global__ void __launch_bounds__(256)
 time_fft_fwd_batched(const InstDev* __restrict__ I, const int* __restrict__ act, int j) {
     const InstDev& d = I[act[blockIdx.y]];
-    if ((int)blockIdx.x * XW >= d.mp) return;
+    if ((int)blockIdx.x * XW >= d.mp || !d.ctl[0]) return;
     fwd_body<float>(d.m, d.mp, d.logs, d.V + (size_t)j * d.n, d.tws32, (float2*)d.rhat, blockIdx.x);
 }
 
 __global__ void __launch_bounds__(256)
 time_fft_inv_batched(const InstDev* __restrict__ I, const int* __restrict__ act, int j) {
     const InstDev& d = I[act[blockIdx.y]];
-    if ((int)blockIdx.x * XW >= d.mp) return;
+    if ((int)blockIdx.x * XW >= d.mp || !d.ctl[0]) return;
     inv_body<float>(d.m, d.mp, d.logs, (const float2*)d.rhat, d.tws32, d.Z + (size_t)j * d.n, blockIdx.x);
 }
 

@@ -115,7 +115,7 @@ def _dataset(net, probs, precision="fp32"):
     feats, targets = [], []
     for c0 in range(0, len(probs), 64):
         chunk = probs[c0:c0 + 64]
-        with FDEBatch(chunk) as b:
+        with FDEBatch(chunk, device_inputs=True) as b:  # solutions stay on the device
             b.assemble().factor(precision)
             xs, st = b.solve(tol=1e-10)
             assert all(s_["status"] == 0 for s_ in st)

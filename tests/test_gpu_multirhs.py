@@ -38,6 +38,31 @@ def test_shared_factors_solve_every_right_hand_side(precision):
     assert np.linalg.norm(xs[0] - xs[4]) > 1e-3 * np.linalg.norm(xs[0])
 
 
+def test_shared_factors_tensor_core_panels():
+    """Four right-hand sides of the benchmark operator (alpha = 1.8, d+ = 1+x, d- = 2-x,
+    GBDF5) at m = 1023, s = 64: eight 128-column panels of the tensor-core LU (the
+    look-ahead path with interior row-pair updates), 33 shared Strang blocks.  Each
+    solution against the oracle's FP64 Strang FGMRES of its own system."""
+    from paper_1305_6653_gb300 import FDEBatch
+    probs = fi.config_many_rhs(count=4, m=1023, s=64)
+    with FDEBatch(probs) as b:
+        b.share_operator().assemble().factor("tf32")
+        xs, stats = b.solve(tol=1e-11, restart=20, maxit=400)
+        xs = [x.cpu().numpy() for x in xs]
+    # the oracle's FGMRES with one factorisation (the operator is shared), to a true residual
+    # of 1e-11: its FP64 floor at this size is 1.5e-12 (a tighter tolerance never converges)
+    J = O.j_of(probs[0])
+    AB = O.bvm_matrices(probs[0].family, probs[0].mu, probs[0].s)
+    P = O.StrangPreconditioner(probs[0], J=J)
+    for pr, x, st in zip(probs, xs, stats):
+        b = O.reduced_rhs(pr, J=J)
+        ref, _, ok, _ = O.gmres(lambda z: O.matvec(pr, z, J=J, AB=AB), b, precond=P.apply, side="right",
+                                restart=20, tol=1e-11, maxit=200, reference="b")
+        assert ok and st["status"] == 0, st
+        assert np.linalg.norm(x - ref) <= 1e-8 * np.linalg.norm(ref), (pr.name, st)
+        assert np.abs(x - ref).max() <= 1e-8 * np.abs(ref).max(), pr.name
+
+
 def test_shared_operator_is_checked():
     from paper_1305_6653_gb300 import FDEBatch, FdeError
     a = fi.manufactured(63, 16, 1.5, "GBDF3")

@@ -85,6 +85,66 @@ def test_matvec(name, make):
     assert np.abs(y - ref).max() <= 1e-12 * scale
 
 
+# FP32 Toeplitz apply (fde_matvec_fp32).  Only J w runs in FP32 (w = the B-band sum of a
+# time row, rounded once to FP32; a length-L/2 complex FFT and its split, the product with
+# the FP32 symbol, a length-L inverse FFT; twiddles accurate to FP32).  The 2-norm error
+# bound of an FFT with twiddle error mu is log2(n) eta / (1 - log2(n) eta) ||x||, eta =
+# mu + gamma_4 (sqrt 2 + mu) ~ 6.7 u (Higham, Accuracy and Stability, Thm. 24.2); two
+# transforms, the split and the symbol product give ||C w - fl(C w)||_2 <=
+# (2 log2(L) 6.7 + 4) u_32 ||lambda_C||_inf ||w||_2 for the complex circulant C = G + i G^T
+# that yields G w and G^T w together, ||lambda_C||_inf <= 2 sum |g_k| = 4 alpha (Wiener
+# bound of Sec. 3.2), and J w = dx^-alpha (D+ Re + D- Im) adds the factor max(d+ + d-)
+# dx^-alpha; u_32 = 2^-24.  Every entry of row t is held to h times that bound for w_t
+# (the A-band part and the output are FP64).
+@pytest.mark.parametrize("name,make", CASES, ids=[c[0] for c in CASES])
+def test_matvec_fp32(name, make):
+    prob = make()
+    rng = np.random.default_rng(13)
+    z = rng.standard_normal(prob.n)
+    with _gpu(prob, precision=None) as p:
+        zt = torch.as_tensor(z, device="cuda")
+        y = p.matvec_fp32(zt).cpu().numpy().reshape(prob.s, prob.m)
+        y64 = p.matvec(zt).cpu().numpy().reshape(prob.s, prob.m)
+    ref = O.matvec(prob, z).reshape(prob.s, prob.m)
+    _, B = O.bvm_matrices(prob.family, prob.mu, prob.s)
+    W = B[1:, 1:] @ z.reshape(prob.s, prob.m)  # the input of the Toeplitz apply, row by row
+    L = 2
+    while L < 2 * prob.m:
+        L *= 2
+    lam = 4 * prob.alpha * (prob.dplus + prob.dminus).max() * prob.dx ** (-prob.alpha)
+    u32 = 2.0 ** -24
+    bound = (2 * np.log2(L) * 6.7 + 4) * u32 * prob.h * lam * np.linalg.norm(W, axis=1)
+    err = np.abs(y - ref).max(axis=1)
+    jscale = 2 * prob.alpha * (prob.dplus + prob.dminus).max() * prob.dx ** (-prob.alpha)
+    fp64_floor = 1e-12 * (prob.h * jscale * np.abs(z).max() + 4 * np.abs(z).max())
+    assert np.all(err <= bound + fp64_floor), (err / (bound + fp64_floor)).max()
+    if prob.m >= 63:  # and it is the FP32 path: far above the FP64 product's error
+        assert np.abs(y - ref).max() > 100 * np.abs(y64 - ref).max()
+
+
+@pytest.mark.parametrize("relax", [0.0, 1e-4])
+@pytest.mark.parametrize("name,make", [c for c in CASES if c[0] in ("small", "ragged_gbdf5", "m255_s64")],
+                         ids=["small", "ragged_gbdf5", "m255_s64"])
+def test_solve_with_fp32_arnoldi_products(name, make, relax):
+    """Flexible GMRES with the FP32 Toeplitz apply in the Arnoldi products (all of them, or
+    while the residual estimate is above 1e-4): the FP64 true residual at every restart still
+    drives the solution to the oracle's within 1e-8."""
+    prob = make()
+    if prob.n <= 5000:
+        ref = O.direct_solve(prob)
+    else:
+        ref, _, ok, _ = O.solve_strang_gmres(prob, side="right", tol=1e-12)
+        assert ok
+    with _gpu(prob, "tf32") as p:
+        x, st = p.solve(tol=1e-11, restart=20, maxit=400, matvec="fp32", relax=relax)
+        xs = x.cpu().numpy()
+    assert st["status"] == 0, st
+    assert st["matvecs_fp32"] >= 1
+    if relax == 0.0:
+        assert st["matvecs_fp32"] == st["iterations"]
+    assert np.linalg.norm(xs - ref) <= 1e-8 * np.linalg.norm(ref), st
+
+
 @pytest.mark.parametrize("name,make", CASES, ids=[c[0] for c in CASES])
 def test_precond_apply_fp64(name, make):
     prob = make()
@@ -93,7 +153,9 @@ def test_precond_apply_fp64(name, make):
     with _gpu(prob, "fp64") as p:
         z = p.precond_apply(torch.as_tensor(r, device="cuda")).cpu().numpy()
     ref = O.StrangPreconditioner(prob).apply(r)
-    assert np.linalg.norm(z - ref) <= 1e-10 * np.linalg.norm(ref)
+    # elementwise, against the largest entry (the bound above is normwise; the FP64
+    # differences are ~1e-14 of max|z|)
+    assert np.abs(z - ref).max() <= 1e-10 * np.abs(ref).max()
 
 
 # Reconstruction tolerance of L U against B_k, relative to max|B_k|: FP64 and FP32
@@ -157,6 +219,42 @@ def test_device_inputs_and_warm_start():
         x, st = p.solve(tol=1e-10, x0=x0)
         assert st["iterations"] <= 1
         np.testing.assert_allclose(x.cpu().numpy(), ref, rtol=0, atol=1e-8 * np.abs(ref).max())
+
+
+def test_host_solution_vectors_through_the_abi():
+    """desc->device_ptrs = 0: pgmres_solve takes x0 and writes x_out in host memory
+    (the library copies them on its stream).  Raw C-ABI call with numpy buffers."""
+    import ctypes as C
+
+    from paper_1305_6653_gb300 import FdePgmresOpts, FdeStats, _lib
+    prob = fi.config_small()
+    ref = O.direct_solve(prob)
+    lib = _lib.load()
+    with _gpu(prob, "fp64") as p:
+        assert not p.device_ptrs
+        opts = FdePgmresOpts(1e-11, 20, 400, 1)
+        x = np.full(prob.n, np.nan)
+        st = FdeStats()
+        assert lib.pgmres_solve(p.h, C.byref(opts), None, C.c_void_p(x.ctypes.data), C.byref(st)) == 0
+        assert np.linalg.norm(x - ref) <= 1e-8 * np.linalg.norm(ref)
+        # a host initial guess, aliased with the output: the exact solution needs no iteration
+        x2 = ref.copy()
+        assert lib.pgmres_solve(p.h, C.byref(opts), C.c_void_p(x2.ctypes.data), C.c_void_p(x2.ctypes.data),
+                                C.byref(st)) == 0
+        assert st.iterations <= 1 and st.x0_rejected == 0
+        np.testing.assert_allclose(x2, ref, rtol=0, atol=1e-8 * np.abs(ref).max())
+
+
+def test_host_batch_solutions():
+    from paper_1305_6653_gb300 import FDEBatch
+    probs = [fi.config_small(), _variable(100, 16, "GBDF5", 1.8)]
+    with FDEBatch(probs) as b:
+        b.assemble().factor("fp32")
+        xs, stats = b.solve(tol=1e-11)
+    for prob, x, st in zip(probs, xs, stats):
+        assert not x.is_cuda and st["status"] == 0
+        ref = O.direct_solve(prob)
+        assert np.linalg.norm(x.numpy() - ref) <= 1e-8 * np.linalg.norm(ref)
 
 
 def test_error_paths():
