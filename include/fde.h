@@ -377,6 +377,31 @@ int fde_profile_read(fde_problem* p, int stage, double* total_ms, int* launches)
 /* Number of kernels this library has launched in this process (all problems). */
 long long fde_launch_count(void);
 
+/* ---- launch-shape autotuner ----------------------------------------------
+ * Two kernel families have variants that compute bit-identical results and differ
+ * only in how the work is spread over threads: the space-time matvec (threads per
+ * time row: 1024, 512, 256, i.e. one, two or more CTAs per SM) and the block
+ * triangular solves (512 threads with 4 rows per register buffer, 384 with 8, 640
+ * with 2).  By default the first use of a shape (the matvec in bvm_assemble, the
+ * block solves at the end of strang_precond_factor) times every variant with CUDA
+ * events on the problem's stream and keeps the fastest for that shape (m_p, s or
+ * s/2+1 blocks, precision) in a process-wide table, which is also appended to a text
+ * file ($FDE_TUNE_CACHE, default $HOME/.cache/libfde_tune.txt; FDE_TUNE_CACHE=""
+ * keeps it in memory) and read back by later processes. */
+#define FDE_TUNE_MATVEC 0
+#define FDE_TUNE_TRSV 1
+#define FDE_TUNE_KERNELS 2
+/* variant -1: autotune (the default); 0 .. n-1: always launch that variant
+ * (0 is the built-in default).  Process-wide.  Errors: FDE_ERR_ARG. */
+int fde_tune_set(int kernel, int variant);
+/* Use `path` for the tuning table (NULL or "": memory only), dropping the table in
+ * memory and loading the file's entries.  Errors: none. */
+int fde_tune_cache(const char* path);
+/* The variant the table holds for a shape (nb: s for the matvec, s/2+1 for the block
+ * solves), the forced variant when one is set, or -1 if the shape is not tuned yet.
+ * Errors: FDE_ERR_ARG. */
+int fde_tune_query(int kernel, int mp, int nb, int precision, int* variant);
+
 /* Return the library's cached device memory to the CUDA driver.  Buffers freed by
  * fde_problem_destroy / fde_batch_destroy (and replaced workspaces) are kept in a
  * process-wide cache of at most 16 GiB, keyed by exact size, so that the next

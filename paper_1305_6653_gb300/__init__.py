@@ -76,6 +76,23 @@ def fde_release_cached_memory() -> None:
     _lib.check(_lib.load().fde_release_cached_memory(), "fde_release_cached_memory")
 
 
+def fde_tune_set(kernel: int, variant: int) -> None:
+    """Force a launch-shape variant of a tuned kernel family (-1: autotune)."""
+    _lib.check(_lib.load().fde_tune_set(int(kernel), int(variant)), "fde_tune_set")
+
+
+def fde_tune_cache(path: str | None) -> None:
+    """Use `path` for the tuning table (None or "": memory only)."""
+    _lib.check(_lib.load().fde_tune_cache(path.encode() if path else None), "fde_tune_cache")
+
+
+def fde_tune_query(kernel: int, mp: int, nb: int, precision) -> int:
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    v = C.c_int()
+    _lib.check(_lib.load().fde_tune_query(int(kernel), int(mp), int(nb), prec, C.byref(v)), "fde_tune_query")
+    return v.value
+
+
 def fde_problem_destroy(h) -> None:
     if h:
         _lib.load().fde_problem_destroy(h)

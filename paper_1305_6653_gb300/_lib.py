@@ -37,7 +37,7 @@ EXPORTED = [
     "fde_problem_destroy",
     "fde_last_error", "fde_matvec", "fde_matvec_fp32", "fde_precond_apply", "fde_get_rhs", "fde_get_factor_block",
     "fde_get_grunwald", "fde_problem_sizes", "fde_profile_enable", "fde_profile_select", "fde_profile_read", "fde_launch_count",
-    "fde_release_cached_memory",
+    "fde_release_cached_memory", "fde_tune_set", "fde_tune_cache", "fde_tune_query",
     "fde_precond_apply_noalloc", "fde_batch_create", "fde_batch_share_operator", "fde_batch_assemble",
     "fde_batch_factor",
     "fde_batch_solve", "fde_batch_size", "fde_batch_problem", "fde_batch_destroy",
@@ -45,6 +45,7 @@ EXPORTED = [
     "fde_nop_forward", "fde_nop_loss_grad", "fde_nop_adam_step", "fde_nop_features", "fde_nop_warm_start",
     "fde_nop_destroy", "fde_nop_coefficients", "fde_nop_synthesize",
 ]
+FDE_TUNE_MATVEC, FDE_TUNE_TRSV = 0, 1
 STAGES = ["assemble", "form", "lu_diag", "lu_panel", "lu_update", "tfft_fwd", "trsv", "tfft_inv", "matvec",
           "krylov", "lu_tc", "lu_pack", "lu_panel_tc"]
 
@@ -115,6 +116,9 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "fde_profile_read": (i32, [vp, i32, C.POINTER(f64), C.POINTER(i32)]),
         "fde_launch_count": (C.c_longlong, []),
         "fde_release_cached_memory": (C.c_int, []),
+        "fde_tune_set": (i32, [i32, i32]),
+        "fde_tune_cache": (i32, [C.c_char_p]),
+        "fde_tune_query": (i32, [i32, i32, i32, i32, C.POINTER(i32)]),
         "fde_precond_apply_noalloc": (i32, [vp, vp, vp]),
         "fde_batch_create": (i32, [C.POINTER(FdeProblemDesc), i32, vp, C.POINTER(vp)]),
         "fde_batch_assemble": (i32, [vp]),

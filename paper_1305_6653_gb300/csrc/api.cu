@@ -764,7 +764,8 @@ int bvm_assemble(fde_problem* h) {
     if ((rc = launch_rhs(P, P.d_work, P.stream))) return rc;
     FDE_CUDA_TRY(cudaGetLastError());
     P.assembled = true;
-    return FDE_OK;
+    // first problem of this shape: time the launch shapes of the space-time product
+    return autotune_matvec(P);
 }
 
 int strang_precond_factor(fde_problem* h, int precision) {
@@ -796,7 +797,8 @@ int strang_precond_factor(fde_problem* h, int precision) {
         }
     P.factored = true;
     P.precond = FDE_PRECOND_STRANG;
-    return FDE_OK;
+    // first factors of this shape: time the launch shapes of the block solves
+    return autotune_trsv(P);
 }
 
 int bccb_precond_setup(fde_problem* h, int modified, int precision) {

@@ -278,6 +278,20 @@ void dev_free(void* p);
 // Frees every cached block (blocks in use are not affected).
 int dev_release_cached();
 
+// tune.cu: launch-shape autotuner.  tune_lookup returns the variant to launch for a
+// shape (forced, tabulated, or 0 = the built-in default, with *need_tuning set when
+// the shape has not been measured yet); tune_measure times every variant of fn and
+// returns the fastest; tune_store records it (memory and the cache file).
+int tune_variants(int kernel);
+int tune_lookup(int kernel, int mp, int nb, int prec, bool* need_tuning);
+void tune_store(int kernel, int mp, int nb, int prec, int variant);
+int tune_measure(int kernel, cudaStream_t st, int (*fn)(void*, int, cudaStream_t), void* ctx, int* best);
+// the tuned kernels' variant launchers (matvec.cu, lu.cu) and the tuning passes
+int launch_matvec64_variant(const Problem& P, const double* z, double* y, int variant, cudaStream_t st);
+int launch_block_trsv_variant(const Problem& P, void* rhat, int variant, cudaStream_t st);
+int autotune_matvec(Problem& P);
+int autotune_trsv(Problem& P);
+
 // The problem behind a C-ABI handle (defined in api.cu).
 Problem* problem_of(fde_problem* h);
 int ensure_factor_buffers(Problem& P, int precision);

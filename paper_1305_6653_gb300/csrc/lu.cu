@@ -465,13 +465,21 @@ __device__ __forceinline__ void named_arrive(int id, int n) {
     asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
 }
 
-constexpr int TRSV_THREADS = 512;
+constexpr int TRSV_THREADS = 512;                           // the default launch shape
 constexpr int TRSV_TPR = 8;                                  // threads per row in the strip update
-constexpr int TRSV_GROUPS = (TRSV_THREADS - 32) / TRSV_TPR;  // 60 row groups in warps 1..15
 constexpr int TRSV_BAR_X = 1, TRSV_BAR_B = 3;                // named barrier ids (+ d & 1)
 // Rows per group whose loads are in flight together: 8 x 2 x 16 B per thread for
 // FP32 factors; FP64 rows are twice as wide per element, 4 keep it spill-free.
 template <typename T> struct trsv_unroll { static constexpr int value = sizeof(T) == 4 ? 8 : 4; };
+// Launch shapes of the block solves (FDE_TUNE_TRSV): NT threads (warp 0 the solver,
+// NT/32 - 1 streaming warps of (NT - 32) / TRSV_TPR row groups) and H rows per
+// register buffer.  The arithmetic of every row does not depend on the shape: each
+// row's strip product is the same 32-term sum, reduced by the same TRSV_TPR lanes in
+// the same order, so all shapes give bit-identical results.
+template <typename T, int V> struct trsv_shape;
+template <typename T> struct trsv_shape<T, 0> { static constexpr int NT = 512, H = trsv_unroll<T>::value / 2; };
+template <typename T> struct trsv_shape<T, 1> { static constexpr int NT = 384, H = trsv_unroll<T>::value; };
+template <typename T> struct trsv_shape<T, 2> { static constexpr int NT = 640, H = trsv_unroll<T>::value / 4; };
 // Solver tiles in shared memory: planar, rows padded by 16 bytes (16-byte aligned
 // cp.async destinations); [buffer 2][D, L][Re, Im][32][LD].
 template <typename T> struct trsv_tile { static constexpr int LD = 32 + 16 / (int)sizeof(T); };
@@ -498,7 +506,7 @@ __device__ __forceinline__ void tile_async(T* dst, const T* plane, int mp, int r
 // Solver side of one sweep (warp 0).  INV: the inverted diagonal tiles are given
 // (tinv: per tile [L^-1 re, L^-1 im, U^-1 re, U^-1 im][32][32]) and a tile solve is
 // the product x = D^-1 a; otherwise the tile is solved by substitution.
-template <typename T, bool FWD, bool INV>
+template <typename T, bool FWD, bool INV, int NT>
 __device__ __forceinline__ void trsv_solver(int mp, int nt, const T* re, const T* im, const cplx_t<T>* dv,
                                             const T* tinv, cplx_t<T>* y, cplx_t<T> (*xs)[32], T* tiles,
                                             cplx_t<T>* av, int lane) {
@@ -533,8 +541,11 @@ __device__ __forceinline__ void trsv_solver(int mp, int nt, const T* re, const T
         const T* Lim = Dre + 3 * TS;
         cp_async_wait1();
         __syncwarp();
-        if (d >= 2) named_sync(TRSV_BAR_B + (d & 1), TRSV_THREADS);  // strip d-2 has reached tile d
+        if (d >= 2) named_sync(TRSV_BAR_B + (d & 1), NT);  // strip d-2 has reached tile d
         C a = y[r0 + lane];
+        // Every product below is written as explicit fused multiply-adds, so that the
+        // rounding is fixed by the source and not by how the compiler contracts a
+        // particular instantiation (the launch shapes must give bit-identical results).
         if (d >= 1) {  // look-ahead: strip d-1 on tile d's rows
             const C* xp = xs[(d - 1) & 1];
             T sx0 = 0, sy0 = 0, sx1 = 0, sy1 = 0;
@@ -543,10 +554,10 @@ __device__ __forceinline__ void trsv_solver(int mp, int nt, const T* re, const T
                 const C x0 = xp[c], x1 = xp[c + 1];
                 const T l0r = Lre[lane * LD + c], l0i = Lim[lane * LD + c];
                 const T l1r = Lre[lane * LD + c + 1], l1i = Lim[lane * LD + c + 1];
-                sx0 += l0r * x0.x - l0i * x0.y;
-                sy0 += l0r * x0.y + l0i * x0.x;
-                sx1 += l1r * x1.x - l1i * x1.y;
-                sy1 += l1r * x1.y + l1i * x1.x;
+                sx0 = fma(-l0i, x0.y, fma(l0r, x0.x, sx0));
+                sy0 = fma(l0i, x0.x, fma(l0r, x0.y, sy0));
+                sx1 = fma(-l1i, x1.y, fma(l1r, x1.x, sx1));
+                sy1 = fma(l1i, x1.x, fma(l1r, x1.y, sy1));
             }
             a.x -= sx0 + sx1;
             a.y -= sy0 + sy1;
@@ -560,10 +571,10 @@ __device__ __forceinline__ void trsv_solver(int mp, int nt, const T* re, const T
                 const C a0 = av[c], a1 = av[c + 1];
                 const T d0r = Dre[lane * LD + c], d0i = Dim[lane * LD + c];
                 const T d1r = Dre[lane * LD + c + 1], d1i = Dim[lane * LD + c + 1];
-                sx0 += d0r * a0.x - d0i * a0.y;
-                sy0 += d0r * a0.y + d0i * a0.x;
-                sx1 += d1r * a1.x - d1i * a1.y;
-                sy1 += d1r * a1.y + d1i * a1.x;
+                sx0 = fma(-d0i, a0.y, fma(d0r, a0.x, sx0));
+                sy0 = fma(d0i, a0.x, fma(d0r, a0.y, sy0));
+                sx1 = fma(-d1i, a1.y, fma(d1r, a1.x, sx1));
+                sy1 = fma(d1i, a1.x, fma(d1r, a1.y, sy1));
             }
             a.x = sx0 + sx1;
             a.y = sy0 + sy1;
@@ -574,8 +585,8 @@ __device__ __forceinline__ void trsv_solver(int mp, int nt, const T* re, const T
                 const T yy = __shfl_sync(0xffffffffu, a.y, c);
                 if (lane > c) {
                     const T lr = Dre[lane * LD + c], li = Dim[lane * LD + c];
-                    a.x -= lr * yx - li * yy;
-                    a.y -= lr * yy + li * yx;
+                    a.x = fma(li, yy, fma(-lr, yx, a.x));
+                    a.y = fma(-li, yx, fma(-lr, yy, a.y));
                 }
             }
         } else {
@@ -587,15 +598,15 @@ __device__ __forceinline__ void trsv_solver(int mp, int nt, const T* re, const T
                 const T yy = __shfl_sync(0xffffffffu, a.y, c);
                 if (lane < c) {
                     const T ur = Dre[lane * LD + c], ui = Dim[lane * LD + c];
-                    a.x -= ur * yx - ui * yy;
-                    a.y -= ur * yy + ui * yx;
+                    a.x = fma(ui, yy, fma(-ur, yx, a.x));
+                    a.y = fma(-ui, yx, fma(-ur, yy, a.y));
                 }
             }
         }
         y[r0 + lane] = a;
         xs[d & 1][lane] = a;
         __syncwarp();
-        if (d <= nt - 3) named_arrive(TRSV_BAR_X + (d & 1), TRSV_THREADS);
+        if (d <= nt - 3) named_arrive(TRSV_BAR_X + (d & 1), NT);
         if (d + 2 < nt) issue(d + 2);  // buffer d & 1 is free again
         cp_async_commit();
     }
@@ -608,12 +619,14 @@ __device__ __forceinline__ void trsv_solver(int mp, int nt, const T* re, const T
 // the shuffles stay warp-uniform.  Two register buffers of H rows alternate: the
 // loads of one are in flight while the other is applied, so the load pipe does
 // not drain between batches.
-template <typename T, bool FWD>
+template <typename T, bool FWD, int NT, int H>
 __device__ __forceinline__ void trsv_stream(int mp, int nt, const T* re, const T* im, cplx_t<T>* y,
                                             const cplx_t<T> (*xs)[32], int bt) {
     using C = cplx_t<T>;
     using V = typename vec4<T>::type;
-    constexpr int H = trsv_unroll<T>::value / 2, HG = H * TRSV_GROUPS;
+    constexpr int TRSV_GROUPS = (NT - 32) / TRSV_TPR;  // a multiple of 4 (NT is a multiple of 32)
+    constexpr int HG = H * TRSV_GROUPS;
+    static_assert(HG >= 32, "the first batch must cover tile d+2");
     const int g = bt / TRSV_TPR, sub = bt % TRSV_TPR;
     for (int d = 0; d + 2 < nt; ++d) {
         const int col = 32 * (FWD ? d : nt - 1 - d) + sub * 4;
@@ -639,10 +652,23 @@ __device__ __forceinline__ void trsv_stream(int mp, int nt, const T* re, const T
                 const int q = q0 + u * TRSV_GROUPS;
                 const V& vr = ar[b][u];
                 const V& vi = ai[b][u];
-                T sx = vr.x * x0.x - vi.x * x0.y + vr.y * x1.x - vi.y * x1.y + vr.z * x2.x - vi.z * x2.y +
-                       vr.w * x3.x - vi.w * x3.y;
-                T sy = vr.x * x0.y + vi.x * x0.x + vr.y * x1.y + vi.y * x1.x + vr.z * x2.y + vi.z * x2.x +
-                       vr.w * x3.y + vi.w * x3.x;
+                // explicit fused multiply-adds: the same rounding in every launch shape
+                T sx = vr.x * x0.x;
+                sx = fma(-vi.x, x0.y, sx);
+                sx = fma(vr.y, x1.x, sx);
+                sx = fma(-vi.y, x1.y, sx);
+                sx = fma(vr.z, x2.x, sx);
+                sx = fma(-vi.z, x2.y, sx);
+                sx = fma(vr.w, x3.x, sx);
+                sx = fma(-vi.w, x3.y, sx);
+                T sy = vr.x * x0.y;
+                sy = fma(vi.x, x0.x, sy);
+                sy = fma(vr.y, x1.y, sy);
+                sy = fma(vi.y, x1.x, sy);
+                sy = fma(vr.z, x2.y, sy);
+                sy = fma(vi.z, x2.x, sy);
+                sy = fma(vr.w, x3.y, sy);
+                sy = fma(vi.w, x3.x, sy);
 #pragma unroll
                 for (int off = 1; off < TRSV_TPR; off <<= 1) {
                     sx += __shfl_xor_sync(0xffffffffu, sx, off);
@@ -659,13 +685,13 @@ __device__ __forceinline__ void trsv_stream(int mp, int nt, const T* re, const T
         };
         load(0, g);  // independent of x_d: in flight across the wait
         load(1, g + HG);
-        named_sync(TRSV_BAR_X + (d & 1), TRSV_THREADS);
+        named_sync(TRSV_BAR_X + (d & 1), NT);
         x0 = xs[d & 1][sub * 4];
         x1 = xs[d & 1][sub * 4 + 1];
         x2 = xs[d & 1][sub * 4 + 2];
         x3 = xs[d & 1][sub * 4 + 3];
         apply(0, g);  // covers q < 32 (tile d+2): groups 0..31, u = 0
-        named_arrive(TRSV_BAR_B + (d & 1), TRSV_THREADS);
+        named_arrive(TRSV_BAR_B + (d & 1), NT);
         for (int q0 = g + HG; q0 < len; q0 += 2 * HG) {
             load(0, q0 + HG);
             apply(1, q0);
@@ -676,7 +702,7 @@ __device__ __forceinline__ void trsv_stream(int mp, int nt, const T* re, const T
     }
 }
 
-template <typename T, bool INV>
+template <typename T, bool INV, int NT = TRSV_THREADS, int H = trsv_unroll<T>::value / 2>
 __device__ __forceinline__ void trsv_body(int mp, const T* __restrict__ re, const cplx_t<T>* __restrict__ dv,
                                           const T* __restrict__ tinv, cplx_t<T>* __restrict__ x) {
     using C = cplx_t<T>;
@@ -690,22 +716,24 @@ __device__ __forceinline__ void trsv_body(int mp, const T* __restrict__ re, cons
     const int nt = mp / 32;
     for (int i = threadIdx.x; i < mp; i += blockDim.x) y[i] = x[i];
     __syncthreads();
-    if (warp == 0) trsv_solver<T, true, INV>(mp, nt, re, im, dv, tinv, y, xs, tiles, av, lane);
-    else trsv_stream<T, true>(mp, nt, re, im, y, xs, threadIdx.x - 32);
+    if (warp == 0) trsv_solver<T, true, INV, NT>(mp, nt, re, im, dv, tinv, y, xs, tiles, av, lane);
+    else trsv_stream<T, true, NT, H>(mp, nt, re, im, y, xs, threadIdx.x - 32);
     __syncthreads();
-    if (warp == 0) trsv_solver<T, false, INV>(mp, nt, re, im, dv, tinv, y, xs, tiles, av, lane);
-    else trsv_stream<T, false>(mp, nt, re, im, y, xs, threadIdx.x - 32);
+    if (warp == 0) trsv_solver<T, false, INV, NT>(mp, nt, re, im, dv, tinv, y, xs, tiles, av, lane);
+    else trsv_stream<T, false, NT, H>(mp, nt, re, im, y, xs, threadIdx.x - 32);
     __syncthreads();
     for (int i = threadIdx.x; i < mp; i += blockDim.x) x[i] = y[i];
 }
 
-template <typename T>
-__global__ void __launch_bounds__(TRSV_THREADS)
+template <typename T, int V = 0>
+__global__ void __launch_bounds__(trsv_shape<T, V>::NT)
 block_trsv_kernel(int mp, const T* __restrict__ fac, const cplx_t<T>* __restrict__ dinv, const T* __restrict__ tinv,
                   cplx_t<T>* __restrict__ rhat) {
     const int k = blockIdx.x;
-    trsv_body<T, true>(mp, fac + (size_t)k * 2 * mp * mp, dinv + (size_t)k * mp,
-                       tinv + (size_t)k * (mp / 32) * 4096, rhat + (size_t)k * mp);
+    trsv_body<T, true, trsv_shape<T, V>::NT, trsv_shape<T, V>::H>(mp, fac + (size_t)k * 2 * mp * mp,
+                                                                  dinv + (size_t)k * mp,
+                                                                  tinv + (size_t)k * (mp / 32) * 4096,
+                                                                  rhat + (size_t)k * mp);
 }
 
 // Batched over the active instances act[0..gridDim.x): block k = blockIdx.y of instance act[blockIdx.x].
@@ -1782,21 +1810,59 @@ int launch_block_lu(Problem& P, int prec, cudaStream_t st) {
     return launch_tile_inverse(P, prec, st);
 }
 
-int launch_block_trsv(const Problem& P, void* rhat, cudaStream_t st) {
-    if (P.precision == FDE_FP64) {
-        const size_t smem = trsv_smem_bytes(P.mp, sizeof(double));
-        FDE_CUDA_TRY(cudaFuncSetAttribute(block_trsv_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)smem));
-        block_trsv_kernel<double><<<P.nblk, TRSV_THREADS, smem, st>>>(
-            P.mp, (const double*)P.d_fac, (const double2*)P.d_dinv, (const double*)P.d_tinv, (double2*)rhat);
-    } else {
-        const size_t smem = trsv_smem_bytes(P.mp, sizeof(float));
-        FDE_CUDA_TRY(cudaFuncSetAttribute(block_trsv_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)smem));
-        block_trsv_kernel<float><<<P.nblk, TRSV_THREADS, smem, st>>>(
-            P.mp, (const float*)P.d_fac, (const float2*)P.d_dinv, (const float*)P.d_tinv, (float2*)rhat);
-    }
+template <typename T, int V>
+static int launch_trsv_shape(const Problem& P, void* rhat, cudaStream_t st) {
+    const size_t smem = trsv_smem_bytes(P.mp, sizeof(T));
+    auto kern = block_trsv_kernel<T, V>;
+    FDE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<P.nblk, trsv_shape<T, V>::NT, smem, st>>>(P.mp, (const T*)P.d_fac, (const cplx_t<T>*)P.d_dinv,
+                                                      (const T*)P.d_tinv, (cplx_t<T>*)rhat);
     FDE_LAUNCH_CHECK("block_trsv_kernel");
+    return FDE_OK;
+}
+
+int launch_block_trsv_variant(const Problem& P, void* rhat, int variant, cudaStream_t st) {
+    if (P.precision == FDE_FP64) {
+        if (variant == 1) return launch_trsv_shape<double, 1>(P, rhat, st);
+        if (variant == 2) return launch_trsv_shape<double, 2>(P, rhat, st);
+        return launch_trsv_shape<double, 0>(P, rhat, st);
+    }
+    if (variant == 1) return launch_trsv_shape<float, 1>(P, rhat, st);
+    if (variant == 2) return launch_trsv_shape<float, 2>(P, rhat, st);
+    return launch_trsv_shape<float, 0>(P, rhat, st);
+}
+
+int launch_block_trsv(const Problem& P, void* rhat, cudaStream_t st) {
+    const int prec = P.precision == FDE_FP64 ? FDE_FP64 : FDE_FP32;  // factor storage
+    return launch_block_trsv_variant(P, rhat, tune_lookup(FDE_TUNE_TRSV, P.mp, P.nblk, prec, nullptr), st);
+}
+
+namespace {
+struct TrsvTuneCtx {
+    const Problem* P;
+    void* rhat;
+};
+int trsv_trial(void* ctx, int v, cudaStream_t st) {
+    const TrsvTuneCtx& c = *static_cast<const TrsvTuneCtx*>(ctx);
+    return launch_block_trsv_variant(*c.P, c.rhat, v, st);
+}
+}  // namespace
+
+// Measure the block-solve shapes for this problem's factors, on its frequency-side
+// vector (zeroed first: the solves run in place and their timing does not depend on
+// the data), unless the table already has the shape or a variant is forced.
+int autotune_trsv(Problem& P) {
+    const int prec = P.precision == FDE_FP64 ? FDE_FP64 : FDE_FP32;
+    bool need = false;
+    tune_lookup(FDE_TUNE_TRSV, P.mp, P.nblk, prec, &need);
+    if (!need) return FDE_OK;
+    const size_t esz = P.precision == FDE_FP64 ? sizeof(double) : sizeof(float);
+    FDE_CUDA_TRY(cudaMemsetAsync(P.d_rhat, 0, (size_t)P.nblk * P.mp * 2 * esz, P.stream));
+    TrsvTuneCtx ctx{&P, P.d_rhat};
+    int best = 0;
+    const int rc = tune_measure(FDE_TUNE_TRSV, P.stream, trsv_trial, &ctx, &best);
+    if (rc) return rc;
+    tune_store(FDE_TUNE_TRSV, P.mp, P.nblk, prec, best);
     return FDE_OK;
 }
 

@@ -105,8 +105,12 @@ __device__ __forceinline__ void matvec_body(int m, int logL, int mu, double h, c
     }
 }
 
-template <typename T, int MODE>
-__global__ void __launch_bounds__(1024)
+// NT: the most threads a launch uses (the launch takes min(NT, L/2), at least 64);
+// every loop is strided by blockDim.x, so all thread counts compute the same result
+// (each butterfly and each output is the same arithmetic on the same operands).
+// Register use is capped so that 1024 / NT CTAs fit an SM when shared memory allows.
+template <typename T, int MODE, int NT = 1024>
+__global__ void __launch_bounds__(NT, 1024 / NT)
 st_matvec_kernel(int m, int logL, int mu, double h, const int* __restrict__ start, const double* __restrict__ A,
                  const double* __restrict__ B, const double* __restrict__ dplus, const double* __restrict__ dminus,
                  const cplx_t<T>* __restrict__ sym, const cplx_t<T>* __restrict__ tw, const double* __restrict__ z,
@@ -161,15 +165,15 @@ int launch_matvec_batched(const InstDev* I, const int* act, int nact, int max_s,
     return FDE_OK;
 }
 
-template <int MODE, typename T = double>
+template <int MODE, typename T = double, int NT = 1024>
 static int launch_st(const Problem& P, const double* z, double* y, int ncols, cudaStream_t st,
                      const double* dplus = nullptr, const double* dminus = nullptr, int dstride = 0) {
     const int L = P.L;
     size_t smem = (size_t)L * sizeof(cplx_t<T>) + (MODE == 0 ? (size_t)P.m * sizeof(double) : 0);
     int threads = L / 2;
-    if (threads > 1024) threads = 1024;
+    if (threads > NT) threads = NT;
     if (threads < 64) threads = 64;
-    auto kern = st_matvec_kernel<T, MODE>;
+    auto kern = st_matvec_kernel<T, MODE, NT>;
     FDE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
     const cplx_t<T>* sym;
     const cplx_t<T>* tw;
@@ -192,8 +196,44 @@ int launch_matvec32(const Problem& P, const double* z, double* y, cudaStream_t s
     return launch_st<0, float>(P, z, y, P.s, st);
 }
 
+// The tuned variants of the FP64 space-time product: at most 1024, 512 or 256
+// threads per time row (FDE_TUNE_MATVEC).
+int launch_matvec64_variant(const Problem& P, const double* z, double* y, int variant, cudaStream_t st) {
+    if (variant == 1) return launch_st<0, double, 512>(P, z, y, P.s, st);
+    if (variant == 2) return launch_st<0, double, 256>(P, z, y, P.s, st);
+    return launch_st<0, double, 1024>(P, z, y, P.s, st);
+}
+
+namespace {
+struct MatvecTuneCtx {
+    const Problem* P;
+    const double* z;
+    double* y;
+};
+int matvec_trial(void* ctx, int v, cudaStream_t st) {
+    const MatvecTuneCtx& c = *static_cast<const MatvecTuneCtx*>(ctx);
+    return launch_matvec64_variant(*c.P, c.z, c.y, v, st);
+}
+}  // namespace
+
+// Measure the variants for this shape (z = b, y = the work vector) unless the table
+// already has it or a variant is forced.
+int autotune_matvec(Problem& P) {
+    if (P.timevar) return FDE_OK;
+    bool need = false;
+    tune_lookup(FDE_TUNE_MATVEC, P.mp, P.s, FDE_FP64, &need);
+    if (!need) return FDE_OK;
+    MatvecTuneCtx ctx{&P, P.d_b_rhs, P.d_work};
+    int best = 0;
+    const int rc = tune_measure(FDE_TUNE_MATVEC, P.stream, matvec_trial, &ctx, &best);
+    if (rc) return rc;
+    tune_store(FDE_TUNE_MATVEC, P.mp, P.s, FDE_FP64, best);
+    return FDE_OK;
+}
+
 int launch_matvec64(const Problem& P, const double* z, double* y, cudaStream_t st) {
-    if (!P.timevar) return launch_st<0>(P, z, y, P.s, st);
+    if (!P.timevar)
+        return launch_matvec64_variant(P, z, y, tune_lookup(FDE_TUNE_MATVEC, P.mp, P.s, FDE_FP64, nullptr), st);
     // J_q z_q for q = 1..s with the coefficients of time level q, then the BVM band
     int rc = launch_st<1>(P, z, P.d_jz, P.s, st, P.d_dplus_t + P.m, P.d_dminus_t + P.m, P.m);
     if (rc) return rc;

@@ -1,0 +1,162 @@
+// Autotuner of launch shapes: for a kernel family and a problem shape it keeps the
+// fastest of a few variants that compute bit-identical results (they differ only in
+// how the work is spread over threads), measured with CUDA events on the GPU at
+// first use and kept in a process-wide table that is also written to a text file
+// (one line per shape) and read back by later processes.
+#include <cstdio>
+#include <cstdlib>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+
+#include <sys/stat.h>
+
+#include "fde_internal.h"
+
+namespace fde {
+
+namespace {
+
+struct TuneState {
+    std::mutex mu;
+    bool loaded = false;
+    bool path_set = false;
+    std::string path;                       // empty: no file
+    int mode[FDE_TUNE_KERNELS] = {-1, -1};  // -1 autotune, >= 0 forced variant
+    std::map<std::tuple<int, int, int, int>, int> table;
+};
+
+TuneState& state() {
+    static TuneState s;
+    return s;
+}
+
+std::string default_path() {
+    const char* env = std::getenv("FDE_TUNE_CACHE");
+    if (env) return env;  // "" disables the file
+    const char* home = std::getenv("HOME");
+    return home ? std::string(home) + "/.cache/libfde_tune.txt" : std::string();
+}
+
+void load_locked(TuneState& s) {
+    if (s.loaded) return;
+    s.loaded = true;
+    if (!s.path_set) s.path = default_path();
+    if (s.path.empty()) return;
+    FILE* f = std::fopen(s.path.c_str(), "r");
+    if (!f) return;
+    char name[32];
+    int k, mp, nb, prec, v;
+    while (std::fscanf(f, "%31s %d %d %d %d %d", name, &k, &mp, &nb, &prec, &v) == 6)
+        if (k >= 0 && k < FDE_TUNE_KERNELS && v >= 0 && v < tune_variants(k)) s.table[{k, mp, nb, prec}] = v;
+    std::fclose(f);
+}
+
+}  // namespace
+
+int tune_variants(int kernel) { return kernel == FDE_TUNE_MATVEC ? 3 : kernel == FDE_TUNE_TRSV ? 3 : 0; }
+
+int tune_lookup(int kernel, int mp, int nb, int prec, bool* need_tuning) {
+    TuneState& s = state();
+    std::lock_guard<std::mutex> lock(s.mu);
+    load_locked(s);
+    if (need_tuning) *need_tuning = false;
+    if (s.mode[kernel] >= 0) return s.mode[kernel];
+    auto it = s.table.find({kernel, mp, nb, prec});
+    if (it != s.table.end()) return it->second;
+    if (need_tuning) *need_tuning = true;
+    return 0;
+}
+
+void tune_store(int kernel, int mp, int nb, int prec, int variant) {
+    TuneState& s = state();
+    std::lock_guard<std::mutex> lock(s.mu);
+    load_locked(s);
+    s.table[{kernel, mp, nb, prec}] = variant;
+    if (s.path.empty()) return;
+    FILE* f = std::fopen(s.path.c_str(), "a");
+    if (!f) {  // the cache directory may not exist yet: create its last level and retry
+        const size_t slash = s.path.rfind('/');
+        if (slash != std::string::npos && slash > 0) mkdir(s.path.substr(0, slash).c_str(), 0755);
+        f = std::fopen(s.path.c_str(), "a");
+        if (!f) return;  // the table stays in memory only
+    }
+    std::fprintf(f, "%s %d %d %d %d %d\n", kernel == FDE_TUNE_MATVEC ? "matvec" : "trsv", kernel, mp, nb, prec,
+                 variant);
+    std::fclose(f);
+}
+
+// Time fn(variant) for every variant (one untimed launch, then the best of three
+// timed ones) on stream st and return the fastest.  fn launches one kernel and
+// returns an FDE status.
+int tune_measure(int kernel, cudaStream_t st, int (*fn)(void*, int, cudaStream_t), void* ctx, int* best) {
+    cudaEvent_t e0, e1;
+    FDE_CUDA_TRY(cudaEventCreate(&e0));
+    FDE_CUDA_TRY(cudaEventCreate(&e1));
+    float best_ms = 1e30f;
+    *best = 0;
+    int rc = FDE_OK;
+    for (int v = 0; v < tune_variants(kernel) && !rc; ++v) {
+        if ((rc = fn(ctx, v, st))) break;
+        float vbest = 1e30f;
+        for (int r = 0; r < 3 && !rc; ++r) {
+            cudaEventRecord(e0, st);
+            rc = fn(ctx, v, st);
+            cudaEventRecord(e1, st);
+            if (rc) break;
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                rc = cuda_error(cudaGetLastError(), "autotune");
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < vbest) vbest = ms;
+        }
+        if (vbest < best_ms) {
+            best_ms = vbest;
+            *best = v;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
+}
+
+}  // namespace fde
+
+using namespace fde;
+
+extern "C" int fde_tune_set(int kernel, int variant) {
+    if (kernel < 0 || kernel >= FDE_TUNE_KERNELS) return set_error(FDE_ERR_ARG, "unknown kernel family");
+    if (variant < -1 || variant >= tune_variants(kernel)) return set_error(FDE_ERR_ARG, "variant out of range");
+    TuneState& s = state();
+    std::lock_guard<std::mutex> lock(s.mu);
+    s.mode[kernel] = variant;
+    return FDE_OK;
+}
+
+extern "C" int fde_tune_cache(const char* path) {
+    TuneState& s = state();
+    std::lock_guard<std::mutex> lock(s.mu);
+    s.path_set = true;
+    s.path = path ? path : "";
+    s.table.clear();
+    s.loaded = false;
+    load_locked(s);
+    return FDE_OK;
+}
+
+extern "C" int fde_tune_query(int kernel, int mp, int nb, int precision, int* variant) {
+    if (kernel < 0 || kernel >= FDE_TUNE_KERNELS || !variant) return set_error(FDE_ERR_ARG, "bad argument");
+    TuneState& s = state();
+    std::lock_guard<std::mutex> lock(s.mu);
+    load_locked(s);
+    if (s.mode[kernel] >= 0) {
+        *variant = s.mode[kernel];
+        return FDE_OK;
+    }
+    auto it = s.table.find({kernel, mp, nb, precision});
+    *variant = it == s.table.end() ? -1 : it->second;
+    return FDE_OK;
+}

@@ -43,14 +43,34 @@ def test_binding_lists_every_declared_symbol():
     assert sorted(_lib.EXPORTED) == _declared_functions()
 
 
-def test_struct_layouts_match_header():
+def test_struct_layouts_match_header(tmp_path):
+    """The ctypes structures have the C layout of include/fde.h: every field's offset
+    and each struct's size, printed by a C program compiled against the header."""
+    import shutil
+    import subprocess
+
     from paper_1305_6653_gb300 import _lib
-    # fde_problem_desc: 2 ints, 5 doubles, 2 pointers, 2 doubles, 2 ints, 2 pointers, 1 int (+ padding),
-    # 2 pointers (time-dependent coefficients)
-    assert ctypes.sizeof(_lib.FdeProblemDesc) == 8 + 40 + 16 + 16 + 8 + 16 + 8 + 16
-    assert _lib.FdeProblemDesc.dplus_t.offset == 112 and _lib.FdeProblemDesc.dminus_t.offset == 120
-    assert ctypes.sizeof(_lib.FdePgmresOpts) == 24
-    assert ctypes.sizeof(_lib.FdeStats) == 16 + 24 + 8
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"fde_problem_desc": _lib.FdeProblemDesc, "fde_pgmres_opts": _lib.FdePgmresOpts,
+               "fde_stats": _lib.FdeStats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "fde.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
 
 
 def test_argument_validation_needs_no_gpu(lib):
@@ -85,3 +105,26 @@ def test_release_of_an_empty_device_cache_needs_no_gpu(lib):
     from paper_1305_6653_gb300 import _lib, fde_release_cached_memory
     assert _lib.load().fde_release_cached_memory() == _lib.FDE_OK
     fde_release_cached_memory()
+
+
+def test_tune_table_is_host_side(tmp_path):
+    """fde_tune_set / fde_tune_cache / fde_tune_query need no GPU: argument checks and
+    a cache file read back."""
+    import ctypes as C
+
+    from paper_1305_6653_gb300 import _lib
+    lib = _lib.load()
+    assert lib.fde_tune_set(5, 0) == _lib.FDE_ERR_ARG
+    assert lib.fde_tune_set(0, 3) == _lib.FDE_ERR_ARG
+    f = tmp_path / "t.txt"
+    f.write_text("matvec 0 2048 256 0 1\ntrsv 1 2048 129 1 2\ntrsv 1 64 9 1 7\n")
+    assert lib.fde_tune_cache(str(f).encode()) == 0
+    v = C.c_int()
+    assert lib.fde_tune_query(0, 2048, 256, 0, C.byref(v)) == 0 and v.value == 1
+    assert lib.fde_tune_query(1, 2048, 129, 1, C.byref(v)) == 0 and v.value == 2
+    assert lib.fde_tune_query(1, 64, 9, 1, C.byref(v)) == 0 and v.value == -1  # out-of-range entry dropped
+    assert lib.fde_tune_query(1, 128, 9, 1, C.byref(v)) == 0 and v.value == -1
+    assert lib.fde_tune_set(1, 0) == 0
+    assert lib.fde_tune_query(1, 2048, 129, 1, C.byref(v)) == 0 and v.value == 0  # forced
+    assert lib.fde_tune_set(1, -1) == 0
+    assert lib.fde_tune_cache(None) == 0

@@ -1,0 +1,76 @@
+"""Launch-shape autotuner (fde_tune_*): the variants of the space-time matvec
+(threads per time row) and of the block triangular solves (threads, rows per
+register buffer) must give bit-identical results, so tuning can never change a
+solution; and a tuned shape is recorded in the table and its cache file."""
+import numpy as np
+import pytest
+
+import fde_inputs as fi
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def lib(tmp_path_factory):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    from paper_1305_6653_gb300 import _lib
+    lib = _lib.load()
+    path = str(tmp_path_factory.mktemp("tune") / "tune.txt")
+    lib.fde_tune_cache(path.encode())
+    yield lib, path
+    for k in (0, 1):
+        lib.fde_tune_set(k, -1)
+    lib.fde_tune_cache(None)
+
+
+def _case():
+    # several 128-row tiles and a ragged tail; 9 Strang blocks
+    return fi.manufactured(300, 16, 1.8, "GBDF5", dplus_fn=lambda x: 1 + x, dminus_fn=lambda x: 2 - x)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "tf32"])
+def test_variants_are_bit_identical(lib, precision):
+    from paper_1305_6653_gb300 import FDEProblem, _lib
+    L, _ = lib
+    prob = _case()
+    rng = np.random.default_rng(4)
+    z = torch.as_tensor(rng.standard_normal(prob.n), device="cuda")
+    outs = []
+    for v in range(3):
+        L.fde_tune_set(_lib.FDE_TUNE_MATVEC, v)
+        L.fde_tune_set(_lib.FDE_TUNE_TRSV, v)
+        with FDEProblem.from_inputs(prob, device_inputs=True) as p:
+            p.assemble().factor(precision)
+            y = p.matvec(z).cpu().numpy()
+            w = p.precond_apply(z).cpu().numpy()
+            x, st = p.solve(tol=1e-11, maxit=400)
+            outs.append((y, w, x.cpu().numpy(), st["iterations"]))
+    for y, w, x, its in outs[1:]:
+        assert np.array_equal(y, outs[0][0])
+        assert np.array_equal(w, outs[0][1])
+        assert np.array_equal(x, outs[0][2]) and its == outs[0][3]
+    for k in (0, 1):
+        L.fde_tune_set(k, -1)
+
+
+def test_autotune_records_the_shape(lib):
+    import ctypes as C
+
+    from paper_1305_6653_gb300 import FDEProblem, _lib
+    L, path = lib
+    prob = fi.manufactured(200, 32, 1.5, "GBDF3")
+    mp, nblk = 256, 17
+    with FDEProblem.from_inputs(prob) as p:
+        p.assemble().factor("fp32")
+        x, st = p.solve(tol=1e-10)
+    v = C.c_int()
+    assert L.fde_tune_query(_lib.FDE_TUNE_MATVEC, mp, prob.s, 0, C.byref(v)) == 0 and 0 <= v.value < 3
+    assert L.fde_tune_query(_lib.FDE_TUNE_TRSV, mp, nblk, 1, C.byref(v)) == 0 and 0 <= v.value < 3
+    text = open(path).read()
+    assert f"matvec 0 {mp} {prob.s} 0 " in text and f"trsv 1 {mp} {nblk} 1 " in text
+    # a fresh table read back from the file has the same entries
+    L.fde_tune_cache(path.encode())
+    assert L.fde_tune_query(_lib.FDE_TUNE_TRSV, mp, nblk, 1, C.byref(v)) == 0 and 0 <= v.value < 3
