@@ -962,6 +962,7 @@ int pgmres_solve(fde_problem* h, const fde_pgmres_opts* opts, const double* x0_a
             x0 = P.d_xsol;
         }
     }
+    FDE_CUDA_TRY(cudaMemsetAsync(P.d_err, 0, sizeof(int), st));  // bounded-wait flag of the block solves
     cudaEvent_t ev0, ev1;
     FDE_CUDA_TRY(cudaEventCreate(&ev0));
     FDE_CUDA_TRY(cudaEventCreate(&ev1));
@@ -978,6 +979,10 @@ int pgmres_solve(fde_problem* h, const fde_pgmres_opts* opts, const double* x0_a
     double bnorm2 = 0, beta2 = 0;
 
     auto finish = [&](int code) -> int {
+        int derr = 0;  // a bounded wait of the block solves ran out
+        if (cudaMemcpyAsync(&derr, P.d_err, sizeof(int), cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+            cudaStreamSynchronize(st) == cudaSuccess && derr && code == FDE_OK)
+            code = set_error(FDE_ERR_TIMEOUT, "a bounded wait in the block solves ran out");
         if (host_x) {  // the solution (or last iterate) back to the caller's host array
             cudaError_t e = cudaMemcpyAsync(x_arg, x, n * sizeof(double), cudaMemcpyDeviceToHost, st);
             if (e != cudaSuccess && code == FDE_OK) code = cuda_error(e, "copy of the solution to the host");

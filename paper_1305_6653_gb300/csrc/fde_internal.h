@@ -284,8 +284,10 @@ int dev_release_cached();
 // returns the fastest; tune_store records it (memory and the cache file).
 int tune_variants(int kernel);
 int tune_lookup(int kernel, int mp, int nb, int prec, bool* need_tuning);
-void tune_store(int kernel, int mp, int nb, int prec, int variant);
-int tune_measure(int kernel, cudaStream_t st, int (*fn)(void*, int, cudaStream_t), void* ctx, int* best);
+void tune_store(int kernel, int mp, int nb, int prec, int variant, const float* ms);  // ms: per variant, or NULL
+int tune_measure(int kernel, cudaStream_t st, int (*fn)(void*, int, cudaStream_t), void* ctx, int* best,
+                 float* ms_out);  // ms_out: the best time of every variant (tune_variants entries), or NULL
+constexpr int TUNE_MAX_VARIANTS = 8;
 // the tuned kernels' variant launchers (matvec.cu, lu.cu) and the tuning passes
 int launch_matvec64_variant(const Problem& P, const double* z, double* y, int variant, cudaStream_t st);
 int launch_block_trsv_variant(const Problem& P, void* rhat, int variant, cudaStream_t st);

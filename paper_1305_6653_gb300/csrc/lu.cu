@@ -484,7 +484,7 @@ template <typename T> struct trsv_shape<T, 2> { static constexpr int NT = 640, H
 // cp.async destinations); [buffer 2][D, L][Re, Im][32][LD].
 template <typename T> struct trsv_tile { static constexpr int LD = 32 + 16 / (int)sizeof(T); };
 
-static size_t trsv_smem_bytes(int mp, size_t elem) {
+__host__ __device__ static size_t trsv_smem_bytes(int mp, size_t elem) {
     const size_t ld = 32 + 16 / elem;
     return (size_t)mp * 2 * elem + 8 * 32 * ld * elem;
 }
@@ -700,6 +700,181 @@ __device__ __forceinline__ void trsv_stream(int mp, int nt, const T* re, const T
             apply(0, q0 + HG);
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// Block solves with the strips streamed by the copy engine.  Same roles and
+// hand-over as trsv_body, but warp 1 is a producer that copies every strip's row
+// segments (32 columns of the Re and Im planes, rows in sweep order) into a ring of
+// shared-memory stages with bulk asynchronous copies (cp.async.bulk, completion
+// counted on a full[] mbarrier), running ahead of the consumers through both sweeps
+// (the factors do not depend on the solution); warps 2.. consume one stage row per
+// group of TRSV_TPR lanes with the same fused multiply-adds and the same shuffle
+// reduction as trsv_stream, so the result is bit-identical.  A stage holds
+// RING_R = (NT - 64) / TRSV_TPR rows (>= 32: the first stage of a strip covers tile
+// d+2).  The producer takes no part in the named barriers; every mbarrier wait is
+// bounded (on timeout the kernel records an error and carries on, so no thread is
+// left waiting at a barrier).
+// ---------------------------------------------------------------------------
+constexpr int TRSV_BAR_SWEEP = 5;  // solver + consumers between the two sweeps
+
+template <typename T> struct ring_cfg {
+    static constexpr int NT = 512;
+    static constexpr int R = (NT - 64) / TRSV_TPR;        // 56 rows per stage
+    static constexpr int ROWB = 2 * 32 * (int)sizeof(T);  // bytes per stage row (Re | Im)
+    static constexpr int S = sizeof(T) == 4 ? 10 : 4;     // stages
+    static constexpr int CW = (NT - 64) / 32;             // consumer warps
+};
+
+static size_t trsv_ring_smem_bytes(int mp, size_t elem) {
+    const size_t s = elem == 4 ? ring_cfg<float>::S : ring_cfg<double>::S;
+    const size_t rowb = 2 * 32 * elem;
+    return trsv_smem_bytes(mp, elem) + s * ((size_t)(512 - 64) / TRSV_TPR) * rowb;
+}
+
+template <typename T>
+__device__ __forceinline__ void ring_wait(uint64_t* bar, uint32_t parity, int* err) {
+    if (!tc::mbar_wait(bar, parity)) atomicCAS(err, 0, 3);  // recorded; carry on (no hang)
+}
+
+// Producer (warp 1): every stage of both sweeps, in the order the consumers take them.
+template <typename T>
+__device__ __forceinline__ void trsv_ring_producer(int mp, int nt, const T* re, const T* im, unsigned char* ring,
+                                                   uint64_t* full, uint64_t* empty, int* err, int lane) {
+    using Cf = ring_cfg<T>;
+    long g = 0;
+    for (int sweep = 0; sweep < 2; ++sweep) {
+        const bool fwd = sweep == 0;
+        for (int d = 0; d + 2 < nt; ++d) {
+            const int col = 32 * (fwd ? d : nt - 1 - d);
+            const int lo = fwd ? 32 * (d + 2) : 0;
+            const int hi = fwd ? mp : 32 * (nt - 2 - d);
+            const int len = hi - lo;
+            for (int q0 = 0; q0 < len; q0 += Cf::R, ++g) {
+                const int s = (int)(g % Cf::S);
+                if (g >= Cf::S) ring_wait<T>(&empty[s], (uint32_t)((g / Cf::S - 1) & 1), err);
+                const int rows = min(Cf::R, len - q0);
+                unsigned char* st = ring + (size_t)s * Cf::R * Cf::ROWB;
+                if (lane == 0) tc::mbar_arrive_expect_tx(&full[s], (uint32_t)(rows * Cf::ROWB));
+                __syncwarp();
+                for (int rr = lane; rr < rows; rr += 32) {
+                    const int q = q0 + rr;
+                    const int r = fwd ? lo + q : hi - 1 - q;
+                    tc::bulk_g2s(st + rr * Cf::ROWB, re + (size_t)r * mp + col, 32 * sizeof(T), &full[s]);
+                    tc::bulk_g2s(st + rr * Cf::ROWB + 32 * sizeof(T), im + (size_t)r * mp + col, 32 * sizeof(T),
+                                 &full[s]);
+                }
+            }
+        }
+    }
+}
+
+// Consumers (warps 2..): strip d of one sweep from the ring, stage by stage; g is the
+// running stage count shared with the producer's enumeration.
+template <typename T, bool FWD>
+__device__ __forceinline__ void trsv_ring_stream(int mp, int nt, cplx_t<T>* y, const cplx_t<T> (*xs)[32],
+                                                 const unsigned char* ring, uint64_t* full, uint64_t* empty,
+                                                 int* err, int bt, long& g) {
+    using C = cplx_t<T>;
+    using V = typename vec4<T>::type;
+    using Cf = ring_cfg<T>;
+    const int grp = bt / TRSV_TPR, sub = bt % TRSV_TPR, lane = bt & 31;
+    for (int d = 0; d + 2 < nt; ++d) {
+        const int lo = FWD ? 32 * (d + 2) : 0;
+        const int hi = FWD ? mp : 32 * (nt - 2 - d);
+        const int len = hi - lo;
+        named_sync(TRSV_BAR_X + (d & 1), Cf::NT - 32);
+        const C x0 = xs[d & 1][sub * 4], x1 = xs[d & 1][sub * 4 + 1];
+        const C x2 = xs[d & 1][sub * 4 + 2], x3 = xs[d & 1][sub * 4 + 3];
+        for (int q0 = 0; q0 < len; q0 += Cf::R, ++g) {
+            const int s = (int)(g % Cf::S);
+            ring_wait<T>(&full[s], (uint32_t)((g / Cf::S) & 1), err);
+            const int q = q0 + grp;
+            if (q < len) {  // uniform across a warp: an aligned quartet of groups, len a multiple of 32
+                const T* row = reinterpret_cast<const T*>(ring + ((size_t)s * Cf::R + grp) * Cf::ROWB);
+                const V vr = *reinterpret_cast<const V*>(row + sub * 4);
+                const V vi = *reinterpret_cast<const V*>(row + 32 + sub * 4);
+                T sx = vr.x * x0.x;
+                sx = fma(-vi.x, x0.y, sx);
+                sx = fma(vr.y, x1.x, sx);
+                sx = fma(-vi.y, x1.y, sx);
+                sx = fma(vr.z, x2.x, sx);
+                sx = fma(-vi.z, x2.y, sx);
+                sx = fma(vr.w, x3.x, sx);
+                sx = fma(-vi.w, x3.y, sx);
+                T sy = vr.x * x0.y;
+                sy = fma(vi.x, x0.x, sy);
+                sy = fma(vr.y, x1.y, sy);
+                sy = fma(vi.y, x1.x, sy);
+                sy = fma(vr.z, x2.y, sy);
+                sy = fma(vi.z, x2.x, sy);
+                sy = fma(vr.w, x3.y, sy);
+                sy = fma(vi.w, x3.x, sy);
+#pragma unroll
+                for (int off = 1; off < TRSV_TPR; off <<= 1) {
+                    sx += __shfl_xor_sync(0xffffffffu, sx, off);
+                    sy += __shfl_xor_sync(0xffffffffu, sy, off);
+                }
+                if (sub == 0) {
+                    const int r = FWD ? lo + q : hi - 1 - q;
+                    C v = y[r];
+                    v.x -= sx;
+                    v.y -= sy;
+                    y[r] = v;
+                }
+            }
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&empty[s]))
+                                        : "memory");
+            if (q0 == 0) named_arrive(TRSV_BAR_B + (d & 1), Cf::NT - 32);  // stage 0 covers tile d+2
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512)
+block_trsv_ring_kernel(int mp, const T* __restrict__ fac, const cplx_t<T>* __restrict__ dinv,
+                       const T* __restrict__ tinv, cplx_t<T>* __restrict__ rhat, int* __restrict__ err) {
+    using C = cplx_t<T>;
+    using Cf = ring_cfg<T>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int k = blockIdx.x;
+    const T* re = fac + (size_t)k * 2 * mp * mp;
+    const T* im = re + (size_t)mp * mp;
+    const C* dv = dinv + (size_t)k * mp;
+    const T* ti = tinv + (size_t)k * (mp / 32) * 4096;
+    C* x = rhat + (size_t)k * mp;
+    C* y = reinterpret_cast<C*>(smem_raw);       // mp
+    T* tiles = reinterpret_cast<T*>(y + mp);     // solver tiles
+    unsigned char* ring = smem_raw + trsv_smem_bytes(mp, sizeof(T));  // 128-byte aligned (mp multiple of 64)
+    __shared__ C xs[2][32];
+    __shared__ C av[32];
+    __shared__ __align__(8) uint64_t full[Cf::S], empty[Cf::S];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nt = mp / 32;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < Cf::S; ++s) {
+            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&empty[s], Cf::CW);
+        }
+        tc::fence_barrier_init();
+    }
+    for (int i = threadIdx.x; i < mp; i += blockDim.x) y[i] = x[i];
+    __syncthreads();
+    if (warp == 1) {
+        trsv_ring_producer<T>(mp, nt, re, im, ring, full, empty, err, lane);
+    } else if (warp == 0) {
+        trsv_solver<T, true, true, Cf::NT - 32>(mp, nt, re, im, dv, ti, y, xs, tiles, av, lane);
+        named_sync(TRSV_BAR_SWEEP, Cf::NT - 32);
+        trsv_solver<T, false, true, Cf::NT - 32>(mp, nt, re, im, dv, ti, y, xs, tiles, av, lane);
+    } else {
+        long g = 0;
+        trsv_ring_stream<T, true>(mp, nt, y, xs, ring, full, empty, err, threadIdx.x - 64, g);
+        named_sync(TRSV_BAR_SWEEP, Cf::NT - 32);
+        trsv_ring_stream<T, false>(mp, nt, y, xs, ring, full, empty, err, threadIdx.x - 64, g);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < mp; i += blockDim.x) x[i] = y[i];
 }
 
 template <typename T, bool INV, int NT = TRSV_THREADS, int H = trsv_unroll<T>::value / 2>
@@ -1821,7 +1996,25 @@ static int launch_trsv_shape(const Problem& P, void* rhat, cudaStream_t st) {
     return FDE_OK;
 }
 
+constexpr size_t TRSV_SMEM_MAX = 227 * 1024;  // dynamic shared memory of one CTA
+
+template <typename T>
+static int launch_trsv_ring(const Problem& P, void* rhat, cudaStream_t st) {
+    const size_t smem = trsv_ring_smem_bytes(P.mp, sizeof(T));
+    if (smem > TRSV_SMEM_MAX) return launch_trsv_shape<T, 0>(P, rhat, st);  // the ring does not fit: default
+    auto kern = block_trsv_ring_kernel<T>;
+    FDE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<P.nblk, ring_cfg<T>::NT, smem, st>>>(P.mp, (const T*)P.d_fac, (const cplx_t<T>*)P.d_dinv,
+                                                 (const T*)P.d_tinv, (cplx_t<T>*)rhat, P.d_err);
+    FDE_LAUNCH_CHECK("block_trsv_ring_kernel");
+    return FDE_OK;
+}
+
 int launch_block_trsv_variant(const Problem& P, void* rhat, int variant, cudaStream_t st) {
+    if (variant == 3) {  // strips streamed through a shared-memory ring by bulk copies
+        if (P.precision == FDE_FP64) return launch_trsv_ring<double>(P, rhat, st);
+        return launch_trsv_ring<float>(P, rhat, st);
+    }
     if (P.precision == FDE_FP64) {
         if (variant == 1) return launch_trsv_shape<double, 1>(P, rhat, st);
         if (variant == 2) return launch_trsv_shape<double, 2>(P, rhat, st);
@@ -1860,9 +2053,10 @@ int autotune_trsv(Problem& P) {
     FDE_CUDA_TRY(cudaMemsetAsync(P.d_rhat, 0, (size_t)P.nblk * P.mp * 2 * esz, P.stream));
     TrsvTuneCtx ctx{&P, P.d_rhat};
     int best = 0;
-    const int rc = tune_measure(FDE_TUNE_TRSV, P.stream, trsv_trial, &ctx, &best);
+    float ms[TUNE_MAX_VARIANTS] = {};
+    const int rc = tune_measure(FDE_TUNE_TRSV, P.stream, trsv_trial, &ctx, &best, ms);
     if (rc) return rc;
-    tune_store(FDE_TUNE_TRSV, P.mp, P.nblk, prec, best);
+    tune_store(FDE_TUNE_TRSV, P.mp, P.nblk, prec, best, ms);
     return FDE_OK;
 }
 

@@ -225,9 +225,10 @@ int autotune_matvec(Problem& P) {
     if (!need) return FDE_OK;
     MatvecTuneCtx ctx{&P, P.d_b_rhs, P.d_work};
     int best = 0;
-    const int rc = tune_measure(FDE_TUNE_MATVEC, P.stream, matvec_trial, &ctx, &best);
+    float ms[TUNE_MAX_VARIANTS] = {};
+    const int rc = tune_measure(FDE_TUNE_MATVEC, P.stream, matvec_trial, &ctx, &best, ms);
     if (rc) return rc;
-    tune_store(FDE_TUNE_MATVEC, P.mp, P.s, FDE_FP64, best);
+    tune_store(FDE_TUNE_MATVEC, P.mp, P.s, FDE_FP64, best, ms);
     return FDE_OK;
 }
 

@@ -46,16 +46,18 @@ void load_locked(TuneState& s) {
     if (s.path.empty()) return;
     FILE* f = std::fopen(s.path.c_str(), "r");
     if (!f) return;
-    char name[32];
+    char line[512], name[32];
     int k, mp, nb, prec, v;
-    while (std::fscanf(f, "%31s %d %d %d %d %d", name, &k, &mp, &nb, &prec, &v) == 6)
-        if (k >= 0 && k < FDE_TUNE_KERNELS && v >= 0 && v < tune_variants(k)) s.table[{k, mp, nb, prec}] = v;
+    while (std::fgets(line, sizeof line, f))  // "name kernel mp nb precision variant [# measured ms ...]"
+        if (std::sscanf(line, "%31s %d %d %d %d %d", name, &k, &mp, &nb, &prec, &v) == 6 && k >= 0 &&
+            k < FDE_TUNE_KERNELS && v >= 0 && v < tune_variants(k))
+            s.table[{k, mp, nb, prec}] = v;
     std::fclose(f);
 }
 
 }  // namespace
 
-int tune_variants(int kernel) { return kernel == FDE_TUNE_MATVEC ? 3 : kernel == FDE_TUNE_TRSV ? 3 : 0; }
+int tune_variants(int kernel) { return kernel == FDE_TUNE_MATVEC ? 3 : kernel == FDE_TUNE_TRSV ? 4 : 0; }
 
 int tune_lookup(int kernel, int mp, int nb, int prec, bool* need_tuning) {
     TuneState& s = state();
@@ -69,7 +71,7 @@ int tune_lookup(int kernel, int mp, int nb, int prec, bool* need_tuning) {
     return 0;
 }
 
-void tune_store(int kernel, int mp, int nb, int prec, int variant) {
+void tune_store(int kernel, int mp, int nb, int prec, int variant, const float* ms) {
     TuneState& s = state();
     std::lock_guard<std::mutex> lock(s.mu);
     load_locked(s);
@@ -82,15 +84,18 @@ void tune_store(int kernel, int mp, int nb, int prec, int variant) {
         f = std::fopen(s.path.c_str(), "a");
         if (!f) return;  // the table stays in memory only
     }
-    std::fprintf(f, "%s %d %d %d %d %d\n", kernel == FDE_TUNE_MATVEC ? "matvec" : "trsv", kernel, mp, nb, prec,
+    std::fprintf(f, "%s %d %d %d %d %d #", kernel == FDE_TUNE_MATVEC ? "matvec" : "trsv", kernel, mp, nb, prec,
                  variant);
+    for (int i = 0; ms && i < tune_variants(kernel); ++i) std::fprintf(f, " %.4f", ms[i]);
+    std::fprintf(f, " ms\n");
     std::fclose(f);
 }
 
 // Time fn(variant) for every variant (one untimed launch, then the best of three
 // timed ones) on stream st and return the fastest.  fn launches one kernel and
 // returns an FDE status.
-int tune_measure(int kernel, cudaStream_t st, int (*fn)(void*, int, cudaStream_t), void* ctx, int* best) {
+int tune_measure(int kernel, cudaStream_t st, int (*fn)(void*, int, cudaStream_t), void* ctx, int* best,
+                 float* ms_out) {
     cudaEvent_t e0, e1;
     FDE_CUDA_TRY(cudaEventCreate(&e0));
     FDE_CUDA_TRY(cudaEventCreate(&e1));
@@ -113,6 +118,7 @@ int tune_measure(int kernel, cudaStream_t st, int (*fn)(void*, int, cudaStream_t
             cudaEventElapsedTime(&ms, e0, e1);
             if (ms < vbest) vbest = ms;
         }
+        if (ms_out) ms_out[v] = vbest;
         if (vbest < best_ms) {
             best_ms = vbest;
             *best = v;

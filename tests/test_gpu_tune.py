@@ -39,8 +39,8 @@ def test_variants_are_bit_identical(lib, precision):
     rng = np.random.default_rng(4)
     z = torch.as_tensor(rng.standard_normal(prob.n), device="cuda")
     outs = []
-    for v in range(3):
-        L.fde_tune_set(_lib.FDE_TUNE_MATVEC, v)
+    for v in range(4):  # matvec: 3 shapes (the fourth setting repeats shape 0); block solves: 4
+        L.fde_tune_set(_lib.FDE_TUNE_MATVEC, v % 3)
         L.fde_tune_set(_lib.FDE_TUNE_TRSV, v)
         with FDEProblem.from_inputs(prob, device_inputs=True) as p:
             p.assemble().factor(precision)
@@ -68,9 +68,9 @@ def test_autotune_records_the_shape(lib):
         x, st = p.solve(tol=1e-10)
     v = C.c_int()
     assert L.fde_tune_query(_lib.FDE_TUNE_MATVEC, mp, prob.s, 0, C.byref(v)) == 0 and 0 <= v.value < 3
-    assert L.fde_tune_query(_lib.FDE_TUNE_TRSV, mp, nblk, 1, C.byref(v)) == 0 and 0 <= v.value < 3
+    assert L.fde_tune_query(_lib.FDE_TUNE_TRSV, mp, nblk, 1, C.byref(v)) == 0 and 0 <= v.value < 4
     text = open(path).read()
     assert f"matvec 0 {mp} {prob.s} 0 " in text and f"trsv 1 {mp} {nblk} 1 " in text
     # a fresh table read back from the file has the same entries
     L.fde_tune_cache(path.encode())
-    assert L.fde_tune_query(_lib.FDE_TUNE_TRSV, mp, nblk, 1, C.byref(v)) == 0 and 0 <= v.value < 3
+    assert L.fde_tune_query(_lib.FDE_TUNE_TRSV, mp, nblk, 1, C.byref(v)) == 0 and 0 <= v.value < 4
