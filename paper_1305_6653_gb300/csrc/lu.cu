@@ -16,6 +16,8 @@
 //                 variant lives in lu_tc.cu)
 #include <algorithm>
 
+#include <cuda.h>  // CUtensorMap (the encoder is fetched from the driver at run time)
+
 #include "fde_internal.h"
 #include "fft_device.cuh"
 #include "lu_tc2.cuh"
@@ -704,9 +706,9 @@ __device__ __forceinline__ void trsv_stream(int mp, int nt, const T* re, const T
 
 // ---------------------------------------------------------------------------
 // Block solves with the strips streamed by the copy engine.  Same roles and
-// hand-over as trsv_body, but warp 1 is a producer that copies every strip's row
-// segments (32 columns of the Re and Im planes, rows in sweep order) into a ring of
-// shared-memory stages with bulk asynchronous copies (cp.async.bulk, completion
+// hand-over as trsv_body, but warp 1 is a producer that loads every strip (32
+// columns of the Re and Im planes, R rows per stage, in sweep order) into a ring of
+// shared-memory stages with tensor-map copies (cp.async.bulk.tensor, completion
 // counted on a full[] mbarrier), running ahead of the consumers through both sweeps
 // (the factors do not depend on the solution); warps 2.. consume one stage row per
 // group of TRSV_TPR lanes with the same fused multiply-adds and the same shuffle
@@ -729,7 +731,7 @@ template <typename T> struct ring_cfg {
 static size_t trsv_ring_smem_bytes(int mp, size_t elem) {
     const size_t s = elem == 4 ? ring_cfg<float>::S : ring_cfg<double>::S;
     const size_t rowb = 2 * 32 * elem;
-    return trsv_smem_bytes(mp, elem) + s * ((size_t)(512 - 64) / TRSV_TPR) * rowb;
+    return trsv_smem_bytes(mp, elem) + 128 + s * ((size_t)(512 - 64) / TRSV_TPR) * rowb;  // + alignment slack
 }
 
 template <typename T>
@@ -737,10 +739,22 @@ __device__ __forceinline__ void ring_wait(uint64_t* bar, uint32_t parity, int* e
     if (!tc::mbar_wait(bar, parity)) atomicCAS(err, 0, 3);  // recorded; carry on (no hang)
 }
 
-// Producer (warp 1): every stage of both sweeps, in the order the consumers take them.
+// Producer (lane 0 of warp 1): every stage of both sweeps, in the order the consumers
+// take them.  A stage is two tensor-map (TMA) boxes of R rows x 32 columns, one per
+// plane, landing as [Re rows][Im rows]; forward sweeps load rows lo+q0 .. upward,
+// backward sweeps the R rows that end at hi-q0 (the last boxes of a sweep may start
+// below row 0 or end past m_p: those rows are filled with zeros and never read).
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(tc::smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(tc::smem_u32(bar))
+        : "memory");
+}
+
 template <typename T>
-__device__ __forceinline__ void trsv_ring_producer(int mp, int nt, const T* re, const T* im, unsigned char* ring,
-                                                   uint64_t* full, uint64_t* empty, int* err, int lane) {
+__device__ __forceinline__ void trsv_ring_producer(int mp, int nt, int k, const CUtensorMap* map, unsigned char* ring,
+                                                   uint64_t* full, uint64_t* empty, int* err) {
     using Cf = ring_cfg<T>;
     long g = 0;
     for (int sweep = 0; sweep < 2; ++sweep) {
@@ -753,17 +767,11 @@ __device__ __forceinline__ void trsv_ring_producer(int mp, int nt, const T* re, 
             for (int q0 = 0; q0 < len; q0 += Cf::R, ++g) {
                 const int s = (int)(g % Cf::S);
                 if (g >= Cf::S) ring_wait<T>(&empty[s], (uint32_t)((g / Cf::S - 1) & 1), err);
-                const int rows = min(Cf::R, len - q0);
                 unsigned char* st = ring + (size_t)s * Cf::R * Cf::ROWB;
-                if (lane == 0) tc::mbar_arrive_expect_tx(&full[s], (uint32_t)(rows * Cf::ROWB));
-                __syncwarp();
-                for (int rr = lane; rr < rows; rr += 32) {
-                    const int q = q0 + rr;
-                    const int r = fwd ? lo + q : hi - 1 - q;
-                    tc::bulk_g2s(st + rr * Cf::ROWB, re + (size_t)r * mp + col, 32 * sizeof(T), &full[s]);
-                    tc::bulk_g2s(st + rr * Cf::ROWB + 32 * sizeof(T), im + (size_t)r * mp + col, 32 * sizeof(T),
-                                 &full[s]);
-                }
+                const int y0 = fwd ? lo + q0 : hi - q0 - Cf::R;
+                tc::mbar_arrive_expect_tx(&full[s], (uint32_t)(Cf::R * Cf::ROWB));
+                tma_load_3d(st, map, col, y0, 2 * k, &full[s]);
+                tma_load_3d(st + Cf::R * Cf::ROWB / 2, map, col, y0, 2 * k + 1, &full[s]);
             }
         }
     }
@@ -791,9 +799,11 @@ __device__ __forceinline__ void trsv_ring_stream(int mp, int nt, cplx_t<T>* y, c
             ring_wait<T>(&full[s], (uint32_t)((g / Cf::S) & 1), err);
             const int q = q0 + grp;
             if (q < len) {  // uniform across a warp: an aligned quartet of groups, len a multiple of 32
-                const T* row = reinterpret_cast<const T*>(ring + ((size_t)s * Cf::R + grp) * Cf::ROWB);
-                const V vr = *reinterpret_cast<const V*>(row + sub * 4);
-                const V vi = *reinterpret_cast<const V*>(row + 32 + sub * 4);
+                const int br = FWD ? grp : Cf::R - 1 - grp;  // row within the stage's boxes
+                const T* pre = reinterpret_cast<const T*>(ring + (size_t)s * Cf::R * Cf::ROWB) + br * 32;
+                const T* pim = pre + Cf::R * 32;
+                const V vr = *reinterpret_cast<const V*>(pre + sub * 4);
+                const V vi = *reinterpret_cast<const V*>(pim + sub * 4);
                 T sx = vr.x * x0.x;
                 sx = fma(-vi.x, x0.y, sx);
                 sx = fma(vr.y, x1.x, sx);
@@ -834,7 +844,8 @@ __device__ __forceinline__ void trsv_ring_stream(int mp, int nt, cplx_t<T>* y, c
 template <typename T>
 __global__ void __launch_bounds__(512)
 block_trsv_ring_kernel(int mp, const T* __restrict__ fac, const cplx_t<T>* __restrict__ dinv,
-                       const T* __restrict__ tinv, cplx_t<T>* __restrict__ rhat, int* __restrict__ err) {
+                       const T* __restrict__ tinv, cplx_t<T>* __restrict__ rhat, int* __restrict__ err,
+                       const __grid_constant__ CUtensorMap fmap) {
     using C = cplx_t<T>;
     using Cf = ring_cfg<T>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -846,7 +857,9 @@ block_trsv_ring_kernel(int mp, const T* __restrict__ fac, const cplx_t<T>* __res
     C* x = rhat + (size_t)k * mp;
     C* y = reinterpret_cast<C*>(smem_raw);       // mp
     T* tiles = reinterpret_cast<T*>(y + mp);     // solver tiles
-    unsigned char* ring = smem_raw + trsv_smem_bytes(mp, sizeof(T));  // 128-byte aligned (mp multiple of 64)
+    // the ring starts at the next 128-byte boundary of the shared window (TMA destinations)
+    const uint32_t base = tc::smem_u32(smem_raw) + (uint32_t)trsv_smem_bytes(mp, sizeof(T));
+    unsigned char* ring = smem_raw + ((base + 127u) & ~127u) - tc::smem_u32(smem_raw);
     __shared__ C xs[2][32];
     __shared__ C av[32];
     __shared__ __align__(8) uint64_t full[Cf::S], empty[Cf::S];
@@ -862,7 +875,7 @@ block_trsv_ring_kernel(int mp, const T* __restrict__ fac, const cplx_t<T>* __res
     for (int i = threadIdx.x; i < mp; i += blockDim.x) y[i] = x[i];
     __syncthreads();
     if (warp == 1) {
-        trsv_ring_producer<T>(mp, nt, re, im, ring, full, empty, err, lane);
+        if (lane == 0) trsv_ring_producer<T>(mp, nt, k, &fmap, ring, full, empty, err);
     } else if (warp == 0) {
         trsv_solver<T, true, true, Cf::NT - 32>(mp, nt, re, im, dv, ti, y, xs, tiles, av, lane);
         named_sync(TRSV_BAR_SWEEP, Cf::NT - 32);
@@ -1998,14 +2011,44 @@ static int launch_trsv_shape(const Problem& P, void* rhat, cudaStream_t st) {
 
 constexpr size_t TRSV_SMEM_MAX = 227 * 1024;  // dynamic shared memory of one CTA
 
+// Tensor map of the factor planes as a 3-D array [2 nblk planes][m_p rows][m_p columns],
+// boxes of R rows x 32 columns of one plane (made once per factor buffer).
+template <typename T>
+static int trsv_tensor_map(const Problem& P, CUtensorMap* map) {
+    using Fn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                            const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                            CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static Fn encode = nullptr;
+    if (!encode) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        FDE_CUDA_TRY(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
+        if (q != cudaDriverEntryPointSuccess || !fn) return set_error(FDE_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+        encode = reinterpret_cast<Fn>(fn);
+    }
+    const cuuint64_t dims[3] = {(cuuint64_t)P.mp, (cuuint64_t)P.mp, (cuuint64_t)2 * P.nblk};
+    const cuuint64_t strides[2] = {(cuuint64_t)P.mp * sizeof(T), (cuuint64_t)P.mp * P.mp * sizeof(T)};
+    const cuuint32_t box[3] = {32, (cuuint32_t)ring_cfg<T>::R, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = encode(map, sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+                              3, P.d_fac, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(FDE_ERR_CUDA, "cuTensorMapEncodeTiled failed for the factor planes");
+    return FDE_OK;
+}
+
 template <typename T>
 static int launch_trsv_ring(const Problem& P, void* rhat, cudaStream_t st) {
     const size_t smem = trsv_ring_smem_bytes(P.mp, sizeof(T));
     if (smem > TRSV_SMEM_MAX) return launch_trsv_shape<T, 0>(P, rhat, st);  // the ring does not fit: default
+    CUtensorMap map;
+    int rc = trsv_tensor_map<T>(P, &map);
+    if (rc) return rc;
     auto kern = block_trsv_ring_kernel<T>;
     FDE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<P.nblk, ring_cfg<T>::NT, smem, st>>>(P.mp, (const T*)P.d_fac, (const cplx_t<T>*)P.d_dinv,
-                                                 (const T*)P.d_tinv, (cplx_t<T>*)rhat, P.d_err);
+                                                 (const T*)P.d_tinv, (cplx_t<T>*)rhat, P.d_err, map);
     FDE_LAUNCH_CHECK("block_trsv_ring_kernel");
     return FDE_OK;
 }
