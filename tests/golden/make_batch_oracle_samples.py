@@ -9,7 +9,10 @@ The solutions are the oracle's FP64 Strang-preconditioned flexible GMRES(20)
 (oracle.solve_strang_gmres, Sec. 3.2 with the dense DFT along time and one LAPACK
 LU per frequency block) to a true relative residual of 1e-11 (the oracle's FP64 floor
 is 2e-13 - 6e-12 at m = 2047, so a tighter tolerance would not terminate); the file
-records the residual each reached (under the oracle's own Kronecker matvec).  Only oracle/ and
+records the residual each reached (under the oracle's own Kronecker matvec).  Four
+instances whose floor lies above 1e-11 (GAM4 at m = 2047, s = 256, alpha 1.76 and
+1.85; ETR3 at m = 2047, s = 64, alpha 1.70 and 1.71) stop at maxit = 1500 with their
+reached residual, 1.0e-11 to 2.1e-11, recorded as "converged 0".  Only oracle/ and
 the input generators are used.  A full run takes about an hour on 8 cores:
 
     python tests/golden/make_batch_oracle_samples.py [--workers 4]
