@@ -68,6 +68,8 @@ def parse():
                     help="precision of the Toeplitz apply in the Arnoldi products (the restart residual is FP64)")
     ap.add_argument("--relax", type=float, default=0.0,
                     help="--matvec fp32: FP32 products while the residual estimate is above this (0: always)")
+    ap.add_argument("--tune", default="",
+                    help="force launch shapes instead of autotuning, e.g. 'trsv=1,matvec=2,lu=1' (fde_tune_set)")
     ap.add_argument("--batch-precision", default="tf32", choices=["fp32", "tf32", "bf16", "tf32x3"],
                     help="factor precision of the batched workload")
     ap.add_argument("--m", type=int, default=2047)
@@ -1085,6 +1087,9 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
+    for item in filter(None, args.tune.split(",")):
+        name, v = item.split("=")
+        fde.fde_tune_set({"matvec": 0, "trsv": 1, "lu": 2}[name.strip()], int(v))
     hbm_peak, bf16_peak, _, peak_kind = peaks()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     xbuf = torch.empty(prob.n, dtype=torch.float64, device="cuda")
@@ -1296,6 +1301,8 @@ def main():
             "plain_fp64": plain, "batch64": batch, "precision_m4095": precision,
             "tensor_core_update": tc_line, "matvec": matvec_line, "path_roofline": path_roof,
             "peaks_measured": measured,
+            "launch_shapes": {"matvec": fde.fde_tune_query(0, mp, prob.s, "fp64"),
+                              "trsv": fde.fde_tune_query(1, mp, nblk, "fp64" if esz == 8 else "fp32")},
             "stage_ms_per_step": stage_ms, "stage_launches_per_step": stage_n,
             "stage_split_source": f"untimed profiled pass of {args.profile_steps} solves after the timed region "
                                   "(every stage with its own event pair, direct launches)",

@@ -391,7 +391,13 @@ long long fde_launch_count(void);
  * keeps it in memory) and read back by later processes. */
 #define FDE_TUNE_MATVEC 0
 #define FDE_TUNE_TRSV 1
-#define FDE_TUNE_KERNELS 2
+/* The interior trailing update of the tensor-core block LU (FDE_TF32 / FDE_BF16 /
+ * FDE_TF32X3): 0 row-pair tiles, 1 warp-specialized CTAs of four tiles with two TMEM
+ * accumulators (one tile's epilogue overlaps the next tile's MMAs); bit-identical.
+ * Not timed automatically (a factorisation is too long to repeat at first use):
+ * variant 0 unless fde_tune_set selects one. */
+#define FDE_TUNE_LU 2
+#define FDE_TUNE_KERNELS 3
 /* variant -1: autotune (the default); 0 .. n-1: always launch that variant
  * (0 is the built-in default).  Process-wide.  Errors: FDE_ERR_ARG. */
 int fde_tune_set(int kernel, int variant);

@@ -45,7 +45,7 @@ EXPORTED = [
     "fde_nop_forward", "fde_nop_loss_grad", "fde_nop_adam_step", "fde_nop_features", "fde_nop_warm_start",
     "fde_nop_destroy", "fde_nop_coefficients", "fde_nop_synthesize",
 ]
-FDE_TUNE_MATVEC, FDE_TUNE_TRSV = 0, 1
+FDE_TUNE_MATVEC, FDE_TUNE_TRSV, FDE_TUNE_LU = 0, 1, 2
 STAGES = ["assemble", "form", "lu_diag", "lu_panel", "lu_update", "tfft_fwd", "trsv", "tfft_inv", "matvec",
           "krylov", "lu_tc", "lu_pack", "lu_panel_tc"]
 

@@ -21,6 +21,7 @@
 #include "fde_internal.h"
 #include "fft_device.cuh"
 #include "lu_tc2.cuh"
+#include "lu_tc2w.cuh"
 
 namespace fde {
 
@@ -1043,6 +1044,19 @@ lu_update_tc2p_kernel(int mp, int R0, int nt, int tj0, int ncol, float* __restri
                         an && two ? an + (size_t)ti0 * Cfg::A_TILE : nullptr);
 }
 
+// Interior of the trailing update (ti, tj >= 1), warp-specialized: CTA x takes tiles
+// x WQ .. x WQ + WQ - 1 of the (nt - 1)^2 interior tiles of block blockIdx.y.
+template <int KIND>
+__global__ void __launch_bounds__(W_THREADS)
+lu_update_tc2w_kernel(int mp, int R0, int nt, float* __restrict__ fac, const unsigned char* __restrict__ apack,
+                      const unsigned char* __restrict__ bpack, size_t pa, size_t pb, int* __restrict__ err) {
+    const int k = blockIdx.y, ni = nt - 1;
+    const int x0 = blockIdx.x * WQ, nq = min(WQ, ni * ni - x0);
+    if (nq <= 0) return;
+    tc2w_body<KIND>(mp, R0, ni, x0, nq, fac + (size_t)k * 2 * mp * mp, apack + (size_t)k * pa,
+                    bpack + (size_t)k * pb, err);
+}
+
 // Batched, in row pairs over every tile of each active block: grid.x = ceil(ntg / 2) * ntg
 // covers the largest block (ntg tiles per dimension); CTA x takes tiles (2p, tj) and
 // (2p + 1, tj), p = x / ntg, tj = x % ntg.
@@ -1082,6 +1096,8 @@ static int set_tc_attrs() {
                                       Tc2p<KIND>::SMEM));
     FDE_CUDA_TRY(cudaFuncSetAttribute(lu_update_tc2p_batched<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       Tc2p<KIND>::SMEM));
+    FDE_CUDA_TRY(cudaFuncSetAttribute(lu_update_tc2w_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      Tc2w<KIND>::SMEM));
     return FDE_OK;
 }
 
@@ -1694,6 +1710,8 @@ static int run_lu_tc(Problem& P, cudaStream_t st) {
                                       Cfg::SMEM_STORE));
     if ((rc = ensure_lu_streams(P))) return rc;
     cudaStream_t sh = P.lu_hi, sl = P.lu_lo;
+    // interior update kernel (FDE_TUNE_LU: 0 row pairs, 1 warp-specialized; bit-identical)
+    const int interior = tune_lookup(FDE_TUNE_LU, mp, nb, P.precision, nullptr);
     FDE_CUDA_TRY(cudaEventRecord(P.lu_ev[0], st));  // fork after the work already queued on st
     FDE_CUDA_TRY(cudaStreamWaitEvent(sh, P.lu_ev[0], 0));
     FDE_CUDA_TRY(cudaStreamWaitEvent(sl, P.lu_ev[0], 0));
@@ -1759,9 +1777,16 @@ static int run_lu_tc(Problem& P, cudaStream_t st) {
             FDE_CUDA_TRY(cudaStreamWaitEvent(sl, P.lu_ev[1], 0));
             if (nt > 1) {
                 StageTimer t(P, FDE_STAGE_LU_TC, sl);
-                lu_update_tc2p_kernel<KIND><<<dim3(((nt - 1 + 1) / 2) * (nt - 1), nb), 128, Tc2p<KIND>::SMEM, sl>>>(
-                    mp, R0, nt, 1, nt - 1, fac, apk(o), bpk(o), pa, pb, P.d_err);
-                FDE_LAUNCH_CHECK("lu_update_tc2p_kernel");
+                if (interior == 1) {  // warp-specialized, two accumulators, WQ tiles per CTA
+                    const int tiles = (nt - 1) * (nt - 1);
+                    lu_update_tc2w_kernel<KIND><<<dim3((tiles + WQ - 1) / WQ, nb), W_THREADS, Tc2w<KIND>::SMEM, sl>>>(
+                        mp, R0, nt, fac, apk(o), bpk(o), pa, pb, P.d_err);
+                    FDE_LAUNCH_CHECK("lu_update_tc2w_kernel");
+                } else {  // row pairs
+                    lu_update_tc2p_kernel<KIND><<<dim3(((nt - 1 + 1) / 2) * (nt - 1), nb), 128, Tc2p<KIND>::SMEM,
+                                                  sl>>>(mp, R0, nt, 1, nt - 1, fac, apk(o), bpk(o), pa, pb, P.d_err);
+                    FDE_LAUNCH_CHECK("lu_update_tc2p_kernel");
+                }
             }
             FDE_CUDA_TRY(cudaEventRecord(P.lu_ev[2], sl));
             if ((r = panel(R0))) return r;

@@ -23,7 +23,7 @@ struct TuneState {
     bool loaded = false;
     bool path_set = false;
     std::string path;                       // empty: no file
-    int mode[FDE_TUNE_KERNELS] = {-1, -1};  // -1 autotune, >= 0 forced variant
+    int mode[FDE_TUNE_KERNELS] = {-1, -1, -1};  // -1 autotune, >= 0 forced variant
     std::map<std::tuple<int, int, int, int>, int> table;
 };
 
@@ -57,7 +57,9 @@ void load_locked(TuneState& s) {
 
 }  // namespace
 
-int tune_variants(int kernel) { return kernel == FDE_TUNE_MATVEC ? 3 : kernel == FDE_TUNE_TRSV ? 4 : 0; }
+int tune_variants(int kernel) {
+    return kernel == FDE_TUNE_MATVEC ? 3 : kernel == FDE_TUNE_TRSV ? 4 : kernel == FDE_TUNE_LU ? 2 : 0;
+}
 
 int tune_lookup(int kernel, int mp, int nb, int prec, bool* need_tuning) {
     TuneState& s = state();
@@ -84,7 +86,8 @@ void tune_store(int kernel, int mp, int nb, int prec, int variant, const float* 
         f = std::fopen(s.path.c_str(), "a");
         if (!f) return;  // the table stays in memory only
     }
-    std::fprintf(f, "%s %d %d %d %d %d #", kernel == FDE_TUNE_MATVEC ? "matvec" : "trsv", kernel, mp, nb, prec,
+    std::fprintf(f, "%s %d %d %d %d %d #", kernel == FDE_TUNE_MATVEC ? "matvec" : kernel == FDE_TUNE_TRSV ? "trsv" : "lu",
+                 kernel, mp, nb, prec,
                  variant);
     for (int i = 0; ms && i < tune_variants(kernel); ++i) std::fprintf(f, " %.4f", ms[i]);
     std::fprintf(f, " ms\n");
