@@ -226,9 +226,10 @@ int fde_batch_solve(fde_batch* b, const fde_pgmres_opts* opts, double* const* x_
 /* Declare that every instance has the same operator M and preconditioner (m, s, alpha,
  * interval, BVM scheme and coefficients d+, d- equal; only u0 and f differ): many
  * right-hand sides of one problem.  fde_batch_factor then factors the Strang blocks
- * once (instance 0, through strang_precond_factor) and every instance's block solves
- * read those factors; the solve kernels of one block index run side by side, so each
- * factor plane is read from HBM once per iteration for all right-hand sides.  Call after
+ * once (instance 0, through strang_precond_factor) and the block solves of every
+ * Arnoldi step take the right-hand sides in groups of eight per CTA (one CTA per
+ * Strang block and group), so each factor plane is streamed from HBM once per group
+ * instead of once per right-hand side.  Call after
  * fde_batch_create and before fde_batch_factor.  Errors: FDE_ERR_ARG (an instance has
  * another operator), FDE_ERR_STATE, FDE_ERR_CUDA.  (The paper solves one right-hand
  * side; the factors depend on J, A and B only, Sec. 3.2.) */
@@ -398,8 +399,11 @@ long long fde_launch_count(void);
  * variant 0 unless fde_tune_set selects one. */
 #define FDE_TUNE_LU 2
 #define FDE_TUNE_KERNELS 3
-/* variant -1: autotune (the default); 0 .. n-1: always launch that variant
- * (0 is the built-in default).  Process-wide.  Errors: FDE_ERR_ARG. */
+/* variant -1: autotune (the default); 0 .. n-1: always launch that variant.
+ * Before a shape is measured the built-in default runs (block solves with FP32
+ * factors: 1, the 384 x 8 shape; otherwise 0); measuring keeps the default unless
+ * another variant is faster by more than 2 % (median of five interleaved rounds).
+ * Process-wide.  Errors: FDE_ERR_ARG. */
 int fde_tune_set(int kernel, int variant);
 /* Use `path` for the tuning table (NULL or "": memory only), dropping the table in
  * memory and loading the file's entries.  Errors: none. */

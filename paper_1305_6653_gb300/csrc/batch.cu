@@ -89,7 +89,12 @@ int cycle_launches(fde_batch* b, int nr, const fde_pgmres_opts& o, cudaStream_t 
     int rc;
     for (int j = 0; j < o.restart; ++j) {
         if ((rc = launch_time_fft_batched(b->d_inst, b->d_act, nr, b->max_mp, b->max_s, j, st))) return rc;
-        if ((rc = launch_trsv_batched(b->d_inst, b->d_act, nr, b->max_nblk, b->max_mp, st))) return rc;
+        // shared operator: groups of right-hand sides per CTA, each factor plane streamed once per group
+        if (b->shared)
+            rc = launch_trsv_multi(b->d_inst, b->d_act, nr, b->max_nblk, b->max_mp, st);
+        else
+            rc = launch_trsv_batched(b->d_inst, b->d_act, nr, b->max_nblk, b->max_mp, st);
+        if (rc) return rc;
         if ((rc = launch_time_ifft_batched(b->d_inst, b->d_act, nr, b->max_mp, b->max_s, j, st))) return rc;
         if ((rc = launch_matvec_batched(b->d_inst, b->d_act, nr, b->max_s, b->max_L, b->max_m, 0, j, st))) return rc;
         if ((rc = launch_dots_batched(b->d_inst, b->d_act, nr, 0, j, st))) return rc;

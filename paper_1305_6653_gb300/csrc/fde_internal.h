@@ -286,7 +286,8 @@ int tune_variants(int kernel);
 int tune_lookup(int kernel, int mp, int nb, int prec, bool* need_tuning);
 void tune_store(int kernel, int mp, int nb, int prec, int variant, const float* ms);  // ms: per variant, or NULL
 int tune_measure(int kernel, cudaStream_t st, int (*fn)(void*, int, cudaStream_t), void* ctx, int* best,
-                 float* ms_out);  // ms_out: the best time of every variant (tune_variants entries), or NULL
+                 float* ms_out, int default_variant);  // ms_out: the median time of every variant, or NULL
+int tune_default_variant(int kernel, int prec);
 constexpr int TUNE_MAX_VARIANTS = 8;
 // the tuned kernels' variant launchers (matvec.cu, lu.cu) and the tuning passes
 int launch_matvec64_variant(const Problem& P, const double* z, double* y, int variant, cudaStream_t st);
@@ -307,6 +308,10 @@ size_t tc_pack_bytes_per_block(int precision, int mp);    // packed tensor-core 
 size_t tc_pack_a_bytes_per_block(int precision, int mp);  // the A' part (B' follows)
 size_t tc_pack_b_bytes_per_block(int precision, int mp);  // the B' part (inverse tiles follow)
 int launch_trsv_batched(const InstDev* I, const int* act, int nact, int max_nblk, int max_mp, cudaStream_t st);
+// Block solves of instances that share one operator's factors (FP32 with inverted
+// diagonal tiles): groups of 8 right-hand sides per CTA, each factor plane streamed once
+// per group
+int launch_trsv_multi(const InstDev* I, const int* act, int nact, int nblk, int mp, cudaStream_t st);
 int launch_time_fft_batched(const InstDev* I, const int* act, int nact, int max_mp, int max_s, int j,
                             cudaStream_t st);
 int launch_time_ifft_batched(const InstDev* I, const int* act, int nact, int max_mp, int max_s, int j,

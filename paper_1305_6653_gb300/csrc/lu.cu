@@ -12,8 +12,9 @@
 // Per panel step p (columns [p NB, (p+1) NB)):
 //   1. lu_diag:   factor the NB x NB diagonal block in shared memory (one CTA per block)
 //   2. lu_panel:  L21 = A21 U11^{-1} and U12 = L11^{-1} A12 (row / column chunks)
-//   3. lu_update: A22 -= L21 U12 (complex GEMM on CUDA cores; the tensor-core
-//                 variant lives in lu_tc.cu)
+//   3. lu_update: A22 -= L21 U12 (complex GEMM on CUDA cores; the two-level
+//                 tensor-core variant is run_lu_tc below, its tile kernels in
+//                 lu_tc2.cuh and lu_tc2w.cuh)
 #include <algorithm>
 
 #include <cuda.h>  // CUtensorMap (the encoder is fetched from the driver at run time)
@@ -943,6 +944,249 @@ block_trsv_batched(const InstDev* __restrict__ I, const int* __restrict__ act) {
         trsv_body<T, true>(d.mp, fac, dinv, (const T*)d.tinv + (size_t)k * (mp / 32) * 4096, rhat);
     else
         trsv_body<T, false>(d.mp, fac, dinv, nullptr, rhat);
+}
+
+// ---------------------------------------------------------------------------
+// Block solves for many right-hand sides of one operator (the instances of a batch
+// that share their factors): one CTA per Strang block and group of up to TRSV_R
+// right-hand sides, so each factor plane is streamed from HBM once per group instead
+// of once per right-hand side.  Same roles and hand-over as trsv_body: warp 0 solves
+// the 32 x 32 diagonal tiles (inverted tiles, look-ahead of the previous strip) for
+// all TRSV_R columns; warps 1.. stream the strips, TRSV_TPR lanes per row, each lane
+// four factor columns times TRSV_R right-hand sides, and a reduce-scatter over the
+// row's lanes leaves lane `sub` with column sub's sum.  The y vectors live in shared
+// memory as [row][column].  Columns without an instance (a short last group) or whose
+// instance has left the restart cycle are computed on zeros and not written back.
+// ---------------------------------------------------------------------------
+constexpr int TRSV_R = 8;           // right-hand sides per CTA (= TRSV_TPR: one column per lane)
+constexpr int TRSVM_THREADS = 384;  // warp 0 + 11 streaming warps (44 row groups)
+static_assert(TRSV_R == TRSV_TPR, "the reduce-scatter leaves one column per lane of a row group");
+
+__host__ __device__ static size_t trsv_multi_smem_bytes(int mp) {
+    return (size_t)mp * TRSV_R * sizeof(float2) + 8 * 32 * trsv_tile<float>::LD * sizeof(float);
+}
+
+// One row's strip product for TRSV_R columns: lane `sub` holds factor columns
+// 4 sub .. 4 sub + 3 (re v, im w) and, in registers, the strip's solution values
+// xr[c][j] of those columns; returns column `sub`'s sum, reduced
+// over the TRSV_TPR lanes of the row by a reduce-scatter (each step keeps half of
+// the columns and adds the partner's half).
+__device__ __forceinline__ float2 multi_row_product(const float4& v, const float4& w, const float2 (&xr)[4][TRSV_R],
+                                                    int sub) {
+    float pr[TRSV_R], pi[TRSV_R];
+#pragma unroll
+    for (int j = 0; j < TRSV_R; ++j) {
+        const float2 x0 = xr[0][j], x1 = xr[1][j], x2 = xr[2][j], x3 = xr[3][j];
+        float a = v.x * x0.x;
+        a = fmaf(-w.x, x0.y, a);
+        a = fmaf(v.y, x1.x, a);
+        a = fmaf(-w.y, x1.y, a);
+        a = fmaf(v.z, x2.x, a);
+        a = fmaf(-w.z, x2.y, a);
+        a = fmaf(v.w, x3.x, a);
+        a = fmaf(-w.w, x3.y, a);
+        float b = v.x * x0.y;
+        b = fmaf(w.x, x0.x, b);
+        b = fmaf(v.y, x1.y, b);
+        b = fmaf(w.y, x1.x, b);
+        b = fmaf(v.z, x2.y, b);
+        b = fmaf(w.z, x2.x, b);
+        b = fmaf(v.w, x3.y, b);
+        b = fmaf(w.w, x3.x, b);
+        pr[j] = a;
+        pi[j] = b;
+    }
+    // reduce-scatter over lanes sub = 0..7 (xor 4, 2, 1): after the step with offset h
+    // a lane keeps the half of its columns selected by (sub & h)
+#pragma unroll
+    for (int h = 4, n = TRSV_R; h >= 1; h >>= 1, n >>= 1) {
+        const bool upper = (sub & h) != 0;
+#pragma unroll
+        for (int j = 0; j < n / 2; ++j) {
+            const float sr = upper ? pr[j] : pr[j + n / 2], si = upper ? pi[j] : pi[j + n / 2];
+            const float rr = __shfl_xor_sync(0xffffffffu, sr, h), ri = __shfl_xor_sync(0xffffffffu, si, h);
+            const float kr = upper ? pr[j + n / 2] : pr[j], ki = upper ? pi[j + n / 2] : pi[j];
+            pr[j] = kr + rr;
+            pi[j] = ki + ri;
+        }
+    }
+    return make_float2(pr[0], pi[0]);
+}
+
+template <bool FWD>
+__device__ __forceinline__ void trsv_multi_stream(int mp, int nt, const float* re, const float* im,
+                                                  float2 (*y)[TRSV_R], const float2 (*xs)[32][TRSV_R], int bt) {
+    constexpr int GROUPS = (TRSVM_THREADS - 32) / TRSV_TPR;  // 44, a multiple of 4
+    constexpr int H = 2;                                      // rows per register buffer
+    constexpr int HG = H * GROUPS;
+    static_assert(HG >= 32, "the first batch must cover tile d+2");
+    const int g = bt / TRSV_TPR, sub = bt % TRSV_TPR;
+    for (int d = 0; d + 2 < nt; ++d) {
+        const int col = 32 * (FWD ? d : nt - 1 - d) + sub * 4;
+        const int lo = FWD ? 32 * (d + 2) : 0;
+        const int hi = FWD ? mp : 32 * (nt - 2 - d);
+        const int len = hi - lo;
+        float4 ar[2][H], ai[2][H];
+        float2 xr[4][TRSV_R];
+        auto load = [&](int b, int q0) {
+#pragma unroll
+            for (int u = 0; u < H; ++u) {
+                const int q = q0 + u * GROUPS;
+                if (q < len) {
+                    const int r = FWD ? lo + q : hi - 1 - q;
+                    ar[b][u] = ld4(re + (size_t)r * mp + col);
+                    ai[b][u] = ld4(im + (size_t)r * mp + col);
+                }
+            }
+        };
+        auto apply = [&](int b, int q0) {
+#pragma unroll
+            for (int u = 0; u < H; ++u) {
+                const int q = q0 + u * GROUPS;
+                if (q < len) {  // uniform across a warp (aligned quartets of groups, len a multiple of 32)
+                    const float2 s2 = multi_row_product(ar[b][u], ai[b][u], xr, sub);
+                    const int r = FWD ? lo + q : hi - 1 - q;
+                    float2 v = y[r][sub];
+                    v.x -= s2.x;
+                    v.y -= s2.y;
+                    y[r][sub] = v;
+                }
+            }
+        };
+        load(0, g);
+        load(1, g + HG);
+        named_sync(TRSV_BAR_X + (d & 1), TRSVM_THREADS);
+#pragma unroll
+        for (int c = 0; c < 4; ++c)  // this lane's four columns of x_d, all right-hand sides
+#pragma unroll
+            for (int j = 0; j < TRSV_R; ++j) xr[c][j] = xs[d & 1][sub * 4 + c][j];
+        apply(0, g);  // covers q < 32 (tile d+2)
+        named_arrive(TRSV_BAR_B + (d & 1), TRSVM_THREADS);
+        for (int q0 = g + HG; q0 < len; q0 += 2 * HG) {
+            load(0, q0 + HG);
+            apply(1, q0);
+            if (q0 + HG >= len) break;
+            load(1, q0 + 2 * HG);
+            apply(0, q0 + HG);
+        }
+    }
+}
+
+// Solver warp for TRSV_R columns: lane = row of the diagonal tile; the inverted tiles
+// D^-1 (tinv) and the look-ahead tile L(d, d-1) arrive by cp.async two steps ahead.
+template <bool FWD>
+__device__ __forceinline__ void trsv_multi_solver(int mp, int nt, const float* re, const float* im,
+                                                  const float* tinv, float2 (*y)[TRSV_R], float2 (*xs)[32][TRSV_R],
+                                                  float* tiles, float2 (*av)[TRSV_R], int lane) {
+    constexpr int LD = trsv_tile<float>::LD, TS = 32 * LD;
+    auto tile_of = [&](int d) { return FWD ? d : nt - 1 - d; };
+    auto issue = [&](int d) {
+        float* b = tiles + (d & 1) * 4 * TS;
+        const int j = tile_of(d);
+        const float* ti = tinv + (size_t)j * 4096 + (FWD ? 0 : 2048);
+        tile_async<float>(b, ti, 32, lane);
+        tile_async<float>(b + TS, ti + 1024, 32, lane);
+        if (d >= 1) {
+            tile_async<float>(b + 2 * TS, re, mp, 32 * j, 32 * tile_of(d - 1), lane);
+            tile_async<float>(b + 3 * TS, im, mp, 32 * j, 32 * tile_of(d - 1), lane);
+        }
+    };
+    issue(0);
+    cp_async_commit();
+    if (nt > 1) issue(1);
+    cp_async_commit();
+    for (int d = 0; d < nt; ++d) {
+        const int r0 = 32 * tile_of(d);
+        const float* Dre = tiles + (d & 1) * 4 * TS;
+        const float* Dim = Dre + TS;
+        const float* Lre = Dre + 2 * TS;
+        const float* Lim = Dre + 3 * TS;
+        cp_async_wait1();
+        __syncwarp();
+        if (d >= 2) named_sync(TRSV_BAR_B + (d & 1), TRSVM_THREADS);
+        float2 a[TRSV_R];
+#pragma unroll
+        for (int j = 0; j < TRSV_R; ++j) a[j] = y[r0 + lane][j];
+        if (d >= 1) {  // look-ahead: strip d-1 on tile d's rows
+            const float2(*xp)[TRSV_R] = xs[(d - 1) & 1];
+            for (int c = 0; c < 32; ++c) {
+                const float lr = Lre[lane * LD + c], li = Lim[lane * LD + c];
+#pragma unroll
+                for (int j = 0; j < TRSV_R; ++j) {
+                    const float2 x = xp[c][j];
+                    a[j].x = fmaf(li, x.y, fmaf(-lr, x.x, a[j].x));
+                    a[j].y = fmaf(-li, x.x, fmaf(-lr, x.y, a[j].y));
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < TRSV_R; ++j) av[lane][j] = a[j];
+        __syncwarp();
+        float2 x[TRSV_R];
+#pragma unroll
+        for (int j = 0; j < TRSV_R; ++j) x[j] = make_float2(0.f, 0.f);
+        for (int c = 0; c < 32; ++c) {  // x = D^-1 a
+            const float dr = Dre[lane * LD + c], di = Dim[lane * LD + c];
+#pragma unroll
+            for (int j = 0; j < TRSV_R; ++j) {
+                const float2 v = av[c][j];
+                x[j].x = fmaf(-di, v.y, fmaf(dr, v.x, x[j].x));
+                x[j].y = fmaf(di, v.x, fmaf(dr, v.y, x[j].y));
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < TRSV_R; ++j) {
+            y[r0 + lane][j] = x[j];
+            xs[d & 1][lane][j] = x[j];
+        }
+        __syncwarp();
+        if (d <= nt - 3) named_arrive(TRSV_BAR_X + (d & 1), TRSVM_THREADS);
+        if (d + 2 < nt) issue(d + 2);
+        cp_async_commit();
+    }
+}
+
+// grid (ceil(nact / TRSV_R), max_nblk): CTA (x, k) solves block k for the instances
+// act[TRSV_R x ..], which all use the factors of instance act[0]'s descriptor.
+__global__ void __launch_bounds__(TRSVM_THREADS)
+block_trsv_multi_kernel(const InstDev* __restrict__ I, const int* __restrict__ act, int nact) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ float2 xs[2][32][TRSV_R];
+    __shared__ float2 av[32][TRSV_R];
+    const InstDev& d0 = I[act[0]];
+    const int k = blockIdx.y;
+    if (k >= d0.nblk) return;
+    const int mp = d0.mp, nt = mp / 32;
+    const float* re = (const float*)d0.fac + (size_t)k * 2 * mp * mp;
+    const float* im = re + (size_t)mp * mp;
+    const float* tinv = (const float*)d0.tinv + (size_t)k * (mp / 32) * 4096;
+    float2(*y)[TRSV_R] = reinterpret_cast<float2(*)[TRSV_R]>(smem_raw);
+    float* tiles = reinterpret_cast<float*>(smem_raw + (size_t)mp * TRSV_R * sizeof(float2));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // the group's right-hand sides: column j <- instance act[TRSV_R blockIdx.x + j] (if live)
+    for (int e = threadIdx.x; e < mp * TRSV_R; e += blockDim.x) {
+        const int r = e / TRSV_R, j = e % TRSV_R, a = TRSV_R * blockIdx.x + j;
+        float2 v = make_float2(0.f, 0.f);
+        if (a < nact) {
+            const InstDev& d = I[act[a]];
+            if (d.ctl[0]) v = ((const float2*)d.rhat)[(size_t)k * mp + r];
+        }
+        y[r][j] = v;
+    }
+    __syncthreads();
+    if (warp == 0) trsv_multi_solver<true>(mp, nt, re, im, tinv, y, xs, tiles, av, lane);
+    else trsv_multi_stream<true>(mp, nt, re, im, y, xs, threadIdx.x - 32);
+    __syncthreads();
+    if (warp == 0) trsv_multi_solver<false>(mp, nt, re, im, tinv, y, xs, tiles, av, lane);
+    else trsv_multi_stream<false>(mp, nt, re, im, y, xs, threadIdx.x - 32);
+    __syncthreads();
+    for (int e = threadIdx.x; e < mp * TRSV_R; e += blockDim.x) {
+        const int r = e / TRSV_R, j = e % TRSV_R, a = TRSV_R * blockIdx.x + j;
+        if (a < nact) {
+            const InstDev& d = I[act[a]];
+            if (d.ctl[0]) ((float2*)d.rhat)[(size_t)k * mp + r] = y[r][j];
+        }
+    }
 }
 
 template <typename T>
@@ -1909,6 +2153,17 @@ size_t tc_pack_a_bytes_per_block(int precision, int mp) {
     return pa;
 }
 
+int launch_trsv_multi(const InstDev* I, const int* act, int nact, int nblk, int mp, cudaStream_t st) {
+    if (nact <= 0) return FDE_OK;
+    const size_t smem = trsv_multi_smem_bytes(mp);
+    if (smem > 227 * 1024) return launch_trsv_batched(I, act, nact, nblk, mp, st);  // m_p > 2560: one per CTA
+    FDE_CUDA_TRY(cudaFuncSetAttribute(block_trsv_multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+    block_trsv_multi_kernel<<<dim3((nact + TRSV_R - 1) / TRSV_R, nblk), TRSVM_THREADS, smem, st>>>(I, act, nact);
+    FDE_LAUNCH_CHECK("block_trsv_multi_kernel");
+    return FDE_OK;
+}
+
 int launch_trsv_batched(const InstDev* I, const int* act, int nact, int max_nblk, int max_mp, cudaStream_t st) {
     if (nact <= 0) return FDE_OK;
     const size_t smem = trsv_smem_bytes(max_mp, sizeof(float));
@@ -2122,7 +2377,8 @@ int autotune_trsv(Problem& P) {
     TrsvTuneCtx ctx{&P, P.d_rhat};
     int best = 0;
     float ms[TUNE_MAX_VARIANTS] = {};
-    const int rc = tune_measure(FDE_TUNE_TRSV, P.stream, trsv_trial, &ctx, &best, ms);
+    const int rc = tune_measure(FDE_TUNE_TRSV, P.stream, trsv_trial, &ctx, &best, ms,
+                                tune_default_variant(FDE_TUNE_TRSV, prec));
     if (rc) return rc;
     tune_store(FDE_TUNE_TRSV, P.mp, P.nblk, prec, best, ms);
     return FDE_OK;

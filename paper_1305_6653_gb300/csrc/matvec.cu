@@ -226,7 +226,8 @@ int autotune_matvec(Problem& P) {
     MatvecTuneCtx ctx{&P, P.d_b_rhs, P.d_work};
     int best = 0;
     float ms[TUNE_MAX_VARIANTS] = {};
-    const int rc = tune_measure(FDE_TUNE_MATVEC, P.stream, matvec_trial, &ctx, &best, ms);
+    const int rc = tune_measure(FDE_TUNE_MATVEC, P.stream, matvec_trial, &ctx, &best, ms,
+                                tune_default_variant(FDE_TUNE_MATVEC, FDE_FP64));
     if (rc) return rc;
     tune_store(FDE_TUNE_MATVEC, P.mp, P.s, FDE_FP64, best, ms);
     return FDE_OK;

@@ -9,6 +9,7 @@
 #include <mutex>
 #include <string>
 #include <tuple>
+#include <utility>
 
 #include <sys/stat.h>
 
@@ -61,6 +62,11 @@ int tune_variants(int kernel) {
     return kernel == FDE_TUNE_MATVEC ? 3 : kernel == FDE_TUNE_TRSV ? 4 : kernel == FDE_TUNE_LU ? 2 : 0;
 }
 
+// The variant used before a shape is measured (or when tuning is impossible): the
+// 384 x 8 block-solve shape for FP32 factors (never slower than 512 x 4 where both were
+// timed), the first variant otherwise.
+static int tune_default(int kernel, int prec) { return kernel == FDE_TUNE_TRSV && prec == FDE_FP32 ? 1 : 0; }
+
 int tune_lookup(int kernel, int mp, int nb, int prec, bool* need_tuning) {
     TuneState& s = state();
     std::lock_guard<std::mutex> lock(s.mu);
@@ -70,8 +76,10 @@ int tune_lookup(int kernel, int mp, int nb, int prec, bool* need_tuning) {
     auto it = s.table.find({kernel, mp, nb, prec});
     if (it != s.table.end()) return it->second;
     if (need_tuning) *need_tuning = true;
-    return 0;
+    return tune_default(kernel, prec);
 }
+
+int tune_default_variant(int kernel, int prec) { return tune_default(kernel, prec); }
 
 void tune_store(int kernel, int mp, int nb, int prec, int variant, const float* ms) {
     TuneState& s = state();
@@ -94,41 +102,49 @@ void tune_store(int kernel, int mp, int nb, int prec, int variant, const float* 
     std::fclose(f);
 }
 
-// Time fn(variant) for every variant (one untimed launch, then the best of three
-// timed ones) on stream st and return the fastest.  fn launches one kernel and
-// returns an FDE status.
+// Time fn(variant) for every variant on stream st and return the fastest: one untimed
+// launch of each, then five rounds that launch every variant once in turn (so that a
+// drift of clocks or memory state during the measurement falls on all of them), the
+// median of each variant's five times.  The default variant is kept unless another is
+// faster by more than 2 % (launch-to-launch noise).  fn launches one kernel and returns
+// an FDE status.
 int tune_measure(int kernel, cudaStream_t st, int (*fn)(void*, int, cudaStream_t), void* ctx, int* best,
-                 float* ms_out) {
-    cudaEvent_t e0, e1;
-    FDE_CUDA_TRY(cudaEventCreate(&e0));
-    FDE_CUDA_TRY(cudaEventCreate(&e1));
-    float best_ms = 1e30f;
-    *best = 0;
-    int rc = FDE_OK;
-    for (int v = 0; v < tune_variants(kernel) && !rc; ++v) {
-        if ((rc = fn(ctx, v, st))) break;
-        float vbest = 1e30f;
-        for (int r = 0; r < 3 && !rc; ++r) {
-            cudaEventRecord(e0, st);
+                 float* ms_out, int default_variant) {
+    constexpr int ROUNDS = 5;
+    const int nv = tune_variants(kernel);
+    cudaEvent_t ev[2 * ROUNDS * TUNE_MAX_VARIANTS];
+    int created = 0, rc = FDE_OK;
+    for (; created < 2 * ROUNDS * nv; ++created)
+        if (cudaEventCreate(&ev[created]) != cudaSuccess) {
+            rc = cuda_error(cudaGetLastError(), "autotune events");
+            break;
+        }
+    for (int v = 0; v < nv && !rc; ++v) rc = fn(ctx, v, st);
+    for (int r = 0; r < ROUNDS && !rc; ++r)
+        for (int v = 0; v < nv && !rc; ++v) {
+            cudaEventRecord(ev[2 * (r * nv + v)], st);
             rc = fn(ctx, v, st);
-            cudaEventRecord(e1, st);
-            if (rc) break;
-            if (cudaEventSynchronize(e1) != cudaSuccess) {
-                rc = cuda_error(cudaGetLastError(), "autotune");
-                break;
+            cudaEventRecord(ev[2 * (r * nv + v) + 1], st);
+        }
+    if (!rc && cudaStreamSynchronize(st) != cudaSuccess) rc = cuda_error(cudaGetLastError(), "autotune");
+    *best = default_variant;
+    if (!rc) {
+        float med[TUNE_MAX_VARIANTS];
+        for (int v = 0; v < nv; ++v) {
+            float t[ROUNDS];
+            for (int r = 0; r < ROUNDS; ++r) {
+                t[r] = 0.f;
+                cudaEventElapsedTime(&t[r], ev[2 * (r * nv + v)], ev[2 * (r * nv + v) + 1]);
             }
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < vbest) vbest = ms;
+            for (int a = 1; a < ROUNDS; ++a)  // insertion sort of five
+                for (int b = a; b > 0 && t[b] < t[b - 1]; --b) std::swap(t[b], t[b - 1]);
+            med[v] = t[ROUNDS / 2];
+            if (ms_out) ms_out[v] = med[v];
         }
-        if (ms_out) ms_out[v] = vbest;
-        if (vbest < best_ms) {
-            best_ms = vbest;
-            *best = v;
-        }
+        for (int v = 0; v < nv; ++v)
+            if (med[v] < 0.98f * med[*best] && (*best == default_variant || med[v] < med[*best])) *best = v;
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    for (int i = 0; i < created; ++i) cudaEventDestroy(ev[i]);
     return rc;
 }
 

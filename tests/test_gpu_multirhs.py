@@ -38,6 +38,21 @@ def test_shared_factors_solve_every_right_hand_side(precision):
     assert np.linalg.norm(xs[0] - xs[4]) > 1e-3 * np.linalg.norm(xs[0])
 
 
+def test_shared_factors_two_groups_of_right_hand_sides():
+    """Ten right-hand sides: the block solves take them in CTA groups of eight, so this
+    runs a full and a short group; each solution against the oracle's direct solve."""
+    from paper_1305_6653_gb300 import FDEBatch
+    probs = fi.config_many_rhs(count=10, m=130, s=16)
+    with FDEBatch(probs) as b:
+        b.share_operator().assemble().factor("tf32")
+        xs, stats = b.solve(tol=1e-11, restart=20, maxit=400)
+        xs = [x.cpu().numpy() for x in xs]
+    for pr, x, st in zip(probs, xs, stats):
+        ref = O.direct_solve(pr)
+        assert st["status"] == 0, st
+        assert np.abs(x - ref).max() <= 1e-8 * np.abs(ref).max(), pr.name
+
+
 def test_shared_factors_tensor_core_panels():
     """Four right-hand sides of the benchmark operator (alpha = 1.8, d+ = 1+x, d- = 2-x,
     GBDF5) at m = 1023, s = 64: eight 128-column panels of the tensor-core LU (the
