@@ -5,7 +5,7 @@ Metric: space-time FDE solves/s at rel.err 1e-8.  One step = one complete solve
 of the space-time system of a problem whose inputs (u0, f, d+, d-) are already
 resident in HBM: bvm_assemble (Grunwald weights, symbols, right-hand side) +
 strang_precond_factor (129 complex 2047 x 2047 block LUs) + pgmres_solve
-(flexible GMRES(20) to a true FP64 relative residual of --tol).
+(flexible GMRES(--restart, default 30) to a true FP64 relative residual of --tol).
 
 Default workload: m=2047 interior points, s=256 time steps, alpha=1.8,
 d+(x)=1+x, d-(x)=2-x, 5-step GBDF, manufactured source (exact solution
@@ -75,6 +75,9 @@ def parse():
     ap.add_argument("--m", type=int, default=2047)
     ap.add_argument("--s", type=int, default=256)
     ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--restart", type=int, default=30,
+                    help="GMRES restart length of the benchmark legs (the paper's Tables 1-2 use 20; the example41 "
+                         "and bccb configurations keep 20)")
     ap.add_argument("--fp64-steps", type=int, default=3,
                     help="plain FP64 solves timed for comparison, after one FP64 warm-up solve (0: skip)")
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -312,11 +315,11 @@ def oracle_sample(prob, iterations: int, its_source: str) -> dict:
     }
 
 
-def oracle_complete_solve(prob, tol: float) -> dict:
+def oracle_complete_solve(prob, tol: float, restart: int) -> dict:
     """One complete solve by the oracle as it stands: right-hand side, the Strang
     preconditioner (dense DFT along time, one LAPACK LU per frequency block), and its
-    right-preconditioned FGMRES(20) to a true relative residual of tol (the steps of
-    oracle.solve_strang_gmres, timed one by one)."""
+    right-preconditioned FGMRES(restart) to a true relative residual of tol (the steps
+    of oracle.solve_strang_gmres, timed one by one)."""
     import oracle as O
 
     t0 = time.perf_counter()
@@ -327,7 +330,7 @@ def oracle_complete_solve(prob, tol: float) -> dict:
     P = O.StrangPreconditioner(prob, J=J)
     t2 = time.perf_counter()
     _, its, ok, _ = O.gmres(lambda z: O.matvec(prob, z, J=J, AB=AB), b, precond=P.apply, side="right",
-                            restart=20, tol=tol, maxit=400, reference="b")
+                            restart=restart, tol=tol, maxit=400, reference="b")
     t3 = time.perf_counter()
     return {"seconds": t3 - t0, "rhs_s": t1 - t0, "factor_s": t2 - t1, "fgmres_s": t3 - t2, "iterations": its,
             "converged": bool(ok), "blocks": len(P.lu)}
@@ -390,7 +393,7 @@ def bench_reference(args, rank, prob, workload):
     solves = []
     t_start = time.perf_counter()
     while True:
-        r = oracle_complete_solve(prob, args.tol)
+        r = oracle_complete_solve(prob, args.tol, args.restart)
         solves.append(r)
         elapsed = time.perf_counter() - t_start
         if len(solves) >= max(1, args.steps) or elapsed + r["seconds"] > args.reference_budget:
@@ -410,7 +413,7 @@ def bench_reference(args, rank, prob, workload):
         single = {"unavailable": f"{type(e).__name__}: {e}"}
     stage = {k: round(sum(r[k] for r in solves) / len(solves), 3) for k in ("rhs_s", "factor_s", "fgmres_s")}
     sample = (f"{len(solves)} complete oracle solve(s) of the workload (m={prob.m}, s={prob.s}): right-hand side, "
-              f"dense LAPACK LUs of all {solves[-1]['blocks']} Strang blocks, FGMRES(20) to a true residual of "
+              f"dense LAPACK LUs of all {solves[-1]['blocks']} Strang blocks, FGMRES({args.restart}) to a true residual of "
               f"{args.tol:g} ({solves[-1]['iterations']} iterations); mean wall per stage {stage}")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
             "steps": len(solves), "warmup": 0, "ms_per_step": t * 1e3, "higher_is_better": True,
@@ -449,7 +452,7 @@ def measure_batch(args, steps: int, warmup: int, sequential: bool = True, sample
 
     def step():
         b.assemble().factor(args.batch_precision)
-        _, st = b.solve(tol=args.tol, restart=20, maxit=400, outs=outs)
+        _, st = b.solve(tol=args.tol, restart=args.restart, maxit=400, outs=outs)
         return st
 
     for _ in range(warmup):
@@ -486,7 +489,7 @@ def measure_batch(args, steps: int, warmup: int, sequential: bool = True, sample
         for pr, o in zip(probs, outs):
             with fde.FDEProblem.from_inputs(pr, device_inputs=True) as p:
                 p.assemble().factor(args.batch_precision)
-                p.solve(tol=args.tol, restart=20, maxit=400, out=o)
+                p.solve(tol=args.tol, restart=args.restart, maxit=400, out=o)
         e1.record()
         e1.synchronize()
         seq_s = max(e0.elapsed_time(e1) / 1e3, time.perf_counter() - t0)
@@ -513,7 +516,7 @@ def bench_batch(args, world, rank, local_rank):
                 "data": "synthetic",
                 "config": {"workload": "batch64_m255-2047_s64-256_etr3_gbdf3_gam4", "instances": r["instances"],
                            "unknowns_total": r["unknowns_total"], "precision": args.batch_precision,
-                           "tol_true_residual": args.tol, "restart": 20,
+                           "tol_true_residual": args.tol, "restart": args.restart,
                            "l2": "flushed (512 MiB write) before every timed step"},
                 "roofline": None, "gpu_launches": r["gpu_launches"], "clocks": r["clocks"],
                 "iterations": r["iterations"], "sequential_single_api": r["sequential_single_api"],
@@ -542,7 +545,7 @@ def bench_many_rhs(args, world, rank, local_rank):
 
     def step():
         b.assemble().factor(args.precision)
-        _, st = b.solve(tol=args.tol, restart=20, maxit=400, outs=outs)
+        _, st = b.solve(tol=args.tol, restart=args.restart, maxit=400, outs=outs)
         return st
 
     for _ in range(args.warmup):
@@ -574,7 +577,7 @@ def bench_many_rhs(args, world, rank, local_rank):
     for pr, out in zip(probs, outs):
         with fde.FDEProblem.from_inputs(pr, device_inputs=True) as p:
             p.assemble().factor(args.precision)
-            p.solve(tol=args.tol, restart=20, maxit=400, out=out)
+            p.solve(tol=args.tol, restart=args.restart, maxit=400, out=out)
     e1.record()
     e1.synchronize()
     seq_s = e0.elapsed_time(e1) / 1e3
@@ -592,7 +595,7 @@ def bench_many_rhs(args, world, rank, local_rank):
                 "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
                 "config": {"workload": f"many_rhs{count}_m{args.m}_s{args.s}_gbdf5_alpha1.8_variable_d",
                            "right_hand_sides": count, "m": args.m, "s": args.s, "precision": args.precision,
-                           "tol_true_residual": args.tol, "restart": 20,
+                           "tol_true_residual": args.tol, "restart": args.restart,
                            "l2": "flushed (512 MiB write) before every timed step; factors (4.3 GB) exceed L2"},
                 "roofline": None, "gpu_launches": launches, "clocks": clocks,
                 "iterations": [st["iterations"] for st in stats],
@@ -625,7 +628,7 @@ def measure_precision(args, steps: int, warmup: int, precisions=("fp64", "fp32",
 
     def step(precision):
         p.assemble().factor(precision)
-        _, st = p.solve(tol=tol, restart=20, maxit=100, out=xbuf, raise_on_error=False)
+        _, st = p.solve(tol=tol, restart=args.restart, maxit=100, out=xbuf, raise_on_error=False)
         return st
 
     variants, sols = {}, {}
@@ -679,7 +682,7 @@ def bench_precision(args, world, rank, local_rank):
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
                 "data": "synthetic",
                 "config": {"workload": r["workload"], "m": r["m"], "s": r["s"], "unknowns": r["unknowns"],
-                           "precision": best, "tol_true_residual": r["tol_true_residual"], "restart": 20,
+                           "precision": best, "tol_true_residual": r["tol_true_residual"], "restart": args.restart,
                            "l2": "flushed (512 MiB write) before every timed step"},
                 "roofline": None, "gpu_launches": r["gpu_launches"], "clocks": r["clocks"],
                 "variants": r["variants"], "note": r["note"]}
@@ -711,7 +714,7 @@ def bench_timevar(args, world, rank, local_rank):
 
     def step():
         p.assemble().factor(args.precision)
-        _, st = p.solve(tol=args.tol, restart=20, maxit=400, out=xbuf)
+        _, st = p.solve(tol=args.tol, restart=args.restart, maxit=400, out=xbuf)
         return st
 
     for _ in range(args.warmup):
@@ -761,7 +764,7 @@ def bench_timevar(args, world, rank, local_rank):
                 "config": {"workload": f"timevar_m{prob.m}_s{prob.s}_gbdf5_alpha1.8_d_of_x_t", "m": prob.m,
                            "s": prob.s, "unknowns": prob.n, "scheme": "GBDF5", "alpha": 1.8,
                            "d": "d+=(1+x)(1+sin(pi t)/2), d-=(2-x)(1+t/2)", "precision": args.precision,
-                           "tol_true_residual": args.tol, "restart": 20,
+                           "tol_true_residual": args.tol, "restart": args.restart,
                            "l2": "flushed (512 MiB write) before every timed step; factors exceed L2"},
                 "roofline": roof, "gpu_launches": launches, "clocks": clocks,
                 "iterations": [s["iterations"] for s in stats], "rel_residual": stats[-1]["rel_residual"],
@@ -1062,7 +1065,7 @@ def main():
     prob = fde_inputs.config_scale(args.m, args.s)
     workload = {"workload": f"scale_m{args.m}_s{args.s}_gbdf5_alpha1.8_variable_d", "m": args.m, "s": args.s,
                 "unknowns": args.m * args.s, "scheme": "GBDF5", "alpha": 1.8, "d": "d+=1+x, d-=2-x",
-                "tol_true_residual": args.tol, "restart": 20, "precision": args.precision,
+                "tol_true_residual": args.tol, "restart": args.restart, "precision": args.precision,
                 "arnoldi_matvec": args.matvec if args.matvec == "fp64" else f"fp32 (relax {args.relax:g})",
                 "l2": "flushed (512 MiB write) before every timed step; factors (4.3 GB fp32) exceed L2"}
 
@@ -1100,7 +1103,7 @@ def main():
         p.assemble()
         p.factor(precision)
         mv = args.matvec if matvec is None else matvec
-        _, st = p.solve(tol=args.tol, restart=20, maxit=400, out=xbuf, matvec=mv, relax=args.relax)
+        _, st = p.solve(tol=args.tol, restart=args.restart, maxit=400, out=xbuf, matvec=mv, relax=args.relax)
         return st
 
     # the block-solve timer is selected before the warm-up, so that the iteration graphs
@@ -1204,7 +1207,7 @@ def main():
             matvec_line["note"] = ("mixed: FP32 Arnoldi products and FP64 restart residuals; no single-precision "
                                    "roofline")
     path_roof = path_roofline(prob.m, prob.s, mp, esz, stats[-1]["iterations"], args.precision, bf16_peak,
-                              hbm_peak, ms_per_step, tf32_peak=tf32_peak, fp64_peak=fp64_peak)
+                              hbm_peak, ms_per_step, restart=args.restart, tf32_peak=tf32_peak, fp64_peak=fp64_peak)
     nps = max(args.profile_steps, 1)
     stage_ms = {k: round(v[0] / nps, 4) for k, v in prof.items()}
     stage_n = {k: v[1] // nps for k, v in prof.items()}
@@ -1253,7 +1256,7 @@ def main():
                                dplus=host["dplus"].numpy(), dminus=host["dminus"].numpy(), u0=host["u0"].numpy(),
                                f=host["f"].numpy(), family=prob.family, mu=prob.mu, device_inputs=False)
             q.assemble().factor(args.precision)
-            q.solve(tol=args.tol, restart=20, maxit=400, out=xh, matvec=args.matvec,
+            q.solve(tol=args.tol, restart=args.restart, maxit=400, out=xh, matvec=args.matvec,
                     relax=args.relax)  # returns after the copy to xh
             q.close()
 

@@ -105,8 +105,8 @@ void tune_store(int kernel, int mp, int nb, int prec, int variant, const float* 
 // Time fn(variant) for every variant on stream st and return the fastest: one untimed
 // launch of each, then five rounds that launch every variant once in turn (so that a
 // drift of clocks or memory state during the measurement falls on all of them), the
-// median of each variant's five times.  The default variant is kept unless another is
-// faster by more than 2 % (launch-to-launch noise).  fn launches one kernel and returns
+// median of each variant's five times.  The fastest variant is taken if it beats the
+// default by more than 2 % (launch-to-launch noise), else the default is kept.  fn launches one kernel and returns
 // an FDE status.
 int tune_measure(int kernel, cudaStream_t st, int (*fn)(void*, int, cudaStream_t), void* ctx, int* best,
                  float* ms_out, int default_variant) {
@@ -141,8 +141,10 @@ int tune_measure(int kernel, cudaStream_t st, int (*fn)(void*, int, cudaStream_t
             med[v] = t[ROUNDS / 2];
             if (ms_out) ms_out[v] = med[v];
         }
+        int fastest = default_variant;
         for (int v = 0; v < nv; ++v)
-            if (med[v] < 0.98f * med[*best] && (*best == default_variant || med[v] < med[*best])) *best = v;
+            if (med[v] < med[fastest]) fastest = v;
+        if (med[fastest] < 0.98f * med[default_variant]) *best = fastest;
     }
     for (int i = 0; i < created; ++i) cudaEventDestroy(ev[i]);
     return rc;
