@@ -170,8 +170,8 @@ __global__ void __launch_bounds__(256) lu_diag_batched(const BlkDev* __restrict_
 constexpr int RC = 128;
 // Ranges: rows mode over rows [rb, rend) against the diagonal block at (od, od);
 // columns mode over columns [cb, cend).  Tensor-core packing (PACK >= 0): rows r >= R0
-// of L21 go to A' tiles, columns >= R0 of U12 to B' tiles, at K' offset kq (Re) and
-// TB + kq (Im) -- the layout of lu_tc2.cuh.
+// of L21 go to A' tiles at K' offset kq (Re) and TB + kq (Im), columns >= R0 of U12 to
+// B' tiles at K offset kq (rows j: Re, TB + j: Im) -- the layout of lu_tc2.cuh.
 template <typename T, int PACK>
 __device__ __forceinline__ void panel_body(int mp, int od, int rb, int rend, int cb, int cend, int nrow,
                                            T* __restrict__ re, unsigned char* __restrict__ apack,
@@ -260,10 +260,8 @@ __device__ __forceinline__ void panel_body(int mp, int od, int rb, int rend, int
                         pack2_store<PACK>(t, T2_BM, rt, TB + kq + c, vi, false);
                     } else {
                         unsigned char* t = bpack + (size_t)tile * Cfg::B_TILE;
-                        pack2_store<PACK>(t, 2 * T2_BN, rt, kq + c, vr, true);  // Re output: Re L Re U - Im L Im U
-                        pack2_store<PACK>(t, 2 * T2_BN, rt, TB + kq + c, -vi, true);
-                        pack2_store<PACK>(t, 2 * T2_BN, T2_BN + rt, kq + c, vi, true);  // Im output
-                        pack2_store<PACK>(t, 2 * T2_BN, T2_BN + rt, TB + kq + c, vr, true);
+                        pack2_store<PACK>(t, 2 * T2_BN, rt, kq + c, vr, true);  // Re part
+                        pack2_store<PACK>(t, 2 * T2_BN, T2_BN + rt, kq + c, vi, true);  // Im part
                     }
                 }
             }
@@ -1759,22 +1757,16 @@ __device__ __forceinline__ void diag128_body(int mp, int o, float* __restrict__ 
         }
         pack2_seg<KIND>(pA, T2_BM, i, kp0, v, false);
     }
-    for (int e = t; e < 2 * TB * SEGS; e += blockDim.x) {
+    for (int e = t; e < TB * SEGS; e += blockDim.x) {
         const int brow = e % (2 * TB), kp0 = (e / (2 * TB)) * EPS;
         const int j = brow & (TB - 1);
-        const bool im_out = brow >= TB, second = kp0 >= TB;
-        // Re output row: [Re U^{-1}[k][j] | -Im U^{-1}[k][j]]; Im output row: [Im | Re]
+        const bool im_part = brow >= TB;
+        // B' row j: Re U^{-1}[k][j]; row TB + j: Im U^{-1}[k][j] (k = K index)
         float v[EPS];
 #pragma unroll
         for (int u = 0; u < EPS; ++u) {
-            const int kk = (kp0 + u) & (TB - 1);
-            float x = 0.f;
-            if (kk <= j) {
-                const bool take_im = im_out != second;
-                x = take_im ? Ai[kk * LD + j] : Ar[kk * LD + j];
-                if (!im_out && second) x = -x;
-            }
-            v[u] = x;
+            const int kk = kp0 + u;
+            v[u] = kk <= j ? (im_part ? Ai[kk * LD + j] : Ar[kk * LD + j]) : 0.f;
         }
         pack2_seg<KIND>(pB, 2 * T2_BN, brow, kp0, v, true);
     }
@@ -1827,20 +1819,16 @@ __device__ __forceinline__ void pack_panel_body(int mp, int o, int R0, const flo
         } else {
             const long e2 = e - items;
             const int g = (int)(e2 / nr), jl = (int)(e2 % nr);
-            float nv[EPS];
 #pragma unroll
             for (int u = 0; u < EPS; ++u) {
                 const size_t off = (size_t)(o + g * EPS + u) * mp + R0 + jl;
                 vr[u] = re[off];
                 vi[u] = im[off];
-                nv[u] = -vi[u];
             }
             unsigned char* tile = bpack + (size_t)(jl / T2_BN) * Cfg::B_TILE;
             const int jr = jl % T2_BN;
             pack2_seg<KIND>(tile, 2 * T2_BN, jr, g * EPS, vr, true);
-            pack2_seg<KIND>(tile, 2 * T2_BN, jr, TB + g * EPS, nv, true);
             pack2_seg<KIND>(tile, 2 * T2_BN, T2_BN + jr, g * EPS, vi, true);
-            pack2_seg<KIND>(tile, 2 * T2_BN, T2_BN + jr, TB + g * EPS, vr, true);
         }
     }
 }

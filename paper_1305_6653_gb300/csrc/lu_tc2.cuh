@@ -4,20 +4,27 @@
 // panel products L21 = A21 U11^{-1}, U12 = L11^{-1} A12 and the rank-128 trailing
 // update A22 -= L21 U12 run here, each as complex GEMMs with K' = 2 x 128.
 //
-// Complex product as one real GEMM (N' = 2 x 128 outputs side by side):
-//   A' = [Re L | Im L]                                      128 rows x K' = 256
-//   B' = [[Re U ; -Im U] | [Im U ; Re U]]^T                256 rows x K'
-//   D  = A' B'^T:  D[:, 0:128] = Re(L U),  D[:, 128:256] = Im(L U).
+// Complex product D = L U of 128 x 128 complex tiles (Re and Im outputs side by
+// side in N' = 2 x 128 accumulator columns), operands packed as
+//   A' = [Re L | Im L]                         128 rows x K' = 256
+//   B' = [Re U | Im U]^T                       256 rows x K = 128
+// (B' row j holds Re U[:, j], row 128 + j holds Im U[:, j]).  Per K step the
+// product is three MMAs:
+//   D[:, 0:256]   += Re L . [Re U | Im U]        (N = 256)
+//   D[:, 0:128]   -= Im L . Im U                 (N = 128, A negated by the instruction)
+//   D[:, 128:256] += Im L . Re U                 (N = 128)
+// so a tile streams 256 KB of operands (A' 128 KB, B' 128 KB) instead of the 384 KB
+// of one real GEMM with the B' operand doubled to [[Re U ; -Im U] | [Im U ; Re U]].
 // Operands are pre-packed as K-chunks of 64 bytes per row, each chunk in the
 // canonical no-swizzle K-major core-matrix layout (8 rows x 16 B core matrices,
 // LBO = 128 B along K, SBO = 512 B between 8-row groups), so one bulk copy lands
 // a chunk of a tile in shared memory.
 //
 // The tile kernel (one 128 x 128 complex output tile per CTA, 128 threads):
-//   * streams the K-chunks through a full / empty mbarrier ring, one thread
-//     issuing the MMAs (M = 128, N = 256, accumulator in 256 TMEM columns);
-//   * update mode (C -= D): prefetches its C rows into L2 at the start, runs an
-//     8-stage ring (192 KB in flight), then copies C from L2 into the freed ring,
+//   * streams the K steps (A' real and imaginary chunk, B' chunk) through a full /
+//     empty mbarrier ring, one thread issuing the MMAs (accumulator in 256 TMEM columns);
+//   * update mode (C -= D): prefetches its C rows into L2 at the start, runs a
+//     6-stage ring (192 KB in flight), then copies C from L2 into the freed ring,
 //     subtracts D (tcgen05.ld) and writes the tile back with bulk copies;
 //   * store mode (C = D): a 3-stage ring (two CTAs per SM) and D goes from TMEM
 //     straight to HBM; C is never read.
@@ -36,8 +43,8 @@ constexpr int T2_BM = 128;          // output rows per CTA
 constexpr int T2_BN = 128;          // complex output columns per CTA (N' = 256)
 constexpr int T2_KP = 2 * TB;       // K' = 256 real (one product)
 constexpr int T2_STAGES = 3;       // store mode
-constexpr int T2_STAGES_UPD = 8;   // update mode
-constexpr int T2_STAGES_MAX = 8;
+constexpr int T2_STAGES_UPD = 6;   // update mode
+constexpr int T2_STAGES_MAX = 6;
 constexpr int T2_CROW = 528;        // bytes per C-tile row in shared memory (512 + 16 pad, 16-B aligned)
 constexpr int T2_C_BYTES = T2_BM * T2_CROW;  // one plane
 
@@ -53,18 +60,53 @@ struct Tc2 {
     static constexpr int NCH = KP / KCH;        // chunks per tile
     static constexpr int A_CHUNK = T2_BM * 64;  // bytes
     static constexpr int B_CHUNK = 2 * T2_BN * 64;
+    static constexpr int CPS = T2_KP / KCH;   // A' chunks per K' = 256 product segment
+    static constexpr int HALF = CPS / 2;      // chunks of its real (or imaginary) K half
+    static constexpr int NIT = NCH / 2;       // main-loop steps: A' re + im chunk, B' chunk
     static constexpr int A_TILE = NCH * A_CHUNK;
-    static constexpr int B_TILE = NCH * B_CHUNK;
-    static constexpr int STAGE = A_CHUNK + B_CHUNK;
+    static constexpr int B_TILE = NIT * B_CHUNK;  // B' keeps K = 128 per product segment
+    static constexpr int STAGE = 2 * A_CHUNK + B_CHUNK;
     static constexpr int SMEM = T2_STAGES_UPD * STAGE;  // the C tile reuses the ring after the main loop
     static_assert(SMEM >= 2 * T2_C_BYTES, "C tile must fit the freed operand ring");
-    // Store mode (no C tile): the operand ring only, padded so that at most two CTAs
-    // (2 x 256 TMEM columns) share an SM.
-    static constexpr int SMEM_STORE = T2_STAGES * STAGE > 80 * 1024 ? T2_STAGES * STAGE : 80 * 1024;
+    // Store mode (no C tile): the operand ring only; at most two CTAs (2 x 256 TMEM
+    // columns) share an SM.
+    static constexpr int SMEM_STORE = T2_STAGES * STAGE;
+    static_assert(3 * SMEM_STORE > 227 * 1024, "store mode: at most two CTAs per SM");
     static constexpr int KSTEP = KIND == 1 ? 16 : 8;          // K per MMA = 32 bytes = 2 core matrices
     static constexpr int MMAS = KCH / KSTEP;                  // MMAs per chunk (2)
     static constexpr uint32_t IDESC = tc::instr_desc(KIND == 1 ? 1u : 2u, T2_BM, 2 * T2_BN);
+    static constexpr uint32_t IDESC_H = tc::instr_desc(KIND == 1 ? 1u : 2u, T2_BM, T2_BN);
+    static constexpr uint32_t IDESC_HN = IDESC_H | tc::IDESC_NEGATE_A;
+    // A' chunk holding the real K part of main-loop step it (its imaginary part is HALF
+    // chunks further; the step's B' chunk is chunk it)
+    __host__ __device__ static constexpr int re_chunk(int it) { return (it / HALF) * CPS + it % HALF; }
 };
+
+// The MMAs of one main-loop step into the accumulator at tacc (256 columns): a_re /
+// a_im the shared addresses of the A' chunks of the real and imaginary K part, b the
+// B' chunk (rows 0..127 Re U, rows 128..255 Im U).  first: the step that starts D.
+template <int KIND>
+__device__ __forceinline__ void cplx_mma_step(uint32_t tacc, uint32_t a_re, uint32_t a_im, uint32_t b, bool first) {
+    using Cfg = Tc2<KIND>;
+    constexpr uint32_t B_IM = (T2_BN / 8) * 512;  // row 128 of the B' chunk
+#pragma unroll
+    for (int j = 0; j < Cfg::MMAS; ++j) {
+        const uint64_t ar = tc::smem_desc(a_re + j * 256, 128, 512);
+        const uint64_t ai = tc::smem_desc(a_im + j * 256, 128, 512);
+        const uint64_t bb = tc::smem_desc(b + j * 256, 128, 512);
+        const uint64_t bi = tc::smem_desc(b + B_IM + j * 256, 128, 512);
+        const uint32_t acc = (!first || j > 0) ? 1u : 0u;
+        if (KIND == 1) {
+            tc::mma_f16(tacc, ar, bb, Cfg::IDESC, acc);
+            tc::mma_f16(tacc, ai, bi, Cfg::IDESC_HN, 1u);
+            tc::mma_f16(tacc + T2_BN, ai, bb, Cfg::IDESC_H, 1u);
+        } else {
+            tc::mma_tf32(tacc, ar, bb, Cfg::IDESC, acc);
+            tc::mma_tf32(tacc, ai, bi, Cfg::IDESC_HN, 1u);
+            tc::mma_tf32(tacc + T2_BN, ai, bb, Cfg::IDESC_H, 1u);
+        }
+    }
+}
 
 // Byte offset of element (row, kp) of a packed tile whose chunks hold `rows` rows.
 template <int KIND>
@@ -83,23 +125,26 @@ __device__ __forceinline__ void pack2_raw(unsigned char* tile, int rows, int row
         *reinterpret_cast<float*>(p) = tc::to_tf32(v);
 }
 
-// Store value v at K' position kp (< 256) of an A' (b_side = false) or B' tile.
+// Store value v at K' position kp of an A' tile (b_side = false, kp < 256) or a B'
+// tile (kp < 128).  Split TF32 repeats each value per product segment (256 K' for A',
+// 128 for B').
 template <int KIND>
 __device__ __forceinline__ void pack2_store(unsigned char* tile, int rows, int row, int kp, float v, bool b_side) {
     if constexpr (KIND == 2) {
         const float hi = tc::to_tf32(v);
         const float lo = tc::to_tf32(v - hi);
+        const int seg = b_side ? TB : T2_KP;
         pack2_raw<KIND>(tile, rows, row, kp, hi);
-        pack2_raw<KIND>(tile, rows, row, T2_KP + kp, b_side ? hi : lo);
-        pack2_raw<KIND>(tile, rows, row, 2 * T2_KP + kp, b_side ? lo : hi);
+        pack2_raw<KIND>(tile, rows, row, seg + kp, b_side ? hi : lo);
+        pack2_raw<KIND>(tile, rows, row, 2 * seg + kp, b_side ? lo : hi);
     } else {
         pack2_raw<KIND>(tile, rows, row, kp, v);
     }
 }
 
 // Store the PER_CORE values v[0..PER_CORE) at K' positions kp0 .. kp0 + PER_CORE - 1
-// (kp0 a multiple of PER_CORE, < 256) of one row: one 16-byte core-matrix row
-// segment per product segment.
+// (kp0 a multiple of PER_CORE, < 256 for A', < 128 for B') of one row: one 16-byte
+// core-matrix row segment per product segment.
 template <int KIND>
 __device__ __forceinline__ void pack2_seg(unsigned char* tile, int rows, int row, int kp0, const float* v,
                                           bool b_side) {
@@ -114,8 +159,9 @@ __device__ __forceinline__ void pack2_seg(unsigned char* tile, int rows, int row
         if constexpr (KIND == 2) {
             const float4 lo = make_float4(tc::to_tf32(v[0] - hi.x), tc::to_tf32(v[1] - hi.y),
                                           tc::to_tf32(v[2] - hi.z), tc::to_tf32(v[3] - hi.w));
-            *reinterpret_cast<float4*>(tile + pack2_off<KIND>(rows, row, T2_KP + kp0)) = b_side ? hi : lo;
-            *reinterpret_cast<float4*>(tile + pack2_off<KIND>(rows, row, 2 * T2_KP + kp0)) = b_side ? lo : hi;
+            const int seg = b_side ? TB : T2_KP;
+            *reinterpret_cast<float4*>(tile + pack2_off<KIND>(rows, row, seg + kp0)) = b_side ? hi : lo;
+            *reinterpret_cast<float4*>(tile + pack2_off<KIND>(rows, row, 2 * seg + kp0)) = b_side ? lo : hi;
         }
     }
 }
@@ -137,7 +183,7 @@ __device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy
 // Operand tiles of the next outer step packed from an updated C tile staged in shared
 // memory (row pitch T2_CROW), one thread per row (A') or column (B'):
 //   A' -- tile row r -> A' row r, K' = [Re | Im] of the tile's 128 columns (the next L21 source);
-//   B' -- tile column j -> B' rows j (Re outputs) and T2_BN + j (Im outputs), K' = the tile
+//   B' -- tile column j -> B' rows j (Re part) and T2_BN + j (Im part), K = the tile
 //         row (the next U12 source).
 template <int KIND>
 __device__ __forceinline__ void pack_staged_a(unsigned char* __restrict__ pk, const unsigned char* sCr,
@@ -168,17 +214,14 @@ __device__ __forceinline__ void pack_staged_b(unsigned char* __restrict__ pk, co
     if (j >= ncols) return;
 #pragma unroll 2
     for (int kp0 = 0; kp0 < TB; kp0 += EPS) {
-        float vr[EPS], vi[EPS], nv[EPS];
+        float vr[EPS], vi[EPS];
 #pragma unroll
         for (int u = 0; u < EPS; ++u) {
             vr[u] = reinterpret_cast<const float*>(sCr + (kp0 + u) * T2_CROW)[j];
             vi[u] = reinterpret_cast<const float*>(sCi + (kp0 + u) * T2_CROW)[j];
-            nv[u] = -vi[u];
         }
         pack2_seg<KIND>(pk, 2 * T2_BN, j, kp0, vr, true);
-        pack2_seg<KIND>(pk, 2 * T2_BN, j, TB + kp0, nv, true);
         pack2_seg<KIND>(pk, 2 * T2_BN, T2_BN + j, kp0, vi, true);
-        pack2_seg<KIND>(pk, 2 * T2_BN, T2_BN + j, TB + kp0, vr, true);
     }
 }
 
@@ -238,36 +281,29 @@ __device__ __forceinline__ void tc2_tile_body(int mp, int r0, int c0, float* __r
         }
     }
     if (threadIdx.x == 0) {
-        auto load_chunk = [&](int c) {
+        auto load_chunk = [&](int c) {  // main-loop step c: A' re, A' im, B' chunks
             const int s = c % NS;
+            const int kc = Cfg::re_chunk(c);
             unsigned char* sa = sStage + s * Cfg::STAGE;
             tc::mbar_arrive_expect_tx(&bar_full[s], Cfg::STAGE);
-            tc::bulk_g2s(sa, ga + (size_t)c * Cfg::A_CHUNK, Cfg::A_CHUNK, &bar_full[s]);
-            tc::bulk_g2s(sa + Cfg::A_CHUNK, gb + (size_t)c * Cfg::B_CHUNK, Cfg::B_CHUNK, &bar_full[s]);
+            tc::bulk_g2s(sa, ga + (size_t)kc * Cfg::A_CHUNK, Cfg::A_CHUNK, &bar_full[s]);
+            tc::bulk_g2s(sa + Cfg::A_CHUNK, ga + (size_t)(kc + Cfg::HALF) * Cfg::A_CHUNK, Cfg::A_CHUNK, &bar_full[s]);
+            tc::bulk_g2s(sa + 2 * Cfg::A_CHUNK, gb + (size_t)c * Cfg::B_CHUNK, Cfg::B_CHUNK, &bar_full[s]);
         };
-        for (int c = 0; c < NS - 1 && c < Cfg::NCH; ++c) load_chunk(c);
+        for (int c = 0; c < NS - 1 && c < Cfg::NIT; ++c) load_chunk(c);
         bool ok = true;
-        for (int c = 0; c < Cfg::NCH && ok; ++c) {
+        for (int c = 0; c < Cfg::NIT && ok; ++c) {
             const int s = c % NS;
             if (!tc::mbar_wait(&bar_full[s], (c / NS) & 1)) {
                 ok = false;
                 break;
             }
             const uint32_t a0 = tc::smem_u32(sStage + s * Cfg::STAGE);
-            const uint32_t b0 = a0 + Cfg::A_CHUNK;
-#pragma unroll
-            for (int j = 0; j < Cfg::MMAS; ++j) {
-                const uint64_t ad = tc::smem_desc(a0 + j * 256, 128, 512);
-                const uint64_t bd = tc::smem_desc(b0 + j * 256, 128, 512);
-                if (KIND == 1)
-                    tc::mma_f16(tbase, ad, bd, Cfg::IDESC, (c > 0 || j > 0) ? 1u : 0u);
-                else
-                    tc::mma_tf32(tbase, ad, bd, Cfg::IDESC, (c > 0 || j > 0) ? 1u : 0u);
-            }
+            cplx_mma_step<KIND>(tbase, a0, a0 + Cfg::A_CHUNK, a0 + 2 * Cfg::A_CHUNK, c == 0);
             tc::mma_commit(&bar_empty[s]);
-            // refill the stage freed by chunk c-1 with chunk c + STAGES - 1
+            // refill the stage freed by step c-1 with step c + STAGES - 1
             const int nxt = c + NS - 1;
-            if (nxt < Cfg::NCH) {
+            if (nxt < Cfg::NIT) {
                 if (c >= 1) {
                     const int sp = (c - 1) % NS;
                     if (!tc::mbar_wait(&bar_empty[sp], ((c - 1) / NS) & 1)) {
@@ -335,15 +371,13 @@ __device__ __forceinline__ void tc2_tile_body(int mp, int r0, int c0, float* __r
                         pack2_seg<KIND>(pk, T2_BM, r, ch * 16 + u * EPS, dr + u * EPS, false);
                         pack2_seg<KIND>(pk, T2_BM, r, TB + ch * 16 + u * EPS, di + u * EPS, false);
                     }
-                } else if (pk) {  // U12 row r = K index: output rows j (Re) and T2_BN + j (Im)
+                } else if (pk) {  // U12 row r = K index: B' rows j (Re) and T2_BN + j (Im)
 #pragma unroll
                     for (int e = 0; e < 16; ++e) {
                         const int j = ch * 16 + e;
                         if (j < ncols) {
                             pack2_store<KIND>(pk, 2 * T2_BN, j, r, dr[e], true);
-                            pack2_store<KIND>(pk, 2 * T2_BN, j, TB + r, -di[e], true);
                             pack2_store<KIND>(pk, 2 * T2_BN, T2_BN + j, r, di[e], true);
-                            pack2_store<KIND>(pk, 2 * T2_BN, T2_BN + j, TB + r, dr[e], true);
                         }
                     }
                 }
@@ -393,20 +427,21 @@ __device__ __forceinline__ void tc2_tile_body(int mp, int r0, int c0, float* __r
 // ---------------------------------------------------------------------------
 // Row-pair tile for the interior of the trailing update: two vertically adjacent
 // 128 x 128 complex tiles (rows r0 .. r0 + 256, columns c0 .. c0 + 128) share each
-// B' chunk, so a CTA brings 2 A' + 1 B' chunk per K step into shared memory for
-// two tiles of output (256 KB of operands per 128 x 128 tile instead of 384 KB; the
-// operand stream through L2 is what bounds the single-tile kernel).  Two MMAs per
-// K step (M = 128 each, N = 256) into two accumulators of 256 TMEM columns.  The
+// B' chunk, so a CTA brings the A' chunks of both tiles and one B' chunk per K step
+// into shared memory (192 KB of operands per 128 x 128 tile instead of 256 KB; the
+// operand stream through L2 is what bounds the single-tile kernel).  The MMAs of a
+// K step go into two accumulators of 256 TMEM columns.  The
 // epilogue runs half by half: C rows staged in the freed operand ring with bulk
 // copies, D subtracted, rows written back with bulk copies; the second half reuses
 // the ring once the first half's stores have read it.  A missing second half (odd
 // tile count) is neither loaded nor computed.  Every wait is bounded.
 // ---------------------------------------------------------------------------
-constexpr int T2P_STAGES = 6;
+constexpr int T2P_STAGES = 4;
 
 template <int KIND>
 struct Tc2p {
-    static constexpr int STAGE = 2 * Tc2<KIND>::A_CHUNK + Tc2<KIND>::B_CHUNK;
+    static constexpr int STAGE = 4 * Tc2<KIND>::A_CHUNK + Tc2<KIND>::B_CHUNK;  // A0 re, im | A1 re, im | B'
+    static_assert(T2P_STAGES * STAGE <= 227 * 1024, "ring must fit one CTA");
     static constexpr int SMEM = T2P_STAGES * STAGE;
     static_assert(SMEM >= 2 * T2_C_BYTES, "a half tile of C must fit the freed operand ring");
 };
@@ -437,7 +472,7 @@ __device__ __forceinline__ void tc2_pair_body(int mp, int r0, int c0, bool two, 
     const int nrow1 = two ? min(T2_BM, mp - r0 - T2_BM) : 0;
     float* gre = re_plane;
     float* gim = re_plane + (size_t)mp * mp;
-    const uint32_t stage_tx = (uint32_t)((two ? 2 : 1) * Cfg::A_CHUNK + Cfg::B_CHUNK);
+    const uint32_t stage_tx = (uint32_t)((two ? 4 : 2) * Cfg::A_CHUNK + Cfg::B_CHUNK);
 
     if (warp == 0) tc::tmem_alloc(&tmem_base, 512);
     if (threadIdx.x == 0) {
@@ -466,45 +501,35 @@ __device__ __forceinline__ void tc2_pair_body(int mp, int r0, int c0, bool two, 
         }
     }
     if (threadIdx.x == 0) {
-        auto load_chunk = [&](int c) {
+        auto load_chunk = [&](int c) {  // main-loop step c
             const int st = c % NS;
+            const int kc = Cfg::re_chunk(c);
+            const size_t ka = (size_t)kc * Cfg::A_CHUNK, kai = (size_t)(kc + Cfg::HALF) * Cfg::A_CHUNK;
             unsigned char* sa = smem + st * Pc::STAGE;
             tc::mbar_arrive_expect_tx(&bar_full[st], stage_tx);
-            tc::bulk_g2s(sa, ga0 + (size_t)c * Cfg::A_CHUNK, Cfg::A_CHUNK, &bar_full[st]);
-            if (two) tc::bulk_g2s(sa + Cfg::A_CHUNK, ga1 + (size_t)c * Cfg::A_CHUNK, Cfg::A_CHUNK, &bar_full[st]);
-            tc::bulk_g2s(sa + 2 * Cfg::A_CHUNK, gb + (size_t)c * Cfg::B_CHUNK, Cfg::B_CHUNK, &bar_full[st]);
+            tc::bulk_g2s(sa, ga0 + ka, Cfg::A_CHUNK, &bar_full[st]);
+            tc::bulk_g2s(sa + Cfg::A_CHUNK, ga0 + kai, Cfg::A_CHUNK, &bar_full[st]);
+            if (two) {
+                tc::bulk_g2s(sa + 2 * Cfg::A_CHUNK, ga1 + ka, Cfg::A_CHUNK, &bar_full[st]);
+                tc::bulk_g2s(sa + 3 * Cfg::A_CHUNK, ga1 + kai, Cfg::A_CHUNK, &bar_full[st]);
+            }
+            tc::bulk_g2s(sa + 4 * Cfg::A_CHUNK, gb + (size_t)c * Cfg::B_CHUNK, Cfg::B_CHUNK, &bar_full[st]);
         };
-        for (int c = 0; c < NS - 1 && c < Cfg::NCH; ++c) load_chunk(c);
+        for (int c = 0; c < NS - 1 && c < Cfg::NIT; ++c) load_chunk(c);
         bool ok = true;
-        for (int c = 0; c < Cfg::NCH && ok; ++c) {
+        for (int c = 0; c < Cfg::NIT && ok; ++c) {
             const int st = c % NS;
             if (!tc::mbar_wait(&bar_full[st], (c / NS) & 1)) {
                 ok = false;
                 break;
             }
             const uint32_t a0 = tc::smem_u32(smem + st * Pc::STAGE);
-            const uint32_t a1 = a0 + Cfg::A_CHUNK;
-            const uint32_t b0 = a0 + 2 * Cfg::A_CHUNK;
-#pragma unroll
-            for (int j = 0; j < Cfg::MMAS; ++j) {
-                const uint64_t bd = tc::smem_desc(b0 + j * 256, 128, 512);
-                const uint64_t ad0 = tc::smem_desc(a0 + j * 256, 128, 512);
-                const uint32_t acc = (c > 0 || j > 0) ? 1u : 0u;
-                if (KIND == 1)
-                    tc::mma_f16(tbase, ad0, bd, Cfg::IDESC, acc);
-                else
-                    tc::mma_tf32(tbase, ad0, bd, Cfg::IDESC, acc);
-                if (two) {
-                    const uint64_t ad1 = tc::smem_desc(a1 + j * 256, 128, 512);
-                    if (KIND == 1)
-                        tc::mma_f16(tbase + 2u * T2_BN, ad1, bd, Cfg::IDESC, acc);
-                    else
-                        tc::mma_tf32(tbase + 2u * T2_BN, ad1, bd, Cfg::IDESC, acc);
-                }
-            }
+            const uint32_t b0 = a0 + 4 * Cfg::A_CHUNK;
+            cplx_mma_step<KIND>(tbase, a0, a0 + Cfg::A_CHUNK, b0, c == 0);
+            if (two) cplx_mma_step<KIND>(tbase + 2u * T2_BN, a0 + 2 * Cfg::A_CHUNK, a0 + 3 * Cfg::A_CHUNK, b0, c == 0);
             tc::mma_commit(&bar_empty[st]);
             const int nxt = c + NS - 1;
-            if (nxt < Cfg::NCH) {
+            if (nxt < Cfg::NIT) {
                 if (c >= 1) {
                     const int sp = (c - 1) % NS;
                     if (!tc::mbar_wait(&bar_empty[sp], ((c - 1) / NS) & 1)) {

@@ -4,9 +4,10 @@
 //
 // One CTA takes up to WQ consecutive 128 x 128 complex tiles of one Strang block
 // (same layout and packed operands as tc2_tile_body in lu_tc2.cuh) with 256 threads:
-//   warp 0 (lane 0)  producer: K-chunks of A' and B' into a ring of W_STAGES stages
-//                    (bulk copies, full / empty mbarriers);
-//   warp 1 (lane 0)  MMA issuer: 2 MMAs per chunk (M = 128, N = 256) into one of two
+//   warp 0 (lane 0)  producer: the A' (real and imaginary K part) and B' chunks of
+//                    each K step into a ring of W_STAGES stages (bulk copies, full /
+//                    empty mbarriers);
+//   warp 1 (lane 0)  MMA issuer: the complex K step of lu_tc2.cuh into one of two
 //                    TMEM accumulators (512 columns), alternating by tile, so that the
 //                    MMAs of tile q + 1 do not wait for the epilogue of tile q;
 //   warps 4..7       epilogue, one TMEM lane quadrant each (thread = tile row): the C
@@ -25,7 +26,7 @@
 
 namespace fde {
 
-constexpr int W_STAGES = 6;
+constexpr int W_STAGES = 4;
 constexpr int WQ = 4;                    // tiles per CTA
 constexpr int W_CROW = 64 * 4 + 16;      // bytes per staged half-row (64 floats + pad)
 constexpr int W_CHALF = T2_BM * W_CROW;  // one plane of a staged half tile
@@ -33,7 +34,7 @@ constexpr int W_THREADS = 256;
 
 template <int KIND>
 struct Tc2w {
-    static constexpr int STAGE = Tc2<KIND>::A_CHUNK + Tc2<KIND>::B_CHUNK;
+    static constexpr int STAGE = Tc2<KIND>::STAGE;  // A' re, A' im, B' chunk of one main-loop step
     static constexpr int RING = W_STAGES * STAGE;
     static constexpr int SMEM = RING + 2 * W_CHALF;
     static_assert(SMEM <= 227 * 1024, "ring + staged C half must fit one CTA");
@@ -126,16 +127,19 @@ __device__ __forceinline__ void tc2w_body(int mp, int R0, int ni, int x0, int nq
                 tile_rc(q, r0, c0, ti, tj);
                 const unsigned char* ga = apack + (size_t)ti * Cfg::A_TILE;
                 const unsigned char* gb = bpack + (size_t)tj * Cfg::B_TILE;
-                for (int c = 0; c < Cfg::NCH && !abort_flag; ++c) {
+                for (int c = 0; c < Cfg::NIT && !abort_flag; ++c) {
                     const int s = (int)(g % NS);
                     if (g >= NS && !tc::mbar_wait(&empty[s], (uint32_t)((g / NS - 1) & 1))) {
                         fail(1);
                         break;
                     }
+                    const int kc = Cfg::re_chunk(c);
                     unsigned char* sa = ring + s * Wc::STAGE;
                     tc::mbar_arrive_expect_tx(&full[s], Wc::STAGE);
-                    tc::bulk_g2s(sa, ga + (size_t)c * Cfg::A_CHUNK, Cfg::A_CHUNK, &full[s]);
-                    tc::bulk_g2s(sa + Cfg::A_CHUNK, gb + (size_t)c * Cfg::B_CHUNK, Cfg::B_CHUNK, &full[s]);
+                    tc::bulk_g2s(sa, ga + (size_t)kc * Cfg::A_CHUNK, Cfg::A_CHUNK, &full[s]);
+                    tc::bulk_g2s(sa + Cfg::A_CHUNK, ga + (size_t)(kc + Cfg::HALF) * Cfg::A_CHUNK, Cfg::A_CHUNK,
+                                 &full[s]);
+                    tc::bulk_g2s(sa + 2 * Cfg::A_CHUNK, gb + (size_t)c * Cfg::B_CHUNK, Cfg::B_CHUNK, &full[s]);
                     n_issued = ++g;
                 }
             }
@@ -151,7 +155,7 @@ __device__ __forceinline__ void tc2w_body(int mp, int R0, int ni, int x0, int nq
                 }
                 tc::fence_after_sync();
                 const uint32_t tacc = tbase + (uint32_t)a * 2u * T2_BN;
-                for (int c = 0; c < Cfg::NCH; ++c) {
+                for (int c = 0; c < Cfg::NIT; ++c) {
                     const int s = (int)(g % NS);
                     if (abort_flag || !tc::mbar_wait(&full[s], (uint32_t)((g / NS) & 1))) {
                         fail(1);
@@ -160,16 +164,7 @@ __device__ __forceinline__ void tc2w_body(int mp, int R0, int ni, int x0, int nq
                     n_taken = ++g;
                     tc::fence_after_sync();
                     const uint32_t a0 = tc::smem_u32(ring + s * Wc::STAGE);
-                    const uint32_t b0 = a0 + Cfg::A_CHUNK;
-#pragma unroll
-                    for (int j = 0; j < Cfg::MMAS; ++j) {
-                        const uint64_t ad = tc::smem_desc(a0 + j * 256, 128, 512);
-                        const uint64_t bd = tc::smem_desc(b0 + j * 256, 128, 512);
-                        if (KIND == 1)
-                            tc::mma_f16(tacc, ad, bd, Cfg::IDESC, (c > 0 || j > 0) ? 1u : 0u);
-                        else
-                            tc::mma_tf32(tacc, ad, bd, Cfg::IDESC, (c > 0 || j > 0) ? 1u : 0u);
-                    }
+                    cplx_mma_step<KIND>(tacc, a0, a0 + Cfg::A_CHUNK, a0 + 2 * Cfg::A_CHUNK, c == 0);
                     tc::mma_commit(&empty[s]);
                 }
                 if (abort_flag) break;
