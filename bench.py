@@ -100,6 +100,8 @@ def parse():
                          "example41: every row of Tables 1-2 with the columns I, S, S^(2), S~^(2); "
                          "rhs: --rhs right-hand sides of the scale operator sharing one factorisation")
     ap.add_argument("--rhs", type=int, default=16, help="rhs: number of right-hand sides")
+    ap.add_argument("--block-solver", default="auto", choices=["auto", "cuda_cores", "tensor_cores"],
+                    help="rhs: block solves of the shared operator")
     ap.add_argument("--train", type=int, default=4096, help="learned: method-generated training solves")
     ap.add_argument("--epochs", type=int, default=40, help="learned: passes over the training set")
     ap.add_argument("--eval", type=int, default=32, help="learned: held-out instances")
@@ -541,35 +543,49 @@ def bench_many_rhs(args, world, rank, local_rank):
     probs = fde_inputs.config_many_rhs(count=count, m=args.m, s=args.s)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     outs = [torch.empty(p.n, dtype=torch.float64, device="cuda") for p in probs]
-    b = fde.FDEBatch(probs, device_inputs=True).share_operator()
 
-    def step():
-        b.assemble().factor(args.precision)
-        _, st = b.solve(tol=args.tol, restart=args.restart, maxit=400, outs=outs)
-        return st
+    def timed(solver, steps, warmup, sample_clocks):
+        b = fde.FDEBatch(probs, device_inputs=True).share_operator().block_solver(solver)
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    sampler = ClockSampler(local_rank)
-    if not args.no_clocks:
-        sampler.start()
-    l0 = fde.fde_launch_count()
-    times, stats = [], None
-    for _ in range(args.steps):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        stats = step()
-        e1.record()
-        e1.synchronize()
-        times.append(e0.elapsed_time(e1))
-    launches = fde.fde_launch_count() - l0
-    clocks = sampler.stop() if not args.no_clocks else None
-    b.close()
-    ms = sum(times) / len(times)
+        def step():
+            b.assemble().factor(args.precision)
+            _, st = b.solve(tol=args.tol, restart=args.restart, maxit=400, outs=outs)
+            return st
+
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        sampler = ClockSampler(local_rank)
+        if sample_clocks:
+            sampler.start()
+        l0 = fde.fde_launch_count()
+        times, stats = [], None
+        for _ in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            stats = step()
+            e1.record()
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        launches = fde.fde_launch_count() - l0
+        clocks = sampler.stop() if sample_clocks else None
+        b.close()
+        return sum(times) / len(times), stats, launches, clocks
+
+    ms, stats, launches, clocks = timed(args.block_solver, args.steps, args.warmup, not args.no_clocks)
     value = world * count / (ms / 1e3)
+    other = {}
+    for solver in ("cuda_cores", "tensor_cores"):  # the block solvers side by side (a short run each)
+        if solver == args.block_solver:
+            continue
+        try:
+            oms, ost, _, _ = timed(solver, min(args.steps, 2), 1, False)
+            other[solver] = {"value": world * count / (oms / 1e3), "unit": "solves/s", "ms_per_step": oms,
+                             "iterations": [st["iterations"] for st in ost]}
+        except fde.FdeError as e:
+            other[solver] = {"unavailable": str(e)}
     # the same right-hand sides one at a time through the single-problem API (own factors each)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -595,11 +611,13 @@ def bench_many_rhs(args, world, rank, local_rank):
                 "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
                 "config": {"workload": f"many_rhs{count}_m{args.m}_s{args.s}_gbdf5_alpha1.8_variable_d",
                            "right_hand_sides": count, "m": args.m, "s": args.s, "precision": args.precision,
+                           "block_solver": args.block_solver,
                            "tol_true_residual": args.tol, "restart": args.restart,
                            "l2": "flushed (512 MiB write) before every timed step; factors (4.3 GB) exceed L2"},
                 "roofline": None, "gpu_launches": launches, "clocks": clocks,
                 "iterations": [st["iterations"] for st in stats],
                 "sequential_single_api": {"value": count / seq_s, "unit": "solves/s", "seconds": seq_s},
+                "other_block_solvers": other,
                 "worst_rel_residual_oracle_matvec_first4": worst}
         print(json.dumps(line))
 

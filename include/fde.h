@@ -227,13 +227,34 @@ int fde_batch_solve(fde_batch* b, const fde_pgmres_opts* opts, double* const* x_
  * interval, BVM scheme and coefficients d+, d- equal; only u0 and f differ): many
  * right-hand sides of one problem.  fde_batch_factor then factors the Strang blocks
  * once (instance 0, through strang_precond_factor) and the block solves of every
- * Arnoldi step take the right-hand sides in groups of eight per CTA (one CTA per
- * Strang block and group), so each factor plane is streamed from HBM once per group
- * instead of once per right-hand side.  Call after
+ * Arnoldi step take the right-hand sides in groups per CTA (one CTA per Strang block
+ * and group; fde_batch_block_solver), so each factor plane is streamed from HBM once
+ * per group instead of once per right-hand side.  Call after
  * fde_batch_create and before fde_batch_factor.  Errors: FDE_ERR_ARG (an instance has
  * another operator), FDE_ERR_STATE, FDE_ERR_CUDA.  (The paper solves one right-hand
  * side; the factors depend on J, A and B only, Sec. 3.2.) */
 int fde_batch_share_operator(fde_batch* b);
+
+/* Block solves of a shared-operator batch (Sec. 3.2: every right-hand side reuses the
+ * factors of the s/2+1 Strang blocks).
+ *   FDE_BLOCK_SOLVE_CUDA_CORES    groups of 8 right-hand sides per CTA, FP32 arithmetic
+ *                                 on CUDA cores with the FP32 factors.
+ *   FDE_BLOCK_SOLVE_TENSOR_CORES  groups of 16 per CTA as tcgen05 products in TF32, in
+ *                                 strips of 128 rows: the off-diagonal blocks of L and U
+ *                                 from the factor planes, the diagonal blocks through
+ *                                 their inverses kept by the tensor-core LU (extra
+ *                                 device memory: (s/2+1) m_p^2 x 16 bytes).  Needs
+ *                                 FDE_TF32 factors and 256 <= m_p <= 2048.
+ *   FDE_BLOCK_SOLVE_AUTO          (default) tensor cores where they apply, else CUDA cores.
+ * The TF32 products make the preconditioner coarser than the FP32 block solves, which
+ * may cost an iteration; the solution is held to the same true FP64 residual.  Call
+ * after fde_batch_share_operator and before fde_batch_factor (the choice is taken at
+ * the factorisation).  Errors: FDE_ERR_ARG (unknown solver; tensor cores requested
+ * where they do not apply: reported by fde_batch_factor), FDE_ERR_STATE. */
+#define FDE_BLOCK_SOLVE_AUTO 0
+#define FDE_BLOCK_SOLVE_CUDA_CORES 1
+#define FDE_BLOCK_SOLVE_TENSOR_CORES 2
+int fde_batch_block_solver(fde_batch* b, int solver);
 
 /* Number of instances, and the problem handle of instance i (owned by the
  * batch; usable with the step-level entry points; NULL if out of range). */

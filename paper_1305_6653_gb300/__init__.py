@@ -343,6 +343,12 @@ class FDEBatch:
         _lib.check(_lib.load().fde_batch_share_operator(self.h), "fde_batch_share_operator")
         return self
 
+    def block_solver(self, kind="auto"):
+        """Block solves of a shared-operator batch: "cuda_cores" (FP32, groups of 8),
+        "tensor_cores" (TF32 tcgen05 products, groups of 16) or "auto"; before factor()."""
+        _lib.check(_lib.load().fde_batch_block_solver(self.h, _lib.BLOCK_SOLVERS[kind]), "fde_batch_block_solver")
+        return self
+
     def assemble(self):
         _lib.check(_lib.load().fde_batch_assemble(self.h), "fde_batch_assemble")
         return self

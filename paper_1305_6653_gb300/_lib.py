@@ -38,7 +38,8 @@ EXPORTED = [
     "fde_last_error", "fde_matvec", "fde_matvec_fp32", "fde_precond_apply", "fde_get_rhs", "fde_get_factor_block",
     "fde_get_grunwald", "fde_problem_sizes", "fde_profile_enable", "fde_profile_select", "fde_profile_read", "fde_launch_count",
     "fde_release_cached_memory", "fde_tune_set", "fde_tune_cache", "fde_tune_query",
-    "fde_precond_apply_noalloc", "fde_batch_create", "fde_batch_share_operator", "fde_batch_assemble",
+    "fde_precond_apply_noalloc", "fde_batch_create", "fde_batch_share_operator", "fde_batch_block_solver",
+    "fde_batch_assemble",
     "fde_batch_factor",
     "fde_batch_solve", "fde_batch_size", "fde_batch_problem", "fde_batch_destroy",
     "fde_nop_create", "fde_nop_num_params", "fde_nop_in_channels", "fde_nop_set_params", "fde_nop_get_params",
@@ -46,6 +47,7 @@ EXPORTED = [
     "fde_nop_destroy", "fde_nop_coefficients", "fde_nop_synthesize",
 ]
 FDE_TUNE_MATVEC, FDE_TUNE_TRSV, FDE_TUNE_LU = 0, 1, 2
+BLOCK_SOLVERS = {"auto": 0, "cuda_cores": 1, "tensor_cores": 2}
 STAGES = ["assemble", "form", "lu_diag", "lu_panel", "lu_update", "tfft_fwd", "trsv", "tfft_inv", "matvec",
           "krylov", "lu_tc", "lu_pack", "lu_panel_tc"]
 
@@ -124,6 +126,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "fde_batch_assemble": (i32, [vp]),
         "fde_batch_factor": (i32, [vp, i32]),
         "fde_batch_share_operator": (i32, [vp]),
+        "fde_batch_block_solver": (i32, [vp, i32]),
         "fde_batch_solve": (i32, [vp, C.POINTER(FdePgmresOpts), C.POINTER(vp), C.POINTER(FdeStats)]),
         "fde_batch_size": (i32, [vp]),
         "fde_batch_problem": (vp, [vp, i32]),

@@ -51,6 +51,8 @@ struct fde_batch {
     // frequency-side vectors
     bool shared = false;
     void* d_rhat_shared = nullptr;  // count * nblk * mp complex FP32
+    int block_solver = FDE_BLOCK_SOLVE_AUTO;  // fde_batch_block_solver
+    bool trsm_tc = false;                     // the factorisation kept what the tensor-core block solves need
     // batched GMRES: per-instance control words (InstDev::ctl, 4 ints each) and their
     // host copy; restart cycles captured as CUDA graphs, keyed by the cycle's shape
     int* d_ctl = nullptr;
@@ -90,7 +92,10 @@ int cycle_launches(fde_batch* b, int nr, const fde_pgmres_opts& o, cudaStream_t 
     for (int j = 0; j < o.restart; ++j) {
         if ((rc = launch_time_fft_batched(b->d_inst, b->d_act, nr, b->max_mp, b->max_s, j, st))) return rc;
         // shared operator: groups of right-hand sides per CTA, each factor plane streamed once per group
-        if (b->shared)
+        if (b->shared && b->trsm_tc) {
+            const Problem& P0 = *problem_of(b->probs[0]);
+            rc = launch_trsm_tc(b->d_inst, b->d_act, nr, P0.d_fac, P0.d_dtile, P0.mp, P0.nblk, b->d_err, st);
+        } else if (b->shared)
             rc = launch_trsv_multi(b->d_inst, b->d_act, nr, b->max_nblk, b->max_mp, st);
         else
             rc = launch_trsv_batched(b->d_inst, b->d_act, nr, b->max_nblk, b->max_mp, st);
@@ -235,6 +240,16 @@ int fde_batch_share_operator(fde_batch* b) {
     return FDE_OK;
 }
 
+int fde_batch_block_solver(fde_batch* b, int solver) {
+    if (!b) return set_error(FDE_ERR_ARG, "NULL batch");
+    if (solver != FDE_BLOCK_SOLVE_AUTO && solver != FDE_BLOCK_SOLVE_CUDA_CORES &&
+        solver != FDE_BLOCK_SOLVE_TENSOR_CORES)
+        return set_error(FDE_ERR_ARG, "unknown block solver");
+    if (b->factored) return set_error(FDE_ERR_STATE, "fde_batch_block_solver must run before fde_batch_factor");
+    b->block_solver = solver;
+    return FDE_OK;
+}
+
 int fde_batch_size(const fde_batch* b) { return b ? (int)b->probs.size() : 0; }
 
 fde_problem* fde_batch_problem(fde_batch* b, int i) {
@@ -258,10 +273,20 @@ int fde_batch_factor(fde_batch* b, int precision) {
     if (precision != FDE_FP32 && precision != FDE_TF32 && precision != FDE_BF16 && precision != FDE_TF32X3)
         return set_error(FDE_ERR_ARG, "batched factorisation supports FDE_FP32, FDE_TF32, FDE_BF16 and FDE_TF32X3");
     if (b->shared) {
-        // one factorisation (the single-problem path: look-ahead tensor-core LU), used by all
+        // one factorisation (the single-problem path: look-ahead tensor-core LU), used by all;
+        // for the tensor-core block solves it also keeps the inverted diagonal blocks
+        Problem& P0w = *problem_of(b->probs[0]);
+        const bool tc = b->shared && b->block_solver != FDE_BLOCK_SOLVE_CUDA_CORES && precision == FDE_TF32 &&
+                        trsm_tc_supported(P0w.mp);
+        if (b->block_solver == FDE_BLOCK_SOLVE_TENSOR_CORES && !tc)
+            return set_error(FDE_ERR_ARG, "tensor-core block solves need FDE_TF32 factors and 256 <= m_p <= 2048");
+        P0w.save_dtile = tc;
+        b->trsm_tc = false;
         int rc = strang_precond_factor(b->probs[0], precision);
+        P0w.save_dtile = false;
         if (rc) return rc;
-        const Problem& P0 = *problem_of(b->probs[0]);
+        b->trsm_tc = tc && P0w.d_dtile != nullptr;
+        const Problem& P0 = P0w;
         const size_t per = (size_t)P0.nblk * P0.mp * 2 * sizeof(float);
         if (!b->d_rhat_shared) FDE_CUDA_TRY(cudaMalloc(&b->d_rhat_shared, per * b->probs.size()));
         FDE_CUDA_TRY(cudaMemsetAsync(b->d_rhat_shared, 0, per * b->probs.size(), b->stream));
@@ -408,6 +433,7 @@ int fde_batch_solve(fde_batch* b, const fde_pgmres_opts* opts, double* const* x_
         FDE_CUDA_TRY(cudaMemsetAsync(xd, 0, P.n * sizeof(double), st));
     }
     FDE_CUDA_TRY(cudaMemcpyAsync(b->d_inst, inst.data(), n * sizeof(InstDev), cudaMemcpyHostToDevice, st));
+    FDE_CUDA_TRY(cudaMemsetAsync(b->d_err, 0, sizeof(int), st));  // bounded waits of the block solves
     const int ldh = o.restart + 1;
     std::vector<int> all(n);
     std::iota(all.begin(), all.end(), 0);
@@ -499,12 +525,15 @@ int fde_batch_solve(fde_batch* b, const fde_pgmres_opts* opts, double* const* x_
         if (!P.device_ptrs)
             FDE_CUDA_TRY(cudaMemcpyAsync(x_out[i], P.d_xsol, P.n * sizeof(double), cudaMemcpyDeviceToHost, st));
     }
+    int derr = 0;
+    FDE_CUDA_TRY(cudaMemcpyAsync(&derr, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
     FDE_CUDA_TRY(cudaEventRecord(ev1, st));
     FDE_CUDA_TRY(cudaEventSynchronize(ev1));
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ev0, ev1);
     cudaEventDestroy(ev0);
     cudaEventDestroy(ev1);
+    if (derr) return set_error(FDE_ERR_TIMEOUT, "a bounded wait of the block solves timed out");
     int worst = FDE_OK;
     for (int i = 0; i < n; ++i) {
         if (stats) {

@@ -201,6 +201,12 @@ struct Problem {
     size_t tinv_bytes = 0;
     void* d_pack = nullptr;     // packed tensor-core operand tiles of the LU panels
     size_t pack_bytes = 0;
+    // inverted 128 x 128 diagonal blocks of L and U, packed as TF32 A' operand tiles,
+    // one pair per 128-row strip of every Strang block (the tensor-core block solves of
+    // a shared-operator batch); written by the TF32 tensor-core LU when save_dtile is set
+    void* d_dtile = nullptr;
+    size_t dtile_bytes = 0;
+    bool save_dtile = false;
     // Strang-type BCCB preconditioner (bccb_precond_setup): the spectra K_k of the
     // circulant inverses, k = 0..s/2, length L each, and its frequency-side vectors
     int precond = 0;            // FDE_PRECOND_STRANG or FDE_PRECOND_BCCB / FDE_PRECOND_BCCB_MODIFIED
@@ -312,6 +318,11 @@ int launch_trsv_batched(const InstDev* I, const int* act, int nact, int max_nblk
 // diagonal tiles): groups of 8 right-hand sides per CTA, each factor plane streamed once
 // per group
 int launch_trsv_multi(const InstDev* I, const int* act, int nact, int nblk, int mp, cudaStream_t st);
+// trsm.cu: tensor-core block solves of a shared-operator batch (groups of 16 right-hand
+// sides; TF32 factors with the inverted 128 x 128 diagonal blocks kept by the LU)
+bool trsm_tc_supported(int mp);
+int launch_trsm_tc(const InstDev* I, const int* act, int nact, const void* fac, const void* dtile, int mp, int nblk,
+                   int* err, cudaStream_t st);
 int launch_time_fft_batched(const InstDev* I, const int* act, int nact, int max_mp, int max_s, int j,
                             cudaStream_t st);
 int launch_time_ifft_batched(const InstDev* I, const int* act, int nact, int max_mp, int max_s, int j,

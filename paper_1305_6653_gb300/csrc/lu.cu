@@ -1444,10 +1444,13 @@ __device__ __noinline__ void panel_col_solve(float* Ar, float* Ai, int col, int 
 //     Y_ij = -Y_ii sum_{i<k<=j} U_ik Y_kj   (U^{-1}, j = i + d),
 //   with the original L_ik, U_ik read back from the factor just written (L2).
 // L^{-1} (unit diagonal, zeros above) is packed as the A' tile and U^{-1} (zeros
-// below) as the B' tile of the panel products (layout of lu_tc2.cuh).
+// below) as the B' tile of the panel products (layout of lu_tc2.cuh).  With psave
+// set, L^{-1} and U^{-1} are also packed as two A' tiles (row i, K' = [Re | Im] of
+// row i of the inverse) at psave, for the tensor-core block solves.
 template <int KIND>
 __device__ __forceinline__ void diag128_body(int mp, int o, float* __restrict__ re, float2* __restrict__ dk,
-                                             int* __restrict__ info, unsigned char* __restrict__ pA, bool invert) {
+                                             int* __restrict__ info, unsigned char* __restrict__ pA, bool invert,
+                                             unsigned char* __restrict__ psave = nullptr) {
     using Cfg = Tc2<KIND>;
     constexpr int LD = D128_LD;
     extern __shared__ __align__(16) float dsm[];
@@ -1770,15 +1773,33 @@ __device__ __forceinline__ void diag128_body(int mp, int o, float* __restrict__ 
         }
         pack2_seg<KIND>(pB, 2 * T2_BN, brow, kp0, v, true);
     }
+    if (psave) {
+        for (int e = t; e < TB * SEGS; e += blockDim.x) {
+            const int i = e % TB, kp0 = (e / TB) * EPS;
+            const bool imag = kp0 >= TB;
+            float vl[EPS], vu[EPS];
+#pragma unroll
+            for (int u = 0; u < EPS; ++u) {
+                const int kk = (kp0 + u) & (TB - 1);
+                const float x = imag ? Ai[i * LD + kk] : Ar[i * LD + kk];
+                vl[u] = kk < i ? x : (kk == i && !imag ? 1.f : 0.f);
+                vu[u] = kk >= i ? x : 0.f;
+            }
+            pack2_seg<KIND>(psave, T2_BM, i, kp0, vl, false);
+            pack2_seg<KIND>(psave + Cfg::A_TILE, T2_BM, i, kp0, vu, false);
+        }
+    }
 }
 
 template <int KIND>
 __global__ void __launch_bounds__(D128_THREADS)
 lu_diag128_kernel(int mp, int o, float* __restrict__ fac, float2* __restrict__ dinv, int* __restrict__ info,
-                  unsigned char* __restrict__ ipack, size_t ipack_stride, int invert) {
+                  unsigned char* __restrict__ ipack, size_t ipack_stride, int invert,
+                  unsigned char* __restrict__ dsave = nullptr, size_t dsave_stride = 0) {
     const int k = blockIdx.x;
     diag128_body<KIND>(mp, o, fac + (size_t)k * 2 * mp * mp, dinv + (size_t)k * mp, info + k,
-                       ipack ? ipack + (size_t)k * ipack_stride : nullptr, invert != 0);
+                       ipack ? ipack + (size_t)k * ipack_stride : nullptr, invert != 0,
+                       dsave ? dsave + (size_t)k * dsave_stride : nullptr);
 }
 
 // Batched: blocks with m_p > o (a prefix of the table sorted by m_p).
@@ -1944,6 +1965,25 @@ static int run_lu_tc(Problem& P, cudaStream_t st) {
     cudaStream_t sh = P.lu_hi, sl = P.lu_lo;
     // interior update kernel (FDE_TUNE_LU: 0 row pairs, 1 warp-specialized; bit-identical)
     const int interior = tune_lookup(FDE_TUNE_LU, mp, nb, P.precision, nullptr);
+    // inverted diagonal blocks kept for the tensor-core block solves (TF32, whole 128-row strips)
+    const int nst = mp / TB;
+    const size_t dtile_stride = (size_t)nst * 2 * Cfg::A_TILE;
+    unsigned char* dsave = nullptr;
+    if (KIND == 0 && P.save_dtile && mp % TB == 0 && mp > TB) {
+        const size_t dneed = (size_t)nb * dtile_stride;
+        if (P.dtile_bytes < dneed) {
+            if (P.d_dtile) {
+                FDE_CUDA_TRY(cudaStreamSynchronize(st));
+                dev_free(P.d_dtile);
+            }
+            P.d_dtile = nullptr;
+            P.dtile_bytes = 0;
+            int arc = dev_alloc(&P.d_dtile, dneed);
+            if (arc) return arc;
+            P.dtile_bytes = dneed;
+        }
+        dsave = reinterpret_cast<unsigned char*>(P.d_dtile);
+    }
     FDE_CUDA_TRY(cudaEventRecord(P.lu_ev[0], st));  // fork after the work already queued on st
     FDE_CUDA_TRY(cudaStreamWaitEvent(sh, P.lu_ev[0], 0));
     FDE_CUDA_TRY(cudaStreamWaitEvent(sl, P.lu_ev[0], 0));
@@ -1954,8 +1994,9 @@ static int run_lu_tc(Problem& P, cudaStream_t st) {
         const bool more = R0 < mp;
         {
             StageTimer t(P, FDE_STAGE_LU_DIAG, sh);
-            lu_diag128_kernel<KIND><<<nb, D128_THREADS, diag128_smem(), sh>>>(mp, o, fac, dinv, P.d_info, ipack, pi,
-                                                                              more ? 1 : 0);
+            lu_diag128_kernel<KIND><<<nb, D128_THREADS, diag128_smem(), sh>>>(
+                mp, o, fac, dinv, P.d_info, ipack, pi, (more || dsave) ? 1 : 0,
+                dsave ? dsave + (size_t)(o / TB) * 2 * Cfg::A_TILE : nullptr, dtile_stride);
             FDE_LAUNCH_CHECK("lu_diag128_kernel");
         }
         if (!more) return FDE_OK;

@@ -1,7 +1,8 @@
 """Many right-hand sides of one operator (fde_batch_share_operator): the Strang blocks
-are factored once and every right-hand side's block solves read the same factors.
-Each solution is checked against the oracle's direct solve of its own system
-(||x - x_oracle|| / ||x_oracle|| <= 1e-8)."""
+are factored once and every right-hand side's block solves read the same factors,
+either on CUDA cores (groups of 8) or as tcgen05 products (groups of 16,
+fde_batch_block_solver).  Each solution is checked against the oracle's solve of its
+own system (||x - x_oracle|| / ||x_oracle|| <= 1e-8)."""
 import numpy as np
 import pytest
 
@@ -38,13 +39,16 @@ def test_shared_factors_solve_every_right_hand_side(precision):
     assert np.linalg.norm(xs[0] - xs[4]) > 1e-3 * np.linalg.norm(xs[0])
 
 
-def test_shared_factors_two_groups_of_right_hand_sides():
-    """Ten right-hand sides: the block solves take them in CTA groups of eight, so this
-    runs a full and a short group; each solution against the oracle's direct solve."""
+@pytest.mark.parametrize("solver,count,m", [("cuda_cores", 10, 130), ("tensor_cores", 10, 250),
+                                            ("tensor_cores", 21, 250)])
+def test_shared_factors_groups_of_right_hand_sides(solver, count, m):
+    """The block solves take the right-hand sides in CTA groups (8 on CUDA cores, 16 on
+    tensor cores), so these run full and short groups (m = 250: m_p = 256, two 128-row
+    strips of the tensor-core solves); each solution against the oracle's direct solve."""
     from paper_1305_6653_gb300 import FDEBatch
-    probs = fi.config_many_rhs(count=10, m=130, s=16)
+    probs = fi.config_many_rhs(count=count, m=m, s=16)
     with FDEBatch(probs) as b:
-        b.share_operator().assemble().factor("tf32")
+        b.share_operator().block_solver(solver).assemble().factor("tf32")
         xs, stats = b.solve(tol=1e-11, restart=20, maxit=400)
         xs = [x.cpu().numpy() for x in xs]
     for pr, x, st in zip(probs, xs, stats):
@@ -53,15 +57,17 @@ def test_shared_factors_two_groups_of_right_hand_sides():
         assert np.abs(x - ref).max() <= 1e-8 * np.abs(ref).max(), pr.name
 
 
-def test_shared_factors_tensor_core_panels():
+@pytest.mark.parametrize("solver", ["cuda_cores", "tensor_cores"])
+def test_shared_factors_tensor_core_panels(solver):
     """Four right-hand sides of the benchmark operator (alpha = 1.8, d+ = 1+x, d- = 2-x,
     GBDF5) at m = 1023, s = 64: eight 128-column panels of the tensor-core LU (the
-    look-ahead path with interior row-pair updates), 33 shared Strang blocks.  Each
-    solution against the oracle's FP64 Strang FGMRES of its own system."""
+    look-ahead path with interior row-pair updates), 33 shared Strang blocks, eight
+    128-row strips of the tensor-core block solves.  Each solution against the oracle's
+    FP64 Strang FGMRES of its own system."""
     from paper_1305_6653_gb300 import FDEBatch
     probs = fi.config_many_rhs(count=4, m=1023, s=64)
     with FDEBatch(probs) as b:
-        b.share_operator().assemble().factor("tf32")
+        b.share_operator().block_solver(solver).assemble().factor("tf32")
         xs, stats = b.solve(tol=1e-11, restart=20, maxit=400)
         xs = [x.cpu().numpy() for x in xs]
     # the oracle's FGMRES with one factorisation (the operator is shared), to a true residual
@@ -89,3 +95,40 @@ def test_shared_operator_is_checked():
     with FDEBatch([a, d]) as b:
         with pytest.raises(FdeError):
             b.share_operator()
+
+
+def test_block_solvers_agree_at_the_benchmark_size():
+    """Sixteen right-hand sides of the benchmark operator at full size (m = 2047, s = 256:
+    129 Strang blocks of m_p = 2048, sixteen 128-row strips, one group of 16 on the tensor
+    cores).  Both block solvers run FGMRES to a true residual of 1e-10, which at this
+    operator puts a solution within 1e-8 of the oracle's (the full-size parity test), so
+    the two agree to 2e-8 of the solution's norm; the first tensor-core solution's true
+    residual is checked with the oracle's own matvec."""
+    from paper_1305_6653_gb300 import FDEBatch
+    probs = fi.config_many_rhs(count=16, m=2047, s=256)
+    out = {}
+    for solver in ("cuda_cores", "tensor_cores"):
+        with FDEBatch(probs, device_inputs=True) as b:
+            b.share_operator().block_solver(solver).assemble().factor("tf32")
+            xs, stats = b.solve(tol=1e-10, restart=30, maxit=300)
+            out[solver] = ([x.cpu().numpy() for x in xs], [st["iterations"] for st in stats],
+                           [st["status"] for st in stats])
+    (xc, ic, sc), (xt, it, stt) = out["cuda_cores"], out["tensor_cores"]
+    assert all(v == 0 for v in sc + stt), (sc, stt)
+    for a, c in zip(xc, xt):
+        assert np.linalg.norm(a - c) <= 2e-8 * np.linalg.norm(a), (ic, it)
+    print("iterations: cuda cores", ic, "tensor cores", it)
+    J = O.j_of(probs[0])
+    AB = O.bvm_matrices(probs[0].family, probs[0].mu, probs[0].s)
+    bb = O.reduced_rhs(probs[0], J=J)
+    assert np.linalg.norm(bb - O.matvec(probs[0], xt[0], J=J, AB=AB)) <= 2e-10 * np.linalg.norm(bb)
+
+
+def test_tensor_core_block_solves_are_checked():
+    """Tensor-core block solves need TF32 factors: asking for them with FP32 factors is an error."""
+    from paper_1305_6653_gb300 import FDEBatch, FdeError
+    probs = fi.config_many_rhs(count=2, m=130, s=16)
+    with FDEBatch(probs) as b:
+        b.share_operator().block_solver("tensor_cores").assemble()
+        with pytest.raises(FdeError):
+            b.factor("fp32")
