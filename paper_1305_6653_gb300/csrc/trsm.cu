@@ -284,6 +284,10 @@ block_trsm_tc_kernel(const InstDev* __restrict__ I, const int* __restrict__ act,
 #pragma unroll
         for (int j = 0; j < TRSM_R; ++j) rp[j] = rh[j];
         long acc_n = 0;
+        // right-hand side of the strip (r_d forward, y_d backward), loaded one strip ahead
+        float2 bv[TRSM_R];
+#pragma unroll
+        for (int j = 0; j < TRSM_R; ++j) bv[j] = rp[j] ? rp[j][r] : make_float2(0.f, 0.f);
         for (int g = 0; g < 2 * nst; ++g) {
             const int d = strip(g);
             const size_t row = (size_t)TRSM_ST * d + r;
@@ -306,9 +310,8 @@ block_trsm_tc_kernel(const InstDev* __restrict__ I, const int* __restrict__ act,
             // A = (r or y) - acc as the B operand of the diagonal product
 #pragma unroll
             for (int j = 0; j < TRSM_R; ++j) {
-                const float2 b = rp[j] ? rp[j][row] : make_float2(0.f, 0.f);
-                *reinterpret_cast<float*>(abuf + xoff(j, r)) = tc::to_tf32(b.x - acc[j]);
-                *reinterpret_cast<float*>(abuf + xoff(TRSM_R + j, r)) = tc::to_tf32(b.y - acc[TRSM_R + j]);
+                *reinterpret_cast<float*>(abuf + xoff(j, r)) = tc::to_tf32(bv[j].x - acc[j]);
+                *reinterpret_cast<float*>(abuf + xoff(TRSM_R + j, r)) = tc::to_tf32(bv[j].y - acc[TRSM_R + j]);
             }
             fence_async_shared();
             tc::fence_before_sync();
@@ -328,6 +331,11 @@ block_trsm_tc_kernel(const InstDev* __restrict__ I, const int* __restrict__ act,
 #pragma unroll
             for (int j = 0; j < TRSM_R; ++j)
                 if (rp[j]) rp[j][row] = make_float2(x[j], x[TRSM_R + j]);
+            if (g + 1 < 2 * nst) {  // the next strip's right-hand side (a forward strip's y was stored above)
+                const size_t nrow = (size_t)TRSM_ST * strip(g + 1) + r;
+#pragma unroll
+                for (int j = 0; j < TRSM_R; ++j) bv[j] = rp[j] ? rp[j][nrow] : make_float2(0.f, 0.f);
+            }
             if (g >= 2) {  // the X buffer of strip g - 2 is free once its column's MMAs completed
                 ok = epi_and(!abort_flag && tc::mbar_wait(&xfree[g & 1], (uint32_t)(((g - 2) >> 1) & 1)));
                 if (!ok) {
