@@ -415,14 +415,16 @@ long long fde_launch_count(void);
 #define FDE_TUNE_TRSV 1
 /* The interior trailing update of the tensor-core block LU (FDE_TF32 / FDE_BF16 /
  * FDE_TF32X3): 0 row-pair tiles, 1 warp-specialized CTAs of four tiles with two TMEM
- * accumulators (one tile's epilogue overlaps the next tile's MMAs); bit-identical.
- * Not timed automatically (a factorisation is too long to repeat at first use):
- * variant 0 unless fde_tune_set selects one. */
+ * accumulators (one tile's epilogue overlaps the next tile's MMAs), 2 warp-specialized
+ * CTAs of eight tiles whose C tiles stream through a ring of tensor-map copies (m_p a
+ * multiple of 128, else row pairs); bit-identical.  Not timed automatically (a
+ * factorisation is too long to repeat at first use): variant 2 unless fde_tune_set
+ * selects one. */
 #define FDE_TUNE_LU 2
 #define FDE_TUNE_KERNELS 3
 /* variant -1: autotune (the default); 0 .. n-1: always launch that variant.
  * Before a shape is measured the built-in default runs (block solves with FP32
- * factors: 1, the 384 x 8 shape; otherwise 0); measuring keeps the default unless
+ * factors: 1, the 384 x 8 shape; LU interior update: 2; otherwise 0); measuring keeps the default unless
  * another variant is faster by more than 2 % (median of five interleaved rounds).
  * Process-wide.  Errors: FDE_ERR_ARG. */
 int fde_tune_set(int kernel, int variant);

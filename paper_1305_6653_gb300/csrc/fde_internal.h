@@ -1,6 +1,7 @@
 // Internal declarations shared by the CUDA translation units of libfde.
 #pragma once
 
+#include <cuda.h>  // CUtensorMap
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -321,6 +322,10 @@ int launch_trsv_multi(const InstDev* I, const int* act, int nact, int nblk, int 
 // trsm.cu: tensor-core block solves of a shared-operator batch (groups of 16 right-hand
 // sides; TF32 factors with the inverted 128 x 128 diagonal blocks kept by the LU)
 bool trsm_tc_supported(int mp);
+// FP32 factor planes of nblk blocks as one 2-D tensor map (rows of m_p floats, block k's
+// Re plane from row 2 k m_p, Im plane from (2 k + 1) m_p), boxes of 128 rows x 32
+// columns, 128-byte swizzle
+int factor_tensor_map_sw128(const void* fac, int mp, int nblk, CUtensorMap* map);
 int launch_trsm_tc(const InstDev* I, const int* act, int nact, const void* fac, const void* dtile, int mp, int nblk,
                    int* err, cudaStream_t st);
 int launch_time_fft_batched(const InstDev* I, const int* act, int nact, int max_mp, int max_s, int j,

@@ -23,6 +23,7 @@
 #include "fft_device.cuh"
 #include "lu_tc2.cuh"
 #include "lu_tc2w.cuh"
+#include "lu_tc2s.cuh"
 
 namespace fde {
 
@@ -1299,6 +1300,20 @@ lu_update_tc2w_kernel(int mp, int R0, int nt, float* __restrict__ fac, const uns
                     bpack + (size_t)k * pb, err);
 }
 
+// Interior of the trailing update (ti, tj >= 1) with the C tiles streamed by tensor-map
+// copies (m_p a multiple of 128): CTA x takes tiles x S_WQ .. x S_WQ + S_WQ - 1 of the
+// (nt - 1)^2 interior tiles of block blockIdx.y.
+template <int KIND>
+__global__ void __launch_bounds__(S_THREADS, 1)
+lu_update_tc2s_kernel(int mp, int R0, int nt, const unsigned char* __restrict__ apack,
+                      const unsigned char* __restrict__ bpack, size_t pa, size_t pb, int* __restrict__ err,
+                      const __grid_constant__ CUtensorMap cmap) {
+    const int k = blockIdx.y, ni = nt - 1;
+    const int x0 = blockIdx.x * S_WQ, nq = min(S_WQ, ni * ni - x0);
+    if (nq <= 0) return;
+    tc2s_body<KIND>(mp, R0, ni, x0, nq, k, apack + (size_t)k * pa, bpack + (size_t)k * pb, err, &cmap);
+}
+
 // Batched, in row pairs over every tile of each active block: grid.x = ceil(ntg / 2) * ntg
 // covers the largest block (ntg tiles per dimension); CTA x takes tiles (2p, tj) and
 // (2p + 1, tj), p = x / ntg, tj = x % ntg.
@@ -1340,6 +1355,8 @@ static int set_tc_attrs() {
                                       Tc2p<KIND>::SMEM));
     FDE_CUDA_TRY(cudaFuncSetAttribute(lu_update_tc2w_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       Tc2w<KIND>::SMEM));
+    FDE_CUDA_TRY(cudaFuncSetAttribute(lu_update_tc2s_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      Tc2s<KIND>::SMEM));
     return FDE_OK;
 }
 
@@ -1926,9 +1943,12 @@ static int ensure_lu_streams(Problem& P) {
 // packing, panel products) and the part of each trailing update that the next
 // panel needs (its rows and columns: the cross tiles) run on a high-priority
 // stream; the interior of the trailing update runs on a low-priority stream
-// alongside the next panel's chain.  The packed L21 / U12 operands alternate
-// between two buffers by step parity, so the interior update of step o keeps
-// reading its operands while step o + 1 packs its own.
+// alongside the cross tiles and the next panel's chain.  The packed L21 / U12
+// operands alternate between two buffers by step parity, so the interior update of
+// step o keeps reading its operands while step o + 1 packs its own.  Dependencies:
+// the interior of step o waits for the panel products of step o (and, in stream
+// order, the interior of step o - 1); the cross tiles of step o wait for the
+// interior of step o - 1 (they update tiles it wrote, and pack over the buffer it reads).
 template <int KIND>
 static int run_lu_tc(Problem& P, cudaStream_t st) {
     using Cfg = Tc2<KIND>;
@@ -1963,8 +1983,14 @@ static int run_lu_tc(Problem& P, cudaStream_t st) {
                                       Cfg::SMEM_STORE));
     if ((rc = ensure_lu_streams(P))) return rc;
     cudaStream_t sh = P.lu_hi, sl = P.lu_lo;
-    // interior update kernel (FDE_TUNE_LU: 0 row pairs, 1 warp-specialized; bit-identical)
-    const int interior = tune_lookup(FDE_TUNE_LU, mp, nb, P.precision, nullptr);
+    // interior update kernel (FDE_TUNE_LU: 0 row pairs, 1 warp-specialized, 2 warp-specialized
+    // with C streamed by tensor-map copies (m_p a multiple of 128); bit-identical)
+    int interior = tune_lookup(FDE_TUNE_LU, mp, nb, P.precision, nullptr);
+    CUtensorMap cmap;
+    if (interior == 2) {
+        if (mp % TB != 0) interior = 0;
+        else if ((rc = factor_tensor_map_sw128(fac, mp, nb, &cmap))) return rc;
+    }
     // inverted diagonal blocks kept for the tensor-core block solves (TF32, whole 128-row strips)
     const int nst = mp / TB;
     const size_t dtile_stride = (size_t)nst * 2 * Cfg::A_TILE;
@@ -2031,6 +2057,10 @@ static int run_lu_tc(Problem& P, cudaStream_t st) {
         for (int o = 0; o + TB < mp; o += TB) {
             const int R0 = o + TB;
             const int nt = cdiv(mp - R0, T2_BM);
+            // the interior update of step o needs this step's packed L21 / U12 (the panel
+            // products just queued on sh), not the cross tiles below: it touches other tiles
+            // and reads other operand buffers, so it runs beside them
+            FDE_CUDA_TRY(cudaEventRecord(P.lu_ev[1], sh));
             if (o > 0) FDE_CUDA_TRY(cudaStreamWaitEvent(sh, P.lu_ev[2], 0));  // interior of step o - TB
             {  // the next panel's rows (single tiles) and the column below them (row pairs); when
                // that panel has a trailing matrix, they are packed as its operand tiles as well
@@ -2046,11 +2076,15 @@ static int run_lu_tc(Problem& P, cudaStream_t st) {
                     FDE_LAUNCH_CHECK("lu_update_tc2p_kernel");
                 }
             }
-            FDE_CUDA_TRY(cudaEventRecord(P.lu_ev[1], sh));
             FDE_CUDA_TRY(cudaStreamWaitEvent(sl, P.lu_ev[1], 0));
             if (nt > 1) {
                 StageTimer t(P, FDE_STAGE_LU_TC, sl);
-                if (interior == 1) {  // warp-specialized, two accumulators, WQ tiles per CTA
+                if (interior == 2) {  // warp-specialized, C through a ring of tensor-map copies
+                    const int tiles = (nt - 1) * (nt - 1);
+                    lu_update_tc2s_kernel<KIND><<<dim3(cdiv(tiles, S_WQ), nb), S_THREADS, Tc2s<KIND>::SMEM, sl>>>(
+                        mp, R0, nt, apk(o), bpk(o), pa, pb, P.d_err, cmap);
+                    FDE_LAUNCH_CHECK("lu_update_tc2s_kernel");
+                } else if (interior == 1) {  // warp-specialized, two accumulators, WQ tiles per CTA
                     const int tiles = (nt - 1) * (nt - 1);
                     lu_update_tc2w_kernel<KIND><<<dim3((tiles + WQ - 1) / WQ, nb), W_THREADS, Tc2w<KIND>::SMEM, sl>>>(
                         mp, R0, nt, fac, apk(o), bpk(o), pa, pb, P.d_err);

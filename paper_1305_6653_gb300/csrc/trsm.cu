@@ -372,7 +372,7 @@ block_trsm_tc_kernel(const InstDev* __restrict__ I, const int* __restrict__ act,
 
 // Factor planes of nblk blocks as a 2-D tensor map: rows of m_p floats, boxes of 128
 // rows x 32 columns with 128-byte swizzle (the K-major layout the MMAs read).
-static int trsm_tensor_map(const void* fac, int mp, int nblk, CUtensorMap* map) {
+int factor_tensor_map_sw128(const void* fac, int mp, int nblk, CUtensorMap* map) {
     using Fn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                             const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                             CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -403,7 +403,7 @@ int launch_trsm_tc(const InstDev* I, const int* act, int nact, const void* fac, 
     if (nact <= 0) return FDE_OK;
     if (!trsm_tc_supported(mp) || !dtile) return set_error(FDE_ERR_ARG, "tensor-core block solves need 256 <= m_p <= 2048, m_p % 128 == 0 and saved diagonal inverses");
     CUtensorMap map;
-    int rc = trsm_tensor_map(fac, mp, nblk, &map);
+    int rc = factor_tensor_map_sw128(fac, mp, nblk, &map);
     if (rc) return rc;
     FDE_CUDA_TRY(cudaFuncSetAttribute(block_trsm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TRSM_SMEM));
     block_trsm_tc_kernel<<<dim3((nact + TRSM_R - 1) / TRSM_R, nblk), TRSM_THREADS, TRSM_SMEM, st>>>(

@@ -59,13 +59,20 @@ void load_locked(TuneState& s) {
 }  // namespace
 
 int tune_variants(int kernel) {
-    return kernel == FDE_TUNE_MATVEC ? 3 : kernel == FDE_TUNE_TRSV ? 4 : kernel == FDE_TUNE_LU ? 2 : 0;
+    return kernel == FDE_TUNE_MATVEC ? 3 : kernel == FDE_TUNE_TRSV ? 4 : kernel == FDE_TUNE_LU ? 3 : 0;
 }
 
 // The variant used before a shape is measured (or when tuning is impossible): the
 // 384 x 8 block-solve shape for FP32 factors (never slower than 512 x 4 where both were
 // timed), the first variant otherwise.
-static int tune_default(int kernel, int prec) { return kernel == FDE_TUNE_TRSV && prec == FDE_FP32 ? 1 : 0; }
+// Built-in defaults: block solves with FP32 factors 384 x 8; the LU interior update with
+// C streamed by tensor-map copies (its kernel falls back to row pairs where m_p is not a
+// multiple of 128); everything else variant 0.
+static int tune_default(int kernel, int prec) {
+    if (kernel == FDE_TUNE_TRSV) return prec == FDE_FP32 ? 1 : 0;
+    if (kernel == FDE_TUNE_LU) return 2;
+    return 0;
+}
 
 int tune_lookup(int kernel, int mp, int nb, int prec, bool* need_tuning) {
     TuneState& s = state();

@@ -76,20 +76,25 @@ def test_autotune_records_the_shape(lib):
     assert L.fde_tune_query(_lib.FDE_TUNE_TRSV, mp, nblk, 1, C.byref(v)) == 0 and 0 <= v.value < 4
 
 
-@pytest.mark.parametrize("precision", ["tf32", "bf16", "tf32x3"])
-def test_lu_interior_variants_are_bit_identical(lib, precision):
-    """The interior trailing update of the tensor-core LU as row-pair tiles (variant 0) or
-    warp-specialized CTAs with two TMEM accumulators (variant 1): the same MMAs in the same
-    K order, so identical factors.  m = 700: several outer steps, ragged 64-wide tiles."""
+@pytest.mark.parametrize("precision,m", [("tf32", 700), ("bf16", 700), ("tf32x3", 700), ("tf32", 1000),
+                                         ("bf16", 1000), ("tf32x3", 1000)])
+def test_lu_interior_variants_are_bit_identical(lib, precision, m):
+    """The interior trailing update of the tensor-core LU as row-pair tiles (variant 0),
+    warp-specialized CTAs with two TMEM accumulators (variant 1), or the same with the C
+    tiles streamed by tensor-map copies (variant 2, m_p a multiple of 128; otherwise row
+    pairs): the same MMAs in the same K order, so identical factors.  m = 700: several
+    outer steps, ragged 64-wide tiles; m = 1000: m_p = 1024, seven interior updates of
+    full tiles (1 to 36 tiles per block)."""
     from paper_1305_6653_gb300 import FDEProblem, _lib
     L, _ = lib
-    prob = fi.manufactured(700, 16, 1.7, "GBDF3", dplus_fn=lambda x: 1 + x, dminus_fn=lambda x: 2 - x)
+    prob = fi.manufactured(m, 16, 1.7, "GBDF3", dplus_fn=lambda x: 1 + x, dminus_fn=lambda x: 2 - x)
     facs = []
-    for v in (0, 1):
+    for v in (0, 1, 2):
         L.fde_tune_set(_lib.FDE_TUNE_LU, v)
         with FDEProblem.from_inputs(prob) as p:
             p.assemble().factor(precision)
             facs.append([p.factor_block(k) for k in (0, 3, prob.s // 2)])
     L.fde_tune_set(_lib.FDE_TUNE_LU, -1)
-    for a, b in zip(facs[0], facs[1]):
-        assert np.array_equal(a, b)
+    for v in (1, 2):
+        for a, b in zip(facs[0], facs[v]):
+            assert np.array_equal(a, b), v
