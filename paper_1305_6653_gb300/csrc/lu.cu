@@ -1237,7 +1237,9 @@ template <int KIND>
 __global__ void __launch_bounds__(128)
 lu_update_tc2_kernel(int mp, int R0, int nt, int part, float* __restrict__ fac,
                      const unsigned char* __restrict__ apack, const unsigned char* __restrict__ bpack, size_t pa,
-                     size_t pb, int* __restrict__ err, unsigned char* __restrict__ bpack_next = nullptr) {
+                     size_t pb, int* __restrict__ err, unsigned char* __restrict__ bpack_next = nullptr,
+                     const unsigned char* __restrict__ apack_old = nullptr,
+                     const unsigned char* __restrict__ bpack_old = nullptr) {
     // part 0: all nt^2 tiles; 1: the cross ti = 0 or tj = 0 (2 nt - 1 tiles: the next
     // panel's rows and columns); 2: the interior ti, tj >= 1 ((nt - 1)^2 tiles); 3: the
     // row ti = 0 only (nt tiles; the column below it goes to the row-pair kernel)
@@ -1260,7 +1262,8 @@ lu_update_tc2_kernel(int mp, int R0, int nt, int part, float* __restrict__ fac,
     unsigned char* pkn = bpack_next && ti == 0 && tj >= 1
                              ? bpack_next + (size_t)k * pb + (size_t)(tj - 1) * Tc2<KIND>::B_TILE
                              : nullptr;
-    tc2_update_body<KIND>(mp, R0, fac + (size_t)k * 2 * mp * mp, apack + k * pa, bpack + k * pb, err, ti, tj, pkn);
+    tc2_update_body<KIND>(mp, R0, fac + (size_t)k * 2 * mp * mp, apack + k * pa, bpack + k * pb, err, ti, tj, pkn,
+                          apack_old ? apack_old + k * pa : nullptr, bpack_old ? bpack_old + k * pb : nullptr);
 }
 
 // Rows ti >= 1 of the trailing update in row pairs, over the columns tj0 .. tj0 + ncol - 1:
@@ -1271,7 +1274,9 @@ template <int KIND>
 __global__ void __launch_bounds__(128)
 lu_update_tc2p_kernel(int mp, int R0, int nt, int tj0, int ncol, float* __restrict__ fac,
                       const unsigned char* __restrict__ apack, const unsigned char* __restrict__ bpack, size_t pa,
-                      size_t pb, int* __restrict__ err, unsigned char* __restrict__ apack_next = nullptr) {
+                      size_t pb, int* __restrict__ err, unsigned char* __restrict__ apack_next = nullptr,
+                      const unsigned char* __restrict__ apack_old = nullptr,
+                      const unsigned char* __restrict__ bpack_old = nullptr) {
     using Cfg = Tc2<KIND>;
     const int k = blockIdx.y, x = blockIdx.x;
     const int p = x / ncol, tj = tj0 + x % ncol;
@@ -1280,11 +1285,16 @@ lu_update_tc2p_kernel(int mp, int R0, int nt, int tj0, int ncol, float* __restri
     const unsigned char* ab = apack + (size_t)k * pa;
     // the next panel's column block (tj = 0) is also packed as the next step's A' tiles ti - 1
     unsigned char* an = apack_next && tj == 0 ? apack_next + (size_t)k * pa : nullptr;
+    // the previous step's operands (merged update): tile indices one larger
+    const unsigned char* abo = apack_old ? apack_old + (size_t)k * pa : nullptr;
     tc2_pair_body<KIND>(mp, R0 + ti0 * T2_BM, R0 + tj * T2_BN, two, fac + (size_t)k * 2 * mp * mp,
                         ab + (size_t)ti0 * Cfg::A_TILE, ab + (size_t)(two ? ti0 + 1 : ti0) * Cfg::A_TILE,
                         bpack + (size_t)k * pb + (size_t)tj * Cfg::B_TILE, err,
                         an ? an + (size_t)(ti0 - 1) * Cfg::A_TILE : nullptr,
-                        an && two ? an + (size_t)ti0 * Cfg::A_TILE : nullptr);
+                        an && two ? an + (size_t)ti0 * Cfg::A_TILE : nullptr,
+                        abo ? abo + (size_t)(ti0 + 1) * Cfg::A_TILE : nullptr,
+                        abo ? abo + (size_t)((two ? ti0 + 1 : ti0) + 1) * Cfg::A_TILE : nullptr,
+                        bpack_old ? bpack_old + (size_t)k * pb + (size_t)(tj + 1) * Cfg::B_TILE : nullptr);
 }
 
 // Interior of the trailing update (ti, tj >= 1), warp-specialized: CTA x takes tiles
@@ -1300,18 +1310,26 @@ lu_update_tc2w_kernel(int mp, int R0, int nt, float* __restrict__ fac, const uns
                     bpack + (size_t)k * pb, err);
 }
 
-// Interior of the trailing update (ti, tj >= 1) with the C tiles streamed by tensor-map
-// copies (m_p a multiple of 128): CTA x takes tiles x S_WQ .. x S_WQ + S_WQ - 1 of the
-// (nt - 1)^2 interior tiles of block blockIdx.y.
+// Trailing-update tiles with the C tiles streamed by tensor-map copies (m_p a multiple
+// of 128): front = 0 -> the square ti, tj >= f ((nt - f)^2 tiles); front = 1 -> row 1 and
+// column 1 (2 nt - 3 tiles).  CTA x takes tiles x S_WQ .. x S_WQ + S_WQ - 1 of block
+// blockIdx.y.  apack_old / bpack_old: the previous step's operands (or NULL).
+static __host__ __device__ int tc2s_tiles(int nt, int f, int front) {
+    return front ? 2 * nt - 3 : (nt - f) * (nt - f);
+}
+
 template <int KIND>
 __global__ void __launch_bounds__(S_THREADS, 1)
-lu_update_tc2s_kernel(int mp, int R0, int nt, const unsigned char* __restrict__ apack,
-                      const unsigned char* __restrict__ bpack, size_t pa, size_t pb, int* __restrict__ err,
+lu_update_tc2s_kernel(int mp, int R0, int nt, int f, int front, const unsigned char* __restrict__ apack,
+                      const unsigned char* __restrict__ bpack, const unsigned char* __restrict__ apack_old,
+                      const unsigned char* __restrict__ bpack_old, size_t pa, size_t pb, int* __restrict__ err,
                       const __grid_constant__ CUtensorMap cmap) {
-    const int k = blockIdx.y, ni = nt - 1;
-    const int x0 = blockIdx.x * S_WQ, nq = min(S_WQ, ni * ni - x0);
+    const int k = blockIdx.y;
+    const int x0 = blockIdx.x * S_WQ, nq = min(S_WQ, tc2s_tiles(nt, f, front) - x0);
     if (nq <= 0) return;
-    tc2s_body<KIND>(mp, R0, ni, x0, nq, k, apack + (size_t)k * pa, bpack + (size_t)k * pb, err, &cmap);
+    tc2s_body<KIND>(mp, R0, nt, f, front, x0, nq, k, apack + (size_t)k * pa, bpack + (size_t)k * pb,
+                    apack_old ? apack_old + (size_t)k * pa : nullptr, bpack_old ? bpack_old + (size_t)k * pb : nullptr,
+                    err, &cmap);
 }
 
 // Batched, in row pairs over every tile of each active block: grid.x = ceil(ntg / 2) * ntg
@@ -1958,7 +1976,15 @@ static int run_lu_tc(Problem& P, cudaStream_t st) {
     size_t pa, pb;
     tc2_pack_sizes<KIND>(mp, &pa, &pb);
     const size_t pi = (size_t)Cfg::A_TILE + Cfg::B_TILE;  // L11^{-1} (A') and U11^{-1} (B') per block
-    const size_t need = mp > TB ? (size_t)nb * (2 * (pa + pb) + pi) : 0;
+    // interior update kernel (FDE_TUNE_LU: 0 row pairs, 1 warp-specialized, 2 C streamed by
+    // tensor-map copies with the updates of consecutive steps merged (m_p a multiple of 128))
+    int interior = tune_lookup(FDE_TUNE_LU, mp, nb, P.precision, nullptr);
+    if (interior == 2 && mp % TB != 0) interior = 0;
+    const bool merge = interior == 2;
+    // operand buffer sets, by step: two alternate; merged updates read two steps' sets
+    // while the next two steps pack theirs, so four rotate
+    const int nsets = merge ? 4 : 2;
+    const size_t need = mp > TB ? (size_t)nb * (nsets * (pa + pb) + pi) : 0;
     if (need > 0 && P.pack_bytes < need) {
         if (P.d_pack) {
             FDE_CUDA_TRY(cudaStreamSynchronize(st));
@@ -1972,9 +1998,9 @@ static int run_lu_tc(Problem& P, cudaStream_t st) {
         FDE_CUDA_TRY(cudaMemsetAsync(P.d_pack, 0, need, st));
     }
     unsigned char* base = reinterpret_cast<unsigned char*>(P.d_pack);
-    auto apk = [&](int o) { return base ? base + (size_t)((o / TB) & 1) * nb * (pa + pb) : nullptr; };
+    auto apk = [&](int o) { return base ? base + (size_t)((o / TB) % nsets) * nb * (pa + pb) : nullptr; };
     auto bpk = [&](int o) { return base ? apk(o) + (size_t)nb * pa : nullptr; };
-    unsigned char* ipack = base ? base + (size_t)2 * nb * (pa + pb) : nullptr;
+    unsigned char* ipack = base ? base + (size_t)nsets * nb * (pa + pb) : nullptr;
     int rc = set_tc_attrs<KIND>();
     if (rc) return rc;
     FDE_CUDA_TRY(cudaFuncSetAttribute(lu_diag128_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1983,14 +2009,8 @@ static int run_lu_tc(Problem& P, cudaStream_t st) {
                                       Cfg::SMEM_STORE));
     if ((rc = ensure_lu_streams(P))) return rc;
     cudaStream_t sh = P.lu_hi, sl = P.lu_lo;
-    // interior update kernel (FDE_TUNE_LU: 0 row pairs, 1 warp-specialized, 2 warp-specialized
-    // with C streamed by tensor-map copies (m_p a multiple of 128); bit-identical)
-    int interior = tune_lookup(FDE_TUNE_LU, mp, nb, P.precision, nullptr);
     CUtensorMap cmap;
-    if (interior == 2) {
-        if (mp % TB != 0) interior = 0;
-        else if ((rc = factor_tensor_map_sw128(fac, mp, nb, &cmap))) return rc;
-    }
+    if (merge && (rc = factor_tensor_map_sw128(fac, mp, nb, &cmap))) return rc;
     // inverted diagonal blocks kept for the tensor-core block solves (TF32, whole 128-row strips)
     const int nst = mp / TB;
     const size_t dtile_stride = (size_t)nst * 2 * Cfg::A_TILE;
@@ -2054,35 +2074,53 @@ static int run_lu_tc(Problem& P, cudaStream_t st) {
         }
         int r = panel(0);
         if (r) return r;
-        for (int o = 0; o + TB < mp; o += TB) {
-            const int R0 = o + TB;
+        const int nsteps = mp > TB ? cdiv(mp - TB, TB) : 0;  // outer steps with a trailing matrix
+        for (int p = 0; p < nsteps; ++p) {
+            const int o = p * TB, R0 = o + TB;
             const int nt = cdiv(mp - R0, T2_BM);
-            // the interior update of step o needs this step's packed L21 / U12 (the panel
+            // merged updates (C streamed): an even step with a successor leaves its interior to the
+            // next step, which applies both steps' products (K = 256) in one pass over C; that odd
+            // step also brings row and column 1 of its trailing matrix (the panel after next) up to
+            // date, so the even step after it needs nothing from the interior update
+            const bool a_step = merge && p % 2 == 0 && p + 1 < nsteps;
+            const bool b_step = merge && p % 2 == 1;
+            const unsigned char* ao = b_step ? apk(o - TB) : nullptr;  // the previous step's operands
+            const unsigned char* bo = b_step ? bpk(o - TB) : nullptr;
+            // the interior update of step p needs this step's packed L21 / U12 (the panel
             // products just queued on sh), not the cross tiles below: it touches other tiles
             // and reads other operand buffers, so it runs beside them
             FDE_CUDA_TRY(cudaEventRecord(P.lu_ev[1], sh));
-            if (o > 0) FDE_CUDA_TRY(cudaStreamWaitEvent(sh, P.lu_ev[2], 0));  // interior of step o - TB
+            // the cross tiles update tiles the last interior update wrote and pack over a buffer
+            // it may read (an even step of a merged pair touches neither)
+            if (p > 0 && !a_step) FDE_CUDA_TRY(cudaStreamWaitEvent(sh, P.lu_ev[2], 0));
             {  // the next panel's rows (single tiles) and the column below them (row pairs); when
                // that panel has a trailing matrix, they are packed as its operand tiles as well
                 StageTimer t(P, FDE_STAGE_LU_TC, sh);
                 const bool next = R0 + TB < mp;
                 lu_update_tc2_kernel<KIND><<<dim3(nt, nb), 128, Cfg::SMEM, sh>>>(mp, R0, nt, 3, fac, apk(o), bpk(o),
                                                                                pa, pb, P.d_err,
-                                                                               next ? bpk(R0) : nullptr);
+                                                                               next ? bpk(R0) : nullptr, ao, bo);
                 FDE_LAUNCH_CHECK("lu_update_tc2_kernel");
                 if (nt > 1) {
                     lu_update_tc2p_kernel<KIND><<<dim3((nt - 1 + 1) / 2, nb), 128, Tc2p<KIND>::SMEM, sh>>>(
-                        mp, R0, nt, 0, 1, fac, apk(o), bpk(o), pa, pb, P.d_err, next ? apk(R0) : nullptr);
+                        mp, R0, nt, 0, 1, fac, apk(o), bpk(o), pa, pb, P.d_err, next ? apk(R0) : nullptr, ao, bo);
                     FDE_LAUNCH_CHECK("lu_update_tc2p_kernel");
                 }
+                if (b_step && nt > 1) {  // row and column 1, both steps' products
+                    lu_update_tc2s_kernel<KIND>
+                        <<<dim3(cdiv(tc2s_tiles(nt, 1, 1), S_WQ), nb), S_THREADS, Tc2s<KIND>::SMEM, sh>>>(
+                            mp, R0, nt, 1, 1, apk(o), bpk(o), ao, bo, pa, pb, P.d_err, cmap);
+                    FDE_LAUNCH_CHECK("lu_update_tc2s_kernel");
+                }
             }
-            FDE_CUDA_TRY(cudaStreamWaitEvent(sl, P.lu_ev[1], 0));
-            if (nt > 1) {
+            const int f = b_step ? 2 : 1;  // first row / column of the interior update
+            if (!a_step && nt > f) {
+                FDE_CUDA_TRY(cudaStreamWaitEvent(sl, P.lu_ev[1], 0));
                 StageTimer t(P, FDE_STAGE_LU_TC, sl);
                 if (interior == 2) {  // warp-specialized, C through a ring of tensor-map copies
-                    const int tiles = (nt - 1) * (nt - 1);
-                    lu_update_tc2s_kernel<KIND><<<dim3(cdiv(tiles, S_WQ), nb), S_THREADS, Tc2s<KIND>::SMEM, sl>>>(
-                        mp, R0, nt, apk(o), bpk(o), pa, pb, P.d_err, cmap);
+                    lu_update_tc2s_kernel<KIND>
+                        <<<dim3(cdiv(tc2s_tiles(nt, f, 0), S_WQ), nb), S_THREADS, Tc2s<KIND>::SMEM, sl>>>(
+                            mp, R0, nt, f, 0, apk(o), bpk(o), ao, bo, pa, pb, P.d_err, cmap);
                     FDE_LAUNCH_CHECK("lu_update_tc2s_kernel");
                 } else if (interior == 1) {  // warp-specialized, two accumulators, WQ tiles per CTA
                     const int tiles = (nt - 1) * (nt - 1);
@@ -2094,8 +2132,8 @@ static int run_lu_tc(Problem& P, cudaStream_t st) {
                                                   sl>>>(mp, R0, nt, 1, nt - 1, fac, apk(o), bpk(o), pa, pb, P.d_err);
                     FDE_LAUNCH_CHECK("lu_update_tc2p_kernel");
                 }
+                FDE_CUDA_TRY(cudaEventRecord(P.lu_ev[2], sl));
             }
-            FDE_CUDA_TRY(cudaEventRecord(P.lu_ev[2], sl));
             if ((r = panel(R0))) return r;
         }
         return FDE_OK;

@@ -236,12 +236,19 @@ __device__ __forceinline__ void pack_staged_b(unsigned char* __restrict__ pk, co
 // The operand tile that D replaces is no longer read once the MMAs are complete.
 // Update mode with pk set packs the updated tile as a B' tile of the next outer step
 // (a tile of the next panel's row block).
+//
+// With ga_old / gb_old set (update mode), D is the sum of two rank-128 products: the
+// K steps of (ga_old, gb_old) first, then those of (ga, gb) -- the trailing updates of
+// two consecutive outer steps applied in one pass over C.
 template <int KIND, bool STORE>
 __device__ __forceinline__ void tc2_tile_body(int mp, int r0, int c0, float* __restrict__ re_plane,
                                               const unsigned char* __restrict__ ga,
                                               const unsigned char* __restrict__ gb, int* __restrict__ err,
-                                              unsigned char* __restrict__ pk = nullptr, int pk_side = 0) {
+                                              unsigned char* __restrict__ pk = nullptr, int pk_side = 0,
+                                              const unsigned char* __restrict__ ga_old = nullptr,
+                                              const unsigned char* __restrict__ gb_old = nullptr) {
     using Cfg = Tc2<KIND>;
+    const int nsteps = (ga_old ? 2 : 1) * Cfg::NIT;
     extern __shared__ __align__(1024) unsigned char smem[];
     constexpr int NS = STORE ? T2_STAGES : T2_STAGES_UPD;
     unsigned char* sStage = smem;
@@ -283,16 +290,20 @@ __device__ __forceinline__ void tc2_tile_body(int mp, int r0, int c0, float* __r
     if (threadIdx.x == 0) {
         auto load_chunk = [&](int c) {  // main-loop step c: A' re, A' im, B' chunks
             const int s = c % NS;
-            const int kc = Cfg::re_chunk(c);
+            const bool old = ga_old && c < Cfg::NIT;
+            const unsigned char* a = old ? ga_old : ga;
+            const unsigned char* b = old ? gb_old : gb;
+            const int cl = old || !ga_old ? c : c - Cfg::NIT;
+            const int kc = Cfg::re_chunk(cl);
             unsigned char* sa = sStage + s * Cfg::STAGE;
             tc::mbar_arrive_expect_tx(&bar_full[s], Cfg::STAGE);
-            tc::bulk_g2s(sa, ga + (size_t)kc * Cfg::A_CHUNK, Cfg::A_CHUNK, &bar_full[s]);
-            tc::bulk_g2s(sa + Cfg::A_CHUNK, ga + (size_t)(kc + Cfg::HALF) * Cfg::A_CHUNK, Cfg::A_CHUNK, &bar_full[s]);
-            tc::bulk_g2s(sa + 2 * Cfg::A_CHUNK, gb + (size_t)c * Cfg::B_CHUNK, Cfg::B_CHUNK, &bar_full[s]);
+            tc::bulk_g2s(sa, a + (size_t)kc * Cfg::A_CHUNK, Cfg::A_CHUNK, &bar_full[s]);
+            tc::bulk_g2s(sa + Cfg::A_CHUNK, a + (size_t)(kc + Cfg::HALF) * Cfg::A_CHUNK, Cfg::A_CHUNK, &bar_full[s]);
+            tc::bulk_g2s(sa + 2 * Cfg::A_CHUNK, b + (size_t)cl * Cfg::B_CHUNK, Cfg::B_CHUNK, &bar_full[s]);
         };
-        for (int c = 0; c < NS - 1 && c < Cfg::NIT; ++c) load_chunk(c);
+        for (int c = 0; c < NS - 1 && c < nsteps; ++c) load_chunk(c);
         bool ok = true;
-        for (int c = 0; c < Cfg::NIT && ok; ++c) {
+        for (int c = 0; c < nsteps && ok; ++c) {
             const int s = c % NS;
             if (!tc::mbar_wait(&bar_full[s], (c / NS) & 1)) {
                 ok = false;
@@ -303,7 +314,7 @@ __device__ __forceinline__ void tc2_tile_body(int mp, int r0, int c0, float* __r
             tc::mma_commit(&bar_empty[s]);
             // refill the stage freed by step c-1 with step c + STAGES - 1
             const int nxt = c + NS - 1;
-            if (nxt < Cfg::NIT) {
+            if (nxt < nsteps) {
                 if (c >= 1) {
                     const int sp = (c - 1) % NS;
                     if (!tc::mbar_wait(&bar_empty[sp], ((c - 1) / NS) & 1)) {
@@ -454,9 +465,13 @@ __device__ __forceinline__ void tc2_pair_body(int mp, int r0, int c0, bool two, 
                                               const unsigned char* __restrict__ ga1,
                                               const unsigned char* __restrict__ gb, int* __restrict__ err,
                                               unsigned char* __restrict__ pk0 = nullptr,
-                                              unsigned char* __restrict__ pk1 = nullptr) {
+                                              unsigned char* __restrict__ pk1 = nullptr,
+                                              const unsigned char* __restrict__ ga0_old = nullptr,
+                                              const unsigned char* __restrict__ ga1_old = nullptr,
+                                              const unsigned char* __restrict__ gb_old = nullptr) {
     using Cfg = Tc2<KIND>;
     using Pc = Tc2p<KIND>;
+    const int nsteps = (ga0_old ? 2 : 1) * Cfg::NIT;
     constexpr int NS = T2P_STAGES;
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* sCr = smem;
@@ -501,23 +516,28 @@ __device__ __forceinline__ void tc2_pair_body(int mp, int r0, int c0, bool two, 
         }
     }
     if (threadIdx.x == 0) {
-        auto load_chunk = [&](int c) {  // main-loop step c
+        auto load_chunk = [&](int c) {  // main-loop step c (the older operand set first, if any)
             const int st = c % NS;
-            const int kc = Cfg::re_chunk(c);
+            const bool old = ga0_old && c < Cfg::NIT;
+            const unsigned char* a0 = old ? ga0_old : ga0;
+            const unsigned char* a1 = old ? ga1_old : ga1;
+            const unsigned char* b = old ? gb_old : gb;
+            const int cl = old || !ga0_old ? c : c - Cfg::NIT;
+            const int kc = Cfg::re_chunk(cl);
             const size_t ka = (size_t)kc * Cfg::A_CHUNK, kai = (size_t)(kc + Cfg::HALF) * Cfg::A_CHUNK;
             unsigned char* sa = smem + st * Pc::STAGE;
             tc::mbar_arrive_expect_tx(&bar_full[st], stage_tx);
-            tc::bulk_g2s(sa, ga0 + ka, Cfg::A_CHUNK, &bar_full[st]);
-            tc::bulk_g2s(sa + Cfg::A_CHUNK, ga0 + kai, Cfg::A_CHUNK, &bar_full[st]);
+            tc::bulk_g2s(sa, a0 + ka, Cfg::A_CHUNK, &bar_full[st]);
+            tc::bulk_g2s(sa + Cfg::A_CHUNK, a0 + kai, Cfg::A_CHUNK, &bar_full[st]);
             if (two) {
-                tc::bulk_g2s(sa + 2 * Cfg::A_CHUNK, ga1 + ka, Cfg::A_CHUNK, &bar_full[st]);
-                tc::bulk_g2s(sa + 3 * Cfg::A_CHUNK, ga1 + kai, Cfg::A_CHUNK, &bar_full[st]);
+                tc::bulk_g2s(sa + 2 * Cfg::A_CHUNK, a1 + ka, Cfg::A_CHUNK, &bar_full[st]);
+                tc::bulk_g2s(sa + 3 * Cfg::A_CHUNK, a1 + kai, Cfg::A_CHUNK, &bar_full[st]);
             }
-            tc::bulk_g2s(sa + 4 * Cfg::A_CHUNK, gb + (size_t)c * Cfg::B_CHUNK, Cfg::B_CHUNK, &bar_full[st]);
+            tc::bulk_g2s(sa + 4 * Cfg::A_CHUNK, b + (size_t)cl * Cfg::B_CHUNK, Cfg::B_CHUNK, &bar_full[st]);
         };
-        for (int c = 0; c < NS - 1 && c < Cfg::NIT; ++c) load_chunk(c);
+        for (int c = 0; c < NS - 1 && c < nsteps; ++c) load_chunk(c);
         bool ok = true;
-        for (int c = 0; c < Cfg::NIT && ok; ++c) {
+        for (int c = 0; c < nsteps && ok; ++c) {
             const int st = c % NS;
             if (!tc::mbar_wait(&bar_full[st], (c / NS) & 1)) {
                 ok = false;
@@ -529,7 +549,7 @@ __device__ __forceinline__ void tc2_pair_body(int mp, int r0, int c0, bool two, 
             if (two) cplx_mma_step<KIND>(tbase + 2u * T2_BN, a0 + 2 * Cfg::A_CHUNK, a0 + 3 * Cfg::A_CHUNK, b0, c == 0);
             tc::mma_commit(&bar_empty[st]);
             const int nxt = c + NS - 1;
-            if (nxt < Cfg::NIT) {
+            if (nxt < nsteps) {
                 if (c >= 1) {
                     const int sp = (c - 1) % NS;
                     if (!tc::mbar_wait(&bar_empty[sp], ((c - 1) / NS) & 1)) {
@@ -618,14 +638,20 @@ __device__ __forceinline__ void tc2_pair_body(int mp, int r0, int c0, bool two, 
 }
 
 // Outer trailing update of tile (ti, tj): C[R0 + 128 ti.., R0 + 128 tj..] -= D.
+// apack_old / bpack_old (optional): the previous outer step's packed operands, whose
+// tiles are one index further (their trailing matrix starts 128 rows and columns earlier).
 template <int KIND>
 __device__ __forceinline__ void tc2_update_body(int mp, int R0, float* __restrict__ re_plane,
                                                 const unsigned char* __restrict__ apack,
                                                 const unsigned char* __restrict__ bpack, int* __restrict__ err, int ti,
-                                                int tj, unsigned char* __restrict__ pk_next = nullptr) {
+                                                int tj, unsigned char* __restrict__ pk_next = nullptr,
+                                                const unsigned char* __restrict__ apack_old = nullptr,
+                                                const unsigned char* __restrict__ bpack_old = nullptr) {
     using Cfg = Tc2<KIND>;
     tc2_tile_body<KIND, false>(mp, R0 + ti * T2_BM, R0 + tj * T2_BN, re_plane, apack + (size_t)ti * Cfg::A_TILE,
-                               bpack + (size_t)tj * Cfg::B_TILE, err, pk_next, 1);
+                               bpack + (size_t)tj * Cfg::B_TILE, err, pk_next, 1,
+                               apack_old ? apack_old + (size_t)(ti + 1) * Cfg::A_TILE : nullptr,
+                               bpack_old ? bpack_old + (size_t)(tj + 1) * Cfg::B_TILE : nullptr);
 }
 
 }  // namespace fde

@@ -55,16 +55,23 @@ __device__ __forceinline__ void tma2d_store(const CUtensorMap* map, int x, int y
                  : "memory");
 }
 
-// Tiles x0 .. x0 + nq - 1 of the interior of block k: x -> (ti, tj) = (1 + x / ni, 1 + x % ni).
-// apack / bpack: this block's packed operand tiles of the step; cmap: the factor planes of
-// all blocks as rows of m_p floats (block k's Re plane from row 2 k m_p, Im plane from
-// row (2 k + 1) m_p), boxes of 128 rows x 32 columns, 128-byte swizzle.
+// Tiles x0 .. x0 + nq - 1 of one block's trailing matrix (tiles of 128 from R0, nt per
+// dimension): front = 0 -> the square of tiles ti, tj >= f, x -> (f + x / (nt - f),
+// f + x % (nt - f)); front = 1 -> row 1 and column 1, x -> (1, 1 + x) for x < nt - 1,
+// else (2 + x - (nt - 1), 1).  apack / bpack: this block's packed operand tiles of the
+// step; apack_old / bpack_old (optional): the previous step's, applied first in the same
+// accumulator (their tile indices are one larger).  cmap: the factor planes of all blocks
+// as rows of m_p floats (block k's Re plane from row 2 k m_p, Im plane from row
+// (2 k + 1) m_p), boxes of 128 rows x 32 columns, 128-byte swizzle.
 template <int KIND>
-__device__ __forceinline__ void tc2s_body(int mp, int R0, int ni, int x0, int nq, int k,
+__device__ __forceinline__ void tc2s_body(int mp, int R0, int nt, int f, int front, int x0, int nq, int k,
                                           const unsigned char* __restrict__ apack,
-                                          const unsigned char* __restrict__ bpack, int* __restrict__ err,
+                                          const unsigned char* __restrict__ bpack,
+                                          const unsigned char* __restrict__ apack_old,
+                                          const unsigned char* __restrict__ bpack_old, int* __restrict__ err,
                                           const CUtensorMap* cmap) {
     using Cfg = Tc2<KIND>;
+    const int nsteps = (apack_old ? 2 : 1) * Cfg::NIT;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t ofull[S_OPS], oempty[S_OPS], cfull[S_C], cempty[S_C], acc_full[2],
         acc_empty[2], mma_done;
@@ -79,8 +86,13 @@ __device__ __forceinline__ void tc2s_body(int mp, int R0, int ni, int x0, int nq
     const int yre0 = k * 2 * mp;  // tensor-map row of block k's Re plane
     auto tile_rc = [&](int q, int& r0, int& c0, int& ti, int& tj) {
         const int x = x0 + q;
-        ti = 1 + x / ni;
-        tj = 1 + x % ni;
+        if (front) {
+            ti = x < nt - 1 ? 1 : 2 + x - (nt - 1);
+            tj = x < nt - 1 ? 1 + x : 1;
+        } else {
+            ti = f + x / (nt - f);
+            tj = f + x % (nt - f);
+        }
         r0 = R0 + ti * T2_BM;
         c0 = R0 + tj * T2_BN;
     };
@@ -121,21 +133,27 @@ __device__ __forceinline__ void tc2s_body(int mp, int R0, int ni, int x0, int nq
                 tile_rc(q, r0, c0, ti, tj);
                 const unsigned char* ga = apack + (size_t)ti * Cfg::A_TILE;
                 const unsigned char* gb = bpack + (size_t)tj * Cfg::B_TILE;
+                const unsigned char* gao = apack_old ? apack_old + (size_t)(ti + 1) * Cfg::A_TILE : nullptr;
+                const unsigned char* gbo = bpack_old ? bpack_old + (size_t)(tj + 1) * Cfg::B_TILE : nullptr;
                 bool ok = true;
-                for (int c = 0; c < Cfg::NIT; ++c) {
+                for (int c = 0; c < nsteps; ++c) {
                     const int s = u % S_OPS;
                     if (u >= S_OPS && !tc::mbar_wait(&oempty[s], (uint32_t)((u / S_OPS - 1) & 1))) {
                         fail(1);
                         ok = false;
                         break;
                     }
-                    const int kc = Cfg::re_chunk(c);
+                    const bool old = gao && c < Cfg::NIT;
+                    const unsigned char* a = old ? gao : ga;
+                    const unsigned char* b = old ? gbo : gb;
+                    const int cl = old || !gao ? c : c - Cfg::NIT;
+                    const int kc = Cfg::re_chunk(cl);
                     unsigned char* dst = ring + s * Cfg::STAGE;
                     tc::mbar_arrive_expect_tx(&ofull[s], Cfg::STAGE);
-                    tc::bulk_g2s(dst, ga + (size_t)kc * Cfg::A_CHUNK, Cfg::A_CHUNK, &ofull[s]);
-                    tc::bulk_g2s(dst + Cfg::A_CHUNK, ga + (size_t)(kc + Cfg::HALF) * Cfg::A_CHUNK, Cfg::A_CHUNK,
+                    tc::bulk_g2s(dst, a + (size_t)kc * Cfg::A_CHUNK, Cfg::A_CHUNK, &ofull[s]);
+                    tc::bulk_g2s(dst + Cfg::A_CHUNK, a + (size_t)(kc + Cfg::HALF) * Cfg::A_CHUNK, Cfg::A_CHUNK,
                                  &ofull[s]);
-                    tc::bulk_g2s(dst + 2 * Cfg::A_CHUNK, gb + (size_t)c * Cfg::B_CHUNK, Cfg::B_CHUNK, &ofull[s]);
+                    tc::bulk_g2s(dst + 2 * Cfg::A_CHUNK, b + (size_t)cl * Cfg::B_CHUNK, Cfg::B_CHUNK, &ofull[s]);
                     n_oi = ++u;
                 }
                 if (!ok) break;
@@ -153,7 +171,7 @@ __device__ __forceinline__ void tc2s_body(int mp, int R0, int ni, int x0, int nq
                 tc::fence_after_sync();
                 const uint32_t tacc = tbase + (uint32_t)a * 2u * T2_BN;
                 bool ok = true;
-                for (int c = 0; c < Cfg::NIT; ++c) {
+                for (int c = 0; c < nsteps; ++c) {
                     const int s = u % S_OPS;
                     if (abort_flag || !tc::mbar_wait(&ofull[s], (uint32_t)((u / S_OPS) & 1))) {
                         fail(1);

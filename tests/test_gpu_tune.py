@@ -78,13 +78,16 @@ def test_autotune_records_the_shape(lib):
 
 @pytest.mark.parametrize("precision,m", [("tf32", 700), ("bf16", 700), ("tf32x3", 700), ("tf32", 1000),
                                          ("bf16", 1000), ("tf32x3", 1000)])
-def test_lu_interior_variants_are_bit_identical(lib, precision, m):
-    """The interior trailing update of the tensor-core LU as row-pair tiles (variant 0),
-    warp-specialized CTAs with two TMEM accumulators (variant 1), or the same with the C
-    tiles streamed by tensor-map copies (variant 2, m_p a multiple of 128; otherwise row
-    pairs): the same MMAs in the same K order, so identical factors.  m = 700: several
-    outer steps, ragged 64-wide tiles; m = 1000: m_p = 1024, seven interior updates of
-    full tiles (1 to 36 tiles per block)."""
+def test_lu_interior_variants(lib, precision, m):
+    """The interior trailing update of the tensor-core LU as row-pair tiles (variant 0) or
+    warp-specialized CTAs with two TMEM accumulators (variant 1): the same MMAs in the same
+    K order, so identical factors.  Variant 2 streams C by tensor-map copies and, where
+    m_p is a multiple of 128, applies the updates of two consecutive outer steps in one
+    pass (one subtraction of the summed products instead of two); elsewhere it is the row
+    pairs (identical).  Where it merges, the factors differ from variant 0 by rounding
+    only: bounded here by 16 units of the operand precision times the largest factor
+    entry.  m = 700: several outer steps, ragged 64-wide tiles; m = 1000: m_p = 1024,
+    seven outer steps (three merged pairs and a single step)."""
     from paper_1305_6653_gb300 import FDEProblem, _lib
     L, _ = lib
     prob = fi.manufactured(m, 16, 1.7, "GBDF3", dplus_fn=lambda x: 1 + x, dminus_fn=lambda x: 2 - x)
@@ -95,6 +98,14 @@ def test_lu_interior_variants_are_bit_identical(lib, precision, m):
             p.assemble().factor(precision)
             facs.append([p.factor_block(k) for k in (0, 3, prob.s // 2)])
     L.fde_tune_set(_lib.FDE_TUNE_LU, -1)
-    for v in (1, 2):
-        for a, b in zip(facs[0], facs[v]):
-            assert np.array_equal(a, b), v
+    for a, b in zip(facs[0], facs[1]):
+        assert np.array_equal(a, b)
+    mp = -(-m // 64) * 64
+    unit = {"tf32": 2.0 ** -11, "bf16": 2.0 ** -8, "tf32x3": 2.0 ** -22}[precision]
+    for a, c in zip(facs[0], facs[2]):
+        if mp % 128:
+            assert np.array_equal(a, c)
+        else:
+            d = np.abs(a - c).max() / np.abs(a).max()
+            print(precision, m, "merged vs per-step max rel diff", d)
+            assert d <= 16 * unit, d
