@@ -649,6 +649,7 @@ void fde_problem_destroy(fde_problem* h) {
     else cudaDeviceSynchronize();
     if (P.lu_hi) cudaStreamSynchronize(P.lu_hi);
     if (P.lu_lo) cudaStreamSynchronize(P.lu_lo);
+    if (P.lu_x) cudaStreamSynchronize(P.lu_x);
     free_workspace(P);
     void* bufs[] = {P.d_start, P.d_a, P.d_b, P.d_dplus, P.d_dminus, P.d_u0, P.d_f, P.d_g, P.d_twL, P.d_twL32,
                     P.d_sym, P.d_sym32, P.d_tws, P.d_tws32, P.d_phi, P.d_psi, P.d_b_rhs, P.d_work, P.d_rhat,
@@ -662,6 +663,7 @@ void fde_problem_destroy(fde_problem* h) {
         if (e) cudaEventDestroy(e);
     if (P.lu_hi) cudaStreamDestroy(P.lu_hi);
     if (P.lu_lo) cudaStreamDestroy(P.lu_lo);
+    if (P.lu_x) cudaStreamDestroy(P.lu_x);
     drop_iter_graphs(P);
     if (P.cap_stream) cudaStreamDestroy(P.cap_stream);
     delete h;

@@ -225,9 +225,11 @@ struct Problem {
     long long graph_key = -1;
     int graph_gen = 0;                           // bumped whenever a buffer the graphs use changes
     int solves = 0;                              // completed pgmres_solve calls
-    // tensor-core LU look-ahead: panel chain on lu_hi, interior updates on lu_lo
-    cudaStream_t lu_hi = nullptr, lu_lo = nullptr;
-    cudaEvent_t lu_ev[3] = {nullptr, nullptr, nullptr};  // fork / cross done / interior done
+    // tensor-core LU look-ahead: panel chain on lu_hi, interior updates on lu_lo, the
+    // cross tiles other than the next diagonal block on lu_x
+    cudaStream_t lu_hi = nullptr, lu_lo = nullptr, lu_x = nullptr;
+    // fork / panel products done / interior done / next diagonal block updated / cross tiles done
+    cudaEvent_t lu_ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
 
     // Krylov workspace
     int restart_cap = 0;

@@ -1242,15 +1242,16 @@ lu_update_tc2_kernel(int mp, int R0, int nt, int part, float* __restrict__ fac,
                      const unsigned char* __restrict__ bpack_old = nullptr) {
     // part 0: all nt^2 tiles; 1: the cross ti = 0 or tj = 0 (2 nt - 1 tiles: the next
     // panel's rows and columns); 2: the interior ti, tj >= 1 ((nt - 1)^2 tiles); 3: the
-    // row ti = 0 only (nt tiles; the column below it goes to the row-pair kernel)
+    // row ti = 0 only (nt tiles; the column below it goes to the row-pair kernel); 4: the
+    // row ti = 0 without its first tile (tj >= 1, nt - 1 tiles)
     const int k = blockIdx.y, x = blockIdx.x;
     int ti, tj;
     if (part == 0) {
         ti = x / nt;
         tj = x % nt;
-    } else if (part == 3) {
+    } else if (part == 3 || part == 4) {
         ti = 0;
-        tj = x;
+        tj = part == 3 ? x : 1 + x;
     } else if (part == 1) {
         ti = x < nt ? 0 : x - nt + 1;
         tj = x < nt ? x : 0;
@@ -1953,6 +1954,7 @@ static int ensure_lu_streams(Problem& P) {
     FDE_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
     FDE_CUDA_TRY(cudaStreamCreateWithPriority(&P.lu_hi, cudaStreamNonBlocking, greatest));
     FDE_CUDA_TRY(cudaStreamCreateWithPriority(&P.lu_lo, cudaStreamNonBlocking, least));
+    FDE_CUDA_TRY(cudaStreamCreateWithPriority(&P.lu_x, cudaStreamNonBlocking, greatest));
     for (cudaEvent_t& e : P.lu_ev) FDE_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     return FDE_OK;
 }
@@ -2008,7 +2010,7 @@ static int run_lu_tc(Problem& P, cudaStream_t st) {
     FDE_CUDA_TRY(cudaFuncSetAttribute(lu_panel_tc2_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       Cfg::SMEM_STORE));
     if ((rc = ensure_lu_streams(P))) return rc;
-    cudaStream_t sh = P.lu_hi, sl = P.lu_lo;
+    cudaStream_t sh = P.lu_hi, sl = P.lu_lo, sx = P.lu_x;
     CUtensorMap cmap;
     if (merge && (rc = factor_tensor_map_sw128(fac, mp, nb, &cmap))) return rc;
     // inverted diagonal blocks kept for the tensor-core block solves (TF32, whole 128-row strips)
@@ -2033,9 +2035,12 @@ static int run_lu_tc(Problem& P, cudaStream_t st) {
     FDE_CUDA_TRY(cudaEventRecord(P.lu_ev[0], st));  // fork after the work already queued on st
     FDE_CUDA_TRY(cudaStreamWaitEvent(sh, P.lu_ev[0], 0));
     FDE_CUDA_TRY(cudaStreamWaitEvent(sl, P.lu_ev[0], 0));
+    FDE_CUDA_TRY(cudaStreamWaitEvent(sx, P.lu_ev[0], 0));
 
     // diagonal block, then (if a trailing matrix follows) packing and panel products
-    auto panel = [&](int o) -> int {
+    // after_cross: the panel products wait for the cross tiles of the previous step (on
+    // sx), the diagonal block only for its own tile (queued on sh before)
+    auto panel = [&](int o, bool after_cross) -> int {
         const int R0 = o + (mp - o < TB ? mp - o : TB);
         const bool more = R0 < mp;
         {
@@ -2045,6 +2050,7 @@ static int run_lu_tc(Problem& P, cudaStream_t st) {
                 dsave ? dsave + (size_t)(o / TB) * 2 * Cfg::A_TILE : nullptr, dtile_stride);
             FDE_LAUNCH_CHECK("lu_diag128_kernel");
         }
+        if (after_cross) FDE_CUDA_TRY(cudaStreamWaitEvent(sh, P.lu_ev[4], 0));
         if (!more) return FDE_OK;
         const int nt = cdiv(mp - R0, T2_BM);
         const long items = 2L * (mp - R0) * (TB / Cfg::PER_CORE);
@@ -2072,7 +2078,7 @@ static int run_lu_tc(Problem& P, cudaStream_t st) {
                                                               P.d_phi, P.d_psi, fac);
             FDE_LAUNCH_CHECK("form_blocks_kernel");
         }
-        int r = panel(0);
+        int r = panel(0, false);
         if (r) return r;
         const int nsteps = mp > TB ? cdiv(mp - TB, TB) : 0;  // outer steps with a trailing matrix
         for (int p = 0; p < nsteps; ++p) {
@@ -2093,26 +2099,35 @@ static int run_lu_tc(Problem& P, cudaStream_t st) {
             // the cross tiles update tiles the last interior update wrote and pack over a buffer
             // it may read (an even step of a merged pair touches neither)
             if (p > 0 && !a_step) FDE_CUDA_TRY(cudaStreamWaitEvent(sh, P.lu_ev[2], 0));
-            {  // the next panel's rows (single tiles) and the column below them (row pairs); when
-               // that panel has a trailing matrix, they are packed as its operand tiles as well
+            const bool next = R0 + TB < mp;
+            {  // the next diagonal block (tile 0, 0): all the next diagonal kernel waits for
                 StageTimer t(P, FDE_STAGE_LU_TC, sh);
-                const bool next = R0 + TB < mp;
-                lu_update_tc2_kernel<KIND><<<dim3(nt, nb), 128, Cfg::SMEM, sh>>>(mp, R0, nt, 3, fac, apk(o), bpk(o),
-                                                                               pa, pb, P.d_err,
-                                                                               next ? bpk(R0) : nullptr, ao, bo);
+                lu_update_tc2_kernel<KIND><<<dim3(1, nb), 128, Cfg::SMEM, sh>>>(mp, R0, nt, 3, fac, apk(o), bpk(o), pa,
+                                                                              pb, P.d_err, nullptr, ao, bo);
                 FDE_LAUNCH_CHECK("lu_update_tc2_kernel");
+            }
+            FDE_CUDA_TRY(cudaEventRecord(P.lu_ev[3], sh));
+            FDE_CUDA_TRY(cudaStreamWaitEvent(sx, P.lu_ev[3], 0));
+            {  // the rest of the next panel's rows (single tiles) and the column below them (row
+               // pairs) beside the next diagonal block; when that panel has a trailing matrix, they
+               // are packed as its operand tiles as well
+                StageTimer t(P, FDE_STAGE_LU_TC, sx);
                 if (nt > 1) {
-                    lu_update_tc2p_kernel<KIND><<<dim3((nt - 1 + 1) / 2, nb), 128, Tc2p<KIND>::SMEM, sh>>>(
+                    lu_update_tc2_kernel<KIND><<<dim3(nt - 1, nb), 128, Cfg::SMEM, sx>>>(
+                        mp, R0, nt, 4, fac, apk(o), bpk(o), pa, pb, P.d_err, next ? bpk(R0) : nullptr, ao, bo);
+                    FDE_LAUNCH_CHECK("lu_update_tc2_kernel");
+                    lu_update_tc2p_kernel<KIND><<<dim3((nt - 1 + 1) / 2, nb), 128, Tc2p<KIND>::SMEM, sx>>>(
                         mp, R0, nt, 0, 1, fac, apk(o), bpk(o), pa, pb, P.d_err, next ? apk(R0) : nullptr, ao, bo);
                     FDE_LAUNCH_CHECK("lu_update_tc2p_kernel");
                 }
                 if (b_step && nt > 1) {  // row and column 1, both steps' products
                     lu_update_tc2s_kernel<KIND>
-                        <<<dim3(cdiv(tc2s_tiles(nt, 1, 1), S_WQ), nb), S_THREADS, Tc2s<KIND>::SMEM, sh>>>(
+                        <<<dim3(cdiv(tc2s_tiles(nt, 1, 1), S_WQ), nb), S_THREADS, Tc2s<KIND>::SMEM, sx>>>(
                             mp, R0, nt, 1, 1, apk(o), bpk(o), ao, bo, pa, pb, P.d_err, cmap);
                     FDE_LAUNCH_CHECK("lu_update_tc2s_kernel");
                 }
             }
+            FDE_CUDA_TRY(cudaEventRecord(P.lu_ev[4], sx));
             const int f = b_step ? 2 : 1;  // first row / column of the interior update
             if (!a_step && nt > f) {
                 FDE_CUDA_TRY(cudaStreamWaitEvent(sl, P.lu_ev[1], 0));
@@ -2134,13 +2149,15 @@ static int run_lu_tc(Problem& P, cudaStream_t st) {
                 }
                 FDE_CUDA_TRY(cudaEventRecord(P.lu_ev[2], sl));
             }
-            if ((r = panel(R0))) return r;
+            if ((r = panel(R0, true))) return r;
         }
         return FDE_OK;
     };
     rc = body();
-    // join: st continues after both streams
+    // join: st continues after all three streams
     cudaEventRecord(P.lu_ev[1], sl);
+    cudaStreamWaitEvent(st, P.lu_ev[1], 0);
+    cudaEventRecord(P.lu_ev[1], sx);
     cudaStreamWaitEvent(st, P.lu_ev[1], 0);
     cudaEventRecord(P.lu_ev[1], sh);
     cudaStreamWaitEvent(st, P.lu_ev[1], 0);
