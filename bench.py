@@ -1049,10 +1049,31 @@ def measure_peaks() -> dict:
         finally:
             torch.backends.cuda.matmul.allow_tf32 = old
 
+    def copy_gbs(reps=5):
+        # device-to-device copy of 2 GiB (read + write bytes), best of several timings: this box's
+        # HBM rate, to set the block solves' roofline fraction beside the pool-wide measurement
+        n = 1 << 29
+        a = torch.ones(n, dtype=torch.float32, device="cuda")
+        b = torch.empty_like(a)
+        b.copy_(a)
+        torch.cuda.synchronize()
+        t = []
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            b.copy_(a)
+            e1.record()
+            e1.synchronize()
+            t.append(e0.elapsed_time(e1))
+        del a, b
+        return 2.0 * n * 4 / (min(t) / 1e3) / 1e9
+
     return {"tf32_tflops": best(8192, torch.float32, 8, True), "fp32_tflops": best(8192, torch.float32, 3, False),
-            "fp64_tflops": best(4096, torch.float64, 3, False),
+            "fp64_tflops": best(4096, torch.float64, 3, False), "hbm_copy_gbs": copy_gbs(),
             "how": "torch.matmul (cuBLAS) best of 3-8 CUDA-event timings: float32 8192^3 with TF32 on / off, "
-                   "float64 4096^3; 2 N^3 flops"}
+                   "float64 4096^3 (2 N^3 flops); hbm_copy_gbs: a 2 GiB device-to-device copy, read + write "
+                   "bytes, best of 5"}
 
 
 def main():
@@ -1190,6 +1211,7 @@ def main():
     roof = {"kernel": "block_trsv_kernel", "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
             "frac": ach / hbm_peak, "traffic": traffic, "peak_kind": peak_kind,
             "algorithmic_bytes_per_launch": per_launch, "launches_timed": dom_n,
+            "frac_of_this_gpu_copy": ach / measured["hbm_copy_gbs"] if measured else None,
             "timing": "CUDA events recorded inside the replayed iteration graphs, over the timed region",
             "traffic_source": "ncu capture at m=1023, s=256 scaled by the factor bytes" if traffic else None}
     # the tensor-core update beside it (profiled pass)
@@ -1200,7 +1222,8 @@ def main():
         tfl = tc_update_flops(mp, nblk) * nps * (3 if args.precision == "tf32x3" else 1)
         tpeak = tf32_peak if args.precision in ("tf32", "tf32x3") else bf16_peak
         tbytes = tc_update_bytes(mp, nblk) * nps
-        tc_line = {"kernel": "lu_update_tc2_kernel (cross tiles) + lu_update_tc2p_kernel (interior row pairs)",
+        tc_line = {"kernel": "lu_update_tc2_kernel, lu_update_tc2p_kernel (cross tiles) + lu_update_tc2s_kernel "
+                             "(interior, consecutive steps merged)",
                    "launches_per_step": tn // nps,
                    "timing": "profiled pass; CUDA events on both LU streams (the interior updates overlap the "
                              "panel chain)",

@@ -1954,7 +1954,10 @@ static int ensure_lu_streams(Problem& P) {
     FDE_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
     FDE_CUDA_TRY(cudaStreamCreateWithPriority(&P.lu_hi, cudaStreamNonBlocking, greatest));
     FDE_CUDA_TRY(cudaStreamCreateWithPriority(&P.lu_lo, cudaStreamNonBlocking, least));
-    FDE_CUDA_TRY(cudaStreamCreateWithPriority(&P.lu_x, cudaStreamNonBlocking, greatest));
+    // the cross tiles one level below the panel chain (the next diagonal kernel gets the SMs
+    // first), above the interior updates
+    const int mid = greatest < least ? greatest + 1 : greatest;
+    FDE_CUDA_TRY(cudaStreamCreateWithPriority(&P.lu_x, cudaStreamNonBlocking, mid));
     for (cudaEvent_t& e : P.lu_ev) FDE_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     return FDE_OK;
 }
