@@ -653,7 +653,7 @@ void fde_problem_destroy(fde_problem* h) {
     free_workspace(P);
     void* bufs[] = {P.d_start, P.d_a, P.d_b, P.d_dplus, P.d_dminus, P.d_u0, P.d_f, P.d_g, P.d_twL, P.d_twL32,
                     P.d_sym, P.d_sym32, P.d_tws, P.d_tws32, P.d_phi, P.d_psi, P.d_b_rhs, P.d_work, P.d_rhat,
-                    P.d_fac, P.d_dinv, P.d_info, P.d_err, P.d_pack, P.d_tinv, P.d_dtile, P.d_scal, P.d_partial,
+                    P.d_fac, P.d_dinv, P.d_info, P.d_err, P.d_pack, P.d_tinv, P.d_dtile, P.d_strips, P.d_scal, P.d_partial,
                     P.d_counter, P.d_bccb_K64, P.d_bccb_K32, P.d_rhat_b, P.d_dplus_t, P.d_dminus_t,
                     P.d_jz, P.d_xsol};
     for (void* b : bufs) dfree(b);

@@ -208,6 +208,11 @@ struct Problem {
     void* d_dtile = nullptr;
     size_t dtile_bytes = 0;
     bool save_dtile = false;
+    // the FP32 factor in strip-major layout (32-column strips, rows contiguous), written
+    // by the tensor-core LU beside the row-major planes for the block solves
+    void* d_strips = nullptr;
+    size_t strips_bytes = 0;
+    bool strips_ok = false;
     // Strang-type BCCB preconditioner (bccb_precond_setup): the spectra K_k of the
     // circulant inverses, k = 0..s/2, length L each, and its frequency-side vectors
     int precond = 0;            // FDE_PRECOND_STRANG or FDE_PRECOND_BCCB / FDE_PRECOND_BCCB_MODIFIED
@@ -328,6 +333,9 @@ bool trsm_tc_supported(int mp);
 // Re plane from row 2 k m_p, Im plane from (2 k + 1) m_p), boxes of 128 rows x 32
 // columns, 128-byte swizzle
 int factor_tensor_map_sw128(const void* fac, int mp, int nblk, CUtensorMap* map);
+// The strip-major copy (rows of 32 floats: element (r, c) of block k's plane at row
+// ((2 k + plane) m_p / 32 + c / 32) m_p + r), same boxes and swizzle
+int strip_tensor_map_sw128(const void* strips, int mp, int nblk, CUtensorMap* map);
 int launch_trsm_tc(const InstDev* I, const int* act, int nact, const void* fac, const void* dtile, int mp, int nblk,
                    int* err, cudaStream_t st);
 int launch_time_fft_batched(const InstDev* I, const int* act, int nact, int max_mp, int max_s, int j,

@@ -506,10 +506,23 @@ __device__ __forceinline__ void tile_async(T* dst, const T* plane, int mp, int r
     tile_async<T>(dst, plane + (size_t)r0 * mp + c0, (size_t)mp, lane);
 }
 
+// Factor planes in one of two layouts: row-major (element (r, c) at r m_p + c) or
+// strip-major (32-column strips one after the other, each strip's rows contiguous:
+// (c / 32) 32 m_p + 32 r + c mod 32), where every strip of the block solves is one
+// sequential stream.  The tensor-core LU writes the final factor in both.
+template <bool STRIPS>
+__device__ __forceinline__ size_t fac_at(int mp, int r, int c) {
+    return STRIPS ? (size_t)(c >> 5) * 32 * mp + (size_t)r * 32 + (c & 31) : (size_t)r * mp + c;
+}
+template <typename T, bool STRIPS>
+__device__ __forceinline__ void tile_async_l(T* dst, const T* plane, int mp, int r0, int c0, int lane) {
+    tile_async<T>(dst, plane + fac_at<STRIPS>(mp, r0, c0), STRIPS ? (size_t)32 : (size_t)mp, lane);
+}
+
 // Solver side of one sweep (warp 0).  INV: the inverted diagonal tiles are given
 // (tinv: per tile [L^-1 re, L^-1 im, U^-1 re, U^-1 im][32][32]) and a tile solve is
 // the product x = D^-1 a; otherwise the tile is solved by substitution.
-template <typename T, bool FWD, bool INV, int NT>
+template <typename T, bool FWD, bool INV, int NT, bool STRIPS = false>
 __device__ __forceinline__ void trsv_solver(int mp, int nt, const T* re, const T* im, const cplx_t<T>* dv,
                                             const T* tinv, cplx_t<T>* y, cplx_t<T> (*xs)[32], T* tiles,
                                             cplx_t<T>* av, int lane) {
@@ -524,12 +537,12 @@ __device__ __forceinline__ void trsv_solver(int mp, int nt, const T* re, const T
             tile_async<T>(b, ti, 32, lane);
             tile_async<T>(b + TS, ti + 1024, 32, lane);
         } else {
-            tile_async<T>(b, re, mp, 32 * j, 32 * j, lane);
-            tile_async<T>(b + TS, im, mp, 32 * j, 32 * j, lane);
+            tile_async_l<T, STRIPS>(b, re, mp, 32 * j, 32 * j, lane);
+            tile_async_l<T, STRIPS>(b + TS, im, mp, 32 * j, 32 * j, lane);
         }
         if (d >= 1) {
-            tile_async<T>(b + 2 * TS, re, mp, 32 * j, 32 * tile_of(d - 1), lane);
-            tile_async<T>(b + 3 * TS, im, mp, 32 * j, 32 * tile_of(d - 1), lane);
+            tile_async_l<T, STRIPS>(b + 2 * TS, re, mp, 32 * j, 32 * tile_of(d - 1), lane);
+            tile_async_l<T, STRIPS>(b + 3 * TS, im, mp, 32 * j, 32 * tile_of(d - 1), lane);
         }
     };
     issue(0);
@@ -622,7 +635,7 @@ __device__ __forceinline__ void trsv_solver(int mp, int nt, const T* re, const T
 // the shuffles stay warp-uniform.  Two register buffers of H rows alternate: the
 // loads of one are in flight while the other is applied, so the load pipe does
 // not drain between batches.
-template <typename T, bool FWD, int NT, int H>
+template <typename T, bool FWD, int NT, int H, bool STRIPS = false>
 __device__ __forceinline__ void trsv_stream(int mp, int nt, const T* re, const T* im, cplx_t<T>* y,
                                             const cplx_t<T> (*xs)[32], int bt) {
     using C = cplx_t<T>;
@@ -643,8 +656,8 @@ __device__ __forceinline__ void trsv_stream(int mp, int nt, const T* re, const T
                 const int q = q0 + u * TRSV_GROUPS;
                 if (q < len) {
                     const int r = FWD ? lo + q : hi - 1 - q;
-                    ar[b][u] = ld4(re + (size_t)r * mp + col);
-                    ai[b][u] = ld4(im + (size_t)r * mp + col);
+                    ar[b][u] = ld4(re + fac_at<STRIPS>(mp, r, col));
+                    ai[b][u] = ld4(im + fac_at<STRIPS>(mp, r, col));
                 }
             }
         };
@@ -891,7 +904,7 @@ block_trsv_ring_kernel(int mp, const T* __restrict__ fac, const cplx_t<T>* __res
     for (int i = threadIdx.x; i < mp; i += blockDim.x) x[i] = y[i];
 }
 
-template <typename T, bool INV, int NT = TRSV_THREADS, int H = trsv_unroll<T>::value / 2>
+template <typename T, bool INV, int NT = TRSV_THREADS, int H = trsv_unroll<T>::value / 2, bool STRIPS = false>
 __device__ __forceinline__ void trsv_body(int mp, const T* __restrict__ re, const cplx_t<T>* __restrict__ dv,
                                           const T* __restrict__ tinv, cplx_t<T>* __restrict__ x) {
     using C = cplx_t<T>;
@@ -905,21 +918,21 @@ __device__ __forceinline__ void trsv_body(int mp, const T* __restrict__ re, cons
     const int nt = mp / 32;
     for (int i = threadIdx.x; i < mp; i += blockDim.x) y[i] = x[i];
     __syncthreads();
-    if (warp == 0) trsv_solver<T, true, INV, NT>(mp, nt, re, im, dv, tinv, y, xs, tiles, av, lane);
-    else trsv_stream<T, true, NT, H>(mp, nt, re, im, y, xs, threadIdx.x - 32);
+    if (warp == 0) trsv_solver<T, true, INV, NT, STRIPS>(mp, nt, re, im, dv, tinv, y, xs, tiles, av, lane);
+    else trsv_stream<T, true, NT, H, STRIPS>(mp, nt, re, im, y, xs, threadIdx.x - 32);
     __syncthreads();
-    if (warp == 0) trsv_solver<T, false, INV, NT>(mp, nt, re, im, dv, tinv, y, xs, tiles, av, lane);
-    else trsv_stream<T, false, NT, H>(mp, nt, re, im, y, xs, threadIdx.x - 32);
+    if (warp == 0) trsv_solver<T, false, INV, NT, STRIPS>(mp, nt, re, im, dv, tinv, y, xs, tiles, av, lane);
+    else trsv_stream<T, false, NT, H, STRIPS>(mp, nt, re, im, y, xs, threadIdx.x - 32);
     __syncthreads();
     for (int i = threadIdx.x; i < mp; i += blockDim.x) x[i] = y[i];
 }
 
-template <typename T, int V = 0>
+template <typename T, int V = 0, bool STRIPS = false>
 __global__ void __launch_bounds__(trsv_shape<T, V>::NT)
 block_trsv_kernel(int mp, const T* __restrict__ fac, const cplx_t<T>* __restrict__ dinv, const T* __restrict__ tinv,
                   cplx_t<T>* __restrict__ rhat) {
     const int k = blockIdx.x;
-    trsv_body<T, true, trsv_shape<T, V>::NT, trsv_shape<T, V>::H>(mp, fac + (size_t)k * 2 * mp * mp,
+    trsv_body<T, true, trsv_shape<T, V>::NT, trsv_shape<T, V>::H, STRIPS>(mp, fac + (size_t)k * 2 * mp * mp,
                                                                   dinv + (size_t)k * mp,
                                                                   tinv + (size_t)k * (mp / 32) * 4096,
                                                                   rhat + (size_t)k * mp);
@@ -1486,7 +1499,8 @@ __device__ __noinline__ void panel_col_solve(float* Ar, float* Ai, int col, int 
 template <int KIND>
 __device__ __forceinline__ void diag128_body(int mp, int o, float* __restrict__ re, float2* __restrict__ dk,
                                              int* __restrict__ info, unsigned char* __restrict__ pA, bool invert,
-                                             unsigned char* __restrict__ psave = nullptr) {
+                                             unsigned char* __restrict__ psave = nullptr,
+                                             float* __restrict__ strips = nullptr) {
     using Cfg = Tc2<KIND>;
     constexpr int LD = D128_LD;
     extern __shared__ __align__(16) float dsm[];
@@ -1602,6 +1616,11 @@ __device__ __forceinline__ void diag128_body(int mp, int o, float* __restrict__ 
         const float* pi = Ai + r * LD + c;
         *reinterpret_cast<float4*>(re + g) = make_float4(pr[0], pr[1], pr[2], pr[3]);
         *reinterpret_cast<float4*>(im + g) = make_float4(pi[0], pi[1], pi[2], pi[3]);
+        if (strips) {  // the strip-major copy of the final factor
+            const size_t gs = fac_at<true>(mp, o + r, o + c);
+            *reinterpret_cast<float4*>(strips + gs) = make_float4(pr[0], pr[1], pr[2], pr[3]);
+            *reinterpret_cast<float4*>(strips + (size_t)mp * mp + gs) = make_float4(pi[0], pi[1], pi[2], pi[3]);
+        }
     }
     if (!invert || W != TB) return;
     __syncthreads();  // the factor in HBM is read back below by other threads of this CTA
@@ -1831,11 +1850,13 @@ template <int KIND>
 __global__ void __launch_bounds__(D128_THREADS)
 lu_diag128_kernel(int mp, int o, float* __restrict__ fac, float2* __restrict__ dinv, int* __restrict__ info,
                   unsigned char* __restrict__ ipack, size_t ipack_stride, int invert,
-                  unsigned char* __restrict__ dsave = nullptr, size_t dsave_stride = 0) {
+                  unsigned char* __restrict__ dsave = nullptr, size_t dsave_stride = 0,
+                  float* __restrict__ strips = nullptr) {
     const int k = blockIdx.x;
     diag128_body<KIND>(mp, o, fac + (size_t)k * 2 * mp * mp, dinv + (size_t)k * mp, info + k,
                        ipack ? ipack + (size_t)k * ipack_stride : nullptr, invert != 0,
-                       dsave ? dsave + (size_t)k * dsave_stride : nullptr);
+                       dsave ? dsave + (size_t)k * dsave_stride : nullptr,
+                       strips ? strips + (size_t)k * 2 * mp * mp : nullptr);
 }
 
 // Batched: blocks with m_p > o (a prefix of the table sorted by m_p).
@@ -1912,18 +1933,22 @@ template <int KIND>
 __global__ void __launch_bounds__(128)
 lu_panel_tc2_kernel(int mp, int o, int R0, int ntr, float* __restrict__ fac, const unsigned char* __restrict__ apack,
                     const unsigned char* __restrict__ bpack, const unsigned char* __restrict__ ipack, size_t pa,
-                    size_t pb, size_t pi, int* __restrict__ err) {
+                    size_t pb, size_t pi, int* __restrict__ err, int strips,
+                    const __grid_constant__ CUtensorMap fmap, const __grid_constant__ CUtensorMap smap) {
     using Cfg = Tc2<KIND>;
     const int k = blockIdx.y, x = blockIdx.x;
     float* re = fac + (size_t)k * 2 * mp * mp;
+    const CUtensorMap* fm = strips ? &fmap : nullptr;
+    const CUtensorMap* sm = strips ? &smap : nullptr;
     const unsigned char* ip = ipack + (size_t)k * pi;
     // D is packed over the operand tile it was computed from (A21 -> L21, A12 -> U12)
     if (x < ntr) {
         unsigned char* at = const_cast<unsigned char*>(apack) + (size_t)k * pa + (size_t)x * Cfg::A_TILE;
-        tc2_tile_body<KIND, true>(mp, R0 + x * T2_BM, o, re, at, ip + Cfg::A_TILE, err, at, 0);
+        tc2_tile_body<KIND, true>(mp, R0 + x * T2_BM, o, re, at, ip + Cfg::A_TILE, err, at, 0, nullptr, nullptr, fm,
+                                  sm, k);
     } else {
         unsigned char* bt = const_cast<unsigned char*>(bpack) + (size_t)k * pb + (size_t)(x - ntr) * Cfg::B_TILE;
-        tc2_tile_body<KIND, true>(mp, o, R0 + (x - ntr) * T2_BN, re, ip, bt, err, bt, 1);
+        tc2_tile_body<KIND, true>(mp, o, R0 + (x - ntr) * T2_BN, re, ip, bt, err, bt, 1, nullptr, nullptr, fm, sm, k);
     }
 }
 
@@ -2014,8 +2039,6 @@ static int run_lu_tc(Problem& P, cudaStream_t st) {
                                       Cfg::SMEM_STORE));
     if ((rc = ensure_lu_streams(P))) return rc;
     cudaStream_t sh = P.lu_hi, sl = P.lu_lo, sx = P.lu_x;
-    CUtensorMap cmap;
-    if (merge && (rc = factor_tensor_map_sw128(fac, mp, nb, &cmap))) return rc;
     // inverted diagonal blocks kept for the tensor-core block solves (TF32, whole 128-row strips)
     const int nst = mp / TB;
     const size_t dtile_stride = (size_t)nst * 2 * Cfg::A_TILE;
@@ -2035,6 +2058,26 @@ static int run_lu_tc(Problem& P, cudaStream_t st) {
         }
         dsave = reinterpret_cast<unsigned char*>(P.d_dtile);
     }
+    // the strip-major copy of the factor for the block solves (whole 128-wide panels); without
+    // the memory for it the block solves read the row-major planes
+    float* strips = nullptr;
+    if (mp % TB == 0) {
+        const size_t sneed = (size_t)nb * 2 * mp * mp * sizeof(float);
+        if (P.strips_bytes < sneed) {
+            ++P.graph_gen;  // captured block solves may hold the old copy's address
+            if (P.d_strips) {
+                FDE_CUDA_TRY(cudaStreamSynchronize(st));
+                dev_free(P.d_strips);
+            }
+            P.d_strips = nullptr;
+            P.strips_bytes = 0;
+            if (dev_alloc(&P.d_strips, sneed) == FDE_OK) P.strips_bytes = sneed;
+        }
+        strips = reinterpret_cast<float*>(P.d_strips);
+    }
+    CUtensorMap cmap{}, smap{};
+    if ((merge || strips) && (rc = factor_tensor_map_sw128(fac, mp, nb, &cmap))) return rc;
+    if (strips && (rc = strip_tensor_map_sw128(strips, mp, nb, &smap))) return rc;
     FDE_CUDA_TRY(cudaEventRecord(P.lu_ev[0], st));  // fork after the work already queued on st
     FDE_CUDA_TRY(cudaStreamWaitEvent(sh, P.lu_ev[0], 0));
     FDE_CUDA_TRY(cudaStreamWaitEvent(sl, P.lu_ev[0], 0));
@@ -2050,7 +2093,7 @@ static int run_lu_tc(Problem& P, cudaStream_t st) {
             StageTimer t(P, FDE_STAGE_LU_DIAG, sh);
             lu_diag128_kernel<KIND><<<nb, D128_THREADS, diag128_smem(), sh>>>(
                 mp, o, fac, dinv, P.d_info, ipack, pi, (more || dsave) ? 1 : 0,
-                dsave ? dsave + (size_t)(o / TB) * 2 * Cfg::A_TILE : nullptr, dtile_stride);
+                dsave ? dsave + (size_t)(o / TB) * 2 * Cfg::A_TILE : nullptr, dtile_stride, strips);
             FDE_LAUNCH_CHECK("lu_diag128_kernel");
         }
         if (after_cross) FDE_CUDA_TRY(cudaStreamWaitEvent(sh, P.lu_ev[4], 0));
@@ -2067,7 +2110,8 @@ static int run_lu_tc(Problem& P, cudaStream_t st) {
             StageTimer t(P, FDE_STAGE_LU_PANEL_TC, sh);
             lu_panel_tc2_kernel<KIND><<<dim3(2 * nt, nb), 128, Cfg::SMEM_STORE, sh>>>(mp, o, R0, nt, fac, apk(o),
                                                                                     bpk(o), ipack, pa, pb, pi,
-                                                                                    P.d_err);
+                                                                                    P.d_err, strips ? 1 : 0,
+                                                                                    cmap, smap);
             FDE_LAUNCH_CHECK("lu_panel_tc2_kernel");
         }
         return FDE_OK;
@@ -2157,6 +2201,7 @@ static int run_lu_tc(Problem& P, cudaStream_t st) {
         return FDE_OK;
     };
     rc = body();
+    P.strips_ok = rc == FDE_OK && strips != nullptr;
     // join: st continues after all three streams
     cudaEventRecord(P.lu_ev[1], sl);
     cudaStreamWaitEvent(st, P.lu_ev[1], 0);
@@ -2390,6 +2435,7 @@ static int launch_tile_inverse(Problem& P, int prec, cudaStream_t st) {
 
 int launch_block_lu(Problem& P, int prec, cudaStream_t st) {
     int rc;
+    P.strips_ok = false;  // set by the tensor-core LU once it has written the strip-major copy
     if (prec == FDE_FP64) rc = run_lu<double>(P, st);
     else if (prec == FDE_TF32) rc = run_lu_tc<0>(P, st);
     else if (prec == FDE_BF16) rc = run_lu_tc<1>(P, st);
@@ -2402,10 +2448,13 @@ int launch_block_lu(Problem& P, int prec, cudaStream_t st) {
 template <typename T, int V>
 static int launch_trsv_shape(const Problem& P, void* rhat, cudaStream_t st) {
     const size_t smem = trsv_smem_bytes(P.mp, sizeof(T));
-    auto kern = block_trsv_kernel<T, V>;
+    // the strip-major copy of the factor, where the tensor-core LU wrote one
+    const bool strips = sizeof(T) == 4 && P.strips_ok && P.d_strips;
+    auto kern = strips ? block_trsv_kernel<T, V, true> : block_trsv_kernel<T, V, false>;
     FDE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<P.nblk, trsv_shape<T, V>::NT, smem, st>>>(P.mp, (const T*)P.d_fac, (const cplx_t<T>*)P.d_dinv,
-                                                      (const T*)P.d_tinv, (cplx_t<T>*)rhat);
+    kern<<<P.nblk, trsv_shape<T, V>::NT, smem, st>>>(P.mp, (const T*)(strips ? P.d_strips : P.d_fac),
+                                                      (const cplx_t<T>*)P.d_dinv, (const T*)P.d_tinv,
+                                                      (cplx_t<T>*)rhat);
     FDE_LAUNCH_CHECK("block_trsv_kernel");
     return FDE_OK;
 }

@@ -32,6 +32,7 @@
 // (bounded) for its own copies and MMAs, frees its TMEM and returns.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include "tc_ptx.cuh"
@@ -72,6 +73,7 @@ struct Tc2 {
     // columns) share an SM.
     static constexpr int SMEM_STORE = T2_STAGES * STAGE;
     static_assert(3 * SMEM_STORE > 227 * 1024, "store mode: at most two CTAs per SM");
+    static_assert(SMEM_STORE >= 2 * 32768 + 1024, "store mode: two staged 32-column strips fit the freed ring");
     static constexpr int KSTEP = KIND == 1 ? 16 : 8;          // K per MMA = 32 bytes = 2 core matrices
     static constexpr int MMAS = KCH / KSTEP;                  // MMAs per chunk (2)
     static constexpr uint32_t IDESC = tc::instr_desc(KIND == 1 ? 1u : 2u, T2_BM, 2 * T2_BN);
@@ -179,6 +181,26 @@ __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.comm
 // CTA needs before it exits or reuses the buffer; the global writes complete on their own).
 __device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// ... until at most one committed group is still reading its source
+__device__ __forceinline__ void bulk_wait_read_1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+
+// 2-D tensor copies (tensor maps with 128-byte swizzle: row r's 16-byte chunk u of a
+// 128-byte box row sits at r * 128 + ((u ^ (r mod 8)) << 4) of a 1024-byte aligned buffer)
+__device__ __forceinline__ void tma2d_load(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];" ::"r"(tc::smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(tc::smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tma2d_store(const CUtensorMap* map, int x, int y, const void* src) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y), "r"(tc::smem_u32(src))
+                 : "memory");
+}
+
 
 // Operand tiles of the next outer step packed from an updated C tile staged in shared
 // memory (row pitch T2_CROW), one thread per row (A') or column (B'):
@@ -246,7 +268,9 @@ __device__ __forceinline__ void tc2_tile_body(int mp, int r0, int c0, float* __r
                                               const unsigned char* __restrict__ gb, int* __restrict__ err,
                                               unsigned char* __restrict__ pk = nullptr, int pk_side = 0,
                                               const unsigned char* __restrict__ ga_old = nullptr,
-                                              const unsigned char* __restrict__ gb_old = nullptr) {
+                                              const unsigned char* __restrict__ gb_old = nullptr,
+                                              const CUtensorMap* fmap = nullptr, const CUtensorMap* smap = nullptr,
+                                              int kblk = 0) {
     using Cfg = Tc2<KIND>;
     const int nsteps = (ga_old ? 2 : 1) * Cfg::NIT;
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -356,7 +380,68 @@ __device__ __forceinline__ void tc2_tile_body(int mp, int r0, int c0, float* __r
         if (!cok && lane == 0) atomicCAS(err, 0, 2);
         done = __syncthreads_and(cok) != 0;
     }
-    if (STORE && ok && done) {
+    if (STORE && ok && done && smap) {
+        // D through shared memory: per 32-column strip, both planes staged with the 128-byte
+        // swizzle in one of two buffers of the freed ring, then stored by tensor copies to the
+        // row-major planes (fmap) and to the strip-major copy (smap), where the strip's 128
+        // rows are one contiguous 16 KB range.  Whole tiles only (m_p a multiple of 128).
+        const int r = warp * 32 + lane;  // TMEM lane = tile row
+        const uint32_t lane_addr = tbase + ((uint32_t)(warp * 32) << 16);
+        unsigned char* sbuf = smem + ((1024u - (tc::smem_u32(smem) & 1023u)) & 1023u);
+        const int yf = kblk * 2 * mp;                 // block kblk's Re plane in fmap
+        const int ys = kblk * 2 * (mp / 32) * mp;     // its first Re strip in smap
+#pragma unroll 1
+        for (int sx = 0; sx < T2_BN / 32; ++sx) {
+            unsigned char* bre = sbuf + (sx & 1) * 32768;
+            unsigned char* bim = bre + 16384;
+            if (sx >= 2) {  // the stores of strip sx - 2 have read this buffer
+                if (threadIdx.x == 0) bulk_wait_read_1();
+                __syncthreads();
+            }
+#pragma unroll 1
+            for (int h = 0; h < 2; ++h) {
+                const int ch = 2 * sx + h;
+                float dr[16], di[16];
+                tc::tmem_ld16(lane_addr + ch * 16, dr);
+                tc::tmem_ld16(lane_addr + T2_BN + ch * 16, di);
+                tc::tmem_ld_wait();
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int off = r * 128 + (((4 * h + q) ^ (r & 7)) << 4);
+                    *reinterpret_cast<float4*>(bre + off) =
+                        make_float4(dr[4 * q], dr[4 * q + 1], dr[4 * q + 2], dr[4 * q + 3]);
+                    *reinterpret_cast<float4*>(bim + off) =
+                        make_float4(di[4 * q], di[4 * q + 1], di[4 * q + 2], di[4 * q + 3]);
+                }
+                if (pk && pk_side == 0) {  // L21 row r: K' = column (Re), TB + column (Im)
+                    constexpr int EPS = Cfg::PER_CORE;
+#pragma unroll
+                    for (int u = 0; u < 16 / EPS; ++u) {
+                        pack2_seg<KIND>(pk, T2_BM, r, ch * 16 + u * EPS, dr + u * EPS, false);
+                        pack2_seg<KIND>(pk, T2_BM, r, TB + ch * 16 + u * EPS, di + u * EPS, false);
+                    }
+                } else if (pk) {  // U12 row r = K index: B' rows j (Re) and T2_BN + j (Im)
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) {
+                        const int j = ch * 16 + e;
+                        pack2_store<KIND>(pk, 2 * T2_BN, j, r, dr[e], true);
+                        pack2_store<KIND>(pk, 2 * T2_BN, T2_BN + j, r, di[e], true);
+                    }
+                }
+            }
+            fence_async_shared();
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                const int col = c0 + 32 * sx;
+                tma2d_store(fmap, col, yf + r0, bre);
+                tma2d_store(fmap, col, yf + mp + r0, bim);
+                tma2d_store(smap, 0, ys + (col >> 5) * mp + r0, bre);
+                tma2d_store(smap, 0, ys + (mp / 32 + (col >> 5)) * mp + r0, bim);
+                bulk_commit();
+            }
+        }
+        if (threadIdx.x == 0) bulk_wait_read_all();  // the buffers stay valid until read
+    } else if (STORE && ok && done) {
         const int r = warp * 32 + lane;  // TMEM lane = tile row
         const uint32_t lane_addr = tbase + ((uint32_t)(warp * 32) << 16);
         float* pr = gre + (size_t)(r0 + r) * mp + c0;

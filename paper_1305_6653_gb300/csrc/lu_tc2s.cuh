@@ -40,21 +40,6 @@ struct Tc2s {
     static_assert(SMEM <= 227 * 1024, "rings must fit one CTA");
 };
 
-__device__ __forceinline__ void tma2d_load(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
-        "[%4];" ::"r"(tc::smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(tc::smem_u32(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ void tma2d_store(const CUtensorMap* map, int x, int y, const void* src) {
-    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
-                     reinterpret_cast<uint64_t>(map)),
-                 "r"(x), "r"(y), "r"(tc::smem_u32(src))
-                 : "memory");
-}
-
 // Tiles x0 .. x0 + nq - 1 of one block's trailing matrix (tiles of 128 from R0, nt per
 // dimension): front = 0 -> the square of tiles ti, tj >= f, x -> (f + x / (nt - f),
 // f + x % (nt - f)); front = 1 -> row 1 and column 1, x -> (1, 1 + x) for x < nt - 1,

@@ -370,9 +370,9 @@ block_trsm_tc_kernel(const InstDev* __restrict__ I, const int* __restrict__ act,
     }
 }
 
-// Factor planes of nblk blocks as a 2-D tensor map: rows of m_p floats, boxes of 128
-// rows x 32 columns with 128-byte swizzle (the K-major layout the MMAs read).
-int factor_tensor_map_sw128(const void* fac, int mp, int nblk, CUtensorMap* map) {
+// A 2-D FP32 array (rows of `width` floats, `rows` rows) as a tensor map with boxes of
+// 128 rows x 32 columns and 128-byte swizzle (the K-major layout the MMAs read).
+static int tensor_map_sw128(const void* base, uint64_t width, uint64_t rows, CUtensorMap* map, const char* what) {
     using Fn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                             const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                             CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -385,15 +385,26 @@ int factor_tensor_map_sw128(const void* fac, int mp, int nblk, CUtensorMap* map)
             return set_error(FDE_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
         encode = reinterpret_cast<Fn>(fn);
     }
-    const cuuint64_t dims[2] = {(cuuint64_t)mp, (cuuint64_t)nblk * 2 * mp};
-    const cuuint64_t strides[1] = {(cuuint64_t)mp * sizeof(float)};
+    const cuuint64_t dims[2] = {(cuuint64_t)width, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)width * sizeof(float)};
     const cuuint32_t box[2] = {32, (cuuint32_t)TRSM_ST};
     const cuuint32_t estr[2] = {1, 1};
-    const CUresult res = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(fac), dims, strides, box,
+    const CUresult res = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box,
                                 estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (res != CUDA_SUCCESS) return set_error(FDE_ERR_CUDA, "cuTensorMapEncodeTiled failed for the factor planes");
+    if (res != CUDA_SUCCESS) return set_error(FDE_ERR_CUDA, std::string("cuTensorMapEncodeTiled failed for ") + what);
     return FDE_OK;
+}
+
+// Factor planes of nblk blocks: rows of m_p floats, row y = (2 k + plane) m_p + r.
+int factor_tensor_map_sw128(const void* fac, int mp, int nblk, CUtensorMap* map) {
+    return tensor_map_sw128(fac, (uint64_t)mp, (uint64_t)nblk * 2 * mp, map, "the factor planes");
+}
+
+// Strip-major copy of the factor planes: rows of 32 floats, row y = ((2 k + plane) m_p / 32
+// + c / 32) m_p + r for element (r, c), so a box is 128 consecutive rows of one strip.
+int strip_tensor_map_sw128(const void* strips, int mp, int nblk, CUtensorMap* map) {
+    return tensor_map_sw128(strips, 32, (uint64_t)nblk * 2 * (mp / 32) * mp, map, "the factor strips");
 }
 
 bool trsm_tc_supported(int mp) { return mp % TRSM_ST == 0 && mp >= 2 * TRSM_ST && mp <= 16 * TRSM_ST; }

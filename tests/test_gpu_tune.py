@@ -26,16 +26,18 @@ def lib(tmp_path_factory):
     lib.fde_tune_cache(None)
 
 
-def _case():
-    # several 128-row tiles and a ragged tail; 9 Strang blocks
-    return fi.manufactured(300, 16, 1.8, "GBDF5", dplus_fn=lambda x: 1 + x, dminus_fn=lambda x: 2 - x)
+def _case(m=300):
+    # m = 300: several 128-row tiles and a ragged tail; 9 Strang blocks.  m = 500 (m_p = 512):
+    # whole 128-wide panels, where the tensor-core LU also writes the strip-major copy of the
+    # factor that block-solve shapes 0-2 read (shape 3 reads the row-major planes)
+    return fi.manufactured(m, 16, 1.8, "GBDF5", dplus_fn=lambda x: 1 + x, dminus_fn=lambda x: 2 - x)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "tf32"])
-def test_variants_are_bit_identical(lib, precision):
+@pytest.mark.parametrize("precision,m", [("fp64", 300), ("tf32", 300), ("tf32", 500), ("bf16", 500)])
+def test_variants_are_bit_identical(lib, precision, m):
     from paper_1305_6653_gb300 import FDEProblem, _lib
     L, _ = lib
-    prob = _case()
+    prob = _case(m)
     rng = np.random.default_rng(4)
     z = torch.as_tensor(rng.standard_normal(prob.n), device="cuda")
     outs = []
