@@ -95,10 +95,11 @@ int cycle_launches(fde_batch* b, int nr, const fde_pgmres_opts& o, cudaStream_t 
         if (b->shared && b->trsm_tc) {
             const Problem& P0 = *problem_of(b->probs[0]);
             rc = launch_trsm_tc(b->d_inst, b->d_act, nr, P0.d_fac, P0.d_dtile, P0.mp, P0.nblk, b->d_err, st);
-        } else if (b->shared)
+        } else if (b->shared) {
             rc = launch_trsv_multi(b->d_inst, b->d_act, nr, b->max_nblk, b->max_mp, st);
-        else
+        } else {
             rc = launch_trsv_batched(b->d_inst, b->d_act, nr, b->max_nblk, b->max_mp, st);
+        }
         if (rc) return rc;
         if ((rc = launch_time_ifft_batched(b->d_inst, b->d_act, nr, b->max_mp, b->max_s, j, st))) return rc;
         if ((rc = launch_matvec_batched(b->d_inst, b->d_act, nr, b->max_s, b->max_L, b->max_m, 0, j, st))) return rc;
@@ -272,6 +273,10 @@ int fde_batch_factor(fde_batch* b, int precision) {
     if (!b->assembled) return set_error(FDE_ERR_STATE, "fde_batch_assemble must run first");
     if (precision != FDE_FP32 && precision != FDE_TF32 && precision != FDE_BF16 && precision != FDE_TF32X3)
         return set_error(FDE_ERR_ARG, "batched factorisation supports FDE_FP32, FDE_TF32, FDE_BF16 and FDE_TF32X3");
+    // the captured cycles hold the block-solve kernel and factor layout of the last
+    // factorisation (an executable graph still in flight is freed when it completes)
+    for (auto& kv : b->cycle_graphs) cudaGraphExecDestroy(kv.second.first);
+    b->cycle_graphs.clear();
     if (b->shared) {
         // one factorisation (the single-problem path: look-ahead tensor-core LU), used by all;
         // for the tensor-core block solves it also keeps the inverted diagonal blocks

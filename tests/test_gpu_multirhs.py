@@ -132,3 +132,44 @@ def test_tensor_core_block_solves_are_checked():
         b.share_operator().block_solver("tensor_cores").assemble()
         with pytest.raises(FdeError):
             b.factor("fp32")
+
+
+def test_refactoring_switches_the_block_solves():
+    """Factoring the shared operator again with another precision changes the block-solve
+    kernel (TF32: tensor-core solves with the saved diagonal inverses; FP32: CUDA-core
+    groups), so the captured restart cycles must not outlive the factorisation.  m = 250
+    (m_p = 256); every solve of the sequence TF32, FP32, TF32 against the oracle's direct
+    solve."""
+    from paper_1305_6653_gb300 import FDEBatch
+    probs = fi.config_many_rhs(count=3, m=250, s=16)
+    refs = [O.direct_solve(pr) for pr in probs]
+    with FDEBatch(probs) as b:
+        b.share_operator().assemble()
+        for precision in ("tf32", "fp32", "tf32"):
+            b.factor(precision)
+            xs, stats = b.solve(tol=1e-11, restart=20, maxit=400)
+            for pr, ref, x, st in zip(probs, refs, xs, stats):
+                x = x.cpu().numpy()
+                assert st["status"] == 0, (precision, st)
+                assert np.abs(x - ref).max() <= 1e-8 * np.abs(ref).max(), (precision, pr.name)
+
+
+def test_refactoring_one_problem_switches_the_factor_layout():
+    """The same for one problem: the preconditioner after TF32, FP32 and TF32 factors
+    (m = 500, m_p = 512).  The two TF32 applications are bit-identical, and each
+    application satisfies S z = r to its precision's bound (oracle Kronecker S)."""
+    from paper_1305_6653_gb300 import FDEProblem
+    prob = fi.manufactured(500, 16, 1.8, "GBDF5", dplus_fn=lambda x: 1 + x, dminus_fn=lambda x: 2 - x)
+    J = O.j_of(prob)
+    r = np.random.default_rng(5).standard_normal(prob.n)
+    out = []
+    with FDEProblem.from_inputs(prob, device_inputs=True) as p:
+        p.assemble()
+        for precision in ("tf32", "fp32", "tf32"):
+            p.factor(precision)
+            out.append(p.precond_apply(torch.as_tensor(r, device="cuda")).cpu().numpy())
+    assert np.array_equal(out[0], out[2])
+    for z, bound in zip(out, (5e-2, 1e-3, 5e-2)):
+        srel = np.linalg.norm(O.strang_matvec(prob, z, J=J) - r) / np.linalg.norm(r)
+        assert srel <= bound, srel
+    assert not np.array_equal(out[0], out[1])
