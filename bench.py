@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", default="tf32", choices=["fp64", "fp32", "tf32", "bf16", "tf32x3"])
+    ap.add_argument("--storage", default="bf16", choices=["fp32", "bf16"],
+                    help="storage of the factor copy the block solves stream (fde_factor_storage)")
     ap.add_argument("--matvec", default="fp64", choices=["fp64", "fp32"],
                     help="precision of the Toeplitz apply in the Arnoldi products (the restart residual is FP64)")
     ap.add_argument("--relax", type=float, default=0.0,
@@ -225,18 +227,21 @@ def matvec_flops(m: int, s: int, L: int, mu: int) -> float:
 
 
 FP64_PEAK_TFLOPS = 1.25  # GB300 nominal FP64 (no measured FP64 figure in MEASURED_PEAKS.json)
-TRSV_TRAFFIC_RATIO = 1.034  # DRAM bytes / algorithmic bytes of block_trsv_kernel<float> (ncu, m=1023, s=256)
+# DRAM bytes / algorithmic bytes of block_trsv_kernel<float> (ncu, m=1023, s=256), by the
+# element size of the factor copy it streams (4: FP32, 2: bfloat16)
+TRSV_TRAFFIC_RATIO = {4: 1.034}
 
 
-def trsv_bytes(mp: int, nblk: int, esz: int) -> float:
+def trsv_bytes(mp: int, nblk: int, esz: int, fac_esz: int | None = None) -> float:
     """Algorithmic bytes of one block-substitution launch: every factor entry once
-    (L below, U on/above the diagonal; Re and Im planes) + the RHS in and out."""
-    return nblk * (2.0 * mp * mp * esz + 4.0 * mp * esz)
+    (L below, U on/above the diagonal; Re and Im planes; fac_esz bytes each, the
+    stored copy's element) + the RHS in and out (esz per real part)."""
+    return nblk * (2.0 * mp * mp * (fac_esz or esz) + 4.0 * mp * esz)
 
 
 def path_roofline(m: int, s: int, mp: int, esz: int, its: int, precision: str, bf16_peak: float,
                   hbm_peak: float, ms_measured: float, restart: int = 20, tf32_peak: float | None = None,
-                  fp64_peak: float | None = None) -> dict:
+                  fp64_peak: float | None = None, fac_esz: int | None = None) -> dict:
     """Whole-path roofline of one solve: the time it would take at the roofs over the
     measured time.  The block LUs' (s/2+1)(8/3)m^3 real flops at the factor
     precision's peak, plus, per iteration at Arnoldi step j, the factor stream
@@ -247,7 +252,7 @@ def path_roofline(m: int, s: int, mp: int, esz: int, its: int, precision: str, b
     tf32 = tf32_peak if tf32_peak else bf16_peak * 1.1 / 2.25
     setup_peak = {"tf32": tf32, "tf32x3": tf32, "bf16": bf16_peak,
                   "fp32": FP32_ALU_PEAK_TFLOPS, "fp64": fp64_peak if fp64_peak else FP64_PEAK_TFLOPS}[precision]
-    iter_bytes = sum(trsv_bytes(mp, nblk, esz) + (4 + 4 * (i % restart + 1)) * 8.0 * n for i in range(its))
+    iter_bytes = sum(trsv_bytes(mp, nblk, esz, fac_esz) + (4 + 4 * (i % restart + 1)) * 8.0 * n for i in range(its))
     roof_ms = setup_flops / (setup_peak * 1e12) * 1e3 + iter_bytes / (hbm_peak * 1e9) * 1e3
     return {"setup_flops": setup_flops, "setup_peak_tflops": setup_peak, "iteration_bytes": iter_bytes,
             "iterations": its, "ms_at_roofs": roof_ms, "ms_measured": ms_measured, "frac": roof_ms / ms_measured}
@@ -768,7 +773,7 @@ def bench_timevar(args, world, rank, local_rank):
         ach = per_launch / (tms / tn / 1e3) / 1e9
         hbm_peak, _, _, peak_kind = peaks()
         roof = {"kernel": "block_trsv_kernel", "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
-                "frac": ach / hbm_peak, "traffic": TRSV_TRAFFIC_RATIO * per_launch if esz == 4 else None,
+                "frac": ach / hbm_peak, "traffic": TRSV_TRAFFIC_RATIO[4] * per_launch if esz == 4 else None,
                 "peak_kind": peak_kind, "algorithmic_bytes_per_launch": per_launch,
                 "traffic_source": "ncu capture at m=1023, s=256 scaled by the factor bytes" if esz == 4 else None}
     xs = xbuf.cpu().numpy()
@@ -1106,6 +1111,7 @@ def main():
                 "unknowns": args.m * args.s, "scheme": "GBDF5", "alpha": 1.8, "d": "d+=1+x, d-=2-x",
                 "tol_true_residual": args.tol, "restart": args.restart, "precision": args.precision,
                 "arnoldi_matvec": args.matvec if args.matvec == "fp64" else f"fp32 (relax {args.relax:g})",
+                "factor_storage": args.storage,
                 "l2": "flushed (512 MiB write) before every timed step; factors (4.3 GB fp32) exceed L2"}
 
     if args.impl == "reference":
@@ -1140,7 +1146,7 @@ def main():
 
     def step(precision, matvec=None):
         p.assemble()
-        p.factor(precision)
+        p.factor(precision, storage=args.storage)
         mv = args.matvec if matvec is None else matvec
         _, st = p.solve(tol=args.tol, restart=args.restart, maxit=400, out=xbuf, matvec=mv, relax=args.relax)
         return st
@@ -1201,13 +1207,17 @@ def main():
     mp = (prob.m + 63) // 64 * 64
     nblk = prob.s // 2 + 1
     esz = 8 if args.precision == "fp64" else 4
+    # the block solves stream the bfloat16 copy of the factors where the tensor-core LU wrote one
+    fac_esz = 2 if (args.storage == "bf16" and args.precision in ("tf32", "bf16", "tf32x3") and mp % 128 == 0) \
+        else esz
     dom_ms, dom_n = timed_prof["trsv"]
-    per_launch = trsv_bytes(mp, nblk, esz)
+    per_launch = trsv_bytes(mp, nblk, esz, fac_esz)
     ach = per_launch / (dom_ms / dom_n / 1e3) / 1e9
     # DRAM traffic of one launch: ncu's dram__bytes_read.sum + dram__bytes_write.sum on the
-    # m=1023, s=256 case (FP32 factors) was 1.034 x its algorithmic bytes; the bytes grow with
-    # the factor planes, so a launch here moves 1.034 x its algorithmic bytes
-    traffic = TRSV_TRAFFIC_RATIO * per_launch if esz == 4 else None
+    # m=1023, s=256 case was TRSV_TRAFFIC_RATIO[element bytes] x its algorithmic bytes; the
+    # bytes grow with the factor planes, so a launch here moves the same multiple
+    ratio = TRSV_TRAFFIC_RATIO.get(fac_esz) if esz == 4 else None
+    traffic = ratio * per_launch if ratio else None
     roof = {"kernel": "block_trsv_kernel", "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
             "frac": ach / hbm_peak, "traffic": traffic, "peak_kind": peak_kind,
             "algorithmic_bytes_per_launch": per_launch, "launches_timed": dom_n,
@@ -1248,7 +1258,8 @@ def main():
             matvec_line["note"] = ("mixed: FP32 Arnoldi products and FP64 restart residuals; no single-precision "
                                    "roofline")
     path_roof = path_roofline(prob.m, prob.s, mp, esz, stats[-1]["iterations"], args.precision, bf16_peak,
-                              hbm_peak, ms_per_step, restart=args.restart, tf32_peak=tf32_peak, fp64_peak=fp64_peak)
+                              hbm_peak, ms_per_step, restart=args.restart, tf32_peak=tf32_peak, fp64_peak=fp64_peak,
+                              fac_esz=fac_esz)
     nps = max(args.profile_steps, 1)
     stage_ms = {k: round(v[0] / nps, 4) for k, v in prof.items()}
     stage_n = {k: v[1] // nps for k, v in prof.items()}
@@ -1296,7 +1307,7 @@ def main():
             q = fde.FDEProblem(m=prob.m, s=prob.s, alpha=prob.alpha, xL=prob.xL, xR=prob.xR, t0=prob.t0, T=prob.T,
                                dplus=host["dplus"].numpy(), dminus=host["dminus"].numpy(), u0=host["u0"].numpy(),
                                f=host["f"].numpy(), family=prob.family, mu=prob.mu, device_inputs=False)
-            q.assemble().factor(args.precision)
+            q.assemble().factor(args.precision, storage=args.storage)
             q.solve(tol=args.tol, restart=args.restart, maxit=400, out=xh, matvec=args.matvec,
                     relax=args.relax)  # returns after the copy to xh
             q.close()

@@ -147,10 +147,30 @@ int bvm_assemble(fde_problem* p);
  * (eq. (1.11), Sec. 3.2) by blocked complex LU without pivoting (the blocks are
  * strictly row diagonally dominant), in the given precision (FDE_FP64, FDE_FP32,
  * FDE_TF32, FDE_BF16, FDE_TF32X3).  The library owns the factors (FP64: 16*(s/2+1)*mp^2
- * bytes, otherwise 8*(s/2+1)*mp^2, mp = m rounded up to 64).  Requires
- * bvm_assemble.  Errors: FDE_ERR_ARG, FDE_ERR_ALLOC, FDE_ERR_SINGULAR,
- * FDE_ERR_STATE, FDE_ERR_CUDA. */
+ * bytes, otherwise 8*(s/2+1)*mp^2, mp = m rounded up to 64).  The tensor-core
+ * precisions (FDE_TF32, FDE_BF16, FDE_TF32X3) with mp a multiple of 128 also write a
+ * copy of the factors in the order the block solves stream them (32-column strips,
+ * rows contiguous), in the storage fde_factor_storage selects: 8*(s/2+1)*mp^2 bytes
+ * more (FP32) or 4*(s/2+1)*mp^2 (bfloat16); when that memory cannot be had, the
+ * block solves read the factors themselves.  Requires bvm_assemble.  Errors:
+ * FDE_ERR_ARG, FDE_ERR_ALLOC, FDE_ERR_SINGULAR, FDE_ERR_STATE, FDE_ERR_CUDA. */
 int strang_precond_factor(fde_problem* p, int precision);
+
+/* Storage of the copy of the factors that the block solves of the preconditioner
+ * (Sec. 3.2: one forward and one backward triangular solve per Strang block and
+ * application) read after a tensor-core factorisation:
+ *   FDE_STORAGE_FP32  (default) the FP32 factor values;
+ *   FDE_STORAGE_BF16  the factor values rounded to bfloat16 (8-bit significand, to
+ *                     nearest even): half the bytes each application streams.  The
+ *                     block solves still compute in FP32 and the diagonal 32 x 32
+ *                     tiles enter through their FP32 inverses; the preconditioner is
+ *                     then the exact inverse of slightly perturbed factors, which the
+ *                     flexible outer iteration in FP64 (true residual) tolerates.
+ * Takes effect at the next strang_precond_factor; the factors themselves
+ * (fde_get_factor_block) stay FP32.  Errors: FDE_ERR_ARG. */
+#define FDE_STORAGE_FP32 0
+#define FDE_STORAGE_BF16 1
+int fde_factor_storage(fde_problem* p, int storage);
 
 /* Set up the Strang-type BCCB preconditioner S^(2) = s(A) (x) I - h s(B) (x) s(J)
  * (eq. (x1), Sec. 3.1), or with modified != 0 the preconditioner S~^(2) of eq. (xc),

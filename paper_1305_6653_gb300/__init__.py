@@ -179,7 +179,10 @@ class FDEProblem:
         bvm_assemble(self.h)
         return self
 
-    def factor(self, precision="fp64"):
+    def factor(self, precision="fp64", storage="fp32"):
+        """Strang-block LU in `precision`; `storage` ("fp32" or "bf16") is the storage of
+        the copy of the factors the block solves stream (tensor-core precisions)."""
+        _lib.check(_lib.load().fde_factor_storage(self.h, _lib.STORAGES[storage]), "fde_factor_storage")
         strang_precond_factor(self.h, precision)
         return self
 

@@ -32,7 +32,8 @@ ERROR_NAMES = {
 
 # Every symbol declared in include/fde.h (checked by the CPU tests).
 EXPORTED = [
-    "fde_problem_create", "bvm_assemble", "strang_precond_factor", "bccb_precond_setup", "fde_precond_none",
+    "fde_problem_create", "bvm_assemble", "strang_precond_factor", "fde_factor_storage", "bccb_precond_setup",
+    "fde_precond_none",
     "pgmres_solve",
     "fde_problem_destroy",
     "fde_last_error", "fde_matvec", "fde_matvec_fp32", "fde_precond_apply", "fde_get_rhs", "fde_get_factor_block",
@@ -48,6 +49,7 @@ EXPORTED = [
 ]
 FDE_TUNE_MATVEC, FDE_TUNE_TRSV, FDE_TUNE_LU = 0, 1, 2
 BLOCK_SOLVERS = {"auto": 0, "cuda_cores": 1, "tensor_cores": 2}
+STORAGES = {"fp32": 0, "bf16": 1}
 STAGES = ["assemble", "form", "lu_diag", "lu_panel", "lu_update", "tfft_fwd", "trsv", "tfft_inv", "matvec",
           "krylov", "lu_tc", "lu_pack", "lu_panel_tc"]
 
@@ -101,6 +103,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "fde_problem_create": (i32, [C.POINTER(FdeProblemDesc), vp, C.POINTER(vp)]),
         "bvm_assemble": (i32, [vp]),
         "strang_precond_factor": (i32, [vp, i32]),
+        "fde_factor_storage": (i32, [vp, i32]),
         "bccb_precond_setup": (i32, [vp, i32, i32]),
         "fde_precond_none": (i32, [vp]),
         "pgmres_solve": (i32, [vp, C.POINTER(FdePgmresOpts), vp, vp, C.POINTER(FdeStats)]),

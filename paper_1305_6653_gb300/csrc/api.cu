@@ -770,6 +770,15 @@ int bvm_assemble(fde_problem* h) {
     return autotune_matvec(P);
 }
 
+int fde_factor_storage(fde_problem* h, int storage) {
+    g_last_error.clear();
+    if (!h) return set_error(FDE_ERR_ARG, "NULL problem");
+    if (storage != FDE_STORAGE_FP32 && storage != FDE_STORAGE_BF16)
+        return set_error(FDE_ERR_ARG, "storage must be FDE_STORAGE_FP32 or FDE_STORAGE_BF16");
+    h->P.strip_storage = storage;
+    return FDE_OK;
+}
+
 int strang_precond_factor(fde_problem* h, int precision) {
     g_last_error.clear();
     if (!h) return set_error(FDE_ERR_ARG, "NULL problem");

@@ -213,6 +213,8 @@ struct Problem {
     void* d_strips = nullptr;
     size_t strips_bytes = 0;
     bool strips_ok = false;
+    bool strips_bf16 = false;  // the copy holds bfloat16 values (fde_factor_storage)
+    int strip_storage = FDE_STORAGE_FP32;
     // Strang-type BCCB preconditioner (bccb_precond_setup): the spectra K_k of the
     // circulant inverses, k = 0..s/2, length L each, and its frequency-side vectors
     int precond = 0;            // FDE_PRECOND_STRANG or FDE_PRECOND_BCCB / FDE_PRECOND_BCCB_MODIFIED

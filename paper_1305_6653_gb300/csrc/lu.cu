@@ -506,27 +506,59 @@ __device__ __forceinline__ void tile_async(T* dst, const T* plane, int mp, int r
     tile_async<T>(dst, plane + (size_t)r0 * mp + c0, (size_t)mp, lane);
 }
 
-// Factor planes in one of two layouts: row-major (element (r, c) at r m_p + c) or
-// strip-major (32-column strips one after the other, each strip's rows contiguous:
-// (c / 32) 32 m_p + 32 r + c mod 32), where every strip of the block solves is one
-// sequential stream.  The tensor-core LU writes the final factor in both.
-template <bool STRIPS>
+// Factor planes as the block solves read them (LAY): 0 row-major in the compute type
+// (element (r, c) at r m_p + c); 1 strip-major in the compute type (32-column strips
+// one after the other, each strip's rows contiguous: (c / 32) 32 m_p + 32 r + c mod 32),
+// so every strip of a sweep is one sequential stream; 2 strip-major in bfloat16 (FP32
+// compute).  The tensor-core LU writes the final factor row-major and, where it can,
+// in one of the strip-major forms as well.
+constexpr int LAY_PLANES = 0, LAY_STRIPS = 1, LAY_STRIPS_BF16 = 2;
+template <int LAY>
 __device__ __forceinline__ size_t fac_at(int mp, int r, int c) {
-    return STRIPS ? (size_t)(c >> 5) * 32 * mp + (size_t)r * 32 + (c & 31) : (size_t)r * mp + c;
+    return LAY != LAY_PLANES ? (size_t)(c >> 5) * 32 * mp + (size_t)r * 32 + (c & 31) : (size_t)r * mp + c;
 }
-template <typename T, bool STRIPS>
+template <typename T, int LAY>
 __device__ __forceinline__ void tile_async_l(T* dst, const T* plane, int mp, int r0, int c0, int lane) {
-    tile_async<T>(dst, plane + fac_at<STRIPS>(mp, r0, c0), STRIPS ? (size_t)32 : (size_t)mp, lane);
+    tile_async<T>(dst, plane + fac_at<LAY>(mp, r0, c0), LAY != LAY_PLANES ? (size_t)32 : (size_t)mp, lane);
+}
+// Element type of the factor as stored for layout LAY, and its streaming loads: four
+// consecutive entries of one row, widened to the compute type (a bfloat16 is the top
+// half of the float it came from, so the widening is exact).
+template <typename T, int LAY> struct fac_store {
+    using elem = T;
+    using raw = typename vec4<T>::type;
+    static __device__ __forceinline__ raw load(const elem* p) { return ld4(p); }
+    static __device__ __forceinline__ raw widen(const raw& v) { return v; }
+};
+template <> struct fac_store<float, LAY_STRIPS_BF16> {
+    using elem = unsigned short;
+    using raw = uint2;
+    static __device__ __forceinline__ raw load(const elem* p) { return __ldcs(reinterpret_cast<const uint2*>(p)); }
+    static __device__ __forceinline__ float4 widen(const raw& v) {
+        return make_float4(__uint_as_float(v.x << 16), __uint_as_float(v.x & 0xffff0000u),
+                           __uint_as_float(v.y << 16), __uint_as_float(v.y & 0xffff0000u));
+    }
+};
+// 32 x 32 bfloat16 tile of a strip (rows of 64 bytes, contiguous) -> shared rows of
+// TRSV_LDH elements (80 bytes: 16-byte aligned cp.async destinations).
+constexpr int TRSV_LDH = 40;
+__device__ __forceinline__ void tile_async_bf16(unsigned short* dst, const unsigned short* src, int lane) {
+    for (int e = lane; e < 32 * 4; e += 32) {
+        const int r = e >> 2, ch = e & 3;
+        cp_async16(dst + r * TRSV_LDH + ch * 8, src + r * 32 + ch * 8);
+    }
 }
 
 // Solver side of one sweep (warp 0).  INV: the inverted diagonal tiles are given
 // (tinv: per tile [L^-1 re, L^-1 im, U^-1 re, U^-1 im][32][32]) and a tile solve is
 // the product x = D^-1 a; otherwise the tile is solved by substitution.
-template <typename T, bool FWD, bool INV, int NT, bool STRIPS = false>
-__device__ __forceinline__ void trsv_solver(int mp, int nt, const T* re, const T* im, const cplx_t<T>* dv,
+template <typename T, bool FWD, bool INV, int NT, int LAY = LAY_PLANES>
+__device__ __forceinline__ void trsv_solver(int mp, int nt, const typename fac_store<T, LAY>::elem* re,
+                                            const typename fac_store<T, LAY>::elem* im, const cplx_t<T>* dv,
                                             const T* tinv, cplx_t<T>* y, cplx_t<T> (*xs)[32], T* tiles,
                                             cplx_t<T>* av, int lane) {
     using C = cplx_t<T>;
+    static_assert(INV || LAY != LAY_STRIPS_BF16, "substitution reads the diagonal tiles in the compute type");
     constexpr int LD = trsv_tile<T>::LD, TS = 32 * LD;
     auto tile_of = [&](int d) { return FWD ? d : nt - 1 - d; };
     auto issue = [&](int d) {
@@ -536,13 +568,19 @@ __device__ __forceinline__ void trsv_solver(int mp, int nt, const T* re, const T
             const T* ti = tinv + (size_t)j * 4096 + (FWD ? 0 : 2048);
             tile_async<T>(b, ti, 32, lane);
             tile_async<T>(b + TS, ti + 1024, 32, lane);
-        } else {
-            tile_async_l<T, STRIPS>(b, re, mp, 32 * j, 32 * j, lane);
-            tile_async_l<T, STRIPS>(b + TS, im, mp, 32 * j, 32 * j, lane);
+        } else if constexpr (LAY != LAY_STRIPS_BF16) {
+            tile_async_l<T, LAY>(b, re, mp, 32 * j, 32 * j, lane);
+            tile_async_l<T, LAY>(b + TS, im, mp, 32 * j, 32 * j, lane);
         }
         if (d >= 1) {
-            tile_async_l<T, STRIPS>(b + 2 * TS, re, mp, 32 * j, 32 * tile_of(d - 1), lane);
-            tile_async_l<T, STRIPS>(b + 3 * TS, im, mp, 32 * j, 32 * tile_of(d - 1), lane);
+            if constexpr (LAY == LAY_STRIPS_BF16) {  // bfloat16 rows in the L slots
+                const size_t o = fac_at<LAY>(mp, 32 * j, 32 * tile_of(d - 1));
+                tile_async_bf16(reinterpret_cast<unsigned short*>(b + 2 * TS), re + o, lane);
+                tile_async_bf16(reinterpret_cast<unsigned short*>(b + 3 * TS), im + o, lane);
+            } else {
+                tile_async_l<T, LAY>(b + 2 * TS, re, mp, 32 * j, 32 * tile_of(d - 1), lane);
+                tile_async_l<T, LAY>(b + 3 * TS, im, mp, 32 * j, 32 * tile_of(d - 1), lane);
+            }
         }
     };
     issue(0);
@@ -568,8 +606,20 @@ __device__ __forceinline__ void trsv_solver(int mp, int nt, const T* re, const T
 #pragma unroll
             for (int c = 0; c < 32; c += 2) {
                 const C x0 = xp[c], x1 = xp[c + 1];
-                const T l0r = Lre[lane * LD + c], l0i = Lim[lane * LD + c];
-                const T l1r = Lre[lane * LD + c + 1], l1i = Lim[lane * LD + c + 1];
+                T l0r, l0i, l1r, l1i;
+                if constexpr (LAY == LAY_STRIPS_BF16) {  // a pair of bfloat16 per 32-bit word
+                    const uint32_t wr = reinterpret_cast<const uint32_t*>(Lre)[lane * (TRSV_LDH / 2) + c / 2];
+                    const uint32_t wi = reinterpret_cast<const uint32_t*>(Lim)[lane * (TRSV_LDH / 2) + c / 2];
+                    l0r = __uint_as_float(wr << 16);
+                    l1r = __uint_as_float(wr & 0xffff0000u);
+                    l0i = __uint_as_float(wi << 16);
+                    l1i = __uint_as_float(wi & 0xffff0000u);
+                } else {
+                    l0r = Lre[lane * LD + c];
+                    l0i = Lim[lane * LD + c];
+                    l1r = Lre[lane * LD + c + 1];
+                    l1i = Lim[lane * LD + c + 1];
+                }
                 sx0 = fma(-l0i, x0.y, fma(l0r, x0.x, sx0));
                 sy0 = fma(l0i, x0.x, fma(l0r, x0.y, sy0));
                 sx1 = fma(-l1i, x1.y, fma(l1r, x1.x, sx1));
@@ -635,11 +685,13 @@ __device__ __forceinline__ void trsv_solver(int mp, int nt, const T* re, const T
 // the shuffles stay warp-uniform.  Two register buffers of H rows alternate: the
 // loads of one are in flight while the other is applied, so the load pipe does
 // not drain between batches.
-template <typename T, bool FWD, int NT, int H, bool STRIPS = false>
-__device__ __forceinline__ void trsv_stream(int mp, int nt, const T* re, const T* im, cplx_t<T>* y,
+template <typename T, bool FWD, int NT, int H, int LAY = LAY_PLANES>
+__device__ __forceinline__ void trsv_stream(int mp, int nt, const typename fac_store<T, LAY>::elem* re,
+                                            const typename fac_store<T, LAY>::elem* im, cplx_t<T>* y,
                                             const cplx_t<T> (*xs)[32], int bt) {
     using C = cplx_t<T>;
     using V = typename vec4<T>::type;
+    using FS = fac_store<T, LAY>;
     constexpr int TRSV_GROUPS = (NT - 32) / TRSV_TPR;  // a multiple of 4 (NT is a multiple of 32)
     constexpr int HG = H * TRSV_GROUPS;
     static_assert(HG >= 32, "the first batch must cover tile d+2");
@@ -649,15 +701,15 @@ __device__ __forceinline__ void trsv_stream(int mp, int nt, const T* re, const T
         const int lo = FWD ? 32 * (d + 2) : 0;
         const int hi = FWD ? mp : 32 * (nt - 2 - d);
         const int len = hi - lo;
-        V ar[2][H], ai[2][H];
+        typename FS::raw ar[2][H], ai[2][H];
         auto load = [&](int b, int q0) {
 #pragma unroll
             for (int u = 0; u < H; ++u) {
                 const int q = q0 + u * TRSV_GROUPS;
                 if (q < len) {
                     const int r = FWD ? lo + q : hi - 1 - q;
-                    ar[b][u] = ld4(re + fac_at<STRIPS>(mp, r, col));
-                    ai[b][u] = ld4(im + fac_at<STRIPS>(mp, r, col));
+                    ar[b][u] = FS::load(re + fac_at<LAY>(mp, r, col));
+                    ai[b][u] = FS::load(im + fac_at<LAY>(mp, r, col));
                 }
             }
         };
@@ -666,8 +718,8 @@ __device__ __forceinline__ void trsv_stream(int mp, int nt, const T* re, const T
 #pragma unroll
             for (int u = 0; u < H; ++u) {
                 const int q = q0 + u * TRSV_GROUPS;
-                const V& vr = ar[b][u];
-                const V& vi = ai[b][u];
+                const V vr = FS::widen(ar[b][u]);
+                const V vi = FS::widen(ai[b][u]);
                 // explicit fused multiply-adds: the same rounding in every launch shape
                 T sx = vr.x * x0.x;
                 sx = fma(-vi.x, x0.y, sx);
@@ -707,6 +759,95 @@ __device__ __forceinline__ void trsv_stream(int mp, int nt, const T* re, const T
         x2 = xs[d & 1][sub * 4 + 2];
         x3 = xs[d & 1][sub * 4 + 3];
         apply(0, g);  // covers q < 32 (tile d+2): groups 0..31, u = 0
+        named_arrive(TRSV_BAR_B + (d & 1), NT);
+        for (int q0 = g + HG; q0 < len; q0 += 2 * HG) {
+            load(0, q0 + HG);
+            apply(1, q0);
+            if (q0 + HG >= len) break;
+            load(1, q0 + 2 * HG);
+            apply(0, q0 + HG);
+        }
+    }
+}
+
+// Streaming side for the bfloat16 strip copy: a row's 32 entries of a strip are 64
+// bytes, so four lanes take a row, eight entries (one 16-byte load per plane) each, and
+// a warp's load covers eight consecutive rows (512 contiguous bytes).  Row groups of a
+// warp hold q values of one aligned octet (GROUPS is a multiple of 8), so the loop exits
+// and shuffles stay warp-uniform.  Otherwise as trsv_stream; every launch shape sums a
+// row's products in the same order, so the shapes agree bit for bit.
+constexpr int TRSV_TPR_H = 4;  // threads per row of the bfloat16 stream
+__device__ __forceinline__ void widen8(const uint4& v, float* f) {
+    f[0] = __uint_as_float(v.x << 16); f[1] = __uint_as_float(v.x & 0xffff0000u);
+    f[2] = __uint_as_float(v.y << 16); f[3] = __uint_as_float(v.y & 0xffff0000u);
+    f[4] = __uint_as_float(v.z << 16); f[5] = __uint_as_float(v.z & 0xffff0000u);
+    f[6] = __uint_as_float(v.w << 16); f[7] = __uint_as_float(v.w & 0xffff0000u);
+}
+template <bool FWD, int NT, int H>
+__device__ __forceinline__ void trsv_stream_bf16(int mp, int nt, const unsigned short* re, const unsigned short* im,
+                                                 float2* y, const float2 (*xs)[32], int bt) {
+    constexpr int GROUPS = (NT - 32) / TRSV_TPR_H;
+    constexpr int HG = H * GROUPS;
+    static_assert(GROUPS % 8 == 0, "a warp's row groups must form aligned octets");
+    static_assert(HG >= 32, "the first batch must cover tile d+2");
+    const int g = bt / TRSV_TPR_H, sub = bt % TRSV_TPR_H;
+    for (int d = 0; d + 2 < nt; ++d) {
+        const int col = 32 * (FWD ? d : nt - 1 - d) + sub * 8;
+        const int lo = FWD ? 32 * (d + 2) : 0;
+        const int hi = FWD ? mp : 32 * (nt - 2 - d);
+        const int len = hi - lo;
+        uint4 ar[2][H], ai[2][H];
+        auto load = [&](int b, int q0) {
+#pragma unroll
+            for (int u = 0; u < H; ++u) {
+                const int q = q0 + u * GROUPS;
+                if (q < len) {
+                    const int r = FWD ? lo + q : hi - 1 - q;
+                    const size_t o = fac_at<LAY_STRIPS_BF16>(mp, r, col);
+                    ar[b][u] = __ldcs(reinterpret_cast<const uint4*>(re + o));
+                    ai[b][u] = __ldcs(reinterpret_cast<const uint4*>(im + o));
+                }
+            }
+        };
+        float2 x[8];
+        auto apply = [&](int b, int q0) {
+#pragma unroll
+            for (int u = 0; u < H; ++u) {
+                const int q = q0 + u * GROUPS;
+                float vr[8], vi[8];
+                widen8(ar[b][u], vr);
+                widen8(ai[b][u], vi);
+                float sx = vr[0] * x[0].x;
+                sx = fmaf(-vi[0], x[0].y, sx);
+                float sy = vr[0] * x[0].y;
+                sy = fmaf(vi[0], x[0].x, sy);
+#pragma unroll
+                for (int c = 1; c < 8; ++c) {
+                    sx = fmaf(vr[c], x[c].x, sx);
+                    sx = fmaf(-vi[c], x[c].y, sx);
+                    sy = fmaf(vr[c], x[c].y, sy);
+                    sy = fmaf(vi[c], x[c].x, sy);
+                }
+#pragma unroll
+                for (int off = 1; off < TRSV_TPR_H; off <<= 1) {
+                    sx += __shfl_xor_sync(0xffffffffu, sx, off);
+                    sy += __shfl_xor_sync(0xffffffffu, sy, off);
+                }
+                if (sub == 0 && q < len) {
+                    const int r = FWD ? lo + q : hi - 1 - q;
+                    float2 v = y[r];
+                    v.x -= sx;
+                    v.y -= sy;
+                    y[r] = v;
+                }
+            }
+        };
+        load(0, g);  // independent of x_d: in flight across the wait
+        load(1, g + HG);
+        named_sync(TRSV_BAR_X + (d & 1), NT);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) x[c] = xs[d & 1][sub * 8 + c];
+        apply(0, g);  // covers q < 32 (tile d+2)
         named_arrive(TRSV_BAR_B + (d & 1), NT);
         for (int q0 = g + HG; q0 < len; q0 += 2 * HG) {
             load(0, q0 + HG);
@@ -904,8 +1045,9 @@ block_trsv_ring_kernel(int mp, const T* __restrict__ fac, const cplx_t<T>* __res
     for (int i = threadIdx.x; i < mp; i += blockDim.x) x[i] = y[i];
 }
 
-template <typename T, bool INV, int NT = TRSV_THREADS, int H = trsv_unroll<T>::value / 2, bool STRIPS = false>
-__device__ __forceinline__ void trsv_body(int mp, const T* __restrict__ re, const cplx_t<T>* __restrict__ dv,
+template <typename T, bool INV, int NT = TRSV_THREADS, int H = trsv_unroll<T>::value / 2, int LAY = LAY_PLANES>
+__device__ __forceinline__ void trsv_body(int mp, const typename fac_store<T, LAY>::elem* __restrict__ re,
+                                          const cplx_t<T>* __restrict__ dv,
                                           const T* __restrict__ tinv, cplx_t<T>* __restrict__ x) {
     using C = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -913,26 +1055,38 @@ __device__ __forceinline__ void trsv_body(int mp, const T* __restrict__ re, cons
     T* tiles = reinterpret_cast<T*>(y + mp);      // solver tiles
     __shared__ C xs[2][32];
     __shared__ C av[32];
-    const T* im = re + (size_t)mp * mp;
+    const auto* im = re + (size_t)mp * mp;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nt = mp / 32;
     for (int i = threadIdx.x; i < mp; i += blockDim.x) y[i] = x[i];
     __syncthreads();
-    if (warp == 0) trsv_solver<T, true, INV, NT, STRIPS>(mp, nt, re, im, dv, tinv, y, xs, tiles, av, lane);
-    else trsv_stream<T, true, NT, H, STRIPS>(mp, nt, re, im, y, xs, threadIdx.x - 32);
-    __syncthreads();
-    if (warp == 0) trsv_solver<T, false, INV, NT, STRIPS>(mp, nt, re, im, dv, tinv, y, xs, tiles, av, lane);
-    else trsv_stream<T, false, NT, H, STRIPS>(mp, nt, re, im, y, xs, threadIdx.x - 32);
+    if constexpr (LAY == LAY_STRIPS_BF16) {
+        if (warp == 0) trsv_solver<T, true, INV, NT, LAY>(mp, nt, re, im, dv, tinv, y, xs, tiles, av, lane);
+        else trsv_stream_bf16<true, NT, H>(mp, nt, re, im, y, xs, threadIdx.x - 32);
+        __syncthreads();
+        if (warp == 0) trsv_solver<T, false, INV, NT, LAY>(mp, nt, re, im, dv, tinv, y, xs, tiles, av, lane);
+        else trsv_stream_bf16<false, NT, H>(mp, nt, re, im, y, xs, threadIdx.x - 32);
+    } else {
+        if (warp == 0) trsv_solver<T, true, INV, NT, LAY>(mp, nt, re, im, dv, tinv, y, xs, tiles, av, lane);
+        else trsv_stream<T, true, NT, H, LAY>(mp, nt, re, im, y, xs, threadIdx.x - 32);
+        __syncthreads();
+        if (warp == 0) trsv_solver<T, false, INV, NT, LAY>(mp, nt, re, im, dv, tinv, y, xs, tiles, av, lane);
+        else trsv_stream<T, false, NT, H, LAY>(mp, nt, re, im, y, xs, threadIdx.x - 32);
+    }
     __syncthreads();
     for (int i = threadIdx.x; i < mp; i += blockDim.x) x[i] = y[i];
 }
 
-template <typename T, int V = 0, bool STRIPS = false>
+// (The bfloat16 stream loads 16 bytes per lane and plane like the FP32 one, so it keeps
+// the shape's rows per register buffer, at most 7: its eight x values per lane take the
+// registers of an eighth row.)
+template <typename T, int V = 0, int LAY = LAY_PLANES>
 __global__ void __launch_bounds__(trsv_shape<T, V>::NT)
-block_trsv_kernel(int mp, const T* __restrict__ fac, const cplx_t<T>* __restrict__ dinv, const T* __restrict__ tinv,
-                  cplx_t<T>* __restrict__ rhat) {
+block_trsv_kernel(int mp, const typename fac_store<T, LAY>::elem* __restrict__ fac,
+                  const cplx_t<T>* __restrict__ dinv, const T* __restrict__ tinv, cplx_t<T>* __restrict__ rhat) {
     const int k = blockIdx.x;
-    trsv_body<T, true, trsv_shape<T, V>::NT, trsv_shape<T, V>::H, STRIPS>(mp, fac + (size_t)k * 2 * mp * mp,
+    constexpr int H = LAY == LAY_STRIPS_BF16 && trsv_shape<T, V>::H > 7 ? 7 : trsv_shape<T, V>::H;
+    trsv_body<T, true, trsv_shape<T, V>::NT, H, LAY>(mp, fac + (size_t)k * 2 * mp * mp,
                                                                   dinv + (size_t)k * mp,
                                                                   tinv + (size_t)k * (mp / 32) * 4096,
                                                                   rhat + (size_t)k * mp);
@@ -1500,7 +1654,7 @@ template <int KIND>
 __device__ __forceinline__ void diag128_body(int mp, int o, float* __restrict__ re, float2* __restrict__ dk,
                                              int* __restrict__ info, unsigned char* __restrict__ pA, bool invert,
                                              unsigned char* __restrict__ psave = nullptr,
-                                             float* __restrict__ strips = nullptr) {
+                                             void* __restrict__ strips = nullptr, bool strips_bf16 = false) {
     using Cfg = Tc2<KIND>;
     constexpr int LD = D128_LD;
     extern __shared__ __align__(16) float dsm[];
@@ -1617,9 +1771,17 @@ __device__ __forceinline__ void diag128_body(int mp, int o, float* __restrict__ 
         *reinterpret_cast<float4*>(re + g) = make_float4(pr[0], pr[1], pr[2], pr[3]);
         *reinterpret_cast<float4*>(im + g) = make_float4(pi[0], pi[1], pi[2], pi[3]);
         if (strips) {  // the strip-major copy of the final factor
-            const size_t gs = fac_at<true>(mp, o + r, o + c);
-            *reinterpret_cast<float4*>(strips + gs) = make_float4(pr[0], pr[1], pr[2], pr[3]);
-            *reinterpret_cast<float4*>(strips + (size_t)mp * mp + gs) = make_float4(pi[0], pi[1], pi[2], pi[3]);
+            const size_t gs = fac_at<LAY_STRIPS>(mp, o + r, o + c);
+            if (strips_bf16) {
+                unsigned short* sb = static_cast<unsigned short*>(strips);
+                *reinterpret_cast<uint2*>(sb + gs) = make_uint2(bf16x2_bits(pr[0], pr[1]), bf16x2_bits(pr[2], pr[3]));
+                *reinterpret_cast<uint2*>(sb + (size_t)mp * mp + gs) =
+                    make_uint2(bf16x2_bits(pi[0], pi[1]), bf16x2_bits(pi[2], pi[3]));
+            } else {
+                float* sf = static_cast<float*>(strips);
+                *reinterpret_cast<float4*>(sf + gs) = make_float4(pr[0], pr[1], pr[2], pr[3]);
+                *reinterpret_cast<float4*>(sf + (size_t)mp * mp + gs) = make_float4(pi[0], pi[1], pi[2], pi[3]);
+            }
         }
     }
     if (!invert || W != TB) return;
@@ -1851,12 +2013,13 @@ __global__ void __launch_bounds__(D128_THREADS)
 lu_diag128_kernel(int mp, int o, float* __restrict__ fac, float2* __restrict__ dinv, int* __restrict__ info,
                   unsigned char* __restrict__ ipack, size_t ipack_stride, int invert,
                   unsigned char* __restrict__ dsave = nullptr, size_t dsave_stride = 0,
-                  float* __restrict__ strips = nullptr) {
+                  void* __restrict__ strips = nullptr, int strips_bf16 = 0) {
     const int k = blockIdx.x;
+    const size_t soff = (size_t)k * 2 * mp * mp * (strips_bf16 ? 2 : 4);
     diag128_body<KIND>(mp, o, fac + (size_t)k * 2 * mp * mp, dinv + (size_t)k * mp, info + k,
                        ipack ? ipack + (size_t)k * ipack_stride : nullptr, invert != 0,
                        dsave ? dsave + (size_t)k * dsave_stride : nullptr,
-                       strips ? strips + (size_t)k * 2 * mp * mp : nullptr);
+                       strips ? static_cast<unsigned char*>(strips) + soff : nullptr, strips_bf16 != 0);
 }
 
 // Batched: blocks with m_p > o (a prefix of the table sorted by m_p).
@@ -1933,22 +2096,25 @@ template <int KIND>
 __global__ void __launch_bounds__(128)
 lu_panel_tc2_kernel(int mp, int o, int R0, int ntr, float* __restrict__ fac, const unsigned char* __restrict__ apack,
                     const unsigned char* __restrict__ bpack, const unsigned char* __restrict__ ipack, size_t pa,
-                    size_t pb, size_t pi, int* __restrict__ err, int strips,
+                    size_t pb, size_t pi, int* __restrict__ err, int strips, unsigned short* __restrict__ sbf,
                     const __grid_constant__ CUtensorMap fmap, const __grid_constant__ CUtensorMap smap) {
     using Cfg = Tc2<KIND>;
     const int k = blockIdx.y, x = blockIdx.x;
     float* re = fac + (size_t)k * 2 * mp * mp;
+    // strips: 1 FP32 copy through smap, 2 bfloat16 copy at sbf (block k at 2 k m_p^2)
     const CUtensorMap* fm = strips ? &fmap : nullptr;
-    const CUtensorMap* sm = strips ? &smap : nullptr;
+    const CUtensorMap* sm = strips == 1 ? &smap : nullptr;
+    unsigned short* sb = strips == 2 ? sbf + (size_t)k * 2 * mp * mp : nullptr;
     const unsigned char* ip = ipack + (size_t)k * pi;
     // D is packed over the operand tile it was computed from (A21 -> L21, A12 -> U12)
     if (x < ntr) {
         unsigned char* at = const_cast<unsigned char*>(apack) + (size_t)k * pa + (size_t)x * Cfg::A_TILE;
         tc2_tile_body<KIND, true>(mp, R0 + x * T2_BM, o, re, at, ip + Cfg::A_TILE, err, at, 0, nullptr, nullptr, fm,
-                                  sm, k);
+                                  sm, k, sb);
     } else {
         unsigned char* bt = const_cast<unsigned char*>(bpack) + (size_t)k * pb + (size_t)(x - ntr) * Cfg::B_TILE;
-        tc2_tile_body<KIND, true>(mp, o, R0 + (x - ntr) * T2_BN, re, ip, bt, err, bt, 1, nullptr, nullptr, fm, sm, k);
+        tc2_tile_body<KIND, true>(mp, o, R0 + (x - ntr) * T2_BN, re, ip, bt, err, bt, 1, nullptr, nullptr, fm, sm, k,
+                                  sb);
     }
 }
 
@@ -2036,7 +2202,7 @@ static int run_lu_tc(Problem& P, cudaStream_t st) {
     FDE_CUDA_TRY(cudaFuncSetAttribute(lu_diag128_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)diag128_smem()));
     FDE_CUDA_TRY(cudaFuncSetAttribute(lu_panel_tc2_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      Cfg::SMEM_STORE));
+                                      Cfg::SMEM_STORE_EPI));
     if ((rc = ensure_lu_streams(P))) return rc;
     cudaStream_t sh = P.lu_hi, sl = P.lu_lo, sx = P.lu_x;
     // inverted diagonal blocks kept for the tensor-core block solves (TF32, whole 128-row strips)
@@ -2060,9 +2226,10 @@ static int run_lu_tc(Problem& P, cudaStream_t st) {
     }
     // the strip-major copy of the factor for the block solves (whole 128-wide panels); without
     // the memory for it the block solves read the row-major planes
-    float* strips = nullptr;
+    void* strips = nullptr;
+    const bool sbf16 = P.strip_storage == FDE_STORAGE_BF16;
     if (mp % TB == 0) {
-        const size_t sneed = (size_t)nb * 2 * mp * mp * sizeof(float);
+        const size_t sneed = (size_t)nb * 2 * mp * mp * (sbf16 ? 2 : 4);
         if (P.strips_bytes < sneed) {
             ++P.graph_gen;  // captured block solves may hold the old copy's address
             if (P.d_strips) {
@@ -2073,11 +2240,12 @@ static int run_lu_tc(Problem& P, cudaStream_t st) {
             P.strips_bytes = 0;
             if (dev_alloc(&P.d_strips, sneed) == FDE_OK) P.strips_bytes = sneed;
         }
-        strips = reinterpret_cast<float*>(P.d_strips);
+        strips = P.d_strips;
     }
     CUtensorMap cmap{}, smap{};
     if ((merge || strips) && (rc = factor_tensor_map_sw128(fac, mp, nb, &cmap))) return rc;
-    if (strips && (rc = strip_tensor_map_sw128(strips, mp, nb, &smap))) return rc;
+    if (strips && !sbf16 && (rc = strip_tensor_map_sw128(strips, mp, nb, &smap))) return rc;
+    const int smode = strips ? (sbf16 ? 2 : 1) : 0;
     FDE_CUDA_TRY(cudaEventRecord(P.lu_ev[0], st));  // fork after the work already queued on st
     FDE_CUDA_TRY(cudaStreamWaitEvent(sh, P.lu_ev[0], 0));
     FDE_CUDA_TRY(cudaStreamWaitEvent(sl, P.lu_ev[0], 0));
@@ -2093,7 +2261,7 @@ static int run_lu_tc(Problem& P, cudaStream_t st) {
             StageTimer t(P, FDE_STAGE_LU_DIAG, sh);
             lu_diag128_kernel<KIND><<<nb, D128_THREADS, diag128_smem(), sh>>>(
                 mp, o, fac, dinv, P.d_info, ipack, pi, (more || dsave) ? 1 : 0,
-                dsave ? dsave + (size_t)(o / TB) * 2 * Cfg::A_TILE : nullptr, dtile_stride, strips);
+                dsave ? dsave + (size_t)(o / TB) * 2 * Cfg::A_TILE : nullptr, dtile_stride, strips, sbf16 ? 1 : 0);
             FDE_LAUNCH_CHECK("lu_diag128_kernel");
         }
         if (after_cross) FDE_CUDA_TRY(cudaStreamWaitEvent(sh, P.lu_ev[4], 0));
@@ -2108,10 +2276,9 @@ static int run_lu_tc(Problem& P, cudaStream_t st) {
         }
         {  // the products also pack L21 / U12 as the update's operand tiles
             StageTimer t(P, FDE_STAGE_LU_PANEL_TC, sh);
-            lu_panel_tc2_kernel<KIND><<<dim3(2 * nt, nb), 128, Cfg::SMEM_STORE, sh>>>(mp, o, R0, nt, fac, apk(o),
-                                                                                    bpk(o), ipack, pa, pb, pi,
-                                                                                    P.d_err, strips ? 1 : 0,
-                                                                                    cmap, smap);
+            lu_panel_tc2_kernel<KIND><<<dim3(2 * nt, nb), 128, Cfg::SMEM_STORE_EPI, sh>>>(
+                mp, o, R0, nt, fac, apk(o), bpk(o), ipack, pa, pb, pi, P.d_err, smode,
+                static_cast<unsigned short*>(strips), cmap, smap);
             FDE_LAUNCH_CHECK("lu_panel_tc2_kernel");
         }
         return FDE_OK;
@@ -2201,7 +2368,11 @@ static int run_lu_tc(Problem& P, cudaStream_t st) {
         return FDE_OK;
     };
     rc = body();
-    P.strips_ok = rc == FDE_OK && strips != nullptr;
+    // the captured block solves name the layout they read: a change of it retires them
+    const bool ok_now = rc == FDE_OK && strips != nullptr;
+    if (ok_now != P.strips_ok || (ok_now && sbf16 != P.strips_bf16)) ++P.graph_gen;
+    P.strips_ok = ok_now;
+    P.strips_bf16 = sbf16;
     // join: st continues after all three streams
     cudaEventRecord(P.lu_ev[1], sl);
     cudaStreamWaitEvent(st, P.lu_ev[1], 0);
@@ -2448,13 +2619,27 @@ int launch_block_lu(Problem& P, int prec, cudaStream_t st) {
 template <typename T, int V>
 static int launch_trsv_shape(const Problem& P, void* rhat, cudaStream_t st) {
     const size_t smem = trsv_smem_bytes(P.mp, sizeof(T));
-    // the strip-major copy of the factor, where the tensor-core LU wrote one
+    // the strip-major copy of the factor (FP32 or bfloat16), where the tensor-core LU wrote one
     const bool strips = sizeof(T) == 4 && P.strips_ok && P.d_strips;
-    auto kern = strips ? block_trsv_kernel<T, V, true> : block_trsv_kernel<T, V, false>;
-    FDE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<P.nblk, trsv_shape<T, V>::NT, smem, st>>>(P.mp, (const T*)(strips ? P.d_strips : P.d_fac),
-                                                      (const cplx_t<T>*)P.d_dinv, (const T*)P.d_tinv,
-                                                      (cplx_t<T>*)rhat);
+    if constexpr (sizeof(T) == 4) {
+        if (strips && P.strips_bf16) {
+            auto kern = block_trsv_kernel<T, V, LAY_STRIPS_BF16>;
+            FDE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            kern<<<P.nblk, trsv_shape<T, V>::NT, smem, st>>>(P.mp, (const unsigned short*)P.d_strips,
+                                                              (const cplx_t<T>*)P.d_dinv, (const T*)P.d_tinv,
+                                                              (cplx_t<T>*)rhat);
+            FDE_LAUNCH_CHECK("block_trsv_kernel");
+            return FDE_OK;
+        }
+    }
+    {
+        constexpr int LS = sizeof(T) == 4 ? LAY_STRIPS : LAY_PLANES;  // FP64 factors have no copy
+        auto kern = strips ? block_trsv_kernel<T, V, LS> : block_trsv_kernel<T, V, LAY_PLANES>;
+        FDE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        kern<<<P.nblk, trsv_shape<T, V>::NT, smem, st>>>(P.mp, (const T*)(strips ? P.d_strips : P.d_fac),
+                                                          (const cplx_t<T>*)P.d_dinv, (const T*)P.d_tinv,
+                                                          (cplx_t<T>*)rhat);
+    }
     FDE_LAUNCH_CHECK("block_trsv_kernel");
     return FDE_OK;
 }

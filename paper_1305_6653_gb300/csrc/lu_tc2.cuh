@@ -73,7 +73,10 @@ struct Tc2 {
     // columns) share an SM.
     static constexpr int SMEM_STORE = T2_STAGES * STAGE;
     static_assert(3 * SMEM_STORE > 227 * 1024, "store mode: at most two CTAs per SM");
-    static_assert(SMEM_STORE >= 2 * 32768 + 1024, "store mode: two staged 32-column strips fit the freed ring");
+    // store mode with whole tiles: two staged 32-column strips of both planes in FP32
+    // (64 KB) and, for a bfloat16 strip copy, in bfloat16 (32 KB), at a 1024-byte boundary
+    static constexpr int SMEM_STORE_EPI = SMEM_STORE + 1024;
+    static_assert(SMEM_STORE_EPI >= 2 * 32768 + 2 * 16384 + 1024, "store mode: the staged strips fit the ring");
     static constexpr int KSTEP = KIND == 1 ? 16 : 8;          // K per MMA = 32 bytes = 2 core matrices
     static constexpr int MMAS = KCH / KSTEP;                  // MMAs per chunk (2)
     static constexpr uint32_t IDESC = tc::instr_desc(KIND == 1 ? 1u : 2u, T2_BM, 2 * T2_BN);
@@ -166,6 +169,12 @@ __device__ __forceinline__ void pack2_seg(unsigned char* tile, int rows, int row
             *reinterpret_cast<float4*>(tile + pack2_off<KIND>(rows, row, 2 * seg + kp0)) = b_side ? lo : hi;
         }
     }
+}
+
+// Two floats rounded to bfloat16 (to nearest even), the first in the low half.
+__device__ __forceinline__ uint32_t bf16x2_bits(float a, float b) {
+    return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(a)) |
+           ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(b)) << 16);
 }
 
 __device__ __forceinline__ void bulk_s2g(void* dst_gmem, const void* src_smem, uint32_t bytes) {
@@ -270,7 +279,7 @@ __device__ __forceinline__ void tc2_tile_body(int mp, int r0, int c0, float* __r
                                               const unsigned char* __restrict__ ga_old = nullptr,
                                               const unsigned char* __restrict__ gb_old = nullptr,
                                               const CUtensorMap* fmap = nullptr, const CUtensorMap* smap = nullptr,
-                                              int kblk = 0) {
+                                              int kblk = 0, unsigned short* __restrict__ sbf = nullptr) {
     using Cfg = Tc2<KIND>;
     const int nsteps = (ga_old ? 2 : 1) * Cfg::NIT;
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -380,11 +389,13 @@ __device__ __forceinline__ void tc2_tile_body(int mp, int r0, int c0, float* __r
         if (!cok && lane == 0) atomicCAS(err, 0, 2);
         done = __syncthreads_and(cok) != 0;
     }
-    if (STORE && ok && done && smap) {
+    if (STORE && ok && done && (smap || sbf)) {
         // D through shared memory: per 32-column strip, both planes staged with the 128-byte
         // swizzle in one of two buffers of the freed ring, then stored by tensor copies to the
         // row-major planes (fmap) and to the strip-major copy (smap), where the strip's 128
-        // rows are one contiguous 16 KB range.  Whole tiles only (m_p a multiple of 128).
+        // rows are one contiguous 16 KB range; or, for a bfloat16 copy (sbf: this block's), the
+        // strip also staged as bfloat16 rows of 64 bytes and stored by one bulk copy of 8 KB
+        // per plane.  Whole tiles only (m_p a multiple of 128).
         const int r = warp * 32 + lane;  // TMEM lane = tile row
         const uint32_t lane_addr = tbase + ((uint32_t)(warp * 32) << 16);
         unsigned char* sbuf = smem + ((1024u - (tc::smem_u32(smem) & 1023u)) & 1023u);
@@ -394,6 +405,8 @@ __device__ __forceinline__ void tc2_tile_body(int mp, int r0, int c0, float* __r
         for (int sx = 0; sx < T2_BN / 32; ++sx) {
             unsigned char* bre = sbuf + (sx & 1) * 32768;
             unsigned char* bim = bre + 16384;
+            unsigned char* hre = sbuf + 65536 + (sx & 1) * 16384;  // bfloat16 rows of 64 bytes
+            unsigned char* him = hre + 8192;
             if (sx >= 2) {  // the stores of strip sx - 2 have read this buffer
                 if (threadIdx.x == 0) bulk_wait_read_1();
                 __syncthreads();
@@ -412,6 +425,20 @@ __device__ __forceinline__ void tc2_tile_body(int mp, int r0, int c0, float* __r
                         make_float4(dr[4 * q], dr[4 * q + 1], dr[4 * q + 2], dr[4 * q + 3]);
                     *reinterpret_cast<float4*>(bim + off) =
                         make_float4(di[4 * q], di[4 * q + 1], di[4 * q + 2], di[4 * q + 3]);
+                }
+                if (sbf) {  // columns 16 h .. 16 h + 15 of row r: 32 bytes per plane
+                    uint32_t wr[8], wi[8];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        wr[e] = bf16x2_bits(dr[2 * e], dr[2 * e + 1]);
+                        wi[e] = bf16x2_bits(di[2 * e], di[2 * e + 1]);
+                    }
+                    uint4* hr = reinterpret_cast<uint4*>(hre + r * 64 + h * 32);
+                    uint4* hi = reinterpret_cast<uint4*>(him + r * 64 + h * 32);
+                    hr[0] = make_uint4(wr[0], wr[1], wr[2], wr[3]);
+                    hr[1] = make_uint4(wr[4], wr[5], wr[6], wr[7]);
+                    hi[0] = make_uint4(wi[0], wi[1], wi[2], wi[3]);
+                    hi[1] = make_uint4(wi[4], wi[5], wi[6], wi[7]);
                 }
                 if (pk && pk_side == 0) {  // L21 row r: K' = column (Re), TB + column (Im)
                     constexpr int EPS = Cfg::PER_CORE;
@@ -435,8 +462,14 @@ __device__ __forceinline__ void tc2_tile_body(int mp, int r0, int c0, float* __r
                 const int col = c0 + 32 * sx;
                 tma2d_store(fmap, col, yf + r0, bre);
                 tma2d_store(fmap, col, yf + mp + r0, bim);
-                tma2d_store(smap, 0, ys + (col >> 5) * mp + r0, bre);
-                tma2d_store(smap, 0, ys + (mp / 32 + (col >> 5)) * mp + r0, bim);
+                if (sbf) {  // 128 rows of strip col / 32 from row r0: 8 KB contiguous per plane
+                    unsigned short* g = sbf + (size_t)(col >> 5) * 32 * mp + (size_t)r0 * 32;
+                    bulk_s2g(g, hre, 8192);
+                    bulk_s2g(g + (size_t)mp * mp, him, 8192);
+                } else {
+                    tma2d_store(smap, 0, ys + (col >> 5) * mp + r0, bre);
+                    tma2d_store(smap, 0, ys + (mp / 32 + (col >> 5)) * mp + r0, bim);
+                }
                 bulk_commit();
             }
         }

@@ -39,12 +39,17 @@ def oracle_solution(setup):
     return x
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp64", "tf32", "tf32x3"])
-def test_fullsize_solve(setup, oracle_solution, precision):
+@pytest.mark.parametrize("precision,storage", [("fp32", "fp32"), ("fp64", "fp32"), ("tf32", "fp32"),
+                                               ("tf32x3", "fp32"), ("tf32", "bf16")])
+def test_fullsize_solve(setup, oracle_solution, precision, storage):
+    """storage: of the copy of the factors the block solves stream.  With bfloat16 the
+    preconditioner is the exact inverse of the factors rounded to 2^-9 per entry, so S z = r
+    holds only to that perturbation times the conditioning of the Strang blocks: measured
+    0.32 here (TF32 factors in FP32: 0.026), bound 0.5; the solution bound is the same."""
     from paper_1305_6653_gb300 import FDEProblem
     prob, J, b = setup
     with FDEProblem.from_inputs(prob, device_inputs=True) as p:
-        p.assemble().factor(precision)
+        p.assemble().factor(precision, storage=storage)
         x, st = p.solve(tol=1e-10, restart=20, maxit=400)
         xs = x.cpu().numpy()
         # preconditioner output satisfies S z = r (oracle Kronecker S)
@@ -56,7 +61,9 @@ def test_fullsize_solve(setup, oracle_solution, precision):
     err = np.linalg.norm(xs - oracle_solution) / np.linalg.norm(oracle_solution)
     assert err <= 1e-8, err
     srel = np.linalg.norm(O.strang_matvec(prob, z, J=J) - r) / np.linalg.norm(r)
-    assert srel <= {"fp64": 1e-11, "fp32": 1e-3, "tf32": 5e-2, "tf32x3": 1e-3}[precision], srel
+    print(precision, storage, "S z = r:", srel, "iterations", st["iterations"])
+    bound = {"fp64": 1e-11, "fp32": 1e-3, "tf32": 5e-2, "tf32x3": 1e-3}[precision]
+    assert srel <= (0.5 if storage == "bf16" else bound), srel
 
 
 def test_fullsize_factor_samples(setup):

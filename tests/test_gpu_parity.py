@@ -203,6 +203,47 @@ def test_solve_matches_direct_solution(name, make, precision):
     assert res <= 1e-10 and abs(res - st["rel_residual"]) <= 1e-11
 
 
+@pytest.mark.parametrize("precision", ["tf32", "bf16", "tf32x3"])
+@pytest.mark.parametrize("name,make", [("m255_s64", lambda: _variable(255, 64, "GBDF3", 1.7)),
+                                       ("m500_s16", lambda: _variable(500, 16, "GBDF3", 1.8))],
+                         ids=["m255_s64", "m500_s16"])
+def test_bf16_factor_storage(name, make, precision):
+    """Block solves from the bfloat16 copy of the factors (fde_factor_storage; m_p = 256 and
+    512, whole 128-wide panels, where the tensor-core LU writes the copy).  The solution
+    against the oracle (1e-8) and the true residual through the oracle's matvec; the
+    preconditioner is the exact inverse of the factors perturbed by bfloat16 rounding
+    (2^-9 relative per entry), so S z = r holds only to the factors' accuracy, and the
+    outer iteration pays at most a few iterations for it."""
+    from paper_1305_6653_gb300 import FDEProblem
+    prob = make()
+    if prob.n <= 5000:
+        ref = O.direct_solve(prob)
+    else:
+        ref, _, ok, _ = O.solve_strang_gmres(prob, side="right", tol=1e-12)
+        assert ok
+    J = O.j_of(prob)
+    r = np.random.default_rng(8).standard_normal(prob.n)
+    out = {}
+    for storage in ("fp32", "bf16"):
+        with FDEProblem.from_inputs(prob, device_inputs=True) as p:
+            p.assemble().factor(precision, storage=storage)
+            z = p.precond_apply(torch.as_tensor(r, device="cuda")).cpu().numpy()
+            x, st = p.solve(tol=1e-11, restart=20, maxit=400)
+            out[storage] = (z, x.cpu().numpy(), st)
+    zf, _, stf = out["fp32"]
+    zb, xb, stb = out["bf16"]
+    assert stb["status"] == 0, stb
+    assert np.linalg.norm(xb - ref) <= 1e-8 * np.linalg.norm(ref)
+    M_b = O.reduced_rhs(prob, J=J)
+    assert np.linalg.norm(M_b - O.matvec(prob, xb, J=J)) <= 1e-10 * np.linalg.norm(M_b)
+    assert not np.array_equal(zb, zf)
+    sf = np.linalg.norm(O.strang_matvec(prob, zf, J=J) - r) / np.linalg.norm(r)
+    sb = np.linalg.norm(O.strang_matvec(prob, zb, J=J) - r) / np.linalg.norm(r)
+    print(name, precision, "S z = r:", sf, sb, "iterations", stf["iterations"], stb["iterations"])
+    assert sb <= 0.2, (sf, sb)
+    assert stb["iterations"] <= stf["iterations"] + 3, (stf, stb)
+
+
 def test_small_config_iterations_are_paper_like():
     prob = fi.config_small()
     with _gpu(prob, "fp64") as p:
