@@ -1357,7 +1357,7 @@ def main():
             "tensor_core_update": tc_line, "matvec": matvec_line, "path_roofline": path_roof,
             "peaks_measured": measured,
             "launch_shapes": {"matvec": fde.fde_tune_query(0, mp, prob.s, "fp64"),
-                              "trsv": fde.fde_tune_query(1, mp, nblk, "fp64" if esz == 8 else "fp32")},
+                              "trsv": fde.fde_tune_query(1, mp, nblk, {8: "fp64", 4: "fp32", 2: "bf16"}[fac_esz])},
             "stage_ms_per_step": stage_ms, "stage_launches_per_step": stage_n,
             "stage_split_source": f"untimed profiled pass of {args.profile_steps} solves after the timed region "
                                   "(every stage with its own event pair, direct launches)",

@@ -444,7 +444,8 @@ long long fde_launch_count(void);
 #define FDE_TUNE_KERNELS 3
 /* variant -1: autotune (the default); 0 .. n-1: always launch that variant.
  * Before a shape is measured the built-in default runs (block solves with FP32
- * factors: 1, the 384 x 8 shape; LU interior update: 2; otherwise 0); measuring keeps the default unless
+ * factors: 1, the 384 x 8 shape; with the bfloat16 copy: 0, 512 threads; LU interior
+ * update: 2; otherwise 0); measuring keeps the default unless
  * another variant is faster by more than 2 % (median of five interleaved rounds).
  * Process-wide.  Errors: FDE_ERR_ARG. */
 int fde_tune_set(int kernel, int variant);
@@ -453,7 +454,9 @@ int fde_tune_set(int kernel, int variant);
 int fde_tune_cache(const char* path);
 /* The variant the table holds for a shape (nb: s for the matvec, s/2+1 for the block
  * solves), the forced variant when one is set, or -1 if the shape is not tuned yet.
- * Errors: FDE_ERR_ARG. */
+ * precision: FDE_FP64 or FDE_FP32 for the matvec; for the block solves the storage of
+ * the factors they read: FDE_FP64, FDE_FP32, or FDE_BF16 for the bfloat16 copy
+ * (fde_factor_storage).  Errors: FDE_ERR_ARG. */
 int fde_tune_query(int kernel, int mp, int nb, int precision, int* variant);
 
 /* Return the library's cached device memory to the CUDA driver.  Buffers freed by

@@ -2703,9 +2703,15 @@ int launch_block_trsv_variant(const Problem& P, void* rhat, int variant, cudaStr
     return launch_trsv_shape<float, 0>(P, rhat, st);
 }
 
+// The tuning key of the block solves: the storage of the factors they read (FP64,
+// FP32, or FDE_BF16 for the bfloat16 strip copy).
+static int trsv_key(const Problem& P) {
+    if (P.precision == FDE_FP64) return FDE_FP64;
+    return P.strips_ok && P.d_strips && P.strips_bf16 ? FDE_BF16 : FDE_FP32;
+}
+
 int launch_block_trsv(const Problem& P, void* rhat, cudaStream_t st) {
-    const int prec = P.precision == FDE_FP64 ? FDE_FP64 : FDE_FP32;  // factor storage
-    return launch_block_trsv_variant(P, rhat, tune_lookup(FDE_TUNE_TRSV, P.mp, P.nblk, prec, nullptr), st);
+    return launch_block_trsv_variant(P, rhat, tune_lookup(FDE_TUNE_TRSV, P.mp, P.nblk, trsv_key(P), nullptr), st);
 }
 
 namespace {
@@ -2723,7 +2729,7 @@ int trsv_trial(void* ctx, int v, cudaStream_t st) {
 // vector (zeroed first: the solves run in place and their timing does not depend on
 // the data), unless the table already has the shape or a variant is forced.
 int autotune_trsv(Problem& P) {
-    const int prec = P.precision == FDE_FP64 ? FDE_FP64 : FDE_FP32;
+    const int prec = trsv_key(P);
     bool need = false;
     tune_lookup(FDE_TUNE_TRSV, P.mp, P.nblk, prec, &need);
     if (!need) return FDE_OK;
