@@ -229,7 +229,7 @@ def matvec_flops(m: int, s: int, L: int, mu: int) -> float:
 FP64_PEAK_TFLOPS = 1.25  # GB300 nominal FP64 (no measured FP64 figure in MEASURED_PEAKS.json)
 # DRAM bytes / algorithmic bytes of block_trsv_kernel<float> (ncu, m=1023, s=256), by the
 # element size of the factor copy it streams (4: FP32, 2: bfloat16)
-TRSV_TRAFFIC_RATIO = {4: 1.034}
+TRSV_TRAFFIC_RATIO = {4: 1.034, 2: 1.098}
 
 
 def trsv_bytes(mp: int, nblk: int, esz: int, fac_esz: int | None = None) -> float:
