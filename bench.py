@@ -1112,7 +1112,8 @@ def main():
                 "tol_true_residual": args.tol, "restart": args.restart, "precision": args.precision,
                 "arnoldi_matvec": args.matvec if args.matvec == "fp64" else f"fp32 (relax {args.relax:g})",
                 "factor_storage": args.storage,
-                "l2": "flushed (512 MiB write) before every timed step; factors (4.3 GB fp32) exceed L2"}
+                "l2": "flushed (512 MiB write) before every timed step; factors (4.3 GB fp32; the bfloat16 copy the "
+                      "block solves read, 2.2 GB) exceed L2"}
 
     if args.impl == "reference":
         return bench_reference(args, rank, prob, workload)

@@ -286,9 +286,11 @@ int fde_batch_factor(fde_batch* b, int precision) {
         if (b->block_solver == FDE_BLOCK_SOLVE_TENSOR_CORES && !tc)
             return set_error(FDE_ERR_ARG, "tensor-core block solves need FDE_TF32 factors and 256 <= m_p <= 2048");
         P0w.save_dtile = tc;
+        P0w.want_strips = false;  // the shared-operator block solves read the factor planes
         b->trsm_tc = false;
         int rc = strang_precond_factor(b->probs[0], precision);
         P0w.save_dtile = false;
+        P0w.want_strips = true;
         if (rc) return rc;
         b->trsm_tc = tc && P0w.d_dtile != nullptr;
         const Problem& P0 = P0w;

@@ -215,6 +215,7 @@ struct Problem {
     bool strips_ok = false;
     bool strips_bf16 = false;  // the copy holds bfloat16 values (fde_factor_storage)
     int strip_storage = FDE_STORAGE_FP32;
+    bool want_strips = true;   // off for a shared-operator batch, whose solves read the planes
     // Strang-type BCCB preconditioner (bccb_precond_setup): the spectra K_k of the
     // circulant inverses, k = 0..s/2, length L each, and its frequency-side vectors
     int precond = 0;            // FDE_PRECOND_STRANG or FDE_PRECOND_BCCB / FDE_PRECOND_BCCB_MODIFIED

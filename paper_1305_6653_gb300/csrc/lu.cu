@@ -2228,7 +2228,7 @@ static int run_lu_tc(Problem& P, cudaStream_t st) {
     // the memory for it the block solves read the row-major planes
     void* strips = nullptr;
     const bool sbf16 = P.strip_storage == FDE_STORAGE_BF16;
-    if (mp % TB == 0) {
+    if (mp % TB == 0 && P.want_strips) {
         const size_t sneed = (size_t)nb * 2 * mp * mp * (sbf16 ? 2 : 4);
         if (P.strips_bytes < sneed) {
             ++P.graph_gen;  // captured block solves may hold the old copy's address
