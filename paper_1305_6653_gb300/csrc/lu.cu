@@ -1079,13 +1079,14 @@ __device__ __forceinline__ void trsv_body(int mp, const typename fac_store<T, LA
 
 // (The bfloat16 stream loads 16 bytes per lane and plane like the FP32 one, so it keeps
 // the shape's rows per register buffer, at most 7: its eight x values per lane take the
-// registers of an eighth row.)
+// registers of an eighth row; the 640-thread shape takes 3, which its registers allow.)
 template <typename T, int V = 0, int LAY = LAY_PLANES>
 __global__ void __launch_bounds__(trsv_shape<T, V>::NT)
 block_trsv_kernel(int mp, const typename fac_store<T, LAY>::elem* __restrict__ fac,
                   const cplx_t<T>* __restrict__ dinv, const T* __restrict__ tinv, cplx_t<T>* __restrict__ rhat) {
     const int k = blockIdx.x;
-    constexpr int H = LAY == LAY_STRIPS_BF16 && trsv_shape<T, V>::H > 7 ? 7 : trsv_shape<T, V>::H;
+    constexpr int HS = trsv_shape<T, V>::H;
+    constexpr int H = LAY != LAY_STRIPS_BF16 ? HS : HS > 7 ? 7 : HS == 2 ? 3 : HS;
     trsv_body<T, true, trsv_shape<T, V>::NT, H, LAY>(mp, fac + (size_t)k * 2 * mp * mp,
                                                                   dinv + (size_t)k * mp,
                                                                   tinv + (size_t)k * (mp / 32) * 4096,
