@@ -425,7 +425,9 @@ long long fde_launch_count(void);
  * time row: 1024, 512, 256, i.e. one, two or more CTAs per SM) and the block
  * triangular solves (512 threads with 4 rows per register buffer, 384 with 8, 640
  * with 2 -- reading a bfloat16 factor copy: 4, 7 and 3 -- or 512 threads fed by bulk
- * asynchronous copies through a ring of shared-memory stages).  By default the first use of a shape (the matvec in bvm_assemble, the
+ * asynchronous copies through a ring of shared-memory stages, which reads the FP32
+ * factors; with a bfloat16 copy that fourth setting launches the first shape, and the
+ * tuner times the three register shapes).  By default the first use of a shape (the matvec in bvm_assemble, the
  * block solves at the end of strang_precond_factor) times every variant with CUDA
  * events on the problem's stream and keeps the fastest for that shape (m_p, s or
  * s/2+1 blocks, precision) in a process-wide table, which is also appended to a text

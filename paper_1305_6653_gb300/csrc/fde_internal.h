@@ -302,8 +302,9 @@ int dev_release_cached();
 int tune_variants(int kernel);
 int tune_lookup(int kernel, int mp, int nb, int prec, bool* need_tuning);
 void tune_store(int kernel, int mp, int nb, int prec, int variant, const float* ms);  // ms: per variant, or NULL
+// ms_out: the median time of every variant, or NULL; nv > 0: only variants 0 .. nv-1
 int tune_measure(int kernel, cudaStream_t st, int (*fn)(void*, int, cudaStream_t), void* ctx, int* best,
-                 float* ms_out, int default_variant);  // ms_out: the median time of every variant, or NULL
+                 float* ms_out, int default_variant, int nv = 0);
 int tune_default_variant(int kernel, int prec);
 constexpr int TUNE_MAX_VARIANTS = 8;
 // the tuned kernels' variant launchers (matvec.cu, lu.cu) and the tuning passes

@@ -2369,10 +2369,7 @@ static int run_lu_tc(Problem& P, cudaStream_t st) {
         return FDE_OK;
     };
     rc = body();
-    // the captured block solves name the layout they read: a change of it retires them
-    const bool ok_now = rc == FDE_OK && strips != nullptr;
-    if (ok_now != P.strips_ok || (ok_now && sbf16 != P.strips_bf16)) ++P.graph_gen;
-    P.strips_ok = ok_now;
+    P.strips_ok = rc == FDE_OK && strips != nullptr;
     P.strips_bf16 = sbf16;
     // join: st continues after all three streams
     cudaEventRecord(P.lu_ev[1], sl);
@@ -2607,12 +2604,16 @@ static int launch_tile_inverse(Problem& P, int prec, cudaStream_t st) {
 
 int launch_block_lu(Problem& P, int prec, cudaStream_t st) {
     int rc;
+    const bool was_ok = P.strips_ok, was_bf16 = P.strips_bf16;
     P.strips_ok = false;  // set by the tensor-core LU once it has written the strip-major copy
     if (prec == FDE_FP64) rc = run_lu<double>(P, st);
     else if (prec == FDE_TF32) rc = run_lu_tc<0>(P, st);
     else if (prec == FDE_BF16) rc = run_lu_tc<1>(P, st);
     else if (prec == FDE_TF32X3) rc = run_lu_tc<2>(P, st);
     else rc = run_lu<float>(P, st);
+    // the captured block solves name the layout they read: a change of it retires them
+    // (a factorisation that keeps the layout keeps the graphs)
+    if (P.strips_ok != was_ok || (P.strips_ok && P.strips_bf16 != was_bf16)) ++P.graph_gen;
     if (rc) return rc;
     return launch_tile_inverse(P, prec, st);
 }
@@ -2689,7 +2690,16 @@ static int launch_trsv_ring(const Problem& P, void* rhat, cudaStream_t st) {
     return FDE_OK;
 }
 
+// The tuning key of the block solves: the storage of the factors they read (FP64,
+// FP32, or FDE_BF16 for the bfloat16 strip copy).
+static int trsv_key(const Problem& P) {
+    if (P.precision == FDE_FP64) return FDE_FP64;
+    return P.strips_ok && P.d_strips && P.strips_bf16 ? FDE_BF16 : FDE_FP32;
+}
+
 int launch_block_trsv_variant(const Problem& P, void* rhat, int variant, cudaStream_t st) {
+    // the ring has no form for the bfloat16 copy: there the register shape 0 stands in for it
+    if (variant == 3 && trsv_key(P) == FDE_BF16) variant = 0;
     if (variant == 3) {  // strips streamed through a shared-memory ring by bulk copies
         if (P.precision == FDE_FP64) return launch_trsv_ring<double>(P, rhat, st);
         return launch_trsv_ring<float>(P, rhat, st);
@@ -2702,13 +2712,6 @@ int launch_block_trsv_variant(const Problem& P, void* rhat, int variant, cudaStr
     if (variant == 1) return launch_trsv_shape<float, 1>(P, rhat, st);
     if (variant == 2) return launch_trsv_shape<float, 2>(P, rhat, st);
     return launch_trsv_shape<float, 0>(P, rhat, st);
-}
-
-// The tuning key of the block solves: the storage of the factors they read (FP64,
-// FP32, or FDE_BF16 for the bfloat16 strip copy).
-static int trsv_key(const Problem& P) {
-    if (P.precision == FDE_FP64) return FDE_FP64;
-    return P.strips_ok && P.d_strips && P.strips_bf16 ? FDE_BF16 : FDE_FP32;
 }
 
 int launch_block_trsv(const Problem& P, void* rhat, cudaStream_t st) {
@@ -2739,8 +2742,9 @@ int autotune_trsv(Problem& P) {
     TrsvTuneCtx ctx{&P, P.d_rhat};
     int best = 0;
     float ms[TUNE_MAX_VARIANTS] = {};
+    // on the bfloat16 copy the three register shapes (the ring reads the FP32 planes)
     const int rc = tune_measure(FDE_TUNE_TRSV, P.stream, trsv_trial, &ctx, &best, ms,
-                                tune_default_variant(FDE_TUNE_TRSV, prec));
+                                tune_default_variant(FDE_TUNE_TRSV, prec), prec == FDE_BF16 ? 3 : 0);
     if (rc) return rc;
     tune_store(FDE_TUNE_TRSV, P.mp, P.nblk, prec, best, ms);
     return FDE_OK;

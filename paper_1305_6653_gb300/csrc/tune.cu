@@ -116,9 +116,9 @@ void tune_store(int kernel, int mp, int nb, int prec, int variant, const float* 
 // default by more than 2 % (launch-to-launch noise), else the default is kept.  fn launches one kernel and returns
 // an FDE status.
 int tune_measure(int kernel, cudaStream_t st, int (*fn)(void*, int, cudaStream_t), void* ctx, int* best,
-                 float* ms_out, int default_variant) {
+                 float* ms_out, int default_variant, int nv_limit) {
     constexpr int ROUNDS = 5;
-    const int nv = tune_variants(kernel);
+    const int nv = nv_limit > 0 && nv_limit < tune_variants(kernel) ? nv_limit : tune_variants(kernel);
     cudaEvent_t ev[2 * ROUNDS * TUNE_MAX_VARIANTS];
     int created = 0, rc = FDE_OK;
     for (; created < 2 * ROUNDS * nv; ++created)

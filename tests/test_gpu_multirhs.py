@@ -173,3 +173,28 @@ def test_refactoring_one_problem_switches_the_factor_layout():
         srel = np.linalg.norm(O.strang_matvec(prob, z, J=J) - r) / np.linalg.norm(r)
         assert srel <= bound, srel
     assert not np.array_equal(out[0], out[1])
+
+
+def test_refactoring_switches_the_factor_storage():
+    """The same precision with another storage of the block solves' factor copy (FP32,
+    bfloat16, FP32 again; m = 500, m_p = 512): each storage is solved twice, so the second
+    solve replays the iteration graphs the first captured, and a graph that still held
+    the previous layout's kernel would read the copy wrongly.  The FP32 solutions agree
+    bit for bit, the bfloat16 ones with each other, and all with the oracle to 1e-8."""
+    from paper_1305_6653_gb300 import FDEProblem
+    prob = fi.manufactured(500, 16, 1.8, "GBDF5", dplus_fn=lambda x: 1 + x, dminus_fn=lambda x: 2 - x)
+    ref, _, ok, _ = O.solve_strang_gmres(prob, side="right", tol=1e-12)
+    assert ok
+    xs = {}
+    with FDEProblem.from_inputs(prob, device_inputs=True) as p:
+        p.assemble()
+        for i, storage in enumerate(("fp32", "bf16", "fp32")):
+            p.factor("tf32", storage=storage)
+            for rep in range(2):
+                x, st = p.solve(tol=1e-11, restart=20, maxit=400)
+                assert st["status"] == 0, (storage, st)
+                xs[(i, rep)] = x.cpu().numpy()
+    for key, x in xs.items():
+        assert np.linalg.norm(x - ref) <= 1e-8 * np.linalg.norm(ref), key
+    assert np.array_equal(xs[(0, 0)], xs[(0, 1)]) and np.array_equal(xs[(0, 0)], xs[(2, 1)])
+    assert np.array_equal(xs[(1, 0)], xs[(1, 1)]) and not np.array_equal(xs[(0, 0)], xs[(1, 0)])

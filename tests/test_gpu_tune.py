@@ -36,15 +36,15 @@ def _case(m=300):
 @pytest.mark.parametrize("precision,m,storage", [("fp64", 300, "fp32"), ("tf32", 300, "fp32"), ("tf32", 500, "fp32"),
                                                  ("bf16", 500, "fp32"), ("tf32", 500, "bf16")])
 def test_variants_are_bit_identical(lib, precision, m, storage):
-    """With storage "bf16" the register shapes read the bfloat16 copy of the factors and
-    the ring shape the FP32 factors, so only the three register shapes are compared."""
+    """With storage "bf16" the register shapes read the bfloat16 copy of the factors; the
+    ring shape has no bfloat16 form, so setting 3 launches shape 0 there."""
     from paper_1305_6653_gb300 import FDEProblem, _lib
     L, _ = lib
     prob = _case(m)
     rng = np.random.default_rng(4)
     z = torch.as_tensor(rng.standard_normal(prob.n), device="cuda")
     outs = []
-    for v in range(4 if storage == "fp32" else 3):  # matvec: 3 shapes (a fourth setting repeats 0); block solves: 4
+    for v in range(4):  # matvec: 3 shapes (the fourth setting repeats shape 0); block solves: 4
         L.fde_tune_set(_lib.FDE_TUNE_MATVEC, v % 3)
         L.fde_tune_set(_lib.FDE_TUNE_TRSV, v)
         with FDEProblem.from_inputs(prob, device_inputs=True) as p:
