@@ -98,6 +98,7 @@ def test_argument_validation_needs_no_gpu(lib):
     d.dplus_t = None
     assert L.bvm_assemble(None) == _lib.FDE_ERR_ARG
     assert L.strang_precond_factor(None, 0) == _lib.FDE_ERR_ARG
+    assert L.fde_factor_storage(None, _lib.STORAGES["bf16"]) == _lib.FDE_ERR_ARG
 
 
 def test_release_of_an_empty_device_cache_needs_no_gpu(lib):

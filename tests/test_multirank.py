@@ -69,3 +69,17 @@ def test_path_roofline_counts():
     vec = sum(4 + 4 * (i % 20 + 1) for i in range(29)) * 8.0 * 2047 * 256
     assert r["iteration_bytes"] == 29 * 129 * (2.0 * 2048 * 2048 * 4 + 4.0 * 2048 * 4) + vec
     assert 0.0 < r["frac"] < 1.0
+
+
+def test_block_solve_bytes_by_factor_storage():
+    """Algorithmic bytes of one block-solve launch: every stored factor entry once (Re and
+    Im planes; 4 bytes in FP32, 2 in the bfloat16 copy) plus the FP32 right-hand side in
+    and out; the whole-path roofline counts the same bytes per iteration."""
+    import bench
+    mp, nblk = 2048, 129
+    assert bench.trsv_bytes(mp, nblk, 4) == nblk * (2.0 * mp * mp * 4 + 4.0 * mp * 4)
+    assert bench.trsv_bytes(mp, nblk, 4, 2) == nblk * (2.0 * mp * mp * 2 + 4.0 * mp * 4)
+    assert abs(bench.trsv_bytes(mp, nblk, 4, 2) - 2.168e9) / 2.168e9 < 1e-3
+    r4 = bench.path_roofline(2047, 256, mp, 4, 26, "tf32", 1900.0, 6800.0, 35.0, restart=30)
+    r2 = bench.path_roofline(2047, 256, mp, 4, 26, "tf32", 1900.0, 6800.0, 35.0, restart=30, fac_esz=2)
+    assert r4["iteration_bytes"] - r2["iteration_bytes"] == 26 * nblk * 2.0 * mp * mp * 2
