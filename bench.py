@@ -458,7 +458,7 @@ def measure_batch(args, steps: int, warmup: int, sequential: bool = True, sample
     b = fde.FDEBatch(probs, device_inputs=True)
 
     def step():
-        b.assemble().factor(args.batch_precision)
+        b.assemble().factor(args.batch_precision, storage=args.storage)
         _, st = b.solve(tol=args.tol, restart=args.restart, maxit=400, outs=outs)
         return st
 
@@ -485,6 +485,7 @@ def measure_batch(args, steps: int, warmup: int, sequential: bool = True, sample
     ms = sum(times) / len(times)
     out = {"value": len(probs) / (ms / 1e3), "unit": "solves/s", "instances": len(probs), "steps": steps,
            "warmup": warmup, "ms_per_step": ms, "per_step_ms": times, "precision": args.batch_precision,
+           "factor_storage": args.storage,
            "tol_true_residual": args.tol, "gpu_launches": launches, "clocks": clocks,
            "iterations": [s_["iterations"] for s_ in stats],
            "unknowns_total": int(sum(p.n for p in probs))}
@@ -495,7 +496,7 @@ def measure_batch(args, steps: int, warmup: int, sequential: bool = True, sample
         e0.record()
         for pr, o in zip(probs, outs):
             with fde.FDEProblem.from_inputs(pr, device_inputs=True) as p:
-                p.assemble().factor(args.batch_precision)
+                p.assemble().factor(args.batch_precision, storage=args.storage)
                 p.solve(tol=args.tol, restart=args.restart, maxit=400, out=o)
         e1.record()
         e1.synchronize()
@@ -523,6 +524,7 @@ def bench_batch(args, world, rank, local_rank):
                 "data": "synthetic",
                 "config": {"workload": "batch64_m255-2047_s64-256_etr3_gbdf3_gam4", "instances": r["instances"],
                            "unknowns_total": r["unknowns_total"], "precision": args.batch_precision,
+                           "factor_storage": args.storage,
                            "tol_true_residual": args.tol, "restart": args.restart,
                            "l2": "flushed (512 MiB write) before every timed step"},
                 "roofline": None, "gpu_launches": r["gpu_launches"], "clocks": r["clocks"],

@@ -166,8 +166,10 @@ int strang_precond_factor(fde_problem* p, int precision);
  *                     tiles enter through their FP32 inverses; the preconditioner is
  *                     then the exact inverse of slightly perturbed factors, which the
  *                     flexible outer iteration in FP64 (true residual) tolerates.
- * Takes effect at the next strang_precond_factor; the factors themselves
- * (fde_get_factor_block) stay FP32.  Errors: FDE_ERR_ARG. */
+ * Takes effect at the next strang_precond_factor, or fde_batch_factor for an instance
+ * of a batch (fde_batch_problem; there only FDE_STORAGE_BF16 makes a copy, and the
+ * instances of a shared operator read the factors themselves); the factors
+ * themselves (fde_get_factor_block) stay FP32.  Errors: FDE_ERR_ARG. */
 #define FDE_STORAGE_FP32 0
 #define FDE_STORAGE_BF16 1
 int fde_factor_storage(fde_problem* p, int storage);
@@ -230,7 +232,9 @@ int fde_batch_create(const fde_problem_desc* descs, int count, void* stream, fde
 int fde_batch_assemble(fde_batch* b);
 
 /* Factor the Strang blocks of every instance in FDE_FP32, FDE_TF32, FDE_BF16 or
- * FDE_TF32X3 (FP32 factor storage).  Errors: FDE_ERR_ARG, FDE_ERR_STATE, FDE_ERR_ALLOC,
+ * FDE_TF32X3 (FP32 factor storage; with the tensor-core precisions an instance set to
+ * FDE_STORAGE_BF16 by fde_factor_storage also gets the bfloat16 copy of its factors
+ * and the FP32 inverses of their diagonal 32 x 32 tiles for its block solves).  Errors: FDE_ERR_ARG, FDE_ERR_STATE, FDE_ERR_ALLOC,
  * FDE_ERR_SINGULAR, FDE_ERR_TIMEOUT, FDE_ERR_CUDA. */
 int fde_batch_factor(fde_batch* b, int precision);
 

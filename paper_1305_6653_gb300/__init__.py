@@ -356,9 +356,15 @@ class FDEBatch:
         _lib.check(_lib.load().fde_batch_assemble(self.h), "fde_batch_assemble")
         return self
 
-    def factor(self, precision="fp32"):
+    def factor(self, precision="fp32", storage="fp32"):
+        """Factor every instance; `storage` ("fp32" or "bf16") is set on each instance
+        (fde_factor_storage) before the batched LU."""
+        L = _lib.load()
+        for i in range(L.fde_batch_size(self.h)):
+            _lib.check(L.fde_factor_storage(C.c_void_p(L.fde_batch_problem(self.h, i)), _lib.STORAGES[storage]),
+                       "fde_factor_storage")
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-        _lib.check(_lib.load().fde_batch_factor(self.h, prec), "fde_batch_factor")
+        _lib.check(L.fde_batch_factor(self.h, prec), "fde_batch_factor")
         return self
 
     def solve(self, tol=1e-10, restart=20, maxit=1000, reorth=1, outs=None, raise_on_error=True):

@@ -315,6 +315,26 @@ int fde_batch_factor(fde_batch* b, int precision) {
         if (rc) return rc;
         P.factored = false;
         P.precision = precision;
+        // an instance set to FDE_STORAGE_BF16 (tensor-core LU, m_p a multiple of 128) gets the
+        // bfloat16 strip-major copy of its factors for the block solves; without the memory
+        // for it, its solves read the planes
+        P.strips_ok = false;
+        unsigned short* strips = nullptr;
+        if (kind >= 0 && P.strip_storage == FDE_STORAGE_BF16 && P.mp % 128 == 0) {
+            const size_t sneed = (size_t)P.nblk * 2 * P.mp * P.mp * sizeof(unsigned short);
+            if (P.strips_bytes < sneed) {
+                if (P.d_strips) {
+                    FDE_CUDA_TRY(cudaStreamSynchronize(b->stream));
+                    dev_free(P.d_strips);
+                }
+                P.d_strips = nullptr;
+                P.strips_bytes = 0;
+                if (dev_alloc(&P.d_strips, sneed) == FDE_OK) P.strips_bytes = sneed;
+                else set_error(FDE_OK, "");
+            }
+            strips = static_cast<unsigned short*>(P.d_strips);
+        }
+        P.strips_bf16 = strips != nullptr;
         const size_t pack_a = tc_pack_a_bytes_per_block(precision, P.mp);
         const size_t pack_all = tc_pack_bytes_per_block(precision, P.mp);
         for (int k = 0; k < P.nblk; ++k) {
@@ -334,6 +354,7 @@ int fde_batch_factor(fde_batch* b, int precision) {
             d.fac = (float*)P.d_fac + (size_t)k * 2 * P.mp * P.mp;
             d.dinv = (float2*)P.d_dinv + (size_t)k * P.mp;
             d.info = P.d_info + k;
+            d.strips = strips ? strips + (size_t)k * 2 * P.mp * P.mp : nullptr;
             if (kind >= 0) {
                 d.apack = (unsigned char*)pack_total;  // offset, rebased below
                 pack_total += pack_all;
@@ -386,6 +407,14 @@ int fde_batch_factor(fde_batch* b, int precision) {
             if (infos[i][k])
                 return set_error(FDE_ERR_SINGULAR, "zero or non-finite pivot in instance " + std::to_string(i) +
                                                        ", block " + std::to_string(k));
+    // the FP32 inverses of the diagonal tiles, through which the solves from a bfloat16 copy
+    // apply the diagonal tiles
+    for (fde_problem* p : b->probs) {
+        Problem& P = *problem_of(p);
+        if (!P.strips_bf16) continue;
+        if ((rc = launch_tile_inverse_fp32(P, b->stream))) return rc;
+        P.strips_ok = true;
+    }
     for (fde_problem* p : b->probs) problem_of(p)->factored = true;
     b->precision = precision;
     b->factored = true;
@@ -424,6 +453,10 @@ int fde_batch_solve(fde_batch* b, const fde_pgmres_opts* opts, double* const* x_
             d.rhat = (unsigned char*)b->d_rhat_shared + (size_t)i * P0.nblk * P0.mp * 2 * sizeof(float);
         } else {
             d.rhat = P.d_rhat; d.fac = P.d_fac; d.dinv = P.d_dinv; d.tinv = nullptr;
+            if (P.strips_ok && P.strips_bf16 && P.d_strips) {  // the bfloat16 copy and the tile inverses
+                d.strips = P.d_strips;
+                d.tinv = P.d_tinv;
+            }
         }
         // host solution arrays (the instance's desc->device_ptrs == 0): solve into the
         // instance's device copy, copied out when the batch is done

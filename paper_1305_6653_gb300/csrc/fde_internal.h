@@ -66,6 +66,7 @@ struct InstDev {
     void* fac;
     void* dinv;
     void* tinv;            // inverted 32 x 32 diagonal tiles of the factors, or NULL
+    const void* strips;    // bfloat16 strip-major copy of the factors (with tinv), or NULL
     double* b;
     double* x;
     double* V;
@@ -99,6 +100,7 @@ struct BlkDev {
     unsigned char* bpack;
     unsigned char* ipack;  // L11^{-1} (A') and U11^{-1} (B') tiles of the current panel
     int* info;
+    unsigned short* strips;  // this block's bfloat16 strip-major copy (Re then Im), or NULL
 };
 
 // ---------------------------------------------------------------------------
@@ -131,6 +133,8 @@ int launch_time_fft_inv(const Problem& P, const void* xhat, double* z, int prec,
 
 // lu.cu
 int launch_block_lu(Problem& P, int prec, cudaStream_t st);
+// The FP32 inverses of the 32 x 32 diagonal tiles of P's factors (P.d_tinv).
+int launch_tile_inverse_fp32(Problem& P, cudaStream_t st);
 int launch_block_trsv(const Problem& P, void* rhat, cudaStream_t st);
 
 // krylov.cu

@@ -1107,6 +1107,14 @@ block_trsv_batched(const InstDev* __restrict__ I, const int* __restrict__ act) {
     const T* fac = (const T*)d.fac + (size_t)k * 2 * mp * mp;
     const cplx_t<T>* dinv = (const cplx_t<T>*)d.dinv + (size_t)k * mp;
     cplx_t<T>* rhat = (cplx_t<T>*)d.rhat + (size_t)k * mp;
+    if constexpr (sizeof(T) == 4) {
+        if (d.strips) {  // the bfloat16 strip copy, diagonal tiles through their FP32 inverses
+            trsv_body<T, true, TRSV_THREADS, trsv_unroll<T>::value / 2, LAY_STRIPS_BF16>(
+                d.mp, (const unsigned short*)d.strips + (size_t)k * 2 * mp * mp, dinv,
+                (const T*)d.tinv + (size_t)k * (mp / 32) * 4096, rhat);
+            return;
+        }
+    }
     if (d.tinv)  // diagonal tiles solved as products with their inverses
         trsv_body<T, true>(d.mp, fac, dinv, (const T*)d.tinv + (size_t)k * (mp / 32) * 4096, rhat);
     else
@@ -2027,7 +2035,8 @@ lu_diag128_kernel(int mp, int o, float* __restrict__ fac, float2* __restrict__ d
 template <int KIND>
 __global__ void __launch_bounds__(D128_THREADS) lu_diag128_batched(const BlkDev* __restrict__ B, int o) {
     const BlkDev& d = B[blockIdx.x];
-    diag128_body<KIND>(d.mp, o, (float*)d.fac, (float2*)d.dinv, d.info, d.ipack, o + TB < d.mp);
+    diag128_body<KIND>(d.mp, o, (float*)d.fac, (float2*)d.dinv, d.info, d.ipack, o + TB < d.mp, nullptr, d.strips,
+                       true);
 }
 
 // Operand tiles of the current panels: rows R0.. of columns o..o+128 (A21 or L21)
@@ -2132,11 +2141,13 @@ lu_panel_tc2_batched(const BlkDev* __restrict__ B, int o, int R0, int ntg, int* 
     if (x < ntg) {
         if (x >= nt) return;
         unsigned char* at = d.apack + (size_t)x * Cfg::A_TILE;
-        tc2_tile_body<KIND, true>(d.mp, R0 + x * T2_BM, o, re, at, d.ipack + Cfg::A_TILE, err, at, 0);
+        tc2_tile_body<KIND, true>(d.mp, R0 + x * T2_BM, o, re, at, d.ipack + Cfg::A_TILE, err, at, 0, nullptr, nullptr,
+                                  nullptr, nullptr, 0, d.strips);
     } else {
         if (x - ntg >= nt) return;
         unsigned char* bt = d.bpack + (size_t)(x - ntg) * Cfg::B_TILE;
-        tc2_tile_body<KIND, true>(d.mp, o, R0 + (x - ntg) * T2_BN, re, d.ipack, bt, err, bt, 1);
+        tc2_tile_body<KIND, true>(d.mp, o, R0 + (x - ntg) * T2_BN, re, d.ipack, bt, err, bt, 1, nullptr, nullptr,
+                                  nullptr, nullptr, 0, d.strips);
     }
 }
 
@@ -2426,7 +2437,7 @@ static int run_lu_batched_tc(const BlkDev* d_blk, const std::vector<int>& mps, i
     FDE_CUDA_TRY(cudaFuncSetAttribute(lu_diag128_batched<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)diag128_smem()));
     FDE_CUDA_TRY(cudaFuncSetAttribute(lu_panel_tc2_batched<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      Cfg::SMEM_STORE));
+                                      Cfg::SMEM_STORE_EPI));
     auto active = [&](int lim) {  // blocks with m_p > lim (a prefix of the sorted table)
         int n = 0;
         while (n < nbt && mps[n] > lim) ++n;
@@ -2446,7 +2457,7 @@ static int run_lu_batched_tc(const BlkDev* d_blk, const std::vector<int>& mps, i
         const int pgrid = (int)std::min<long>((items + 255) / 256, 1024);
         lu_pack_panel_batched<KIND><<<dim3(pgrid, nact), 256, 0, st>>>(d_blk, o, R0);
         FDE_LAUNCH_CHECK("lu_pack_panel_batched");
-        lu_panel_tc2_batched<KIND><<<dim3(2 * ntg, nact), 128, Cfg::SMEM_STORE, st>>>(d_blk, o, R0, ntg, err);
+        lu_panel_tc2_batched<KIND><<<dim3(2 * ntg, nact), 128, Cfg::SMEM_STORE_EPI, st>>>(d_blk, o, R0, ntg, err);
         FDE_LAUNCH_CHECK("lu_panel_tc2_batched");  // also packs L21 / U12
         lu_update_tc2p_batched<KIND><<<dim3(((ntg + 1) / 2) * ntg, nact), 128, Tc2p<KIND>::SMEM, st>>>(d_blk, R0,
                                                                                                      ntg, err);
@@ -2602,6 +2613,8 @@ static int launch_tile_inverse(Problem& P, int prec, cudaStream_t st) {
     FDE_LAUNCH_CHECK("tile_inverse_kernel");
     return FDE_OK;
 }
+
+int launch_tile_inverse_fp32(Problem& P, cudaStream_t st) { return launch_tile_inverse(P, FDE_FP32, st); }
 
 int launch_block_lu(Problem& P, int prec, cudaStream_t st) {
     int rc;

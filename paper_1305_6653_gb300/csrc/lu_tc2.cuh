@@ -395,7 +395,8 @@ __device__ __forceinline__ void tc2_tile_body(int mp, int r0, int c0, float* __r
         // row-major planes (fmap) and to the strip-major copy (smap), where the strip's 128
         // rows are one contiguous 16 KB range; or, for a bfloat16 copy (sbf: this block's), the
         // strip also staged as bfloat16 rows of 64 bytes and stored by one bulk copy of 8 KB
-        // per plane.  Whole tiles only (m_p a multiple of 128).
+        // per plane (without fmap -- the blocks of a batch have no common tensor map -- the
+        // planes are then written from registers).  Whole tiles only (m_p a multiple of 128).
         const int r = warp * 32 + lane;  // TMEM lane = tile row
         const uint32_t lane_addr = tbase + ((uint32_t)(warp * 32) << 16);
         unsigned char* sbuf = smem + ((1024u - (tc::smem_u32(smem) & 1023u)) & 1023u);
@@ -418,13 +419,25 @@ __device__ __forceinline__ void tc2_tile_body(int mp, int r0, int c0, float* __r
                 tc::tmem_ld16(lane_addr + ch * 16, dr);
                 tc::tmem_ld16(lane_addr + T2_BN + ch * 16, di);
                 tc::tmem_ld_wait();
+                if (fmap) {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int off = r * 128 + (((4 * h + q) ^ (r & 7)) << 4);
-                    *reinterpret_cast<float4*>(bre + off) =
-                        make_float4(dr[4 * q], dr[4 * q + 1], dr[4 * q + 2], dr[4 * q + 3]);
-                    *reinterpret_cast<float4*>(bim + off) =
-                        make_float4(di[4 * q], di[4 * q + 1], di[4 * q + 2], di[4 * q + 3]);
+                    for (int q = 0; q < 4; ++q) {
+                        const int off = r * 128 + (((4 * h + q) ^ (r & 7)) << 4);
+                        *reinterpret_cast<float4*>(bre + off) =
+                            make_float4(dr[4 * q], dr[4 * q + 1], dr[4 * q + 2], dr[4 * q + 3]);
+                        *reinterpret_cast<float4*>(bim + off) =
+                            make_float4(di[4 * q], di[4 * q + 1], di[4 * q + 2], di[4 * q + 3]);
+                    }
+                } else {
+                    float* pr = gre + (size_t)(r0 + r) * mp + c0 + ch * 16;
+                    float* pi = gim + (size_t)(r0 + r) * mp + c0 + ch * 16;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        reinterpret_cast<float4*>(pr)[q] =
+                            make_float4(dr[4 * q], dr[4 * q + 1], dr[4 * q + 2], dr[4 * q + 3]);
+                        reinterpret_cast<float4*>(pi)[q] =
+                            make_float4(di[4 * q], di[4 * q + 1], di[4 * q + 2], di[4 * q + 3]);
+                    }
                 }
                 if (sbf) {  // columns 16 h .. 16 h + 15 of row r: 32 bytes per plane
                     uint32_t wr[8], wi[8];
@@ -460,8 +473,10 @@ __device__ __forceinline__ void tc2_tile_body(int mp, int r0, int c0, float* __r
             __syncthreads();
             if (threadIdx.x == 0) {
                 const int col = c0 + 32 * sx;
-                tma2d_store(fmap, col, yf + r0, bre);
-                tma2d_store(fmap, col, yf + mp + r0, bim);
+                if (fmap) {
+                    tma2d_store(fmap, col, yf + r0, bre);
+                    tma2d_store(fmap, col, yf + mp + r0, bim);
+                }
                 if (sbf) {  // 128 rows of strip col / 32 from row r0: 8 KB contiguous per plane
                     unsigned short* g = sbf + (size_t)(col >> 5) * 32 * mp + (size_t)r0 * 32;
                     bulk_s2g(g, hre, 8192);

@@ -64,6 +64,32 @@ def test_batch_matches_oracle(precision):
         assert st["iterations"] <= 2 * prob.m * prob.mu + 1  # Theorem 3.3 bound
 
 
+@pytest.mark.parametrize("precision", ["tf32", "tf32x3"])
+def test_batch_bf16_factor_storage(precision):
+    """Instances set to bfloat16 storage with whole 128-wide panels (m_p = 128 and 256
+    here) solve from the bfloat16 copy of their factors, with the FP32 inverses of the
+    diagonal tiles; the others (m_p = 64, 192) from the planes, as with FP32 storage.
+    Every solution against the oracle (1e-8); the instances without the copy run
+    bit-identically in both batches, the others differ (it is the copy that is read)."""
+    from paper_1305_6653_gb300 import FDEBatch
+    probs = _mixed_batch()
+    out = {}
+    for storage in ("fp32", "bf16"):
+        with FDEBatch(probs) as b:
+            b.assemble().factor(precision, storage=storage)
+            xs, stats = b.solve(tol=1e-11, restart=20, maxit=400)
+            out[storage] = ([x.cpu().numpy() for x in xs], stats)
+    for prob, x, st in zip(probs, *out["bf16"]):
+        ref = _reference(prob)
+        err = np.linalg.norm(x - ref) / np.linalg.norm(ref)
+        assert st["status"] == 0, (prob.name, st)
+        assert err <= 1e-8, (prob.name, err, st)
+    for i, prob in enumerate(probs):
+        mp = (prob.m + 63) // 64 * 64
+        same = np.array_equal(out["fp32"][0][i], out["bf16"][0][i])
+        assert same == (mp % 128 != 0), (prob.name, mp)
+
+
 def test_batch_iterations_match_single_solves():
     from paper_1305_6653_gb300 import FDEBatch, FDEProblem
     probs = _mixed_batch()
