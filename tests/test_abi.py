@@ -129,3 +129,19 @@ def test_tune_table_is_host_side(tmp_path):
     assert lib.fde_tune_query(1, 2048, 129, 1, C.byref(v)) == 0 and v.value == 0  # forced
     assert lib.fde_tune_set(1, -1) == 0
     assert lib.fde_tune_cache(None) == 0
+
+
+def test_binding_constants_match_header():
+    """The binding's enumerations (precisions, factor storages, block solvers, tuner
+    kernels) have the values the header defines."""
+    from paper_1305_6653_gb300 import PRECISIONS, _lib
+    defines = dict((k, int(v)) for k, v in re.findall(r"^#define\s+(FDE_\w+)\s+(-?\d+)", open(HEADER).read(), re.M))
+    for name, value in {"fp64": "FDE_FP64", "fp32": "FDE_FP32", "tf32": "FDE_TF32", "bf16": "FDE_BF16",
+                        "tf32x3": "FDE_TF32X3"}.items():
+        assert PRECISIONS[name] == defines[value], name
+    assert _lib.STORAGES == {"fp32": defines["FDE_STORAGE_FP32"], "bf16": defines["FDE_STORAGE_BF16"]}
+    assert _lib.BLOCK_SOLVERS == {"auto": defines["FDE_BLOCK_SOLVE_AUTO"],
+                                  "cuda_cores": defines["FDE_BLOCK_SOLVE_CUDA_CORES"],
+                                  "tensor_cores": defines["FDE_BLOCK_SOLVE_TENSOR_CORES"]}
+    assert (_lib.FDE_TUNE_MATVEC, _lib.FDE_TUNE_TRSV, _lib.FDE_TUNE_LU) == (
+        defines["FDE_TUNE_MATVEC"], defines["FDE_TUNE_TRSV"], defines["FDE_TUNE_LU"])
